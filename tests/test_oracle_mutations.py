@@ -1,0 +1,76 @@
+"""Planted mistakes in the oracle (on the CPU) must be caught by its pins.
+
+Each case patches one step of the oracle with a plausible error and checks
+that the corresponding pin quantity moves far outside its tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fmg_oracle as O
+from paper_1611_05677_gb300 import workloads as W
+
+
+def _closed_form_error(dim=2, H=4, r=2, c=2.0):
+    prob = W.Problem(dim=dim, coarse_cells=H, refinements=r, f="linear", a=c, modes=[((1,) * dim, 1.0)])
+    hier = O.build_hierarchy(dim, H, r)
+    lev = hier.level(r + 1)
+    h = lev.h
+    mu = 4 * dim * math.sin(math.pi * h / 2) ** 2 * h ** (dim - 2)
+    lam = h ** dim * (dim * math.pi ** 2 + c) / (mu + c * h ** dim)
+    res = O.fmg(hier, prob.g_nodal(), "linear", c, m=2, p=10)
+    return float(np.max(np.abs(res.u[-1] - lam * O.from_nodal(lev, prob.u_star()))))
+
+
+def test_unmutated_baseline():
+    assert _closed_form_error() < 1e-12
+
+
+def test_dropped_quadrature_weight_is_caught(monkeypatch):
+    monkeypatch.setattr(O, "load_vector", lambda lev, g: g.ravel()[lev.interior])
+    assert _closed_form_error() > 1e-3
+
+
+def test_wrong_coarse_correction_sign_is_caught(monkeypatch):
+    orig = O.prolongation
+
+    def bad(dim, nc):
+        P = orig(dim, nc).tolil()
+        P[0, :] = -P[0, :]          # one wrong row
+        return P.tocsr()
+
+    monkeypatch.setattr(O, "prolongation", bad)
+    Ac = O.assemble_level(2, 4).A
+    Af = O.assemble_level(2, 8).A
+    P = O.prolongation(2, 4)
+    assert abs(P.T @ Af @ P - Ac).max() > 0.1
+
+
+def test_dropped_nonlinear_term_in_linearized_rhs_is_caught(monkeypatch):
+    """Algorithm 3.1 step 1 without -(f(x,u),v): the augmented solve still fixes
+    the answer only up to the V_H + span{u~} approximation, so the FMG result
+    drifts from the discrete solution beyond the accuracy criterion."""
+    # patch the correction step to skip the nonlinear RHS term
+    def bad_step(hier, k, u, G, kind, a, m=2, nu_pre=2, nu_post=2, tol=1e-12):
+        lev = hier.level(k)
+        b = G.copy()
+        ut = u.copy()
+        for _ in range(m):
+            ut = O.vcycle(hier, k, b, ut, nu_pre, nu_post)
+        y, B, it = O.augmented_newton(lev, hier.P_H[k - 1], ut, G, kind, a, tol)
+        return B @ y, O.StepInfo(newton_iters=it)
+
+    prob = W.Problem(dim=2, coarse_cells=4, refinements=3, f="cubic", a=1.0,
+                     modes=[((1, 1), 1.0), ((2, 1), 0.5)])
+    hier = O.build_hierarchy(2, 4, 3)
+    g = prob.g_nodal()
+    lev = hier.level(4)
+    G = O.load_vector(lev, g)
+    ub, _ = O.newton_full(lev, G, prob.f, prob.a)
+    good = O.fmg(hier, g, prob.f, prob.a).u[-1]
+    monkeypatch.setattr(O, "correction_step", bad_step)
+    bad = O.fmg(hier, g, prob.f, prob.a).u[-1]
+    e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star()))
+    assert O.discrete_l2(lev, good - ub) <= 0.1 * e_disc
+    assert O.discrete_l2(lev, bad - ub) > 1.0 * e_disc
