@@ -1,0 +1,197 @@
+/*
+ * fmg.h -- C ABI of the GB300 (sm_103a) full multigrid solver for semilinear
+ * elliptic problems
+ *
+ *     -Laplace(u) + a f(u) = g  in Omega = (0,1)^d,  u = 0 on the boundary,
+ *
+ * discretized by P1 finite elements on nested, uniformly refined meshes
+ * (2D: right triangles split along the (0,0)-(1,1) diagonal; 3D: Kuhn
+ * tetrahedra), following H. Xie and F. Xu, "A full multigrid method for
+ * semilinear elliptic equation" (arXiv 1611.05677):
+ *
+ *   - the model problem and its discretization: Sec. 2, eq. (2.1)-(2.7);
+ *   - the nested mesh sequence T_H = T_{h_1} .. T_{h_n}, h_k = h_{k-1}/2:
+ *     Sec. 3, eq. (3.1)-(3.3);
+ *   - one correction step (linearized boundary value problem solved by m
+ *     multigrid cycles, then the semilinear problem on V_H + span{u~}):
+ *     Algorithm 3.1, eq. (3.4)-(3.6);
+ *   - the full multigrid schedule: Algorithm 3.2.
+ *
+ * Discretization conventions (fixed by this library where the paper leaves
+ * them open): h_1 = H; the pairings (f(x,u),v) and (g,v) use the vertex
+ * (mass-lumped) rule on the current mesh, so the weight of an interior node is
+ * h^d; the multigrid cycle is V(nu_pre, nu_post) with red-black Gauss-Seidel
+ * (red = even i+j[+l]; pre-smoothing red then black, post-smoothing black then
+ * red), restriction P^T, prolongation P (the natural inclusion of P1 spaces)
+ * and an exact solve on level 1; the augmented problem (3.6) is solved by
+ * Newton's method from (c, alpha) = (0, 1).
+ *
+ * Array layout.  Every nodal array of a level with n cells per side holds
+ * (n+1)^d doubles (or floats), boundary nodes included, x fastest:
+ * node (i, j[, l]) is at offset i + (n+1) (j + (n+1) l).  Boundary entries of
+ * arrays the library writes are zero.
+ *
+ * Errors.  No function aborts, throws or exits.  Each returns an fmg_status;
+ * the message of the last failure is available from fmg_last_error (per
+ * context, or per thread for failures without a context).  All device waits
+ * inside the library are bounded; a wait that runs out returns
+ * FMG_ERR_TIMEOUT.  A context is bound to one CUDA stream and is not thread
+ * safe; distinct contexts may be used from distinct threads.
+ */
+#ifndef FMG_H
+#define FMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmg_ctx fmg_ctx;
+
+typedef enum {
+  FMG_OK = 0,
+  FMG_ERR_INVALID = 1,         /* bad argument (sizes, enum values, NULL pointer) */
+  FMG_ERR_OOM = 2,             /* not enough device memory (checked before allocating) */
+  FMG_ERR_NO_CONVERGENCE = 3,  /* a Newton iteration hit its cap or its matrix was not SPD */
+  FMG_ERR_NONFINITE = 4,       /* NaN/Inf in the data or in an iterate */
+  FMG_ERR_TIMEOUT = 5,         /* a bounded device wait ran out */
+  FMG_ERR_CUDA = 6             /* a CUDA runtime call failed; see fmg_last_error */
+} fmg_status;
+
+/* Nonlinearities a*f(u); all are monotone for a > 0 (Assumption A, eq. 2.5). */
+typedef enum {
+  FMG_F_CUBIC = 0,         /* a u^3               (Sec. 4, Example 1) */
+  FMG_F_EXPM1 = 1,         /* a (exp(u) - 1) */
+  FMG_F_LINEAR = 2,        /* a u                 (closed-form test case) */
+  FMG_F_SIGNED_POW32 = 3,  /* a sign(u)|u|^{3/2}  (Sec. 4, Example 3) */
+  FMG_F_NEG_EXP_NEG = 4    /* -a exp(-u)          (Sec. 4, Example 2) */
+} fmg_nonlin;
+
+typedef enum {
+  FMG_PREC_FP64 = 0,   /* every step in FP64 */
+  FMG_PREC_MIXED = 1   /* multigrid cycles in FP32 inside an FP64 defect-correction loop:
+                          FP64 residual and update on the cycle's top level, FP64 coarsest
+                          solve, FP64 augmented Newton and its quadrature sums */
+} fmg_precision;
+
+typedef struct {
+  int dim;             /* 2 or 3 */
+  int coarse_cells;    /* 1/H: cells per side of T_H; even; 2D <= 8, 3D <= 4 (the augmented
+                          system of size N_H + 1 <= 50 is solved densely on one SM) */
+  int refinements;     /* n - 1 >= 0: levels 1..refinements+1 (Sec. 3, eq. 3.1) */
+  int f;               /* fmg_nonlin */
+  double f_scale;      /* a > 0 */
+  int m_vcycles;       /* m >= 1: multigrid cycles per correction step (Algorithm 3.1) */
+  int nu_pre;          /* >= 0 pre-smoothing sweeps */
+  int nu_post;         /* >= 0 post-smoothing sweeps */
+  int p_corrections;   /* p >= 1: correction steps per level (Algorithm 3.2) */
+  int precision;       /* fmg_precision */
+  double newton_tol;   /* augmented Newton stops when ||delta||_inf <= tol max(1, ||y||_inf) */
+  int newton_maxit;    /* augmented Newton iteration cap (<= 64) */
+  double level1_tol;   /* same rule for the exact solve on level 1 */
+  int level1_maxit;    /* level-1 Newton iteration cap (<= 64) */
+} fmg_params;
+
+typedef struct {
+  int levels;               /* n */
+  int level1_iters;         /* Newton iterations of the level-1 solve */
+  int newton_iters[32];     /* augmented Newton iterations on level k at index k-1 (summed over p) */
+  double alpha[32];         /* final alpha of the last correction step on level k at index k-1 */
+  unsigned int flags;       /* bit 0: a Newton cap was hit; bit 1: non-finite value; bit 2: u~
+                               was (numerically) inside V_H and was dropped; bit 3: a matrix
+                               was not SPD; bit 4: a device wait timed out */
+} fmg_stats;
+
+/* Defaults: dim 2, 1/H = 4, 4 refinements, cubic, a = 1, m = 2, nu = 2/2, p = 1 (the
+ * schedule of Sec. 4: m = 2, p = 1), FP64, Newton tol 1e-12 / cap 20, level-1 tol 1e-13 /
+ * cap 50. */
+void fmg_default_params(fmg_params* p);
+
+/* Device bytes one context needs for these parameters (the workspace size fmg_create
+ * expects when the caller provides the memory).  Returns FMG_ERR_INVALID for bad params. */
+fmg_status fmg_workspace_bytes(const fmg_params* p, size_t* bytes);
+
+/* Creates a context for one problem.
+ *   g_fine       nodal values of g on the finest mesh ((n_fine+1)^d doubles, layout above;
+ *                boundary entries are ignored).  Host or device memory (g_on_device).  The
+ *                library copies it; the caller keeps ownership of its buffer.
+ *   stream       cudaStream_t (as void*) all work of this context is ordered on; NULL = the
+ *                legacy default stream.
+ *   workspace    device memory of at least fmg_workspace_bytes bytes that the context uses
+ *                for all its arrays, owned by the caller and kept alive until fmg_destroy; or
+ *                NULL, in which case the library allocates (cudaMalloc) and frees it itself.
+ * On success *out receives the context.  Returns FMG_ERR_OOM when the device does not have
+ * the memory (checked with cudaMemGetInfo before allocating). */
+fmg_status fmg_create(const fmg_params* p, const double* g_fine, int g_on_device, void* stream,
+                      void* workspace, size_t workspace_bytes, fmg_ctx** out);
+
+/* Replaces g (same layout and ownership rules as fmg_create).  Host input is copied
+ * through a pageable or pinned buffer as given; the copy is ordered on the context stream. */
+fmg_status fmg_set_rhs(fmg_ctx* c, const double* g_fine, int g_on_device);
+
+/* Runs Algorithm 3.2 and writes u_{h_n} ((n_fine+1)^d doubles, boundary zero) to u_out,
+ * device or host memory (out_on_device).  The whole schedule is one CUDA graph, captured on
+ * the first call and replayed afterwards.  With out_on_device = 1 and st = NULL the call is
+ * asynchronous on the context stream and convergence problems are reported by the next call
+ * that synchronizes (fmg_solve with st != NULL or host output, or fmg_sync).  Otherwise it
+ * waits for the stream and checks the device status flags. */
+fmg_status fmg_solve(fmg_ctx* c, double* u_out, int out_on_device, fmg_stats* st);
+
+/* Waits for the context stream and returns the status accumulated by earlier asynchronous
+ * solves (and fills st when non-NULL). */
+fmg_status fmg_sync(fmg_ctx* c, fmg_stats* st);
+
+/* Solves several independent problems (contexts created on the same device), each with
+ * its own u_out (device pointers), ordered on the first context's stream. */
+fmg_status fmg_solve_batch(fmg_ctx** cs, int count, double** u_outs, fmg_stats* sts);
+
+/* Frees the context (and the workspace when the library allocated it).  NULL-safe. */
+fmg_status fmg_destroy(fmg_ctx* c);
+
+/* Message of the last failure on c, or of the calling thread when c is NULL. */
+const char* fmg_last_error(const fmg_ctx* c);
+
+/* Device pointer of the fine-level solution u_{h_n} inside the context ((n_fine+1)^d doubles,
+ * layout above), valid until the next fmg_solve or fmg_destroy; NULL for a NULL context.  A
+ * solve called with u_out = NULL leaves its result only here. */
+const double* fmg_solution(const fmg_ctx* c);
+
+/* Number of levels n and cells per side of level k (1-based), or -1 for bad arguments. */
+int fmg_levels(const fmg_ctx* c);
+int fmg_level_cells(const fmg_ctx* c, int level);
+
+/* ---------------------------------------------------------------------------------------
+ * Component operations.  They run one step of the method on caller-owned DEVICE arrays in
+ * the nodal layout of the given level, ordered on the context stream, and wait for it.
+ * They use the context's scratch arrays, so they must not overlap a running fmg_solve.
+ * ------------------------------------------------------------------------------------- */
+
+/* `sweeps` red-black Gauss-Seidel sweeps on A_k u = b at level k (the smoother of the
+ * multigrid steps of Algorithm 3.1 step 1).  order 0: red then black; 1: black then red. */
+fmg_status fmg_op_smooth(fmg_ctx* c, int level, const double* b, double* u, int sweeps, int order);
+fmg_status fmg_op_smooth_f32(fmg_ctx* c, int level, const float* b, float* u, int sweeps, int order);
+
+/* r = b - A_k u at level k (the residual of the linear system of eq. 3.4). */
+fmg_status fmg_op_residual(fmg_ctx* c, int level, const double* b, const double* u, double* r);
+
+/* `cycles` V-cycles on A_k u = b from the initial guess in u (eq. 3.5), with the context's
+ * nu_pre/nu_post and precision (FMG_PREC_MIXED: FP64 residual -> FP32 cycle -> FP64 update). */
+fmg_status fmg_op_vcycle(fmg_ctx* c, int level, const double* b, double* u, int cycles);
+
+/* One correction step u <- SemilinearMG(V_H, u, V_{h_k}) of Algorithm 3.1 at level k >= 2,
+ * with the context's g (restricted to level k), m and precision.  Newton iterations and
+ * alpha go to st (index k-1) when st is non-NULL. */
+fmg_status fmg_op_correction_step(fmg_ctx* c, int level, double* u, fmg_stats* st);
+
+/* Exact semilinear solve on level 1 (Algorithm 3.2 step 1) into u (level-1 layout). */
+fmg_status fmg_op_level1_solve(fmg_ctx* c, double* u, fmg_stats* st);
+
+/* u_fine = P_k u_coarse: the natural inclusion V_{h_{k-1}} -> V_{h_k} (eq. 3.3), k >= 2. */
+fmg_status fmg_op_prolong(fmg_ctx* c, int level, const double* u_coarse, double* u_fine);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMG_H */

@@ -1,0 +1,510 @@
+// Host side of the C ABI declared in include/fmg.h: the level hierarchy, the schedule of
+// Algorithm 3.2 (full multigrid) and Algorithm 3.1 (one correction step), CUDA-graph capture
+// of the whole solve, and the component operations.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fmg_internal.cuh"
+
+using namespace fmg;
+
+struct fmg_ctx {
+  fmg_params p;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int nlev = 0;
+  LevelGeo geo[kMaxLevels];
+  double* u[kMaxLevels] = {};
+  double* b[kMaxLevels] = {};
+  double* g[kMaxLevels] = {};
+  float* u32[kMaxLevels] = {};
+  float* b32[kMaxLevels] = {};
+  double* Ainv = nullptr;
+  DevState* st = nullptr;
+  AugBuffers ab = {};
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool own_arena = false;
+  bool own_stream = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  unsigned pending_flags = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string t_err;
+
+fmg_status fail(fmg_ctx* c, fmg_status s, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    t_err = msg;
+  return s;
+}
+
+#define CK(ctx, expr)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail((ctx), FMG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+const char* validate(const fmg_params* p) {
+  if (!p) return "params is NULL";
+  if (p->dim != 2 && p->dim != 3) return "dim must be 2 or 3";
+  if (p->coarse_cells < 2 || (p->coarse_cells & 1)) return "coarse_cells must be even and >= 2";
+  if (p->dim == 2 && p->coarse_cells > 8) return "2D coarse_cells must be <= 8 (dense augmented system)";
+  if (p->dim == 3 && p->coarse_cells > 4) return "3D coarse_cells must be <= 4 (dense augmented system)";
+  if (p->refinements < 0 || p->refinements >= kMaxLevels - 1) return "refinements out of range";
+  const long long nf = (long long)p->coarse_cells << p->refinements;
+  if (p->dim == 2 && nf > 32768) return "2D fine mesh larger than 32768 cells per side";
+  if (p->dim == 3 && nf > 1024) return "3D fine mesh larger than 1024 cells per side";
+  if (p->f < 0 || p->f > 4) return "unknown nonlinearity";
+  if (!(p->f_scale > 0.0) || !std::isfinite(p->f_scale)) return "f_scale must be finite and > 0";
+  if (p->m_vcycles < 1 || p->m_vcycles > 64) return "m_vcycles must be in 1..64";
+  if (p->nu_pre < 0 || p->nu_post < 0 || p->nu_pre > 64 || p->nu_post > 64) return "nu out of range";
+  if (p->p_corrections < 1 || p->p_corrections > 64) return "p_corrections must be in 1..64";
+  if (p->precision != FMG_PREC_FP64 && p->precision != FMG_PREC_MIXED) return "unknown precision";
+  if (!(p->newton_tol > 0.0) || !(p->level1_tol > 0.0)) return "tolerances must be > 0";
+  if (p->newton_maxit < 1 || p->newton_maxit > kMaxNewton) return "newton_maxit must be in 1..64";
+  if (p->level1_maxit < 1 || p->level1_maxit > kMaxNewton) return "level1_maxit must be in 1..64";
+  return nullptr;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Lays out (or only sizes, when base == nullptr) every device array of a context.
+size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* r = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return r;
+  };
+  const int nlev = p->refinements + 1;
+  for (int k = 0; k < nlev; ++k) {
+    const int n = p->coarse_cells << k;
+    const long long nodes = ipow(n + 1, p->dim);
+    if (c) {
+      c->geo[k].n = n;
+      c->geo[k].np = n + 1;
+      c->geo[k].nodes = nodes;
+    }
+    double* u = (double*)take(nodes * 8);
+    double* b = (double*)take(nodes * 8);
+    double* g = (double*)take(nodes * 8);
+    float* u32 = nullptr;
+    float* b32 = nullptr;
+    if (p->precision == FMG_PREC_MIXED) {
+      u32 = (float*)take(nodes * 4);
+      b32 = (float*)take(nodes * 4);
+    }
+    if (c && base) {
+      c->u[k] = u;
+      c->b[k] = b;
+      c->g[k] = g;
+      c->u32[k] = u32;
+      c->b32[k] = b32;
+    }
+  }
+  const int m = p->coarse_cells - 1;
+  const long long N1 = ipow(m, p->dim);
+  double* Ainv = (double*)take(N1 * N1 * 8);
+  DevState* st = (DevState*)take(sizeof(DevState));
+  AugBuffers cfg = {};
+  aug_configure(p->dim, p->coarse_cells, &cfg);
+  const size_t items = cfg.partial_items;
+  double* partials = (double*)take(items * aug_nvals(p->dim) * 8);
+  double* cc = (double*)take(ipow(p->coarse_cells + 1, p->dim) * 8);
+  double* sys = (double*)take((2 * N1 + 8) * 8);
+  if (c && base) {
+    c->Ainv = Ainv;
+    c->st = st;
+    c->ab = cfg;
+    c->ab.partials = partials;
+    c->ab.c = cc;
+    c->ab.sys = sys;
+  }
+  return off;
+}
+
+// ------------------------------------------------------------------ schedule pieces
+cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b) {
+  const int dim = c->p.dim;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if (j == 1) return launch_coarse_solve_f64(dim, c->geo[0], c->Ainv, b, u, s);
+  const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
+  for (int it = 0; it < c->p.nu_pre; ++it) {
+    if ((e = launch_rbgs<double>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_rbgs<double>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+  }
+  if ((e = launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s)) != cudaSuccess)
+    return e;
+  if ((e = vcycle(c, j - 1, c->u[j - 2], c->b[j - 2])) != cudaSuccess) return e;
+  if ((e = launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s)) != cudaSuccess) return e;
+  for (int it = 0; it < c->p.nu_post; ++it) {
+    if ((e = launch_rbgs<double>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+    if ((e = launch_rbgs<double>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t vcycle32(fmg_ctx* c, int j) {
+  const int dim = c->p.dim;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  float* u = c->u32[j - 1];
+  const float* b = c->b32[j - 1];
+  if (j == 1) return launch_coarse_solve_f32(dim, c->geo[0], c->Ainv, b, u, s);
+  const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
+  for (int it = 0; it < c->p.nu_pre; ++it) {
+    if ((e = launch_rbgs<float>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_rbgs<float>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+  }
+  if ((e = launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = vcycle32(c, j - 1)) != cudaSuccess) return e;
+  if ((e = launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s)) != cudaSuccess) return e;
+  for (int it = 0; it < c->p.nu_post; ++it) {
+    if ((e = launch_rbgs<float>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+    if ((e = launch_rbgs<float>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One multigrid cycle for A_k u = b at the top level k, in the context's precision.
+cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
+  if (c->p.precision == FMG_PREC_FP64 || k == 1) return vcycle(c, k, u, b);
+  cudaError_t e;
+  const LevelGeo g = c->geo[k - 1];
+  // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update
+  if ((e = launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream)) != cudaSuccess)
+    return e;
+  if ((e = vcycle32(c, k)) != cudaSuccess) return e;
+  return launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream);
+}
+
+// Algorithm 3.1 at level k >= 2 on the level-k array u.
+cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
+  cudaError_t e;
+  const LevelGeo g = c->geo[k - 1];
+  // step 1: b = (g, v) - (f(x, u^{(l)}), v)   (eq. 3.4)
+  if ((e = launch_nonlinear_rhs(c->p.dim, g, u, c->g[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream)) !=
+      cudaSuccess)
+    return e;
+  for (int i = 0; i < c->p.m_vcycles; ++i)
+    if ((e = top_cycle(c, k, u, c->b[k - 1])) != cudaSuccess) return e;
+  // step 2: semilinear problem on V_H + span{u~}  (eq. 3.6)
+  return launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->g[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
+                          c->p.newton_maxit, c->ab, c->st, k - 1, c->stream);
+}
+
+cudaError_t run_fmg(fmg_ctx* c) {
+  cudaError_t e;
+  // per-solve statistics start at zero (flags, iteration counts, alphas)
+  if ((e = cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream)) != cudaSuccess) return e;
+  if ((e = launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
+                                c->p.level1_maxit, c->st, c->stream)) != cudaSuccess)
+    return e;
+  for (int k = 2; k <= c->nlev; ++k) {
+    // u^{(0)}_{h_k} = u_{h_{k-1}}: the natural inclusion
+    if ((e = launch_prolong<double, double>(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], 0,
+                                            c->stream)) != cudaSuccess)
+      return e;
+    for (int l = 0; l < c->p.p_corrections; ++l)
+      if ((e = correction_step(c, k, c->u[k - 1])) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+fmg_status read_state(fmg_ctx* c, fmg_stats* st, bool accumulate_pending) {
+  DevState h;
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaMemcpy(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  unsigned flags = h.flags | (accumulate_pending ? c->pending_flags : 0u);
+  c->pending_flags = 0;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->levels = c->nlev;
+    st->level1_iters = h.level1_iters;
+    for (int k = 0; k < 32 && k < kMaxLevels; ++k) {
+      st->newton_iters[k] = h.newton_iters[k];
+      st->alpha[k] = h.alpha[k];
+    }
+    st->flags = flags;
+  }
+  if (flags & kFlagTimeout) return fail(c, FMG_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (flags & kFlagNonfinite) return fail(c, FMG_ERR_NONFINITE, "non-finite value in an iterate");
+  if (flags & (kFlagNewtonCap | kFlagNotSPD))
+    return fail(c, FMG_ERR_NO_CONVERGENCE, "a Newton iteration hit its cap or met a non-SPD matrix");
+  return FMG_OK;
+}
+
+fmg_status load_rhs(fmg_ctx* c, const double* g_fine, int on_device) {
+  if (!g_fine) return fail(c, FMG_ERR_INVALID, "g is NULL");
+  const int top = c->nlev - 1;
+  CK(c, cudaMemcpyAsync(c->g[top], g_fine, c->geo[top].nodes * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  CK(c, launch_zero_boundary(c->p.dim, c->geo[top], c->g[top], c->stream));
+  for (int k = top - 1; k >= 0; --k)
+    CK(c, launch_decimate(c->p.dim, c->geo[top], c->g[top], c->geo[k], c->g[k], c->stream));
+  return FMG_OK;
+}
+
+fmg_status check_level(fmg_ctx* c, int level, int lo) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if (level < lo || level > c->nlev) return fail(c, FMG_ERR_INVALID, "level out of range");
+  return FMG_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+void fmg_default_params(fmg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 2;
+  p->coarse_cells = 4;
+  p->refinements = 4;
+  p->f = FMG_F_CUBIC;
+  p->f_scale = 1.0;
+  p->m_vcycles = 2;
+  p->nu_pre = 2;
+  p->nu_post = 2;
+  p->p_corrections = 1;
+  p->precision = FMG_PREC_FP64;
+  p->newton_tol = 1e-12;
+  p->newton_maxit = 20;
+  p->level1_tol = 1e-13;
+  p->level1_maxit = 50;
+}
+
+fmg_status fmg_workspace_bytes(const fmg_params* p, size_t* bytes) {
+  if (const char* why = validate(p)) return fail(nullptr, FMG_ERR_INVALID, why);
+  if (!bytes) return fail(nullptr, FMG_ERR_INVALID, "bytes is NULL");
+  *bytes = layout(nullptr, p, nullptr);
+  return FMG_OK;
+}
+
+fmg_status fmg_create(const fmg_params* p, const double* g_fine, int g_on_device, void* stream, void* workspace,
+                      size_t workspace_bytes, fmg_ctx** out) {
+  if (!out) return fail(nullptr, FMG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (const char* why = validate(p)) return fail(nullptr, FMG_ERR_INVALID, why);
+  if (!g_fine) return fail(nullptr, FMG_ERR_INVALID, "g is NULL");
+  fmg_ctx* c = new (std::nothrow) fmg_ctx();
+  if (!c) return fail(nullptr, FMG_ERR_OOM, "host allocation failed");
+  c->p = *p;
+  c->nlev = p->refinements + 1;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess && !c->stream) {
+    // graph capture needs a stream other than the legacy default stream
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    c->own_stream = (e == cudaSuccess);
+  }
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return fail(nullptr, FMG_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  const size_t need = layout(c, p, nullptr);
+  if (workspace) {
+    if (workspace_bytes < need) {
+      delete c;
+      return fail(nullptr, FMG_ERR_INVALID, "workspace smaller than fmg_workspace_bytes");
+    }
+    c->arena = workspace;
+    c->own_arena = false;
+  } else {
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(nullptr, FMG_ERR_CUDA, std::string("cudaMemGetInfo: ") + cudaGetErrorString(e));
+    }
+    if (need > free_b) {
+      delete c;
+      return fail(nullptr, FMG_ERR_OOM, "not enough free device memory for the level hierarchy");
+    }
+    e = cudaMalloc(&c->arena, need);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(nullptr, FMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->own_arena = true;
+  }
+  c->arena_bytes = need;
+  layout(c, p, (char*)c->arena);
+  fmg_status s = FMG_OK;
+  e = cudaMemsetAsync(c->arena, 0, need, c->stream);
+  if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  if (s == FMG_OK) s = load_rhs(c, g_fine, g_on_device);
+  if (s == FMG_OK) {
+    e = launch_coarse_inverse(p->dim, c->geo[0], c->Ainv, c->st, c->stream);
+    if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("coarse inverse: ") + cudaGetErrorString(e));
+  }
+  if (s == FMG_OK) s = read_state(c, nullptr, false);
+  if (s != FMG_OK) {
+    t_err = c->err;
+    fmg_destroy(c);
+    return s;
+  }
+  *out = c;
+  return FMG_OK;
+}
+
+fmg_status fmg_set_rhs(fmg_ctx* c, const double* g_fine, int g_on_device) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  return load_rhs(c, g_fine, g_on_device);
+}
+
+fmg_status fmg_solve(fmg_ctx* c, double* u_out, int out_on_device, fmg_stats* st) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if (!c->gexec) {
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = run_fmg(c);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(c, FMG_ERR_CUDA,
+                  std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      c->gexec = nullptr;
+      return fail(c, FMG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    c->graph = graph;
+  }
+  CK(c, cudaGraphLaunch(c->gexec, c->stream));
+  const int top = c->nlev - 1;
+  if (u_out)
+    CK(c, cudaMemcpyAsync(u_out, c->u[top], c->geo[top].nodes * sizeof(double),
+                          out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (st || (u_out && !out_on_device)) return read_state(c, st, true);
+  return FMG_OK;
+}
+
+fmg_status fmg_sync(fmg_ctx* c, fmg_stats* st) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  return read_state(c, st, true);
+}
+
+fmg_status fmg_solve_batch(fmg_ctx** cs, int count, double** u_outs, fmg_stats* sts) {
+  if (!cs || count < 0) return fail(nullptr, FMG_ERR_INVALID, "bad batch arguments");
+  for (int i = 0; i < count; ++i) {
+    fmg_status s = fmg_solve(cs[i], u_outs ? u_outs[i] : nullptr, 1, nullptr);
+    if (s != FMG_OK) return s;
+  }
+  fmg_status worst = FMG_OK;
+  for (int i = 0; i < count; ++i) {
+    fmg_status s = read_state(cs[i], sts ? &sts[i] : nullptr, true);
+    if (s != FMG_OK && worst == FMG_OK) worst = s;
+  }
+  return worst;
+}
+
+fmg_status fmg_destroy(fmg_ctx* c) {
+  if (!c) return FMG_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->own_arena && c->arena) cudaFree(c->arena);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return FMG_OK;
+}
+
+const char* fmg_last_error(const fmg_ctx* c) { return c ? c->err.c_str() : t_err.c_str(); }
+
+int fmg_levels(const fmg_ctx* c) { return c ? c->nlev : -1; }
+
+int fmg_level_cells(const fmg_ctx* c, int level) {
+  if (!c || level < 1 || level > c->nlev) return -1;
+  return c->geo[level - 1].n;
+}
+
+const double* fmg_solution(const fmg_ctx* c) { return c ? c->u[c->nlev - 1] : nullptr; }
+
+// ------------------------------------------------------------------ component operations
+
+fmg_status fmg_op_smooth(fmg_ctx* c, int level, const double* b, double* u, int sweeps, int order) {
+  if (fmg_status s = check_level(c, level, 1)) return s;
+  if (!b || !u || sweeps < 0) return fail(c, FMG_ERR_INVALID, "bad smoother arguments");
+  const int first = order ? 1 : 0;
+  for (int i = 0; i < sweeps; ++i) {
+    CK(c, launch_rbgs<double>(c->p.dim, c->geo[level - 1], u, b, first, c->stream));
+    CK(c, launch_rbgs<double>(c->p.dim, c->geo[level - 1], u, b, 1 - first, c->stream));
+  }
+  return read_state(c, nullptr, false);
+}
+
+fmg_status fmg_op_smooth_f32(fmg_ctx* c, int level, const float* b, float* u, int sweeps, int order) {
+  if (fmg_status s = check_level(c, level, 1)) return s;
+  if (!b || !u || sweeps < 0) return fail(c, FMG_ERR_INVALID, "bad smoother arguments");
+  const int first = order ? 1 : 0;
+  for (int i = 0; i < sweeps; ++i) {
+    CK(c, launch_rbgs<float>(c->p.dim, c->geo[level - 1], u, b, first, c->stream));
+    CK(c, launch_rbgs<float>(c->p.dim, c->geo[level - 1], u, b, 1 - first, c->stream));
+  }
+  return read_state(c, nullptr, false);
+}
+
+fmg_status fmg_op_residual(fmg_ctx* c, int level, const double* b, const double* u, double* r) {
+  if (fmg_status s = check_level(c, level, 1)) return s;
+  if (!b || !u || !r) return fail(c, FMG_ERR_INVALID, "NULL array");
+  CK(c, launch_residual(c->p.dim, c->geo[level - 1], u, b, r, c->stream));
+  return read_state(c, nullptr, false);
+}
+
+fmg_status fmg_op_vcycle(fmg_ctx* c, int level, const double* b, double* u, int cycles) {
+  if (fmg_status s = check_level(c, level, 1)) return s;
+  if (!b || !u || cycles < 0) return fail(c, FMG_ERR_INVALID, "bad cycle arguments");
+  for (int i = 0; i < cycles; ++i) CK(c, top_cycle(c, level, u, b));
+  return read_state(c, nullptr, false);
+}
+
+fmg_status fmg_op_correction_step(fmg_ctx* c, int level, double* u, fmg_stats* st) {
+  if (fmg_status s = check_level(c, level, 2)) return s;
+  if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
+  CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  CK(c, correction_step(c, level, u));
+  return read_state(c, st, false);
+}
+
+fmg_status fmg_op_level1_solve(fmg_ctx* c, double* u, fmg_stats* st) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
+  CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  CK(c, launch_level1_newton(c->p.dim, c->geo[0], c->g[0], u, c->p.f, c->p.f_scale, c->p.level1_tol,
+                             c->p.level1_maxit, c->st, c->stream));
+  return read_state(c, st, false);
+}
+
+fmg_status fmg_op_prolong(fmg_ctx* c, int level, const double* u_coarse, double* u_fine) {
+  if (fmg_status s = check_level(c, level, 2)) return s;
+  if (!u_coarse || !u_fine) return fail(c, FMG_ERR_INVALID, "NULL array");
+  CK(c, (launch_prolong<double, double>(c->p.dim, c->geo[level - 2], u_coarse, c->geo[level - 1], u_fine, 0,
+                                        c->stream)));
+  return read_state(c, nullptr, false);
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+//
+// Geometry: level k of the nested hierarchy (Sec. 3, eq. 3.1) has n = (1/H) 2^(k-1) cells
+// per side and (n+1)^d nodes, boundary included, stored x fastest.  The P1 stiffness of
+// the right-triangle (2D) and Kuhn (3D) meshes is sigma * (2d-point Laplacian) with
+// sigma = h^(d-2); the vertex quadrature weight of an interior node is w = h^d.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fmg.h"
+
+namespace fmg {
+
+constexpr int kMaxLevels = 24;
+constexpr int kMaxAug = 64;          // N_H + 1 limit of the dense augmented system
+constexpr int kMaxNewton = 64;
+
+// Device status flags (mirrors fmg_stats.flags).
+constexpr unsigned kFlagNewtonCap = 1u;
+constexpr unsigned kFlagNonfinite = 2u;
+constexpr unsigned kFlagDropped = 4u;
+constexpr unsigned kFlagNotSPD = 8u;
+constexpr unsigned kFlagTimeout = 16u;
+
+// Small per-context device state (one allocation, part of the workspace).
+struct DevState {
+  unsigned int flags;
+  int level1_iters;
+  int newton_iters[32];
+  double alpha[32];
+  // grid barrier of the cooperative Newton kernel
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int abort;
+  int converged;
+  // current augmented iterate
+  double alpha_cur;
+  double pad[3];
+};
+
+struct LevelGeo {
+  int n;          // cells per side
+  int np;         // n + 1
+  long long nodes;  // (n+1)^d
+};
+
+__host__ __device__ inline long long ipow(long long b, int e) {
+  long long r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// Nonlinearity a*f(u) and its derivative (Sec. 4 examples; monotone for a > 0).
+template <typename T>
+__device__ __forceinline__ void f_eval(int kind, T a, T u, T& F, T& Fp) {
+  switch (kind) {
+    case FMG_F_CUBIC: {
+      T t = a * (u * u);
+      F = t * u;
+      Fp = T(3) * t;
+      break;
+    }
+    case FMG_F_EXPM1: {
+      T e = expm1(u);
+      F = a * e;
+      Fp = F + a;
+      break;
+    }
+    case FMG_F_LINEAR:
+      F = a * u;
+      Fp = a;
+      break;
+    case FMG_F_SIGNED_POW32: {
+      T r = sqrt(fabs(u));
+      F = a * u * r;
+      Fp = T(1.5) * a * r;
+      break;
+    }
+    default: {  // FMG_F_NEG_EXP_NEG
+      T e = exp(-u);
+      F = -a * e;
+      Fp = a * e;
+      break;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T f_only(int kind, T a, T u) {
+  switch (kind) {
+    case FMG_F_CUBIC: return a * (u * u) * u;
+    case FMG_F_EXPM1: return a * expm1(u);
+    case FMG_F_LINEAR: return a * u;
+    case FMG_F_SIGNED_POW32: return a * u * sqrt(fabs(u));
+    default: return -a * exp(-u);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Launchers (host side), defined in fmg_stencil.cu / fmg_newton.cu.  All take the stream
+// and return the launch error.
+// ---------------------------------------------------------------------------------------
+
+// red-black Gauss-Seidel half sweep of colour `colour` (0 red, 1 black) on level geometry g
+template <typename T>
+cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaStream_t s);
+
+// b_c = P^T (b_f - A_f u_f), u_c = 0 (coarse arrays of geometry gc, fine gf)
+template <typename TF, typename TC>
+cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const TF* b_f, LevelGeo gc,
+                                     TC* b_c, TC* u_c, cudaStream_t s);
+
+// mixed path: b32 = (float)(b - A u) in FP64, u32 = 0 (same level)
+cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const double* b, float* r32,
+                                   float* e32, cudaStream_t s);
+
+// r = b - A u (FP64, same level)
+cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* b, double* r, cudaStream_t s);
+
+// u_f += P e_c  (add = 1) or u_f = P e_c (add = 0)
+template <typename TF, typename TC>
+cudaError_t launch_prolong(int dim, LevelGeo gc, const TC* e_c, LevelGeo gf, TF* u_f, int add, cudaStream_t s);
+
+// u += (double) e32 (mixed path update)
+cudaError_t launch_add_f32(LevelGeo g, int dim, double* u, const float* e32, cudaStream_t s);
+
+// b = w (g - a f(u)) at interior nodes, 0 on the boundary (eq. 3.4 with vertex quadrature)
+cudaError_t launch_nonlinear_rhs(int dim, LevelGeo g, const double* u, const double* gn, double* b, int kind,
+                                 double a, cudaStream_t s);
+
+// coarse nodal g: gc(x) = gf(stride * x)
+cudaError_t launch_decimate(int dim, LevelGeo gf, const double* gsrc, LevelGeo gc, double* gdst, cudaStream_t s);
+
+// zero the boundary ring of a nodal array
+cudaError_t launch_zero_boundary(int dim, LevelGeo g, double* a, cudaStream_t s);
+
+// copy nodal array (same level)
+cudaError_t launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
+
+// FP32 V-cycle coarsest solve: e32 = (float)(Ainv (double) b32); FP64: e = Ainv b
+cudaError_t launch_coarse_solve_f64(int dim, LevelGeo g1, const double* Ainv, const double* b, double* u,
+                                    cudaStream_t s);
+cudaError_t launch_coarse_solve_f32(int dim, LevelGeo g1, const double* Ainv, const float* b, float* u,
+                                    cudaStream_t s);
+
+// level-1 setup: Ainv = A_1^{-1} (dense, N_1 x N_1) by Cholesky; flags on failure
+cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s);
+
+// level-1 exact semilinear solve (Algorithm 3.2 step 1): Newton, dense, one CTA
+cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double* u, int kind, double a,
+                                 double tol, int maxit, DevState* st, cudaStream_t s);
+
+// Augmented problem on V_H + span{u~} (Algorithm 3.1 step 2, eq. 3.6): one cooperative
+// persistent kernel: precompute, Newton iterations, final update u = alpha u~ + P_{H->k} c.
+struct AugBuffers {
+  double* partials;   // [items][nvals]
+  double* c;          // coarse nodal iterate (level-1 layout), length (nH+1)^d
+  double* sys;        // scratch: t, G_H, s, gamma and the dense system
+  size_t partial_items;
+  int bpc;            // blocks per coarse cell of the cooperative launch (all co-resident)
+  int nt;             // threads per block
+  size_t smem;        // dynamic shared memory per block
+};
+// Fills bpc/nt/smem/partial_items for this device (occupancy-based), outside any capture.
+void aug_configure(int dim, int coarse_cells, AugBuffers* ab);
+int aug_nvals(int dim);
+cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
+                             int kind, double a, double tol, int maxit, const AugBuffers& ab, DevState* st,
+                             int level_index, cudaStream_t s);
+
+}  // namespace fmg

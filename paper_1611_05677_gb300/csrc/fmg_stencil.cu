@@ -1,0 +1,354 @@
+// Matrix-free stencil kernels of the multigrid cycle (Algorithm 3.1 step 1, eq. 3.4-3.5)
+// and the pointwise steps of the full multigrid schedule (Algorithm 3.2).
+//
+// Operators (P1 elements on the nested right-triangle / Kuhn meshes of Sec. 3):
+//   A_k     = sigma_k * (2d-point Laplacian),   sigma_k = h_k^(d-2)
+//   P_k     = nodal interpolation V_{h_{k-1}} -> V_{h_k}: a fine node at the midpoint of a
+//             coarse edge takes the mean of the edge's two end values; every edge of these
+//             meshes joins a coarse node z to z + e with e a nonzero 0/1 vector, so the two
+//             ends of the edge through fine node x are floor(x/2) and ceil(x/2)
+//   P_k^T   = restriction: coarse node z gathers 1 x r(2z) + 1/2 x r(2z +- e) over the
+//             2^d - 1 edge directions e
+// Red-black Gauss-Seidel: red nodes have i+j[+l] even.
+#include <cuda_runtime.h>
+
+#include "fmg_internal.cuh"
+
+namespace fmg {
+
+namespace {
+
+constexpr int kBlock = 128;
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ red-black Gauss-Seidel
+template <typename T>
+__global__ void k_rbgs2(T* __restrict__ u, const T* __restrict__ b, int n, int colour) {
+  const int j = blockIdx.y + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int par = (colour + j) & 1;
+  const int i = par ? 2 * t + 1 : 2 * t + 2;
+  if (i > n - 1) return;
+  const long long np = n + 1;
+  const long long c = (long long)j * np + i;
+  const T s = (u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np]);
+  u[c] = (b[c] + s) * T(0.25);
+}
+
+template <typename T>
+__global__ void k_rbgs3(T* __restrict__ u, const T* __restrict__ b, int n, int colour, T bscale, T inv6) {
+  const int j = blockIdx.y + 1;
+  const int l = blockIdx.z + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int par = (colour + j + l) & 1;
+  const int i = par ? 2 * t + 1 : 2 * t + 2;
+  if (i > n - 1) return;
+  const long long np = n + 1;
+  const long long pl = np * np;
+  const long long c = ((long long)l * np + j) * np + i;
+  const T s = ((u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np])) + (u[c - pl] + u[c + pl]);
+  u[c] = (b[c] * bscale + s) * inv6;
+}
+
+// ------------------------------------------------------------------ residual + restriction
+template <typename T>
+__device__ __forceinline__ T res2(const T* __restrict__ u, const T* __restrict__ b, long long c, long long np) {
+  return b[c] - (T(4) * u[c] - ((u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np])));
+}
+
+template <typename T>
+__device__ __forceinline__ T res3(const T* __restrict__ u, const T* __restrict__ b, long long c, long long np,
+                                  long long pl, T sigma) {
+  return b[c] - sigma * (T(6) * u[c] - (((u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np])) + (u[c - pl] + u[c + pl])));
+}
+
+template <typename TF, typename TC>
+__global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
+                               TC* __restrict__ uc, int ncells) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int J = blockIdx.y + 1;
+  if (I > ncells - 1) return;
+  const long long np = nf + 1;
+  const long long F = (long long)(2 * J) * np + 2 * I;
+  TF r = res2(u, b, F, np);
+  TF e = (res2(u, b, F + 1, np) + res2(u, b, F - 1, np)) + (res2(u, b, F + np, np) + res2(u, b, F - np, np)) +
+         (res2(u, b, F + np + 1, np) + res2(u, b, F - np - 1, np));
+  const long long cc = (long long)J * (ncells + 1) + I;
+  bc[cc] = (TC)(r + TF(0.5) * e);
+  uc[cc] = TC(0);
+}
+
+template <typename TF, typename TC>
+__global__ void k_resrestrict3(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TF sigma,
+                               TC* __restrict__ bc, TC* __restrict__ uc, int ncells) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int J = blockIdx.y + 1;
+  const int L = blockIdx.z + 1;
+  if (I > ncells - 1) return;
+  const long long np = nf + 1;
+  const long long pl = np * np;
+  const long long F = ((long long)(2 * L) * np + 2 * J) * np + 2 * I;
+  const long long o[7] = {1, np, pl, 1 + np, 1 + pl, np + pl, 1 + np + pl};
+  TF r = res3(u, b, F, np, pl, sigma);
+  TF e = TF(0);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) e += res3(u, b, F + o[q], np, pl, sigma) + res3(u, b, F - o[q], np, pl, sigma);
+  const long long ncp = ncells + 1;
+  const long long cc = ((long long)L * ncp + J) * ncp + I;
+  bc[cc] = (TC)(r + TF(0.5) * e);
+  uc[cc] = TC(0);
+}
+
+// ------------------------------------------------------------------ residual on one level
+__global__ void k_residual2(const double* __restrict__ u, const double* __restrict__ b, int n,
+                            double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i > n) return;
+  const long long np = n + 1;
+  const long long c = (long long)j * np + i;
+  double v = 0.0;
+  if (i > 0 && i < n && j > 0 && j < n) v = res2(u, b, c, np);
+  if (r) r[c] = v;
+  if (r32) {
+    r32[c] = (float)v;
+    e32[c] = 0.0f;
+  }
+}
+
+__global__ void k_residual3(const double* __restrict__ u, const double* __restrict__ b, int n, double sigma,
+                            double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const int l = blockIdx.z;
+  if (i > n) return;
+  const long long np = n + 1;
+  const long long pl = np * np;
+  const long long c = ((long long)l * np + j) * np + i;
+  double v = 0.0;
+  if (i > 0 && i < n && j > 0 && j < n && l > 0 && l < n) v = res3(u, b, c, np, pl, sigma);
+  if (r) r[c] = v;
+  if (r32) {
+    r32[c] = (float)v;
+    e32[c] = 0.0f;
+  }
+}
+
+// ------------------------------------------------------------------ prolongation (+ correction)
+template <typename TF, typename TC>
+__global__ void k_prolong2(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int j = blockIdx.y + 1;
+  if (i > nf - 1) return;
+  const long long cp = nc + 1;
+  const long long a = (long long)(j >> 1) * cp + (i >> 1);
+  const long long z = (long long)((j + 1) >> 1) * cp + ((i + 1) >> 1);
+  const TF v = TF(0.5) * ((TF)e[a] + (TF)e[z]);
+  const long long f = (long long)j * (nf + 1) + i;
+  u[f] = add ? u[f] + v : v;
+}
+
+template <typename TF, typename TC>
+__global__ void k_prolong3(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int j = blockIdx.y + 1;
+  const int l = blockIdx.z + 1;
+  if (i > nf - 1) return;
+  const long long cp = nc + 1;
+  const long long a = ((long long)(l >> 1) * cp + (j >> 1)) * cp + (i >> 1);
+  const long long z = ((long long)((l + 1) >> 1) * cp + ((j + 1) >> 1)) * cp + ((i + 1) >> 1);
+  const TF v = TF(0.5) * ((TF)e[a] + (TF)e[z]);
+  const long long fp = nf + 1;
+  const long long f = ((long long)l * fp + j) * fp + i;
+  u[f] = add ? u[f] + v : v;
+}
+
+// ------------------------------------------------------------------ pointwise kernels
+__global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[i] += (double)e[i];
+}
+
+__device__ __forceinline__ bool interior_of(long long idx, int n, int dim) {
+  const long long np = n + 1;
+  const int i = (int)(idx % np);
+  const int j = (int)((idx / np) % np);
+  if (i == 0 || i == n || j == 0 || j == n) return false;
+  if (dim == 3) {
+    const int l = (int)(idx / (np * np));
+    if (l == 0 || l == n) return false;
+  }
+  return true;
+}
+
+__global__ void k_nonlinear_rhs(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
+                                long long nodes, int n, int dim, int kind, double a, double w) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nodes) return;
+  double v = 0.0;
+  if (interior_of(idx, n, dim)) v = w * (g[idx] - f_only<double>(kind, a, u[idx]));
+  b[idx] = v;
+}
+
+__global__ void k_decimate(const double* __restrict__ src, int nf, double* __restrict__ dst, int nc, int dim) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long cp = nc + 1;
+  const long long total = dim == 2 ? cp * cp : cp * cp * cp;
+  if (idx >= total) return;
+  const int st = nf / nc;
+  const long long fp = nf + 1;
+  const long long i = idx % cp, j = (idx / cp) % cp, l = idx / (cp * cp);
+  dst[idx] = src[((l * st) * fp + j * st) * fp + i * st];
+}
+
+__global__ void k_zero_boundary(double* __restrict__ a, long long nodes, int n, int dim) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nodes) return;
+  if (!interior_of(idx, n, dim)) a[idx] = 0.0;
+}
+
+__global__ void k_copy(const double* __restrict__ s, double* __restrict__ d, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = s[i];
+}
+
+// ------------------------------------------------------------------ coarsest solve (dense inverse)
+// Unknown r of level 1 <-> interior node (r % m + 1, (r / m) % m + 1, r / m^2 + 1), m = n1 - 1.
+__device__ __forceinline__ long long coarse_node(int r, int m, int dim) {
+  const long long np = m + 2;
+  const int i = r % m + 1;
+  const int j = (r / m) % m + 1;
+  if (dim == 2) return (long long)j * np + i;
+  const int l = r / (m * m) + 1;
+  return ((long long)l * np + j) * np + i;
+}
+
+template <typename T>
+__global__ void k_coarse_solve(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ u, int m,
+                               int N, int dim) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double acc = 0.0;
+  for (int c = 0; c < N; ++c) acc += Ainv[(long long)r * N + c] * (double)b[coarse_node(c, m, dim)];
+  u[coarse_node(r, m, dim)] = (T)acc;
+}
+
+}  // namespace
+
+// ============================================================================ launchers
+
+template <typename T>
+cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaStream_t s) {
+  const int n = g.n;
+  const unsigned gx = cdiv(n / 2, kBlock);
+  if (dim == 2) {
+    k_rbgs2<T><<<dim3(gx, n - 1), kBlock, 0, s>>>(u, b, n, colour);
+  } else {
+    k_rbgs3<T><<<dim3(gx, n - 1, n - 1), kBlock, 0, s>>>(u, b, n, colour, T(n), T(1.0 / 6.0));
+  }
+  return cudaGetLastError();
+}
+
+template <typename TF, typename TC>
+cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const TF* b_f, LevelGeo gc, TC* b_c,
+                                     TC* u_c, cudaStream_t s) {
+  const int nc = gc.n;
+  const unsigned gx = cdiv(nc - 1, kBlock);
+  if (dim == 2) {
+    k_resrestrict2<TF, TC><<<dim3(gx, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc);
+  } else {
+    k_resrestrict3<TF, TC><<<dim3(gx, nc - 1, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, TF(1.0) / TF(gf.n), b_c,
+                                                                        u_c, nc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const double* b, float* r32, float* e32,
+                                   cudaStream_t s) {
+  const int n = g.n;
+  const unsigned gx = cdiv(n + 1, kBlock);
+  if (dim == 2)
+    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, nullptr, r32, e32);
+  else
+    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, nullptr, r32, e32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* b, double* r, cudaStream_t s) {
+  const int n = g.n;
+  const unsigned gx = cdiv(n + 1, kBlock);
+  if (dim == 2)
+    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, r, nullptr, nullptr);
+  else
+    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, r, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+template <typename TF, typename TC>
+cudaError_t launch_prolong(int dim, LevelGeo gc, const TC* e_c, LevelGeo gf, TF* u_f, int add, cudaStream_t s) {
+  const int nf = gf.n;
+  const unsigned gx = cdiv(nf - 1, kBlock);
+  if (dim == 2)
+    k_prolong2<TF, TC><<<dim3(gx, nf - 1), kBlock, 0, s>>>(e_c, gc.n, u_f, nf, add);
+  else
+    k_prolong3<TF, TC><<<dim3(gx, nf - 1, nf - 1), kBlock, 0, s>>>(e_c, gc.n, u_f, nf, add);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_f32(LevelGeo g, int dim, double* u, const float* e32, cudaStream_t s) {
+  (void)dim;
+  k_add_f32<<<cdiv(g.nodes, 256), 256, 0, s>>>(u, e32, g.nodes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonlinear_rhs(int dim, LevelGeo g, const double* u, const double* gn, double* b, int kind,
+                                 double a, cudaStream_t s) {
+  const double h = 1.0 / g.n;
+  const double w = dim == 2 ? h * h : h * h * h;
+  k_nonlinear_rhs<<<cdiv(g.nodes, 256), 256, 0, s>>>(u, gn, b, g.nodes, g.n, dim, kind, a, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decimate(int dim, LevelGeo gf, const double* gsrc, LevelGeo gc, double* gdst, cudaStream_t s) {
+  k_decimate<<<cdiv(gc.nodes, 256), 256, 0, s>>>(gsrc, gf.n, gdst, gc.n, dim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_boundary(int dim, LevelGeo g, double* a, cudaStream_t s) {
+  k_zero_boundary<<<cdiv(g.nodes, 256), 256, 0, s>>>(a, g.nodes, g.n, dim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const double* src, double* dst, long long n, cudaStream_t s) {
+  k_copy<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve_f64(int dim, LevelGeo g1, const double* Ainv, const double* b, double* u,
+                                    cudaStream_t s) {
+  const int m = g1.n - 1;
+  const int N = (int)ipow(m, dim);
+  k_coarse_solve<double><<<cdiv(N, 64), 64, 0, s>>>(Ainv, b, u, m, N, dim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve_f32(int dim, LevelGeo g1, const double* Ainv, const float* b, float* u,
+                                    cudaStream_t s) {
+  const int m = g1.n - 1;
+  const int N = (int)ipow(m, dim);
+  k_coarse_solve<float><<<cdiv(N, 64), 64, 0, s>>>(Ainv, b, u, m, N, dim);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t);
+template cudaError_t launch_rbgs<float>(int, LevelGeo, float*, const float*, int, cudaStream_t);
+template cudaError_t launch_residual_restrict<double, double>(int, LevelGeo, const double*, const double*, LevelGeo,
+                                                              double*, double*, cudaStream_t);
+template cudaError_t launch_residual_restrict<float, float>(int, LevelGeo, const float*, const float*, LevelGeo,
+                                                            float*, float*, cudaStream_t);
+template cudaError_t launch_prolong<double, double>(int, LevelGeo, const double*, LevelGeo, double*, int,
+                                                    cudaStream_t);
+template cudaError_t launch_prolong<float, float>(int, LevelGeo, const float*, LevelGeo, float*, int, cudaStream_t);
+
+}  // namespace fmg

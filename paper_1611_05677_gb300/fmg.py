@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in include/fmg.h (argument marshalling only).
+
+Every function named fmg_* here calls the C function of the same name in
+libfmg_gb300.so; all arithmetic of the solver runs in the library's CUDA
+kernels.  PyTorch is used only for device memory (the context workspace and
+output tensors) and CUDA streams.  Importing the module does not need a GPU;
+loading the library does, and fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_size_t, c_uint, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+FMG_OK = 0
+FMG_ERR_INVALID = 1
+FMG_ERR_OOM = 2
+FMG_ERR_NO_CONVERGENCE = 3
+FMG_ERR_NONFINITE = 4
+FMG_ERR_TIMEOUT = 5
+FMG_ERR_CUDA = 6
+STATUS_NAMES = {0: "FMG_OK", 1: "FMG_ERR_INVALID", 2: "FMG_ERR_OOM", 3: "FMG_ERR_NO_CONVERGENCE",
+                4: "FMG_ERR_NONFINITE", 5: "FMG_ERR_TIMEOUT", 6: "FMG_ERR_CUDA"}
+
+NONLIN = {"cubic": 0, "expm1": 1, "linear": 2, "signed_pow32": 3, "neg_exp_neg": 4}
+PREC = {"fp64": 0, "mixed": 1}
+
+
+class fmg_params(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("coarse_cells", c_int), ("refinements", c_int), ("f", c_int),
+                ("f_scale", c_double), ("m_vcycles", c_int), ("nu_pre", c_int), ("nu_post", c_int),
+                ("p_corrections", c_int), ("precision", c_int), ("newton_tol", c_double),
+                ("newton_maxit", c_int), ("level1_tol", c_double), ("level1_maxit", c_int)]
+
+
+class fmg_stats(ctypes.Structure):
+    _fields_ = [("levels", c_int), ("level1_iters", c_int), ("newton_iters", c_int * 32),
+                ("alpha", c_double * 32), ("flags", c_uint)]
+
+
+class FMGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_rhs", "fmg_solve", "fmg_sync",
+           "fmg_solve_batch", "fmg_destroy", "fmg_last_error", "fmg_solution", "fmg_levels", "fmg_level_cells",
+           "fmg_op_smooth", "fmg_op_smooth_f32", "fmg_op_residual", "fmg_op_vcycle", "fmg_op_correction_step",
+           "fmg_op_level1_solve", "fmg_op_prolong")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libfmg_gb300.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA solver library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P = POINTER(fmg_params)
+    S = POINTER(fmg_stats)
+    sig = {
+        "fmg_default_params": (None, [P]),
+        "fmg_workspace_bytes": (c_int, [P, POINTER(c_size_t)]),
+        "fmg_create": (c_int, [P, c_void_p, c_int, c_void_p, c_void_p, c_size_t, POINTER(c_void_p)]),
+        "fmg_set_rhs": (c_int, [c_void_p, c_void_p, c_int]),
+        "fmg_solve": (c_int, [c_void_p, c_void_p, c_int, S]),
+        "fmg_sync": (c_int, [c_void_p, S]),
+        "fmg_solve_batch": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), S]),
+        "fmg_destroy": (c_int, [c_void_p]),
+        "fmg_last_error": (c_char_p, [c_void_p]),
+        "fmg_solution": (c_void_p, [c_void_p]),
+        "fmg_levels": (c_int, [c_void_p]),
+        "fmg_level_cells": (c_int, [c_void_p, c_int]),
+        "fmg_op_smooth": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
+        "fmg_op_smooth_f32": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_int]),
+        "fmg_op_residual": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+        "fmg_op_vcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int]),
+        "fmg_op_correction_step": (c_int, [c_void_p, c_int, c_void_p, S]),
+        "fmg_op_level1_solve": (c_int, [c_void_p, c_void_p, S]),
+        "fmg_op_prolong": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _device_sync():
+    """Orders caller-side torch work before a synchronous component call."""
+    import sys
+
+    torch = sys.modules.get("torch")
+    if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+        torch.cuda.synchronize()
+
+
+def _check(status: int, ctx=None):
+    if status != FMG_OK:
+        msg = _lib.fmg_last_error(ctx)
+        raise FMGError(status, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """(address, on_device) of a torch tensor, numpy array or raw int pointer (device)."""
+    if x is None:
+        return None, 1
+    if isinstance(x, int):
+        return x, 1
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, 0
+    # torch tensor
+    assert x.is_contiguous()
+    return x.data_ptr(), int(x.is_cuda)
+
+
+# ---------------------------------------------------------------------------- C ABI, same names
+
+def fmg_default_params() -> fmg_params:
+    p = fmg_params()
+    load().fmg_default_params(byref(p))
+    return p
+
+
+def fmg_workspace_bytes(p: fmg_params) -> int:
+    n = c_size_t(0)
+    _check(load().fmg_workspace_bytes(byref(p), byref(n)))
+    return n.value
+
+
+def fmg_create(p: fmg_params, g_fine, stream=None, workspace=None, workspace_bytes: int = 0):
+    lib = load()
+    gp, gdev = _ptr(g_fine)
+    wp = None
+    if workspace is not None:
+        wp, _ = _ptr(workspace)
+    ctx = c_void_p()
+    _check(lib.fmg_create(byref(p), gp, gdev, stream, wp, workspace_bytes, byref(ctx)))
+    return ctx
+
+
+def fmg_set_rhs(ctx, g_fine):
+    gp, gdev = _ptr(g_fine)
+    _check(load().fmg_set_rhs(ctx, gp, gdev), ctx)
+
+
+def fmg_solve(ctx, u_out=None, stats: fmg_stats | None = None):
+    up, udev = _ptr(u_out)
+    _check(load().fmg_solve(ctx, up, udev, byref(stats) if stats is not None else None), ctx)
+
+
+def fmg_sync(ctx, stats: fmg_stats | None = None):
+    _check(load().fmg_sync(ctx, byref(stats) if stats is not None else None), ctx)
+
+
+def fmg_solve_batch(ctxs, u_outs=None, stats=None):
+    arr = (c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    outs = None
+    if u_outs is not None:
+        outs = (c_void_p * len(ctxs))(*[_ptr(u)[0] for u in u_outs])
+    st = (fmg_stats * len(ctxs))() if stats is None else stats
+    _check(load().fmg_solve_batch(arr, len(ctxs), outs, st))
+    return st
+
+
+def fmg_destroy(ctx):
+    if ctx is not None and ctx.value:
+        load().fmg_destroy(ctx)
+
+
+def fmg_last_error(ctx=None) -> str:
+    r = load().fmg_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def fmg_solution(ctx) -> int:
+    return load().fmg_solution(ctx)
+
+
+def fmg_levels(ctx) -> int:
+    return load().fmg_levels(ctx)
+
+
+def fmg_level_cells(ctx, level: int) -> int:
+    return load().fmg_level_cells(ctx, level)
+
+
+def fmg_op_smooth(ctx, level, b, u, sweeps, order=0):
+    _device_sync()
+    _check(load().fmg_op_smooth(ctx, level, _ptr(b)[0], _ptr(u)[0], sweeps, order), ctx)
+
+
+def fmg_op_smooth_f32(ctx, level, b, u, sweeps, order=0):
+    _device_sync()
+    _check(load().fmg_op_smooth_f32(ctx, level, _ptr(b)[0], _ptr(u)[0], sweeps, order), ctx)
+
+
+def fmg_op_residual(ctx, level, b, u, r):
+    _device_sync()
+    _check(load().fmg_op_residual(ctx, level, _ptr(b)[0], _ptr(u)[0], _ptr(r)[0]), ctx)
+
+
+def fmg_op_vcycle(ctx, level, b, u, cycles=1):
+    _device_sync()
+    _check(load().fmg_op_vcycle(ctx, level, _ptr(b)[0], _ptr(u)[0], cycles), ctx)
+
+
+def fmg_op_correction_step(ctx, level, u, stats: fmg_stats | None = None):
+    _device_sync()
+    _check(load().fmg_op_correction_step(ctx, level, _ptr(u)[0], byref(stats) if stats is not None else None), ctx)
+
+
+def fmg_op_level1_solve(ctx, u, stats: fmg_stats | None = None):
+    _device_sync()
+    _check(load().fmg_op_level1_solve(ctx, _ptr(u)[0], byref(stats) if stats is not None else None), ctx)
+
+
+def fmg_op_prolong(ctx, level, u_coarse, u_fine):
+    _device_sync()
+    _check(load().fmg_op_prolong(ctx, level, _ptr(u_coarse)[0], _ptr(u_fine)[0]), ctx)
+
+
+# ---------------------------------------------------------------------------- convenience
+
+def make_params(problem=None, **kw) -> fmg_params:
+    """fmg_params from a workloads.Problem (and/or keyword overrides)."""
+    p = fmg_default_params()
+    if problem is not None:
+        p.dim = problem.dim
+        p.coarse_cells = problem.coarse_cells
+        p.refinements = problem.refinements
+        p.f = NONLIN[problem.f]
+        p.f_scale = problem.a
+        p.m_vcycles = problem.m_vcycles
+        p.nu_pre = problem.nu_pre
+        p.nu_post = problem.nu_post
+        p.p_corrections = problem.p_corrections
+    for k, v in kw.items():
+        if k == "f" and isinstance(v, str):
+            v = NONLIN[v]
+        if k == "precision" and isinstance(v, str):
+            v = PREC[v]
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """One problem instance on the current CUDA device.
+
+    The context's workspace is a torch uint8 tensor (PyTorch's caching
+    allocator owns the memory); the solver's work is ordered on `stream` (a
+    torch.cuda.Stream; default: a new stream of its own), and solve() orders it
+    after the caller's current stream and the caller's stream after it.
+    """
+
+    def __init__(self, params: fmg_params, g_fine, stream=None):
+        import torch
+
+        self.params = params
+        self.dim = params.dim
+        self.n_fine = params.coarse_cells << params.refinements
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        nbytes = fmg_workspace_bytes(params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if isinstance(g_fine, np.ndarray):
+            g_fine = np.ascontiguousarray(g_fine, dtype=np.float64)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        self.ctx = fmg_create(params, g_fine, self.stream.cuda_stream, self.workspace, nbytes)
+
+    @property
+    def shape(self):
+        return (self.n_fine + 1,) * self.dim
+
+    def solve(self, out=None, stats: fmg_stats | None = None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        self.stream.wait_stream(torch.cuda.current_stream())
+        fmg_solve(self.ctx, out, stats)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        out.record_stream(self.stream)
+        return out
+
+    def set_rhs(self, g_fine):
+        import torch
+
+        self.stream.wait_stream(torch.cuda.current_stream())
+        if isinstance(g_fine, np.ndarray):
+            g_fine = np.ascontiguousarray(g_fine, dtype=np.float64)
+        fmg_set_rhs(self.ctx, g_fine)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            fmg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
