@@ -72,7 +72,9 @@ typedef enum {
   FMG_PREC_FP64 = 0,   /* every step in FP64 */
   FMG_PREC_MIXED = 1   /* multigrid cycles in FP32 inside an FP64 defect-correction loop:
                           FP64 residual and update on the cycle's top level, FP64 coarsest
-                          solve, FP64 augmented Newton and its quadrature sums */
+                          solve, FP64 augmented Newton residual and its quadrature sums; the
+                          Newton Jacobian's per-node products are FP32 (summed in FP64 across
+                          threads), which changes the convergence rate, not the solution */
 } fmg_precision;
 
 typedef struct {
@@ -104,8 +106,10 @@ typedef struct {
 } fmg_stats;
 
 /* Defaults: dim 2, 1/H = 4, 4 refinements, cubic, a = 1, m = 2, nu = 2/2, p = 1 (the
- * schedule of Sec. 4: m = 2, p = 1), FP64, Newton tol 1e-12 / cap 20, level-1 tol 1e-13 /
- * cap 50. */
+ * schedule of Sec. 4: m = 2, p = 1), FP64, Newton tol 1e-8 / cap 20, level-1 tol 1e-8 /
+ * cap 50.  Newton converges quadratically near the solution, so the update that passes the
+ * 1e-8 test leaves an error of order 1e-16; in the mixed path the FP32 Jacobian makes the
+ * convergence linear with a rate near 1e-5, leaving about 1e-13. */
 void fmg_default_params(fmg_params* p);
 
 /* Device bytes one context needs for these parameters (the workspace size fmg_create
@@ -189,6 +193,29 @@ fmg_status fmg_op_level1_solve(fmg_ctx* c, double* u, fmg_stats* st);
 
 /* u_fine = P_k u_coarse: the natural inclusion V_{h_{k-1}} -> V_{h_k} (eq. 3.3), k >= 2. */
 fmg_status fmg_op_prolong(fmg_ctx* c, int level, const double* u_coarse, double* u_fine);
+
+/* ---------------------------------------------------------------------------------------
+ * Diagnostics: kernel timing inside the captured solve graph, and its size.
+ * ------------------------------------------------------------------------------------- */
+
+typedef enum {
+  FMG_KT_AUGMENTED = 0,   /* the augmented-space Newton kernel of a correction step (eq. 3.6) */
+  FMG_KT_SMOOTH_TOP = 1,  /* one red-black sweep (both colours) on the cycle's top level */
+  FMG_KT_CORRECTION = 2   /* a whole correction step (Algorithm 3.1) */
+} fmg_kernel_kind;
+
+/* on != 0: the next fmg_solve recaptures its graph with a pair of CUDA events around every
+ * instrumented launch (event-record nodes; they add a little time to the solve).  on = 0
+ * recaptures without them. */
+fmg_status fmg_set_kernel_timing(fmg_ctx* c, int on);
+
+/* Sum of the durations (ms) of the instrumented launches of `kind` in the most recent solve,
+ * on `level` (1-based) or on all levels (level = 0), and their number.  Waits for the
+ * context stream. */
+fmg_status fmg_kernel_time(fmg_ctx* c, int kind, int level, double* total_ms, int* launches);
+
+/* Kernel nodes in the captured solve graph (0 before the first solve, -1 for NULL). */
+int fmg_graph_kernels(const fmg_ctx* c);
 
 #ifdef __cplusplus
 }

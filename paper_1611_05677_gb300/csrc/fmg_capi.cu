@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "fmg_internal.cuh"
 
@@ -36,6 +37,15 @@ struct fmg_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   unsigned pending_flags = 0;
+  int graph_kernels = 0;
+  // kernel timing (diagnostics): event pairs recorded inside the captured graph
+  bool timing = false;
+  struct Timed {
+    int kind, level;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Timed> timed;
+  size_t timed_next = 0;
   std::string err;
 };
 
@@ -137,39 +147,100 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
   return off;
 }
 
+// ------------------------------------------------------------------ kernel timing
+// In timing mode every instrumented launch is bracketed by two events recorded on the
+// context stream; inside a capture they become event-record nodes of the graph, so each
+// replay refreshes the timestamps.  Events are created on the first capture and reused.
+// tbegin allocates a slot (or returns -1 when timing is off) and records its first event;
+// tend records the second event of that slot.  Slots nest freely.
+cudaError_t tbegin(fmg_ctx* c, int kind, int level, int* slot) {
+  *slot = -1;
+  if (!c->timing) return cudaSuccess;
+  cudaError_t e;
+  if (c->timed_next == c->timed.size()) {
+    fmg_ctx::Timed t{kind, level, nullptr, nullptr};
+    if ((e = cudaEventCreate(&t.e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&t.e1)) != cudaSuccess) {
+      cudaEventDestroy(t.e0);
+      return e;
+    }
+    c->timed.push_back(t);
+  }
+  const size_t i = c->timed_next++;
+  c->timed[i].kind = kind;
+  c->timed[i].level = level;
+  *slot = (int)i;
+  return cudaEventRecordWithFlags(c->timed[i].e0, c->stream, cudaEventRecordExternal);
+}
+
+cudaError_t tend(fmg_ctx* c, int slot) {
+  if (slot < 0 || (size_t)slot >= c->timed.size()) return cudaSuccess;
+  return cudaEventRecordWithFlags(c->timed[slot].e1, c->stream, cudaEventRecordExternal);
+}
+
+#define TRY(expr)                                 \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return e_;             \
+  } while (0)
+
 // ------------------------------------------------------------------ schedule pieces
-cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b) {
+// Largest level handled by the one-CTA coarse cycle: its level arrays (u and b of every level
+// up to it) must fit in shared memory; 2D up to 64 cells per side, 3D up to 16.
+template <typename T>
+int coarse_cycle_top(const fmg_ctx* c) {
+  const int nmax = c->p.dim == 2 ? 64 : 16;
+  int j = 1;
+  while (j < c->nlev && c->geo[j].n <= nmax && coarse_cycle_smem<T>(c->p.dim, c->p.coarse_cells, j + 1) <= 200 * 1024)
+    ++j;
+  return j;
+}
+
+cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
   cudaError_t e;
   if (j == 1) return launch_coarse_solve_f64(dim, c->geo[0], c->Ainv, b, u, s);
+  if (j <= coarse_cycle_top<double>(c))
+    return launch_coarse_cycle<double>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s);
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
   for (int it = 0; it < c->p.nu_pre; ++it) {
+    int slot = -1;
+    if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     if ((e = launch_rbgs<double>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
     if ((e = launch_rbgs<double>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+    TRY(tend(c, slot));
   }
   if ((e = launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s)) != cudaSuccess)
     return e;
   if ((e = vcycle(c, j - 1, c->u[j - 2], c->b[j - 2])) != cudaSuccess) return e;
   if ((e = launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s)) != cudaSuccess) return e;
   for (int it = 0; it < c->p.nu_post; ++it) {
+    int slot = -1;
+    if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     if ((e = launch_rbgs<double>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
     if ((e = launch_rbgs<double>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+    TRY(tend(c, slot));
   }
   return cudaSuccess;
 }
 
-cudaError_t vcycle32(fmg_ctx* c, int j) {
+cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
   cudaError_t e;
   float* u = c->u32[j - 1];
   const float* b = c->b32[j - 1];
   if (j == 1) return launch_coarse_solve_f32(dim, c->geo[0], c->Ainv, b, u, s);
+  if (j <= coarse_cycle_top<float>(c))
+    return launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s);
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
   for (int it = 0; it < c->p.nu_pre; ++it) {
+    int slot = -1;
+    if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     if ((e = launch_rbgs<float>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
     if ((e = launch_rbgs<float>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+    TRY(tend(c, slot));
   }
   if ((e = launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s)) !=
       cudaSuccess)
@@ -177,21 +248,24 @@ cudaError_t vcycle32(fmg_ctx* c, int j) {
   if ((e = vcycle32(c, j - 1)) != cudaSuccess) return e;
   if ((e = launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s)) != cudaSuccess) return e;
   for (int it = 0; it < c->p.nu_post; ++it) {
+    int slot = -1;
+    if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     if ((e = launch_rbgs<float>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
     if ((e = launch_rbgs<float>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+    TRY(tend(c, slot));
   }
   return cudaSuccess;
 }
 
 // One multigrid cycle for A_k u = b at the top level k, in the context's precision.
 cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
-  if (c->p.precision == FMG_PREC_FP64 || k == 1) return vcycle(c, k, u, b);
+  if (c->p.precision == FMG_PREC_FP64 || k == 1) return vcycle(c, k, u, b, true);
   cudaError_t e;
   const LevelGeo g = c->geo[k - 1];
   // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update
   if ((e = launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream)) != cudaSuccess)
     return e;
-  if ((e = vcycle32(c, k)) != cudaSuccess) return e;
+  if ((e = vcycle32(c, k, true)) != cudaSuccess) return e;
   return launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream);
 }
 
@@ -199,6 +273,8 @@ cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
 cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
   cudaError_t e;
   const LevelGeo g = c->geo[k - 1];
+  int slot_step = -1, slot_aug = -1;
+  TRY(tbegin(c, FMG_KT_CORRECTION, k, &slot_step));
   // step 1: b = (g, v) - (f(x, u^{(l)}), v)   (eq. 3.4)
   if ((e = launch_nonlinear_rhs(c->p.dim, g, u, c->g[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream)) !=
       cudaSuccess)
@@ -206,12 +282,16 @@ cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
   for (int i = 0; i < c->p.m_vcycles; ++i)
     if ((e = top_cycle(c, k, u, c->b[k - 1])) != cudaSuccess) return e;
   // step 2: semilinear problem on V_H + span{u~}  (eq. 3.6)
-  return launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->g[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
-                          c->p.newton_maxit, c->ab, c->st, k - 1, c->stream);
+  TRY(tbegin(c, FMG_KT_AUGMENTED, k, &slot_aug));
+  TRY(launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->g[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
+                       c->p.newton_maxit, c->p.precision == FMG_PREC_MIXED, c->ab, c->st, k - 1, c->stream));
+  TRY(tend(c, slot_aug));
+  return tend(c, slot_step);
 }
 
 cudaError_t run_fmg(fmg_ctx* c) {
   cudaError_t e;
+  c->timed_next = 0;
   // per-solve statistics start at zero (flags, iteration counts, alphas)
   if ((e = cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream)) != cudaSuccess) return e;
   if ((e = launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
@@ -287,9 +367,9 @@ void fmg_default_params(fmg_params* p) {
   p->nu_post = 2;
   p->p_corrections = 1;
   p->precision = FMG_PREC_FP64;
-  p->newton_tol = 1e-12;
+  p->newton_tol = 1e-8;
   p->newton_maxit = 20;
-  p->level1_tol = 1e-13;
+  p->level1_tol = 1e-8;
   p->level1_maxit = 50;
 }
 
@@ -386,6 +466,16 @@ fmg_status fmg_solve(fmg_ctx* c, double* u_out, int out_on_device, fmg_stats* st
       return fail(c, FMG_ERR_CUDA,
                   std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
+    size_t nn = 0;
+    c->graph_kernels = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c->graph_kernels;
+        }
+    }
     e = cudaGraphInstantiate(&c->gexec, graph, 0);
     if (e != cudaSuccess) {
       cudaGraphDestroy(graph);
@@ -422,9 +512,46 @@ fmg_status fmg_solve_batch(fmg_ctx** cs, int count, double** u_outs, fmg_stats* 
   return worst;
 }
 
+fmg_status fmg_set_kernel_timing(fmg_ctx* c, int on) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if ((on != 0) != c->timing) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->timing = on != 0;
+  }
+  return FMG_OK;
+}
+
+fmg_status fmg_kernel_time(fmg_ctx* c, int kind, int level, double* total_ms, int* launches) {
+  if (!c || !total_ms) return fail(c, FMG_ERR_INVALID, "bad arguments");
+  CK(c, cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  int n = 0;
+  for (size_t i = 0; i < c->timed_next && i < c->timed.size(); ++i) {
+    const fmg_ctx::Timed& t = c->timed[i];
+    if (t.kind != kind || (level != 0 && t.level != level)) continue;
+    float ms = 0.0f;
+    CK(c, cudaEventElapsedTime(&ms, t.e0, t.e1));
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  if (launches) *launches = n;
+  return FMG_OK;
+}
+
+int fmg_graph_kernels(const fmg_ctx* c) { return c ? c->graph_kernels : -1; }
+
 fmg_status fmg_destroy(fmg_ctx* c) {
   if (!c) return FMG_OK;
   cudaStreamSynchronize(c->stream);
+  for (auto& t : c->timed) {
+    cudaEventDestroy(t.e0);
+    cudaEventDestroy(t.e1);
+  }
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->own_arena && c->arena) cudaFree(c->arena);
@@ -478,6 +605,7 @@ fmg_status fmg_op_residual(fmg_ctx* c, int level, const double* b, const double*
 fmg_status fmg_op_vcycle(fmg_ctx* c, int level, const double* b, double* u, int cycles) {
   if (fmg_status s = check_level(c, level, 1)) return s;
   if (!b || !u || cycles < 0) return fail(c, FMG_ERR_INVALID, "bad cycle arguments");
+  c->timed_next = 0;
   for (int i = 0; i < cycles; ++i) CK(c, top_cycle(c, level, u, b));
   return read_state(c, nullptr, false);
 }
@@ -486,6 +614,7 @@ fmg_status fmg_op_correction_step(fmg_ctx* c, int level, double* u, fmg_stats* s
   if (fmg_status s = check_level(c, level, 2)) return s;
   if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
   CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  c->timed_next = 0;
   CK(c, correction_step(c, level, u));
   return read_state(c, st, false);
 }

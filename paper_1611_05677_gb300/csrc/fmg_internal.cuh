@@ -145,6 +145,14 @@ cudaError_t launch_coarse_solve_f64(int dim, LevelGeo g1, const double* Ainv, co
 cudaError_t launch_coarse_solve_f32(int dim, LevelGeo g1, const double* Ainv, const float* b, float* u,
                                     cudaStream_t s);
 
+// The whole V-cycle on levels jtop..1 in one CTA with shared-memory level arrays (level j
+// has n0 << (j-1) cells per side); u (in/out) and b are level jtop's nodal arrays.
+template <typename T>
+size_t coarse_cycle_smem(int dim, int n0, int jtop);
+template <typename T>
+cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int nu_pre, int nu_post,
+                                const double* Ainv, cudaStream_t s);
+
 // level-1 setup: Ainv = A_1^{-1} (dense, N_1 x N_1) by Cholesky; flags on failure
 cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s);
 
@@ -166,8 +174,9 @@ struct AugBuffers {
 // Fills bpc/nt/smem/partial_items for this device (occupancy-based), outside any capture.
 void aug_configure(int dim, int coarse_cells, AugBuffers* ab);
 int aug_nvals(int dim);
+// jac_f32: Jacobian moments in FP32 (residual stays FP64) -- the mixed-precision path.
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
-                             int kind, double a, double tol, int maxit, const AugBuffers& ab, DevState* st,
-                             int level_index, cudaStream_t s);
+                             int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
+                             DevState* st, int level_index, cudaStream_t s);
 
 }  // namespace fmg

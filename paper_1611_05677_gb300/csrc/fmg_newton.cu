@@ -4,7 +4,7 @@
 //   * Algorithm 3.1 step 2 (eq. 3.6): the semilinear problem on V_{H,h_k} = V_H + span{u~},
 //     solved by Newton on y = (c, alpha), u = P_{H->k} c + alpha u~.  Every Newton iteration
 //     assembles the (N_H+1)-dimensional system from one pass over the fine nodes (the
-//     O(N_k) assembly the paper's work estimate, Theorem 3.3, counts per nonlinear step).
+//     O(N_k) assembly the work estimate of Theorem 3.3 counts per nonlinear step).
 //
 // Galerkin structure of the augmented system with B = [P_{H->k} | u~] and vertex quadrature
 // (weights w = h_k^d):
@@ -13,15 +13,26 @@
 //   J_HH  = A_H + P^T diag(w f'(U)) P,  J_Ha = t + P^T (w f'(U) u~),  J_aa = s + u~.(w f'(U) u~)
 // with U = alpha u~ + P c and A_H = P^T A_k P the coarse stiffness (nested P1 spaces).
 //
-// P_{H->k} c at a fine node x is the P1 interpolant of the coarse nodal values: x lies in
-// coarse cell floor(x / s) (s = 2^(k-1) fine cells per coarse cell) with local offsets o in
-// [0, s)^d; sorting the axes by decreasing o gives the Kuhn simplex v_0 = 0,
-// v_{t+1} = v_t + e_{pi_t} and barycentric weights lambda_0 = (s - o_{pi_0})/s,
-// lambda_t = (o_{pi_{t-1}} - o_{pi_t})/s, lambda_d = o_{pi_{d-1}}/s.
+// P_{H->k} c at a fine node is the P1 interpolant of the coarse nodal values.  A fine node
+// lies in coarse cell floor(x/s) (s = 2^(k-1) fine cells per coarse cell) at local offsets
+// o in [0,s)^d; sorting the axes by decreasing offset (ties: lower axis first) gives the Kuhn
+// simplex v_0 = 0, v_{t+1} = v_t + e_{pi_t}, with barycentric weights
+// lambda_0 = (s - o_{pi_0})/s, lambda_t = (o_{pi_{t-1}} - o_{pi_t})/s, lambda_d = o_{pi_{d-1}}/s.
 //
-// Reductions are deterministic: per-thread accumulators in shared memory, fixed-order
-// warp-shuffle and block sums, fixed-order sums over blocks and coarse cells.
+// Fine pass layout.  A thread walks a column of a coarse cell: all offsets fixed except the
+// last one (z).  Along the column the simplex changes only where z crosses the fixed
+// offsets, so the column splits into d segments; on a segment every lambda_t is affine in z,
+// lambda_t = (P_t + R_t z)/s, and every sum the system needs is a combination of the
+// segment's moments sum X, sum X z, sum X z^2.  The thread accumulates those moments in
+// registers (FP64 for the residual; FP32 or FP64 for the Jacobian) and converts them to the
+// cell's vertex channels once per segment.  The first pass also gathers t, G_H, s and gamma
+// (at (c, alpha) = (0, 1), U = u~), so no separate precompute pass is needed.
+//
+// Reductions are deterministic: per-thread channel rows in shared memory, fixed-order block
+// sums, fixed-order sums over blocks and cells.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "fmg_internal.cuh"
 
@@ -29,69 +40,77 @@ namespace fmg {
 
 namespace {
 
-// ------------------------------------------------------------------ dense SPD solve (one CTA)
-// In-place Cholesky (lower) of the n x n matrix M (row-major, leading dimension ld, in shared
-// memory) followed by the solve M x = rhs (rhs overwritten).  `shared` must hold 2 doubles.
-// If `drop_last` and the last pivot is below drop_tol times its original value, the last
-// unknown is frozen (its increment is 0) and *dropped is set.  Returns false if not SPD.
-__device__ bool block_chol_solve(double* M, int n, int ld, double* rhs, double* shared, bool drop_last,
-                                 double drop_tol, int* dropped) {
-  const int tid = threadIdx.x;
-  const int nt = blockDim.x;
-  __shared__ int bad;
-  __shared__ int drop;
-  if (tid == 0) {
-    bad = 0;
-    drop = 0;
-    shared[1] = drop_last ? M[(long long)(n - 1) * ld + (n - 1)] : 0.0;
-  }
-  __syncthreads();
+// ------------------------------------------------------------------ small dense SPD solve
+// 1/sqrt(d) for d > 0: FP32 estimate refined by two Newton steps in FP64
+// (y <- y (3 - d y^2) / 2), accurate to a few ulp.
+__device__ __forceinline__ double rsqrt_refined(double d) {
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
+// Cholesky (lower) of the n x n SPD matrix M (row-major, leading dimension ld, shared
+// memory) and solve M x = rhs (rhs overwritten), by ONE warp; the other warps of the block
+// must not touch M/rhs meanwhile.  invd (n doubles, shared) receives 1/L_kk.
+// If drop_last and the last pivot falls below drop_tol times the original last diagonal
+// entry, the last unknown is frozen (increment 0) and *dropped = 1.  Returns false if not SPD.
+__device__ bool warp_chol_solve(double* M, int n, int ld, double* rhs, double* invd, bool drop_last,
+                                double drop_tol, int* dropped) {
+  const int lane = threadIdx.x & 31;
+  bool bad = false;
+  int drop = 0;
+  const double last0 = drop_last ? M[(n - 1) * ld + (n - 1)] : 0.0;
   for (int k = 0; k < n; ++k) {
-    if (tid == 0) {
-      double d = M[k * ld + k];
-      if (drop_last && k == n - 1 && !(d > drop_tol * shared[1])) {
-        drop = 1;
-        d = 1.0;
-        for (int j = 0; j < k; ++j) M[k * ld + j] = 0.0;
-        rhs[k] = 0.0;
-      } else if (!(d > 0.0)) {
-        bad = 1;
-        d = 1.0;
-      }
-      const double r = sqrt(d);
-      M[k * ld + k] = r;
-      shared[0] = 1.0 / r;
+    double d = M[k * ld + k];
+    __syncwarp();
+    if (drop_last && k == n - 1 && !(d > drop_tol * last0)) {
+      drop = 1;
+      d = 1.0;
+      for (int j = lane; j < k; j += 32) M[k * ld + j] = 0.0;
+      if (lane == 0) rhs[k] = 0.0;
+    } else if (!(d > 0.0)) {
+      bad = true;
+      d = 1.0;
     }
-    __syncthreads();
-    const double inv = shared[0];
-    for (int i = k + 1 + tid; i < n; i += nt) M[i * ld + k] *= inv;
-    __syncthreads();
+    const double inv = rsqrt_refined(d);
+    if (lane == 0) {
+      M[k * ld + k] = d * inv;
+      invd[k] = inv;
+    }
+    for (int i = k + 1 + lane; i < n; i += 32) M[i * ld + k] *= inv;
+    __syncwarp();
+    // trailing update of rows i > k, columns k < j <= i: the triangle flattened over lanes
     const int m = n - k - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      const int i = k + 1 + idx / m;
-      const int j = k + 1 + idx % m;
-      if (j <= i) M[i * ld + j] -= M[i * ld + k] * M[j * ld + k];
+    const int T = m * (m + 1) / 2;
+    for (int idx = lane; idx < T; idx += 32) {
+      int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+      if ((r + 1) * (r + 2) / 2 <= idx) ++r;
+      if (r * (r + 1) / 2 > idx) --r;
+      const int i = k + 1 + r;
+      const int j = k + 1 + (idx - r * (r + 1) / 2);
+      M[i * ld + j] -= M[i * ld + k] * M[j * ld + k];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  // forward substitution L y = rhs
+  // forward L y = rhs
   for (int k = 0; k < n; ++k) {
-    if (tid == 0) rhs[k] /= M[k * ld + k];
-    __syncthreads();
-    const double yk = rhs[k];
-    for (int i = k + 1 + tid; i < n; i += nt) rhs[i] -= M[i * ld + k] * yk;
-    __syncthreads();
+    const double yk = rhs[k] * invd[k];
+    __syncwarp();
+    if (lane == 0) rhs[k] = yk;
+    for (int i = k + 1 + lane; i < n; i += 32) rhs[i] -= M[i * ld + k] * yk;
+    __syncwarp();
   }
-  // back substitution L^T x = y
+  // backward L^T x = y
   for (int k = n - 1; k >= 0; --k) {
-    if (tid == 0) rhs[k] /= M[k * ld + k];
-    __syncthreads();
-    const double xk = rhs[k];
-    for (int i = tid; i < k; i += nt) rhs[i] -= M[k * ld + i] * xk;
-    __syncthreads();
+    const double xk = rhs[k] * invd[k];
+    __syncwarp();
+    if (lane == 0) rhs[k] = xk;
+    for (int i = lane; i < k; i += 32) rhs[i] -= M[k * ld + i] * xk;
+    __syncwarp();
   }
   if (dropped) *dropped = drop;
-  return bad == 0;
+  return !bad;
 }
 
 // Level-1 unknown r <-> nodal offset of interior node (r % m + 1, (r/m) % m + 1, r/m^2 + 1).
@@ -104,16 +123,28 @@ __device__ __forceinline__ long long node_of(int r, int m, int dim) {
   return ((long long)l * np + j) * np + i;
 }
 
-// A_1 entry between unknowns p and q: sigma (2d on the diagonal, -1 for axis neighbours).
-__device__ __forceinline__ double stiff_entry(int p, int q, int m, int dim, double sigma) {
-  if (p == q) return sigma * 2 * dim;
-  int pc[3] = {p % m, (p / m) % m, p / (m * m)};
-  int qc[3] = {q % m, (q / m) % m, q / (m * m)};
-  int dist = 0;
-  for (int a = 0; a < dim; ++a) dist += abs(pc[a] - qc[a]);
-  return dist == 1 ? -sigma : 0.0;
+// Writes the dense A_1 = sigma (2d on the diagonal, -1 for axis neighbours) into M.
+__device__ void fill_stiffness(double* M, int N, int ld, int m, int dim, double sigma) {
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int p = idx / N, q = idx % N;
+    double v = 0.0;
+    if (p == q) {
+      v = sigma * 2 * dim;
+    } else {
+      int dist = 0;
+      int pp = p, qq = q;
+      for (int a = 0; a < dim; ++a) {
+        dist += abs(pp % m - qq % m);
+        pp /= m;
+        qq /= m;
+      }
+      if (dist == 1) v = -sigma;
+    }
+    M[p * ld + q] = v;
+  }
 }
 
+// Level-1 setup: Cholesky of A_1 once, then A_1^{-1} column by column (one thread per column).
 __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, DevState* st) {
   extern __shared__ double sm[];
   const int m = n1 - 1;
@@ -121,23 +152,33 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
   const int ld = N + 1;
   double* M = sm;
   double* rhs = M + (size_t)N * ld;
-  double* sh = rhs + N;
+  double* invd = rhs + N;
   const double sigma = dim == 2 ? 1.0 : 1.0 / n1;
-  for (int col = 0; col < N; ++col) {
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int i = idx / N, j = idx % N;
-      M[i * ld + j] = stiff_entry(i, j, m, dim, sigma);
-    }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) rhs[i] = (i == col) ? 1.0 : 0.0;
-    __syncthreads();
-    bool ok = block_chol_solve(M, N, ld, rhs, sh, false, 0.0, nullptr);
+  fill_stiffness(M, N, ld, m, dim, sigma);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) rhs[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool ok = warp_chol_solve(M, N, ld, rhs, invd, false, 0.0, nullptr);
     if (!ok && threadIdx.x == 0) atomicOr(&st->flags, kFlagNotSPD);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) Ainv[(long long)i * N + col] = rhs[i];
-    __syncthreads();
+  }
+  __syncthreads();
+  // column `col` of the inverse: L L^T x = e_col (A^{-1} is symmetric: column = row)
+  for (int col = threadIdx.x; col < N; col += blockDim.x) {
+    double* x = Ainv + (long long)col * N;
+    for (int k = 0; k < N; ++k) {
+      double acc = (k == col) ? 1.0 : 0.0;
+      for (int j = 0; j < k; ++j) acc -= M[k * ld + j] * x[j];
+      x[k] = acc * invd[k];
+    }
+    for (int k = N - 1; k >= 0; --k) {
+      double acc = x[k];
+      for (int j = k + 1; j < N; ++j) acc -= M[j * ld + k] * x[j];
+      x[k] = acc * invd[k];
+    }
   }
 }
 
-// Algorithm 3.2 step 1: Newton on A_1 U + w f(U) = w g, from U = 0.
+// Algorithm 3.2 step 1: Newton on A_1 U + w f(U) = w g, from U = 0 (one CTA).
 __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
                                 double a, double tol, int maxit, DevState* st) {
   extern __shared__ double sm[];
@@ -147,10 +188,8 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
   double* M = sm;
   double* rhs = M + (size_t)N * ld;
   double* U = rhs + N;
-  double* Fp = U + N;
-  double* sh = Fp + N;
+  double* invd = U + N;
   __shared__ int done;
-  __shared__ double red[2];
   const double h = 1.0 / n1;
   const double sigma = dim == 2 ? 1.0 : h;
   const double w = dim == 2 ? h * h : h * h * h;
@@ -159,41 +198,50 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
   __syncthreads();
   int it = 0;
   for (it = 1; it <= maxit; ++it) {
-    // residual R = A U + w f(U) - w g  (stored negated in rhs) and Jacobian
+    fill_stiffness(M, N, ld, m, dim, sigma);
+    __syncthreads();
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       double F, D;
       f_eval<double>(kind, a, U[p], F, D);
-      double au = 0.0;
-      for (int q = 0; q < N; ++q) au += stiff_entry(p, q, m, dim, sigma) * U[q];
+      // (A U)_p from the stencil: sigma (2d U_p - sum of interior axis neighbours)
+      double nb = 0.0;
+      int rem = p, mul = 1;
+      for (int ax = 0; ax < dim; ++ax) {
+        const int c = rem % m;
+        rem /= m;
+        if (c > 0) nb += U[p - mul];
+        if (c < m - 1) nb += U[p + mul];
+        mul *= m;
+      }
+      const double au = sigma * (2.0 * dim * U[p] - nb);
       rhs[p] = -(au + w * F - w * g[node_of(p, m, dim)]);
-      Fp[p] = w * D;
+      M[p * ld + p] += w * D;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int i = idx / N, j = idx % N;
-      M[i * ld + j] = stiff_entry(i, j, m, dim, sigma) + (i == j ? Fp[i] : 0.0);
-    }
-    __syncthreads();
-    const bool ok = block_chol_solve(M, N, ld, rhs, sh, false, 0.0, nullptr);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      const bool ok = warp_chol_solve(M, N, ld, rhs, invd, false, 0.0, nullptr);
       double dmax = 0.0, umax = 0.0;
       bool finite = true;
-      for (int p = 0; p < N; ++p) {
+      for (int p = threadIdx.x; p < N; p += 32) {
         const double v = U[p] + rhs[p];
         if (!isfinite(v)) finite = false;
         dmax = fmax(dmax, fabs(rhs[p]));
         umax = fmax(umax, fabs(v));
+        U[p] = v;
       }
-      red[0] = dmax;
-      red[1] = umax;
-      if (!ok) atomicOr(&st->flags, kFlagNotSPD);
-      if (!finite) atomicOr(&st->flags, kFlagNonfinite);
-      if (!ok || !finite) done = 2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+      }
+      finite = __all_sync(0xffffffffu, finite);
+      if (threadIdx.x == 0) {
+        if (!ok) atomicOr(&st->flags, kFlagNotSPD);
+        if (!finite) atomicOr(&st->flags, kFlagNonfinite);
+        if (!ok || !finite) done = 2;
+        else if (dmax <= tol * fmax(1.0, umax)) done = 1;
+      }
     }
-    __syncthreads();
-    for (int p = threadIdx.x; p < N; p += blockDim.x) U[p] += rhs[p];
-    __syncthreads();
-    if (threadIdx.x == 0 && done == 0 && red[0] <= tol * fmax(1.0, red[1])) done = 1;
     __syncthreads();
     if (done) break;
   }
@@ -205,16 +253,22 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
 }
 
 // ------------------------------------------------------------------ augmented problem
-template <int D>
+template <int D, bool JF32>
 struct Aug {
-  static constexpr int NV = 1 << D;                      // vertices of a coarse cell
-  static constexpr int NP = NV * (NV + 1) / 2;           // vertex pairs (packed upper)
-  static constexpr int VA = 0;                           // vector channel A
-  static constexpr int VB = NV;                          // vector channel B
-  static constexpr int PP = 2 * NV;                      // pair channel
-  static constexpr int S0 = 2 * NV + NP;                 // scalar channels
-  static constexpr int NVAL = 2 * NV + NP + 2;
-  static constexpr int NT = D == 2 ? 256 : 128;          // threads per block
+  static constexpr int NV = 1 << D;             // vertices of a coarse cell
+  static constexpr int NP = NV * (NV + 1) / 2;  // vertex pairs (packed upper)
+  // channel layout of a block's partial sums (all stored as double)
+  static constexpr int RA = 0;                  // sum w f(U) lambda_v              [NV]
+  static constexpr int SA = NV;                 // sum w f(U) u~                     [1]
+  static constexpr int TT = NV + 1;             // sum (A u~) lambda_v  (first pass) [NV]
+  static constexpr int GH = 2 * NV + 1;         // sum w g lambda_v     (first pass) [NV]
+  static constexpr int SS = 3 * NV + 1;         // sum u~ A u~          (first pass) [1]
+  static constexpr int SG = 3 * NV + 2;         // sum w g u~           (first pass) [1]
+  static constexpr int JB = 3 * NV + 3;         // sum w f'(U) u~ lambda_v           [NV]
+  static constexpr int JP = 4 * NV + 3;         // sum w f'(U) lambda_v lambda_u     [NP]
+  static constexpr int JS = 4 * NV + 3 + NP;    // sum w f'(U) u~^2                  [1]
+  static constexpr int NVAL = 4 * NV + 4 + NP;
+  static constexpr int NT = D == 2 ? 256 : 128;
 };
 
 __device__ __forceinline__ int pair_index(int NV, int v, int u) {
@@ -227,7 +281,7 @@ __device__ __forceinline__ int pair_index(int NV, int v, int u) {
 }
 
 struct AugArgs {
-  int dim, nc, s, n, kind, maxit, level_index, bpc;
+  int dim, nc, s, n, kind, maxit, level_index, bpc, chunk;
   double a, w, sigma_k, sigma_H, tol;
   double* u;            // u~ on entry, u^{(l+1)} on exit (level-k nodal)
   const double* g;      // level-k nodal g
@@ -241,7 +295,7 @@ struct AugArgs {
 // abort word is set and every block leaves at its next check.
 __device__ void grid_barrier(DevState* st, unsigned nblocks) {
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (nblocks > 1 && threadIdx.x == 0) {
     volatile unsigned* genp = &st->bar_gen;
     const unsigned gen = *genp;
     __threadfence();
@@ -253,7 +307,7 @@ __device__ void grid_barrier(DevState* st, unsigned nblocks) {
     } else {
       long long spins = 0;
       while (*genp == gen) {
-        __nanosleep(64);
+        __nanosleep(32);
         if (++spins > (1ll << 25)) {
           atomicOr(&st->flags, kFlagTimeout);
           atomicExch(&st->abort, 1);
@@ -267,54 +321,68 @@ __device__ void grid_barrier(DevState* st, unsigned nblocks) {
   __syncthreads();
 }
 
-// Kuhn simplex of the local offsets o (in [0,s)^D): vertex ids and barycentric numerators.
+// One segment of a column: vertex ids, lambda numerators P + R z, and its z range [z0, z1].
 template <int D>
-__device__ __forceinline__ void kuhn_simplex(const int* o, int s, int* vid, int* lnum) {
-  int pi[D];
-#pragma unroll
-  for (int q = 0; q < D; ++q) pi[q] = q;
-  // sort axes by decreasing offset (ties keep axis order)
-#pragma unroll
-  for (int q = 0; q < D; ++q)
-#pragma unroll
-    for (int r = 0; r < D - 1 - q; ++r)
-      if (o[pi[r]] < o[pi[r + 1]]) {
-        const int t = pi[r];
-        pi[r] = pi[r + 1];
-        pi[r + 1] = t;
-      }
-  vid[0] = 0;
-  lnum[0] = s - o[pi[0]];
-#pragma unroll
-  for (int q = 1; q < D; ++q) {
-    vid[q] = vid[q - 1] | (1 << pi[q - 1]);
-    lnum[q] = o[pi[q - 1]] - o[pi[q]];
+struct Seg {
+  int vid[D + 1];
+  int P[D + 1];
+  int R[D + 1];
+  int z0, z1;
+};
+
+// Segments of the column with fixed offsets o[0..D-2] (the last axis, z, varies in [0,s)).
+template <int D>
+__device__ __forceinline__ int column_segments(const int* o, int s, Seg<D>* sg) {
+  if constexpr (D == 2) {
+    const int ox = o[0];
+    // z <= ox: pi = (x, y)
+    sg[0].vid[0] = 0; sg[0].vid[1] = 1; sg[0].vid[2] = 3;
+    sg[0].P[0] = s - ox; sg[0].P[1] = ox; sg[0].P[2] = 0;
+    sg[0].R[0] = 0; sg[0].R[1] = -1; sg[0].R[2] = 1;
+    sg[0].z0 = 0; sg[0].z1 = ox;
+    // z > ox: pi = (y, x)
+    sg[1].vid[0] = 0; sg[1].vid[1] = 2; sg[1].vid[2] = 3;
+    sg[1].P[0] = s; sg[1].P[1] = -ox; sg[1].P[2] = ox;
+    sg[1].R[0] = -1; sg[1].R[1] = 1; sg[1].R[2] = 0;
+    sg[1].z0 = ox + 1; sg[1].z1 = s - 1;
+    return 2;
+  } else {
+    const int ox = o[0], oy = o[1];
+    const bool xhi = ox >= oy;
+    const int hi = xhi ? ox : oy, lo = xhi ? oy : ox;
+    const int bh = xhi ? 1 : 2, bl = xhi ? 2 : 1;  // vertex bits of the hi / lo axis
+    // A: z <= lo, pi = (hi, lo, z)
+    sg[0].vid[0] = 0; sg[0].vid[1] = bh; sg[0].vid[2] = bh | bl; sg[0].vid[3] = 7;
+    sg[0].P[0] = s - hi; sg[0].P[1] = hi - lo; sg[0].P[2] = lo; sg[0].P[3] = 0;
+    sg[0].R[0] = 0; sg[0].R[1] = 0; sg[0].R[2] = -1; sg[0].R[3] = 1;
+    sg[0].z0 = 0; sg[0].z1 = lo;
+    // B: lo < z <= hi, pi = (hi, z, lo)
+    sg[1].vid[0] = 0; sg[1].vid[1] = bh; sg[1].vid[2] = bh | 4; sg[1].vid[3] = 7;
+    sg[1].P[0] = s - hi; sg[1].P[1] = hi; sg[1].P[2] = -lo; sg[1].P[3] = lo;
+    sg[1].R[0] = 0; sg[1].R[1] = -1; sg[1].R[2] = 1; sg[1].R[3] = 0;
+    sg[1].z0 = lo + 1; sg[1].z1 = hi;
+    // C: z > hi, pi = (z, hi, lo)
+    sg[2].vid[0] = 0; sg[2].vid[1] = 4; sg[2].vid[2] = 4 | bh; sg[2].vid[3] = 7;
+    sg[2].P[0] = s; sg[2].P[1] = -hi; sg[2].P[2] = hi - lo; sg[2].P[3] = lo;
+    sg[2].R[0] = -1; sg[2].R[1] = 1; sg[2].R[2] = 0; sg[2].R[3] = 0;
+    sg[2].z0 = hi + 1; sg[2].z1 = s - 1;
+    return 3;
   }
-  vid[D] = (1 << D) - 1;
-  lnum[D] = o[pi[D - 1]];
 }
 
-// Coarse nodal offset of vertex v of cell (I,J,L).
-__device__ __forceinline__ long long cell_vertex_node(int D, const int* cellc, int v, int nc) {
-  const long long cp = nc + 1;
-  long long off = 0, mul = 1;
-  for (int q = 0; q < D; ++q) {
-    off += (long long)(cellc[q] + ((v >> q) & 1)) * mul;
-    mul *= cp;
-  }
-  return off;
-}
+enum { kFirst = 0, kNewton = 1, kUpdate = 2 };
 
-// Phase kinds of the per-node pass.
-enum { kPre = 0, kNewton = 1, kUpdate = 2 };
-
-template <int D>
-__device__ void node_pass(const AugArgs& A, int phase, double* acc, const double* cv, double alpha, int cell,
+// The fine pass of one block: columns of its cell, chunk by chunk.  `acc` holds the
+// per-thread channel rows ([NVAL][NT] doubles), zero on entry.
+template <int D, bool JF32>
+__device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double* cv, double alpha, int cell,
                           int bic) {
-  using G = Aug<D>;
+  using G = Aug<D, JF32>;
+  using JT = typename std::conditional<JF32, float, double>::type;
   const int tid = threadIdx.x;
   const int s = A.s;
   const long long np = A.n + 1;
+  const long long zstride = D == 2 ? np : np * np;
   int cellc[3] = {0, 0, 0};
   {
     int t = cell;
@@ -323,79 +391,122 @@ __device__ void node_pass(const AugArgs& A, int phase, double* acc, const double
       t /= A.nc;
     }
   }
-  const long long per_cell = ipow(s, D);
+  const int ncol = D == 2 ? s : s * s;
+  const int nch = s / A.chunk;
+  const long long items = (long long)ncol * nch;
   const double inv_s = 1.0 / s;
-  const long long stride = (long long)A.bpc * G::NT;
-  for (long long li = (long long)bic * G::NT + tid; li < per_cell; li += stride) {
-    int o[D];
-    long long t = li;
-    long long off = 0, mul = 1;
-    bool interior = true;
+  const double inv_s2 = inv_s * inv_s;
+  for (long long q = (long long)bic * G::NT + tid; q < items; q += (long long)A.bpc * G::NT) {
+    const int col = (int)(q % ncol);
+    const int ch = (int)(q / ncol);
+    const int o[2] = {col % s, D == 3 ? col / s : 0};
+    // fine coordinates of the column; a column on the x = 0 (or y = 0) face is boundary
+    const int x = cellc[0] * s + o[0];
+    const int y = D == 3 ? cellc[1] * s + o[1] : 0;
+    if (x == 0 || (D == 3 && y == 0)) continue;
+    const int zc = cellc[D - 1] * s;                   // fine z of local offset 0
+    const long long base = D == 2 ? (long long)x : (long long)y * np + x;
+    const int zlo_chunk = ch * A.chunk;
+    const int zhi_chunk = zlo_chunk + A.chunk - 1;
+    const int zmin = (zc == 0) ? 1 : 0;                // z = 0 is the boundary face
+    Seg<D> sg[D];
+    const int nseg = column_segments<D>(o, s, sg);
+    for (int si = 0; si < nseg; ++si) {
+      const Seg<D>& S = sg[si];
+      const int z0 = max(max(S.z0, zlo_chunk), zmin);
+      const int z1 = min(S.z1, zhi_chunk);
+      if (z0 > z1) continue;
+      // P c on the segment: pc0 + pc1 z
+      double pc0 = 0.0, pc1 = 0.0;
+      if (phase != kFirst) {
 #pragma unroll
-    for (int q = 0; q < D; ++q) {
-      o[q] = (int)(t % s);
-      t /= s;
-      const int x = cellc[q] * s + o[q];
-      if (x == 0) interior = false;
-      off += (long long)x * mul;
-      mul *= np;
-    }
-    if (!interior) continue;
-    int vid[D + 1], lnum[D + 1];
-    kuhn_simplex<D>(o, s, vid, lnum);
-    double lam[D + 1];
-#pragma unroll
-    for (int q = 0; q <= D; ++q) lam[q] = lnum[q] * inv_s;
-    const double ut = A.u[off];
-    if (phase == kPre) {
-      double au;
-      if (D == 2) {
-        au = 4.0 * ut - ((A.u[off - 1] + A.u[off + 1]) + (A.u[off - np] + A.u[off + np]));
-      } else {
-        const long long pl = np * np;
-        au = A.sigma_k *
-             (6.0 * ut - (((A.u[off - 1] + A.u[off + 1]) + (A.u[off - np] + A.u[off + np])) +
-                          (A.u[off - pl] + A.u[off + pl])));
+        for (int t = 0; t <= D; ++t) {
+          pc0 += S.P[t] * cv[S.vid[t]];
+          pc1 += S.R[t] * cv[S.vid[t]];
+        }
+        pc0 *= inv_s;
+        pc1 *= inv_s;
       }
-      const double wg = A.w * A.g[off];
-#pragma unroll
-      for (int q = 0; q <= D; ++q) {
-        acc[(G::VA + vid[q]) * G::NT + tid] += au * lam[q];
-        acc[(G::VB + vid[q]) * G::NT + tid] += wg * lam[q];
+      double Q0 = 0.0, Q1 = 0.0, SAv = 0.0;                 // residual moments
+      JT D0 = 0, D1 = 0, D2 = 0, E0 = 0, E1 = 0, JSv = 0;   // Jacobian moments
+      double T0 = 0.0, T1 = 0.0, SSv = 0.0, G0 = 0.0, G1 = 0.0, SGv = 0.0;  // first pass
+      double zd = (double)z0;
+      long long off = base + (long long)(zc + z0) * zstride;
+      for (int z = z0; z <= z1; ++z, off += zstride, zd += 1.0) {
+        const double ut = A.u[off];
+        const double U = phase == kFirst ? ut : fma(alpha, ut, fma(pc1, zd, pc0));
+        if (phase == kUpdate) {
+          A.u[off] = U;
+          continue;
+        }
+        double F, Fp;
+        f_eval<double>(A.kind, A.a, U, F, Fp);
+        Q0 += F;
+        Q1 = fma(F, zd, Q1);
+        SAv = fma(F, ut, SAv);
+        const JT dj = (JT)Fp;
+        const JT uj = (JT)ut;
+        const JT zj = (JT)zd;
+        const JT dz = dj * zj;
+        const JT du = dj * uj;
+        D0 += dj;
+        D1 += dz;
+        D2 += dz * zj;
+        E0 += du;
+        E1 += du * zj;
+        JSv += du * uj;
+        if (phase == kFirst) {
+          double nb;
+          if constexpr (D == 2) {
+            nb = (A.u[off - 1] + A.u[off + 1]) + (A.u[off - zstride] + A.u[off + zstride]);
+          } else {
+            nb = ((A.u[off - 1] + A.u[off + 1]) + (A.u[off - np] + A.u[off + np])) +
+                 (A.u[off - zstride] + A.u[off + zstride]);
+          }
+          const double au = A.sigma_k * (2.0 * D * ut - nb);
+          const double gv = A.g[off];
+          T0 += au;
+          T1 = fma(au, zd, T1);
+          SSv = fma(au, ut, SSv);
+          G0 += gv;
+          G1 = fma(gv, zd, G1);
+          SGv = fma(gv, ut, SGv);
+        }
       }
-      acc[(G::S0) * G::NT + tid] += ut * au;
-      acc[(G::S0 + 1) * G::NT + tid] += wg * ut;
-    } else {
-      double U = alpha * ut;
+      if (phase == kUpdate) continue;
+      // moments -> vertex channels of this thread's row
+      const double w = A.w;
 #pragma unroll
-      for (int q = 0; q <= D; ++q) U += lam[q] * cv[vid[q]];
-      if (phase == kUpdate) {
-        A.u[off] = U;
-        continue;
+      for (int t = 0; t <= D; ++t) {
+        const double Pt = S.P[t], Rt = S.R[t];
+        const int v = S.vid[t];
+        acc[(G::RA + v) * G::NT + tid] += w * inv_s * (Pt * Q0 + Rt * Q1);
+        acc[(G::JB + v) * G::NT + tid] += w * inv_s * (Pt * (double)E0 + Rt * (double)E1);
+        if (phase == kFirst) {
+          acc[(G::TT + v) * G::NT + tid] += inv_s * (Pt * T0 + Rt * T1);
+          acc[(G::GH + v) * G::NT + tid] += w * inv_s * (Pt * G0 + Rt * G1);
+        }
+#pragma unroll
+        for (int r = t; r <= D; ++r) {
+          const double Pr = S.P[r], Rr = S.R[r];
+          acc[(G::JP + pair_index(G::NV, v, S.vid[r])) * G::NT + tid] +=
+              w * inv_s2 * (Pt * Pr * (double)D0 + (Pt * Rr + Rt * Pr) * (double)D1 + Rt * Rr * (double)D2);
+        }
       }
-      double F, Fp;
-      f_eval<double>(A.kind, A.a, U, F, Fp);
-      const double q_ = A.w * F;
-      const double d_ = A.w * Fp;
-      const double du = d_ * ut;
-#pragma unroll
-      for (int q = 0; q <= D; ++q) {
-        acc[(G::VA + vid[q]) * G::NT + tid] += q_ * lam[q];
-        acc[(G::VB + vid[q]) * G::NT + tid] += du * lam[q];
-        const double dl = d_ * lam[q];
-#pragma unroll
-        for (int r = q; r <= D; ++r) acc[(G::PP + pair_index(G::NV, vid[q], vid[r])) * G::NT + tid] += dl * lam[r];
+      acc[G::SA * G::NT + tid] += w * SAv;
+      acc[G::JS * G::NT + tid] += w * (double)JSv;
+      if (phase == kFirst) {
+        acc[G::SS * G::NT + tid] += SSv;
+        acc[G::SG * G::NT + tid] += w * SGv;
       }
-      acc[(G::S0) * G::NT + tid] += q_ * ut;
-      acc[(G::S0 + 1) * G::NT + tid] += du * ut;
     }
   }
 }
 
-// Block sum of the accumulator rows into partials[blockIdx.x][*] (fixed order).
-template <int D>
+// Block sum of the channel rows into out[0..NVAL) (fixed order).
+template <int D, bool JF32>
 __device__ void block_reduce_rows(const double* acc, double* out) {
-  using G = Aug<D>;
+  using G = Aug<D, JF32>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = G::NT / 32;
   __syncthreads();
   for (int v = warp; v < G::NVAL; v += nw) {
@@ -404,22 +515,6 @@ __device__ void block_reduce_rows(const double* acc, double* out) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) out[v] = x;
-  }
-  __syncthreads();
-}
-
-// Sum over the blocks of each cell, then over the cells around each coarse node (fixed
-// orders).  Result: per coarse unknown p: vecA[p], vecB[p]; per unknown pair: pairs; scalars.
-// Writes into the dense system arrays of block 0 in shared memory.
-template <int D>
-__device__ void gather_cells(const AugArgs& A, double* cellsum) {
-  using G = Aug<D>;
-  const int ncell = (int)ipow(A.nc, D);
-  for (int idx = threadIdx.x; idx < ncell * G::NVAL; idx += blockDim.x) {
-    const int cell = idx / G::NVAL, v = idx % G::NVAL;
-    double x = 0.0;
-    for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + v]);
-    cellsum[idx] = x;
   }
   __syncthreads();
 }
@@ -435,53 +530,213 @@ __device__ __forceinline__ void unknown_coords(int p, int nc, int* z) {
   }
 }
 
-// Sum of channel `ch` at vertex p over the 2^D cells around coarse node p.
 template <int D>
+__device__ __forceinline__ long long coarse_offset(const int* z, int nc) {
+  const long long cp = nc + 1;
+  long long off = 0, mul = 1;
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    off += (long long)z[q] * mul;
+    mul *= cp;
+  }
+  return off;
+}
+
+// Sum of channel `ch` at vertex p over the cells around coarse node p.
+template <int D, bool JF32>
 __device__ double node_channel(const double* cellsum, int nc, const int* z, int ch) {
-  using G = Aug<D>;
+  using G = Aug<D, JF32>;
   double x = 0.0;
   for (int o = 0; o < G::NV; ++o) {
-    int cc[3];
     bool ok = true;
     int cell = 0, mul = 1;
     for (int q = 0; q < D; ++q) {
-      cc[q] = z[q] - ((o >> q) & 1);
-      if (cc[q] < 0 || cc[q] >= nc) ok = false;
-      cell += cc[q] * mul;
+      const int cc = z[q] - ((o >> q) & 1);
+      if (cc < 0 || cc >= nc) ok = false;
+      cell += cc * mul;
       mul *= nc;
     }
-    if (!ok) continue;
-    x += cellsum[(long long)cell * G::NVAL + ch + o];
+    if (ok) x += cellsum[(long long)cell * G::NVAL + ch + o];
   }
   return x;
 }
 
-template <int D>
+template <int D, bool JF32>
 __device__ double pair_channel(const double* cellsum, int nc, const int* zp, const int* zq) {
-  using G = Aug<D>;
+  using G = Aug<D, JF32>;
   double x = 0.0;
   for (int o = 0; o < G::NV; ++o) {
-    int cc[3];
     bool ok = true;
     int cell = 0, mul = 1, vq = 0;
     for (int q = 0; q < D; ++q) {
-      cc[q] = zp[q] - ((o >> q) & 1);
-      if (cc[q] < 0 || cc[q] >= nc) ok = false;
-      const int dq = zq[q] - cc[q];
+      const int cc = zp[q] - ((o >> q) & 1);
+      if (cc < 0 || cc >= nc) ok = false;
+      const int dq = zq[q] - cc;
       if (dq < 0 || dq > 1) ok = false;
       vq |= dq << q;
-      cell += cc[q] * mul;
+      cell += cc * mul;
       mul *= nc;
     }
-    if (!ok) continue;
-    x += cellsum[(long long)cell * G::NVAL + G::PP + pair_index(G::NV, o, vq)];
+    if (ok) x += cellsum[(long long)cell * G::NVAL + G::JP + pair_index(G::NV, o, vq)];
   }
   return x;
 }
 
-template <int D>
-__global__ void __launch_bounds__(Aug<D>::NT) k_augmented(AugArgs A) {
-  using G = Aug<D>;
+// Block 0, after a pass: cell sums, the dense system, the Newton step, convergence.
+template <int D, bool JF32>
+__device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double* R, double* invd, double alpha,
+                            bool first) {
+  using G = Aug<D, JF32>;
+  const int tid = threadIdx.x;
+  const int ncell = (int)ipow(A.nc, D);
+  const int NH = (int)ipow(A.nc - 1, D);
+  const int NA = NH + 1;
+  const int ld = NA + 1;
+  constexpr int N3 = D == 2 ? 9 : 27;
+  double* t_vec = A.sys;
+  double* gh_vec = A.sys + NH;
+  double* s_gam = A.sys + 2 * NH;
+  // cell sums over the blocks of each cell (fixed order)
+  for (int idx = tid; idx < ncell * G::NVAL; idx += blockDim.x) {
+    const int cell = idx / G::NVAL, v = idx % G::NVAL;
+    double x = 0.0;
+    for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + v]);
+    cellsum[idx] = x;
+  }
+  for (int idx = tid; idx < NA * ld; idx += blockDim.x) M[idx] = 0.0;
+  __syncthreads();
+  if (first) {
+    for (int p = tid; p < NH; p += blockDim.x) {
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      t_vec[p] = node_channel<D, JF32>(cellsum, A.nc, z, G::TT);
+      gh_vec[p] = node_channel<D, JF32>(cellsum, A.nc, z, G::GH);
+    }
+    if (tid < 32) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int c = tid; c < ncell; c += 32) {
+        s0 += cellsum[(long long)c * G::NVAL + G::SS];
+        s1 += cellsum[(long long)c * G::NVAL + G::SG];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (tid == 0) {
+        s_gam[0] = s0;
+        s_gam[1] = s1;
+      }
+    }
+    __syncthreads();
+  }
+  const double sig = A.sigma_H;
+  // J_HH on the coarse-edge pattern (entries for every neighbour in the 3^d box)
+  for (int idx = tid; idx < NH * N3; idx += blockDim.x) {
+    const int p = idx / N3;
+    int r = idx % N3;
+    int z[3], zq[3];
+    unknown_coords<D>(p, A.nc, z);
+    bool ok = true;
+    int q = 0, mul = 1, dist = 0;
+    for (int ax = 0; ax < D; ++ax) {
+      const int d = r % 3 - 1;
+      r /= 3;
+      zq[ax] = z[ax] + d;
+      if (zq[ax] < 1 || zq[ax] > A.nc - 1) ok = false;
+      q += (zq[ax] - 1) * mul;
+      mul *= (A.nc - 1);
+      dist += abs(d);
+    }
+    if (!ok) continue;
+    double v = pair_channel<D, JF32>(cellsum, A.nc, z, zq);
+    if (dist == 0) v += sig * 2.0 * D;
+    else if (dist == 1) v -= sig;
+    M[p * ld + q] = v;
+  }
+  // residual and the alpha border
+  for (int p = tid; p < NH; p += blockDim.x) {
+    int z[3];
+    unknown_coords<D>(p, A.nc, z);
+    const long long off = coarse_offset<D>(z, A.nc);
+    double nb = 0.0;
+    long long mul = 1;
+    for (int q = 0; q < D; ++q) {
+      nb += __ldcg(&A.c[off - mul]) + __ldcg(&A.c[off + mul]);
+      mul *= (A.nc + 1);
+    }
+    const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
+    R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA) - gh_vec[p]);
+    const double jb = t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::JB);
+    M[p * ld + NH] = jb;
+    M[NH * ld + p] = jb;
+  }
+  if (tid < 32) {
+    double s2 = 0.0, s3 = 0.0, tc = 0.0;
+    for (int c = tid; c < ncell; c += 32) {
+      s2 += cellsum[(long long)c * G::NVAL + G::SA];
+      s3 += cellsum[(long long)c * G::NVAL + G::JS];
+    }
+    for (int p = tid; p < NH; p += 32) {
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      tc += t_vec[p] * __ldcg(&A.c[coarse_offset<D>(z, A.nc)]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+      tc += __shfl_xor_sync(0xffffffffu, tc, o);
+    }
+    if (tid == 0) {
+      R[NH] = -(tc + alpha * s_gam[0] + s2 - s_gam[1]);
+      M[NH * ld + NH] = s_gam[0] + s3;
+    }
+  }
+  __syncthreads();
+  // Newton step (one warp), update of (c, alpha), convergence test
+  if (tid < 32) {
+    int dropped = 0;
+    const bool ok = warp_chol_solve(M, NA, ld, R, invd, true, 1e-14, &dropped);
+    double dmax = 0.0, ymax = 0.0;
+    bool finite = true;
+    for (int p = tid; p < NH; p += 32) {
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      const long long off = coarse_offset<D>(z, A.nc);
+      const double nv = __ldcg(&A.c[off]) + R[p];
+      if (!isfinite(nv)) finite = false;
+      A.c[off] = nv;
+      dmax = fmax(dmax, fabs(R[p]));
+      ymax = fmax(ymax, fabs(nv));
+    }
+    const double na = alpha + R[NH];
+    if (tid == 0) {
+      if (!isfinite(na)) finite = false;
+      dmax = fmax(dmax, fabs(R[NH]));
+      ymax = fmax(ymax, fabs(na));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    }
+    finite = __all_sync(0xffffffffu, finite);
+    if (tid == 0) {
+      A.st->alpha_cur = na;
+      if (dropped) atomicOr(&A.st->flags, kFlagDropped);
+      if (!ok) atomicOr(&A.st->flags, kFlagNotSPD);
+      if (!finite) atomicOr(&A.st->flags, kFlagNonfinite);
+      if (!ok || !finite) A.st->abort = 1;
+      if (dmax <= A.tol * fmax(1.0, ymax)) A.st->converged = 1;
+      __threadfence();
+    }
+  }
+}
+
+template <int D, bool JF32>
+__global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
+  using G = Aug<D, JF32>;
   extern __shared__ double sm[];
   double* acc = sm;                                 // NVAL * NT
   __shared__ double cv[G::NV];
@@ -502,158 +757,43 @@ __global__ void __launch_bounds__(Aug<D>::NT) k_augmented(AugArgs A) {
       t /= A.nc;
     }
   }
-  // block-0 scratch (after acc): cellsum [ncell * NVAL], M [NA * (NA+1)], R [NA], misc
+  long long vert_off = 0;   // coarse nodal offset of this thread's cell vertex (tid < NV)
+  if (tid < G::NV) {
+    long long mul = 1;
+    for (int q = 0; q < D; ++q) {
+      vert_off += (long long)(cellc[q] + ((tid >> q) & 1)) * mul;
+      mul *= (A.nc + 1);
+    }
+  }
+  // block-0 scratch after acc: cellsum [ncell * NVAL], M [NA * (NA+1)], R [NA], invd [NA]
   double* cellsum = acc + G::NVAL * G::NT;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  double* sh = R + NA;
-  double* t_vec = A.sys;
-  double* gh_vec = A.sys + NH;
-  double* s_gam = A.sys + 2 * NH;
+  double* invd = R + NA;
 
-  // -------- phase 0: t = P^T A_k u~, G_H = P^T (w g), s, gamma
-  for (int v = 0; v < G::NVAL; ++v) acc[v * G::NT + tid] = 0.0;
-  node_pass<D>(A, kPre, acc, nullptr, 0.0, cell, bic);
-  block_reduce_rows<D>(acc, A.partials + (long long)blockIdx.x * G::NVAL);
-  grid_barrier(A.st, nblocks);
   if (blockIdx.x == 0) {
-    gather_cells<D>(A, cellsum);
-    for (int p = tid; p < NH; p += blockDim.x) {
-      int z[3];
-      unknown_coords<D>(p, A.nc, z);
-      t_vec[p] = node_channel<D>(cellsum, A.nc, z, G::VA);
-      gh_vec[p] = node_channel<D>(cellsum, A.nc, z, G::VB);
-    }
+    const long long cn = ipow(A.nc + 1, D);
+    for (long long i = tid; i < cn; i += blockDim.x) A.c[i] = 0.0;
     if (tid == 0) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int c = 0; c < ncell; ++c) {
-        s0 += cellsum[(long long)c * G::NVAL + G::S0];
-        s1 += cellsum[(long long)c * G::NVAL + G::S0 + 1];
-      }
-      s_gam[0] = s0;
-      s_gam[1] = s1;
       A.st->alpha_cur = 1.0;
       A.st->converged = 0;
     }
-    const long long cn = ipow(A.nc + 1, D);
-    for (long long i = tid; i < cn; i += blockDim.x) A.c[i] = 0.0;
   }
-  grid_barrier(A.st, nblocks);
-
-  // -------- Newton iterations
   int it = 0;
   for (it = 1; it <= A.maxit; ++it) {
-    if (tid < G::NV) cv[tid] = __ldcg(&A.c[cell_vertex_node(D, cellc, tid, A.nc)]);
+    const bool first = it == 1;
+    if (tid < G::NV) cv[tid] = first ? 0.0 : __ldcg(&A.c[vert_off]);
     if (tid == 0) {
-      alpha_sh = ((volatile double*)&A.st->alpha_cur)[0];
+      alpha_sh = first ? 1.0 : ((volatile double*)&A.st->alpha_cur)[0];
       stop = ((volatile int*)&A.st->abort)[0];
     }
     for (int v = 0; v < G::NVAL; ++v) acc[v * G::NT + tid] = 0.0;
     __syncthreads();
     if (stop) break;
-    node_pass<D>(A, kNewton, acc, cv, alpha_sh, cell, bic);
-    block_reduce_rows<D>(acc, A.partials + (long long)blockIdx.x * G::NVAL);
+    fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, bic);
+    block_reduce_rows<D, JF32>(acc, A.partials + (long long)blockIdx.x * G::NVAL);
     grid_barrier(A.st, nblocks);
-    if (blockIdx.x == 0) {
-      gather_cells<D>(A, cellsum);
-      const double alpha = alpha_sh;
-      const double sig = A.sigma_H;
-      // residual (negated into R) and Jacobian
-      for (int p = tid; p < NH; p += blockDim.x) {
-        int z[3];
-        unknown_coords<D>(p, A.nc, z);
-        // A_H c at p
-        const long long cp = A.nc + 1;
-        long long off = 0, mul = 1;
-        for (int q = 0; q < D; ++q) {
-          off += (long long)z[q] * mul;
-          mul *= cp;
-        }
-        double nb = 0.0;
-        mul = 1;
-        for (int q = 0; q < D; ++q) {
-          nb += __ldcg(&A.c[off - mul]) + __ldcg(&A.c[off + mul]);
-          mul *= cp;
-        }
-        const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
-        const double rp = ahc + alpha * t_vec[p] + node_channel<D>(cellsum, A.nc, z, G::VA) - gh_vec[p];
-        R[p] = -rp;
-        M[(long long)p * (NA + 1) + NH] = t_vec[p] + node_channel<D>(cellsum, A.nc, z, G::VB);
-        for (int q2 = 0; q2 < NH; ++q2) {
-          int zq[3];
-          unknown_coords<D>(q2, A.nc, zq);
-          int dist = 0;
-          bool near = true;
-          for (int q = 0; q < D; ++q) {
-            const int dd = zq[q] - z[q];
-            dist += abs(dd);
-            if (dd < -1 || dd > 1) near = false;
-          }
-          double v = 0.0;
-          if (near) {
-            v = pair_channel<D>(cellsum, A.nc, z, zq);
-            if (dist == 0) v += sig * 2.0 * D;
-            else if (dist == 1) v -= sig;
-          }
-          M[(long long)p * (NA + 1) + q2] = v;
-        }
-      }
-      if (tid == 0) {
-        double s2 = 0.0, s3 = 0.0, tc = 0.0;
-        for (int c = 0; c < ncell; ++c) {
-          s2 += cellsum[(long long)c * G::NVAL + G::S0];
-          s3 += cellsum[(long long)c * G::NVAL + G::S0 + 1];
-        }
-        for (int p = 0; p < NH; ++p) {
-          int z[3];
-          unknown_coords<D>(p, A.nc, z);
-          const long long cp = A.nc + 1;
-          long long off = 0, mul = 1;
-          for (int q = 0; q < D; ++q) {
-            off += (long long)z[q] * mul;
-            mul *= cp;
-          }
-          tc += t_vec[p] * __ldcg(&A.c[off]);
-        }
-        R[NH] = -(tc + alpha * s_gam[0] + s2 - s_gam[1]);
-        M[(long long)NH * (NA + 1) + NH] = s_gam[0] + s3;
-      }
-      __syncthreads();
-      for (int p = tid; p < NH; p += blockDim.x) M[(long long)NH * (NA + 1) + p] = M[(long long)p * (NA + 1) + NH];
-      __syncthreads();
-      int dropped = 0;
-      const bool ok = block_chol_solve(M, NA, NA + 1, R, sh, true, 1e-14, &dropped);
-      if (tid == 0) {
-        double dmax = 0.0, ymax = 0.0;
-        bool finite = true;
-        const long long cp = A.nc + 1;
-        for (int p = 0; p < NH; ++p) {
-          int z[3];
-          unknown_coords<D>(p, A.nc, z);
-          long long off = 0, mul = 1;
-          for (int q = 0; q < D; ++q) {
-            off += (long long)z[q] * mul;
-            mul *= cp;
-          }
-          const double nv = __ldcg(&A.c[off]) + R[p];
-          if (!isfinite(nv)) finite = false;
-          A.c[off] = nv;
-          dmax = fmax(dmax, fabs(R[p]));
-          ymax = fmax(ymax, fabs(nv));
-        }
-        const double na = alpha + R[NH];
-        if (!isfinite(na)) finite = false;
-        dmax = fmax(dmax, fabs(R[NH]));
-        ymax = fmax(ymax, fabs(na));
-        A.st->alpha_cur = na;
-        if (dropped) atomicOr(&A.st->flags, kFlagDropped);
-        if (!ok) atomicOr(&A.st->flags, kFlagNotSPD);
-        if (!finite) atomicOr(&A.st->flags, kFlagNonfinite);
-        if (!ok || !finite) A.st->abort = 1;
-        if (dmax <= A.tol * fmax(1.0, ymax)) A.st->converged = 1;
-        __threadfence();
-      }
-    }
+    if (blockIdx.x == 0) newton_step<D, JF32>(A, cellsum, M, R, invd, alpha_sh, first);
     grid_barrier(A.st, nblocks);
     if (tid == 0) stop = ((volatile int*)&A.st->converged)[0] | ((volatile int*)&A.st->abort)[0];
     __syncthreads();
@@ -665,19 +805,29 @@ __global__ void __launch_bounds__(Aug<D>::NT) k_augmented(AugArgs A) {
     A.st->newton_iters[A.level_index] += it > A.maxit ? A.maxit : it;
     A.st->alpha[A.level_index] = ((volatile double*)&A.st->alpha_cur)[0];
   }
-  // -------- final update u = alpha u~ + P_{H->k} c
-  if (tid < G::NV) cv[tid] = __ldcg(&A.c[cell_vertex_node(D, cellc, tid, A.nc)]);
+  // final update u = alpha u~ + P_{H->k} c
+  if (tid < G::NV) cv[tid] = __ldcg(&A.c[vert_off]);
   if (tid == 0) alpha_sh = ((volatile double*)&A.st->alpha_cur)[0];
   __syncthreads();
-  node_pass<D>(A, kUpdate, acc, cv, alpha_sh, cell, bic);
+  fine_pass<D, JF32>(A, kUpdate, acc, cv, alpha_sh, cell, bic);
 }
 
-template <int D>
+template <int D, bool JF32>
 size_t aug_smem(int nc) {
-  using G = Aug<D>;
+  using G = Aug<D, JF32>;
   const int ncell = (int)ipow(nc, D);
   const int NA = (int)ipow(nc - 1, D) + 1;
-  return sizeof(double) * ((size_t)G::NVAL * G::NT + (size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 4);
+  return sizeof(double) * ((size_t)G::NVAL * G::NT + (size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + 2 * NA + 8);
+}
+
+template <int D, bool JF32>
+int aug_occupancy(int nc, size_t* smem_out) {
+  const size_t smem = aug_smem<D, JF32>(nc);
+  int occ = 0;
+  cudaFuncSetAttribute(k_augmented<D, JF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_augmented<D, JF32>, Aug<D, JF32>::NT, smem);
+  *smem_out = smem;
+  return occ;
 }
 
 }  // namespace
@@ -687,10 +837,10 @@ size_t aug_smem(int nc) {
 cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s) {
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
-  const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + N + 4);
+  const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 2 * N + 4);
   cudaError_t e = cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_coarse_inverse<<<1, 256, smem, s>>>(dim, g1.n, Ainv, st);
+  k_coarse_inverse<<<1, 64, smem, s>>>(dim, g1.n, Ainv, st);
   return cudaGetLastError();
 }
 
@@ -701,69 +851,63 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
   const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 3 * (size_t)N + 4);
   cudaError_t e = cudaFuncSetAttribute(k_level1_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_level1_newton<<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
+  k_level1_newton<<<1, 128, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
   return cudaGetLastError();
 }
 
-int aug_nvals(int dim) { return dim == 2 ? Aug<2>::NVAL : Aug<3>::NVAL; }
-
-// Blocks per coarse cell for the cooperative launch; at most what fits co-resident.
-static int aug_bpc(int dim, int coarse_cells, int num_sms, size_t* smem_out, int* nt_out) {
-  const int ncell = (int)ipow(coarse_cells, dim);
-  int occ = 0;
-  size_t smem;
-  int nt;
-  if (dim == 2) {
-    smem = aug_smem<2>(coarse_cells);
-    nt = Aug<2>::NT;
-    cudaFuncSetAttribute(k_augmented<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_augmented<2>, nt, smem);
-  } else {
-    smem = aug_smem<3>(coarse_cells);
-    nt = Aug<3>::NT;
-    cudaFuncSetAttribute(k_augmented<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_augmented<3>, nt, smem);
-  }
-  if (smem_out) *smem_out = smem;
-  if (nt_out) *nt_out = nt;
-  const int maxblocks = occ * num_sms;
-  int bpc = maxblocks / ncell;
-  if (bpc < 1) bpc = 0;  // cannot launch: not enough co-resident blocks
-  return bpc;
-}
+int aug_nvals(int dim) { return dim == 2 ? Aug<2, false>::NVAL : Aug<3, false>::NVAL; }
 
 void aug_configure(int dim, int coarse_cells, AugBuffers* ab) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                  cudaSuccess)
     sms = 0;
-  size_t smem = 0;
-  int nt = 0;
-  const int bpc = sms > 0 ? aug_bpc(dim, coarse_cells, sms, &smem, &nt) : 1;
+  const int ncell = (int)ipow(coarse_cells, dim);
+  size_t smem[2] = {0, 0};
+  int occ[2] = {0, 0};
+  if (sms > 0) {
+    if (dim == 2) {
+      occ[0] = aug_occupancy<2, false>(coarse_cells, &smem[0]);
+      occ[1] = aug_occupancy<2, true>(coarse_cells, &smem[1]);
+    } else {
+      occ[0] = aug_occupancy<3, false>(coarse_cells, &smem[0]);
+      occ[1] = aug_occupancy<3, true>(coarse_cells, &smem[1]);
+    }
+  }
+  const int occ_min = occ[0] < occ[1] ? occ[0] : occ[1];
+  int bpc = sms > 0 ? (occ_min * sms) / ncell : 1;
+  if (bpc < 0) bpc = 0;
   ab->bpc = bpc;
-  ab->smem = smem;
-  ab->nt = nt;
-  ab->partial_items = (size_t)ipow(coarse_cells, dim) * (bpc > 0 ? bpc : 1);
+  ab->smem = smem[0] > smem[1] ? smem[0] : smem[1];
+  ab->nt = dim == 2 ? Aug<2, false>::NT : Aug<3, false>::NT;
+  ab->partial_items = (size_t)ncell * (bpc > 0 ? bpc : 1);
 }
 
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
-                             int kind, double a, double tol, int maxit, const AugBuffers& ab, DevState* st,
-                             int level_index, cudaStream_t s) {
+                             int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
+                             DevState* st, int level_index, cudaStream_t s) {
   const size_t smem = ab.smem;
   const int nt = ab.nt;
-  const int bpc = ab.bpc;
-  if (bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
+  if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
   const int ncell = (int)ipow(coarse_cells, dim);
-  if ((size_t)ncell * bpc > ab.partial_items) return cudaErrorInvalidValue;
+  const int sfine = 1 << (level - 1);
+  const int chunk = sfine < 32 ? sfine : 32;
+  // blocks per cell for this level: about one column chunk per thread, at most what is
+  // co-resident
+  const long long items = ipow(sfine, dim - 1) * (sfine / chunk);
+  int bpc = (int)((items + nt - 1) / nt);
+  if (bpc > ab.bpc) bpc = ab.bpc;
+  if (bpc < 1) bpc = 1;
   AugArgs A;
   A.dim = dim;
   A.nc = coarse_cells;
-  A.s = 1 << (level - 1);
+  A.s = sfine;
   A.n = gk.n;
   A.kind = kind;
   A.maxit = maxit;
   A.level_index = level_index;
   A.bpc = bpc;
+  A.chunk = chunk;
   A.a = a;
   const double h = 1.0 / gk.n;
   A.w = dim == 2 ? h * h : h * h * h;
@@ -789,8 +933,12 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (dim == 2) return cudaLaunchKernelEx(&cfg, k_augmented<2>, A);
-  return cudaLaunchKernelEx(&cfg, k_augmented<3>, A);
+  if (dim == 2) {
+    if (jac_f32) return cudaLaunchKernelEx(&cfg, k_augmented<2, true>, A);
+    return cudaLaunchKernelEx(&cfg, k_augmented<2, false>, A);
+  }
+  if (jac_f32) return cudaLaunchKernelEx(&cfg, k_augmented<3, true>, A);
+  return cudaLaunchKernelEx(&cfg, k_augmented<3, false>, A);
 }
 
 }  // namespace fmg

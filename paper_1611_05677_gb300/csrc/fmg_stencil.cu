@@ -224,14 +224,179 @@ __device__ __forceinline__ long long coarse_node(int r, int m, int dim) {
   return ((long long)l * np + j) * np + i;
 }
 
+// u = A_1^{-1} b on the level-1 unknowns.  b is staged in shared memory; A_1^{-1} is
+// symmetric, so thread r reads column r (coalesced across threads).
 template <typename T>
 __global__ void k_coarse_solve(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ u, int m,
                                int N, int dim) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N) return;
-  double acc = 0.0;
-  for (int c = 0; c < N; ++c) acc += Ainv[(long long)r * N + c] * (double)b[coarse_node(c, m, dim)];
-  u[coarse_node(r, m, dim)] = (T)acc;
+  extern __shared__ double bs[];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) bs[c] = (double)b[coarse_node(c, m, dim)];
+  __syncthreads();
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    int c = 0;
+    for (; c + 1 < N; c += 2) {
+      a0 = fma(Ainv[(long long)c * N + r], bs[c], a0);
+      a1 = fma(Ainv[(long long)(c + 1) * N + r], bs[c + 1], a1);
+    }
+    if (c < N) a0 = fma(Ainv[(long long)c * N + r], bs[c], a0);
+    u[coarse_node(r, m, dim)] = (T)(a0 + a1);
+  }
+}
+
+// ------------------------------------------------------------------ coarse V-cycle in one CTA
+// The V(nu_pre, nu_post) cycle on levels jtop..1 with every level's u and b in shared
+// memory: the same red-black sweeps, restriction P^T, exact level-1 solve (dense
+// A_1^{-1} in FP64) and prolongation as the per-level kernels, separated by __syncthreads
+// instead of launches.  Level jtop's u and b are read from and u written back to global
+// memory.  Level j has n0 << (j-1) cells per side.
+template <typename T, int D>
+struct CoarseLevel {
+  int n;        // cells per side
+  int np;       // n + 1
+  T* u;
+  T* b;
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void cta_rbgs(const CoarseLevel<T, D>& L, int colour, T bscale, T inv2d) {
+  const int n = L.n, np = L.np, half = n >> 1;
+  const int rows = n - 1;
+  const int total = D == 2 ? rows * half : rows * rows * half;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int p = t % half;
+    const int rest = t / half;
+    const int j = rest % rows + 1;
+    const int l = D == 3 ? rest / rows + 1 : 0;
+    const int par = (colour + j + l) & 1;
+    const int i = par ? 2 * p + 1 : 2 * p + 2;
+    if (i > n - 1) continue;
+    const int c = (l * np + j) * np + i;
+    T s = (L.u[c - 1] + L.u[c + 1]) + (L.u[c - np] + L.u[c + np]);
+    if (D == 3) s += L.u[c - np * np] + L.u[c + np * np];
+    L.u[c] = (L.b[c] * bscale + s) * inv2d;
+  }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T cta_res(const CoarseLevel<T, D>& L, int c, T sigma) {
+  const int np = L.np;
+  T s = (L.u[c - 1] + L.u[c + 1]) + (L.u[c - np] + L.u[c + np]);
+  if (D == 3) s += L.u[c - np * np] + L.u[c + np * np];
+  return L.b[c] - sigma * (T(2 * D) * L.u[c] - s);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, const T* __restrict__ bg, int n0, int jtop, int nu_pre,
+                                int nu_post, const double* __restrict__ Ainv) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  CoarseLevel<T, D> L[8];
+  {
+    int off = 0;
+    for (int j = 1; j <= jtop; ++j) {
+      const int n = n0 << (j - 1);
+      const int np = n + 1;
+      const int nodes = D == 2 ? np * np : np * np * np;
+      L[j - 1].n = n;
+      L[j - 1].np = np;
+      L[j - 1].u = sm + off;
+      L[j - 1].b = sm + off + nodes;
+      off += 2 * nodes;
+    }
+  }
+  {
+    const CoarseLevel<T, D>& top = L[jtop - 1];
+    const int nodes = D == 2 ? top.np * top.np : top.np * top.np * top.np;
+    for (int i = threadIdx.x; i < nodes; i += blockDim.x) {
+      top.u[i] = ug[i];
+      top.b[i] = bg[i];
+    }
+    // lower levels: zero (boundary rings stay zero)
+    for (int j = 1; j < jtop; ++j) {
+      const int nn = D == 2 ? L[j - 1].np * L[j - 1].np : L[j - 1].np * L[j - 1].np * L[j - 1].np;
+      for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) L[j - 1].u[i] = T(0);
+    }
+  }
+  __syncthreads();
+  const T inv2d = T(1) / T(2 * D);
+  // descend
+  for (int j = jtop; j >= 2; --j) {
+    const CoarseLevel<T, D>& F = L[j - 1];
+    const CoarseLevel<T, D>& C = L[j - 2];
+    const T bscale = D == 2 ? T(1) : T(F.n);
+    const T sigma = D == 2 ? T(1) : T(1) / T(F.n);
+    for (int it = 0; it < nu_pre; ++it) {
+      cta_rbgs<T, D>(F, 0, bscale, inv2d);
+      __syncthreads();
+      cta_rbgs<T, D>(F, 1, bscale, inv2d);
+      __syncthreads();
+    }
+    // b_c = P^T (b - A u), u_c = 0
+    const int m = C.n - 1;
+    const int total = D == 2 ? m * m : m * m * m;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int I = t % m + 1, J = (t / m) % m + 1, K = D == 3 ? t / (m * m) + 1 : 0;
+      const int np = F.np;
+      const int Fc = ((2 * K) * np + 2 * J) * np + 2 * I;
+      T r = cta_res<T, D>(F, Fc, sigma);
+      T e = (cta_res<T, D>(F, Fc + 1, sigma) + cta_res<T, D>(F, Fc - 1, sigma)) +
+            (cta_res<T, D>(F, Fc + np, sigma) + cta_res<T, D>(F, Fc - np, sigma)) +
+            (cta_res<T, D>(F, Fc + np + 1, sigma) + cta_res<T, D>(F, Fc - np - 1, sigma));
+      if (D == 3) {
+        const int pl = np * np;
+        const int o[4] = {pl, 1 + pl, np + pl, 1 + np + pl};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e += cta_res<T, D>(F, Fc + o[q], sigma) + cta_res<T, D>(F, Fc - o[q], sigma);
+      }
+      const int cc = (K * C.np + J) * C.np + I;
+      C.b[cc] = r + T(0.5) * e;
+      C.u[cc] = T(0);
+    }
+    __syncthreads();
+  }
+  // level 1: u_1 = A_1^{-1} b_1 in FP64
+  {
+    const CoarseLevel<T, D>& C = L[0];
+    const int m = C.n - 1;
+    const int N = D == 2 ? m * m : m * m * m;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < N; ++c) {
+        const int i = c % m + 1, j = (c / m) % m + 1, l = D == 3 ? c / (m * m) + 1 : 0;
+        acc = fma(Ainv[(long long)c * N + r], (double)C.b[(l * C.np + j) * C.np + i], acc);
+      }
+      const int i = r % m + 1, j = (r / m) % m + 1, l = D == 3 ? r / (m * m) + 1 : 0;
+      C.u[(l * C.np + j) * C.np + i] = (T)acc;
+    }
+    __syncthreads();
+  }
+  // ascend
+  for (int j = 2; j <= jtop; ++j) {
+    const CoarseLevel<T, D>& F = L[j - 1];
+    const CoarseLevel<T, D>& C = L[j - 2];
+    const T bscale = D == 2 ? T(1) : T(F.n);
+    const int m = F.n - 1;
+    const int total = D == 2 ? m * m : m * m * m;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int i = t % m + 1, jj = (t / m) % m + 1, l = D == 3 ? t / (m * m) + 1 : 0;
+      const int a = ((l >> 1) * C.np + (jj >> 1)) * C.np + (i >> 1);
+      const int z = (((l + 1) >> 1) * C.np + ((jj + 1) >> 1)) * C.np + ((i + 1) >> 1);
+      F.u[(l * F.np + jj) * F.np + i] += T(0.5) * (C.u[a] + C.u[z]);
+    }
+    __syncthreads();
+    for (int it = 0; it < nu_post; ++it) {
+      cta_rbgs<T, D>(F, 1, bscale, inv2d);
+      __syncthreads();
+      cta_rbgs<T, D>(F, 0, bscale, inv2d);
+      __syncthreads();
+    }
+  }
+  {
+    const CoarseLevel<T, D>& top = L[jtop - 1];
+    const int nodes = D == 2 ? top.np * top.np : top.np * top.np * top.np;
+    for (int i = threadIdx.x; i < nodes; i += blockDim.x) ug[i] = top.u[i];
+  }
 }
 
 }  // namespace
@@ -329,7 +494,7 @@ cudaError_t launch_coarse_solve_f64(int dim, LevelGeo g1, const double* Ainv, co
                                     cudaStream_t s) {
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
-  k_coarse_solve<double><<<cdiv(N, 64), 64, 0, s>>>(Ainv, b, u, m, N, dim);
+  k_coarse_solve<double><<<1, 64, N * sizeof(double), s>>>(Ainv, b, u, m, N, dim);
   return cudaGetLastError();
 }
 
@@ -337,10 +502,45 @@ cudaError_t launch_coarse_solve_f32(int dim, LevelGeo g1, const double* Ainv, co
                                     cudaStream_t s) {
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
-  k_coarse_solve<float><<<cdiv(N, 64), 64, 0, s>>>(Ainv, b, u, m, N, dim);
+  k_coarse_solve<float><<<1, 64, N * sizeof(double), s>>>(Ainv, b, u, m, N, dim);
   return cudaGetLastError();
 }
 
+template <typename T>
+size_t coarse_cycle_smem(int dim, int n0, int jtop) {
+  size_t tot = 0;
+  for (int j = 1; j <= jtop; ++j) {
+    const long long np = (long long)(n0 << (j - 1)) + 1;
+    tot += 2 * (size_t)ipow(np, dim);
+  }
+  return tot * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int nu_pre, int nu_post,
+                                const double* Ainv, cudaStream_t s) {
+  const size_t smem = coarse_cycle_smem<T>(dim, n0, jtop);
+  cudaError_t e;
+  if (dim == 2) {
+    if ((e = cudaFuncSetAttribute(k_vcycle_coarse<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    k_vcycle_coarse<T, 2><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv);
+  } else {
+    if ((e = cudaFuncSetAttribute(k_vcycle_coarse<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    k_vcycle_coarse<T, 3><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv);
+  }
+  return cudaGetLastError();
+}
+
+template size_t coarse_cycle_smem<double>(int, int, int);
+template size_t coarse_cycle_smem<float>(int, int, int);
+template cudaError_t launch_coarse_cycle<double>(int, int, int, double*, const double*, int, int, const double*,
+                                                 cudaStream_t);
+template cudaError_t launch_coarse_cycle<float>(int, int, int, float*, const float*, int, int, const double*,
+                                                cudaStream_t);
 template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t);
 template cudaError_t launch_rbgs<float>(int, LevelGeo, float*, const float*, int, cudaStream_t);
 template cudaError_t launch_residual_restrict<double, double>(int, LevelGeo, const double*, const double*, LevelGeo,

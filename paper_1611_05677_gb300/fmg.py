@@ -52,7 +52,11 @@ _lib = None
 EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_rhs", "fmg_solve", "fmg_sync",
            "fmg_solve_batch", "fmg_destroy", "fmg_last_error", "fmg_solution", "fmg_levels", "fmg_level_cells",
            "fmg_op_smooth", "fmg_op_smooth_f32", "fmg_op_residual", "fmg_op_vcycle", "fmg_op_correction_step",
-           "fmg_op_level1_solve", "fmg_op_prolong")
+           "fmg_op_level1_solve", "fmg_op_prolong", "fmg_set_kernel_timing", "fmg_kernel_time",
+           "fmg_graph_kernels")
+KT_AUGMENTED = 0
+KT_SMOOTH_TOP = 1
+KT_CORRECTION = 2
 
 
 def library_path() -> str:
@@ -90,6 +94,9 @@ def load():
         "fmg_op_correction_step": (c_int, [c_void_p, c_int, c_void_p, S]),
         "fmg_op_level1_solve": (c_int, [c_void_p, c_void_p, S]),
         "fmg_op_prolong": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+        "fmg_set_kernel_timing": (c_int, [c_void_p, c_int]),
+        "fmg_kernel_time": (c_int, [c_void_p, c_int, c_int, POINTER(c_double), POINTER(c_int)]),
+        "fmg_graph_kernels": (c_int, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -232,6 +239,22 @@ def fmg_op_level1_solve(ctx, u, stats: fmg_stats | None = None):
 def fmg_op_prolong(ctx, level, u_coarse, u_fine):
     _device_sync()
     _check(load().fmg_op_prolong(ctx, level, _ptr(u_coarse)[0], _ptr(u_fine)[0]), ctx)
+
+
+def fmg_set_kernel_timing(ctx, on: bool):
+    _check(load().fmg_set_kernel_timing(ctx, int(bool(on))), ctx)
+
+
+def fmg_kernel_time(ctx, kind: int, level: int = 0):
+    """(total milliseconds, launches) of one instrumented kernel kind in the last solve."""
+    ms = c_double(0.0)
+    n = c_int(0)
+    _check(load().fmg_kernel_time(ctx, kind, level, byref(ms), byref(n)), ctx)
+    return ms.value, n.value
+
+
+def fmg_graph_kernels(ctx) -> int:
+    return load().fmg_graph_kernels(ctx)
 
 
 # ---------------------------------------------------------------------------- convenience
