@@ -295,7 +295,8 @@ cudaError_t run_fmg(fmg_ctx* c) {
   // per-solve statistics start at zero (flags, iteration counts, alphas)
   if ((e = cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream)) != cudaSuccess) return e;
   if ((e = launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
-                                c->p.level1_maxit, c->st, c->stream)) != cudaSuccess)
+                                c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream)) !=
+      cudaSuccess)
     return e;
   for (int k = 2; k <= c->nlev; ++k) {
     // u^{(0)}_{h_k} = u_{h_{k-1}}: the natural inclusion
@@ -624,7 +625,7 @@ fmg_status fmg_op_level1_solve(fmg_ctx* c, double* u, fmg_stats* st) {
   if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
   CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
   CK(c, launch_level1_newton(c->p.dim, c->geo[0], c->g[0], u, c->p.f, c->p.f_scale, c->p.level1_tol,
-                             c->p.level1_maxit, c->st, c->stream));
+                             c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream));
   return read_state(c, st, false);
 }
 

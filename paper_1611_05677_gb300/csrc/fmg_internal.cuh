@@ -158,7 +158,7 @@ cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* 
 
 // level-1 exact semilinear solve (Algorithm 3.2 step 1): Newton, dense, one CTA
 cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double* u, int kind, double a,
-                                 double tol, int maxit, DevState* st, cudaStream_t s);
+                                 double tol, int maxit, bool f32_factor, DevState* st, cudaStream_t s);
 
 // Augmented problem on V_H + span{u~} (Algorithm 3.1 step 2, eq. 3.6): one cooperative
 // persistent kernel: precompute, Newton iterations, final update u = alpha u~ + P_{H->k} c.

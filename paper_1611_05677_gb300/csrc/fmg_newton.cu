@@ -50,67 +50,77 @@ __device__ __forceinline__ double rsqrt_refined(double d) {
   return y;
 }
 
-// Cholesky (lower) of the n x n SPD matrix M (row-major, leading dimension ld, shared
-// memory) and solve M x = rhs (rhs overwritten), by ONE warp; the other warps of the block
-// must not touch M/rhs meanwhile.  invd (n doubles, shared) receives 1/L_kk.
-// If drop_last and the last pivot falls below drop_tol times the original last diagonal
-// entry, the last unknown is frozen (increment 0) and *dropped = 1.  Returns false if not SPD.
-__device__ bool warp_chol_solve(double* M, int n, int ld, double* rhs, double* invd, bool drop_last,
-                                double drop_tol, int* dropped) {
-  const int lane = threadIdx.x & 31;
-  bool bad = false;
-  int drop = 0;
-  const double last0 = drop_last ? M[(n - 1) * ld + (n - 1)] : 0.0;
+__device__ __forceinline__ float rsqrt_refined(float d) {
+  float y = rsqrtf(d);
+  return y * (1.5f - 0.5f * d * y * y);
+}
+
+// Cholesky (lower, in place) of the n x n SPD matrix L (row-major, leading dimension ld,
+// shared memory, precision T) by the whole block, then the solve L L^T x = rhs (rhs is
+// FP64 in and out; the substitution runs in T).  work and invd: n values of T in shared
+// memory.  If drop_last and the last pivot falls below drop_tol times the original last
+// diagonal entry, the last unknown is frozen (increment 0) and *dropped = 1.  Returns false
+// if the matrix is not SPD.  Every thread of the block must call it.
+template <typename T>
+__device__ bool block_chol_solve(T* L, int n, int ld, double* rhs, T* work, T* invd, bool drop_last,
+                                 double drop_tol, int* dropped) {
+  __shared__ int bad_sh, drop_sh;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const T last0 = drop_last ? L[(n - 1) * ld + (n - 1)] : T(0);
+  if (tid == 0) {
+    bad_sh = 0;
+    drop_sh = 0;
+  }
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
-    double d = M[k * ld + k];
-    __syncwarp();
-    if (drop_last && k == n - 1 && !(d > drop_tol * last0)) {
-      drop = 1;
-      d = 1.0;
-      for (int j = lane; j < k; j += 32) M[k * ld + j] = 0.0;
-      if (lane == 0) rhs[k] = 0.0;
-    } else if (!(d > 0.0)) {
-      bad = true;
-      d = 1.0;
-    }
-    const double inv = rsqrt_refined(d);
-    if (lane == 0) {
-      M[k * ld + k] = d * inv;
+    if (tid == 0) {
+      T d = L[k * ld + k];
+      if (drop_last && k == n - 1 && !(d > T(drop_tol) * last0)) {
+        drop_sh = 1;
+        d = T(1);
+      } else if (!(d > T(0))) {
+        bad_sh = 1;
+        d = T(1);
+      }
+      const T inv = rsqrt_refined(d);
+      L[k * ld + k] = d * inv;
       invd[k] = inv;
     }
-    for (int i = k + 1 + lane; i < n; i += 32) M[i * ld + k] *= inv;
-    __syncwarp();
-    // trailing update of rows i > k, columns k < j <= i: the triangle flattened over lanes
-    const int m = n - k - 1;
-    const int T = m * (m + 1) / 2;
-    for (int idx = lane; idx < T; idx += 32) {
-      int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
-      if ((r + 1) * (r + 2) / 2 <= idx) ++r;
-      if (r * (r + 1) / 2 > idx) --r;
-      const int i = k + 1 + r;
-      const int j = k + 1 + (idx - r * (r + 1) / 2);
-      M[i * ld + j] -= M[i * ld + k] * M[j * ld + k];
+    __syncthreads();
+    if (drop_sh && k == n - 1)
+      for (int j = tid; j < k; j += nt) L[k * ld + j] = T(0);
+    const T inv = invd[k];
+    for (int i = k + 1 + tid; i < n; i += nt) L[i * ld + k] *= inv;
+    __syncthreads();
+    const int W = n - k - 1;
+    for (int t = tid; t < W * W; t += nt) {
+      const int i = k + 1 + t / W;
+      const int j = k + 1 + t % W;
+      if (j <= i) L[i * ld + j] -= L[i * ld + k] * L[j * ld + k];
     }
-    __syncwarp();
+    __syncthreads();
   }
-  // forward L y = rhs
-  for (int k = 0; k < n; ++k) {
-    const double yk = rhs[k] * invd[k];
-    __syncwarp();
-    if (lane == 0) rhs[k] = yk;
-    for (int i = k + 1 + lane; i < n; i += 32) rhs[i] -= M[i * ld + k] * yk;
-    __syncwarp();
+  for (int i = tid; i < n; i += nt) work[i] = (drop_sh && i == n - 1) ? T(0) : (T)rhs[i];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {  // L y = rhs
+    if (tid == 0) work[k] *= invd[k];
+    __syncthreads();
+    const T yk = work[k];
+    for (int i = k + 1 + tid; i < n; i += nt) work[i] -= L[i * ld + k] * yk;
+    __syncthreads();
   }
-  // backward L^T x = y
-  for (int k = n - 1; k >= 0; --k) {
-    const double xk = rhs[k] * invd[k];
-    __syncwarp();
-    if (lane == 0) rhs[k] = xk;
-    for (int i = lane; i < k; i += 32) rhs[i] -= M[k * ld + i] * xk;
-    __syncwarp();
+  for (int k = n - 1; k >= 0; --k) {  // L^T x = y
+    if (tid == 0) work[k] *= invd[k];
+    __syncthreads();
+    const T xk = work[k];
+    for (int i = tid; i < k; i += nt) work[i] -= L[k * ld + i] * xk;
+    __syncthreads();
   }
-  if (dropped) *dropped = drop;
-  return !bad;
+  for (int i = tid; i < n; i += nt) rhs[i] = (double)work[i];
+  if (dropped) *dropped = drop_sh;
+  const bool ok = bad_sh == 0;
+  __syncthreads();
+  return ok;
 }
 
 // Level-1 unknown r <-> nodal offset of interior node (r % m + 1, (r/m) % m + 1, r/m^2 + 1).
@@ -157,8 +167,9 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
   fill_stiffness(M, N, ld, m, dim, sigma);
   for (int i = threadIdx.x; i < N; i += blockDim.x) rhs[i] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const bool ok = warp_chol_solve(M, N, ld, rhs, invd, false, 0.0, nullptr);
+  {
+    double* work = invd + N;
+    const bool ok = block_chol_solve<double>(M, N, ld, rhs, work, invd, false, 0.0, nullptr);
     if (!ok && threadIdx.x == 0) atomicOr(&st->flags, kFlagNotSPD);
   }
   __syncthreads();
@@ -178,17 +189,23 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
   }
 }
 
-// Algorithm 3.2 step 1: Newton on A_1 U + w f(U) = w g, from U = 0 (one CTA).
+// Algorithm 3.2 step 1: Newton on A_1 U + w f(U) = w g, from U = 0 (one CTA).  The residual,
+// the iterate and the convergence test are FP64; the Jacobian A_1 + diag(w f'(U)) is factored
+// in precision T (T = float in the mixed path: an inexact Newton step whose error the next
+// FP64 residual corrects, so the iteration converges to the same FP64 solution).
+template <typename T>
 __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
                                 double a, double tol, int maxit, DevState* st) {
   extern __shared__ double sm[];
   const int m = n1 - 1;
   const int N = dim == 2 ? m * m : m * m * m;
   const int ld = N + 1;
-  double* M = sm;
-  double* rhs = M + (size_t)N * ld;
-  double* U = rhs + N;
-  double* invd = U + N;
+  double* U = sm;
+  double* rhs = U + N;
+  double* Fp = rhs + N;
+  T* L = reinterpret_cast<T*>(Fp + N);
+  T* work = L + (size_t)N * ld;
+  T* invd = work + N;
   __shared__ int done;
   const double h = 1.0 / n1;
   const double sigma = dim == 2 ? 1.0 : h;
@@ -198,8 +215,6 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
   __syncthreads();
   int it = 0;
   for (it = 1; it <= maxit; ++it) {
-    fill_stiffness(M, N, ld, m, dim, sigma);
-    __syncthreads();
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       double F, D;
       f_eval<double>(kind, a, U[p], F, D);
@@ -215,11 +230,28 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
       }
       const double au = sigma * (2.0 * dim * U[p] - nb);
       rhs[p] = -(au + w * F - w * g[node_of(p, m, dim)]);
-      M[p * ld + p] += w * D;
+      Fp[p] = w * D;
     }
     __syncthreads();
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int p = idx / N, q = idx % N;
+      double v = 0.0;
+      if (p == q) {
+        v = sigma * 2 * dim + Fp[p];
+      } else {
+        int dist = 0, pp = p, qq = q;
+        for (int ax = 0; ax < dim; ++ax) {
+          dist += abs(pp % m - qq % m);
+          pp /= m;
+          qq /= m;
+        }
+        if (dist == 1) v = -sigma;
+      }
+      L[p * ld + q] = (T)v;
+    }
+    __syncthreads();
+    const bool ok = block_chol_solve<T>(L, N, ld, rhs, work, invd, false, 0.0, nullptr);
     if (threadIdx.x < 32) {
-      const bool ok = warp_chol_solve(M, N, ld, rhs, invd, false, 0.0, nullptr);
       double dmax = 0.0, umax = 0.0;
       bool finite = true;
       for (int p = threadIdx.x; p < N; p += 32) {
@@ -584,8 +616,9 @@ __device__ double pair_channel(const double* cellsum, int nc, const int* zp, con
 
 // Block 0, after a pass: cell sums, the dense system, the Newton step, convergence.
 template <int D, bool JF32>
-__device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double* R, double* invd, double alpha,
-                            bool first) {
+__device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double* R,
+                            typename std::conditional<JF32, float, double>::type* L, double alpha, bool first) {
+  using FT = typename std::conditional<JF32, float, double>::type;
   using G = Aug<D, JF32>;
   const int tid = threadIdx.x;
   const int ncell = (int)ipow(A.nc, D);
@@ -694,10 +727,15 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     }
   }
   __syncthreads();
-  // Newton step (one warp), update of (c, alpha), convergence test
+  // Newton step: factor (FP64, or FP32 in the mixed path) and solve by the whole block
+  for (int idx = tid; idx < NA * ld; idx += blockDim.x) L[idx] = (FT)M[idx];
+  __syncthreads();
+  FT* work = L + (size_t)NA * ld;
+  FT* invd = work + NA;
+  int dropped = 0;
+  const bool ok = block_chol_solve<FT>(L, NA, ld, R, work, invd, true, 1e-14, &dropped);
+  // update of (c, alpha), convergence test (one warp)
   if (tid < 32) {
-    int dropped = 0;
-    const bool ok = warp_chol_solve(M, NA, ld, R, invd, true, 1e-14, &dropped);
     double dmax = 0.0, ymax = 0.0;
     bool finite = true;
     for (int p = tid; p < NH; p += 32) {
@@ -765,11 +803,14 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
       mul *= (A.nc + 1);
     }
   }
-  // block-0 scratch after acc: cellsum [ncell * NVAL], M [NA * (NA+1)], R [NA], invd [NA]
-  double* cellsum = acc + G::NVAL * G::NT;
+  // block-0 scratch, reusing the channel rows once they are reduced: cellsum [ncell * NVAL],
+  // M [NA * (NA+1)], R [NA], then the factor L [NA * (NA+1)] and work/invd [2 NA] in the
+  // factor's precision
+  using FT = typename std::conditional<JF32, float, double>::type;
+  double* cellsum = acc;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  double* invd = R + NA;
+  FT* L = reinterpret_cast<FT*>(R + NA + 1);
 
   if (blockIdx.x == 0) {
     const long long cn = ipow(A.nc + 1, D);
@@ -793,7 +834,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
     fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, bic);
     block_reduce_rows<D, JF32>(acc, A.partials + (long long)blockIdx.x * G::NVAL);
     grid_barrier(A.st, nblocks);
-    if (blockIdx.x == 0) newton_step<D, JF32>(A, cellsum, M, R, invd, alpha_sh, first);
+    if (blockIdx.x == 0) newton_step<D, JF32>(A, cellsum, M, R, L, alpha_sh, first);
     grid_barrier(A.st, nblocks);
     if (tid == 0) stop = ((volatile int*)&A.st->converged)[0] | ((volatile int*)&A.st->abort)[0];
     __syncthreads();
@@ -817,7 +858,9 @@ size_t aug_smem(int nc) {
   using G = Aug<D, JF32>;
   const int ncell = (int)ipow(nc, D);
   const int NA = (int)ipow(nc - 1, D) + 1;
-  return sizeof(double) * ((size_t)G::NVAL * G::NT + (size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + 2 * NA + 8);
+  const size_t rows = (size_t)G::NVAL * G::NT;
+  const size_t scratch = (size_t)ncell * G::NVAL + 2 * ((size_t)NA * (NA + 1)) + 3 * NA + 4;
+  return sizeof(double) * (rows > scratch ? rows : scratch);
 }
 
 template <int D, bool JF32>
@@ -837,7 +880,7 @@ int aug_occupancy(int nc, size_t* smem_out) {
 cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s) {
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
-  const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 2 * N + 4);
+  const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 3 * N + 4);
   cudaError_t e = cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_coarse_inverse<<<1, 64, smem, s>>>(dim, g1.n, Ainv, st);
@@ -845,13 +888,23 @@ cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* 
 }
 
 cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double* u, int kind, double a, double tol,
-                                 int maxit, DevState* st, cudaStream_t s) {
+                                 int maxit, bool f32_factor, DevState* st, cudaStream_t s) {
   const int m = g1.n - 1;
-  const int N = (int)ipow(m, dim);
-  const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 3 * (size_t)N + 4);
-  cudaError_t e = cudaFuncSetAttribute(k_level1_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_level1_newton<<<1, 128, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
+  const size_t N = (size_t)ipow(m, dim);
+  cudaError_t e;
+  if (f32_factor) {
+    const size_t smem = sizeof(double) * (3 * N + 2) + sizeof(float) * (N * (N + 1) + 2 * N + 4);
+    if ((e = cudaFuncSetAttribute(k_level1_newton<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return e;
+    k_level1_newton<float><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
+  } else {
+    const size_t smem = sizeof(double) * (3 * N + 2 + N * (N + 1) + 2 * N + 4);
+    if ((e = cudaFuncSetAttribute(k_level1_newton<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return e;
+    k_level1_newton<double><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
+  }
   return cudaGetLastError();
 }
 
