@@ -55,69 +55,148 @@ __device__ __forceinline__ float rsqrt_refined(float d) {
   return y * (1.5f - 0.5f * d * y * y);
 }
 
-// Cholesky (lower, in place) of the n x n SPD matrix L (row-major, leading dimension ld,
-// shared memory, precision T) by the whole block, then the solve L L^T x = rhs (rhs is
-// FP64 in and out; the substitution runs in T).  work and invd: n values of T in shared
-// memory.  If drop_last and the last pivot falls below drop_tol times the original last
-// diagonal entry, the last unknown is frozen (increment 0) and *dropped = 1.  Returns false
-// if the matrix is not SPD.  Every thread of the block must call it.
+// Blocked Cholesky (lower, in place) of the n x n SPD matrix L (row-major, leading dimension
+// ld, shared memory, precision T), then the solve L L^T x = rhs (rhs FP64 in and out; the
+// substitutions run in T).  work and invd: n values of T in shared memory.  Block size 8:
+// each 8 x 8 diagonal block is factored by one warp in registers (row per lane, shuffles),
+// the panel below it and the trailing update run on the whole thread block, so there are
+// about n/8 barrier-separated steps instead of n.  If drop_last and the last pivot falls
+// below drop_tol times the original last diagonal entry, the last unknown is frozen
+// (increment 0) and *dropped = 1.  Returns false if the matrix is not SPD.  Every thread of
+// the block must call it.
+constexpr int kCB = 8;
+
 template <typename T>
 __device__ bool block_chol_solve(T* L, int n, int ld, double* rhs, T* work, T* invd, bool drop_last,
                                  double drop_tol, int* dropped) {
   __shared__ int bad_sh, drop_sh;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const T last0 = drop_last ? L[(n - 1) * ld + (n - 1)] : T(0);
   if (tid == 0) {
     bad_sh = 0;
     drop_sh = 0;
   }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (tid == 0) {
-      T d = L[k * ld + k];
-      if (drop_last && k == n - 1 && !(d > T(drop_tol) * last0)) {
-        drop_sh = 1;
-        d = T(1);
-      } else if (!(d > T(0))) {
-        bad_sh = 1;
-        d = T(1);
+  for (int kb = 0; kb < n; kb += kCB) {
+    const int nb = min(kCB, n - kb);
+    // (1) diagonal block, warp 0: lane r holds row kb+r
+    if (warp == 0) {
+      T a[kCB];
+      const int r = lane;
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) a[c] = (r < nb && c <= r) ? L[(kb + r) * ld + kb + c] : T(0);
+      bool bad = false, drop = false;
+#pragma unroll
+      for (int j = 0; j < kCB; ++j) {
+        if (j < nb) {
+          T d = __shfl_sync(0xffffffffu, a[j], j);
+          if (drop_last && kb + j == n - 1 && !(d > T(drop_tol) * last0)) {
+            drop = true;
+            d = T(1);
+          } else if (!(d > T(0))) {
+            bad = true;
+            d = T(1);
+          }
+          const T inv = rsqrt_refined(d);
+          if (r == j) a[j] = d * inv;
+          else if (r > j) a[j] *= inv;
+          if (lane == 0) invd[kb + j] = inv;
+#pragma unroll
+          for (int c = j + 1; c < kCB; ++c) {
+            const T lcj = __shfl_sync(0xffffffffu, a[j], c);
+            if (c < nb && r >= c && r < nb) a[c] -= a[j] * lcj;
+          }
+        }
       }
-      const T inv = rsqrt_refined(d);
-      L[k * ld + k] = d * inv;
-      invd[k] = inv;
+      if (r < nb)
+#pragma unroll
+        for (int c = 0; c < kCB; ++c)
+          if (c <= r) L[(kb + r) * ld + kb + c] = a[c];
+      if (lane == 0) {
+        if (bad) bad_sh = 1;
+        if (drop) drop_sh = 1;
+      }
     }
     __syncthreads();
-    if (drop_sh && k == n - 1)
-      for (int j = tid; j < k; j += nt) L[k * ld + j] = T(0);
-    const T inv = invd[k];
-    for (int i = k + 1 + tid; i < n; i += nt) L[i * ld + k] *= inv;
+    // (2) panel rows below the block: x Lkk^T = L[i, kb:kb+nb]
+    for (int i = kb + nb + tid; i < n; i += nt) {
+      T x[kCB];
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) x[c] = c < nb ? L[i * ld + kb + c] : T(0);
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) {
+        if (c < nb) {
+          T s = x[c];
+#pragma unroll
+          for (int q = 0; q < c; ++q) s -= x[q] * L[(kb + c) * ld + kb + q];
+          x[c] = s * invd[kb + c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kCB; ++c)
+        if (c < nb) L[i * ld + kb + c] = x[c];
+    }
     __syncthreads();
-    const int W = n - k - 1;
+    // (3) trailing update of the lower triangle below/right of the block
+    const int W = n - kb - nb;
     for (int t = tid; t < W * W; t += nt) {
-      const int i = k + 1 + t / W;
-      const int j = k + 1 + t % W;
-      if (j <= i) L[i * ld + j] -= L[i * ld + k] * L[j * ld + k];
+      const int i = kb + nb + t / W;
+      const int j = kb + nb + t % W;
+      if (j > i) continue;
+      T s = L[i * ld + j];
+#pragma unroll
+      for (int c = 0; c < kCB; ++c)
+        if (c < nb) s -= L[i * ld + kb + c] * L[j * ld + kb + c];
+      L[i * ld + j] = s;
     }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += nt) work[i] = (drop_sh && i == n - 1) ? T(0) : (T)rhs[i];
+  const bool drop = drop_sh != 0;
+  if (drop)
+    for (int j = tid; j < n - 1; j += nt) L[(n - 1) * ld + j] = T(0);
+  for (int i = tid; i < n; i += nt) work[i] = (drop && i == n - 1) ? T(0) : (T)rhs[i];
   __syncthreads();
-  for (int k = 0; k < n; ++k) {  // L y = rhs
-    if (tid == 0) work[k] *= invd[k];
+  // forward L y = rhs, by blocks
+  for (int kb = 0; kb < n; kb += kCB) {
+    const int nb = min(kCB, n - kb);
+    if (tid == 0) {
+      for (int c = 0; c < nb; ++c) {
+        const T y = work[kb + c] * invd[kb + c];
+        work[kb + c] = y;
+        for (int q = c + 1; q < nb; ++q) work[kb + q] -= L[(kb + q) * ld + kb + c] * y;
+      }
+    }
     __syncthreads();
-    const T yk = work[k];
-    for (int i = k + 1 + tid; i < n; i += nt) work[i] -= L[i * ld + k] * yk;
+    for (int i = kb + nb + tid; i < n; i += nt) {
+      T s = work[i];
+      for (int c = 0; c < nb; ++c) s -= L[i * ld + kb + c] * work[kb + c];
+      work[i] = s;
+    }
     __syncthreads();
   }
-  for (int k = n - 1; k >= 0; --k) {  // L^T x = y
-    if (tid == 0) work[k] *= invd[k];
+  // backward L^T x = y, by blocks
+  for (int kb = ((n - 1) / kCB) * kCB; kb >= 0; kb -= kCB) {
+    const int nb = min(kCB, n - kb);
+    if (tid == 0) {
+      for (int c = nb - 1; c >= 0; --c) {
+        const T x = work[kb + c] * invd[kb + c];
+        work[kb + c] = x;
+        for (int q = 0; q < c; ++q) work[kb + q] -= L[(kb + c) * ld + kb + q] * x;
+      }
+    }
     __syncthreads();
-    const T xk = work[k];
-    for (int i = tid; i < k; i += nt) work[i] -= L[k * ld + i] * xk;
+    for (int i = tid; i < kb; i += nt) {
+      T s = work[i];
+      for (int c = 0; c < nb; ++c) s -= L[(kb + c) * ld + i] * work[kb + c];
+      work[i] = s;
+    }
     __syncthreads();
   }
+  if (drop && tid == 0) work[n - 1] = T(0);
+  __syncthreads();
   for (int i = tid; i < n; i += nt) rhs[i] = (double)work[i];
-  if (dropped) *dropped = drop_sh;
+  if (dropped) *dropped = drop ? 1 : 0;
   const bool ok = bad_sh == 0;
   __syncthreads();
   return ok;

@@ -19,6 +19,7 @@ namespace fmg {
 namespace {
 
 constexpr int kBlock = 128;
+constexpr int kMaxCoarseN = 64;   // level-1 unknowns (2D: (1/H - 1)^2 <= 49, 3D: <= 27)
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
@@ -252,22 +253,24 @@ __global__ void k_coarse_solve(const double* __restrict__ Ainv, const T* __restr
 // memory.  Level j has n0 << (j-1) cells per side.
 template <typename T, int D>
 struct CoarseLevel {
-  int n;        // cells per side
+  int n;        // cells per side (a power of two)
+  int lg;       // log2(n)
   int np;       // n + 1
   T* u;
   T* b;
 };
 
+// One colour of a red-black sweep: items are (p, j[, l]) with i = 2p + 1 or 2p + 2, decoded
+// with shifts; rows 0 and n and out-of-range i are skipped.
 template <typename T, int D>
 __device__ __forceinline__ void cta_rbgs(const CoarseLevel<T, D>& L, int colour, T bscale, T inv2d) {
-  const int n = L.n, np = L.np, half = n >> 1;
-  const int rows = n - 1;
-  const int total = D == 2 ? rows * half : rows * rows * half;
+  const int n = L.n, np = L.np, lgh = L.lg - 1;
+  const int total = D == 2 ? (n << lgh) : (n << (lgh + L.lg));
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int p = t % half;
-    const int rest = t / half;
-    const int j = rest % rows + 1;
-    const int l = D == 3 ? rest / rows + 1 : 0;
+    const int p = t & ((1 << lgh) - 1);
+    const int j = (t >> lgh) & (n - 1);
+    const int l = D == 3 ? (t >> (lgh + L.lg)) : 0;
+    if (j == 0 || (D == 3 && l == 0)) continue;
     const int par = (colour + j + l) & 1;
     const int i = par ? 2 * p + 1 : 2 * p + 2;
     if (i > n - 1) continue;
@@ -299,6 +302,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       const int np = n + 1;
       const int nodes = D == 2 ? np * np : np * np * np;
       L[j - 1].n = n;
+      L[j - 1].lg = 31 - __clz(n);
       L[j - 1].np = np;
       L[j - 1].u = sm + off;
       L[j - 1].b = sm + off + nodes;
@@ -332,11 +336,12 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       cta_rbgs<T, D>(F, 1, bscale, inv2d);
       __syncthreads();
     }
-    // b_c = P^T (b - A u), u_c = 0
-    const int m = C.n - 1;
-    const int total = D == 2 ? m * m : m * m * m;
+    // b_c = P^T (b - A u), u_c = 0: items (I, J[, K]) over [0, n_c)^d, boundary skipped
+    const int lgc = C.lg;
+    const int total = D == 2 ? (1 << (2 * lgc)) : (1 << (3 * lgc));
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int I = t % m + 1, J = (t / m) % m + 1, K = D == 3 ? t / (m * m) + 1 : 0;
+      const int I = t & (C.n - 1), J = (t >> lgc) & (C.n - 1), K = D == 3 ? (t >> (2 * lgc)) : 0;
+      if (I == 0 || J == 0 || (D == 3 && K == 0)) continue;
       const int np = F.np;
       const int Fc = ((2 * K) * np + 2 * J) * np + 2 * I;
       T r = cta_res<T, D>(F, Fc, sigma);
@@ -355,19 +360,28 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
     }
     __syncthreads();
   }
-  // level 1: u_1 = A_1^{-1} b_1 in FP64
+  // level 1: u_1 = A_1^{-1} b_1 in FP64; b_1 staged as FP64 in the (now unused) level-1 u
+  // slots is not possible for FP32 levels, so it goes to a small shared array
   {
+    __shared__ double b1[kMaxCoarseN];
+    __shared__ int off1[kMaxCoarseN];
     const CoarseLevel<T, D>& C = L[0];
     const int m = C.n - 1;
     const int N = D == 2 ? m * m : m * m * m;
-    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      const int i = c % m + 1, j = (c / m) % m + 1, l = D == 3 ? c / (m * m) + 1 : 0;
+      off1[c] = (l * C.np + j) * C.np + i;
+      b1[c] = (double)C.b[off1[c]];
+    }
+    __syncthreads();
+    // row r: lanes of one warp split the columns, then a shuffle sum (fixed order)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < N; r += nw) {
       double acc = 0.0;
-      for (int c = 0; c < N; ++c) {
-        const int i = c % m + 1, j = (c / m) % m + 1, l = D == 3 ? c / (m * m) + 1 : 0;
-        acc = fma(Ainv[(long long)c * N + r], (double)C.b[(l * C.np + j) * C.np + i], acc);
-      }
-      const int i = r % m + 1, j = (r / m) % m + 1, l = D == 3 ? r / (m * m) + 1 : 0;
-      C.u[(l * C.np + j) * C.np + i] = (T)acc;
+      for (int c = lane; c < N; c += 32) acc = fma(Ainv[(long long)c * N + r], b1[c], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) C.u[off1[r]] = (T)acc;
     }
     __syncthreads();
   }
@@ -376,10 +390,11 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
     const CoarseLevel<T, D>& F = L[j - 1];
     const CoarseLevel<T, D>& C = L[j - 2];
     const T bscale = D == 2 ? T(1) : T(F.n);
-    const int m = F.n - 1;
-    const int total = D == 2 ? m * m : m * m * m;
+    const int lgf = F.lg;
+    const int total = D == 2 ? (1 << (2 * lgf)) : (1 << (3 * lgf));
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int i = t % m + 1, jj = (t / m) % m + 1, l = D == 3 ? t / (m * m) + 1 : 0;
+      const int i = t & (F.n - 1), jj = (t >> lgf) & (F.n - 1), l = D == 3 ? (t >> (2 * lgf)) : 0;
+      if (i == 0 || jj == 0 || (D == 3 && l == 0)) continue;
       const int a = ((l >> 1) * C.np + (jj >> 1)) * C.np + (i >> 1);
       const int z = (((l + 1) >> 1) * C.np + ((jj + 1) >> 1)) * C.np + ((i + 1) >> 1);
       F.u[(l * F.np + jj) * F.np + i] += T(0.5) * (C.u[a] + C.u[z]);
