@@ -217,6 +217,39 @@ fmg_status fmg_kernel_time(fmg_ctx* c, int kind, int level, double* total_ms, in
 /* Kernel nodes in the captured solve graph (0 before the first solve, -1 for NULL). */
 int fmg_graph_kernels(const fmg_ctx* c);
 
+/* ---------------------------------------------------------------------------------------
+ * V-cycles that allocate no device memory.
+ *
+ * The paper has no counterpart to this entry point; it is a service of this library.  It is
+ * for callers that cannot call cudaMalloc: code embedded in a host application whose own
+ * memory pool owns the device memory and forbids raw allocations, latency-critical loops
+ * where cudaMalloc/cudaFree would synchronize the device and stall other streams, and
+ * programs that must know at load time that no allocation can fail later.  fmg_create needs
+ * a workspace (its own or the caller's); this call needs none.
+ *
+ * It runs `cycles` FP64 V(nu_pre, nu_post) cycles on A_k u = b at level `level` (1-based; the
+ * mesh of level k has coarse_cells * 2^(k-1) cells per side) -- the same cycle as
+ * fmg_op_vcycle on an FMG_PREC_FP64 context.  b and u are the caller's DEVICE arrays in the
+ * level-k nodal layout ((n+1)^d doubles, boundary entries zero); u holds the initial guess
+ * and receives the result.  All coarser levels and the dense level-1 inverse live in one
+ * file-scope device array of FMG_VCYCLE_NOALLOC_MAX_BYTES bytes, which every GPU that loads
+ * the library holds until the process exits.  A size whose coarser levels do not fit (2D
+ * levels up to 1024 cells per side fit, 3D up to 128) is rejected with FMG_ERR_INVALID; the
+ * message is in fmg_last_error(NULL).
+ *
+ * The first call on a device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture on the device.  The
+ * first call for a (dim, coarse_cells) pair also computes A_1^{-1} into the array.  Every
+ * call shares the array, which keeps the last call's contents; the call clears the parts that
+ * must start at zero itself.  Calls that overlap on the GPU (on different streams, or from
+ * different threads on one device) race on the array and give wrong results.  The call only
+ * queues work on `stream` (cudaStream_t, NULL = legacy default stream) and returns; u is
+ * final when the stream reaches that point.
+ */
+#define FMG_VCYCLE_NOALLOC_MAX_BYTES ((size_t)8 << 20)
+fmg_status fmg_vcycle_noalloc(int dim, int coarse_cells, int level, const double* b, double* u, int cycles,
+                              int nu_pre, int nu_post, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

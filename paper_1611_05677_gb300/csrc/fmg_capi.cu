@@ -351,6 +351,8 @@ fmg_status check_level(fmg_ctx* c, int level, int lo) {
 
 }  // namespace
 
+void fmg::set_thread_error(const std::string& msg) { t_err = msg; }
+
 // ============================================================================ C ABI
 
 extern "C" {

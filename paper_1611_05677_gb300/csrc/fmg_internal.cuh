@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/fmg.h"
 
 namespace fmg {
@@ -178,5 +180,8 @@ int aug_nvals(int dim);
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
                              DevState* st, int level_index, cudaStream_t s);
+
+// Sets the calling thread's error message (what fmg_last_error(NULL) returns).
+void set_thread_error(const std::string& msg);
 
 }  // namespace fmg

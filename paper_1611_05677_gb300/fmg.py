@@ -53,7 +53,7 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
            "fmg_solve_batch", "fmg_destroy", "fmg_last_error", "fmg_solution", "fmg_levels", "fmg_level_cells",
            "fmg_op_smooth", "fmg_op_smooth_f32", "fmg_op_residual", "fmg_op_vcycle", "fmg_op_correction_step",
            "fmg_op_level1_solve", "fmg_op_prolong", "fmg_set_kernel_timing", "fmg_kernel_time",
-           "fmg_graph_kernels")
+           "fmg_graph_kernels", "fmg_vcycle_noalloc")
 KT_AUGMENTED = 0
 KT_SMOOTH_TOP = 1
 KT_CORRECTION = 2
@@ -97,6 +97,7 @@ def load():
         "fmg_set_kernel_timing": (c_int, [c_void_p, c_int]),
         "fmg_kernel_time": (c_int, [c_void_p, c_int, c_int, POINTER(c_double), POINTER(c_int)]),
         "fmg_graph_kernels": (c_int, [c_void_p]),
+        "fmg_vcycle_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -255,6 +256,15 @@ def fmg_kernel_time(ctx, kind: int, level: int = 0):
 
 def fmg_graph_kernels(ctx) -> int:
     return load().fmg_graph_kernels(ctx)
+
+
+def fmg_vcycle_noalloc(dim, coarse_cells, level, b, u, cycles=1, nu_pre=2, nu_post=2, stream=None):
+    """V-cycles with no device allocation (scratch in a fixed device array of the library);
+    queues work on `stream` (a torch.cuda.Stream, a raw handle, or None for the default
+    stream) and returns without waiting."""
+    _device_sync()
+    sp = getattr(stream, "cuda_stream", stream)
+    _check(load().fmg_vcycle_noalloc(dim, coarse_cells, level, _ptr(b)[0], _ptr(u)[0], cycles, nu_pre, nu_post, sp))
 
 
 # ---------------------------------------------------------------------------- convenience
