@@ -135,12 +135,13 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
   const size_t items = cfg.partial_items;
   double* partials = (double*)take(items * aug_nvals(p->dim) * 8);
   double* cc = (double*)take(ipow(p->coarse_cells + 1, p->dim) * 8);
-  double* sys = (double*)take((2 * N1 + 8) * 8);
+  double* sys = (double*)take((2 * N1 + 8 + ipow(p->coarse_cells, p->dim) * ((1 << p->dim) + 1)) * 8);
   if (c && base) {
     c->Ainv = Ainv;
     c->st = st;
     c->ab = cfg;
     c->ab.partials = partials;
+    c->ab.Ainv = Ainv;
     c->ab.c = cc;
     c->ab.sys = sys;
   }

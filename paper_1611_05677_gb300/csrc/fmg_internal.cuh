@@ -168,6 +168,7 @@ struct AugBuffers {
   double* partials;   // [items][nvals]
   double* c;          // coarse nodal iterate (level-1 layout), length (nH+1)^d
   double* sys;        // scratch: t, G_H, s, gamma and the dense system
+  const double* Ainv; // A_H^{-1}: preconditioner of the mixed path's Newton solves
   size_t partial_items;
   int bpc;            // blocks per coarse cell of the cooperative launch (all co-resident)
   int nt;             // threads per block

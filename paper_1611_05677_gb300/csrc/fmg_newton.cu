@@ -398,7 +398,8 @@ struct AugArgs {
   const double* g;      // level-k nodal g
   double* partials;     // [cells * bpc][NVAL]
   double* c;            // coarse nodal iterate ((nc+1)^d, boundary 0)
-  double* sys;          // t[NH] G_H[NH] s gamma
+  double* sys;          // t[NH] G_H[NH] s gamma, mixed path: first-pass residual sums
+  const double* Ainv;   // A_H^{-1} (= A_1^{-1}, h_1 = H), dense NH x NH, preconditioner
   DevState* st;
 };
 
@@ -483,6 +484,47 @@ __device__ __forceinline__ int column_segments(const int* o, int s, Seg<D>* sg) 
 
 enum { kFirst = 0, kNewton = 1, kUpdate = 2 };
 
+// Mixed path, passes after the first: the increment dF = a (f(u~ + d) - f(u~)) and a f'(u~ + d)
+// in FP32, from closed forms that do not cancel (d is the small Newton correction
+// (alpha - 1) u~ + P c).  The residual sums of the first pass (FP64, at U = u~) plus these
+// increments give the residual at U to FP64-level accuracy.  signed |u|^{3/2} has no such
+// form and is evaluated in FP64.
+__device__ __forceinline__ void delta_f(int kind, double a, double ut, float utf, float d, float af, float& dF,
+                                        float& Fp) {
+  switch (kind) {
+    case FMG_F_CUBIC: {
+      const float U = utf + d;
+      dF = af * d * fmaf(3.0f * utf, U, d * d);
+      Fp = 3.0f * af * U * U;
+      break;
+    }
+    case FMG_F_EXPM1: {
+      const float e = expf(utf);
+      dF = af * e * expm1f(d);
+      Fp = af * e * expf(d);
+      break;
+    }
+    case FMG_F_LINEAR:
+      dF = af * d;
+      Fp = af;
+      break;
+    case FMG_F_NEG_EXP_NEG: {
+      const float e = expf(-utf);
+      dF = -af * e * expm1f(-d);
+      Fp = af * e * expf(-d);
+      break;
+    }
+    default: {  // FMG_F_SIGNED_POW32
+      double F1, F0, Fp1, Fp0;
+      f_eval<double>(kind, a, ut + (double)d, F1, Fp1);
+      f_eval<double>(kind, a, ut, F0, Fp0);
+      dF = (float)(F1 - F0);
+      Fp = (float)Fp1;
+      break;
+    }
+  }
+}
+
 // The fine pass of one block: columns of its cell, chunk by chunk.  `acc` holds the
 // per-thread channel rows ([NVAL][NT] doubles), zero on entry.
 template <int D, bool JF32>
@@ -543,7 +585,56 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
       double T0 = 0.0, T1 = 0.0, SSv = 0.0, G0 = 0.0, G1 = 0.0, SGv = 0.0;  // first pass
       double zd = (double)z0;
       long long off = base + (long long)(zc + z0) * zstride;
+      if (JF32 && phase != kFirst) {
+        // mixed path: FP32 increments on top of the first pass's FP64 residual sums
+        const float pc0f = (float)pc0, pc1f = (float)pc1, am1f = (float)(alpha - 1.0), af = (float)A.a;
+        float q0 = 0.f, q1 = 0.f, sa = 0.f;
+        auto node = [&](double ut, float zf, long long o) {
+          const float utf = (float)ut;
+          const float dl = fmaf(am1f, utf, fmaf(pc1f, zf, pc0f));
+          if (phase == kUpdate) {
+            A.u[o] = ut + (double)dl;
+            return;
+          }
+          float dF, fp;
+          delta_f(A.kind, A.a, ut, utf, dl, af, dF, fp);
+          q0 += dF;
+          q1 = fmaf(dF, zf, q1);
+          sa = fmaf(dF, utf, sa);
+          const JT dz = (JT)fp * (JT)zf;
+          const JT du = (JT)fp * (JT)utf;
+          D0 += (JT)fp;
+          D1 += dz;
+          D2 += dz * (JT)zf;
+          E0 += du;
+          E1 += du * (JT)zf;
+          JSv += du * (JT)utf;
+        };
+        int z = z0;
+        // four independent loads in flight before the arithmetic
+        for (; z + 3 <= z1; z += 4, off += 4 * zstride) {
+          double v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = A.u[off + q * zstride];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) node(v[q], (float)(z + q), off + q * zstride);
+        }
+        for (; z <= z1; ++z, off += zstride) node(A.u[off], (float)z, off);
+        Q0 = q0;
+        Q1 = q1;
+        SAv = sa;
+      } else
       for (int z = z0; z <= z1; ++z, off += zstride, zd += 1.0) {
+        if (phase == kFirst && ((z - z0) & 3) == 0) {
+          // touch the next four column entries and their g values so that their loads are
+          // in flight together (they stay in L1 for the iterations below)
+#pragma unroll
+          for (int q = 1; q < 4; ++q)
+            if (z + q <= z1) {
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(A.u + off + q * zstride));
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(A.g + off + q * zstride));
+            }
+        }
         const double ut = A.u[off];
         const double U = phase == kFirst ? ut : fma(alpha, ut, fma(pc1, zd, pc0));
         if (phase == kUpdate) {
@@ -614,18 +705,31 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
   }
 }
 
-// Block sum of the channel rows into out[0..NVAL) (fixed order).
+// Block sum of the channel rows into out[0..NVAL) (fixed order).  Only the channels the
+// phase produced are summed (the first-pass gatherings t, G_H, s, gamma only in the first
+// pass); in the mixed path the Jacobian channels, FP32 products to begin with, are summed in
+// FP32 -- FP64 adds issue slowly on this part.
 template <int D, bool JF32>
-__device__ void block_reduce_rows(const double* acc, double* out) {
+__device__ void block_reduce_rows(const double* acc, double* out, bool first) {
   using G = Aug<D, JF32>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = G::NT / 32;
   __syncthreads();
   for (int v = warp; v < G::NVAL; v += nw) {
-    double x = 0.0;
-    for (int t = lane; t < G::NT; t += 32) x += acc[v * G::NT + t];
+    const bool pre = v >= G::TT && v < G::JB;
+    if (pre && !first) continue;
+    if (JF32 && v >= G::JB) {
+      float x = 0.f;
+      for (int t = lane; t < G::NT; t += 32) x += (float)acc[v * G::NT + t];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) out[v] = x;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) out[v] = (double)x;
+    } else {
+      double x = 0.0;
+      for (int t = lane; t < G::NT; t += 32) x += acc[v * G::NT + t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) out[v] = x;
+    }
   }
   __syncthreads();
 }
@@ -693,6 +797,187 @@ __device__ double pair_channel(const double* cellsum, int nc, const int* zp, con
   return x;
 }
 
+// The Newton system J d = rhs with J = [[K, j], [j^T, q]] (K = J_HH, N_H x N_H; the last
+// unknown is alpha), solved through its Schur complement: K z1 = j and K z2 = rhs_H by
+// preconditioned conjugate gradients with the precomputed A_H^{-1} (K = A_H + P^T W D P with
+// D >= 0, so the preconditioned spectrum is 1 + O(max f' / 2 pi^2)), then
+// d_alpha = (rhs_alpha - j.z2) / (q - j.z1) and d_H = z2 - d_alpha z1.  FP32 throughout
+// (the mixed path's inexact Newton step; the FP64 residual makes the next step correct for
+// it).  Matrix-vector products run on all warps, scalar recurrences on warp 0.  rhs (FP64)
+// is overwritten by d.  Returns false if CG did not reach 1e-3 relative accuracy (the
+// caller then factors instead); *dropped as in block_chol_solve.
+__device__ bool pcg_schur_solve(const double* M, int NA, int ld, double* rhs, const double* Ainv_g, float* wk,
+                                double drop_tol, int* dropped) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int n = NA - 1;
+  const int n2 = n * n;
+  float* K = wk;                     // n x n
+  float* Ai = K + n2;                // n x n
+  float* x1 = Ai + n2;               // per-RHS vectors, stride n
+  float* x2 = x1 + n;
+  float* r1 = x2 + n;
+  float* r2 = r1 + n;
+  float* z1 = r2 + n;
+  float* z2 = z1 + n;
+  float* p1 = z2 + n;
+  float* p2 = p1 + n;
+  float* w1 = p2 + n;
+  float* w2 = w1 + n;
+  float* sc = w2 + n;                // scalars: rho1, rho2, b0n1, b0n2, done, ...
+  __shared__ int cg_ok, cg_drop;
+  for (int idx = tid; idx < n2; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    K[idx] = (float)M[i * ld + j];
+    Ai[idx] = (float)__ldg(&Ainv_g[idx]);
+  }
+  for (int i = tid; i < n; i += blockDim.x) {
+    x1[i] = 0.f;
+    x2[i] = 0.f;
+    r1[i] = (float)M[i * ld + n];   // j
+    r2[i] = (float)rhs[i];          // rhs_H
+  }
+  __syncthreads();
+  // thread-per-row products (n <= 64): no reductions; row stride n keeps the banks distinct
+  // for odd n and at most 2-way conflicts for even n
+  auto matvec2 = [&](const float* A, const float* v1, const float* v2, float* o1, float* o2) {
+    for (int i = tid; i < n; i += blockDim.x) {
+      const float* Ar = A + i * n;
+      float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+      int j = 0;
+      for (; j + 1 < n; j += 2) {
+        a1 = fmaf(Ar[j], v1[j], a1);
+        a2 = fmaf(Ar[j], v2[j], a2);
+        b1 = fmaf(Ar[j + 1], v1[j + 1], b1);
+        b2 = fmaf(Ar[j + 1], v2[j + 1], b2);
+      }
+      if (j < n) {
+        a1 = fmaf(Ar[j], v1[j], a1);
+        a2 = fmaf(Ar[j], v2[j], a2);
+      }
+      o1[i] = a1 + b1;
+      o2[i] = a2 + b2;
+    }
+  };
+  auto dot2 = [&](const float* a1, const float* b1, const float* a2, const float* b2, float& s1, float& s2) {
+    float t1 = 0.f, t2 = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      t1 = fmaf(a1[i], b1[i], t1);
+      t2 = fmaf(a2[i], b2[i], t2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+      t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+    }
+    s1 = t1;
+    s2 = t2;
+  };
+  matvec2(Ai, r1, r2, z1, z2);
+  __syncthreads();
+  if (warp == 0) {
+    float rho1, rho2, m1 = 0.f, m2 = 0.f;
+    dot2(r1, z1, r2, z2, rho1, rho2);
+    for (int i = lane; i < n; i += 32) {
+      p1[i] = z1[i];
+      p2[i] = z2[i];
+      m1 = fmaxf(m1, fabsf(r1[i]));
+      m2 = fmaxf(m2, fabsf(r2[i]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+      m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if (lane == 0) {
+      sc[0] = rho1;
+      sc[1] = rho2;
+      sc[2] = m1;
+      sc[3] = m2;
+      sc[4] = 0.f;   // done
+      sc[5] = 0.f;   // best relative residual reached (max of the two)
+    }
+  }
+  __syncthreads();
+  const float tol = 2e-7f;
+  int it = 0;
+  for (it = 0; it < 60; ++it) {
+    matvec2(K, p1, p2, w1, w2);
+    __syncthreads();
+    if (warp == 0) {
+      float mu1, mu2;
+      dot2(p1, w1, p2, w2, mu1, mu2);
+      const float a1 = (mu1 > 0.f) ? sc[0] / mu1 : 0.f;
+      const float a2 = (mu2 > 0.f) ? sc[1] / mu2 : 0.f;
+      float e1 = 0.f, e2 = 0.f;
+      for (int i = lane; i < n; i += 32) {
+        x1[i] = fmaf(a1, p1[i], x1[i]);
+        x2[i] = fmaf(a2, p2[i], x2[i]);
+        r1[i] = fmaf(-a1, w1[i], r1[i]);
+        r2[i] = fmaf(-a2, w2[i], r2[i]);
+        e1 = fmaxf(e1, fabsf(r1[i]));
+        e2 = fmaxf(e2, fabsf(r2[i]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e1 = fmaxf(e1, __shfl_xor_sync(0xffffffffu, e1, o));
+        e2 = fmaxf(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+      }
+      if (lane == 0) {
+        const float rel = fmaxf(sc[2] > 0.f ? e1 / sc[2] : 0.f, sc[3] > 0.f ? e2 / sc[3] : 0.f);
+        sc[5] = rel;
+        sc[4] = (rel <= tol) ? 1.f : 0.f;
+      }
+    }
+    __syncthreads();
+    if (sc[4] != 0.f) break;
+    matvec2(Ai, r1, r2, z1, z2);
+    __syncthreads();
+    if (warp == 0) {
+      float rn1, rn2;
+      dot2(r1, z1, r2, z2, rn1, rn2);
+      const float b1 = sc[0] > 0.f ? rn1 / sc[0] : 0.f;
+      const float b2 = sc[1] > 0.f ? rn2 / sc[1] : 0.f;
+      for (int i = lane; i < n; i += 32) {
+        p1[i] = fmaf(b1, p1[i], z1[i]);
+        p2[i] = fmaf(b2, p2[i], z2[i]);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        sc[0] = rn1;
+        sc[1] = rn2;
+      }
+    }
+    __syncthreads();
+  }
+  // Schur complement for alpha (FP64 scalars from the FP32 solves)
+  if (warp == 0) {
+    double jz1 = 0.0, jz2 = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double jv = M[i * ld + n];
+      jz1 += jv * (double)x1[i];
+      jz2 += jv * (double)x2[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      jz1 += __shfl_xor_sync(0xffffffffu, jz1, o);
+      jz2 += __shfl_xor_sync(0xffffffffu, jz2, o);
+    }
+    const double q = M[n * ld + n];
+    const double sa = q - jz1;
+    const bool drop = !(sa > drop_tol * q);
+    const double da = drop ? 0.0 : (rhs[n] - jz2) / sa;
+    for (int i = lane; i < n; i += 32) rhs[i] = (double)x2[i] - da * (double)x1[i];
+    if (lane == 0) {
+      rhs[n] = da;
+      cg_drop = drop;
+      cg_ok = sc[5] <= 1e-3f;
+    }
+  }
+  __syncthreads();
+  if (dropped) *dropped = cg_drop;
+  return cg_ok != 0;
+}
+
 // Block 0, after a pass: cell sums, the dense system, the Newton step, convergence.
 template <int D, bool JF32>
 __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double* R,
@@ -711,12 +996,27 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
   // cell sums over the blocks of each cell (fixed order)
   for (int idx = tid; idx < ncell * G::NVAL; idx += blockDim.x) {
     const int cell = idx / G::NVAL, v = idx % G::NVAL;
+    if (!first && v >= G::TT && v < G::JB) continue;
     double x = 0.0;
     for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + v]);
     cellsum[idx] = x;
   }
   for (int idx = tid; idx < NA * ld; idx += blockDim.x) M[idx] = 0.0;
   __syncthreads();
+  if (JF32) {
+    // mixed path: after the first pass the residual channels hold increments; the first
+    // pass's FP64 sums are kept in sys and added back (fixed order, same thread each time)
+    double* basev = A.sys + 2 * NH + 2;
+    for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
+      const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
+      const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
+      if (first)
+        basev[idx] = cellsum[ch];
+      else
+        cellsum[ch] += basev[idx];
+    }
+    __syncthreads();
+  }
   if (first) {
     for (int p = tid; p < NH; p += blockDim.x) {
       int z[3];
@@ -806,13 +1106,28 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     }
   }
   __syncthreads();
-  // Newton step: factor (FP64, or FP32 in the mixed path) and solve by the whole block
-  for (int idx = tid; idx < NA * ld; idx += blockDim.x) L[idx] = (FT)M[idx];
-  __syncthreads();
-  FT* work = L + (size_t)NA * ld;
-  FT* invd = work + NA;
+  // Newton step.  FP64 path: blocked Cholesky in FP64.  Mixed path: Schur complement with
+  // A_H^{-1}-preconditioned CG in FP32, falling back to the FP32 Cholesky if CG stalls.
   int dropped = 0;
-  const bool ok = block_chol_solve<FT>(L, NA, ld, R, work, invd, true, 1e-14, &dropped);
+  bool ok = true;
+  bool solved = false;
+  if (JF32) {
+    __shared__ double rsave[kMaxAug];
+    for (int i = tid; i < NA; i += blockDim.x) rsave[i] = R[i];
+    __syncthreads();
+    solved = pcg_schur_solve(M, NA, ld, R, A.Ainv, reinterpret_cast<float*>(L), 1e-6, &dropped);
+    if (!solved) {
+      for (int i = tid; i < NA; i += blockDim.x) R[i] = rsave[i];
+      __syncthreads();
+    }
+  }
+  if (!solved) {
+    for (int idx = tid; idx < NA * ld; idx += blockDim.x) L[idx] = (FT)M[idx];
+    __syncthreads();
+    FT* work = L + (size_t)NA * ld;
+    FT* invd = work + NA;
+    ok = block_chol_solve<FT>(L, NA, ld, R, work, invd, true, 1e-14, &dropped);
+  }
   // update of (c, alpha), convergence test (one warp)
   if (tid < 32) {
     double dmax = 0.0, ymax = 0.0;
@@ -911,7 +1226,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
     __syncthreads();
     if (stop) break;
     fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, bic);
-    block_reduce_rows<D, JF32>(acc, A.partials + (long long)blockIdx.x * G::NVAL);
+    block_reduce_rows<D, JF32>(acc, A.partials + (long long)blockIdx.x * G::NVAL, first);
     grid_barrier(A.st, nblocks);
     if (blockIdx.x == 0) newton_step<D, JF32>(A, cellsum, M, R, L, alpha_sh, first);
     grid_barrier(A.st, nblocks);
@@ -938,7 +1253,8 @@ size_t aug_smem(int nc) {
   const int ncell = (int)ipow(nc, D);
   const int NA = (int)ipow(nc - 1, D) + 1;
   const size_t rows = (size_t)G::NVAL * G::NT;
-  const size_t scratch = (size_t)ncell * G::NVAL + 2 * ((size_t)NA * (NA + 1)) + 3 * NA + 4;
+  // cellsum, M, R, then the factor (NA (NA+1) values) or the CG workspace (2 NA^2 + 12 NA floats)
+  const size_t scratch = (size_t)ncell * G::NVAL + 2 * ((size_t)NA * (NA + 1)) + 3 * NA + 4 + (size_t)NA * NA + 8 * NA;
   return sizeof(double) * (rows > scratch ? rows : scratch);
 }
 
@@ -1051,6 +1367,7 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.partials = ab.partials;
   A.c = ab.c;
   A.sys = ab.sys;
+  A.Ainv = ab.Ainv;
   A.st = st;
   // barrier words and abort/converged flags start cleared
   cudaError_t e = cudaMemsetAsync(&st->bar_count, 0, 4 * sizeof(unsigned), s);
