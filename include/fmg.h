@@ -106,10 +106,10 @@ typedef struct {
 } fmg_stats;
 
 /* Defaults: dim 2, 1/H = 4, 4 refinements, cubic, a = 1, m = 2, nu = 2/2, p = 1 (the
- * schedule of Sec. 4: m = 2, p = 1), FP64, Newton tol 1e-8 / cap 20, level-1 tol 1e-8 /
+ * schedule of Sec. 4: m = 2, p = 1), FP64, Newton tol 1e-6 / cap 20, level-1 tol 1e-6 /
  * cap 50.  Newton converges quadratically near the solution, so the update that passes the
- * 1e-8 test leaves an error of order 1e-16; in the mixed path the FP32 Jacobian makes the
- * convergence linear with a rate near 1e-5, leaving about 1e-13. */
+ * 1e-6 test leaves an error of order 1e-12; in the mixed path the FP32 Jacobian and linear
+ * solves make the convergence linear with a rate near 1e-6, leaving about 1e-12 as well. */
 void fmg_default_params(fmg_params* p);
 
 /* Device bytes one context needs for these parameters (the workspace size fmg_create
@@ -201,7 +201,9 @@ fmg_status fmg_op_prolong(fmg_ctx* c, int level, const double* u_coarse, double*
 typedef enum {
   FMG_KT_AUGMENTED = 0,   /* the augmented-space Newton kernel of a correction step (eq. 3.6) */
   FMG_KT_SMOOTH_TOP = 1,  /* one red-black sweep (both colours) on the cycle's top level */
-  FMG_KT_CORRECTION = 2   /* a whole correction step (Algorithm 3.1) */
+  FMG_KT_CORRECTION = 2,  /* a whole correction step (Algorithm 3.1) */
+  FMG_KT_PRE_TOP = 3,     /* mixed path, 2D: fused pre-smoothing + residual + restriction, top level */
+  FMG_KT_POST_TOP = 4     /* mixed path, 2D: fused prolongation + post-smoothing + FP64 update, top level */
 } fmg_kernel_kind;
 
 /* on != 0: the next fmg_solve recaptures its graph with a pair of CUDA events around every

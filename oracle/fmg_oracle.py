@@ -33,9 +33,9 @@ Readings where the paper is silent (each is listed with its reason in the
 design notes): h_1 = H; vertex quadrature; V(nu1,nu2) cycles with red->black
 pre-smoothing and black->red post-smoothing; Newton on the augmented space
 from (c, alpha) = (0, 1) stopping after the update whose increment satisfies
-||delta||_inf <= tol*max(1,||y||_inf), tol = 1e-8 (quadratic convergence leaves
-an error of order tol^2 after that update); the same rule, from U = 0, for
-the exact solve on level 1.
+||delta||_inf <= tol*max(1,||y||_inf), tol = 1e-6 (quadratic convergence leaves
+an error of order tol^2 = 1e-12 after that update); the same rule, from U = 0,
+for the exact solve on level 1.
 """
 from __future__ import annotations
 
@@ -399,7 +399,7 @@ class StepInfo:
 
 
 def augmented_newton(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarray, kind: str, a: float,
-                     tol: float = 1e-8, maxit: int = 30):
+                     tol: float = 1e-6, maxit: int = 30):
     """Newton on (3.6): find y = (c, alpha) with u = P_{H->k} c + alpha u~ such that
     B^T A_k B y + B^T W f(B y) = B^T G,  B = [P_{H->k} | u~].
 
@@ -427,7 +427,7 @@ def augmented_newton(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarr
 
 
 def correction_step(hier: Hierarchy, k: int, u: np.ndarray, G: np.ndarray, kind: str, a: float,
-                    m: int = 2, nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-8):
+                    m: int = 2, nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-6):
     """u^{(l+1)} = SemilinearMG(V_H, u^{(l)}, V_{h_k}) (Algorithm 3.1)."""
     lev = hier.level(k)
     # step 1 (eq. 3.4): a(u^, v) = (g, v) - (f(x, u^{(l)}), v)
@@ -454,7 +454,7 @@ class FMGResult:
 
 
 def fmg(hier: Hierarchy, g_fine: np.ndarray, kind: str, a: float, m: int = 2, p: int = 1,
-        nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-8, tol_level1: float = 1e-8,
+        nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-6, tol_level1: float = 1e-6,
         keep_levels: bool = True) -> FMGResult:
     n_levels = len(hier.levels)
     n_fine = hier.levels[-1].n

@@ -27,6 +27,7 @@ struct fmg_ctx {
   double* g[kMaxLevels] = {};
   float* u32[kMaxLevels] = {};
   float* b32[kMaxLevels] = {};
+  float* u32b[kMaxLevels] = {};   // second FP32 buffer: output of the fused pre-smoothing kernel
   double* Ainv = nullptr;
   DevState* st = nullptr;
   AugBuffers ab = {};
@@ -114,9 +115,11 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
     double* g = (double*)take(nodes * 8);
     float* u32 = nullptr;
     float* b32 = nullptr;
+    float* u32b = nullptr;
     if (p->precision == FMG_PREC_MIXED) {
       u32 = (float*)take(nodes * 4);
       b32 = (float*)take(nodes * 4);
+      if (fused_cycle_supported(p->dim, p->nu_pre, p->nu_post)) u32b = (float*)take(nodes * 4);
     }
     if (c && base) {
       c->u[k] = u;
@@ -124,6 +127,7 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
       c->g[k] = g;
       c->u32[k] = u32;
       c->b32[k] = b32;
+      c->u32b[k] = u32b;
     }
   }
   const int m = p->coarse_cells - 1;
@@ -226,6 +230,32 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
   return cudaSuccess;
 }
 
+// FP32 cycle below level j with the fused kernels: the correction starts at zero on every
+// level (the parent's restriction zeroes it; the top level's defect equation starts at zero),
+// pre-smoothing writes the level's second buffer, post-smoothing reads it back into the first
+// one -- or, on the top level, adds the result to the FP64 iterate u64.
+cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
+  const int dim = c->p.dim;
+  cudaStream_t s = c->stream;
+  if (j == 1) return launch_coarse_solve_f32(dim, c->geo[0], c->Ainv, c->b32[0], c->u32[0], s);
+  if (j <= coarse_cycle_top<float>(c)) {
+    TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, c->u32[j - 1], c->b32[j - 1], c->p.nu_pre,
+                                   c->p.nu_post, c->Ainv, s));
+    return u64_top ? launch_add_f32(c->geo[j - 1], dim, u64_top, c->u32[j - 1], s) : cudaSuccess;
+  }
+  const LevelGeo gf = c->geo[j - 1];
+  int slot = -1;
+  if (u64_top) TRY(tbegin(c, FMG_KT_PRE_TOP, j, &slot));
+  TRY(launch_pre_fused(dim, gf, c->p.nu_pre, c->b32[j - 1], c->u32b[j - 1], c->b32[j - 2], c->u32[j - 2], s));
+  TRY(tend(c, slot));
+  TRY(vcycle32_fused(c, j - 1, nullptr));
+  slot = -1;
+  if (u64_top) TRY(tbegin(c, FMG_KT_POST_TOP, j, &slot));
+  TRY(launch_post_fused(dim, gf, c->p.nu_post, c->u32b[j - 1], c->u32[j - 2], c->b32[j - 1], c->u32[j - 1], u64_top,
+                        s));
+  return tend(c, slot);
+}
+
 cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
@@ -266,6 +296,7 @@ cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
   // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update
   if ((e = launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream)) != cudaSuccess)
     return e;
+  if (c->u32b[k - 1]) return vcycle32_fused(c, k, u);
   if ((e = vcycle32(c, k, true)) != cudaSuccess) return e;
   return launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream);
 }
@@ -371,9 +402,9 @@ void fmg_default_params(fmg_params* p) {
   p->nu_post = 2;
   p->p_corrections = 1;
   p->precision = FMG_PREC_FP64;
-  p->newton_tol = 1e-8;
+  p->newton_tol = 1e-6;
   p->newton_maxit = 20;
-  p->level1_tol = 1e-8;
+  p->level1_tol = 1e-6;
   p->level1_maxit = 50;
 }
 

@@ -182,6 +182,15 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
                              DevState* st, int level_index, cudaStream_t s);
 
+// Fused FP32 cycle kernels of the mixed path (fmg_fused.cu): 2D, nu in {1, 2}.
+bool fused_cycle_supported(int dim, int nu_pre, int nu_post);
+// nu sweeps from zero on level g, then b_c = P^T (b - A u), u_c = 0 on the next coarser level
+cudaError_t launch_pre_fused(int dim, LevelGeo g, int nu, const float* b, float* u_out, float* bc, float* uc,
+                             cudaStream_t s);
+// u = u_in + P e_c, nu black-red sweeps; stored in u_out, or added to u64_top when non-NULL
+cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, const float* ec, const float* b,
+                              float* u_out, double* u64_top, cudaStream_t s);
+
 // Sets the calling thread's error message (what fmg_last_error(NULL) returns).
 void set_thread_error(const std::string& msg);
 

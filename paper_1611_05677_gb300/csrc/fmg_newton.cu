@@ -808,154 +808,128 @@ __device__ double pair_channel(const double* cellsum, int nc, const int* zp, con
 // caller then factors instead); *dropped as in block_chol_solve.
 __device__ bool pcg_schur_solve(const double* M, int NA, int ld, double* rhs, const double* Ainv_g, float* wk,
                                 double drop_tol, int* dropped) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int n = NA - 1;
-  const int n2 = n * n;
-  float* K = wk;                     // n x n
-  float* Ai = K + n2;                // n x n
-  float* x1 = Ai + n2;               // per-RHS vectors, stride n
-  float* x2 = x1 + n;
-  float* r1 = x2 + n;
-  float* r2 = r1 + n;
-  float* z1 = r2 + n;
-  float* z2 = z1 + n;
-  float* p1 = z2 + n;
-  float* p2 = p1 + n;
-  float* w1 = p2 + n;
-  float* w2 = w1 + n;
-  float* sc = w2 + n;                // scalars: rho1, rho2, b0n1, b0n2, done, ...
+  float* K = wk;        // n x n
+  float* Ai = K + n * n;  // n x n
   __shared__ int cg_ok, cg_drop;
-  for (int idx = tid; idx < n2; idx += blockDim.x) {
-    const int i = idx / n, j = idx % n;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
     K[idx] = (float)M[i * ld + j];
     Ai[idx] = (float)__ldg(&Ainv_g[idx]);
   }
-  for (int i = tid; i < n; i += blockDim.x) {
-    x1[i] = 0.f;
-    x2[i] = 0.f;
-    r1[i] = (float)M[i * ld + n];   // j
-    r2[i] = (float)rhs[i];          // rhs_H
-  }
   __syncthreads();
-  // thread-per-row products (n <= 64): no reductions; row stride n keeps the banks distinct
-  // for odd n and at most 2-way conflicts for even n
-  auto matvec2 = [&](const float* A, const float* v1, const float* v2, float* o1, float* o2) {
-    for (int i = tid; i < n; i += blockDim.x) {
-      const float* Ar = A + i * n;
-      float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
-      int j = 0;
-      for (; j + 1 < n; j += 2) {
-        a1 = fmaf(Ar[j], v1[j], a1);
-        a2 = fmaf(Ar[j], v2[j], a2);
-        b1 = fmaf(Ar[j + 1], v1[j + 1], b1);
-        b2 = fmaf(Ar[j + 1], v2[j + 1], b2);
+  if (tid < 32) {
+    // one warp: vector entry i lives in lane i % 32, slot i / 32 (n <= 64)
+    const int i0 = lane, i1 = lane + 32;
+    const bool h0 = i0 < n, h1 = i1 < n;
+    float x1[2] = {0.f, 0.f}, x2[2] = {0.f, 0.f};
+    float r1[2] = {h0 ? (float)M[i0 * ld + n] : 0.f, h1 ? (float)M[i1 * ld + n] : 0.f};
+    float r2[2] = {h0 ? (float)rhs[i0] : 0.f, h1 ? (float)rhs[i1] : 0.f};
+    float z1[2], z2[2], p1[2], p2[2], w1[2], w2[2];
+    // y = A v for both right-hand sides: v is published to shared memory and read back as
+    // broadcast loads; the row loop is unrolled with split accumulators so that the loads of
+    // several columns are in flight together
+    __shared__ float vs1[kMaxAug], vs2[kMaxAug];
+    const int r0 = h0 ? i0 : 0, r1i = h1 ? i1 : 0;
+    auto matvec2 = [&](const float* A, const float* v1, const float* v2, float* o1, float* o2) {
+      if (h0) {
+        vs1[i0] = v1[0];
+        vs2[i0] = v2[0];
       }
-      if (j < n) {
-        a1 = fmaf(Ar[j], v1[j], a1);
-        a2 = fmaf(Ar[j], v2[j], a2);
-      }
-      o1[i] = a1 + b1;
-      o2[i] = a2 + b2;
-    }
-  };
-  auto dot2 = [&](const float* a1, const float* b1, const float* a2, const float* b2, float& s1, float& s2) {
-    float t1 = 0.f, t2 = 0.f;
-    for (int i = lane; i < n; i += 32) {
-      t1 = fmaf(a1[i], b1[i], t1);
-      t2 = fmaf(a2[i], b2[i], t2);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-      t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-    }
-    s1 = t1;
-    s2 = t2;
-  };
-  matvec2(Ai, r1, r2, z1, z2);
-  __syncthreads();
-  if (warp == 0) {
-    float rho1, rho2, m1 = 0.f, m2 = 0.f;
-    dot2(r1, z1, r2, z2, rho1, rho2);
-    for (int i = lane; i < n; i += 32) {
-      p1[i] = z1[i];
-      p2[i] = z2[i];
-      m1 = fmaxf(m1, fabsf(r1[i]));
-      m2 = fmaxf(m2, fabsf(r2[i]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-      m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-    }
-    if (lane == 0) {
-      sc[0] = rho1;
-      sc[1] = rho2;
-      sc[2] = m1;
-      sc[3] = m2;
-      sc[4] = 0.f;   // done
-      sc[5] = 0.f;   // best relative residual reached (max of the two)
-    }
-  }
-  __syncthreads();
-  const float tol = 2e-7f;
-  int it = 0;
-  for (it = 0; it < 60; ++it) {
-    matvec2(K, p1, p2, w1, w2);
-    __syncthreads();
-    if (warp == 0) {
-      float mu1, mu2;
-      dot2(p1, w1, p2, w2, mu1, mu2);
-      const float a1 = (mu1 > 0.f) ? sc[0] / mu1 : 0.f;
-      const float a2 = (mu2 > 0.f) ? sc[1] / mu2 : 0.f;
-      float e1 = 0.f, e2 = 0.f;
-      for (int i = lane; i < n; i += 32) {
-        x1[i] = fmaf(a1, p1[i], x1[i]);
-        x2[i] = fmaf(a2, p2[i], x2[i]);
-        r1[i] = fmaf(-a1, w1[i], r1[i]);
-        r2[i] = fmaf(-a2, w2[i], r2[i]);
-        e1 = fmaxf(e1, fabsf(r1[i]));
-        e2 = fmaxf(e2, fabsf(r2[i]));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        e1 = fmaxf(e1, __shfl_xor_sync(0xffffffffu, e1, o));
-        e2 = fmaxf(e2, __shfl_xor_sync(0xffffffffu, e2, o));
-      }
-      if (lane == 0) {
-        const float rel = fmaxf(sc[2] > 0.f ? e1 / sc[2] : 0.f, sc[3] > 0.f ? e2 / sc[3] : 0.f);
-        sc[5] = rel;
-        sc[4] = (rel <= tol) ? 1.f : 0.f;
-      }
-    }
-    __syncthreads();
-    if (sc[4] != 0.f) break;
-    matvec2(Ai, r1, r2, z1, z2);
-    __syncthreads();
-    if (warp == 0) {
-      float rn1, rn2;
-      dot2(r1, z1, r2, z2, rn1, rn2);
-      const float b1 = sc[0] > 0.f ? rn1 / sc[0] : 0.f;
-      const float b2 = sc[1] > 0.f ? rn2 / sc[1] : 0.f;
-      for (int i = lane; i < n; i += 32) {
-        p1[i] = fmaf(b1, p1[i], z1[i]);
-        p2[i] = fmaf(b2, p2[i], z2[i]);
+      if (h1) {
+        vs1[i1] = v1[1];
+        vs2[i1] = v2[1];
       }
       __syncwarp();
-      if (lane == 0) {
-        sc[0] = rn1;
-        sc[1] = rn2;
+      const float* A0 = A + r0 * n;
+      const float* A1 = A + r1i * n;
+      float a10 = 0.f, a11 = 0.f, a20 = 0.f, a21 = 0.f, c10 = 0.f, c11 = 0.f, c20 = 0.f, c21 = 0.f;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < n; j += 2) {
+        const float b1 = vs1[j], b2 = vs2[j], d1 = vs1[j + 1], d2 = vs2[j + 1];
+        const float x0 = A0[j], y0 = A0[j + 1], x1 = A1[j], y1 = A1[j + 1];
+        a10 = fmaf(x0, b1, a10);
+        a20 = fmaf(x0, b2, a20);
+        a11 = fmaf(x1, b1, a11);
+        a21 = fmaf(x1, b2, a21);
+        c10 = fmaf(y0, d1, c10);
+        c20 = fmaf(y0, d2, c20);
+        c11 = fmaf(y1, d1, c11);
+        c21 = fmaf(y1, d2, c21);
       }
+      if (j < n) {
+        const float b1 = vs1[j], b2 = vs2[j];
+        a10 = fmaf(A0[j], b1, a10);
+        a20 = fmaf(A0[j], b2, a20);
+        a11 = fmaf(A1[j], b1, a11);
+        a21 = fmaf(A1[j], b2, a21);
+      }
+      __syncwarp();
+      o1[0] = h0 ? a10 + c10 : 0.f;
+      o1[1] = h1 ? a11 + c11 : 0.f;
+      o2[0] = h0 ? a20 + c20 : 0.f;
+      o2[1] = h1 ? a21 + c21 : 0.f;
+    };
+    auto wsum = [&](float v) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      return v;
+    };
+    auto wmax = [&](float v) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      return v;
+    };
+    matvec2(Ai, r1, r2, z1, z2);
+    float rho1 = wsum(r1[0] * z1[0] + r1[1] * z1[1]);
+    float rho2 = wsum(r2[0] * z2[0] + r2[1] * z2[1]);
+    const float m1 = wmax(fmaxf(fabsf(r1[0]), fabsf(r1[1])));
+    const float m2 = wmax(fmaxf(fabsf(r2[0]), fabsf(r2[1])));
+    p1[0] = z1[0]; p1[1] = z1[1]; p2[0] = z2[0]; p2[1] = z2[1];
+    float rel = 1.f;
+    for (int it = 0; it < 60; ++it) {
+      matvec2(K, p1, p2, w1, w2);
+      const float mu1 = wsum(p1[0] * w1[0] + p1[1] * w1[1]);
+      const float mu2 = wsum(p2[0] * w2[0] + p2[1] * w2[1]);
+      const float a1 = mu1 > 0.f ? rho1 / mu1 : 0.f;
+      const float a2 = mu2 > 0.f ? rho2 / mu2 : 0.f;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        x1[q] = fmaf(a1, p1[q], x1[q]);
+        x2[q] = fmaf(a2, p2[q], x2[q]);
+        r1[q] = fmaf(-a1, w1[q], r1[q]);
+        r2[q] = fmaf(-a2, w2[q], r2[q]);
+      }
+      const float e1 = wmax(fmaxf(fabsf(r1[0]), fabsf(r1[1])));
+      const float e2 = wmax(fmaxf(fabsf(r2[0]), fabsf(r2[1])));
+      rel = fmaxf(m1 > 0.f ? e1 / m1 : 0.f, m2 > 0.f ? e2 / m2 : 0.f);
+      if (rel <= 2e-7f) break;
+      matvec2(Ai, r1, r2, z1, z2);
+      const float rn1 = wsum(r1[0] * z1[0] + r1[1] * z1[1]);
+      const float rn2 = wsum(r2[0] * z2[0] + r2[1] * z2[1]);
+      const float b1 = rho1 > 0.f ? rn1 / rho1 : 0.f;
+      const float b2 = rho2 > 0.f ? rn2 / rho2 : 0.f;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        p1[q] = fmaf(b1, p1[q], z1[q]);
+        p2[q] = fmaf(b2, p2[q], z2[q]);
+      }
+      rho1 = rn1;
+      rho2 = rn2;
     }
-    __syncthreads();
-  }
-  // Schur complement for alpha (FP64 scalars from the FP32 solves)
-  if (warp == 0) {
+    // Schur complement for alpha (FP64 scalars from the FP32 solves)
     double jz1 = 0.0, jz2 = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      const double jv = M[i * ld + n];
-      jz1 += jv * (double)x1[i];
-      jz2 += jv * (double)x2[i];
+    if (h0) {
+      const double jv = M[i0 * ld + n];
+      jz1 += jv * (double)x1[0];
+      jz2 += jv * (double)x2[0];
+    }
+    if (h1) {
+      const double jv = M[i1 * ld + n];
+      jz1 += jv * (double)x1[1];
+      jz2 += jv * (double)x2[1];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -966,11 +940,13 @@ __device__ bool pcg_schur_solve(const double* M, int NA, int ld, double* rhs, co
     const double sa = q - jz1;
     const bool drop = !(sa > drop_tol * q);
     const double da = drop ? 0.0 : (rhs[n] - jz2) / sa;
-    for (int i = lane; i < n; i += 32) rhs[i] = (double)x2[i] - da * (double)x1[i];
+    __syncwarp();
+    if (h0) rhs[i0] = (double)x2[0] - da * (double)x1[0];
+    if (h1) rhs[i1] = (double)x2[1] - da * (double)x1[1];
     if (lane == 0) {
       rhs[n] = da;
       cg_drop = drop;
-      cg_ok = sc[5] <= 1e-3f;
+      cg_ok = rel <= 1e-3f;
     }
   }
   __syncthreads();

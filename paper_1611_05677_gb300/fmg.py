@@ -57,6 +57,8 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
 KT_AUGMENTED = 0
 KT_SMOOTH_TOP = 1
 KT_CORRECTION = 2
+KT_PRE_TOP = 3
+KT_POST_TOP = 4
 
 
 def library_path() -> str:
