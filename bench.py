@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refinements", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-solve", action="store_true",
+                    help="build, create one solver and run one solve, then exit (for ncu captures)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="large2d", choices=["large2d", "batch"],
+                    help="large2d: the headline single-instance solve; batch: 256 independent instances")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -224,7 +230,8 @@ def kernel_times(torch, fmg, solver, flush, steps, level):
     """Instrumented solves: per-kind durations on the finest level (CUDA events in the graph)."""
     fmg.fmg_set_kernel_timing(solver.ctx, True)
     fmg.fmg_solve(solver.ctx, None, fmg.fmg_stats())
-    acc = {fmg.KT_AUGMENTED: [0.0, 0], fmg.KT_SMOOTH_TOP: [0.0, 0], fmg.KT_CORRECTION: [0.0, 0]}
+    acc = {fmg.KT_AUGMENTED: [0.0, 0], fmg.KT_PRE_TOP: [0.0, 0], fmg.KT_POST_TOP: [0.0, 0],
+           fmg.KT_CORRECTION: [0.0, 0]}
     for _ in range(steps):
         with torch.cuda.stream(solver.stream):
             flush.zero_()
@@ -301,30 +308,42 @@ def run_ours(args):
     log("kernel timing")
     top = prob.levels
     kt = kernel_times(torch, fmg, solvers["mixed"], flush, max(3, args.steps // 2), top)
-    smooth_ms, smooth_n = kt[fmg.KT_SMOOTH_TOP]
     aug_ms, aug_n = kt[fmg.KT_AUGMENTED]
-    # algorithmic bytes of one FP32 red-black sweep: read b, read u, write u (4 B each) per node
+    pre_ms, pre_n = kt[fmg.KT_PRE_TOP]
+    post_ms, post_n = kt[fmg.KT_POST_TOP]
     nodes = (n + 1) ** 2
-    sweep_bytes = 12.0 * nodes
-    smooth_gbs = sweep_bytes / (smooth_ms * 1e-3) / 1e9 if smooth_ms > 0 else None
-    # augmented kernel at the top level: FP64 flops per launch (counted per fine node and pass)
-    iters = int(results["mixed"]["stats"].newton_iters[top - 1])
-    aug_flops = (40.0 * iters + 24.0) * dofs
+    # fused pre-smoothing on the top level: reads b (4 B/node), writes the correction
+    # (4 B/node) and the coarse b and u (8 B per coarse node = 2 B/node)
+    pre_bytes = 10.0 * nodes
+    # fused post-smoothing on the top level: reads the correction and b (8 B/node), the
+    # coarse correction (1 B/node), read-modify-writes the FP64 iterate (16 B/node)
+    post_bytes = 25.0 * nodes
+    pre_gbs = pre_bytes / (pre_ms * 1e-3) / 1e9 if pre_ms > 0 else None
+    post_gbs = post_bytes / (post_ms * 1e-3) / 1e9 if post_ms > 0 else None
+    # augmented Newton on the top level: the FP64 work is the first pass, 24 FP64 flops per
+    # fine node (f, residual moments, stencil A u~ and the t, G_H, s, gamma moments); the
+    # later passes are FP32 increments
+    aug_flops = 24.0 * dofs
     aug_tflops = aug_flops / (aug_ms * 1e-3) / 1e12 if aug_ms > 0 else None
-    shares = {"augmented": aug_ms * aug_n, "smooth_top": smooth_ms * smooth_n}
-    roof_smooth = {"kernel": "rbgs sweep (FP32, both colours) on the finest level", "bound": "hbm",
-                   "achieved": smooth_gbs, "peak": hbm_peak, "unit": "GB/s",
-                   "frac": (smooth_gbs / hbm_peak) if smooth_gbs else None, "traffic": None,
-                   "peak_source": peak_kind, "avg_launch_ms": smooth_ms, "launches": smooth_n,
-                   "algorithmic_bytes_per_launch": sweep_bytes}
-    roof_aug = {"kernel": "augmented Newton (FP64) on the finest level", "bound": "alu",
-                "achieved": aug_tflops, "peak": FP64_FLOPS_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
-                "frac": (aug_tflops * 1e12 / FP64_FLOPS_PEAK_DERIVED) if aug_tflops else None,
-                "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                "avg_launch_ms": aug_ms, "launches": aug_n, "algorithmic_flops_per_launch": aug_flops}
+    shares = {"augmented": aug_ms * aug_n, "pre_top": pre_ms * pre_n, "post_top": post_ms * post_n}
+    roof = {
+        "augmented": {"kernel": "k_augmented (mixed) on the finest level", "bound": "alu",
+                      "achieved": aug_tflops, "peak": FP64_FLOPS_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
+                      "frac": (aug_tflops * 1e12 / FP64_FLOPS_PEAK_DERIVED) if aug_tflops else None,
+                      "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                      "avg_launch_ms": aug_ms, "launches": aug_n, "algorithmic_flops_per_launch": aug_flops},
+        "pre_top": {"kernel": "k_pre2_fused on the finest level", "bound": "hbm", "achieved": pre_gbs,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": (pre_gbs / hbm_peak) if pre_gbs else None,
+                    "traffic": None, "peak_source": peak_kind, "avg_launch_ms": pre_ms, "launches": pre_n,
+                    "algorithmic_bytes_per_launch": pre_bytes},
+        "post_top": {"kernel": "k_post2_fused (top) on the finest level", "bound": "hbm", "achieved": post_gbs,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": (post_gbs / hbm_peak) if post_gbs else None,
+                     "traffic": None, "peak_source": peak_kind, "avg_launch_ms": post_ms, "launches": post_n,
+                     "algorithmic_bytes_per_launch": post_bytes},
+    }
     dominant = max(shares, key=shares.get)
-    roofline = roof_aug if dominant == "augmented" else roof_smooth
-    other = roof_smooth if dominant == "augmented" else roof_aug
+    roofline = roof[dominant]
+    other = {k: v for k, v in roof.items() if k != dominant}
 
     # ---- end to end through the public API with host buffers (pinned)
     log("e2e")
@@ -390,10 +409,142 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+BATCH_WORKLOAD = ("batched: independent 2D P1 instances, H=1/4, refinements U{5..9}, a*u^3 with a~U[0.5,2], "
+                  "seeded random-mode g; one CUDA graph, a branch per instance")
+
+
+def run_batch(args):
+    """Batched solves: one step = one launch of the batch graph (every instance solved once)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    dist, world, rank, local = dist_setup(torch)
+    assert torch.cuda.is_available(), "the GPU arm needs a CUDA device"
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_1611_05677_gb300 import fmg, workloads as W
+
+    probs = W.config_batch(seed=rank, count=args.batch_count)
+    dofs = sum(p.fine_dofs for p in probs)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    for prec in ("mixed", "fp64"):
+        log(f"batch {prec}: creating {len(probs)} solvers")
+        t0 = time.perf_counter()
+        solvers = [fmg.Solver(fmg.make_params(p, precision=prec), p.g_nodal()) for p in probs]
+        batch = fmg.Batch(solvers)
+        stats = batch.solve(wait=True)
+        setup_s = time.perf_counter() - t0
+        res[prec] = {"solvers": solvers, "batch": batch, "setup_s": setup_s,
+                     "flags": int(np.bitwise_or.reduce([st.flags for st in stats]))}
+    barrier(dist, torch)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for prec in ("mixed", "fp64"):
+            b = res[prec]["batch"]
+            for _ in range(args.warmup):
+                b.solve()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                with torch.cuda.stream(b.stream):
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(b.stream)
+                fmg.fmg_batch_solve(b.handle, None)
+                e1.record(b.stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            res[prec]["ms"] = max_over_ranks(dist, torch, statistics.mean(ms))
+    torch.cuda.synchronize()
+    barrier(dist, torch)
+    # one instance at a time (each instance's own graph), for comparison
+    log("sequential")
+    seq = {}
+    for prec in ("mixed", "fp64"):
+        solvers = res[prec]["solvers"]
+        for s in solvers:
+            fmg.fmg_solve(s.ctx, None, None)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st = solvers[0].stream
+        e0.record(st)
+        for s in solvers:
+            st.wait_stream(s.stream)
+            s.stream.wait_stream(st)
+            fmg.fmg_solve(s.ctx, None, None)
+            st.wait_stream(s.stream)
+        e1.record(st)
+        e1.synchronize()
+        seq[prec] = e0.elapsed_time(e1)
+    # accuracy: the mixed results against the FP64 results, relative discrete L2 per instance
+    res["mixed"]["batch"].solve(wait=True)
+    res["fp64"]["batch"].solve(wait=True)
+    worst = 0.0
+    for sm, sd in zip(res["mixed"]["solvers"], res["fp64"]["solvers"]):
+        a = sm.solution().double()
+        b = sd.solution().double()
+        worst = max(worst, float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)))
+    launches = sum(fmg.fmg_graph_kernels(s.ctx) for s in res["mixed"]["solvers"])
+    if rank == 0:
+        mix, f64 = res["mixed"]["ms"], res["fp64"]["ms"]
+        line = {
+            "metric": METRIC, "value": world * dofs / (mix * 1e-3), "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mix, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 residual/Newton",
+            "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "instances": len(probs) * world, "fine_dofs_per_step": dofs,
+                       "precision": "mixed", "l2": "flushed between steps (512 MB write outside the timed events)",
+                       "parallelism": f"independent batches x{world}"},
+            "fp64": {"value": world * dofs / (f64 * 1e-3), "unit": "DOF/s", "ms_per_step": f64,
+                     "speedup_mixed_over_fp64": f64 / mix},
+            "one_at_a_time": {"mixed_ms": seq["mixed"], "fp64_ms": seq["fp64"],
+                              "batch_speedup_mixed": seq["mixed"] / mix},
+            "accuracy": {"max_rel_l2_diff_mixed_fp64": worst,
+                         "flags": res["mixed"]["flags"] | res["fp64"]["flags"]},
+            "setup_s": {p: res[p]["setup_s"] for p in ("mixed", "fp64")},
+            "gpu_launches": launches * args.steps, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    for prec in ("mixed", "fp64"):
+        res[prec]["batch"].close()
+        for s in res[prec]["solvers"]:
+            s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def single_solve(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_05677_gb300 import fmg, workloads as W
+
+    prob = W.config_large_2d(refinements=args.refinements)
+    s = fmg.Solver(fmg.make_params(prob, precision=args.precision), prob.g_nodal())
+    st = fmg.fmg_stats()
+    s.solve(stats=st)
+    torch.cuda.synchronize()
+    print(json.dumps({"single_solve": prob.name, "precision": args.precision,
+                      "newton_iters": list(st.newton_iters[:prob.levels]), "flags": int(st.flags)}))
+    s.close()
+
+
 def main():
     args = parse()
+    if args.single_solve:
+        single_solve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

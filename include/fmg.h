@@ -146,9 +146,25 @@ fmg_status fmg_solve(fmg_ctx* c, double* u_out, int out_on_device, fmg_stats* st
  * solves (and fills st when non-NULL). */
 fmg_status fmg_sync(fmg_ctx* c, fmg_stats* st);
 
-/* Solves several independent problems (contexts created on the same device), each with
- * its own u_out (device pointers), ordered on the first context's stream. */
+/* Solves several independent problems (contexts created on the same device) at once, each
+ * with its own u_out (device pointers, or NULL entries / NULL array to leave the results in
+ * the contexts); a one-shot fmg_batch (below) ordered on the first context's stream.  Waits
+ * for the work; sts (count entries) receives each instance's statistics when non-NULL. */
 fmg_status fmg_solve_batch(fmg_ctx** cs, int count, double** u_outs, fmg_stats* sts);
+
+/* A reusable batch: one CUDA graph in which every instance's whole Algorithm 3.2 schedule is
+ * an independent branch on a stream of its own, so their work overlaps on the device.  The
+ * instances' augmented-space Newton kernels run on thread-block clusters (hardware barriers,
+ * no cooperative launch), which many instances can run concurrently.  The contexts must stay
+ * alive and must not be solved on their own while a batch solve is running; their results
+ * are at fmg_solution(ctx).  stream: the launch stream (NULL: one the batch creates). */
+typedef struct fmg_batch fmg_batch;
+fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** out);
+/* Launches the batch graph (after work already queued on the contexts' own streams).  With
+ * sts == NULL it returns at once; otherwise it waits and fills count fmg_stats. */
+fmg_status fmg_batch_solve(fmg_batch* b, fmg_stats* sts);
+fmg_status fmg_batch_sync(fmg_batch* b);
+fmg_status fmg_batch_destroy(fmg_batch* b);
 
 /* Frees the context (and the workspace when the library allocated it).  NULL-safe. */
 fmg_status fmg_destroy(fmg_ctx* c);

@@ -39,6 +39,7 @@ struct fmg_ctx {
   cudaGraphExec_t gexec = nullptr;
   unsigned pending_flags = 0;
   int graph_kernels = 0;
+  int cluster_aug = 0;   // > 0 while a batch graph is captured: cluster-variant Newton kernel
   // kernel timing (diagnostics): event pairs recorded inside the captured graph
   bool timing = false;
   struct Timed {
@@ -48,6 +49,16 @@ struct fmg_ctx {
   std::vector<Timed> timed;
   size_t timed_next = 0;
   std::string err;
+};
+
+struct fmg_batch {
+  std::vector<fmg_ctx*> cs;
+  cudaStream_t launch = nullptr;
+  bool own_launch = false;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -183,10 +194,16 @@ cudaError_t tend(fmg_ctx* c, int slot) {
   return cudaEventRecordWithFlags(c->timed[slot].e1, c->stream, cudaEventRecordExternal);
 }
 
-#define TRY(expr)                                 \
+// The schedule's launch calls: on failure the call's text is kept (per thread) so that a
+// capture error can name the launch that failed.
+thread_local const char* t_site = nullptr;
+#define TRY(...)                                  \
   do {                                            \
-    cudaError_t e_ = (expr);                      \
-    if (e_ != cudaSuccess) return e_;             \
+    cudaError_t e_ = (__VA_ARGS__);               \
+    if (e_ != cudaSuccess) {                      \
+      t_site = #__VA_ARGS__;                      \
+      return e_;                                  \
+    }                                             \
   } while (0)
 
 // ------------------------------------------------------------------ schedule pieces
@@ -204,27 +221,30 @@ int coarse_cycle_top(const fmg_ctx* c) {
 cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
-  cudaError_t e;
-  if (j == 1) return launch_coarse_solve_f64(dim, c->geo[0], c->Ainv, b, u, s);
-  if (j <= coarse_cycle_top<double>(c))
-    return launch_coarse_cycle<double>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s);
+  if (j == 1) {
+    TRY(launch_coarse_solve_f64(dim, c->geo[0], c->Ainv, b, u, s));
+    return cudaSuccess;
+  }
+  if (j <= coarse_cycle_top<double>(c)) {
+    TRY(launch_coarse_cycle<double>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s));
+    return cudaSuccess;
+  }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
   for (int it = 0; it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    if ((e = launch_rbgs<double>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
-    if ((e = launch_rbgs<double>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+    TRY(launch_rbgs<double>(dim, gf, u, b, 0, s));
+    TRY(launch_rbgs<double>(dim, gf, u, b, 1, s));
     TRY(tend(c, slot));
   }
-  if ((e = launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s)) != cudaSuccess)
-    return e;
-  if ((e = vcycle(c, j - 1, c->u[j - 2], c->b[j - 2])) != cudaSuccess) return e;
-  if ((e = launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s)) != cudaSuccess) return e;
+  TRY(launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s));
+  TRY(vcycle(c, j - 1, c->u[j - 2], c->b[j - 2]));
+  TRY(launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s));
   for (int it = 0; it < c->p.nu_post; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    if ((e = launch_rbgs<double>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
-    if ((e = launch_rbgs<double>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+    TRY(launch_rbgs<double>(dim, gf, u, b, 1, s));
+    TRY(launch_rbgs<double>(dim, gf, u, b, 0, s));
     TRY(tend(c, slot));
   }
   return cudaSuccess;
@@ -237,11 +257,15 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
 cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
-  if (j == 1) return launch_coarse_solve_f32(dim, c->geo[0], c->Ainv, c->b32[0], c->u32[0], s);
+  if (j == 1) {
+    TRY(launch_coarse_solve_f32(dim, c->geo[0], c->Ainv, c->b32[0], c->u32[0], s));
+    return cudaSuccess;
+  }
   if (j <= coarse_cycle_top<float>(c)) {
     TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, c->u32[j - 1], c->b32[j - 1], c->p.nu_pre,
                                    c->p.nu_post, c->Ainv, s));
-    return u64_top ? launch_add_f32(c->geo[j - 1], dim, u64_top, c->u32[j - 1], s) : cudaSuccess;
+    if (u64_top) TRY(launch_add_f32(c->geo[j - 1], dim, u64_top, c->u32[j - 1], s));
+    return cudaSuccess;
   }
   const LevelGeo gf = c->geo[j - 1];
   int slot = -1;
@@ -259,30 +283,32 @@ cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
 cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
-  cudaError_t e;
   float* u = c->u32[j - 1];
   const float* b = c->b32[j - 1];
-  if (j == 1) return launch_coarse_solve_f32(dim, c->geo[0], c->Ainv, b, u, s);
-  if (j <= coarse_cycle_top<float>(c))
-    return launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s);
+  if (j == 1) {
+    TRY(launch_coarse_solve_f32(dim, c->geo[0], c->Ainv, b, u, s));
+    return cudaSuccess;
+  }
+  if (j <= coarse_cycle_top<float>(c)) {
+    TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s));
+    return cudaSuccess;
+  }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
   for (int it = 0; it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    if ((e = launch_rbgs<float>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
-    if ((e = launch_rbgs<float>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
+    TRY(launch_rbgs<float>(dim, gf, u, b, 0, s));
+    TRY(launch_rbgs<float>(dim, gf, u, b, 1, s));
     TRY(tend(c, slot));
   }
-  if ((e = launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s)) !=
-      cudaSuccess)
-    return e;
-  if ((e = vcycle32(c, j - 1)) != cudaSuccess) return e;
-  if ((e = launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s)) != cudaSuccess) return e;
+  TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s));
+  TRY(vcycle32(c, j - 1));
+  TRY(launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s));
   for (int it = 0; it < c->p.nu_post; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    if ((e = launch_rbgs<float>(dim, gf, u, b, 1, s)) != cudaSuccess) return e;
-    if ((e = launch_rbgs<float>(dim, gf, u, b, 0, s)) != cudaSuccess) return e;
+    TRY(launch_rbgs<float>(dim, gf, u, b, 1, s));
+    TRY(launch_rbgs<float>(dim, gf, u, b, 0, s));
     TRY(tend(c, slot));
   }
   return cudaSuccess;
@@ -291,52 +317,44 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
 // One multigrid cycle for A_k u = b at the top level k, in the context's precision.
 cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
   if (c->p.precision == FMG_PREC_FP64 || k == 1) return vcycle(c, k, u, b, true);
-  cudaError_t e;
   const LevelGeo g = c->geo[k - 1];
   // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update
-  if ((e = launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream)) != cudaSuccess)
-    return e;
+  TRY(launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream));
   if (c->u32b[k - 1]) return vcycle32_fused(c, k, u);
-  if ((e = vcycle32(c, k, true)) != cudaSuccess) return e;
-  return launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream);
+  TRY(vcycle32(c, k, true));
+  TRY(launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream));
+  return cudaSuccess;
 }
 
 // Algorithm 3.1 at level k >= 2 on the level-k array u.
 cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
-  cudaError_t e;
   const LevelGeo g = c->geo[k - 1];
   int slot_step = -1, slot_aug = -1;
   TRY(tbegin(c, FMG_KT_CORRECTION, k, &slot_step));
   // step 1: b = (g, v) - (f(x, u^{(l)}), v)   (eq. 3.4)
-  if ((e = launch_nonlinear_rhs(c->p.dim, g, u, c->g[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream)) !=
-      cudaSuccess)
-    return e;
-  for (int i = 0; i < c->p.m_vcycles; ++i)
-    if ((e = top_cycle(c, k, u, c->b[k - 1])) != cudaSuccess) return e;
+  TRY(launch_nonlinear_rhs(c->p.dim, g, u, c->g[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream));
+  for (int i = 0; i < c->p.m_vcycles; ++i) TRY(top_cycle(c, k, u, c->b[k - 1]));
   // step 2: semilinear problem on V_H + span{u~}  (eq. 3.6)
   TRY(tbegin(c, FMG_KT_AUGMENTED, k, &slot_aug));
   TRY(launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->g[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
-                       c->p.newton_maxit, c->p.precision == FMG_PREC_MIXED, c->ab, c->st, k - 1, c->stream));
+                       c->p.newton_maxit, c->p.precision == FMG_PREC_MIXED, c->ab, c->st, k - 1, c->stream,
+                       c->cluster_aug));
   TRY(tend(c, slot_aug));
   return tend(c, slot_step);
 }
 
 cudaError_t run_fmg(fmg_ctx* c) {
-  cudaError_t e;
   c->timed_next = 0;
   // per-solve statistics start at zero (flags, iteration counts, alphas)
-  if ((e = cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream)) != cudaSuccess) return e;
-  if ((e = launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
-                                c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream)) !=
-      cudaSuccess)
-    return e;
+  TRY(cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  TRY(launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
+                           c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream));
   for (int k = 2; k <= c->nlev; ++k) {
     // u^{(0)}_{h_k} = u_{h_{k-1}}: the natural inclusion
-    if ((e = launch_prolong<double, double>(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], 0,
-                                            c->stream)) != cudaSuccess)
-      return e;
+    TRY(launch_prolong<double, double>(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], 0,
+                                       c->stream));
     for (int l = 0; l < c->p.p_corrections; ++l)
-      if ((e = correction_step(c, k, c->u[k - 1])) != cudaSuccess) return e;
+      TRY(correction_step(c, k, c->u[k - 1]));
   }
   return cudaSuccess;
 }
@@ -492,14 +510,15 @@ fmg_status fmg_set_rhs(fmg_ctx* c, const double* g_fine, int g_on_device) {
 fmg_status fmg_solve(fmg_ctx* c, double* u_out, int out_on_device, fmg_stats* st) {
   if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
   if (!c->gexec) {
+    t_site = nullptr;
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = run_fmg(c);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
-      return fail(c, FMG_ERR_CUDA,
-                  std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+      return fail(c, FMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2) +
+                                       (t_site ? std::string(" at ") + t_site : std::string()));
     }
     size_t nn = 0;
     c->graph_kernels = 0;
@@ -534,17 +553,151 @@ fmg_status fmg_sync(fmg_ctx* c, fmg_stats* st) {
 }
 
 fmg_status fmg_solve_batch(fmg_ctx** cs, int count, double** u_outs, fmg_stats* sts) {
-  if (!cs || count < 0) return fail(nullptr, FMG_ERR_INVALID, "bad batch arguments");
-  for (int i = 0; i < count; ++i) {
-    fmg_status s = fmg_solve(cs[i], u_outs ? u_outs[i] : nullptr, 1, nullptr);
-    if (s != FMG_OK) return s;
+  if (!cs || count < 1) return fail(nullptr, FMG_ERR_INVALID, "bad batch arguments");
+  fmg_batch* b = nullptr;
+  fmg_status s = fmg_batch_create(cs, count, cs[0]->stream, &b);
+  if (s != FMG_OK) return s;
+  std::vector<fmg_stats> tmp(sts ? 0 : count);
+  s = fmg_batch_solve(b, sts ? sts : tmp.data());
+  if (s == FMG_OK && u_outs) {
+    for (int i = 0; i < count && s == FMG_OK; ++i) {
+      if (!u_outs[i]) continue;
+      const int top = cs[i]->nlev - 1;
+      cudaError_t e = cudaMemcpyAsync(u_outs[i], cs[i]->u[top], cs[i]->geo[top].nodes * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, b->launch);
+      if (e != cudaSuccess) s = fail(nullptr, FMG_ERR_CUDA, std::string("batch output: ") + cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(b->launch);
   }
-  fmg_status worst = FMG_OK;
+  fmg_batch_destroy(b);
+  return s;
+}
+
+fmg_status fmg_batch_destroy(fmg_batch* b) {
+  if (!b) return FMG_OK;
+  if (b->launch) cudaStreamSynchronize(b->launch);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  if (b->own_launch && b->launch) cudaStreamDestroy(b->launch);
+  delete b;
+  return FMG_OK;
+}
+
+fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** out) {
+  if (!out || !cs || count < 1) return fail(nullptr, FMG_ERR_INVALID, "bad batch arguments");
+  *out = nullptr;
+  int dev = -1;
   for (int i = 0; i < count; ++i) {
-    fmg_status s = read_state(cs[i], sts ? &sts[i] : nullptr, true);
-    if (s != FMG_OK && worst == FMG_OK) worst = s;
+    if (!cs[i]) return fail(nullptr, FMG_ERR_INVALID, "NULL context in batch");
+    if (dev < 0) dev = cs[i]->device;
+    if (cs[i]->device != dev) return fail(nullptr, FMG_ERR_INVALID, "batch contexts on different devices");
+  }
+  fmg_batch* b = new (std::nothrow) fmg_batch();
+  if (!b) return fail(nullptr, FMG_ERR_OOM, "host allocation failed");
+  b->cs.assign(cs, cs + count);
+  auto bail = [&](cudaError_t e, const std::string& what) {
+    fmg_batch_destroy(b);
+    return fail(nullptr, FMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  b->launch = (cudaStream_t)stream;
+  if (!b->launch) {
+    if ((e = cudaStreamCreateWithFlags(&b->launch, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+    b->own_launch = true;
+  }
+  b->streams.resize(count, nullptr);
+  b->events.resize(count + 1, nullptr);
+  for (int i = 0; i < count; ++i)
+    if ((e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+  for (int i = 0; i <= count; ++i)
+    if ((e = cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
+  // cluster size of each instance's Newton kernel (outside the capture)
+  std::vector<int> csz(count);
+  for (int i = 0; i < count; ++i) {
+    fmg_ctx* c = cs[i];
+    csz[i] = aug_cluster_size(c->p.dim, c->p.coarse_cells, c->p.precision == FMG_PREC_MIXED, c->ab.smem);
+    if (csz[i] < 1) {
+      fmg_batch_destroy(b);
+      return fail(nullptr, FMG_ERR_CUDA, "no usable thread-block cluster size for the batched Newton kernel");
+    }
+  }
+  // one graph: fork on the launch stream, every instance's whole schedule on its own stream, join
+  if ((e = cudaStreamBeginCapture(b->launch, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return bail(e, "begin capture");
+  t_site = nullptr;
+  int fail_at = -1;
+  cudaError_t ce = cudaEventRecord(b->events[count], b->launch);
+  for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+    fail_at = i;
+    fmg_ctx* c = cs[i];
+    ce = cudaStreamWaitEvent(b->streams[i], b->events[count], 0);
+    if (ce != cudaSuccess) break;
+    cudaStream_t saved = c->stream;
+    const bool timing = c->timing;
+    c->stream = b->streams[i];
+    c->cluster_aug = csz[i];
+    c->timing = false;   // the batch graph carries no per-kernel timing events
+    ce = run_fmg(c);
+    c->timing = timing;
+    c->cluster_aug = 0;
+    c->stream = saved;
+    if (ce == cudaSuccess) ce = cudaEventRecord(b->events[i], b->streams[i]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->launch, b->events[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->launch, &g);
+  if (ce != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bail(ce != cudaSuccess ? ce : e,
+                "batch capture (instance " + std::to_string(fail_at) + ")" +
+                    (t_site ? std::string(" at ") + t_site : std::string()));
+  }
+  b->graph = g;
+  if ((e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) return bail(e, "batch instantiate");
+  *out = b;
+  return FMG_OK;
+}
+
+fmg_status fmg_batch_solve(fmg_batch* b, fmg_stats* sts) {
+  if (!b) return fail(nullptr, FMG_ERR_INVALID, "batch is NULL");
+  // the instances' work waits for anything queued on their own streams before
+  for (fmg_ctx* c : b->cs) {
+    if (c->stream == b->launch) continue;
+    cudaEvent_t ev = b->events[0];
+    cudaError_t e = cudaEventRecord(ev, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->launch, ev, 0);
+    if (e != cudaSuccess) return fail(nullptr, FMG_ERR_CUDA, std::string("batch ordering: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, b->launch);
+  if (e != cudaSuccess) return fail(nullptr, FMG_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  // later work on the contexts' own streams sees the batch's results
+  const int n = (int)b->cs.size();
+  if ((e = cudaEventRecord(b->events[n], b->launch)) != cudaSuccess)
+    return fail(nullptr, FMG_ERR_CUDA, std::string("batch ordering: ") + cudaGetErrorString(e));
+  for (fmg_ctx* c : b->cs)
+    if (c->stream != b->launch && (e = cudaStreamWaitEvent(c->stream, b->events[n], 0)) != cudaSuccess)
+      return fail(nullptr, FMG_ERR_CUDA, std::string("batch ordering: ") + cudaGetErrorString(e));
+  if (!sts) return FMG_OK;
+  e = cudaStreamSynchronize(b->launch);
+  if (e != cudaSuccess) return fail(nullptr, FMG_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(e));
+  fmg_status worst = FMG_OK;
+  for (size_t i = 0; i < b->cs.size(); ++i) {
+    fmg_status s = read_state(b->cs[i], &sts[i], true);
+    if (s != FMG_OK && worst == FMG_OK) {
+      worst = s;
+      t_err = b->cs[i]->err;
+    }
   }
   return worst;
+}
+
+fmg_status fmg_batch_sync(fmg_batch* b) {
+  if (!b) return fail(nullptr, FMG_ERR_INVALID, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->launch);
+  if (e != cudaSuccess) return fail(nullptr, FMG_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(e));
+  return FMG_OK;
 }
 
 fmg_status fmg_set_kernel_timing(fmg_ctx* c, int on) {

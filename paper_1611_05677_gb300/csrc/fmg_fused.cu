@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kFB) k_post2_fused(const float* __restrict__ u
 
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return raise_dyn_smem((const void*)kernel, bytes);
 }
 
 }  // namespace

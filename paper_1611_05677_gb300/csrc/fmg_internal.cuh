@@ -178,9 +178,13 @@ struct AugBuffers {
 void aug_configure(int dim, int coarse_cells, AugBuffers* ab);
 int aug_nvals(int dim);
 // jac_f32: Jacobian moments in FP32 (residual stays FP64) -- the mixed-precision path.
+// cluster_size > 0: the thread-block-cluster variant (no cooperative launch; used when many
+// instances run concurrently), with that many CTAs; 0: the cooperative grid variant.
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
-                             DevState* st, int level_index, cudaStream_t s);
+                             DevState* st, int level_index, cudaStream_t s, int cluster_size = 0);
+// Largest usable cluster size (<= 16, <= number of coarse cells) for the cluster variant, 0 if none.
+int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem);
 
 // Fused FP32 cycle kernels of the mixed path (fmg_fused.cu): 2D, nu in {1, 2}.
 bool fused_cycle_supported(int dim, int nu_pre, int nu_post);
@@ -192,6 +196,11 @@ cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, co
                               float* u_out, double* u64_top, cudaStream_t s);
 
 // Sets the calling thread's error message (what fmg_last_error(NULL) returns).
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
+// (never lowers it: contexts of different sizes share the kernels, and a graph captured
+// for a larger one must keep launching after a smaller one was set up).
+cudaError_t raise_dyn_smem(const void* kernel, size_t bytes);
+
 void set_thread_error(const std::string& msg);
 
 }  // namespace fmg

@@ -30,6 +30,7 @@
 //
 // Reductions are deterministic: per-thread channel rows in shared memory, fixed-order block
 // sums, fixed-order sums over blocks and cells.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -1223,6 +1224,88 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
   fine_pass<D, JF32>(A, kUpdate, acc, cv, alpha_sh, cell, bic);
 }
 
+// The same Newton iteration for one instance on a thread-block cluster instead of a
+// cooperative grid: CTA r of the cluster takes coarse cells r, r + CS, ...; the hardware
+// cluster barrier replaces the grid barrier.  Clusters are co-scheduled by the hardware, so
+// many instances can run this kernel concurrently (batched solves) without the risk of two
+// partially resident cooperative grids waiting on each other.
+template <int D, bool JF32>
+__global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs A) {
+  using G = Aug<D, JF32>;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int CS = (int)cluster.num_blocks();
+  extern __shared__ double sm[];
+  double* acc = sm;
+  __shared__ double cv[G::NV];
+  __shared__ double alpha_sh;
+  __shared__ int stop;
+  const int tid = threadIdx.x;
+  const int ncell = (int)ipow(A.nc, D);
+  const int NH = (int)ipow(A.nc - 1, D);
+  const int NA = NH + 1;
+  using FT = typename std::conditional<JF32, float, double>::type;
+  double* cellsum = acc;
+  double* M = cellsum + (size_t)ncell * G::NVAL;
+  double* R = M + (size_t)NA * (NA + 1);
+  FT* L = reinterpret_cast<FT*>(R + NA + 1);
+  auto vertex_offset = [&](int cell, int v) {
+    long long off = 0, mul = 1;
+    int t = cell;
+    for (int q = 0; q < D; ++q) {
+      off += (long long)(t % A.nc + ((v >> q) & 1)) * mul;
+      t /= A.nc;
+      mul *= (A.nc + 1);
+    }
+    return off;
+  };
+  if (rank == 0) {
+    const long long cn = ipow(A.nc + 1, D);
+    for (long long i = tid; i < cn; i += blockDim.x) A.c[i] = 0.0;
+    if (tid == 0) {
+      A.st->alpha_cur = 1.0;
+      A.st->converged = 0;
+    }
+  }
+  int it = 0;
+  for (it = 1; it <= A.maxit; ++it) {
+    const bool first = it == 1;
+    if (tid == 0) {
+      alpha_sh = first ? 1.0 : ((volatile double*)&A.st->alpha_cur)[0];
+      stop = ((volatile int*)&A.st->abort)[0];
+    }
+    __syncthreads();
+    if (stop) break;
+    for (int cell = rank; cell < ncell; cell += CS) {
+      if (tid < G::NV) cv[tid] = first ? 0.0 : __ldcg(&A.c[vertex_offset(cell, tid)]);
+      for (int v = 0; v < G::NVAL; ++v) acc[v * G::NT + tid] = 0.0;
+      __syncthreads();
+      fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, 0);
+      block_reduce_rows<D, JF32>(acc, A.partials + (long long)cell * G::NVAL, first);
+    }
+    cluster.sync();
+    if (rank == 0) newton_step<D, JF32>(A, cellsum, M, R, L, alpha_sh, first);
+    cluster.sync();
+    if (tid == 0) stop = ((volatile int*)&A.st->converged)[0] | ((volatile int*)&A.st->abort)[0];
+    __syncthreads();
+    if (stop) break;
+  }
+  if (rank == 0 && tid == 0) {
+    const int conv = ((volatile int*)&A.st->converged)[0];
+    if (!conv) atomicOr(&A.st->flags, kFlagNewtonCap);
+    A.st->newton_iters[A.level_index] += it > A.maxit ? A.maxit : it;
+    A.st->alpha[A.level_index] = ((volatile double*)&A.st->alpha_cur)[0];
+  }
+  if (tid == 0) alpha_sh = ((volatile double*)&A.st->alpha_cur)[0];
+  for (int cell = rank; cell < ncell; cell += CS) {
+    if (tid < G::NV) cv[tid] = __ldcg(&A.c[vertex_offset(cell, tid)]);
+    __syncthreads();
+    fine_pass<D, JF32>(A, kUpdate, acc, cv, alpha_sh, cell, 0);
+    __syncthreads();
+  }
+}
+
 template <int D, bool JF32>
 size_t aug_smem(int nc) {
   using G = Aug<D, JF32>;
@@ -1238,7 +1321,7 @@ template <int D, bool JF32>
 int aug_occupancy(int nc, size_t* smem_out) {
   const size_t smem = aug_smem<D, JF32>(nc);
   int occ = 0;
-  cudaFuncSetAttribute(k_augmented<D, JF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_dyn_smem((const void*)k_augmented<D, JF32>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_augmented<D, JF32>, Aug<D, JF32>::NT, smem);
   *smem_out = smem;
   return occ;
@@ -1252,7 +1335,7 @@ cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* 
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
   const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 3 * N + 4);
-  cudaError_t e = cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_dyn_smem((const void*)k_coarse_inverse, smem);
   if (e != cudaSuccess) return e;
   k_coarse_inverse<<<1, 64, smem, s>>>(dim, g1.n, Ainv, st);
   return cudaGetLastError();
@@ -1265,15 +1348,11 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
   cudaError_t e;
   if (f32_factor) {
     const size_t smem = sizeof(double) * (3 * N + 2) + sizeof(float) * (N * (N + 1) + 2 * N + 4);
-    if ((e = cudaFuncSetAttribute(k_level1_newton<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-      return e;
+    if ((e = raise_dyn_smem((const void*)k_level1_newton<float>, smem)) != cudaSuccess) return e;
     k_level1_newton<float><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
   } else {
     const size_t smem = sizeof(double) * (3 * N + 2 + N * (N + 1) + 2 * N + 4);
-    if ((e = cudaFuncSetAttribute(k_level1_newton<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-      return e;
+    if ((e = raise_dyn_smem((const void*)k_level1_newton<double>, smem)) != cudaSuccess) return e;
     k_level1_newton<double><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
   }
   return cudaGetLastError();
@@ -1307,9 +1386,39 @@ void aug_configure(int dim, int coarse_cells, AugBuffers* ab) {
   ab->partial_items = (size_t)ncell * (bpc > 0 ? bpc : 1);
 }
 
+template <int D, bool JF32>
+int cluster_size_for(int ncell, size_t smem) {
+  const int nt = Aug<D, JF32>::NT;
+  raise_dyn_smem((const void*)k_augmented_cluster<D, JF32>, smem);
+  cudaFuncSetAttribute(k_augmented_cluster<D, JF32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int cs = ncell < 16 ? ncell : 16; cs >= 1; cs >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_augmented_cluster<D, JF32>, &cfg) == cudaSuccess && n > 0) return cs;
+  }
+  cudaGetLastError();
+  return 0;
+}
+
+int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem) {
+  const int ncell = (int)ipow(coarse_cells, dim);
+  if (dim == 2) return jac_f32 ? cluster_size_for<2, true>(ncell, smem) : cluster_size_for<2, false>(ncell, smem);
+  return jac_f32 ? cluster_size_for<3, true>(ncell, smem) : cluster_size_for<3, false>(ncell, smem);
+}
+
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
-                             DevState* st, int level_index, cudaStream_t s) {
+                             DevState* st, int level_index, cudaStream_t s, int cluster_size) {
   const size_t smem = ab.smem;
   const int nt = ab.nt;
   if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
@@ -1348,6 +1457,27 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   // barrier words and abort/converged flags start cleared
   cudaError_t e = cudaMemsetAsync(&st->bar_count, 0, 4 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
+  if (cluster_size > 0) {
+    A.bpc = 1;
+    cudaLaunchConfig_t cc = {};
+    cc.gridDim = dim3(cluster_size);
+    cc.blockDim = dim3(nt);
+    cc.dynamicSmemBytes = smem;
+    cc.stream = s;
+    cudaLaunchAttribute ca[1];
+    ca[0].id = cudaLaunchAttributeClusterDimension;
+    ca[0].val.clusterDim.x = cluster_size;
+    ca[0].val.clusterDim.y = 1;
+    ca[0].val.clusterDim.z = 1;
+    cc.attrs = ca;
+    cc.numAttrs = 1;
+    if (dim == 2) {
+      if (jac_f32) return cudaLaunchKernelEx(&cc, k_augmented_cluster<2, true>, A);
+      return cudaLaunchKernelEx(&cc, k_augmented_cluster<2, false>, A);
+    }
+    if (jac_f32) return cudaLaunchKernelEx(&cc, k_augmented_cluster<3, true>, A);
+    return cudaLaunchKernelEx(&cc, k_augmented_cluster<3, false>, A);
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ncell * bpc);
   cfg.blockDim = dim3(nt);

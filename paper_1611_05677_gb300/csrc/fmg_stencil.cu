@@ -12,6 +12,10 @@
 // Red-black Gauss-Seidel: red nodes have i+j[+l] even.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "fmg_internal.cuh"
 
 namespace fmg {
@@ -537,14 +541,10 @@ cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int
   const size_t smem = coarse_cycle_smem<T>(dim, n0, jtop);
   cudaError_t e;
   if (dim == 2) {
-    if ((e = cudaFuncSetAttribute(k_vcycle_coarse<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-      return e;
+    if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 2>, smem)) != cudaSuccess) return e;
     k_vcycle_coarse<T, 2><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv);
   } else {
-    if ((e = cudaFuncSetAttribute(k_vcycle_coarse<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-      return e;
+    if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 3>, smem)) != cudaSuccess) return e;
     k_vcycle_coarse<T, 3><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv);
   }
   return cudaGetLastError();
@@ -565,5 +565,23 @@ template cudaError_t launch_residual_restrict<float, float>(int, LevelGeo, const
 template cudaError_t launch_prolong<double, double>(int, LevelGeo, const double*, LevelGeo, double*, int,
                                                     cudaStream_t);
 template cudaError_t launch_prolong<float, float>(int, LevelGeo, const float*, LevelGeo, float*, int, cudaStream_t);
+
+}  // namespace fmg
+
+namespace fmg {
+
+cudaError_t raise_dyn_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[std::make_pair(dev, kernel)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 }  // namespace fmg

@@ -53,7 +53,8 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
            "fmg_solve_batch", "fmg_destroy", "fmg_last_error", "fmg_solution", "fmg_levels", "fmg_level_cells",
            "fmg_op_smooth", "fmg_op_smooth_f32", "fmg_op_residual", "fmg_op_vcycle", "fmg_op_correction_step",
            "fmg_op_level1_solve", "fmg_op_prolong", "fmg_set_kernel_timing", "fmg_kernel_time",
-           "fmg_graph_kernels", "fmg_vcycle_noalloc")
+           "fmg_graph_kernels", "fmg_vcycle_noalloc", "fmg_batch_create", "fmg_batch_solve", "fmg_batch_sync",
+           "fmg_batch_destroy")
 KT_AUGMENTED = 0
 KT_SMOOTH_TOP = 1
 KT_CORRECTION = 2
@@ -100,6 +101,10 @@ def load():
         "fmg_kernel_time": (c_int, [c_void_p, c_int, c_int, POINTER(c_double), POINTER(c_int)]),
         "fmg_graph_kernels": (c_int, [c_void_p]),
         "fmg_vcycle_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+        "fmg_batch_create": (c_int, [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]),
+        "fmg_batch_solve": (c_int, [c_void_p, S]),
+        "fmg_batch_sync": (c_int, [c_void_p]),
+        "fmg_batch_destroy": (c_int, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -269,6 +274,27 @@ def fmg_vcycle_noalloc(dim, coarse_cells, level, b, u, cycles=1, nu_pre=2, nu_po
     _check(load().fmg_vcycle_noalloc(dim, coarse_cells, level, _ptr(b)[0], _ptr(u)[0], cycles, nu_pre, nu_post, sp))
 
 
+def fmg_batch_create(ctxs, stream=None):
+    arr = (c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    out = c_void_p()
+    _check(load().fmg_batch_create(arr, len(ctxs), getattr(stream, "cuda_stream", stream), byref(out)))
+    return out
+
+
+def fmg_batch_solve(batch, stats=None):
+    """Launches the batch; with stats (an array of fmg_stats, e.g. (fmg_stats * n)()) it waits."""
+    _check(load().fmg_batch_solve(batch, stats))
+
+
+def fmg_batch_sync(batch):
+    _check(load().fmg_batch_sync(batch))
+
+
+def fmg_batch_destroy(batch):
+    if batch is not None and batch.value:
+        load().fmg_batch_destroy(batch)
+
+
 # ---------------------------------------------------------------------------- convenience
 
 def make_params(problem=None, **kw) -> fmg_params:
@@ -339,10 +365,55 @@ class Solver:
             g_fine = np.ascontiguousarray(g_fine, dtype=np.float64)
         fmg_set_rhs(self.ctx, g_fine)
 
+    def solution(self):
+        """The context's fine-level result as a float64 view into its workspace (no copy)."""
+        import torch
+
+        off = fmg_solution(self.ctx) - self.workspace.data_ptr()
+        nbytes = 8 * int(np.prod(self.shape))
+        if off < 0 or off + nbytes > self.workspace.numel():
+            raise FMGError(FMG_ERR_INVALID, "solution does not lie in the workspace")
+        return self.workspace[off:off + nbytes].view(torch.float64).view(self.shape)
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             fmg_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Solver instances solved together: one CUDA graph with a branch per instance.
+
+    solve() launches it after the caller's current stream and orders the caller's
+    stream after it; results are each solver's solution().
+    """
+
+    def __init__(self, solvers, stream=None):
+        import torch
+
+        self.solvers = list(solvers)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.handle = fmg_batch_create([s.ctx for s in self.solvers], self.stream.cuda_stream)
+
+    def solve(self, wait: bool = False):
+        import torch
+
+        self.stream.wait_stream(torch.cuda.current_stream())
+        st = (fmg_stats * len(self.solvers))() if wait else None
+        fmg_batch_solve(self.handle, st)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return list(st) if wait else None
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            fmg_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:
