@@ -45,8 +45,13 @@ def parse():
     ap.add_argument("--single-solve", action="store_true",
                     help="build, create one solver and run one solve, then exit (for ncu captures)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="large2d", choices=["large2d", "batch"],
-                    help="large2d: the headline single-instance solve; batch: 256 independent instances")
+    ap.add_argument("--workload", default="large2d", choices=["large2d", "batch", "serve"],
+                    help="large2d: the headline single-instance solve; batch: 256 independent instances; "
+                         "serve: a Poisson request stream through the request server")
+    ap.add_argument("--serve-count", type=int, default=2200)
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--max-inflight", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
@@ -518,6 +523,126 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+SERVE_WORKLOAD = ("served: Poisson arrivals (mean 200 req/s), 70% 2D (refinements U{5..10} of H=1/4), 30% 3D "
+                  "(U{3..6} of H=1/4), u^3 or exp(u)-1, random-mode g; mixed precision; request server with "
+                  "continuous batching")
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    lo, hi = int(math.floor(k)), int(math.ceil(k))
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def run_serve(args):
+    """Open-loop serving: requests submitted at their Poisson arrival times; then the same
+    requests submitted at once (the server's capacity).  Host buffers are pinned; g fields come
+    from a pool of two seeded random-mode fields per shape (drawing a 16.8M-node field on the
+    host takes longer than the mean gap between requests)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    dist, world, rank, local = dist_setup(torch)
+    assert torch.cuda.is_available(), "the GPU arm needs a CUDA device"
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_1611_05677_gb300 import fmg, workloads as W
+
+    reqs = W.request_stream(seed=rank, count=args.serve_count, rate=args.serve_rate)
+    log("drawing g pool")
+    pool = {}
+    for _, p in reqs:
+        key = (p.dim, p.refinements)
+        lst = pool.setdefault(key, [])
+        if len(lst) < 2:
+            lst.append(torch.from_numpy(p.g_nodal()).pin_memory())
+    outs = {k: [torch.empty(v[0].shape, dtype=torch.float64).pin_memory() for _ in range(args.max_inflight + 2)]
+            for k, v in pool.items()}
+    params = [fmg.make_params(p, precision="mixed") for _, p in reqs]
+    server = fmg.Server(max_inflight=args.max_inflight)
+    rr = {k: 0 for k in pool}
+
+    def buffers(i):
+        p = reqs[i][1]
+        key = (p.dim, p.refinements)
+        j = rr[key]
+        rr[key] = (j + 1) % len(outs[key])
+        return pool[key][i % len(pool[key])], outs[key][j]
+
+    def collect(into):
+        while True:
+            rs = server.poll(256)
+            if not rs:
+                return
+            for r in rs:
+                into[r.ticket] = r
+
+    # ---- open loop at the arrival times
+    log("open loop")
+    done = {}
+    tickets = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i, (t_arr, p) in enumerate(reqs):
+            while True:
+                dt = t0 + t_arr - time.perf_counter()
+                if dt <= 0:
+                    break
+                collect(done)
+                time.sleep(min(dt, 0.0005))
+            g, u = buffers(i)
+            tickets.append(server.submit(params[i], g, u))
+        server.drain(600.0)
+        t_end = time.perf_counter()
+        collect(done)
+        # ---- closed loop: everything at once (capacity)
+        log("burst")
+        burst = {}
+        tb0 = time.perf_counter()
+        btickets = []
+        for i in range(args.serve_warmup, len(reqs)):
+            g, u = buffers(i)
+            btickets.append(server.submit(params[i], g, u))
+        server.drain(600.0)
+        tb1 = time.perf_counter()
+        collect(burst)
+    info = server.info()
+    measured = range(args.serve_warmup, len(reqs))
+    lat = [done[tickets[i]].latency_ms for i in measured]
+    que = [done[tickets[i]].queue_ms for i in measured]
+    bad = sum(1 for t in tickets if done[t].status != fmg.FMG_OK) + sum(
+        1 for t in btickets if burst[t].status != fmg.FMG_OK)
+    dofs = sum(reqs[i][1].fine_dofs for i in measured)
+    span = t_end - (t0 + reqs[args.serve_warmup][0])
+    server.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * dofs / span, "unit": "DOF/s", "n_gpus": world,
+            "steps": len(measured), "warmup": args.serve_warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 residual/Newton", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "requests": len(reqs), "measured": len(measured),
+                       "rate_per_s": args.serve_rate, "max_inflight": args.max_inflight,
+                       "g": "pool of 2 seeded random-mode fields per (dim, refinements)"},
+            "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99), "max": max(lat),
+                           "queue_p50": percentile(que, 0.5), "queue_p99": percentile(que, 0.99)},
+            "served_dofs_per_s_open_loop": dofs / span,
+            "offered_dofs_per_s": dofs / (reqs[-1][0] - reqs[args.serve_warmup][0]),
+            "capacity_dofs_per_s_burst": dofs / (tb1 - tb0),
+            "failed_requests": bad,
+            "server": {"contexts_created": info.contexts_created, "contexts_evicted": info.contexts_evicted,
+                       "bytes_held": info.bytes_held, "hbm_budget": info.hbm_budget},
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def single_solve(args):
     import torch
 
@@ -545,6 +670,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -268,6 +268,63 @@ int fmg_graph_kernels(const fmg_ctx* c);
 fmg_status fmg_vcycle_noalloc(int dim, int coarse_cells, int level, const double* b, double* u, int cycles,
                               int nu_pre, int nu_post, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Request server: continuous batching of independent solves on the current device.
+ *
+ * The paper solves one problem at a time; this is a serving layer over Algorithm 3.2.  A
+ * worker thread admits queued requests in arrival order as soon as one of max_inflight
+ * slots is free and the level hierarchy of the request fits the device memory budget
+ * (idle cached contexts of other shapes are destroyed, least recently used first, to make
+ * room).  Each admitted request runs on a context of its own shape: an idle cached one when
+ * there is one (its hierarchy and captured graph stay on the device between requests), else
+ * a new one.  Requests in flight overlap on the device; their augmented-space Newton kernels
+ * run on thread-block clusters, which any number of solves may run side by side.  A request
+ * gives the same bits whether it runs alone or among others.
+ * ------------------------------------------------------------------------------------- */
+typedef struct fmg_server fmg_server;
+
+typedef struct {
+  size_t hbm_budget;   /* device bytes the cached hierarchies may hold; 0 = 80% of the free
+                          memory at creation */
+  int max_inflight;    /* requests on the device at once, 1..64; 0 = 8 */
+  int poll_us;         /* worker's pause between completion polls while requests are in
+                          flight, microseconds; 0 = 20 */
+} fmg_server_config;
+
+typedef struct {
+  unsigned long long ticket;  /* as returned by fmg_server_submit */
+  fmg_status status;          /* FMG_ERR_OOM: the hierarchy alone exceeds the budget */
+  fmg_stats stats;
+  double queue_ms;            /* submit -> launch on the device (host clock) */
+  double latency_ms;          /* submit -> result in u_host (host clock) */
+} fmg_server_result;
+
+typedef struct {
+  size_t hbm_budget, bytes_held;
+  int contexts_cached, in_flight, queued;
+  size_t submitted, completed;
+  int contexts_created, contexts_evicted;
+} fmg_server_info;
+
+/* Starts a server (and its worker thread) on the current device. */
+fmg_status fmg_server_create(const fmg_server_config* cfg, fmg_server** out);
+/* Queues one solve.  p as for fmg_create; g_host: nodal g on the finest mesh; u_host receives
+ * u_{h_n}.  Both are HOST buffers ((n_fine+1)^d doubles) that must stay valid until the
+ * request's result has been polled; pinned memory makes the copies asynchronous.  Returns at
+ * once; *ticket identifies the request. */
+fmg_status fmg_server_submit(fmg_server* s, const fmg_params* p, const double* g_host, double* u_host,
+                             unsigned long long* ticket);
+/* Moves up to max finished requests into out (completion order); returns how many. */
+int fmg_server_poll(fmg_server* s, fmg_server_result* out, int max);
+/* Waits until every submitted request has finished (results stay available to poll), at most
+ * timeout_s seconds (FMG_ERR_TIMEOUT). */
+fmg_status fmg_server_drain(fmg_server* s, double timeout_s);
+fmg_status fmg_server_get_info(fmg_server* s, fmg_server_info* info);
+/* Message of the calling thread's last server failure. */
+const char* fmg_server_last_error(void);
+/* Finishes the submitted requests, stops the worker and frees every cached hierarchy. */
+fmg_status fmg_server_destroy(fmg_server* s);
+
 #ifdef __cplusplus
 }
 #endif

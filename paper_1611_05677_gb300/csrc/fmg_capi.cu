@@ -39,7 +39,7 @@ struct fmg_ctx {
   cudaGraphExec_t gexec = nullptr;
   unsigned pending_flags = 0;
   int graph_kernels = 0;
-  int cluster_aug = 0;   // > 0 while a batch graph is captured: cluster-variant Newton kernel
+  int cluster_aug = 0;   // > 0: cluster-variant Newton kernel of that size (batches, the server)
   // kernel timing (diagnostics): event pairs recorded inside the captured graph
   bool timing = false;
   struct Timed {
@@ -359,12 +359,9 @@ cudaError_t run_fmg(fmg_ctx* c) {
   return cudaSuccess;
 }
 
-fmg_status read_state(fmg_ctx* c, fmg_stats* st, bool accumulate_pending) {
-  DevState h;
-  CK(c, cudaStreamSynchronize(c->stream));
-  CK(c, cudaMemcpy(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost));
-  unsigned flags = h.flags | (accumulate_pending ? c->pending_flags : 0u);
-  c->pending_flags = 0;
+// Statistics and status of one solve from a host copy of its DevState.
+fmg_status decode_state(fmg_ctx* c, const DevState& h, unsigned extra_flags, fmg_stats* st) {
+  const unsigned flags = h.flags | extra_flags;
   if (st) {
     std::memset(st, 0, sizeof(*st));
     st->levels = c->nlev;
@@ -382,6 +379,15 @@ fmg_status read_state(fmg_ctx* c, fmg_stats* st, bool accumulate_pending) {
   return FMG_OK;
 }
 
+fmg_status read_state(fmg_ctx* c, fmg_stats* st, bool accumulate_pending) {
+  DevState h;
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaMemcpy(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  const unsigned extra = accumulate_pending ? c->pending_flags : 0u;
+  c->pending_flags = 0;
+  return decode_state(c, h, extra, st);
+}
+
 fmg_status load_rhs(fmg_ctx* c, const double* g_fine, int on_device) {
   if (!g_fine) return fail(c, FMG_ERR_INVALID, "g is NULL");
   const int top = c->nlev - 1;
@@ -396,6 +402,41 @@ fmg_status load_rhs(fmg_ctx* c, const double* g_fine, int on_device) {
 fmg_status check_level(fmg_ctx* c, int level, int lo) {
   if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
   if (level < lo || level > c->nlev) return fail(c, FMG_ERR_INVALID, "level out of range");
+  return FMG_OK;
+}
+
+// Captures the whole schedule of Algorithm 3.2 into the context's graph (once).
+fmg_status ensure_graph(fmg_ctx* c) {
+  if (c->gexec) return FMG_OK;
+  {
+    t_site = nullptr;
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = run_fmg(c);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(c, FMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2) +
+                                       (t_site ? std::string(" at ") + t_site : std::string()));
+    }
+    size_t nn = 0;
+    c->graph_kernels = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c->graph_kernels;
+        }
+    }
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      c->gexec = nullptr;
+      return fail(c, FMG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    c->graph = graph;
+  }
   return FMG_OK;
 }
 
@@ -509,35 +550,7 @@ fmg_status fmg_set_rhs(fmg_ctx* c, const double* g_fine, int g_on_device) {
 
 fmg_status fmg_solve(fmg_ctx* c, double* u_out, int out_on_device, fmg_stats* st) {
   if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
-  if (!c->gexec) {
-    t_site = nullptr;
-    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = run_fmg(c);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return fail(c, FMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2) +
-                                       (t_site ? std::string(" at ") + t_site : std::string()));
-    }
-    size_t nn = 0;
-    c->graph_kernels = 0;
-    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
-      std::vector<cudaGraphNode_t> nodes(nn);
-      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
-        for (size_t i = 0; i < nn; ++i) {
-          cudaGraphNodeType t;
-          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c->graph_kernels;
-        }
-    }
-    e = cudaGraphInstantiate(&c->gexec, graph, 0);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      c->gexec = nullptr;
-      return fail(c, FMG_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-    }
-    c->graph = graph;
-  }
+  if (fmg_status s = ensure_graph(c)) return s;
   CK(c, cudaGraphLaunch(c->gexec, c->stream));
   const int top = c->nlev - 1;
   if (u_out)
@@ -636,12 +649,13 @@ fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** o
     if (ce != cudaSuccess) break;
     cudaStream_t saved = c->stream;
     const bool timing = c->timing;
+    const int cluster = c->cluster_aug;
     c->stream = b->streams[i];
     c->cluster_aug = csz[i];
     c->timing = false;   // the batch graph carries no per-kernel timing events
     ce = run_fmg(c);
     c->timing = timing;
-    c->cluster_aug = 0;
+    c->cluster_aug = cluster;
     c->stream = saved;
     if (ce == cudaSuccess) ce = cudaEventRecord(b->events[i], b->streams[i]);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->launch, b->events[i], 0);
@@ -825,3 +839,43 @@ fmg_status fmg_op_prolong(fmg_ctx* c, int level, const double* u_coarse, double*
 }
 
 }  // extern "C"
+
+// ============================================================================ server services
+
+namespace fmg {
+
+cudaStream_t ctx_stream(const fmg_ctx* c) { return c->stream; }
+
+size_t ctx_bytes(const fmg_ctx* c) { return c->arena_bytes; }
+
+size_t ctx_fine_nodes(const fmg_ctx* c) { return (size_t)c->geo[c->nlev - 1].nodes; }
+
+fmg_status ctx_make_concurrent(fmg_ctx* c) {
+  const int cs = aug_cluster_size(c->p.dim, c->p.coarse_cells, c->p.precision == FMG_PREC_MIXED, c->ab.smem);
+  if (cs < 1) return fail(c, FMG_ERR_CUDA, "no usable thread-block cluster size for the Newton kernel");
+  if (cs != c->cluster_aug) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->cluster_aug = cs;
+  }
+  return FMG_OK;
+}
+
+fmg_status ctx_enqueue(fmg_ctx* c, const double* g_host, double* u_host, DevState* state_host) {
+  if (fmg_status s = load_rhs(c, g_host, 0)) return s;
+  if (fmg_status s = ensure_graph(c)) return s;
+  const int top = c->nlev - 1;
+  CK(c, cudaGraphLaunch(c->gexec, c->stream));
+  CK(c, cudaMemcpyAsync(u_host, c->u[top], c->geo[top].nodes * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(state_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  return FMG_OK;
+}
+
+fmg_status ctx_decode(fmg_ctx* c, const DevState& h, fmg_stats* st) { return decode_state(c, h, 0u, st); }
+
+const char* ctx_error(const fmg_ctx* c) { return c->err.c_str(); }
+
+}  // namespace fmg

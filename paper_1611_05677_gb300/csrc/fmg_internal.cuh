@@ -196,6 +196,19 @@ cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, co
                               float* u_out, double* u64_top, cudaStream_t s);
 
 // Sets the calling thread's error message (what fmg_last_error(NULL) returns).
+// Context services for the request server (fmg_capi.cu).
+cudaStream_t ctx_stream(const fmg_ctx* c);
+size_t ctx_bytes(const fmg_ctx* c);
+size_t ctx_fine_nodes(const fmg_ctx* c);
+// Switches the context to the cluster-variant Newton kernel, which any number of solves can
+// run concurrently (drops a graph captured with the cooperative kernel).
+fmg_status ctx_make_concurrent(fmg_ctx* c);
+// Queues on the context stream: g from host, the solve graph, u and the DevState to host.
+fmg_status ctx_enqueue(fmg_ctx* c, const double* g_host, double* u_host, DevState* state_host);
+// Status and statistics of a finished solve from its DevState.
+fmg_status ctx_decode(fmg_ctx* c, const DevState& h, fmg_stats* st);
+const char* ctx_error(const fmg_ctx* c);
+
 // Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
 // (never lowers it: contexts of different sizes share the kernels, and a graph captured
 // for a larger one must keep launching after a smaller one was set up).

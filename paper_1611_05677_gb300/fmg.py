@@ -42,6 +42,21 @@ class fmg_stats(ctypes.Structure):
                 ("alpha", c_double * 32), ("flags", c_uint)]
 
 
+class fmg_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", c_size_t), ("max_inflight", c_int), ("poll_us", c_int)]
+
+
+class fmg_server_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_ulonglong), ("status", c_int), ("stats", fmg_stats),
+                ("queue_ms", c_double), ("latency_ms", c_double)]
+
+
+class fmg_server_info(ctypes.Structure):
+    _fields_ = [("hbm_budget", c_size_t), ("bytes_held", c_size_t), ("contexts_cached", c_int),
+                ("in_flight", c_int), ("queued", c_int), ("submitted", c_size_t), ("completed", c_size_t),
+                ("contexts_created", c_int), ("contexts_evicted", c_int)]
+
+
 class FMGError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -54,7 +69,8 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
            "fmg_op_smooth", "fmg_op_smooth_f32", "fmg_op_residual", "fmg_op_vcycle", "fmg_op_correction_step",
            "fmg_op_level1_solve", "fmg_op_prolong", "fmg_set_kernel_timing", "fmg_kernel_time",
            "fmg_graph_kernels", "fmg_vcycle_noalloc", "fmg_batch_create", "fmg_batch_solve", "fmg_batch_sync",
-           "fmg_batch_destroy")
+           "fmg_batch_destroy", "fmg_server_create", "fmg_server_submit", "fmg_server_poll", "fmg_server_drain",
+           "fmg_server_get_info", "fmg_server_last_error", "fmg_server_destroy")
 KT_AUGMENTED = 0
 KT_SMOOTH_TOP = 1
 KT_CORRECTION = 2
@@ -105,6 +121,13 @@ def load():
         "fmg_batch_solve": (c_int, [c_void_p, S]),
         "fmg_batch_sync": (c_int, [c_void_p]),
         "fmg_batch_destroy": (c_int, [c_void_p]),
+        "fmg_server_create": (c_int, [POINTER(fmg_server_config), POINTER(c_void_p)]),
+        "fmg_server_submit": (c_int, [c_void_p, P, c_void_p, c_void_p, POINTER(ctypes.c_ulonglong)]),
+        "fmg_server_poll": (c_int, [c_void_p, POINTER(fmg_server_result), c_int]),
+        "fmg_server_drain": (c_int, [c_void_p, c_double]),
+        "fmg_server_get_info": (c_int, [c_void_p, POINTER(fmg_server_info)]),
+        "fmg_server_last_error": (c_char_p, []),
+        "fmg_server_destroy": (c_int, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -295,6 +318,56 @@ def fmg_batch_destroy(batch):
         load().fmg_batch_destroy(batch)
 
 
+def _check_server(status: int):
+    if status != FMG_OK:
+        msg = _lib.fmg_server_last_error()
+        raise FMGError(status, msg.decode() if msg else "")
+
+
+def fmg_server_last_error() -> str:
+    msg = load().fmg_server_last_error()
+    return msg.decode() if msg else ""
+
+
+def fmg_server_create(hbm_budget: int = 0, max_inflight: int = 0, poll_us: int = 0):
+    cfg = fmg_server_config(hbm_budget, max_inflight, poll_us)
+    out = c_void_p()
+    _check_server(load().fmg_server_create(byref(cfg), byref(out)))
+    return out
+
+
+def fmg_server_submit(server, params: fmg_params, g_host, u_host) -> int:
+    """Queues a solve; g_host and u_host are host arrays (numpy or CPU torch tensors)."""
+    gp, gdev = _ptr(g_host)
+    up, udev = _ptr(u_host)
+    if gdev or udev:
+        raise FMGError(FMG_ERR_INVALID, "the server takes host buffers")
+    t = ctypes.c_ulonglong()
+    _check_server(load().fmg_server_submit(server, byref(params), gp, up, byref(t)))
+    return t.value
+
+
+def fmg_server_poll(server, max_results: int = 64):
+    buf = (fmg_server_result * max_results)()
+    n = load().fmg_server_poll(server, buf, max_results)
+    return [buf[i] for i in range(n)]
+
+
+def fmg_server_drain(server, timeout_s: float = 600.0):
+    _check_server(load().fmg_server_drain(server, timeout_s))
+
+
+def fmg_server_get_info(server) -> fmg_server_info:
+    info = fmg_server_info()
+    _check_server(load().fmg_server_get_info(server, byref(info)))
+    return info
+
+
+def fmg_server_destroy(server):
+    if server is not None and server.value:
+        load().fmg_server_destroy(server)
+
+
 # ---------------------------------------------------------------------------- convenience
 
 def make_params(problem=None, **kw) -> fmg_params:
@@ -414,6 +487,46 @@ class Batch:
         if getattr(self, "handle", None) is not None:
             fmg_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request server over the C ABI: submit() queues a solve with host buffers, poll() returns
+    finished requests.  The buffers of a request are kept referenced until it is polled."""
+
+    def __init__(self, hbm_budget: int = 0, max_inflight: int = 0, poll_us: int = 0):
+        self.handle = fmg_server_create(hbm_budget, max_inflight, poll_us)
+        self._pending = {}
+
+    def submit(self, params: fmg_params, g_host, u_host) -> int:
+        if isinstance(g_host, np.ndarray):
+            g_host = np.ascontiguousarray(g_host, dtype=np.float64)
+        t = fmg_server_submit(self.handle, params, g_host, u_host)
+        self._pending[t] = (g_host, u_host)
+        return t
+
+    def poll(self, max_results: int = 64):
+        out = fmg_server_poll(self.handle, max_results)
+        for r in out:
+            self._pending.pop(r.ticket, None)
+        return out
+
+    def drain(self, timeout_s: float = 600.0):
+        fmg_server_drain(self.handle, timeout_s)
+
+    def info(self) -> fmg_server_info:
+        return fmg_server_get_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            fmg_server_destroy(self.handle)
+            self.handle = None
+            self._pending.clear()
 
     def __del__(self):
         try:

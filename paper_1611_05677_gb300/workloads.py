@@ -94,17 +94,26 @@ class Problem:
         # of the C-ordered array (x fastest).
         return [g.transpose(tuple(range(self.dim))[::-1]) for g in grids]
 
+    def _mode_sum(self, modes, n: int, weight=None) -> np.ndarray:
+        """Sum over modes of c * prod_ax sin(k_ax pi x_ax) on the nodal grid (x fastest).
+
+        Evaluated as outer products of 1D factors, multiplied in the order c, x, y[, z]."""
+        x = np.arange(n + 1, dtype=np.float64) / n
+        out = np.zeros((n + 1,) * self.dim)
+        for kv, c in modes:
+            amp = float(c) if weight is None else weight(kv, c)
+            t = amp * np.sin(kv[0] * math.pi * x)
+            for ax in range(1, self.dim):
+                s_ax = np.sin(kv[ax] * math.pi * x)
+                t = t[None, ...] * s_ax.reshape((-1,) + (1,) * t.ndim)
+            out += t
+        return out
+
     def u_star(self, n: int | None = None) -> np.ndarray | None:
         if self.modes is None:
             return None
-        xs = self.coords(n)
-        u = np.zeros_like(xs[0])
-        for kv, c in self.modes:
-            t = np.full_like(xs[0], float(c))
-            for ax in range(self.dim):
-                t = t * np.sin(kv[ax] * math.pi * xs[ax])
-            u += t
-        return u
+        n = self.n_fine if n is None else n
+        return self._mode_sum(self.modes, n)
 
     def grad_u_star(self, pts: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
         """u* and grad u* at points pts (M, dim); used for FE error norms."""
@@ -124,23 +133,14 @@ class Problem:
     def g_nodal(self, n: int | None = None) -> np.ndarray:
         """Nodal g on the (n+1)^d grid (boundary entries included, not used)."""
         n = self.n_fine if n is None else n
-        xs = self.coords(n)
         if self.modes is not None:
             # g = -Laplace(u*) + a f(u*) in closed form.
-            lap = np.zeros_like(xs[0])
-            for kv, c in self.modes:
-                t = np.full_like(xs[0], float(c) * math.pi ** 2 * float(sum(k * k for k in kv)))
-                for ax in range(self.dim):
-                    t = t * np.sin(kv[ax] * math.pi * xs[ax])
-                lap += t
+            lap = self._mode_sum(self.modes, n,
+                                 weight=lambda kv, c: float(c) * math.pi ** 2 * float(sum(k * k for k in kv)))
             return np.ascontiguousarray(lap + _f_problem(self.f, self.a, self.u_star(n)))
-        g = np.zeros_like(xs[0])
+        g = np.zeros((n + 1,) * self.dim)
         if self.g_modes is not None:
-            for kv, c in self.g_modes:
-                t = np.full_like(xs[0], float(c))
-                for ax in range(self.dim):
-                    t = t * np.sin(kv[ax] * math.pi * xs[ax])
-                g += t
+            g += self._mode_sum(self.g_modes, n)
         if self.g_const is not None:
             g += self.g_const
         return np.ascontiguousarray(g)
