@@ -194,14 +194,14 @@ cudaError_t tend(fmg_ctx* c, int slot) {
   return cudaEventRecordWithFlags(c->timed[slot].e1, c->stream, cudaEventRecordExternal);
 }
 
-// The schedule's launch calls: on failure the call's text is kept (per thread) so that a
-// capture error can name the launch that failed.
+// The schedule's launch calls: on failure the innermost call's text is kept (per thread) so
+// that a capture error can name the launch that failed.
 thread_local const char* t_site = nullptr;
 #define TRY(...)                                  \
   do {                                            \
     cudaError_t e_ = (__VA_ARGS__);               \
     if (e_ != cudaSuccess) {                      \
-      t_site = #__VA_ARGS__;                      \
+      if (!t_site) t_site = #__VA_ARGS__;         \
       return e_;                                  \
     }                                             \
   } while (0)

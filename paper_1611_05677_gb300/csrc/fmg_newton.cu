@@ -42,165 +42,111 @@ namespace fmg {
 namespace {
 
 // ------------------------------------------------------------------ small dense SPD solve
-// 1/sqrt(d) for d > 0: FP32 estimate refined by two Newton steps in FP64
-// (y <- y (3 - d y^2) / 2), accurate to a few ulp.
-__device__ __forceinline__ double rsqrt_refined(double d) {
-  double y = (double)rsqrtf((float)d);
-  y = y * (1.5 - 0.5 * d * y * y);
-  y = y * (1.5 - 0.5 * d * y * y);
-  return y;
+// 1/d for d > 0 from the fast FP32 reciprocal estimate (about 2 ulp), refined by Newton's
+// iteration for 1/d (y <- y (2 - d y)) in the target precision: one step for FP32, two for
+// FP64 (the error squares each step).
+__device__ __forceinline__ float recip_pivot(float d) {
+  const float y = __fdividef(1.0f, d);
+  return y * (2.0f - d * y);
+}
+__device__ __forceinline__ double recip_pivot(double d) {
+  double y = (double)__fdividef(1.0f, (float)d);
+  y = y * (2.0 - d * y);
+  return y * (2.0 - d * y);
 }
 
-__device__ __forceinline__ float rsqrt_refined(float d) {
-  float y = rsqrtf(d);
-  return y * (1.5f - 0.5f * d * y * y);
-}
-
-// Blocked Cholesky (lower, in place) of the n x n SPD matrix L (row-major, leading dimension
-// ld, shared memory, precision T), then the solve L L^T x = rhs (rhs FP64 in and out; the
-// substitutions run in T).  work and invd: n values of T in shared memory.  Block size 8:
-// each 8 x 8 diagonal block is factored by one warp in registers (row per lane, shuffles),
-// the panel below it and the trailing update run on the whole thread block, so there are
-// about n/8 barrier-separated steps instead of n.  If drop_last and the last pivot falls
-// below drop_tol times the original last diagonal entry, the last unknown is frozen
-// (increment 0) and *dropped = 1.  Returns false if the matrix is not SPD.  Every thread of
-// the block must call it.
-constexpr int kCB = 8;
-
-template <typename T>
-__device__ bool block_chol_solve(T* L, int n, int ld, double* rhs, T* work, T* invd, bool drop_last,
-                                 double drop_tol, int* dropped) {
+// LDL^T factorization (no pivoting) of the n x n SPD matrix A (n <= 64; row-major, leading
+// dimension ld, shared memory, precision T; only the lower triangle is read), in place: below
+// the diagonal A[i][k] keeps the k-th column of the reduced matrix (= L_ik d_k), and
+// rd[k] = 1/d_k.  Step k subtracts A_ik A_jk / d_k from every trailing entry (k < j <= i).
+// The entries of the trailing triangle are dealt to the NT threads through a table of
+// (row, column) offsets listed row by row, so that the triangle of any size m is the table's
+// first m(m+1)/2 entries and a thread touches only live entries.  The thread that updates
+// the next pivot also forms its reciprocal, so a step's critical path is one barrier, one
+// load of 1/d_k and one update.  If drop_last and the last pivot (the Schur complement of the
+// last unknown) falls below drop_tol times the original last diagonal entry, rd[n-1] = 0:
+// that unknown is frozen (*dropped = 1).  Returns false if a pivot is not positive.  Every
+// thread of the block (blockDim.x == NT) calls it.
+template <typename T, int NT>
+__device__ bool ldlt_factor(T* A, int n, int ld, T* rd, bool drop_last, double drop_tol, int* dropped) {
+  __shared__ unsigned short tri[63 * 64 / 2];
   __shared__ int bad_sh, drop_sh;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const T last0 = drop_last ? L[(n - 1) * ld + (n - 1)] : T(0);
+  const int tid = threadIdx.x;
+  for (int di = tid >> 5; di < 63; di += NT / 32)
+    for (int dj = tid & 31; dj <= di; dj += 32) tri[di * (di + 1) / 2 + dj] = (unsigned short)(di | (dj << 8));
+  const T last0 = drop_last ? A[(n - 1) * ld + (n - 1)] : T(0);
+  // pivot k's reciprocal, or 0 with the flags set (called by one thread per pivot)
+  auto pivot = [&](int k, T d) {
+    T r;
+    if (drop_last && k == n - 1 && !(d > T(drop_tol) * last0)) {
+      drop_sh = 1;
+      r = T(0);
+    } else if (!(d > T(0))) {
+      bad_sh = 1;
+      r = T(0);
+    } else {
+      r = recip_pivot(d);
+    }
+    rd[k] = r;
+  };
   if (tid == 0) {
     bad_sh = 0;
     drop_sh = 0;
+    pivot(0, A[0]);
   }
   __syncthreads();
-  for (int kb = 0; kb < n; kb += kCB) {
-    const int nb = min(kCB, n - kb);
-    // (1) diagonal block, warp 0: lane r holds row kb+r
-    if (warp == 0) {
-      T a[kCB];
-      const int r = lane;
-#pragma unroll
-      for (int c = 0; c < kCB; ++c) a[c] = (r < nb && c <= r) ? L[(kb + r) * ld + kb + c] : T(0);
-      bool bad = false, drop = false;
-#pragma unroll
-      for (int j = 0; j < kCB; ++j) {
-        if (j < nb) {
-          T d = __shfl_sync(0xffffffffu, a[j], j);
-          if (drop_last && kb + j == n - 1 && !(d > T(drop_tol) * last0)) {
-            drop = true;
-            d = T(1);
-          } else if (!(d > T(0))) {
-            bad = true;
-            d = T(1);
-          }
-          const T inv = rsqrt_refined(d);
-          if (r == j) a[j] = d * inv;
-          else if (r > j) a[j] *= inv;
-          if (lane == 0) invd[kb + j] = inv;
-#pragma unroll
-          for (int c = j + 1; c < kCB; ++c) {
-            const T lcj = __shfl_sync(0xffffffffu, a[j], c);
-            if (c < nb && r >= c && r < nb) a[c] -= a[j] * lcj;
-          }
-        }
-      }
-      if (r < nb)
-#pragma unroll
-        for (int c = 0; c < kCB; ++c)
-          if (c <= r) L[(kb + r) * ld + kb + c] = a[c];
-      if (lane == 0) {
-        if (bad) bad_sh = 1;
-        if (drop) drop_sh = 1;
-      }
-    }
-    __syncthreads();
-    // (2) panel rows below the block: x Lkk^T = L[i, kb:kb+nb]
-    for (int i = kb + nb + tid; i < n; i += nt) {
-      T x[kCB];
-#pragma unroll
-      for (int c = 0; c < kCB; ++c) x[c] = c < nb ? L[i * ld + kb + c] : T(0);
-#pragma unroll
-      for (int c = 0; c < kCB; ++c) {
-        if (c < nb) {
-          T s = x[c];
-#pragma unroll
-          for (int q = 0; q < c; ++q) s -= x[q] * L[(kb + c) * ld + kb + q];
-          x[c] = s * invd[kb + c];
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < kCB; ++c)
-        if (c < nb) L[i * ld + kb + c] = x[c];
-    }
-    __syncthreads();
-    // (3) trailing update of the lower triangle below/right of the block
-    const int W = n - kb - nb;
-    for (int t = tid; t < W * W; t += nt) {
-      const int i = kb + nb + t / W;
-      const int j = kb + nb + t % W;
-      if (j > i) continue;
-      T s = L[i * ld + j];
-#pragma unroll
-      for (int c = 0; c < kCB; ++c)
-        if (c < nb) s -= L[i * ld + kb + c] * L[j * ld + kb + c];
-      L[i * ld + j] = s;
+  for (int k = 0; k < n; ++k) {
+    const T r = rd[k];
+    const int m = n - k - 1, cnt = m * (m + 1) / 2;
+    T* trail = A + (size_t)(k + 1) * ld + (k + 1);   // trail[di * ld + dj] = A[k+1+di][k+1+dj]
+    const T* colk = A + (size_t)(k + 1) * ld + k;    // colk[di * ld] = A[k+1+di][k]
+    for (int t = tid; t < cnt; t += NT) {
+      const unsigned e = tri[t];
+      const int di = (int)(e & 255u), dj = (int)(e >> 8);
+      const T v = trail[di * ld + dj] - colk[di * ld] * r * colk[dj * ld];
+      trail[di * ld + dj] = v;
+      if (t == 0) pivot(k + 1, v);   // entry (0, 0) is the next pivot
     }
     __syncthreads();
   }
-  const bool drop = drop_sh != 0;
-  if (drop)
-    for (int j = tid; j < n - 1; j += nt) L[(n - 1) * ld + j] = T(0);
-  for (int i = tid; i < n; i += nt) work[i] = (drop && i == n - 1) ? T(0) : (T)rhs[i];
-  __syncthreads();
-  // forward L y = rhs, by blocks
-  for (int kb = 0; kb < n; kb += kCB) {
-    const int nb = min(kCB, n - kb);
-    if (tid == 0) {
-      for (int c = 0; c < nb; ++c) {
-        const T y = work[kb + c] * invd[kb + c];
-        work[kb + c] = y;
-        for (int q = c + 1; q < nb; ++q) work[kb + q] -= L[(kb + q) * ld + kb + c] * y;
-      }
-    }
-    __syncthreads();
-    for (int i = kb + nb + tid; i < n; i += nt) {
-      T s = work[i];
-      for (int c = 0; c < nb; ++c) s -= L[i * ld + kb + c] * work[kb + c];
-      work[i] = s;
-    }
-    __syncthreads();
+  if (dropped) *dropped = drop_sh;
+  return bad_sh == 0;
+}
+
+// Solves L D L^T x = b with the factor of ldlt_factor, on one warp (lane l holds entries l
+// and l + 32; n <= 64): forward substitution column by column, then the backward one row by
+// row, each step one shuffle and no barrier.  b (FP64, shared) is overwritten by x.  Only
+// the calling warp takes part; the caller synchronizes before others read b.
+template <typename T>
+__device__ void ldlt_solve_warp(const T* A, int n, int ld, const T* rd, double* b) {
+  const int lane = threadIdx.x & 31;
+  const int i0 = lane, i1 = lane + 32;
+  T z0 = i0 < n ? (T)b[i0] : T(0), z1 = i1 < n ? (T)b[i1] : T(0);
+  // forward: w_k = z_k / d_k, then z_i -= A_ik w_k for i > k
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    const T zk = __shfl_sync(0xffffffffu, k < 32 ? z0 : z1, k & 31);
+    const T wk = zk * rd[k];
+    if (i0 > k && i0 < n) z0 -= A[i0 * ld + k] * wk;
+    if (i1 > k && i1 < n) z1 -= A[i1 * ld + k] * wk;
+    if (i0 == k) z0 = wk;
+    if (i1 == k) z1 = wk;
   }
-  // backward L^T x = y, by blocks
-  for (int kb = ((n - 1) / kCB) * kCB; kb >= 0; kb -= kCB) {
-    const int nb = min(kCB, n - kb);
-    if (tid == 0) {
-      for (int c = nb - 1; c >= 0; --c) {
-        const T x = work[kb + c] * invd[kb + c];
-        work[kb + c] = x;
-        for (int q = 0; q < c; ++q) work[kb + q] -= L[(kb + c) * ld + kb + q] * x;
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < kb; i += nt) {
-      T s = work[i];
-      for (int c = 0; c < nb; ++c) s -= L[(kb + c) * ld + i] * work[kb + c];
-      work[i] = s;
-    }
-    __syncthreads();
+  // backward: x_k = w_k - (1/d_k) sum_{i>k} A_ik x_i, accumulated row by row
+  T s0 = T(0), s1 = T(0);
+#pragma unroll 4
+  for (int k = n - 1; k >= 0; --k) {
+    T xk = T(0);
+    if (i0 == k) xk = z0 - rd[k] * s0;
+    if (i1 == k) xk = z1 - rd[k] * s1;
+    xk = __shfl_sync(0xffffffffu, xk, k & 31);
+    if (i0 == k) z0 = xk;
+    if (i1 == k) z1 = xk;
+    if (i0 < k) s0 += A[k * ld + i0] * xk;
+    if (i1 < k) s1 += A[k * ld + i1] * xk;
   }
-  if (drop && tid == 0) work[n - 1] = T(0);
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) rhs[i] = (double)work[i];
-  if (dropped) *dropped = drop ? 1 : 0;
-  const bool ok = bad_sh == 0;
-  __syncthreads();
-  return ok;
+  if (i0 < n) b[i0] = (double)z0;
+  if (i1 < n) b[i1] = (double)z1;
 }
 
 // Level-1 unknown r <-> nodal offset of interior node (r % m + 1, (r/m) % m + 1, r/m^2 + 1).
@@ -234,37 +180,34 @@ __device__ void fill_stiffness(double* M, int N, int ld, int m, int dim, double 
   }
 }
 
-// Level-1 setup: Cholesky of A_1 once, then A_1^{-1} column by column (one thread per column).
+// Level-1 setup: LDL^T of A_1 once, then A_1^{-1} column by column (one thread per column).
+// Launched with 64 threads.
 __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, DevState* st) {
   extern __shared__ double sm[];
   const int m = n1 - 1;
   const int N = dim == 2 ? m * m : m * m * m;
   const int ld = N + 1;
   double* M = sm;
-  double* rhs = M + (size_t)N * ld;
-  double* invd = rhs + N;
+  double* rd = M + (size_t)N * ld;
   const double sigma = dim == 2 ? 1.0 : 1.0 / n1;
   fill_stiffness(M, N, ld, m, dim, sigma);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) rhs[i] = 0.0;
   __syncthreads();
-  {
-    double* work = invd + N;
-    const bool ok = block_chol_solve<double>(M, N, ld, rhs, work, invd, false, 0.0, nullptr);
-    if (!ok && threadIdx.x == 0) atomicOr(&st->flags, kFlagNotSPD);
-  }
-  __syncthreads();
-  // column `col` of the inverse: L L^T x = e_col (A^{-1} is symmetric: column = row)
+  const bool ok = ldlt_factor<double, 64>(M, N, ld, rd, false, 0.0, nullptr);
+  if (!ok && threadIdx.x == 0) atomicOr(&st->flags, kFlagNotSPD);
+  // column `col` of the inverse: L D L^T x = e_col (A^{-1} is symmetric: column = row), with
+  // L_kj = M[k][j] / d_j below the diagonal
   for (int col = threadIdx.x; col < N; col += blockDim.x) {
     double* x = Ainv + (long long)col * N;
     for (int k = 0; k < N; ++k) {
       double acc = (k == col) ? 1.0 : 0.0;
-      for (int j = 0; j < k; ++j) acc -= M[k * ld + j] * x[j];
-      x[k] = acc * invd[k];
+      for (int j = 0; j < k; ++j) acc -= M[k * ld + j] * rd[j] * x[j];
+      x[k] = acc;
     }
+    for (int k = 0; k < N; ++k) x[k] *= rd[k];
     for (int k = N - 1; k >= 0; --k) {
-      double acc = x[k];
-      for (int j = k + 1; j < N; ++j) acc -= M[j * ld + k] * x[j];
-      x[k] = acc * invd[k];
+      double acc = 0.0;
+      for (int j = k + 1; j < N; ++j) acc += M[j * ld + k] * x[j];
+      x[k] -= rd[k] * acc;
     }
   }
 }
@@ -330,7 +273,9 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
       L[p * ld + q] = (T)v;
     }
     __syncthreads();
-    const bool ok = block_chol_solve<T>(L, N, ld, rhs, work, invd, false, 0.0, nullptr);
+    const bool ok = ldlt_factor<T, 256>(L, N, ld, invd, false, 0.0, nullptr);
+    if (threadIdx.x < 32) ldlt_solve_warp<T>(L, N, ld, invd, rhs);
+    __syncthreads();
     if (threadIdx.x < 32) {
       double dmax = 0.0, umax = 0.0;
       bool finite = true;
@@ -597,19 +542,13 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
             A.u[o] = ut + (double)dl;
             return;
           }
+          // chord step: the Jacobian of the first pass is reused, so only the residual
+          // increments are summed here
           float dF, fp;
           delta_f(A.kind, A.a, ut, utf, dl, af, dF, fp);
           q0 += dF;
           q1 = fmaf(dF, zf, q1);
           sa = fmaf(dF, utf, sa);
-          const JT dz = (JT)fp * (JT)zf;
-          const JT du = (JT)fp * (JT)utf;
-          D0 += (JT)fp;
-          D1 += dz;
-          D2 += dz * (JT)zf;
-          E0 += du;
-          E1 += du * (JT)zf;
-          JSv += du * (JT)utf;
         };
         int z = z0;
         // four independent loads in flight before the arithmetic
@@ -679,6 +618,16 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
       if (phase == kUpdate) continue;
       // moments -> vertex channels of this thread's row
       const double w = A.w;
+      if (JF32 && phase != kFirst) {
+        // mixed path, chord step: residual channels only, converted in FP32 (the moments
+        // are FP32 sums of increments) and added to the FP64 rows
+        const float wf = (float)(w * inv_s), q0f = (float)Q0, q1f = (float)Q1;
+#pragma unroll
+        for (int t = 0; t <= D; ++t)
+          acc[(G::RA + S.vid[t]) * G::NT + tid] += (double)(wf * fmaf((float)S.P[t], q0f, (float)S.R[t] * q1f));
+        acc[G::SA * G::NT + tid] += (double)((float)w * (float)SAv);
+        continue;
+      }
 #pragma unroll
       for (int t = 0; t <= D; ++t) {
         const double Pt = S.P[t], Rt = S.R[t];
@@ -718,6 +667,7 @@ __device__ void block_reduce_rows(const double* acc, double* out, bool first) {
   for (int v = warp; v < G::NVAL; v += nw) {
     const bool pre = v >= G::TT && v < G::JB;
     if (pre && !first) continue;
+    if (JF32 && !first && v >= G::JB) continue;   // chord step: no Jacobian channels
     if (JF32 && v >= G::JB) {
       float x = 0.f;
       for (int t = lane; t < G::NT; t += 32) x += (float)acc[v * G::NT + t];
@@ -798,164 +748,12 @@ __device__ double pair_channel(const double* cellsum, int nc, const int* zp, con
   return x;
 }
 
-// The Newton system J d = rhs with J = [[K, j], [j^T, q]] (K = J_HH, N_H x N_H; the last
-// unknown is alpha), solved through its Schur complement: K z1 = j and K z2 = rhs_H by
-// preconditioned conjugate gradients with the precomputed A_H^{-1} (K = A_H + P^T W D P with
-// D >= 0, so the preconditioned spectrum is 1 + O(max f' / 2 pi^2)), then
-// d_alpha = (rhs_alpha - j.z2) / (q - j.z1) and d_H = z2 - d_alpha z1.  FP32 throughout
-// (the mixed path's inexact Newton step; the FP64 residual makes the next step correct for
-// it).  Matrix-vector products run on all warps, scalar recurrences on warp 0.  rhs (FP64)
-// is overwritten by d.  Returns false if CG did not reach 1e-3 relative accuracy (the
-// caller then factors instead); *dropped as in block_chol_solve.
-__device__ bool pcg_schur_solve(const double* M, int NA, int ld, double* rhs, const double* Ainv_g, float* wk,
-                                double drop_tol, int* dropped) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int n = NA - 1;
-  float* K = wk;        // n x n
-  float* Ai = K + n * n;  // n x n
-  __shared__ int cg_ok, cg_drop;
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - i * n;
-    K[idx] = (float)M[i * ld + j];
-    Ai[idx] = (float)__ldg(&Ainv_g[idx]);
-  }
-  __syncthreads();
-  if (tid < 32) {
-    // one warp: vector entry i lives in lane i % 32, slot i / 32 (n <= 64)
-    const int i0 = lane, i1 = lane + 32;
-    const bool h0 = i0 < n, h1 = i1 < n;
-    float x1[2] = {0.f, 0.f}, x2[2] = {0.f, 0.f};
-    float r1[2] = {h0 ? (float)M[i0 * ld + n] : 0.f, h1 ? (float)M[i1 * ld + n] : 0.f};
-    float r2[2] = {h0 ? (float)rhs[i0] : 0.f, h1 ? (float)rhs[i1] : 0.f};
-    float z1[2], z2[2], p1[2], p2[2], w1[2], w2[2];
-    // y = A v for both right-hand sides: v is published to shared memory and read back as
-    // broadcast loads; the row loop is unrolled with split accumulators so that the loads of
-    // several columns are in flight together
-    __shared__ float vs1[kMaxAug], vs2[kMaxAug];
-    const int r0 = h0 ? i0 : 0, r1i = h1 ? i1 : 0;
-    auto matvec2 = [&](const float* A, const float* v1, const float* v2, float* o1, float* o2) {
-      if (h0) {
-        vs1[i0] = v1[0];
-        vs2[i0] = v2[0];
-      }
-      if (h1) {
-        vs1[i1] = v1[1];
-        vs2[i1] = v2[1];
-      }
-      __syncwarp();
-      const float* A0 = A + r0 * n;
-      const float* A1 = A + r1i * n;
-      float a10 = 0.f, a11 = 0.f, a20 = 0.f, a21 = 0.f, c10 = 0.f, c11 = 0.f, c20 = 0.f, c21 = 0.f;
-      int j = 0;
-#pragma unroll 4
-      for (; j + 1 < n; j += 2) {
-        const float b1 = vs1[j], b2 = vs2[j], d1 = vs1[j + 1], d2 = vs2[j + 1];
-        const float x0 = A0[j], y0 = A0[j + 1], x1 = A1[j], y1 = A1[j + 1];
-        a10 = fmaf(x0, b1, a10);
-        a20 = fmaf(x0, b2, a20);
-        a11 = fmaf(x1, b1, a11);
-        a21 = fmaf(x1, b2, a21);
-        c10 = fmaf(y0, d1, c10);
-        c20 = fmaf(y0, d2, c20);
-        c11 = fmaf(y1, d1, c11);
-        c21 = fmaf(y1, d2, c21);
-      }
-      if (j < n) {
-        const float b1 = vs1[j], b2 = vs2[j];
-        a10 = fmaf(A0[j], b1, a10);
-        a20 = fmaf(A0[j], b2, a20);
-        a11 = fmaf(A1[j], b1, a11);
-        a21 = fmaf(A1[j], b2, a21);
-      }
-      __syncwarp();
-      o1[0] = h0 ? a10 + c10 : 0.f;
-      o1[1] = h1 ? a11 + c11 : 0.f;
-      o2[0] = h0 ? a20 + c20 : 0.f;
-      o2[1] = h1 ? a21 + c21 : 0.f;
-    };
-    auto wsum = [&](float v) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      return v;
-    };
-    auto wmax = [&](float v) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-      return v;
-    };
-    matvec2(Ai, r1, r2, z1, z2);
-    float rho1 = wsum(r1[0] * z1[0] + r1[1] * z1[1]);
-    float rho2 = wsum(r2[0] * z2[0] + r2[1] * z2[1]);
-    const float m1 = wmax(fmaxf(fabsf(r1[0]), fabsf(r1[1])));
-    const float m2 = wmax(fmaxf(fabsf(r2[0]), fabsf(r2[1])));
-    p1[0] = z1[0]; p1[1] = z1[1]; p2[0] = z2[0]; p2[1] = z2[1];
-    float rel = 1.f;
-    for (int it = 0; it < 60; ++it) {
-      matvec2(K, p1, p2, w1, w2);
-      const float mu1 = wsum(p1[0] * w1[0] + p1[1] * w1[1]);
-      const float mu2 = wsum(p2[0] * w2[0] + p2[1] * w2[1]);
-      const float a1 = mu1 > 0.f ? rho1 / mu1 : 0.f;
-      const float a2 = mu2 > 0.f ? rho2 / mu2 : 0.f;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        x1[q] = fmaf(a1, p1[q], x1[q]);
-        x2[q] = fmaf(a2, p2[q], x2[q]);
-        r1[q] = fmaf(-a1, w1[q], r1[q]);
-        r2[q] = fmaf(-a2, w2[q], r2[q]);
-      }
-      const float e1 = wmax(fmaxf(fabsf(r1[0]), fabsf(r1[1])));
-      const float e2 = wmax(fmaxf(fabsf(r2[0]), fabsf(r2[1])));
-      rel = fmaxf(m1 > 0.f ? e1 / m1 : 0.f, m2 > 0.f ? e2 / m2 : 0.f);
-      if (rel <= 2e-7f) break;
-      matvec2(Ai, r1, r2, z1, z2);
-      const float rn1 = wsum(r1[0] * z1[0] + r1[1] * z1[1]);
-      const float rn2 = wsum(r2[0] * z2[0] + r2[1] * z2[1]);
-      const float b1 = rho1 > 0.f ? rn1 / rho1 : 0.f;
-      const float b2 = rho2 > 0.f ? rn2 / rho2 : 0.f;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        p1[q] = fmaf(b1, p1[q], z1[q]);
-        p2[q] = fmaf(b2, p2[q], z2[q]);
-      }
-      rho1 = rn1;
-      rho2 = rn2;
-    }
-    // Schur complement for alpha (FP64 scalars from the FP32 solves)
-    double jz1 = 0.0, jz2 = 0.0;
-    if (h0) {
-      const double jv = M[i0 * ld + n];
-      jz1 += jv * (double)x1[0];
-      jz2 += jv * (double)x2[0];
-    }
-    if (h1) {
-      const double jv = M[i1 * ld + n];
-      jz1 += jv * (double)x1[1];
-      jz2 += jv * (double)x2[1];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      jz1 += __shfl_xor_sync(0xffffffffu, jz1, o);
-      jz2 += __shfl_xor_sync(0xffffffffu, jz2, o);
-    }
-    const double q = M[n * ld + n];
-    const double sa = q - jz1;
-    const bool drop = !(sa > drop_tol * q);
-    const double da = drop ? 0.0 : (rhs[n] - jz2) / sa;
-    __syncwarp();
-    if (h0) rhs[i0] = (double)x2[0] - da * (double)x1[0];
-    if (h1) rhs[i1] = (double)x2[1] - da * (double)x1[1];
-    if (lane == 0) {
-      rhs[n] = da;
-      cg_drop = drop;
-      cg_ok = rel <= 1e-3f;
-    }
-  }
-  __syncthreads();
-  if (dropped) *dropped = cg_drop;
-  return cg_ok != 0;
-}
+template <int D>
+__device__ void newton_update(const AugArgs& A, const double* R, int NH, double alpha, int dropped, bool ok);
 
-// Block 0, after a pass: cell sums, the dense system, the Newton step, convergence.
+// Block 0, after a pass: cell sums, the dense system, the Newton step, convergence.  In the
+// mixed path (JF32) the first iteration factors its Jacobian into L (LDL^T, FP32, with the
+// reciprocal pivots after it) and the later iterations are chord steps with that factor.
 template <int D, bool JF32>
 __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double* R,
                             typename std::conditional<JF32, float, double>::type* L, double alpha, bool first) {
@@ -970,6 +768,54 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
   double* t_vec = A.sys;
   double* gh_vec = A.sys + NH;
   double* s_gam = A.sys + 2 * NH;
+  if (JF32 && !first) {
+    // mixed path, chord step: the residual at the new iterate (first-pass FP64 sums plus this
+    // pass's increments), solved with the LDL^T factor of the first iteration's Jacobian
+    const double* basev = A.sys + 2 * NH + 2;
+    for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
+      const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
+      const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
+      double x = 0.0;
+      for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + ch % G::NVAL]);
+      cellsum[ch] = x + basev[idx];
+    }
+    __syncthreads();
+    const double sig = A.sigma_H;
+    for (int p = tid; p < NH; p += blockDim.x) {
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      const long long off = coarse_offset<D>(z, A.nc);
+      double nb = 0.0;
+      long long mul = 1;
+      for (int q = 0; q < D; ++q) {
+        nb += __ldcg(&A.c[off - mul]) + __ldcg(&A.c[off + mul]);
+        mul *= (A.nc + 1);
+      }
+      const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
+      R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA) - gh_vec[p]);
+    }
+    if (tid < 32) {
+      double s2 = 0.0, tc = 0.0;
+      for (int c = tid; c < ncell; c += 32) s2 += cellsum[(long long)c * G::NVAL + G::SA];
+      for (int p = tid; p < NH; p += 32) {
+        int z[3];
+        unknown_coords<D>(p, A.nc, z);
+        tc += t_vec[p] * __ldcg(&A.c[coarse_offset<D>(z, A.nc)]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        tc += __shfl_xor_sync(0xffffffffu, tc, o);
+      }
+      if (tid == 0) R[NH] = -(tc + alpha * s_gam[0] + s2 - s_gam[1]);
+    }
+    __syncthreads();
+    if (tid < 32) ldlt_solve_warp<float>(reinterpret_cast<const float*>(L), NA, ld,
+                                        reinterpret_cast<const float*>(L) + (size_t)NA * ld, R);
+    __syncthreads();
+    newton_update<D>(A, R, NH, alpha, 0, true);
+    return;
+  }
   // cell sums over the blocks of each cell (fixed order)
   for (int idx = tid; idx < ncell * G::NVAL; idx += blockDim.x) {
     const int cell = idx / G::NVAL, v = idx % G::NVAL;
@@ -1083,29 +929,31 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     }
   }
   __syncthreads();
-  // Newton step.  FP64 path: blocked Cholesky in FP64.  Mixed path: Schur complement with
-  // A_H^{-1}-preconditioned CG in FP32, falling back to the FP32 Cholesky if CG stalls.
+  // Newton step.  FP64 path: LDL^T in FP64.  Mixed path: LDL^T in FP32, kept in L for the
+  // chord steps of the later iterations.
   int dropped = 0;
   bool ok = true;
-  bool solved = false;
+  for (int idx = tid; idx < NA * ld; idx += blockDim.x) L[idx] = (FT)M[idx];
+  __syncthreads();
   if (JF32) {
-    __shared__ double rsave[kMaxAug];
-    for (int i = tid; i < NA; i += blockDim.x) rsave[i] = R[i];
+    float* Lf = reinterpret_cast<float*>(L);
+    float* rd = Lf + (size_t)NA * ld;
+    ok = ldlt_factor<float, G::NT>(Lf, NA, ld, rd, true, 1e-6, &dropped);
+    if (tid < 32) ldlt_solve_warp<float>(Lf, NA, ld, rd, R);
     __syncthreads();
-    solved = pcg_schur_solve(M, NA, ld, R, A.Ainv, reinterpret_cast<float*>(L), 1e-6, &dropped);
-    if (!solved) {
-      for (int i = tid; i < NA; i += blockDim.x) R[i] = rsave[i];
-      __syncthreads();
-    }
-  }
-  if (!solved) {
-    for (int idx = tid; idx < NA * ld; idx += blockDim.x) L[idx] = (FT)M[idx];
+  } else {
+    FT* rd = L + (size_t)NA * ld;
+    ok = ldlt_factor<FT, G::NT>(L, NA, ld, rd, true, 1e-14, &dropped);
+    if (tid < 32) ldlt_solve_warp<FT>(L, NA, ld, rd, R);
     __syncthreads();
-    FT* work = L + (size_t)NA * ld;
-    FT* invd = work + NA;
-    ok = block_chol_solve<FT>(L, NA, ld, R, work, invd, true, 1e-14, &dropped);
   }
-  // update of (c, alpha), convergence test (one warp)
+  newton_update<D>(A, R, NH, alpha, dropped, ok);
+}
+
+// (c, alpha) += the step in R, convergence test and status flags (warp 0 of the solving block).
+template <int D>
+__device__ void newton_update(const AugArgs& A, const double* R, int NH, double alpha, int dropped, bool ok) {
+  const int tid = threadIdx.x;
   if (tid < 32) {
     double dmax = 0.0, ymax = 0.0;
     bool finite = true;
@@ -1141,6 +989,15 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       __threadfence();
     }
   }
+}
+
+// Where the solving block keeps the Newton factor.  FP64 path: after R (a scratch that the
+// next pass may overwrite).  Mixed path: past the channel rows, so that the first
+// iteration's factor survives the later passes for the chord steps.
+template <int D, bool JF32, typename FT>
+__device__ __forceinline__ FT* aug_factor(double* sm, double* R, int NA) {
+  if (JF32) return reinterpret_cast<FT*>(sm + (size_t)Aug<D, JF32>::NVAL * Aug<D, JF32>::NT);
+  return reinterpret_cast<FT*>(R + NA + 1);
 }
 
 template <int D, bool JF32>
@@ -1181,7 +1038,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
   double* cellsum = acc;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  FT* L = reinterpret_cast<FT*>(R + NA + 1);
+  FT* L = aug_factor<D, JF32, FT>(sm, R, NA);
 
   if (blockIdx.x == 0) {
     const long long cn = ipow(A.nc + 1, D);
@@ -1199,7 +1056,9 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
       alpha_sh = first ? 1.0 : ((volatile double*)&A.st->alpha_cur)[0];
       stop = ((volatile int*)&A.st->abort)[0];
     }
-    for (int v = 0; v < G::NVAL; ++v) acc[v * G::NT + tid] = 0.0;
+    // chord steps of the mixed path fill the residual channels RA, SA only
+    const int nzero = (JF32 && !first) ? G::NV + 1 : G::NVAL;
+    for (int v = 0; v < nzero; ++v) acc[v * G::NT + tid] = 0.0;
     __syncthreads();
     if (stop) break;
     fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, bic);
@@ -1249,7 +1108,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs 
   double* cellsum = acc;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  FT* L = reinterpret_cast<FT*>(R + NA + 1);
+  FT* L = aug_factor<D, JF32, FT>(sm, R, NA);
   auto vertex_offset = [&](int cell, int v) {
     long long off = 0, mul = 1;
     int t = cell;
@@ -1279,7 +1138,8 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs 
     if (stop) break;
     for (int cell = rank; cell < ncell; cell += CS) {
       if (tid < G::NV) cv[tid] = first ? 0.0 : __ldcg(&A.c[vertex_offset(cell, tid)]);
-      for (int v = 0; v < G::NVAL; ++v) acc[v * G::NT + tid] = 0.0;
+      const int nzero = (JF32 && !first) ? G::NV + 1 : G::NVAL;
+      for (int v = 0; v < nzero; ++v) acc[v * G::NT + tid] = 0.0;
       __syncthreads();
       fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, 0);
       block_reduce_rows<D, JF32>(acc, A.partials + (long long)cell * G::NVAL, first);
@@ -1312,18 +1172,23 @@ size_t aug_smem(int nc) {
   const int ncell = (int)ipow(nc, D);
   const int NA = (int)ipow(nc - 1, D) + 1;
   const size_t rows = (size_t)G::NVAL * G::NT;
-  // cellsum, M, R, then the factor (NA (NA+1) values) or the CG workspace (2 NA^2 + 12 NA floats)
-  const size_t scratch = (size_t)ncell * G::NVAL + 2 * ((size_t)NA * (NA + 1)) + 3 * NA + 4 + (size_t)NA * NA + 8 * NA;
+  if (JF32) {
+    // channel rows (reused for cellsum, M, R), then the FP32 factor and its pivots
+    const size_t scratch = (size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 1;
+    return sizeof(double) * (rows > scratch ? rows : scratch) + sizeof(float) * ((size_t)NA * (NA + 1) + NA);
+  }
+  // cellsum, M, R, then the FP64 factor (NA (NA+1) values) and work/invd (2 NA)
+  const size_t scratch = (size_t)ncell * G::NVAL + 2 * ((size_t)NA * (NA + 1)) + 3 * NA + 4;
   return sizeof(double) * (rows > scratch ? rows : scratch);
 }
 
+// Blocks per SM of the cooperative kernel when launched with `smem` dynamic bytes (the
+// launch uses the larger of the two precisions' needs, so both kernels are sized with it).
 template <int D, bool JF32>
-int aug_occupancy(int nc, size_t* smem_out) {
-  const size_t smem = aug_smem<D, JF32>(nc);
+int aug_occupancy(size_t smem) {
   int occ = 0;
   raise_dyn_smem((const void*)k_augmented<D, JF32>, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_augmented<D, JF32>, Aug<D, JF32>::NT, smem);
-  *smem_out = smem;
   return occ;
 }
 
@@ -1366,22 +1231,24 @@ void aug_configure(int dim, int coarse_cells, AugBuffers* ab) {
                                                  cudaSuccess)
     sms = 0;
   const int ncell = (int)ipow(coarse_cells, dim);
-  size_t smem[2] = {0, 0};
+  const size_t s0 = dim == 2 ? aug_smem<2, false>(coarse_cells) : aug_smem<3, false>(coarse_cells);
+  const size_t s1 = dim == 2 ? aug_smem<2, true>(coarse_cells) : aug_smem<3, true>(coarse_cells);
+  const size_t smem = s0 > s1 ? s0 : s1;
   int occ[2] = {0, 0};
   if (sms > 0) {
     if (dim == 2) {
-      occ[0] = aug_occupancy<2, false>(coarse_cells, &smem[0]);
-      occ[1] = aug_occupancy<2, true>(coarse_cells, &smem[1]);
+      occ[0] = aug_occupancy<2, false>(smem);
+      occ[1] = aug_occupancy<2, true>(smem);
     } else {
-      occ[0] = aug_occupancy<3, false>(coarse_cells, &smem[0]);
-      occ[1] = aug_occupancy<3, true>(coarse_cells, &smem[1]);
+      occ[0] = aug_occupancy<3, false>(smem);
+      occ[1] = aug_occupancy<3, true>(smem);
     }
   }
   const int occ_min = occ[0] < occ[1] ? occ[0] : occ[1];
   int bpc = sms > 0 ? (occ_min * sms) / ncell : 1;
   if (bpc < 0) bpc = 0;
   ab->bpc = bpc;
-  ab->smem = smem[0] > smem[1] ? smem[0] : smem[1];
+  ab->smem = smem;
   ab->nt = dim == 2 ? Aug<2, false>::NT : Aug<3, false>::NT;
   ab->partial_items = (size_t)ncell * (bpc > 0 ? bpc : 1);
 }
