@@ -31,7 +31,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FMG fine DOFs/s to discretization error, mixed vs FP64; HBM GB/s; p50/p99"
 FP64_FLOPS_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9  # SMs x DFMA/clk x 2 flop x max SM clock
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, keyed by
+# (kind, dim); a kernel changed since its capture has no entry (traffic null)
+TRAFFIC = {("pre_top", 2): 16_792_064 + 6_912}
 WORKLOAD = "2D unit square P1, H=1/8, 8 refinements (2049x2049 nodes, 4,190,209 fine DOFs), u^3, 8 sin modes"
+WORKLOAD_3D = ("3D unit cube P1 on Kuhn tetrahedra, H=1/4, 6 refinements (257^3 nodes, 16,581,375 fine DOFs), "
+               "exp(u)-1, 8 sin modes with U[0,1] amplitudes")
 
 
 def parse():
@@ -45,9 +50,9 @@ def parse():
     ap.add_argument("--single-solve", action="store_true",
                     help="build, create one solver and run one solve, then exit (for ncu captures)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="large2d", choices=["large2d", "batch", "serve"],
-                    help="large2d: the headline single-instance solve; batch: 256 independent instances; "
-                         "serve: a Poisson request stream through the request server")
+    ap.add_argument("--workload", default="large2d", choices=["large2d", "3d", "batch", "serve"],
+                    help="large2d: the headline single-instance solve; 3d: the 3D Kuhn-mesh solve (257^3); "
+                         "batch: 256 independent instances; serve: a Poisson request stream through the server")
     ap.add_argument("--serve-count", type=int, default=2200)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -155,7 +160,7 @@ def max_over_ranks(dist, torch, x: float) -> float:
 
 # ------------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(refinements: int, repeats: int, seed: int = 0):
+def oracle_sample(refinements: int, repeats: int, seed: int = 0, dim: int = 2):
     """FP64 oracle FMG on a bounded sample of the workload: same H, fewer refinements."""
     try:
         from threadpoolctl import threadpool_limits
@@ -164,9 +169,10 @@ def oracle_sample(refinements: int, repeats: int, seed: int = 0):
     from oracle import fmg_oracle as O
     from paper_1611_05677_gb300 import workloads as W
 
-    prob = W.config_large_2d(seed=seed, refinements=refinements)
+    prob = (W.config_large_2d(seed=seed, refinements=refinements) if dim == 2
+            else W.config_3d(seed=seed, refinements=refinements))
     g = prob.g_nodal()
-    hier = O.build_hierarchy(2, prob.coarse_cells, refinements)
+    hier = O.build_hierarchy(dim, prob.coarse_cells, refinements)
     ctx = threadpool_limits(1) if threadpool_limits else None
     times = []
     try:
@@ -182,13 +188,13 @@ def oracle_sample(refinements: int, repeats: int, seed: int = 0):
     return prob.fine_dofs, times
 
 
-def cpu_baseline(refinements: int = 7, repeats: int = 5):
-    dofs, times = oracle_sample(refinements, repeats)
+def cpu_baseline(refinements: int = 7, repeats: int = 5, dim: int = 2):
+    dofs, times = oracle_sample(refinements, repeats, dim=dim)
     t = statistics.median(times)
     return {"value": dofs / t, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy/scipy oracle FMG of the same problem family at 7 refinements "
-                      f"({dofs} fine DOFs, 1/4 of the workload), median of {repeats} solves, hierarchy "
-                      f"assembly excluded, BLAS limited to 1 thread"}
+            "sample": f"FP64 numpy/scipy oracle FMG of the same problem family at {refinements} refinements "
+                      f"({dofs} fine DOFs), median of {repeats} solves, hierarchy assembly excluded, BLAS "
+                      f"limited to 1 thread"}
 
 
 def run_reference(args):
@@ -236,7 +242,7 @@ def kernel_times(torch, fmg, solver, flush, steps, level):
     fmg.fmg_set_kernel_timing(solver.ctx, True)
     fmg.fmg_solve(solver.ctx, None, fmg.fmg_stats())
     acc = {fmg.KT_AUGMENTED: [0.0, 0], fmg.KT_PRE_TOP: [0.0, 0], fmg.KT_POST_TOP: [0.0, 0],
-           fmg.KT_CORRECTION: [0.0, 0]}
+           fmg.KT_CORRECTION: [0.0, 0], fmg.KT_SMOOTH_TOP: [0.0, 0]}
     for _ in range(steps):
         with torch.cuda.stream(solver.stream):
             flush.zero_()
@@ -266,7 +272,11 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1611_05677_gb300 import fmg, workloads as W
 
-    prob = W.config_large_2d(seed=rank, refinements=args.refinements)
+    if args.workload == "3d":
+        prob = W.config_3d(seed=rank, refinements=6 if args.refinements == 8 else args.refinements)
+    else:
+        prob = W.config_large_2d(seed=rank, refinements=args.refinements)
+    dim = prob.dim
     g = prob.g_nodal()
     dofs = prob.fine_dofs
     n = prob.n_fine
@@ -306,46 +316,59 @@ def run_ours(args):
     for prec in ("mixed", "fp64"):
         u = solvers[prec].solve().cpu().numpy()
         outs[prec] = u
-        acc[prec] = float(math.sqrt(np.sum((u - us) ** 2) / n ** 2))
-    diff = float(math.sqrt(np.sum((outs["mixed"] - outs["fp64"]) ** 2) / n ** 2))
+        acc[prec] = float(math.sqrt(np.sum((u - us) ** 2) / n ** dim))
+    diff = float(math.sqrt(np.sum((outs["mixed"] - outs["fp64"]) ** 2) / n ** dim))
 
     # ---- per-kernel durations (instrumented graph), finest level
     log("kernel timing")
     top = prob.levels
     kt = kernel_times(torch, fmg, solvers["mixed"], flush, max(3, args.steps // 2), top)
     aug_ms, aug_n = kt[fmg.KT_AUGMENTED]
-    pre_ms, pre_n = kt[fmg.KT_PRE_TOP]
-    post_ms, post_n = kt[fmg.KT_POST_TOP]
-    nodes = (n + 1) ** 2
-    # fused pre-smoothing on the top level: reads b (4 B/node), writes the correction
-    # (4 B/node) and the coarse b and u (8 B per coarse node = 2 B/node)
-    pre_bytes = 10.0 * nodes
-    # fused post-smoothing on the top level: reads the correction and b (8 B/node), the
-    # coarse correction (1 B/node), read-modify-writes the FP64 iterate (16 B/node)
-    post_bytes = 25.0 * nodes
-    pre_gbs = pre_bytes / (pre_ms * 1e-3) / 1e9 if pre_ms > 0 else None
-    post_gbs = post_bytes / (post_ms * 1e-3) / 1e9 if post_ms > 0 else None
-    # augmented Newton on the top level: the FP64 work is the first pass, 24 FP64 flops per
-    # fine node (f, residual moments, stencil A u~ and the t, G_H, s, gamma moments); the
-    # later passes are FP32 increments
-    aug_flops = 24.0 * dofs
+    nodes = (n + 1) ** dim
+    # augmented Newton on the top level: the FP64 work is the first pass, about 24 (2D) / 28 (3D)
+    # FP64 flops per fine node (f and f', the residual moments, the stencil A u~ and the t, G_H,
+    # s, gamma moments); the later passes are FP32 increments
+    aug_flops = (24.0 if dim == 2 else 28.0) * dofs
     aug_tflops = aug_flops / (aug_ms * 1e-3) / 1e12 if aug_ms > 0 else None
-    shares = {"augmented": aug_ms * aug_n, "pre_top": pre_ms * pre_n, "post_top": post_ms * post_n}
+    shares = {"augmented": aug_ms * aug_n}
     roof = {
         "augmented": {"kernel": "k_augmented (mixed) on the finest level", "bound": "alu",
                       "achieved": aug_tflops, "peak": FP64_FLOPS_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
                       "frac": (aug_tflops * 1e12 / FP64_FLOPS_PEAK_DERIVED) if aug_tflops else None,
-                      "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                      "traffic": TRAFFIC.get(("augmented", dim)), "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
                       "avg_launch_ms": aug_ms, "launches": aug_n, "algorithmic_flops_per_launch": aug_flops},
-        "pre_top": {"kernel": "k_pre2_fused on the finest level", "bound": "hbm", "achieved": pre_gbs,
-                    "peak": hbm_peak, "unit": "GB/s", "frac": (pre_gbs / hbm_peak) if pre_gbs else None,
-                    "traffic": None, "peak_source": peak_kind, "avg_launch_ms": pre_ms, "launches": pre_n,
-                    "algorithmic_bytes_per_launch": pre_bytes},
-        "post_top": {"kernel": "k_post2_fused (top) on the finest level", "bound": "hbm", "achieved": post_gbs,
-                     "peak": hbm_peak, "unit": "GB/s", "frac": (post_gbs / hbm_peak) if post_gbs else None,
-                     "traffic": None, "peak_source": peak_kind, "avg_launch_ms": post_ms, "launches": post_n,
-                     "algorithmic_bytes_per_launch": post_bytes},
     }
+    if dim == 2:
+        pre_ms, pre_n = kt[fmg.KT_PRE_TOP]
+        post_ms, post_n = kt[fmg.KT_POST_TOP]
+        # fused pre-smoothing on the top level: reads b (4 B/node), writes the correction
+        # (4 B/node) and the coarse b and u (8 B per coarse node = 2 B/node)
+        pre_bytes = 10.0 * nodes
+        # fused post-smoothing on the top level: reads the correction and b (8 B/node), the
+        # coarse correction (1 B/node), read-modify-writes the FP64 iterate (16 B/node)
+        post_bytes = 25.0 * nodes
+        pre_gbs = pre_bytes / (pre_ms * 1e-3) / 1e9 if pre_ms > 0 else None
+        post_gbs = post_bytes / (post_ms * 1e-3) / 1e9 if post_ms > 0 else None
+        shares.update({"pre_top": pre_ms * pre_n, "post_top": post_ms * post_n})
+        roof["pre_top"] = {"kernel": "k_pre2_fused on the finest level", "bound": "hbm", "achieved": pre_gbs,
+                           "peak": hbm_peak, "unit": "GB/s", "frac": (pre_gbs / hbm_peak) if pre_gbs else None,
+                           "traffic": TRAFFIC.get(("pre_top", dim)), "peak_source": peak_kind, "avg_launch_ms": pre_ms,
+                           "launches": pre_n, "algorithmic_bytes_per_launch": pre_bytes}
+        roof["post_top"] = {"kernel": "k_post2_fused (top) on the finest level", "bound": "hbm", "achieved": post_gbs,
+                            "peak": hbm_peak, "unit": "GB/s", "frac": (post_gbs / hbm_peak) if post_gbs else None,
+                            "traffic": TRAFFIC.get(("post_top", dim)), "peak_source": peak_kind,
+                            "avg_launch_ms": post_ms, "launches": post_n, "algorithmic_bytes_per_launch": post_bytes}
+    else:
+        sm_ms, sm_n = kt[fmg.KT_SMOOTH_TOP]
+        # one red-black sweep (both colours) in FP32: read u and b, write u = 12 B/node
+        sm_bytes = 12.0 * nodes
+        sm_gbs = sm_bytes / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
+        shares["smooth_top"] = sm_ms * sm_n
+        roof["smooth_top"] = {"kernel": "k_rbgs3<float> sweep (both colours) on the finest level", "bound": "hbm",
+                              "achieved": sm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": (sm_gbs / hbm_peak) if sm_gbs else None,
+                              "traffic": TRAFFIC.get(("smooth_top", dim)), "peak_source": peak_kind,
+                              "avg_launch_ms": sm_ms, "launches": sm_n, "algorithmic_bytes_per_launch": sm_bytes}
     dominant = max(shares, key=shares.get)
     roofline = roof[dominant]
     other = {k: v for k, v in roof.items() if k != dominant}
@@ -369,7 +392,7 @@ def run_ours(args):
     cpu = None
     log("cpu baseline")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline() if dim == 2 else cpu_baseline(refinements=4, repeats=5, dim=3)
 
     if rank == 0:
         mix = results["mixed"]["mean_ms"]
@@ -387,7 +410,7 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f32 cycles + f64 residual/Newton",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "mixed", "instances": world,
+            "config": {"workload": WORKLOAD if dim == 2 else WORKLOAD_3D, "precision": "mixed", "instances": world,
                        "global_batch": world, "seq_len": None, "parallelism": f"independent instances x{world}",
                        "l2": "flushed between steps (512 MB write outside the timed events)",
                        "m": 2, "nu": [2, 2], "p": 1},
