@@ -167,12 +167,13 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
 struct AugBuffers {
   double* partials;   // [items][nvals]
   double* c;          // coarse nodal iterate (level-1 layout), length (nH+1)^d
-  double* sys;        // scratch: t, G_H, s, gamma and the dense system
-  const double* Ainv; // A_H^{-1}: preconditioner of the mixed path's Newton solves
+  double* sys;        // scratch: t, s and the mixed path's first-pass residual sums
+  const double* Ainv; // A_H^{-1} (level-1 inverse; kept with the buffers of the system)
   size_t partial_items;
   int bpc;            // blocks per coarse cell of the cooperative launch (all co-resident)
   int nt;             // threads per block
   size_t smem;        // dynamic shared memory per block
+  int sms;            // multiprocessors of the device
 };
 // Fills bpc/nt/smem/partial_items for this device (occupancy-based), outside any capture.
 void aug_configure(int dim, int coarse_cells, AugBuffers* ab);

@@ -25,7 +25,8 @@
 // lambda_t = (P_t + R_t z)/s, and every sum the system needs is a combination of the
 // segment's moments sum X, sum X z, sum X z^2.  The thread accumulates those moments in
 // registers (FP64 for the residual; FP32 or FP64 for the Jacobian) and converts them to the
-// cell's vertex channels once per segment.  The first pass also gathers t, G_H, s and gamma
+// cell's vertex channels once per segment.  The residual sums carry f(U) - g, so G_H and gamma
+// are never formed apart; the first pass also gathers t and s
 // (at (c, alpha) = (0, 1), U = u~), so no separate precompute pass is needed.
 //
 // Reductions are deterministic: per-thread channel rows in shared memory, fixed-order block
@@ -315,17 +316,43 @@ struct Aug {
   static constexpr int NV = 1 << D;             // vertices of a coarse cell
   static constexpr int NP = NV * (NV + 1) / 2;  // vertex pairs (packed upper)
   // channel layout of a block's partial sums (all stored as double)
-  static constexpr int RA = 0;                  // sum w f(U) lambda_v              [NV]
-  static constexpr int SA = NV;                 // sum w f(U) u~                     [1]
+  // f(U) and g enter the residual only as f(U) - g (R_H = A_H c + alpha t + P^T w (f(U) - g),
+  // R_a = t.c + alpha s + u~.w (f(U) - g)), so G_H and gamma need no channels of their own
+  static constexpr int RA = 0;                  // sum w (f(U) - g) lambda_v        [NV]
+  static constexpr int SA = NV;                 // sum w (f(U) - g) u~               [1]
   static constexpr int TT = NV + 1;             // sum (A u~) lambda_v  (first pass) [NV]
-  static constexpr int GH = 2 * NV + 1;         // sum w g lambda_v     (first pass) [NV]
-  static constexpr int SS = 3 * NV + 1;         // sum u~ A u~          (first pass) [1]
-  static constexpr int SG = 3 * NV + 2;         // sum w g u~           (first pass) [1]
-  static constexpr int JB = 3 * NV + 3;         // sum w f'(U) u~ lambda_v           [NV]
-  static constexpr int JP = 4 * NV + 3;         // sum w f'(U) lambda_v lambda_u     [NP]
-  static constexpr int JS = 4 * NV + 3 + NP;    // sum w f'(U) u~^2                  [1]
-  static constexpr int NVAL = 4 * NV + 4 + NP;
+  static constexpr int SS = 2 * NV + 1;         // sum u~ A u~          (first pass) [1]
+  static constexpr int JB = 2 * NV + 2;         // sum w f'(U) u~ lambda_v           [NV]
+  static constexpr int JP = 3 * NV + 2;         // sum w f'(U) lambda_v lambda_u     [NP]
+  static constexpr int JS = 3 * NV + 2 + NP;    // sum w f'(U) u~^2                  [1]
+  static constexpr int NVAL = 3 * NV + 3 + NP;
   static constexpr int NT = D == 2 ? 256 : 128;
+};
+
+// Channel rows of a block: one row of NT per-thread partial sums per channel.  Residual
+// channels (RA .. SS) are FP64; in the mixed path the Jacobian channels (JB .. JS) are FP32
+// rows after them (FP32 products to begin with), which halves their shared memory and
+// keeps FP64 work out of their accumulation.
+template <int D, bool JF32>
+struct Rows {
+  using G = Aug<D, JF32>;
+  static constexpr int NF = JF32 ? G::NVAL - G::JB : 0;   // FP32 rows
+  static constexpr int ND = G::NVAL - NF;                  // FP64 rows
+  static constexpr size_t bytes = (size_t)ND * G::NT * sizeof(double) + (size_t)NF * G::NT * sizeof(float);
+  __device__ static float* jac(double* acc) { return reinterpret_cast<float*>(acc + (size_t)ND * G::NT); }
+  __device__ static const float* jac(const double* acc) {
+    return reinterpret_cast<const float*>(acc + (size_t)ND * G::NT);
+  }
+  // zero this thread's rows of the channels the pass fills
+  __device__ static void zero(double* acc, bool first, int tid) {
+    if (JF32 && !first) {
+      for (int v = 0; v <= G::SA; ++v) acc[v * G::NT + tid] = 0.0;
+      return;
+    }
+    for (int v = 0; v < ND; ++v) acc[v * G::NT + tid] = 0.0;
+    float* f = jac(acc);
+    for (int v = 0; v < NF; ++v) f[v * G::NT + tid] = 0.f;
+  }
 };
 
 __device__ __forceinline__ int pair_index(int NV, int v, int u) {
@@ -344,7 +371,7 @@ struct AugArgs {
   const double* g;      // level-k nodal g
   double* partials;     // [cells * bpc][NVAL]
   double* c;            // coarse nodal iterate ((nc+1)^d, boundary 0)
-  double* sys;          // t[NH] G_H[NH] s gamma, mixed path: first-pass residual sums
+  double* sys;          // t[NH], s, (pad), mixed path: first-pass residual sums [ncell (NV+1)]
   const double* Ainv;   // A_H^{-1} (= A_1^{-1}, h_1 = H), dense NH x NH, preconditioner
   DevState* st;
 };
@@ -495,7 +522,15 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
   const long long items = (long long)ncol * nch;
   const double inv_s = 1.0 / s;
   const double inv_s2 = inv_s * inv_s;
-  for (long long q = (long long)bic * G::NT + tid; q < items; q += (long long)A.bpc * G::NT) {
+  // Items (column chunks) are dealt to the cell's blocks contiguously when they fill every
+  // block; on small levels they are interleaved across the blocks, so that the cell's work
+  // spreads over as many SM sub-partitions as there are items (the FP64 rate of one
+  // sub-partition is one warp instruction per 64 clocks, so a single busy warp per cell would
+  // serialize the pass).
+  const bool spread = items < (long long)A.bpc * G::NT;
+  const long long q0 = spread ? (long long)tid * A.bpc + bic : (long long)bic * G::NT + tid;
+  const long long qstep = (long long)A.bpc * G::NT;
+  for (long long q = q0; q < items; q += qstep) {
     const int col = (int)(q % ncol);
     const int ch = (int)(q / ncol);
     const int o[2] = {col % s, D == 3 ? col / s : 0};
@@ -528,7 +563,7 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
       }
       double Q0 = 0.0, Q1 = 0.0, SAv = 0.0;                 // residual moments
       JT D0 = 0, D1 = 0, D2 = 0, E0 = 0, E1 = 0, JSv = 0;   // Jacobian moments
-      double T0 = 0.0, T1 = 0.0, SSv = 0.0, G0 = 0.0, G1 = 0.0, SGv = 0.0;  // first pass
+      double T0 = 0.0, T1 = 0.0, SSv = 0.0;                 // first pass
       double zd = (double)z0;
       long long off = base + (long long)(zc + z0) * zstride;
       if (JF32 && phase != kFirst) {
@@ -551,13 +586,13 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
           sa = fmaf(dF, utf, sa);
         };
         int z = z0;
-        // four independent loads in flight before the arithmetic
-        for (; z + 3 <= z1; z += 4, off += 4 * zstride) {
-          double v[4];
+        // eight independent loads in flight before the arithmetic
+        for (; z + 7 <= z1; z += 8, off += 8 * zstride) {
+          double v[8];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) v[q] = A.u[off + q * zstride];
+          for (int q = 0; q < 8; ++q) v[q] = A.u[off + q * zstride];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) node(v[q], (float)(z + q), off + q * zstride);
+          for (int q = 0; q < 8; ++q) node(v[q], (float)(z + q), off + q * zstride);
         }
         for (; z <= z1; ++z, off += zstride) node(A.u[off], (float)z, off);
         Q0 = q0;
@@ -565,14 +600,14 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         SAv = sa;
       } else
       for (int z = z0; z <= z1; ++z, off += zstride, zd += 1.0) {
-        if (phase == kFirst && ((z - z0) & 3) == 0) {
-          // touch the next four column entries and their g values so that their loads are
+        if (((z - z0) & 7) == 0) {
+          // touch the next eight column entries (and their g values) so that their loads are
           // in flight together (they stay in L1 for the iterations below)
 #pragma unroll
-          for (int q = 1; q < 4; ++q)
+          for (int q = 1; q < 8; ++q)
             if (z + q <= z1) {
               asm volatile("prefetch.global.L1 [%0];" ::"l"(A.u + off + q * zstride));
-              asm volatile("prefetch.global.L1 [%0];" ::"l"(A.g + off + q * zstride));
+              if (phase != kUpdate) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.g + off + q * zstride));
             }
         }
         const double ut = A.u[off];
@@ -581,14 +616,26 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
           A.u[off] = U;
           continue;
         }
-        double F, Fp;
-        f_eval<double>(A.kind, A.a, U, F, Fp);
-        Q0 += F;
-        Q1 = fma(F, zd, Q1);
-        SAv = fma(F, ut, SAv);
-        const JT dj = (JT)Fp;
+        double F, Fp = 0.0;
+        JT dj, zj;
         const JT uj = (JT)ut;
-        const JT zj = (JT)zd;
+        if (JF32) {
+          // mixed path: f in FP64 for the residual; f' (the Jacobian's factor) in FP32 from
+          // the FP32 value, so no FP64 work or conversion goes into the Jacobian moments
+          F = f_only<double>(A.kind, A.a, U);
+          float Ff, Fpf;
+          f_eval<float>(A.kind, (float)A.a, (float)uj, Ff, Fpf);
+          dj = (JT)Fpf;
+          zj = (JT)z;
+        } else {
+          f_eval<double>(A.kind, A.a, U, F, Fp);
+          dj = (JT)Fp;
+          zj = (JT)zd;
+        }
+        const double Fm = F - A.g[off];
+        Q0 += Fm;
+        Q1 = fma(Fm, zd, Q1);
+        SAv = fma(Fm, ut, SAv);
         const JT dz = dj * zj;
         const JT du = dj * uj;
         D0 += dj;
@@ -606,13 +653,9 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
                  (A.u[off - zstride] + A.u[off + zstride]);
           }
           const double au = A.sigma_k * (2.0 * D * ut - nb);
-          const double gv = A.g[off];
           T0 += au;
           T1 = fma(au, zd, T1);
           SSv = fma(au, ut, SSv);
-          G0 += gv;
-          G1 = fma(gv, zd, G1);
-          SGv = fma(gv, ut, SGv);
         }
       }
       if (phase == kUpdate) continue;
@@ -633,30 +676,49 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         const double Pt = S.P[t], Rt = S.R[t];
         const int v = S.vid[t];
         acc[(G::RA + v) * G::NT + tid] += w * inv_s * (Pt * Q0 + Rt * Q1);
-        acc[(G::JB + v) * G::NT + tid] += w * inv_s * (Pt * (double)E0 + Rt * (double)E1);
-        if (phase == kFirst) {
-          acc[(G::TT + v) * G::NT + tid] += inv_s * (Pt * T0 + Rt * T1);
-          acc[(G::GH + v) * G::NT + tid] += w * inv_s * (Pt * G0 + Rt * G1);
-        }
-#pragma unroll
-        for (int r = t; r <= D; ++r) {
-          const double Pr = S.P[r], Rr = S.R[r];
-          acc[(G::JP + pair_index(G::NV, v, S.vid[r])) * G::NT + tid] +=
-              w * inv_s2 * (Pt * Pr * (double)D0 + (Pt * Rr + Rt * Pr) * (double)D1 + Rt * Rr * (double)D2);
-        }
+        if (phase == kFirst) acc[(G::TT + v) * G::NT + tid] += inv_s * (Pt * T0 + Rt * T1);
       }
       acc[G::SA * G::NT + tid] += w * SAv;
-      acc[G::JS * G::NT + tid] += w * (double)JSv;
-      if (phase == kFirst) {
-        acc[G::SS * G::NT + tid] += SSv;
-        acc[G::SG * G::NT + tid] += w * SGv;
+      if (phase == kFirst) acc[G::SS * G::NT + tid] += SSv;
+      if (JF32) {
+        // FP32 Jacobian channels, converted in FP32 into the FP32 rows
+        float* fj = Rows<D, JF32>::jac(acc);
+        const float wf = (float)(w * inv_s), wf2 = (float)(w * inv_s2);
+        const float d0 = (float)D0, d1 = (float)D1, d2 = (float)D2, e0 = (float)E0, e1 = (float)E1;
+#pragma unroll
+        for (int t = 0; t <= D; ++t) {
+          const float Pt = (float)S.P[t], Rt = (float)S.R[t];
+          const int v = S.vid[t];
+          fj[(G::JB - G::JB + v) * G::NT + tid] += wf * fmaf(Pt, e0, Rt * e1);
+#pragma unroll
+          for (int r = t; r <= D; ++r) {
+            const float Pr = (float)S.P[r], Rr = (float)S.R[r];
+            fj[(G::JP - G::JB + pair_index(G::NV, v, S.vid[r])) * G::NT + tid] +=
+                wf2 * fmaf(Pt * Pr, d0, fmaf(fmaf(Pt, Rr, Rt * Pr), d1, Rt * Rr * d2));
+          }
+        }
+        fj[(G::JS - G::JB) * G::NT + tid] += (float)w * (float)JSv;
+      } else {
+#pragma unroll
+        for (int t = 0; t <= D; ++t) {
+          const double Pt = S.P[t], Rt = S.R[t];
+          const int v = S.vid[t];
+          acc[(G::JB + v) * G::NT + tid] += w * inv_s * (Pt * (double)E0 + Rt * (double)E1);
+#pragma unroll
+          for (int r = t; r <= D; ++r) {
+            const double Pr = S.P[r], Rr = S.R[r];
+            acc[(G::JP + pair_index(G::NV, v, S.vid[r])) * G::NT + tid] +=
+                w * inv_s2 * (Pt * Pr * (double)D0 + (Pt * Rr + Rt * Pr) * (double)D1 + Rt * Rr * (double)D2);
+          }
+        }
+        acc[G::JS * G::NT + tid] += w * (double)JSv;
       }
     }
   }
 }
 
 // Block sum of the channel rows into out[0..NVAL) (fixed order).  Only the channels the
-// phase produced are summed (the first-pass gatherings t, G_H, s, gamma only in the first
+// phase produced are summed (the first-pass gatherings t and s only in the first
 // pass); in the mixed path the Jacobian channels, FP32 products to begin with, are summed in
 // FP32 -- FP64 adds issue slowly on this part.
 template <int D, bool JF32>
@@ -669,8 +731,9 @@ __device__ void block_reduce_rows(const double* acc, double* out, bool first) {
     if (pre && !first) continue;
     if (JF32 && !first && v >= G::JB) continue;   // chord step: no Jacobian channels
     if (JF32 && v >= G::JB) {
+      const float* fj = Rows<D, JF32>::jac(acc);
       float x = 0.f;
-      for (int t = lane; t < G::NT; t += 32) x += (float)acc[v * G::NT + t];
+      for (int t = lane; t < G::NT; t += 32) x += fj[(v - G::JB) * G::NT + t];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       if (lane == 0) out[v] = (double)x;
@@ -766,12 +829,11 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
   const int ld = NA + 1;
   constexpr int N3 = D == 2 ? 9 : 27;
   double* t_vec = A.sys;
-  double* gh_vec = A.sys + NH;
-  double* s_gam = A.sys + 2 * NH;
+  double* s_val = A.sys + NH;        // s; the mixed path's first-pass residual sums follow
+  double* basev = A.sys + NH + 2;
   if (JF32 && !first) {
     // mixed path, chord step: the residual at the new iterate (first-pass FP64 sums plus this
     // pass's increments), solved with the LDL^T factor of the first iteration's Jacobian
-    const double* basev = A.sys + 2 * NH + 2;
     for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
       const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
       const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
@@ -792,7 +854,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
         mul *= (A.nc + 1);
       }
       const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
-      R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA) - gh_vec[p]);
+      R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA));
     }
     if (tid < 32) {
       double s2 = 0.0, tc = 0.0;
@@ -807,7 +869,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         tc += __shfl_xor_sync(0xffffffffu, tc, o);
       }
-      if (tid == 0) R[NH] = -(tc + alpha * s_gam[0] + s2 - s_gam[1]);
+      if (tid == 0) R[NH] = -(tc + alpha * s_val[0] + s2);
     }
     __syncthreads();
     if (tid < 32) ldlt_solve_warp<float>(reinterpret_cast<const float*>(L), NA, ld,
@@ -829,7 +891,6 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
   if (JF32) {
     // mixed path: after the first pass the residual channels hold increments; the first
     // pass's FP64 sums are kept in sys and added back (fixed order, same thread each time)
-    double* basev = A.sys + 2 * NH + 2;
     for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
       const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
       const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
@@ -845,23 +906,13 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       int z[3];
       unknown_coords<D>(p, A.nc, z);
       t_vec[p] = node_channel<D, JF32>(cellsum, A.nc, z, G::TT);
-      gh_vec[p] = node_channel<D, JF32>(cellsum, A.nc, z, G::GH);
     }
     if (tid < 32) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int c = tid; c < ncell; c += 32) {
-        s0 += cellsum[(long long)c * G::NVAL + G::SS];
-        s1 += cellsum[(long long)c * G::NVAL + G::SG];
-      }
+      double s0 = 0.0;
+      for (int c = tid; c < ncell; c += 32) s0 += cellsum[(long long)c * G::NVAL + G::SS];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      }
-      if (tid == 0) {
-        s_gam[0] = s0;
-        s_gam[1] = s1;
-      }
+      for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      if (tid == 0) s_val[0] = s0;
     }
     __syncthreads();
   }
@@ -901,7 +952,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       mul *= (A.nc + 1);
     }
     const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
-    R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA) - gh_vec[p]);
+    R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA));
     const double jb = t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::JB);
     M[p * ld + NH] = jb;
     M[NH * ld + p] = jb;
@@ -924,8 +975,8 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       tc += __shfl_xor_sync(0xffffffffu, tc, o);
     }
     if (tid == 0) {
-      R[NH] = -(tc + alpha * s_gam[0] + s2 - s_gam[1]);
-      M[NH * ld + NH] = s_gam[0] + s3;
+      R[NH] = -(tc + alpha * s_val[0] + s2);
+      M[NH * ld + NH] = s_val[0] + s3;
     }
   }
   __syncthreads();
@@ -996,7 +1047,11 @@ __device__ void newton_update(const AugArgs& A, const double* R, int NH, double 
 // iteration's factor survives the later passes for the chord steps.
 template <int D, bool JF32, typename FT>
 __device__ __forceinline__ FT* aug_factor(double* sm, double* R, int NA) {
-  if (JF32) return reinterpret_cast<FT*>(sm + (size_t)Aug<D, JF32>::NVAL * Aug<D, JF32>::NT);
+  if (JF32) {
+    char* rows_end = reinterpret_cast<char*>(sm) + Rows<D, JF32>::bytes;
+    char* scratch_end = reinterpret_cast<char*>(R + NA + 1);
+    return reinterpret_cast<FT*>(rows_end > scratch_end ? rows_end : scratch_end);
+  }
   return reinterpret_cast<FT*>(R + NA + 1);
 }
 
@@ -1057,8 +1112,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
       stop = ((volatile int*)&A.st->abort)[0];
     }
     // chord steps of the mixed path fill the residual channels RA, SA only
-    const int nzero = (JF32 && !first) ? G::NV + 1 : G::NVAL;
-    for (int v = 0; v < nzero; ++v) acc[v * G::NT + tid] = 0.0;
+    Rows<D, JF32>::zero(acc, first, tid);
     __syncthreads();
     if (stop) break;
     fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, bic);
@@ -1138,8 +1192,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs 
     if (stop) break;
     for (int cell = rank; cell < ncell; cell += CS) {
       if (tid < G::NV) cv[tid] = first ? 0.0 : __ldcg(&A.c[vertex_offset(cell, tid)]);
-      const int nzero = (JF32 && !first) ? G::NV + 1 : G::NVAL;
-      for (int v = 0; v < nzero; ++v) acc[v * G::NT + tid] = 0.0;
+      Rows<D, JF32>::zero(acc, first, tid);
       __syncthreads();
       fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, 0);
       block_reduce_rows<D, JF32>(acc, A.partials + (long long)cell * G::NVAL, first);
@@ -1173,9 +1226,11 @@ size_t aug_smem(int nc) {
   const int NA = (int)ipow(nc - 1, D) + 1;
   const size_t rows = (size_t)G::NVAL * G::NT;
   if (JF32) {
-    // channel rows (reused for cellsum, M, R), then the FP32 factor and its pivots
-    const size_t scratch = (size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 1;
-    return sizeof(double) * (rows > scratch ? rows : scratch) + sizeof(float) * ((size_t)NA * (NA + 1) + NA);
+    // channel rows (reused for cellsum, M, R), then the FP32 factor and its pivots; the factor
+    // sits past the rows, so the rows are padded to the scratch when that is larger
+    const size_t rbytes = Rows<D, JF32>::bytes;
+    const size_t scratch = sizeof(double) * ((size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 1);
+    return (rbytes > scratch ? rbytes : scratch) + sizeof(float) * ((size_t)NA * (NA + 1) + NA);
   }
   // cellsum, M, R, then the FP64 factor (NA (NA+1) values) and work/invd (2 NA)
   const size_t scratch = (size_t)ncell * G::NVAL + 2 * ((size_t)NA * (NA + 1)) + 3 * NA + 4;
@@ -1249,6 +1304,7 @@ void aug_configure(int dim, int coarse_cells, AugBuffers* ab) {
   if (bpc < 0) bpc = 0;
   ab->bpc = bpc;
   ab->smem = smem;
+  ab->sms = sms;
   ab->nt = dim == 2 ? Aug<2, false>::NT : Aug<3, false>::NT;
   ab->partial_items = (size_t)ncell * (bpc > 0 ? bpc : 1);
 }
@@ -1291,12 +1347,18 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
   const int ncell = (int)ipow(coarse_cells, dim);
   const int sfine = 1 << (level - 1);
-  const int chunk = sfine < 32 ? sfine : 32;
-  // blocks per cell for this level: about one column chunk per thread, at most what is
-  // co-resident
-  const long long items = ipow(sfine, dim - 1) * (sfine / chunk);
+  // column chunks of up to 32 nodes; on small levels shorter ones, until there are enough
+  // items for one warp per SM sub-partition (each chunk costs one moment-to-channel
+  // conversion, so they are no shorter than that needs)
+  const long long ncol = ipow(sfine, dim - 1);
+  const long long target = (long long)(ab.sms > 0 ? ab.sms : 1) * 4 * 32;
+  int chunk = sfine < 32 ? sfine : 32;
+  while (chunk > 1 && ncol * (sfine / chunk) * ncell < target) chunk >>= 1;
+  const long long items = ncol * (sfine / chunk);
+  // blocks per cell: about one chunk per thread; when that leaves blocks unfilled, the
+  // chunks are spread over all co-resident blocks of the cell instead
   int bpc = (int)((items + nt - 1) / nt);
-  if (bpc > ab.bpc) bpc = ab.bpc;
+  if (bpc > ab.bpc || items < (long long)ab.bpc * nt) bpc = (int)(items < ab.bpc ? items : ab.bpc);
   if (bpc < 1) bpc = 1;
   AugArgs A;
   A.dim = dim;
