@@ -19,7 +19,8 @@ assembled sparse matrices:
   the coarse basis at the fine nodes; restriction is P_k^T.
 * Algorithm 3.1 step 1, eq. (3.4)-(3.5): the linearized boundary value problem
   with the nonlinearity frozen at the current iterate, solved by m V-cycles
-  (red-black Gauss-Seidel smoothing, exact solve on the coarsest mesh).
+  (red-black Gauss-Seidel smoothing, or Chebyshev-Jacobi smoothing as the colour-free
+  alternative; exact solve on the coarsest mesh).
 * Algorithm 3.1 step 2, eq. (3.6): the semilinear problem on
   V_{H,h_k} = V_H + span{u~}, solved by Newton's method on the assembled
   (N_H+1)-dimensional Galerkin system (the nonlinear iteration is left open
@@ -327,19 +328,59 @@ def smooth(lev: Level, b, u, sweeps: int, order: tuple) -> None:
             rbgs_half(lev, b, u, c)
 
 
+# Chebyshev-Jacobi smoothing: the colour-free alternative smoother of the multigrid step.
+# The smoothing polynomial is the Chebyshev polynomial of the Jacobi-preconditioned operator
+# D^{-1} A shifted to the interval [lmin, lmax] = [lmax/ratio, lmax] of the high-frequency
+# eigenvalues: after `degree` steps the error is p(D^{-1}A) e0 with
+# p(lam) = T_degree((theta - lam)/delta) / T_degree(theta/delta), theta = (lmax+lmin)/2,
+# delta = (lmax-lmin)/2, by the standard three-term Chebyshev iteration.  lmax = 2 bounds the
+# spectrum of D^{-1}A for the 2d+1-point stiffness of these meshes (its eigenvalues are
+# 1 - (cos + ... + cos)/d, all inside (0, 2)).
+CHEB_LMAX = 2.0
+CHEB_RATIO = 4.0
+
+
+def chebyshev_smooth(lev: Level, b: np.ndarray, u: np.ndarray, degree: int,
+                     lmax: float = CHEB_LMAX, ratio: float = CHEB_RATIO) -> None:
+    """`degree` Chebyshev-Jacobi steps on A u = b, in place."""
+    if degree <= 0:
+        return
+    lmin = lmax / ratio
+    theta = 0.5 * (lmax + lmin)
+    delta = 0.5 * (lmax - lmin)
+    sig = theta / delta
+    rho = 1.0 / sig
+    d = (b - lev.A @ u) / lev.diag / theta
+    u += d
+    for _ in range(1, degree):
+        r = (b - lev.A @ u) / lev.diag
+        rho_new = 1.0 / (2.0 * sig - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * r
+        rho = rho_new
+        u += d
+
+
 def vcycle(hier: Hierarchy, k: int, b: np.ndarray, u: np.ndarray,
-           nu_pre: int = 2, nu_post: int = 2) -> np.ndarray:
-    """One V(nu_pre, nu_post) cycle for A_k u = b from the initial guess u."""
+           nu_pre: int = 2, nu_post: int = 2, smoother: str = "rbgs") -> np.ndarray:
+    """One V(nu_pre, nu_post) cycle for A_k u = b from the initial guess u.  smoother:
+    "rbgs" (red-black Gauss-Seidel sweeps) or "chebyshev" (Chebyshev-Jacobi steps of degree
+    nu_pre / nu_post)."""
     lev = hier.level(k)
     u = u.copy()
     if k == 1:
         return sla.cho_solve(lev.chol, b)
-    smooth(lev, b, u, nu_pre, ("red", "black"))
+    if smoother == "chebyshev":
+        chebyshev_smooth(lev, b, u, nu_pre)
+    else:
+        smooth(lev, b, u, nu_pre, ("red", "black"))
     r = b - lev.A @ u
     bc = lev.P.T @ r
-    ec = vcycle(hier, k - 1, bc, np.zeros_like(bc), nu_pre, nu_post)
+    ec = vcycle(hier, k - 1, bc, np.zeros_like(bc), nu_pre, nu_post, smoother)
     u += lev.P @ ec
-    smooth(lev, b, u, nu_post, ("black", "red"))
+    if smoother == "chebyshev":
+        chebyshev_smooth(lev, b, u, nu_post)
+    else:
+        smooth(lev, b, u, nu_post, ("black", "red"))
     return u
 
 
@@ -427,14 +468,15 @@ def augmented_newton(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarr
 
 
 def correction_step(hier: Hierarchy, k: int, u: np.ndarray, G: np.ndarray, kind: str, a: float,
-                    m: int = 2, nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-6):
+                    m: int = 2, nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-6,
+                    smoother: str = "rbgs"):
     """u^{(l+1)} = SemilinearMG(V_H, u^{(l)}, V_{h_k}) (Algorithm 3.1)."""
     lev = hier.level(k)
     # step 1 (eq. 3.4): a(u^, v) = (g, v) - (f(x, u^{(l)}), v)
     b = G - lev.w * f_val(kind, a, u)
     ut = u.copy()
     for _ in range(m):                     # eq. (3.5): m multigrid steps from u^{(l)}
-        ut = vcycle(hier, k, b, ut, nu_pre, nu_post)
+        ut = vcycle(hier, k, b, ut, nu_pre, nu_post, smoother)
     # step 2 (eq. 3.6): semilinear problem on V_H + span{u~}
     y, B, iters = augmented_newton(lev, hier.P_H[k - 1], ut, G, kind, a, tol)
     info = StepInfo(newton_iters=iters, alpha=float(y[-1]), c=y[:-1].copy(), u_tilde=ut)
@@ -455,7 +497,7 @@ class FMGResult:
 
 def fmg(hier: Hierarchy, g_fine: np.ndarray, kind: str, a: float, m: int = 2, p: int = 1,
         nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-6, tol_level1: float = 1e-6,
-        keep_levels: bool = True) -> FMGResult:
+        keep_levels: bool = True, smoother: str = "rbgs") -> FMGResult:
     n_levels = len(hier.levels)
     n_fine = hier.levels[-1].n
     dim = hier.dim
@@ -470,7 +512,7 @@ def fmg(hier: Hierarchy, g_fine: np.ndarray, kind: str, a: float, m: int = 2, p:
         G = load_vector(lev, restrict_nodal(g_fine, dim, n_fine, lev.n))
         u = lev.P @ u                      # u^{(0)}_{h_k} = u_{h_{k-1}} (natural inclusion)
         for _ in range(p):
-            u, info = correction_step(hier, k, u, G, kind, a, m, nu_pre, nu_post, tol)
+            u, info = correction_step(hier, k, u, G, kind, a, m, nu_pre, nu_post, tol, smoother)
             steps.append((k, info))
         if keep_levels:
             us.append(u)

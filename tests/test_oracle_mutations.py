@@ -52,7 +52,7 @@ def test_dropped_nonlinear_term_in_linearized_rhs_is_caught(monkeypatch):
     the answer only up to the V_H + span{u~} approximation, so the FMG result
     drifts from the discrete solution beyond the accuracy criterion."""
     # patch the correction step to skip the nonlinear RHS term
-    def bad_step(hier, k, u, G, kind, a, m=2, nu_pre=2, nu_post=2, tol=1e-12):
+    def bad_step(hier, k, u, G, kind, a, m=2, nu_pre=2, nu_post=2, tol=1e-12, smoother="rbgs"):
         lev = hier.level(k)
         b = G.copy()
         ut = u.copy()
@@ -74,3 +74,38 @@ def test_dropped_nonlinear_term_in_linearized_rhs_is_caught(monkeypatch):
     e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star()))
     assert O.discrete_l2(lev, good - ub) <= 0.1 * e_disc
     assert O.discrete_l2(lev, bad - ub) > 1.0 * e_disc
+
+
+def test_wrong_chebyshev_coefficient_is_caught(monkeypatch):
+    """A Chebyshev step that reuses the previous rho in the momentum term (a plausible slip
+    in the three-term recurrence) no longer gives the Chebyshev error polynomial."""
+    def bad(lev, b, u, degree, lmax=O.CHEB_LMAX, ratio=O.CHEB_RATIO):
+        lmin = lmax / ratio
+        theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+        sig = theta / delta
+        rho = 1.0 / sig
+        d = (b - lev.A @ u) / lev.diag / theta
+        u += d
+        for _ in range(1, degree):
+            r = (b - lev.A @ u) / lev.diag
+            rho_new = 1.0 / (2.0 * sig - rho)
+            d = rho * rho * d + (2.0 * rho_new / delta) * r     # planted: rho instead of rho_new
+            rho = rho_new
+            u += d
+
+    lev = O.assemble_level(2, 16)
+    X = lev.nodes[lev.interior] * lev.h
+    e0 = np.sin(7 * math.pi * X[:, 0]) * np.sin(12 * math.pi * X[:, 1])
+    lam = 1.0 - 0.5 * (math.cos(7 * math.pi * lev.h) + math.cos(12 * math.pi * lev.h))
+    lmin = O.CHEB_LMAX / O.CHEB_RATIO
+    theta, delta = 0.5 * (O.CHEB_LMAX + lmin), 0.5 * (O.CHEB_LMAX - lmin)
+    coef = np.array([0.0, 0.0, 0.0, 1.0])
+    p = np.polynomial.chebyshev.chebval((theta - lam) / delta, coef) / np.polynomial.chebyshev.chebval(
+        theta / delta, coef)
+    good = e0.copy()
+    O.chebyshev_smooth(lev, np.zeros_like(e0), good, 3)
+    assert np.max(np.abs(good - p * e0)) < 1e-12
+    monkeypatch.setattr(O, "chebyshev_smooth", bad)
+    u = e0.copy()
+    O.chebyshev_smooth(lev, np.zeros_like(e0), u, 3)
+    assert np.max(np.abs(u - p * e0)) > 1e-3 * np.max(np.abs(e0))

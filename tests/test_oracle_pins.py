@@ -361,3 +361,105 @@ def test_level_one_is_exact():
     lev = hier.level(1)
     G = O.load_vector(lev, O.restrict_nodal(g, 2, 8, 4))
     assert np.max(np.abs(O.nonlinear_residual(lev, G, prob.f, prob.a, res.u[0]))) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Chebyshev-Jacobi smoother (the colour-free alternative smoother)
+# ---------------------------------------------------------------------------
+
+
+def _mode_vector(lev, kv):
+    """Nodal sine mode prod_ax sin(k_ax pi x_ax) on the unknowns of a level: an eigenvector
+    of the 2d+1-point stiffness with D^{-1}A eigenvalue 1 - mean_ax cos(k_ax pi h)."""
+    X = lev.nodes[lev.interior] * lev.h
+    v = np.ones(X.shape[0])
+    for ax in range(lev.dim):
+        v *= np.sin(kv[ax] * math.pi * X[:, ax])
+    lam = 1.0 - np.mean([math.cos(k * math.pi * lev.h) for k in kv])
+    return v, lam
+
+
+@pytest.mark.parametrize("dim,n,kv", [(2, 16, (1, 1)), (2, 16, (7, 12)), (2, 16, (15, 15)), (3, 8, (2, 5, 7))])
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+def test_chebyshev_error_polynomial(dim, n, kv, degree):
+    """After `degree` steps on A u = 0 the error is p(lam) e0 with the shifted, scaled
+    Chebyshev polynomial p(lam) = T_k((theta - lam)/delta) / T_k(theta/delta) (evaluated
+    here with numpy's Chebyshev series, not the smoother's recurrence)."""
+    lev = O.assemble_level(dim, n)
+    e0, lam = _mode_vector(lev, kv)
+    u = e0.copy()
+    O.chebyshev_smooth(lev, np.zeros_like(u), u, degree)
+    lmin = O.CHEB_LMAX / O.CHEB_RATIO
+    theta, delta = 0.5 * (O.CHEB_LMAX + lmin), 0.5 * (O.CHEB_LMAX - lmin)
+    coef = np.zeros(degree + 1)
+    coef[degree] = 1.0
+    p = np.polynomial.chebyshev.chebval((theta - lam) / delta, coef) / np.polynomial.chebyshev.chebval(
+        theta / delta, coef)
+    assert np.allclose(u, p * e0, rtol=0, atol=1e-12 * np.max(np.abs(e0)))
+
+
+def test_chebyshev_degree_one_is_damped_jacobi():
+    lev = O.assemble_level(2, 8)
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(lev.A.shape[0])
+    u0 = rng.standard_normal(lev.A.shape[0])
+    u = u0.copy()
+    O.chebyshev_smooth(lev, b, u, 1)
+    omega = 1.0 / (0.5 * (O.CHEB_LMAX + O.CHEB_LMAX / O.CHEB_RATIO))
+    assert np.allclose(u, u0 + omega * (b - lev.A @ u0) / lev.diag, rtol=1e-14, atol=1e-14)
+
+
+def test_chebyshev_damps_the_upper_spectrum():
+    """The smoothing factor: every mode with D^{-1}A eigenvalue in [lmax/ratio, 2) is
+    reduced at least by 1 / T_k(theta/delta) for degree k."""
+    lev = O.assemble_level(2, 16)
+    degree = 2
+    lmin = O.CHEB_LMAX / O.CHEB_RATIO
+    theta, delta = 0.5 * (O.CHEB_LMAX + lmin), 0.5 * (O.CHEB_LMAX - lmin)
+    bound = 1.0 / math.cosh(degree * math.acosh(theta / delta))
+    worst = 0.0
+    for kx in range(1, 16):
+        for ky in range(1, 16):
+            e0, lam = _mode_vector(lev, (kx, ky))
+            if lam < lmin:
+                continue
+            u = e0.copy()
+            O.chebyshev_smooth(lev, np.zeros_like(u), u, degree)
+            worst = max(worst, np.linalg.norm(u) / np.linalg.norm(e0))
+    assert worst <= bound * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("dim,H,r,lo", [(2, 4, 5, 4), (3, 4, 4, 4)])
+def test_chebyshev_vcycle_contraction_is_mesh_independent(dim, H, r, lo):
+    hier = O.build_hierarchy(dim, H, r)
+    thetas = []
+    for k in range(lo, r + 2):
+        lev = hier.level(k)
+        u = np.random.default_rng(0).standard_normal(lev.A.shape[0])
+        z = np.zeros_like(u)
+        prev = None
+        for _ in range(8):
+            u = O.vcycle(hier, k, z, u, smoother="chebyshev")
+            e = O.energy_norm(lev, u)
+            if prev is not None:
+                ratio = e / prev
+            prev = e
+        thetas.append(ratio)
+    assert max(thetas) < 0.5
+    assert max(thetas[-2:]) / min(thetas[-2:]) < 1.1
+
+
+@pytest.mark.parametrize("dim,H,r,kind,m", [(2, 4, 4, "cubic", 2), (3, 4, 2, "expm1", 3)])
+def test_fmg_with_chebyshev_reaches_discretization_accuracy(dim, H, r, kind, m):
+    """With degree-2 Chebyshev smoothing the 3D V-cycle contracts by about 0.33 (red-black
+    Gauss-Seidel: 0.26), so the 3D case takes m = 3 cycles per correction step."""
+    prob = W.Problem(dim=dim, coarse_cells=H, refinements=r, f=kind, a=1.0,
+                     modes=[((1,) * dim, 1.0), ((2, 1, 3)[:dim], 0.5)])
+    hier = O.build_hierarchy(dim, H, r)
+    g = prob.g_nodal()
+    res = O.fmg(hier, g, prob.f, prob.a, m=m, smoother="chebyshev")
+    lev = hier.level(r + 1)
+    ub, _ = O.newton_full(lev, O.load_vector(lev, g), prob.f, prob.a, U0=res.u[-1])
+    e_alg = O.discrete_l2(lev, res.u[-1] - ub)
+    e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star()))
+    assert e_alg <= 0.1 * e_disc, (e_alg, e_disc)
