@@ -1347,13 +1347,13 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
   const int ncell = (int)ipow(coarse_cells, dim);
   const int sfine = 1 << (level - 1);
-  // column chunks of up to 32 nodes; on small levels shorter ones, until there are enough
-  // items for one warp per SM sub-partition (each chunk costs one moment-to-channel
-  // conversion, so they are no shorter than that needs)
+  // column chunks of up to 32 nodes; on smaller levels shorter ones, until every
+  // co-resident thread has an item (each chunk costs one moment-to-channel conversion, so
+  // they are no shorter than that needs, and at least 2 nodes long)
   const long long ncol = ipow(sfine, dim - 1);
-  const long long target = (long long)(ab.sms > 0 ? ab.sms : 1) * 4 * 32;
+  const long long target = (long long)ab.bpc * nt * ncell;
   int chunk = sfine < 32 ? sfine : 32;
-  while (chunk > 1 && ncol * (sfine / chunk) * ncell < target) chunk >>= 1;
+  while (chunk > 2 && ncol * (sfine / chunk) * ncell < target) chunk >>= 1;
   const long long items = ncol * (sfine / chunk);
   // blocks per cell: about one chunk per thread; when that leaves blocks unfilled, the
   // chunks are spread over all co-resident blocks of the cell instead
