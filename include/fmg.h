@@ -77,6 +77,13 @@ typedef enum {
                           threads), which changes the convergence rate, not the solution */
 } fmg_precision;
 
+typedef enum {
+  FMG_SMOOTHER_RBGS = 0,       /* red-black Gauss-Seidel sweeps (nu_pre / nu_post sweeps) */
+  FMG_SMOOTHER_CHEBYSHEV = 1   /* Chebyshev-Jacobi: the three-term Chebyshev iteration on D^{-1}A
+                                  over [1/2, 2] (2 bounds that spectrum on these meshes), nu_pre /
+                                  nu_post steps of one colour-free stencil pass each (<= 16) */
+} fmg_smoother;
+
 typedef struct {
   int dim;             /* 2 or 3 */
   int coarse_cells;    /* 1/H: cells per side of T_H; even; 2D <= 8, 3D <= 4 (the augmented
@@ -93,6 +100,7 @@ typedef struct {
   int newton_maxit;    /* augmented Newton iteration cap (<= 64) */
   double level1_tol;   /* same rule for the exact solve on level 1 */
   int level1_maxit;    /* level-1 Newton iteration cap (<= 64) */
+  int smoother;        /* fmg_smoother of the multigrid cycles */
 } fmg_params;
 
 typedef struct {
@@ -188,7 +196,9 @@ int fmg_level_cells(const fmg_ctx* c, int level);
  * ------------------------------------------------------------------------------------- */
 
 /* `sweeps` red-black Gauss-Seidel sweeps on A_k u = b at level k (the smoother of the
- * multigrid steps of Algorithm 3.1 step 1).  order 0: red then black; 1: black then red. */
+ * multigrid steps of Algorithm 3.1 step 1).  order 0: red then black; 1: black then red.
+ * On a context with FMG_SMOOTHER_CHEBYSHEV: `sweeps` Chebyshev-Jacobi steps (order
+ * ignored); the FP32 form then needs an FMG_PREC_MIXED context (its FP32 scratch). */
 fmg_status fmg_op_smooth(fmg_ctx* c, int level, const double* b, double* u, int sweeps, int order);
 fmg_status fmg_op_smooth_f32(fmg_ctx* c, int level, const float* b, float* u, int sweeps, int order);
 

@@ -27,7 +27,12 @@ struct fmg_ctx {
   double* g[kMaxLevels] = {};
   float* u32[kMaxLevels] = {};
   float* b32[kMaxLevels] = {};
-  float* u32b[kMaxLevels] = {};   // second FP32 buffer: output of the fused pre-smoothing kernel
+  float* u32b[kMaxLevels] = {};   // second FP32 buffer: output of the fused pre-smoothing kernel,
+                                  // or the Chebyshev smoother's second iterate (mixed path)
+  float* d32[kMaxLevels] = {};    // Chebyshev step direction (mixed path)
+  double* ua[kMaxLevels] = {};    // Chebyshev second iterate and direction (FP64 path and ops)
+  double* dd[kMaxLevels] = {};
+  ChebCoef cheb = {};
   double* Ainv = nullptr;
   DevState* st = nullptr;
   AugBuffers ab = {};
@@ -99,6 +104,9 @@ const char* validate(const fmg_params* p) {
   if (!(p->newton_tol > 0.0) || !(p->level1_tol > 0.0)) return "tolerances must be > 0";
   if (p->newton_maxit < 1 || p->newton_maxit > kMaxNewton) return "newton_maxit must be in 1..64";
   if (p->level1_maxit < 1 || p->level1_maxit > kMaxNewton) return "level1_maxit must be in 1..64";
+  if (p->smoother != FMG_SMOOTHER_RBGS && p->smoother != FMG_SMOOTHER_CHEBYSHEV) return "unknown smoother";
+  if (p->smoother == FMG_SMOOTHER_CHEBYSHEV && (p->nu_pre > kMaxCheb || p->nu_post > kMaxCheb))
+    return "Chebyshev smoothing takes at most 16 steps";
   return nullptr;
 }
 
@@ -127,10 +135,19 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
     float* u32 = nullptr;
     float* b32 = nullptr;
     float* u32b = nullptr;
+    float* d32 = nullptr;
+    double* ua = nullptr;
+    double* dd = nullptr;
+    const bool cheb = p->smoother == FMG_SMOOTHER_CHEBYSHEV;
     if (p->precision == FMG_PREC_MIXED) {
       u32 = (float*)take(nodes * 4);
       b32 = (float*)take(nodes * 4);
-      if (fused_cycle_supported(p->dim, p->nu_pre, p->nu_post)) u32b = (float*)take(nodes * 4);
+      if (cheb || fused_cycle_supported(p->dim, p->nu_pre, p->nu_post)) u32b = (float*)take(nodes * 4);
+      if (cheb) d32 = (float*)take(nodes * 4);
+    }
+    if (cheb) {
+      ua = (double*)take(nodes * 8);
+      dd = (double*)take(nodes * 8);
     }
     if (c && base) {
       c->u[k] = u;
@@ -139,6 +156,9 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
       c->u32[k] = u32;
       c->b32[k] = b32;
       c->u32b[k] = u32b;
+      c->d32[k] = d32;
+      c->ua[k] = ua;
+      c->dd[k] = dd;
     }
   }
   const int m = p->coarse_cells - 1;
@@ -207,13 +227,38 @@ thread_local const char* t_site = nullptr;
   } while (0)
 
 // ------------------------------------------------------------------ schedule pieces
+const ChebCoef* cheb_coef(const fmg_ctx* c) {
+  return c->p.smoother == FMG_SMOOTHER_CHEBYSHEV ? &c->cheb : nullptr;
+}
+
+// `steps` Chebyshev-Jacobi steps on A u = b at level j (one stencil pass each, the iterate
+// alternating between u and alt, d the step direction); the result ends in u.
+template <typename T>
+cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int steps, bool top) {
+  const LevelGeo g = c->geo[j - 1];
+  T* cur = u;
+  T* oth = alt;
+  for (int k = 0; k < steps; ++k) {
+    int slot = -1;
+    if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
+    TRY(launch_cheb<T>(c->p.dim, g, cur, oth, d, b, c->cheb.cd[k], c->cheb.cr[k], k == 0, c->stream));
+    TRY(tend(c, slot));
+    T* t = cur;
+    cur = oth;
+    oth = t;
+  }
+  if (cur != u) TRY(launch_copy_t<T>(cur, u, g.nodes, c->stream));
+  return cudaSuccess;
+}
+
 // Largest level handled by the one-CTA coarse cycle: its level arrays (u and b of every level
 // up to it) must fit in shared memory; 2D up to 64 cells per side, 3D up to 16.
 template <typename T>
 int coarse_cycle_top(const fmg_ctx* c) {
   const int nmax = c->p.dim == 2 ? 64 : 16;
   int j = 1;
-  while (j < c->nlev && c->geo[j].n <= nmax && coarse_cycle_smem<T>(c->p.dim, c->p.coarse_cells, j + 1) <= 200 * 1024)
+  while (j < c->nlev && c->geo[j].n <= nmax &&
+         coarse_cycle_smem<T>(c->p.dim, c->p.coarse_cells, j + 1, c->p.smoother == FMG_SMOOTHER_CHEBYSHEV) <= 200 * 1024)
     ++j;
   return j;
 }
@@ -226,11 +271,14 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
     return cudaSuccess;
   }
   if (j <= coarse_cycle_top<double>(c)) {
-    TRY(launch_coarse_cycle<double>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s));
+    TRY(launch_coarse_cycle<double>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv,
+                                    cheb_coef(c), s));
     return cudaSuccess;
   }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
-  for (int it = 0; it < c->p.nu_pre; ++it) {
+  const bool cheb = c->p.smoother == FMG_SMOOTHER_CHEBYSHEV;
+  if (cheb) TRY(cheb_steps<double>(c, j, u, c->ua[j - 1], c->dd[j - 1], b, c->p.nu_pre, top));
+  for (int it = 0; !cheb && it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     TRY(launch_rbgs<double>(dim, gf, u, b, 0, s));
@@ -240,7 +288,8 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
   TRY(launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s));
   TRY(vcycle(c, j - 1, c->u[j - 2], c->b[j - 2]));
   TRY(launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s));
-  for (int it = 0; it < c->p.nu_post; ++it) {
+  if (cheb) TRY(cheb_steps<double>(c, j, u, c->ua[j - 1], c->dd[j - 1], b, c->p.nu_post, top));
+  for (int it = 0; !cheb && it < c->p.nu_post; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     TRY(launch_rbgs<double>(dim, gf, u, b, 1, s));
@@ -263,7 +312,7 @@ cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
   }
   if (j <= coarse_cycle_top<float>(c)) {
     TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, c->u32[j - 1], c->b32[j - 1], c->p.nu_pre,
-                                   c->p.nu_post, c->Ainv, s));
+                                   c->p.nu_post, c->Ainv, cheb_coef(c), s));
     if (u64_top) TRY(launch_add_f32(c->geo[j - 1], dim, u64_top, c->u32[j - 1], s));
     return cudaSuccess;
   }
@@ -290,11 +339,14 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
     return cudaSuccess;
   }
   if (j <= coarse_cycle_top<float>(c)) {
-    TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, s));
+    TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv,
+                                   cheb_coef(c), s));
     return cudaSuccess;
   }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
-  for (int it = 0; it < c->p.nu_pre; ++it) {
+  const bool cheb = c->p.smoother == FMG_SMOOTHER_CHEBYSHEV;
+  if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_pre, top));
+  for (int it = 0; !cheb && it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     TRY(launch_rbgs<float>(dim, gf, u, b, 0, s));
@@ -304,7 +356,8 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
   TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s));
   TRY(vcycle32(c, j - 1));
   TRY(launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s));
-  for (int it = 0; it < c->p.nu_post; ++it) {
+  if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_post, top));
+  for (int it = 0; !cheb && it < c->p.nu_post; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     TRY(launch_rbgs<float>(dim, gf, u, b, 1, s));
@@ -320,7 +373,7 @@ cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
   const LevelGeo g = c->geo[k - 1];
   // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update
   TRY(launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream));
-  if (c->u32b[k - 1]) return vcycle32_fused(c, k, u);
+  if (c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS) return vcycle32_fused(c, k, u);
   TRY(vcycle32(c, k, true));
   TRY(launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream));
   return cudaSuccess;
@@ -465,6 +518,7 @@ void fmg_default_params(fmg_params* p) {
   p->newton_maxit = 20;
   p->level1_tol = 1e-6;
   p->level1_maxit = 50;
+  p->smoother = FMG_SMOOTHER_RBGS;
 }
 
 fmg_status fmg_workspace_bytes(const fmg_params* p, size_t* bytes) {
@@ -525,6 +579,7 @@ fmg_status fmg_create(const fmg_params* p, const double* g_fine, int g_on_device
   }
   c->arena_bytes = need;
   layout(c, p, (char*)c->arena);
+  c->cheb = cheb_coefficients();
   fmg_status s = FMG_OK;
   e = cudaMemsetAsync(c->arena, 0, need, c->stream);
   if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
@@ -778,6 +833,11 @@ const double* fmg_solution(const fmg_ctx* c) { return c ? c->u[c->nlev - 1] : nu
 fmg_status fmg_op_smooth(fmg_ctx* c, int level, const double* b, double* u, int sweeps, int order) {
   if (fmg_status s = check_level(c, level, 1)) return s;
   if (!b || !u || sweeps < 0) return fail(c, FMG_ERR_INVALID, "bad smoother arguments");
+  if (c->p.smoother == FMG_SMOOTHER_CHEBYSHEV) {
+    if (sweeps > kMaxCheb) return fail(c, FMG_ERR_INVALID, "Chebyshev smoothing takes at most 16 steps");
+    CK(c, cheb_steps<double>(c, level, u, c->ua[level - 1], c->dd[level - 1], b, sweeps, false));
+    return read_state(c, nullptr, false);
+  }
   const int first = order ? 1 : 0;
   for (int i = 0; i < sweeps; ++i) {
     CK(c, launch_rbgs<double>(c->p.dim, c->geo[level - 1], u, b, first, c->stream));
@@ -789,6 +849,12 @@ fmg_status fmg_op_smooth(fmg_ctx* c, int level, const double* b, double* u, int 
 fmg_status fmg_op_smooth_f32(fmg_ctx* c, int level, const float* b, float* u, int sweeps, int order) {
   if (fmg_status s = check_level(c, level, 1)) return s;
   if (!b || !u || sweeps < 0) return fail(c, FMG_ERR_INVALID, "bad smoother arguments");
+  if (c->p.smoother == FMG_SMOOTHER_CHEBYSHEV) {
+    if (sweeps > kMaxCheb) return fail(c, FMG_ERR_INVALID, "Chebyshev smoothing takes at most 16 steps");
+    if (!c->d32[level - 1]) return fail(c, FMG_ERR_INVALID, "FP32 Chebyshev smoothing needs a mixed-precision context");
+    CK(c, cheb_steps<float>(c, level, u, c->u32b[level - 1], c->d32[level - 1], b, sweeps, false));
+    return read_state(c, nullptr, false);
+  }
   const int first = order ? 1 : 0;
   for (int i = 0; i < sweeps; ++i) {
     CK(c, launch_rbgs<float>(c->p.dim, c->geo[level - 1], u, b, first, c->stream));

@@ -147,13 +147,32 @@ cudaError_t launch_coarse_solve_f64(int dim, LevelGeo g1, const double* Ainv, co
 cudaError_t launch_coarse_solve_f32(int dim, LevelGeo g1, const double* Ainv, const float* b, float* u,
                                     cudaStream_t s);
 
-// The whole V-cycle on levels jtop..1 in one CTA with shared-memory level arrays (level j
-// has n0 << (j-1) cells per side); u (in/out) and b are level jtop's nodal arrays.
+// Chebyshev-Jacobi smoothing, the colour-free alternative smoother: step k of the three-term
+// Chebyshev iteration on D^{-1} A over [lmax/4, lmax], lmax = 2, is
+//   z = D^{-1}(b - A u),  d <- cd[k] d + cr[k] z  (cd[0] = 0),  u <- u + d.
+constexpr int kMaxCheb = 16;
+struct ChebCoef {
+  double cd[kMaxCheb];
+  double cr[kMaxCheb];
+};
+// Coefficients of steps 0..kMaxCheb-1 (host).
+ChebCoef cheb_coefficients();
+// One Chebyshev step on level geometry g: reads u (stencil), b and d (k > 0), writes uo and d.
 template <typename T>
-size_t coarse_cycle_smem(int dim, int n0, int jtop);
+cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr, bool first,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s);
+
+// The whole V-cycle on levels jtop..1 in one CTA with shared-memory level arrays (level j
+// has n0 << (j-1) cells per side); u (in/out) and b are level jtop's nodal arrays.  cheb:
+// NULL for red-black Gauss-Seidel smoothing, else Chebyshev-Jacobi steps (nu_pre / nu_post
+// of them), which need two more arrays per level.
+template <typename T>
+size_t coarse_cycle_smem(int dim, int n0, int jtop, bool cheb);
 template <typename T>
 cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int nu_pre, int nu_post,
-                                const double* Ainv, cudaStream_t s);
+                                const double* Ainv, const ChebCoef* cheb, cudaStream_t s);
 
 // level-1 setup: Ainv = A_1^{-1} (dense, N_1 x N_1) by Cholesky; flags on failure
 cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s);

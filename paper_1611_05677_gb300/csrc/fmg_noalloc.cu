@@ -69,7 +69,7 @@ struct Ctx {
 int coarse_top(const Ctx& c, int level) {
   const int nmax = c.dim == 2 ? 64 : 16;
   int j = 1;
-  while (j < level && c.geo(j + 1).n <= nmax && coarse_cycle_smem<double>(c.dim, c.nc, j + 1) <= 200 * 1024) ++j;
+  while (j < level && c.geo(j + 1).n <= nmax && coarse_cycle_smem<double>(c.dim, c.nc, j + 1, false) <= 200 * 1024) ++j;
   return j;
 }
 
@@ -77,7 +77,7 @@ cudaError_t vcycle(const Ctx& c, int j, int level, double* u, const double* b) {
   cudaError_t e;
   if (j == 1) return launch_coarse_solve_f64(c.dim, c.geo(1), c.ainv, b, u, c.s);
   if (j <= coarse_top(c, level))
-    return launch_coarse_cycle<double>(c.dim, c.nc, j, u, b, c.nu_pre, c.nu_post, c.ainv, c.s);
+    return launch_coarse_cycle<double>(c.dim, c.nc, j, u, b, c.nu_pre, c.nu_post, c.ainv, nullptr, c.s);
   const LevelGeo gf = c.geo(j), gc = c.geo(j - 1);
   for (int it = 0; it < c.nu_pre; ++it) {
     if ((e = launch_rbgs<double>(c.dim, gf, u, b, 0, c.s)) != cudaSuccess) return e;

@@ -56,6 +56,34 @@ __global__ void k_rbgs3(T* __restrict__ u, const T* __restrict__ b, int n, int c
   u[c] = (b[c] * bscale + s) * inv6;
 }
 
+// ------------------------------------------------------------------ Chebyshev-Jacobi step
+// z = D^{-1}(b - A u) = (b / sigma + sum of the 2d neighbours) / 2d - u; d <- cd d + cr z;
+// uo = u + d.  Every interior node at once (colour-free): u is read, uo written.
+template <typename T, int D>
+__global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restrict__ d, const T* __restrict__ b, int n,
+                       T bscale, T cd, T cr, int first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int j = blockIdx.y + 1;
+  const int l = D == 3 ? blockIdx.z + 1 : 0;
+  if (i > n - 1) return;
+  const long long np = n + 1;
+  const long long pl = np * np;
+  const long long c = ((long long)l * np + j) * np + i;
+  T s = (u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np]);
+  if (D == 3) s += u[c - pl] + u[c + pl];
+  const T uc = u[c];
+  const T z = (b[c] * bscale + s) * (T(1) / T(2 * D)) - uc;
+  const T dn = first ? cr * z : cd * d[c] + cr * z;
+  d[c] = dn;
+  uo[c] = uc + dn;
+}
+
+template <typename T>
+__global__ void k_copy_t(const T* __restrict__ s, T* __restrict__ d, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = s[i];
+}
+
 // ------------------------------------------------------------------ residual + restriction
 template <typename T>
 __device__ __forceinline__ T res2(const T* __restrict__ u, const T* __restrict__ b, long long c, long long np) {
@@ -262,6 +290,8 @@ struct CoarseLevel {
   int np;       // n + 1
   T* u;
   T* b;
+  T* ua;        // Chebyshev smoothing: second iterate buffer and the step direction
+  T* d;
 };
 
 // One colour of a red-black sweep: items are (p, j[, l]) with i = 2p + 1 or 2p + 2, decoded
@@ -285,6 +315,39 @@ __device__ __forceinline__ void cta_rbgs(const CoarseLevel<T, D>& L, int colour,
   }
 }
 
+// `steps` Chebyshev-Jacobi steps on level L (colour-free: every interior node per step, the
+// iterate alternating between u and ua); the result ends in L.u.
+template <typename T, int D>
+__device__ void cta_cheb(const CoarseLevel<T, D>& L, const ChebCoef& cf, int steps, T bscale, T inv2d) {
+  const int n = L.n, np = L.np, lg = L.lg;
+  const int total = D == 2 ? (1 << (2 * lg)) : (1 << (3 * lg));
+  T* u = L.u;
+  T* ua = L.ua;
+  for (int k = 0; k < steps; ++k) {
+    const T cd = (T)cf.cd[k], cr = (T)cf.cr[k];
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int i = t & (n - 1), j = (t >> lg) & (n - 1), l = D == 3 ? (t >> (2 * lg)) : 0;
+      if (i == 0 || j == 0 || (D == 3 && l == 0)) continue;
+      const int c = (l * np + j) * np + i;
+      T s = (u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np]);
+      if (D == 3) s += u[c - np * np] + u[c + np * np];
+      const T z = (L.b[c] * bscale + s) * inv2d - u[c];
+      const T dn = k == 0 ? cr * z : cd * L.d[c] + cr * z;
+      L.d[c] = dn;
+      ua[c] = u[c] + dn;
+    }
+    __syncthreads();
+    T* t2 = u;
+    u = ua;
+    ua = t2;
+  }
+  if (u != L.u) {
+    const int nodes = D == 2 ? np * np : np * np * np;
+    for (int c = threadIdx.x; c < nodes; c += blockDim.x) L.u[c] = u[c];
+    __syncthreads();
+  }
+}
+
 template <typename T, int D>
 __device__ __forceinline__ T cta_res(const CoarseLevel<T, D>& L, int c, T sigma) {
   const int np = L.np;
@@ -295,7 +358,7 @@ __device__ __forceinline__ T cta_res(const CoarseLevel<T, D>& L, int c, T sigma)
 
 template <typename T, int D>
 __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, const T* __restrict__ bg, int n0, int jtop, int nu_pre,
-                                int nu_post, const double* __restrict__ Ainv) {
+                                int nu_post, const double* __restrict__ Ainv, int cheb, ChebCoef cf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   CoarseLevel<T, D> L[8];
@@ -310,7 +373,9 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       L[j - 1].np = np;
       L[j - 1].u = sm + off;
       L[j - 1].b = sm + off + nodes;
-      off += 2 * nodes;
+      L[j - 1].ua = cheb ? sm + off + 2 * nodes : nullptr;
+      L[j - 1].d = cheb ? sm + off + 3 * nodes : nullptr;
+      off += (cheb ? 4 : 2) * nodes;
     }
   }
   {
@@ -320,10 +385,13 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       top.u[i] = ug[i];
       top.b[i] = bg[i];
     }
-    // lower levels: zero (boundary rings stay zero)
-    for (int j = 1; j < jtop; ++j) {
+    // lower levels: zero (boundary rings stay zero); the Chebyshev buffers of every level too
+    for (int j = 1; j <= jtop; ++j) {
       const int nn = D == 2 ? L[j - 1].np * L[j - 1].np : L[j - 1].np * L[j - 1].np * L[j - 1].np;
-      for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) L[j - 1].u[i] = T(0);
+      if (j < jtop)
+        for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) L[j - 1].u[i] = T(0);
+      if (cheb)
+        for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) L[j - 1].ua[i] = T(0);
     }
   }
   __syncthreads();
@@ -334,11 +402,15 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
     const CoarseLevel<T, D>& C = L[j - 2];
     const T bscale = D == 2 ? T(1) : T(F.n);
     const T sigma = D == 2 ? T(1) : T(1) / T(F.n);
-    for (int it = 0; it < nu_pre; ++it) {
-      cta_rbgs<T, D>(F, 0, bscale, inv2d);
-      __syncthreads();
-      cta_rbgs<T, D>(F, 1, bscale, inv2d);
-      __syncthreads();
+    if (cheb) {
+      cta_cheb<T, D>(F, cf, nu_pre, bscale, inv2d);
+    } else {
+      for (int it = 0; it < nu_pre; ++it) {
+        cta_rbgs<T, D>(F, 0, bscale, inv2d);
+        __syncthreads();
+        cta_rbgs<T, D>(F, 1, bscale, inv2d);
+        __syncthreads();
+      }
     }
     // b_c = P^T (b - A u), u_c = 0: items (I, J[, K]) over [0, n_c)^d, boundary skipped
     const int lgc = C.lg;
@@ -404,11 +476,15 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       F.u[(l * F.np + jj) * F.np + i] += T(0.5) * (C.u[a] + C.u[z]);
     }
     __syncthreads();
-    for (int it = 0; it < nu_post; ++it) {
-      cta_rbgs<T, D>(F, 1, bscale, inv2d);
-      __syncthreads();
-      cta_rbgs<T, D>(F, 0, bscale, inv2d);
-      __syncthreads();
+    if (cheb) {
+      cta_cheb<T, D>(F, cf, nu_post, bscale, inv2d);
+    } else {
+      for (int it = 0; it < nu_post; ++it) {
+        cta_rbgs<T, D>(F, 1, bscale, inv2d);
+        __syncthreads();
+        cta_rbgs<T, D>(F, 0, bscale, inv2d);
+        __syncthreads();
+      }
     }
   }
   {
@@ -526,36 +602,80 @@ cudaError_t launch_coarse_solve_f32(int dim, LevelGeo g1, const double* Ainv, co
 }
 
 template <typename T>
-size_t coarse_cycle_smem(int dim, int n0, int jtop) {
+size_t coarse_cycle_smem(int dim, int n0, int jtop, bool cheb) {
   size_t tot = 0;
   for (int j = 1; j <= jtop; ++j) {
     const long long np = (long long)(n0 << (j - 1)) + 1;
-    tot += 2 * (size_t)ipow(np, dim);
+    tot += (cheb ? 4 : 2) * (size_t)ipow(np, dim);
   }
   return tot * sizeof(T);
 }
 
 template <typename T>
 cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int nu_pre, int nu_post,
-                                const double* Ainv, cudaStream_t s) {
-  const size_t smem = coarse_cycle_smem<T>(dim, n0, jtop);
+                                const double* Ainv, const ChebCoef* cheb, cudaStream_t s) {
+  if (cheb && (nu_pre > kMaxCheb || nu_post > kMaxCheb)) return cudaErrorInvalidValue;
+  const size_t smem = coarse_cycle_smem<T>(dim, n0, jtop, cheb != nullptr);
+  const ChebCoef cf = cheb ? *cheb : ChebCoef{};
   cudaError_t e;
   if (dim == 2) {
     if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 2>, smem)) != cudaSuccess) return e;
-    k_vcycle_coarse<T, 2><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv);
+    k_vcycle_coarse<T, 2><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, cheb ? 1 : 0, cf);
   } else {
     if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 3>, smem)) != cudaSuccess) return e;
-    k_vcycle_coarse<T, 3><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv);
+    k_vcycle_coarse<T, 3><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, cheb ? 1 : 0, cf);
   }
   return cudaGetLastError();
 }
 
-template size_t coarse_cycle_smem<double>(int, int, int);
-template size_t coarse_cycle_smem<float>(int, int, int);
+ChebCoef cheb_coefficients() {
+  // lmax = 2 bounds the spectrum of D^{-1}A for the 2d+1-point stiffness; the smoother
+  // targets [lmax/4, lmax]
+  const double lmax = 2.0, lmin = lmax / 4.0;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sig = theta / delta;
+  ChebCoef c{};
+  c.cd[0] = 0.0;
+  c.cr[0] = 1.0 / theta;
+  double rho = 1.0 / sig;
+  for (int k = 1; k < kMaxCheb; ++k) {
+    const double rn = 1.0 / (2.0 * sig - rho);
+    c.cd[k] = rn * rho;
+    c.cr[k] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  return c;
+}
+
+template <typename T>
+cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr, bool first,
+                        cudaStream_t s) {
+  const int n = g.n;
+  const unsigned gx = cdiv(n - 1, kBlock);
+  if (dim == 2)
+    k_cheb<T, 2><<<dim3(gx, n - 1), kBlock, 0, s>>>(u, uo, d, b, n, T(1), T(cd), T(cr), first ? 1 : 0);
+  else
+    k_cheb<T, 3><<<dim3(gx, n - 1, n - 1), kBlock, 0, s>>>(u, uo, d, b, n, T(n), T(cd), T(cr), first ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s) {
+  k_copy_t<T><<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+template size_t coarse_cycle_smem<double>(int, int, int, bool);
+template size_t coarse_cycle_smem<float>(int, int, int, bool);
 template cudaError_t launch_coarse_cycle<double>(int, int, int, double*, const double*, int, int, const double*,
-                                                 cudaStream_t);
+                                                 const ChebCoef*, cudaStream_t);
 template cudaError_t launch_coarse_cycle<float>(int, int, int, float*, const float*, int, int, const double*,
-                                                cudaStream_t);
+                                                const ChebCoef*, cudaStream_t);
+template cudaError_t launch_cheb<double>(int, LevelGeo, const double*, double*, double*, const double*, double, double,
+                                         bool, cudaStream_t);
+template cudaError_t launch_cheb<float>(int, LevelGeo, const float*, float*, float*, const float*, double, double, bool,
+                                        cudaStream_t);
+template cudaError_t launch_copy_t<double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_copy_t<float>(const float*, float*, long long, cudaStream_t);
 template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t);
 template cudaError_t launch_rbgs<float>(int, LevelGeo, float*, const float*, int, cudaStream_t);
 template cudaError_t launch_residual_restrict<double, double>(int, LevelGeo, const double*, const double*, LevelGeo,

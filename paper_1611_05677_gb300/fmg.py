@@ -28,13 +28,14 @@ STATUS_NAMES = {0: "FMG_OK", 1: "FMG_ERR_INVALID", 2: "FMG_ERR_OOM", 3: "FMG_ERR
 
 NONLIN = {"cubic": 0, "expm1": 1, "linear": 2, "signed_pow32": 3, "neg_exp_neg": 4}
 PREC = {"fp64": 0, "mixed": 1}
+SMOOTHER = {"rbgs": 0, "chebyshev": 1}
 
 
 class fmg_params(ctypes.Structure):
     _fields_ = [("dim", c_int), ("coarse_cells", c_int), ("refinements", c_int), ("f", c_int),
                 ("f_scale", c_double), ("m_vcycles", c_int), ("nu_pre", c_int), ("nu_post", c_int),
                 ("p_corrections", c_int), ("precision", c_int), ("newton_tol", c_double),
-                ("newton_maxit", c_int), ("level1_tol", c_double), ("level1_maxit", c_int)]
+                ("newton_maxit", c_int), ("level1_tol", c_double), ("level1_maxit", c_int), ("smoother", c_int)]
 
 
 class fmg_stats(ctypes.Structure):
@@ -388,6 +389,8 @@ def make_params(problem=None, **kw) -> fmg_params:
             v = NONLIN[v]
         if k == "precision" and isinstance(v, str):
             v = PREC[v]
+        if k == "smoother" and isinstance(v, str):
+            v = SMOOTHER[v]
         setattr(p, k, v)
     return p
 
