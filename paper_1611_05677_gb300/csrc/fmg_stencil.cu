@@ -58,24 +58,38 @@ __global__ void k_rbgs3(T* __restrict__ u, const T* __restrict__ b, int n, int c
 
 // ------------------------------------------------------------------ Chebyshev-Jacobi step
 // z = D^{-1}(b - A u) = (b / sigma + sum of the 2d neighbours) / 2d - u; d <- cd d + cr z;
-// uo = u + d.  Every interior node at once (colour-free): u is read, uo written.
+// uo = u + d.  Every interior node at once (colour-free): u is read, uo written.  A thread
+// walks a strip of `strip` (<= kChebStrip) nodes along the outermost axis (y in 2D, z in 3D),
+// keeping the previous, current and next values of u on that axis in registers, so u is read
+// once per node from memory along the strip plus the in-plane neighbours from cache.
+constexpr int kChebStrip = 8;
+
 template <typename T, int D>
 __global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restrict__ d, const T* __restrict__ b, int n,
-                       T bscale, T cd, T cr, int first) {
+                       T bscale, T cd, T cr, int first, int strip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int j = blockIdx.y + 1;
-  const int l = D == 3 ? blockIdx.z + 1 : 0;
+  const int j = D == 3 ? blockIdx.y + 1 : 0;                 // in-plane row (3D only)
+  const int z0 = (D == 2 ? blockIdx.y : blockIdx.z) * strip + 1;   // strip start (outer axis)
   if (i > n - 1) return;
   const long long np = n + 1;
-  const long long pl = np * np;
-  const long long c = ((long long)l * np + j) * np + i;
-  T s = (u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np]);
-  if (D == 3) s += u[c - pl] + u[c + pl];
-  const T uc = u[c];
-  const T z = (b[c] * bscale + s) * (T(1) / T(2 * D)) - uc;
-  const T dn = first ? cr * z : cd * d[c] + cr * z;
-  d[c] = dn;
-  uo[c] = uc + dn;
+  const long long so = D == 2 ? np : np * np;                // stride of the outer axis
+  long long c = (D == 2 ? (long long)z0 * np : ((long long)z0 * np + j) * np) + i;
+  T um = u[c - so], uc = u[c];
+  const T inv2d = T(1) / T(2 * D);
+#pragma unroll
+  for (int r = 0; r < kChebStrip; ++r) {
+    if (r >= strip || z0 + r > n - 1) break;
+    const T up = u[c + so];
+    T s = (u[c - 1] + u[c + 1]) + (um + up);
+    if (D == 3) s += u[c - np] + u[c + np];
+    const T zr = (b[c] * bscale + s) * inv2d - uc;
+    const T dn = first ? cr * zr : cd * d[c] + cr * zr;
+    d[c] = dn;
+    uo[c] = uc + dn;
+    um = uc;
+    uc = up;
+    c += so;
+  }
 }
 
 template <typename T>
@@ -651,10 +665,15 @@ cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b
                         cudaStream_t s) {
   const int n = g.n;
   const unsigned gx = cdiv(n - 1, kBlock);
+  const unsigned plane = dim == 2 ? gx : gx * (unsigned)(n - 1);
+  // the longest strip that still leaves at least 1024 blocks (small levels: one node each)
+  int strip = kChebStrip;
+  while (strip > 1 && (long long)plane * cdiv(n - 1, strip) < 1024) strip >>= 1;
+  const unsigned gs = cdiv(n - 1, strip);
   if (dim == 2)
-    k_cheb<T, 2><<<dim3(gx, n - 1), kBlock, 0, s>>>(u, uo, d, b, n, T(1), T(cd), T(cr), first ? 1 : 0);
+    k_cheb<T, 2><<<dim3(gx, gs), kBlock, 0, s>>>(u, uo, d, b, n, T(1), T(cd), T(cr), first ? 1 : 0, strip);
   else
-    k_cheb<T, 3><<<dim3(gx, n - 1, n - 1), kBlock, 0, s>>>(u, uo, d, b, n, T(n), T(cd), T(cr), first ? 1 : 0);
+    k_cheb<T, 3><<<dim3(gx, n - 1, gs), kBlock, 0, s>>>(u, uo, d, b, n, T(n), T(cd), T(cr), first ? 1 : 0, strip);
   return cudaGetLastError();
 }
 
