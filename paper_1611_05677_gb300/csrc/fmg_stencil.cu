@@ -309,23 +309,42 @@ struct CoarseLevel {
 };
 
 // One colour of a red-black sweep: items are (p, j[, l]) with i = 2p + 1 or 2p + 2, decoded
-// with shifts; rows 0 and n and out-of-range i are skipped.
+// with shifts; rows 0 and n and out-of-range i are skipped.  Nodes of one colour do not
+// couple, so a thread takes two items at a time with all loads before both stores.
+template <typename T, int D>
+__device__ __forceinline__ int cta_rb_node(const CoarseLevel<T, D>& L, int t, int colour) {
+  const int n = L.n, np = L.np, lgh = L.lg - 1;
+  const int p = t & ((1 << lgh) - 1);
+  const int j = (t >> lgh) & (n - 1);
+  const int l = D == 3 ? (t >> (lgh + L.lg)) : 0;
+  if (j == 0 || (D == 3 && l == 0)) return -1;
+  const int par = (colour + j + l) & 1;
+  const int i = par ? 2 * p + 1 : 2 * p + 2;
+  if (i > n - 1) return -1;
+  return (l * np + j) * np + i;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T cta_nbsum(const CoarseLevel<T, D>& L, int c) {
+  const int np = L.np;
+  T s = (L.u[c - 1] + L.u[c + 1]) + (L.u[c - np] + L.u[c + np]);
+  if (D == 3) s += L.u[c - np * np] + L.u[c + np * np];
+  return s;
+}
+
 template <typename T, int D>
 __device__ __forceinline__ void cta_rbgs(const CoarseLevel<T, D>& L, int colour, T bscale, T inv2d) {
-  const int n = L.n, np = L.np, lgh = L.lg - 1;
+  const int n = L.n, lgh = L.lg - 1;
   const int total = D == 2 ? (n << lgh) : (n << (lgh + L.lg));
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int p = t & ((1 << lgh) - 1);
-    const int j = (t >> lgh) & (n - 1);
-    const int l = D == 3 ? (t >> (lgh + L.lg)) : 0;
-    if (j == 0 || (D == 3 && l == 0)) continue;
-    const int par = (colour + j + l) & 1;
-    const int i = par ? 2 * p + 1 : 2 * p + 2;
-    if (i > n - 1) continue;
-    const int c = (l * np + j) * np + i;
-    T s = (L.u[c - 1] + L.u[c + 1]) + (L.u[c - np] + L.u[c + np]);
-    if (D == 3) s += L.u[c - np * np] + L.u[c + np * np];
-    L.u[c] = (L.b[c] * bscale + s) * inv2d;
+  const int step = 2 * blockDim.x;
+  for (int t = threadIdx.x; t < total; t += step) {
+    const int c1 = cta_rb_node<T, D>(L, t, colour);
+    const int c2 = t + (int)blockDim.x < total ? cta_rb_node<T, D>(L, t + blockDim.x, colour) : -1;
+    T v1 = T(0), v2 = T(0);
+    if (c1 >= 0) v1 = (L.b[c1] * bscale + cta_nbsum<T, D>(L, c1)) * inv2d;
+    if (c2 >= 0) v2 = (L.b[c2] * bscale + cta_nbsum<T, D>(L, c2)) * inv2d;
+    if (c1 >= 0) L.u[c1] = v1;
+    if (c2 >= 0) L.u[c2] = v2;
   }
 }
 
@@ -464,11 +483,12 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       b1[c] = (double)C.b[off1[c]];
     }
     __syncthreads();
-    // row r: lanes of one warp split the columns, then a shuffle sum (fixed order)
+    // row r: lanes of one warp split the columns (row r of the symmetric A_1^{-1} is read
+    // contiguously), then a shuffle sum (fixed order)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = warp; r < N; r += nw) {
       double acc = 0.0;
-      for (int c = lane; c < N; c += 32) acc = fma(Ainv[(long long)c * N + r], b1[c], acc);
+      for (int c = lane; c < N; c += 32) acc = fma(__ldg(&Ainv[(long long)r * N + c]), b1[c], acc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) C.u[off1[r]] = (T)acc;
