@@ -467,9 +467,32 @@ def augmented_newton(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarr
     raise RuntimeError("augmented Newton did not converge")
 
 
+def augmented_fixed_point(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarray, kind: str, a: float,
+                          tol: float = 1e-6, maxit: int = 60):
+    """The fixed-point iteration on (3.6), the other nonlinear solver the paper names: the
+    linear part implicit, the nonlinear term at the previous iterate,
+    B^T A_k B y_{k+1} = B^T G - B^T W f(B y_k),  B = [P_{H->k} | u~],
+    from (c, alpha) = (0, 1), with Newton's stopping rule.  It converges when the nonlinear
+    term is a contraction relative to the Galerkin stiffness (mild nonlinearities)."""
+    NH = PHk.shape[1]
+    B = sp.hstack([PHk, sp.csr_matrix(ut[:, None])]).tocsr()
+    Kaug = (B.T @ (lev.A @ B)).toarray()
+    Gaug = B.T @ G
+    fac = sla.cho_factor(Kaug, lower=True)
+    y = np.zeros(NH + 1)
+    y[-1] = 1.0
+    for it in range(1, maxit + 1):
+        y_new = sla.cho_solve(fac, Gaug - B.T @ (lev.w * f_val(kind, a, B @ y)))
+        delta = y_new - y
+        y = y_new
+        if np.max(np.abs(delta)) <= tol * max(1.0, np.max(np.abs(y))):
+            return y, B, it
+    raise RuntimeError("augmented fixed-point iteration did not converge")
+
+
 def correction_step(hier: Hierarchy, k: int, u: np.ndarray, G: np.ndarray, kind: str, a: float,
                     m: int = 2, nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-6,
-                    smoother: str = "rbgs"):
+                    smoother: str = "rbgs", nonlinear: str = "newton"):
     """u^{(l+1)} = SemilinearMG(V_H, u^{(l)}, V_{h_k}) (Algorithm 3.1)."""
     lev = hier.level(k)
     # step 1 (eq. 3.4): a(u^, v) = (g, v) - (f(x, u^{(l)}), v)
@@ -478,7 +501,8 @@ def correction_step(hier: Hierarchy, k: int, u: np.ndarray, G: np.ndarray, kind:
     for _ in range(m):                     # eq. (3.5): m multigrid steps from u^{(l)}
         ut = vcycle(hier, k, b, ut, nu_pre, nu_post, smoother)
     # step 2 (eq. 3.6): semilinear problem on V_H + span{u~}
-    y, B, iters = augmented_newton(lev, hier.P_H[k - 1], ut, G, kind, a, tol)
+    solve = augmented_fixed_point if nonlinear == "fixed_point" else augmented_newton
+    y, B, iters = solve(lev, hier.P_H[k - 1], ut, G, kind, a, tol)
     info = StepInfo(newton_iters=iters, alpha=float(y[-1]), c=y[:-1].copy(), u_tilde=ut)
     return B @ y, info
 
@@ -497,7 +521,7 @@ class FMGResult:
 
 def fmg(hier: Hierarchy, g_fine: np.ndarray, kind: str, a: float, m: int = 2, p: int = 1,
         nu_pre: int = 2, nu_post: int = 2, tol: float = 1e-6, tol_level1: float = 1e-6,
-        keep_levels: bool = True, smoother: str = "rbgs") -> FMGResult:
+        keep_levels: bool = True, smoother: str = "rbgs", nonlinear: str = "newton") -> FMGResult:
     n_levels = len(hier.levels)
     n_fine = hier.levels[-1].n
     dim = hier.dim
@@ -512,7 +536,7 @@ def fmg(hier: Hierarchy, g_fine: np.ndarray, kind: str, a: float, m: int = 2, p:
         G = load_vector(lev, restrict_nodal(g_fine, dim, n_fine, lev.n))
         u = lev.P @ u                      # u^{(0)}_{h_k} = u_{h_{k-1}} (natural inclusion)
         for _ in range(p):
-            u, info = correction_step(hier, k, u, G, kind, a, m, nu_pre, nu_post, tol, smoother)
+            u, info = correction_step(hier, k, u, G, kind, a, m, nu_pre, nu_post, tol, smoother, nonlinear)
             steps.append((k, info))
         if keep_levels:
             us.append(u)

@@ -52,7 +52,7 @@ def test_dropped_nonlinear_term_in_linearized_rhs_is_caught(monkeypatch):
     the answer only up to the V_H + span{u~} approximation, so the FMG result
     drifts from the discrete solution beyond the accuracy criterion."""
     # patch the correction step to skip the nonlinear RHS term
-    def bad_step(hier, k, u, G, kind, a, m=2, nu_pre=2, nu_post=2, tol=1e-12, smoother="rbgs"):
+    def bad_step(hier, k, u, G, kind, a, m=2, nu_pre=2, nu_post=2, tol=1e-12, smoother="rbgs", nonlinear="newton"):
         lev = hier.level(k)
         b = G.copy()
         ut = u.copy()

@@ -463,3 +463,64 @@ def test_fmg_with_chebyshev_reaches_discretization_accuracy(dim, H, r, kind, m):
     e_alg = O.discrete_l2(lev, res.u[-1] - ub)
     e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star()))
     assert e_alg <= 0.1 * e_disc, (e_alg, e_disc)
+
+
+# ---------------------------------------------------------------------------
+# Fixed-point variant of the augmented solve (the other nonlinear solver the paper names)
+# ---------------------------------------------------------------------------
+
+
+def test_augmented_fixed_point_reaches_the_newton_solution():
+    prob, hier, k, lev, G = _step_setup()
+    rng = np.random.default_rng(3)
+    ut = O.newton_full(lev, G, prob.f, prob.a)[0] + 0.05 * rng.standard_normal(lev.A.shape[0])
+    yn, B, _ = O.augmented_newton(lev, hier.P_H[k - 1], ut, G, prob.f, prob.a, tol=1e-13)
+    yf, _, it = O.augmented_fixed_point(lev, hier.P_H[k - 1], ut, G, prob.f, prob.a, tol=1e-13)
+    assert it > 3   # linear convergence: more iterations than Newton's
+    assert np.max(np.abs(B @ yf - B @ yn)) <= 1e-11 * np.max(np.abs(B @ yn))
+
+
+def test_augmented_fixed_point_contracts_at_the_linear_rate():
+    """f(u) = c u: the fixed-point map is affine, y_{k+1} - y* = -K^{-1} (c B^T W B)(y_k - y*), so
+    the increments shrink by the spectral radius of that matrix (from scipy's eigensolver)."""
+    c = 10.0
+    prob = W.Problem(dim=2, coarse_cells=4, refinements=2, f="linear", a=c, modes=[((1, 1), 1.0)])
+    hier = O.build_hierarchy(2, 4, 2)
+    k = 3
+    lev = hier.level(k)
+    G = O.load_vector(lev, prob.g_nodal())
+    rng = np.random.default_rng(8)
+    ut = rng.standard_normal(lev.A.shape[0])
+    B = sp.hstack([hier.P_H[k - 1], sp.csr_matrix(ut[:, None])]).tocsr()
+    K = (B.T @ (lev.A @ B)).toarray()
+    Mw = (B.T @ (sp.diags(lev.w * c) @ B)).toarray()
+    rho = max(abs(np.linalg.eigvals(np.linalg.solve(K, Mw))))
+    assert 0.05 < rho < 0.9
+    deltas = []
+    y = np.zeros(B.shape[1])
+    y[-1] = 1.0
+    Gaug = B.T @ G
+    for _ in range(12):
+        y_new = np.linalg.solve(K, Gaug - B.T @ (lev.w * O.f_val("linear", c, B @ y)))
+        deltas.append(np.linalg.norm(y_new - y))
+        y = y_new
+    assert abs(deltas[-1] / deltas[-2] - rho) < 1e-3 * rho
+    # and the oracle's iteration takes the same steps
+    yf, _, it = O.augmented_fixed_point(lev, hier.P_H[k - 1], ut, G, "linear", c, tol=1e-13, maxit=1000)
+    exact = B @ np.linalg.solve(K + Mw, Gaug)
+    assert np.max(np.abs(B @ yf - exact)) <= 1e-10 * np.max(np.abs(exact))
+
+
+def test_fmg_with_fixed_point_reaches_discretization_accuracy():
+    prob = W.Problem(dim=2, coarse_cells=4, refinements=4, f="cubic", a=1.0,
+                     modes=[((1, 1), 1.0), ((2, 1), 0.5)])
+    hier = O.build_hierarchy(2, 4, 4)
+    g = prob.g_nodal()
+    res = O.fmg(hier, g, prob.f, prob.a, nonlinear="fixed_point")
+    newton = O.fmg(hier, g, prob.f, prob.a)
+    lev = hier.level(5)
+    ub, _ = O.newton_full(lev, O.load_vector(lev, g), prob.f, prob.a, U0=res.u[-1])
+    e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star()))
+    assert O.discrete_l2(lev, res.u[-1] - ub) <= 0.1 * e_disc
+    assert O.discrete_l2(lev, res.u[-1] - newton.u[-1]) <= 1e-3 * e_disc
+    assert sum(i.newton_iters for _, i in res.steps) > sum(i.newton_iters for _, i in newton.steps)
