@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--max-inflight", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the launch shapes of the Chebyshev step kernel before timing")
     ap.add_argument("--smoother", default="rbgs", choices=["rbgs", "chebyshev"],
                     help="smoother of the multigrid cycles (large2d / 3d workloads)")
     return ap.parse_args()
@@ -294,6 +296,8 @@ def run_ours(args):
     log("creating solvers")
     for prec in ("mixed", "fp64"):
         s = fmg.Solver(fmg.make_params(prob, precision=prec, smoother=args.smoother, m_vcycles=m_cycles), g)
+        if args.autotune:
+            fmg.fmg_autotune(s.ctx)
         st = fmg.fmg_stats()
         s.solve(stats=st)
         solvers[prec] = s
@@ -425,6 +429,9 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD if dim == 2 else WORKLOAD_3D, "precision": "mixed",
                        "smoother": args.smoother, "instances": world,
+                       "autotuned": bool(args.autotune),
+                       "top_level_cheb_shape": (fmg.fmg_tuned_shape(solvers["mixed"].ctx, top)
+                                                if args.smoother == "chebyshev" else None),
                        "global_batch": world, "seq_len": None, "parallelism": f"independent instances x{world}",
                        "l2": "flushed between steps (512 MB write outside the timed events)",
                        "m": m_cycles, "nu": [2, 2], "p": 1},
@@ -689,11 +696,11 @@ def single_solve(args):
     from paper_1611_05677_gb300 import fmg, workloads as W
 
     prob = W.config_large_2d(refinements=args.refinements)
-    s = fmg.Solver(fmg.make_params(prob, precision=args.precision), prob.g_nodal())
+    s = fmg.Solver(fmg.make_params(prob, precision=args.precision, smoother=args.smoother), prob.g_nodal())
     st = fmg.fmg_stats()
     s.solve(stats=st)
     torch.cuda.synchronize()
-    print(json.dumps({"single_solve": prob.name, "precision": args.precision,
+    print(json.dumps({"single_solve": prob.name, "precision": args.precision, "smoother": args.smoother,
                       "newton_iters": list(st.newton_iters[:prob.levels]), "flags": int(st.flags)}))
     s.close()
 

@@ -84,6 +84,13 @@ typedef enum {
                                   nu_post steps of one colour-free stencil pass each (<= 16) */
 } fmg_smoother;
 
+typedef enum {
+  FMG_NONLINEAR_NEWTON = 0,      /* Newton on (3.6) (the mixed path: chord steps after the first) */
+  FMG_NONLINEAR_FIXED_POINT = 1  /* fixed-point iteration on (3.6): the Galerkin stiffness on
+                                    V_H + span{u~} implicit, f at the previous iterate; converges
+                                    for nonlinearities that are mild against that stiffness */
+} fmg_nonlinear_solver;
+
 typedef struct {
   int dim;             /* 2 or 3 */
   int coarse_cells;    /* 1/H: cells per side of T_H; even; 2D <= 8, 3D <= 4 (the augmented
@@ -101,6 +108,7 @@ typedef struct {
   double level1_tol;   /* same rule for the exact solve on level 1 */
   int level1_maxit;    /* level-1 Newton iteration cap (<= 64) */
   int smoother;        /* fmg_smoother of the multigrid cycles */
+  int nonlinear;       /* fmg_nonlinear_solver of the augmented problem (3.6) */
 } fmg_params;
 
 typedef struct {
@@ -173,6 +181,18 @@ fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** o
 fmg_status fmg_batch_solve(fmg_batch* b, fmg_stats* sts);
 fmg_status fmg_batch_sync(fmg_batch* b);
 fmg_status fmg_batch_destroy(fmg_batch* b);
+
+/* Autotuner of launch shapes.  For a context with FMG_SMOOTHER_CHEBYSHEV it times every
+ * candidate shape (threads per block 64..512 x nodes per thread along the outer axis 1..8)
+ * of the Chebyshev step kernel on each of the context's levels that run it, on the
+ * context's own scratch arrays, and keeps the fastest per (device, dimension, level size,
+ * precision) for the whole process: every context on the device uses them from its next
+ * graph capture (this context's captured graph is dropped).  Waits for the context stream
+ * and must not overlap other work of the context.  *tuned (optional) receives the number of
+ * levels tuned (0 for red-black smoothing, whose kernels have fixed shapes). */
+fmg_status fmg_autotune(fmg_ctx* c, int* tuned);
+/* Launch shape the context's Chebyshev step kernel uses on `level` (tuned or default). */
+fmg_status fmg_tuned_shape(const fmg_ctx* c, int level, int* block, int* strip);
 
 /* Frees the context (and the workspace when the library allocated it).  NULL-safe. */
 fmg_status fmg_destroy(fmg_ctx* c);

@@ -105,6 +105,8 @@ const char* validate(const fmg_params* p) {
   if (p->newton_maxit < 1 || p->newton_maxit > kMaxNewton) return "newton_maxit must be in 1..64";
   if (p->level1_maxit < 1 || p->level1_maxit > kMaxNewton) return "level1_maxit must be in 1..64";
   if (p->smoother != FMG_SMOOTHER_RBGS && p->smoother != FMG_SMOOTHER_CHEBYSHEV) return "unknown smoother";
+  if (p->nonlinear != FMG_NONLINEAR_NEWTON && p->nonlinear != FMG_NONLINEAR_FIXED_POINT)
+    return "unknown nonlinear solver";
   if (p->smoother == FMG_SMOOTHER_CHEBYSHEV && (p->nu_pre > kMaxCheb || p->nu_post > kMaxCheb))
     return "Chebyshev smoothing takes at most 16 steps";
   return nullptr;
@@ -391,7 +393,7 @@ cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
   TRY(tbegin(c, FMG_KT_AUGMENTED, k, &slot_aug));
   TRY(launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->g[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
                        c->p.newton_maxit, c->p.precision == FMG_PREC_MIXED, c->ab, c->st, k - 1, c->stream,
-                       c->cluster_aug));
+                       c->cluster_aug, c->p.nonlinear == FMG_NONLINEAR_FIXED_POINT ? 1 : 0));
   TRY(tend(c, slot_aug));
   return tend(c, slot_step);
 }
@@ -519,6 +521,7 @@ void fmg_default_params(fmg_params* p) {
   p->level1_tol = 1e-6;
   p->level1_maxit = 50;
   p->smoother = FMG_SMOOTHER_RBGS;
+  p->nonlinear = FMG_NONLINEAR_NEWTON;
 }
 
 fmg_status fmg_workspace_bytes(const fmg_params* p, size_t* bytes) {
@@ -801,6 +804,76 @@ fmg_status fmg_kernel_time(fmg_ctx* c, int kind, int level, double* total_ms, in
 }
 
 int fmg_graph_kernels(const fmg_ctx* c) { return c ? c->graph_kernels : -1; }
+
+fmg_status fmg_autotune(fmg_ctx* c, int* tuned) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if (tuned) *tuned = 0;
+  if (c->p.smoother != FMG_SMOOTHER_CHEBYSHEV) return FMG_OK;   // the other kernels' shapes are fixed
+  CK(c, cudaStreamSynchronize(c->stream));
+  const bool mixed = c->p.precision == FMG_PREC_MIXED;
+  const int top_cta = mixed ? coarse_cycle_top<float>(c) : coarse_cycle_top<double>(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(c, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, FMG_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+  }
+  static const int kBlocks[] = {64, 128, 256, 512};
+  static const int kStrips[] = {1, 2, 4, 8};
+  int count = 0;
+  for (int j = top_cta + 1; j <= c->nlev && ce == cudaSuccess; ++j) {
+    const LevelGeo g = c->geo[j - 1];
+    float best = 0.f;
+    ChebShape best_sh = cheb_shape(c->p.dim, g.n, mixed ? 4 : 8);
+    for (int bi = 0; bi < 4 && ce == cudaSuccess; ++bi)
+      for (int si = 0; si < 4 && ce == cudaSuccess; ++si) {
+        const ChebShape sh{kBlocks[bi], kStrips[si]};
+        // time the kernel on the context's scratch arrays (their contents are rebuilt by
+        // every solve): two warm-up launches, then five timed ones
+        auto launch = [&]() -> cudaError_t {
+          if (mixed)
+            return launch_cheb_shaped<float>(c->p.dim, g, c->u32[j - 1], c->u32b[j - 1], c->d32[j - 1],
+                                             c->u32[j - 1], c->cheb.cd[1], c->cheb.cr[1], false, sh, c->stream);
+          return launch_cheb_shaped<double>(c->p.dim, g, c->ua[j - 1], c->dd[j - 1], c->b[j - 1], c->ua[j - 1],
+                                            c->cheb.cd[1], c->cheb.cr[1], false, sh, c->stream);
+        };
+        for (int w = 0; w < 2 && ce == cudaSuccess; ++w) ce = launch();
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 5 && ce == cudaSuccess; ++r) ce = launch();
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce == cudaSuccess && (best == 0.f || ms < best)) {
+          best = ms;
+          best_sh = sh;
+        }
+      }
+    if (ce == cudaSuccess) {
+      set_cheb_shape(c->p.dim, g.n, mixed ? 4 : 8, best_sh);
+      ++count;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return fail(c, FMG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+  // the next solve captures its graph again with the tuned shapes
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  if (tuned) *tuned = count;
+  return FMG_OK;
+}
+
+fmg_status fmg_tuned_shape(const fmg_ctx* c, int level, int* block, int* strip) {
+  if (!c || level < 1 || level > c->nlev || !block || !strip) return fail(nullptr, FMG_ERR_INVALID, "bad arguments");
+  const ChebShape sh = cheb_shape(c->p.dim, c->geo[level - 1].n, c->p.precision == FMG_PREC_MIXED ? 4 : 8);
+  *block = sh.block;
+  *strip = sh.strip;
+  return FMG_OK;
+}
 
 fmg_status fmg_destroy(fmg_ctx* c) {
   if (!c) return FMG_OK;

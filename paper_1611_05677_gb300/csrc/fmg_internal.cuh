@@ -161,6 +161,19 @@ ChebCoef cheb_coefficients();
 template <typename T>
 cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr, bool first,
                         cudaStream_t s);
+// Launch shape of the Chebyshev step kernel: threads per block along x and nodes per thread
+// along the outer axis.  cheb_shape: the autotuned shape of this device and size if there
+// is one, else the default rule; set_cheb_shape records a tuned one (process-wide).
+struct ChebShape {
+  int block;
+  int strip;
+};
+ChebShape cheb_shape(int dim, int n, int elem_bytes);
+bool cheb_shape_tuned(int dim, int n, int elem_bytes, ChebShape* out);
+void set_cheb_shape(int dim, int n, int elem_bytes, ChebShape sh);
+template <typename T>
+cudaError_t launch_cheb_shaped(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr,
+                               bool first, ChebShape sh, cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s);
 
@@ -198,11 +211,12 @@ struct AugBuffers {
 void aug_configure(int dim, int coarse_cells, AugBuffers* ab);
 int aug_nvals(int dim);
 // jac_f32: Jacobian moments in FP32 (residual stays FP64) -- the mixed-precision path.
+// fixed_point: the fixed-point iteration on the Galerkin stiffness instead of Newton.
 // cluster_size > 0: the thread-block-cluster variant (no cooperative launch; used when many
 // instances run concurrently), with that many CTAs; 0: the cooperative grid variant.
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
-                             DevState* st, int level_index, cudaStream_t s, int cluster_size = 0);
+                             DevState* st, int level_index, cudaStream_t s, int cluster_size = 0, int fixed_point = 0);
 // Largest usable cluster size (<= 16, <= number of coarse cells) for the cluster variant, 0 if none.
 int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem);
 

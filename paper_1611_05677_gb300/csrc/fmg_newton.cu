@@ -344,12 +344,14 @@ struct Rows {
     return reinterpret_cast<const float*>(acc + (size_t)ND * G::NT);
   }
   // zero this thread's rows of the channels the pass fills
-  __device__ static void zero(double* acc, bool first, int tid) {
-    if (JF32 && !first) {
+  __device__ static void zero(double* acc, bool first, bool fixed_point, int tid) {
+    if ((JF32 || fixed_point) && !first) {
       for (int v = 0; v <= G::SA; ++v) acc[v * G::NT + tid] = 0.0;
       return;
     }
-    for (int v = 0; v < ND; ++v) acc[v * G::NT + tid] = 0.0;
+    const int nd = fixed_point ? G::JB : ND;   // no Jacobian channels in the fixed-point iteration
+    for (int v = 0; v < nd; ++v) acc[v * G::NT + tid] = 0.0;
+    if (fixed_point) return;
     float* f = jac(acc);
     for (int v = 0; v < NF; ++v) f[v * G::NT + tid] = 0.f;
   }
@@ -366,6 +368,7 @@ __device__ __forceinline__ int pair_index(int NV, int v, int u) {
 
 struct AugArgs {
   int dim, nc, s, n, kind, maxit, level_index, bpc, chunk;
+  int fixed_point;      // 1: fixed-point iteration (Galerkin stiffness only, no Jacobian)
   double a, w, sigma_k, sigma_H, tol;
   double* u;            // u~ on entry, u^{(l+1)} on exit (level-k nodal)
   const double* g;      // level-k nodal g
@@ -636,14 +639,16 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         Q0 += Fm;
         Q1 = fma(Fm, zd, Q1);
         SAv = fma(Fm, ut, SAv);
-        const JT dz = dj * zj;
-        const JT du = dj * uj;
-        D0 += dj;
-        D1 += dz;
-        D2 += dz * zj;
-        E0 += du;
-        E1 += du * zj;
-        JSv += du * uj;
+        if (!A.fixed_point) {
+          const JT dz = dj * zj;
+          const JT du = dj * uj;
+          D0 += dj;
+          D1 += dz;
+          D2 += dz * zj;
+          E0 += du;
+          E1 += du * zj;
+          JSv += du * uj;
+        }
         if (phase == kFirst) {
           double nb;
           if constexpr (D == 2) {
@@ -680,6 +685,7 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
       }
       acc[G::SA * G::NT + tid] += w * SAv;
       if (phase == kFirst) acc[G::SS * G::NT + tid] += SSv;
+      if (A.fixed_point) continue;   // the fixed-point iteration needs no Jacobian
       if (JF32) {
         // FP32 Jacobian channels, converted in FP32 into the FP32 rows
         float* fj = Rows<D, JF32>::jac(acc);
@@ -722,14 +728,14 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
 // pass); in the mixed path the Jacobian channels, FP32 products to begin with, are summed in
 // FP32 -- FP64 adds issue slowly on this part.
 template <int D, bool JF32>
-__device__ void block_reduce_rows(const double* acc, double* out, bool first) {
+__device__ void block_reduce_rows(const double* acc, double* out, bool first, bool fixed_point) {
   using G = Aug<D, JF32>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = G::NT / 32;
   __syncthreads();
   for (int v = warp; v < G::NVAL; v += nw) {
     const bool pre = v >= G::TT && v < G::JB;
     if (pre && !first) continue;
-    if (JF32 && !first && v >= G::JB) continue;   // chord step: no Jacobian channels
+    if ((fixed_point || (JF32 && !first)) && v >= G::JB) continue;   // no Jacobian channels
     if (JF32 && v >= G::JB) {
       const float* fj = Rows<D, JF32>::jac(acc);
       float x = 0.f;
@@ -817,6 +823,9 @@ __device__ void newton_update(const AugArgs& A, const double* R, int NH, double 
 // Block 0, after a pass: cell sums, the dense system, the Newton step, convergence.  In the
 // mixed path (JF32) the first iteration factors its Jacobian into L (LDL^T, FP32, with the
 // reciprocal pivots after it) and the later iterations are chord steps with that factor.
+// The fixed-point iteration (A.fixed_point) factors the Galerkin stiffness [[A_H, t], [t^T, s]]
+// once, in the path's precision, and every iteration solves with it against the residual
+// (y_{k+1} = y_k - K^{-1} R(y_k), i.e. K y_{k+1} = G - B^T W f(B y_k)).
 template <int D, bool JF32>
 __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double* R,
                             typename std::conditional<JF32, float, double>::type* L, double alpha, bool first) {
@@ -831,15 +840,16 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
   double* t_vec = A.sys;
   double* s_val = A.sys + NH;        // s; the mixed path's first-pass residual sums follow
   double* basev = A.sys + NH + 2;
-  if (JF32 && !first) {
-    // mixed path, chord step: the residual at the new iterate (first-pass FP64 sums plus this
-    // pass's increments), solved with the LDL^T factor of the first iteration's Jacobian
+  if ((JF32 || A.fixed_point) && !first) {
+    // chord / fixed-point step: the residual at the new iterate (mixed path: first-pass FP64
+    // sums plus this pass's increments; FP64 path: this pass's sums), solved with the factor
+    // of the first iteration
     for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
       const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
       const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
       double x = 0.0;
       for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + ch % G::NVAL]);
-      cellsum[ch] = x + basev[idx];
+      cellsum[ch] = JF32 ? x + basev[idx] : x;
     }
     __syncthreads();
     const double sig = A.sigma_H;
@@ -872,8 +882,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       if (tid == 0) R[NH] = -(tc + alpha * s_val[0] + s2);
     }
     __syncthreads();
-    if (tid < 32) ldlt_solve_warp<float>(reinterpret_cast<const float*>(L), NA, ld,
-                                        reinterpret_cast<const float*>(L) + (size_t)NA * ld, R);
+    if (tid < 32) ldlt_solve_warp<FT>(L, NA, ld, L + (size_t)NA * ld, R);
     __syncthreads();
     newton_update<D>(A, R, NH, alpha, 0, true);
     return;
@@ -882,6 +891,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
   for (int idx = tid; idx < ncell * G::NVAL; idx += blockDim.x) {
     const int cell = idx / G::NVAL, v = idx % G::NVAL;
     if (!first && v >= G::TT && v < G::JB) continue;
+    if (A.fixed_point && v >= G::JB) continue;
     double x = 0.0;
     for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + v]);
     cellsum[idx] = x;
@@ -935,7 +945,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       dist += abs(d);
     }
     if (!ok) continue;
-    double v = pair_channel<D, JF32>(cellsum, A.nc, z, zq);
+    double v = A.fixed_point ? 0.0 : pair_channel<D, JF32>(cellsum, A.nc, z, zq);
     if (dist == 0) v += sig * 2.0 * D;
     else if (dist == 1) v -= sig;
     M[p * ld + q] = v;
@@ -953,7 +963,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     }
     const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
     R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA));
-    const double jb = t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::JB);
+    const double jb = t_vec[p] + (A.fixed_point ? 0.0 : node_channel<D, JF32>(cellsum, A.nc, z, G::JB));
     M[p * ld + NH] = jb;
     M[NH * ld + p] = jb;
   }
@@ -961,7 +971,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     double s2 = 0.0, s3 = 0.0, tc = 0.0;
     for (int c = tid; c < ncell; c += 32) {
       s2 += cellsum[(long long)c * G::NVAL + G::SA];
-      s3 += cellsum[(long long)c * G::NVAL + G::JS];
+      if (!A.fixed_point) s3 += cellsum[(long long)c * G::NVAL + G::JS];
     }
     for (int p = tid; p < NH; p += 32) {
       int z[3];
@@ -1042,12 +1052,12 @@ __device__ void newton_update(const AugArgs& A, const double* R, int NH, double 
   }
 }
 
-// Where the solving block keeps the Newton factor.  FP64 path: after R (a scratch that the
-// next pass may overwrite).  Mixed path: past the channel rows, so that the first
-// iteration's factor survives the later passes for the chord steps.
+// Where the solving block keeps the Newton factor.  FP64 Newton: after R (a scratch that the
+// next pass may overwrite).  Mixed path and fixed-point iteration: past the channel rows, so
+// that the first iteration's factor survives the later passes.
 template <int D, bool JF32, typename FT>
-__device__ __forceinline__ FT* aug_factor(double* sm, double* R, int NA) {
-  if (JF32) {
+__device__ __forceinline__ FT* aug_factor(double* sm, double* R, int NA, bool fixed_point) {
+  if (JF32 || fixed_point) {
     char* rows_end = reinterpret_cast<char*>(sm) + Rows<D, JF32>::bytes;
     char* scratch_end = reinterpret_cast<char*>(R + NA + 1);
     return reinterpret_cast<FT*>(rows_end > scratch_end ? rows_end : scratch_end);
@@ -1093,7 +1103,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
   double* cellsum = acc;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  FT* L = aug_factor<D, JF32, FT>(sm, R, NA);
+  FT* L = aug_factor<D, JF32, FT>(sm, R, NA, A.fixed_point != 0);
 
   if (blockIdx.x == 0) {
     const long long cn = ipow(A.nc + 1, D);
@@ -1112,11 +1122,11 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
       stop = ((volatile int*)&A.st->abort)[0];
     }
     // chord steps of the mixed path fill the residual channels RA, SA only
-    Rows<D, JF32>::zero(acc, first, tid);
+    Rows<D, JF32>::zero(acc, first, A.fixed_point != 0, tid);
     __syncthreads();
     if (stop) break;
     fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, bic);
-    block_reduce_rows<D, JF32>(acc, A.partials + (long long)blockIdx.x * G::NVAL, first);
+    block_reduce_rows<D, JF32>(acc, A.partials + (long long)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
     grid_barrier(A.st, nblocks);
     if (blockIdx.x == 0) newton_step<D, JF32>(A, cellsum, M, R, L, alpha_sh, first);
     grid_barrier(A.st, nblocks);
@@ -1162,7 +1172,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs 
   double* cellsum = acc;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  FT* L = aug_factor<D, JF32, FT>(sm, R, NA);
+  FT* L = aug_factor<D, JF32, FT>(sm, R, NA, A.fixed_point != 0);
   auto vertex_offset = [&](int cell, int v) {
     long long off = 0, mul = 1;
     int t = cell;
@@ -1192,10 +1202,10 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs 
     if (stop) break;
     for (int cell = rank; cell < ncell; cell += CS) {
       if (tid < G::NV) cv[tid] = first ? 0.0 : __ldcg(&A.c[vertex_offset(cell, tid)]);
-      Rows<D, JF32>::zero(acc, first, tid);
+      Rows<D, JF32>::zero(acc, first, A.fixed_point != 0, tid);
       __syncthreads();
       fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, 0);
-      block_reduce_rows<D, JF32>(acc, A.partials + (long long)cell * G::NVAL, first);
+      block_reduce_rows<D, JF32>(acc, A.partials + (long long)cell * G::NVAL, first, A.fixed_point != 0);
     }
     cluster.sync();
     if (rank == 0) newton_step<D, JF32>(A, cellsum, M, R, L, alpha_sh, first);
@@ -1232,9 +1242,10 @@ size_t aug_smem(int nc) {
     const size_t scratch = sizeof(double) * ((size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 1);
     return (rbytes > scratch ? rbytes : scratch) + sizeof(float) * ((size_t)NA * (NA + 1) + NA);
   }
-  // cellsum, M, R, then the FP64 factor (NA (NA+1) values) and work/invd (2 NA)
-  const size_t scratch = (size_t)ncell * G::NVAL + 2 * ((size_t)NA * (NA + 1)) + 3 * NA + 4;
-  return sizeof(double) * (rows > scratch ? rows : scratch);
+  // cellsum, M, R in the rows (or past them), then the FP64 factor and its pivots (past the
+  // rows, where the fixed-point iteration keeps it from pass to pass)
+  const size_t scratch = (size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 1;
+  return sizeof(double) * ((rows > scratch ? rows : scratch) + (size_t)NA * (NA + 1) + NA);
 }
 
 // Blocks per SM of the cooperative kernel when launched with `smem` dynamic bytes (the
@@ -1341,7 +1352,7 @@ int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem) {
 
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
-                             DevState* st, int level_index, cudaStream_t s, int cluster_size) {
+                             DevState* st, int level_index, cudaStream_t s, int cluster_size, int fixed_point) {
   const size_t smem = ab.smem;
   const int nt = ab.nt;
   if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
@@ -1368,6 +1379,7 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.kind = kind;
   A.maxit = maxit;
   A.level_index = level_index;
+  A.fixed_point = fixed_point;
   A.bpc = bpc;
   A.chunk = chunk;
   A.a = a;

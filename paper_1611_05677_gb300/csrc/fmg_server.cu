@@ -39,7 +39,7 @@ bool same_shape(const fmg_params& a, const fmg_params& b) {
          a.f_scale == b.f_scale && a.m_vcycles == b.m_vcycles && a.nu_pre == b.nu_pre && a.nu_post == b.nu_post &&
          a.p_corrections == b.p_corrections && a.precision == b.precision && a.newton_tol == b.newton_tol &&
          a.newton_maxit == b.newton_maxit && a.level1_tol == b.level1_tol && a.level1_maxit == b.level1_maxit &&
-         a.smoother == b.smoother;
+         a.smoother == b.smoother && a.nonlinear == b.nonlinear;
 }
 
 struct Cached {

@@ -14,6 +14,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "fmg_internal.cuh"
@@ -309,42 +310,23 @@ struct CoarseLevel {
 };
 
 // One colour of a red-black sweep: items are (p, j[, l]) with i = 2p + 1 or 2p + 2, decoded
-// with shifts; rows 0 and n and out-of-range i are skipped.  Nodes of one colour do not
-// couple, so a thread takes two items at a time with all loads before both stores.
-template <typename T, int D>
-__device__ __forceinline__ int cta_rb_node(const CoarseLevel<T, D>& L, int t, int colour) {
-  const int n = L.n, np = L.np, lgh = L.lg - 1;
-  const int p = t & ((1 << lgh) - 1);
-  const int j = (t >> lgh) & (n - 1);
-  const int l = D == 3 ? (t >> (lgh + L.lg)) : 0;
-  if (j == 0 || (D == 3 && l == 0)) return -1;
-  const int par = (colour + j + l) & 1;
-  const int i = par ? 2 * p + 1 : 2 * p + 2;
-  if (i > n - 1) return -1;
-  return (l * np + j) * np + i;
-}
-
-template <typename T, int D>
-__device__ __forceinline__ T cta_nbsum(const CoarseLevel<T, D>& L, int c) {
-  const int np = L.np;
-  T s = (L.u[c - 1] + L.u[c + 1]) + (L.u[c - np] + L.u[c + np]);
-  if (D == 3) s += L.u[c - np * np] + L.u[c + np * np];
-  return s;
-}
-
+// with shifts; rows 0 and n and out-of-range i are skipped.
 template <typename T, int D>
 __device__ __forceinline__ void cta_rbgs(const CoarseLevel<T, D>& L, int colour, T bscale, T inv2d) {
-  const int n = L.n, lgh = L.lg - 1;
+  const int n = L.n, np = L.np, lgh = L.lg - 1;
   const int total = D == 2 ? (n << lgh) : (n << (lgh + L.lg));
-  const int step = 2 * blockDim.x;
-  for (int t = threadIdx.x; t < total; t += step) {
-    const int c1 = cta_rb_node<T, D>(L, t, colour);
-    const int c2 = t + (int)blockDim.x < total ? cta_rb_node<T, D>(L, t + blockDim.x, colour) : -1;
-    T v1 = T(0), v2 = T(0);
-    if (c1 >= 0) v1 = (L.b[c1] * bscale + cta_nbsum<T, D>(L, c1)) * inv2d;
-    if (c2 >= 0) v2 = (L.b[c2] * bscale + cta_nbsum<T, D>(L, c2)) * inv2d;
-    if (c1 >= 0) L.u[c1] = v1;
-    if (c2 >= 0) L.u[c2] = v2;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int p = t & ((1 << lgh) - 1);
+    const int j = (t >> lgh) & (n - 1);
+    const int l = D == 3 ? (t >> (lgh + L.lg)) : 0;
+    if (j == 0 || (D == 3 && l == 0)) continue;
+    const int par = (colour + j + l) & 1;
+    const int i = par ? 2 * p + 1 : 2 * p + 2;
+    if (i > n - 1) continue;
+    const int c = (l * np + j) * np + i;
+    T s = (L.u[c - 1] + L.u[c + 1]) + (L.u[c - np] + L.u[c + np]);
+    if (D == 3) s += L.u[c - np * np] + L.u[c + np * np];
+    L.u[c] = (L.b[c] * bscale + s) * inv2d;
   }
 }
 
@@ -680,21 +662,67 @@ ChebCoef cheb_coefficients() {
   return c;
 }
 
-template <typename T>
-cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr, bool first,
-                        cudaStream_t s) {
-  const int n = g.n;
+// Launch shapes of the Chebyshev step kernel picked by the autotuner (fmg_autotune), per
+// device, dimension, cells per side and element size; absent entries use the default rule.
+namespace {
+std::mutex g_shape_mu;
+std::map<std::tuple<int, int, int, int>, ChebShape> g_shapes;
+
+ChebShape default_cheb_shape(int dim, int n) {
   const unsigned gx = cdiv(n - 1, kBlock);
   const unsigned plane = dim == 2 ? gx : gx * (unsigned)(n - 1);
   // the longest strip that still leaves at least 1024 blocks (small levels: one node each)
   int strip = kChebStrip;
   while (strip > 1 && (long long)plane * cdiv(n - 1, strip) < 1024) strip >>= 1;
-  const unsigned gs = cdiv(n - 1, strip);
+  return ChebShape{kBlock, strip};
+}
+}  // namespace
+
+ChebShape cheb_shape(int dim, int n, int elem_bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  auto it = g_shapes.find(std::make_tuple(dev, dim, n, elem_bytes));
+  return it != g_shapes.end() ? it->second : default_cheb_shape(dim, n);
+}
+
+bool cheb_shape_tuned(int dim, int n, int elem_bytes, ChebShape* out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  auto it = g_shapes.find(std::make_tuple(dev, dim, n, elem_bytes));
+  if (it == g_shapes.end()) return false;
+  if (out) *out = it->second;
+  return true;
+}
+
+void set_cheb_shape(int dim, int n, int elem_bytes, ChebShape sh) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  g_shapes[std::make_tuple(dev, dim, n, elem_bytes)] = sh;
+}
+
+template <typename T>
+cudaError_t launch_cheb_shaped(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr,
+                               bool first, ChebShape sh, cudaStream_t s) {
+  const int n = g.n;
+  if (sh.block < 32 || sh.block > 1024 || (sh.block & 31) || sh.strip < 1 || sh.strip > kChebStrip)
+    return cudaErrorInvalidValue;
+  const unsigned gx = cdiv(n - 1, sh.block);
+  const unsigned gs = cdiv(n - 1, sh.strip);
   if (dim == 2)
-    k_cheb<T, 2><<<dim3(gx, gs), kBlock, 0, s>>>(u, uo, d, b, n, T(1), T(cd), T(cr), first ? 1 : 0, strip);
+    k_cheb<T, 2><<<dim3(gx, gs), sh.block, 0, s>>>(u, uo, d, b, n, T(1), T(cd), T(cr), first ? 1 : 0, sh.strip);
   else
-    k_cheb<T, 3><<<dim3(gx, n - 1, gs), kBlock, 0, s>>>(u, uo, d, b, n, T(n), T(cd), T(cr), first ? 1 : 0, strip);
+    k_cheb<T, 3><<<dim3(gx, n - 1, gs), sh.block, 0, s>>>(u, uo, d, b, n, T(n), T(cd), T(cr), first ? 1 : 0,
+                                                          sh.strip);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr, bool first,
+                        cudaStream_t s) {
+  return launch_cheb_shaped<T>(dim, g, u, uo, d, b, cd, cr, first, cheb_shape(dim, g.n, (int)sizeof(T)), s);
 }
 
 template <typename T>
@@ -713,6 +741,10 @@ template cudaError_t launch_cheb<double>(int, LevelGeo, const double*, double*, 
                                          bool, cudaStream_t);
 template cudaError_t launch_cheb<float>(int, LevelGeo, const float*, float*, float*, const float*, double, double, bool,
                                         cudaStream_t);
+template cudaError_t launch_cheb_shaped<double>(int, LevelGeo, const double*, double*, double*, const double*, double,
+                                                double, bool, ChebShape, cudaStream_t);
+template cudaError_t launch_cheb_shaped<float>(int, LevelGeo, const float*, float*, float*, const float*, double,
+                                               double, bool, ChebShape, cudaStream_t);
 template cudaError_t launch_copy_t<double>(const double*, double*, long long, cudaStream_t);
 template cudaError_t launch_copy_t<float>(const float*, float*, long long, cudaStream_t);
 template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t);

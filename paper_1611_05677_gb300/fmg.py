@@ -29,13 +29,15 @@ STATUS_NAMES = {0: "FMG_OK", 1: "FMG_ERR_INVALID", 2: "FMG_ERR_OOM", 3: "FMG_ERR
 NONLIN = {"cubic": 0, "expm1": 1, "linear": 2, "signed_pow32": 3, "neg_exp_neg": 4}
 PREC = {"fp64": 0, "mixed": 1}
 SMOOTHER = {"rbgs": 0, "chebyshev": 1}
+NONLINEAR = {"newton": 0, "fixed_point": 1}
 
 
 class fmg_params(ctypes.Structure):
     _fields_ = [("dim", c_int), ("coarse_cells", c_int), ("refinements", c_int), ("f", c_int),
                 ("f_scale", c_double), ("m_vcycles", c_int), ("nu_pre", c_int), ("nu_post", c_int),
                 ("p_corrections", c_int), ("precision", c_int), ("newton_tol", c_double),
-                ("newton_maxit", c_int), ("level1_tol", c_double), ("level1_maxit", c_int), ("smoother", c_int)]
+                ("newton_maxit", c_int), ("level1_tol", c_double), ("level1_maxit", c_int), ("smoother", c_int),
+                ("nonlinear", c_int)]
 
 
 class fmg_stats(ctypes.Structure):
@@ -71,7 +73,7 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
            "fmg_op_level1_solve", "fmg_op_prolong", "fmg_set_kernel_timing", "fmg_kernel_time",
            "fmg_graph_kernels", "fmg_vcycle_noalloc", "fmg_batch_create", "fmg_batch_solve", "fmg_batch_sync",
            "fmg_batch_destroy", "fmg_server_create", "fmg_server_submit", "fmg_server_poll", "fmg_server_drain",
-           "fmg_server_get_info", "fmg_server_last_error", "fmg_server_destroy")
+           "fmg_server_get_info", "fmg_server_last_error", "fmg_server_destroy", "fmg_autotune", "fmg_tuned_shape")
 KT_AUGMENTED = 0
 KT_SMOOTH_TOP = 1
 KT_CORRECTION = 2
@@ -129,6 +131,8 @@ def load():
         "fmg_server_get_info": (c_int, [c_void_p, POINTER(fmg_server_info)]),
         "fmg_server_last_error": (c_char_p, []),
         "fmg_server_destroy": (c_int, [c_void_p]),
+        "fmg_autotune": (c_int, [c_void_p, POINTER(c_int)]),
+        "fmg_tuned_shape": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,6 +329,19 @@ def _check_server(status: int):
         raise FMGError(status, msg.decode() if msg else "")
 
 
+def fmg_autotune(ctx) -> int:
+    """Tunes the launch shapes of the context's stencil kernels; returns the levels tuned."""
+    n = c_int(0)
+    _check(load().fmg_autotune(ctx, byref(n)), ctx)
+    return n.value
+
+
+def fmg_tuned_shape(ctx, level: int):
+    block, strip = c_int(0), c_int(0)
+    _check(load().fmg_tuned_shape(ctx, level, byref(block), byref(strip)), ctx)
+    return block.value, strip.value
+
+
 def fmg_server_last_error() -> str:
     msg = load().fmg_server_last_error()
     return msg.decode() if msg else ""
@@ -391,6 +408,8 @@ def make_params(problem=None, **kw) -> fmg_params:
             v = PREC[v]
         if k == "smoother" and isinstance(v, str):
             v = SMOOTHER[v]
+        if k == "nonlinear" and isinstance(v, str):
+            v = NONLINEAR[v]
         setattr(p, k, v)
     return p
 

@@ -119,3 +119,20 @@ def test_fmg_chebyshev_mixed_below_discretization_error(fmg, dim, H, r, f, m):
     e_alg64 = O.discrete_l2(lev, res.u[-1] - ub)
     assert O.discrete_l2(lev, u - ub) <= e_alg64 + 0.1 * e_disc
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_autotuned_shapes_give_the_same_bits(fmg, precision):
+    """The autotuner only changes how nodes are dealt to threads: every node is computed the
+    same way, so the solve gives the same bits before and after tuning."""
+    prob = problem(2, 4, 6, "cubic")
+    s = solver(fmg, prob, precision)
+    before = s.solve().cpu().numpy()
+    tuned = fmg.fmg_autotune(s.ctx)
+    assert tuned >= 1
+    for level in range(1, prob.levels + 1):
+        block, strip = fmg.fmg_tuned_shape(s.ctx, level)
+        assert block in (64, 128, 256, 512) and strip in (1, 2, 4, 8)
+    after = s.solve().cpu().numpy()
+    assert np.array_equal(before, after)
+    s.close()

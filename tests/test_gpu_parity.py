@@ -320,3 +320,56 @@ def test_mixed_cycle_equals_fp64_cycle_to_fp32_precision(fmg, dim, H, r, nu):
     got = O.from_nodal(lev, ud.cpu().numpy())
     assert np.max(np.abs(got - ref)) <= 2e-5 * np.max(np.abs(ref - u))
     s.close()
+
+
+@pytest.mark.parametrize("dim,H,r,kind,p", [(2, 4, 4, "cubic", 2), (3, 4, 2, "expm1", 3)])
+def test_fmg_several_correction_steps_per_level(fmg, dim, H, r, kind, p):
+    """Algorithm 3.2 with p > 1 correction steps per level: every level's steps repeat
+    Algorithm 3.1 from the previous step's result."""
+    prob = prob2d(H, r, kind) if dim == 2 else prob3d(H, r, kind)
+    hier = O.build_hierarchy(dim, H, r)
+    res = O.fmg(hier, prob.g_nodal(), kind, prob.a, p=p)
+    s = make_solver(fmg, prob, p_corrections=p)
+    st = fmg.fmg_stats()
+    u = s.solve(stats=st).cpu().numpy()
+    assert st.flags == 0
+    assert rel(u, O.to_nodal(hier.level(r + 1), res.u[-1])) <= FP64_TOL
+    # the per-level Newton counts are summed over the p steps
+    for k in range(2, r + 2):
+        want = sum(info.newton_iters for kk, info in res.steps if kk == k)
+        assert abs(st.newton_iters[k - 1] - want) <= p
+    s.close()
+
+
+@pytest.mark.parametrize("dim,H,r,kind", [(2, 4, 4, "cubic"), (2, 8, 3, "cubic"), (3, 4, 2, "cubic"),
+                                          (2, 4, 4, "expm1")])
+def test_fmg_fixed_point_fp64_matches_oracle(fmg, dim, H, r, kind):
+    """The fixed-point variant of the augmented solve (Galerkin stiffness factored once)."""
+    prob = prob2d(H, r, kind) if dim == 2 else prob3d(H, r, kind)
+    hier = O.build_hierarchy(dim, H, r)
+    res = O.fmg(hier, prob.g_nodal(), kind, prob.a, nonlinear="fixed_point")
+    s = make_solver(fmg, prob, nonlinear="fixed_point", newton_maxit=60)
+    st = fmg.fmg_stats()
+    u = s.solve(stats=st).cpu().numpy()
+    assert st.flags == 0
+    assert rel(u, O.to_nodal(hier.level(r + 1), res.u[-1])) <= FP64_TOL
+    for k, info in res.steps:
+        assert abs(st.newton_iters[k - 1] - info.newton_iters) <= 1
+    s.close()
+
+
+@pytest.mark.parametrize("dim,H,r,kind", [(2, 4, 5, "cubic"), (3, 4, 3, "cubic")])
+def test_fmg_fixed_point_mixed_below_discretization_error(fmg, dim, H, r, kind):
+    prob = prob2d(H, r, kind) if dim == 2 else prob3d(H, r, kind)
+    hier = O.build_hierarchy(dim, H, r)
+    g = prob.g_nodal()
+    res = O.fmg(hier, g, kind, prob.a, nonlinear="fixed_point")
+    lev = hier.level(r + 1)
+    ub, _ = O.newton_full(lev, O.load_vector(lev, g), kind, prob.a, U0=res.u[-1])
+    e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star()))
+    s = make_solver(fmg, prob, precision="mixed", nonlinear="fixed_point", newton_maxit=60)
+    st = fmg.fmg_stats()
+    u = O.from_nodal(lev, s.solve(stats=st).cpu().numpy())
+    assert st.flags == 0
+    assert O.discrete_l2(lev, u - res.u[-1]) <= 0.1 * e_disc
+    s.close()
