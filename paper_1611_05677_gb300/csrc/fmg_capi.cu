@@ -233,14 +233,16 @@ const ChebCoef* cheb_coef(const fmg_ctx* c) {
   return c->p.smoother == FMG_SMOOTHER_CHEBYSHEV ? &c->cheb : nullptr;
 }
 
-// `steps` Chebyshev-Jacobi steps on A u = b at level j (one stencil pass each, the iterate
-// alternating between u and alt, d the step direction); the result ends in u.
+// Chebyshev-Jacobi steps first..steps-1 on A u = b at level j (one stencil pass each, the
+// iterate alternating between u and alt, d the step direction); the result ends in u.  A
+// caller that already took step 0 (from a zero start, fused into the kernel that produced b)
+// passes first = 1.
 template <typename T>
-cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int steps, bool top) {
+cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int steps, bool top, int first = 0) {
   const LevelGeo g = c->geo[j - 1];
   T* cur = u;
   T* oth = alt;
-  for (int k = 0; k < steps; ++k) {
+  for (int k = first; k < steps; ++k) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
     TRY(launch_cheb<T>(c->p.dim, g, cur, oth, d, b, c->cheb.cd[k], c->cheb.cr[k], k == 0, c->stream));
@@ -265,7 +267,20 @@ int coarse_cycle_top(const fmg_ctx* c) {
   return j;
 }
 
-cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = false) {
+// Factor of Chebyshev step 0 from a zero start at level j: u = d = cr_0 D^{-1} b.
+double cheb_e0(const fmg_ctx* c, int j) {
+  const double bscale = c->p.dim == 2 ? 1.0 : (double)c->geo[j - 1].n;
+  return c->cheb.cr[0] * bscale / (2.0 * c->p.dim);
+}
+
+// Whether a coarse level j, entered from zero by the restriction, takes its first Chebyshev
+// step inside that restriction (it runs the per-level kernels and pre-smooths at all).
+template <typename T>
+bool fuse_first_step(const fmg_ctx* c, int j) {
+  return c->p.smoother == FMG_SMOOTHER_CHEBYSHEV && c->p.nu_pre >= 1 && j > coarse_cycle_top<T>(c);
+}
+
+cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = false, bool started = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
   if (j == 1) {
@@ -279,7 +294,7 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
   }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
   const bool cheb = c->p.smoother == FMG_SMOOTHER_CHEBYSHEV;
-  if (cheb) TRY(cheb_steps<double>(c, j, u, c->ua[j - 1], c->dd[j - 1], b, c->p.nu_pre, top));
+  if (cheb) TRY(cheb_steps<double>(c, j, u, c->ua[j - 1], c->dd[j - 1], b, c->p.nu_pre, top, started ? 1 : 0));
   for (int it = 0; !cheb && it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
@@ -287,8 +302,10 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
     TRY(launch_rbgs<double>(dim, gf, u, b, 1, s));
     TRY(tend(c, slot));
   }
-  TRY(launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s));
-  TRY(vcycle(c, j - 1, c->u[j - 2], c->b[j - 2]));
+  const bool fuse = fuse_first_step<double>(c, j - 1);
+  TRY(launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s,
+                                               fuse ? c->dd[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0));
+  TRY(vcycle(c, j - 1, c->u[j - 2], c->b[j - 2], false, fuse));
   TRY(launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s));
   if (cheb) TRY(cheb_steps<double>(c, j, u, c->ua[j - 1], c->dd[j - 1], b, c->p.nu_post, top));
   for (int it = 0; !cheb && it < c->p.nu_post; ++it) {
@@ -331,7 +348,10 @@ cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
   return tend(c, slot);
 }
 
-cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
+// FP32 cycle on level j (unfused kernels).  started: Chebyshev step 0 was already taken by the
+// kernel that produced b; u64_top (top level of the mixed path): the last post-smoothing step
+// is fused with the FP64 update u64 += correction.
+cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, double* u64_top = nullptr) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
   float* u = c->u32[j - 1];
@@ -347,7 +367,7 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
   }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
   const bool cheb = c->p.smoother == FMG_SMOOTHER_CHEBYSHEV;
-  if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_pre, top));
+  if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_pre, top, started ? 1 : 0));
   for (int it = 0; !cheb && it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
@@ -355,9 +375,17 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
     TRY(launch_rbgs<float>(dim, gf, u, b, 1, s));
     TRY(tend(c, slot));
   }
-  TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s));
-  TRY(vcycle32(c, j - 1));
+  const bool fuse = fuse_first_step<float>(c, j - 1);
+  TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s,
+                                             fuse ? c->d32[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0));
+  TRY(vcycle32(c, j - 1, false, fuse));
   TRY(launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s));
+  if (cheb && u64_top && c->p.nu_post >= 1) {
+    const int last = c->p.nu_post - 1;
+    TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, last, top));
+    TRY(launch_cheb_add64(dim, gf, u, c->d32[j - 1], b, u64_top, c->cheb.cd[last], c->cheb.cr[last], last == 0, s));
+    return cudaSuccess;
+  }
   if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_post, top));
   for (int it = 0; !cheb && it < c->p.nu_post; ++it) {
     int slot = -1;
@@ -366,6 +394,7 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
     TRY(launch_rbgs<float>(dim, gf, u, b, 0, s));
     TRY(tend(c, slot));
   }
+  if (u64_top) TRY(launch_add_f32(gf, dim, u64_top, u, s));
   return cudaSuccess;
 }
 
@@ -373,9 +402,13 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false) {
 cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
   if (c->p.precision == FMG_PREC_FP64 || k == 1) return vcycle(c, k, u, b, true);
   const LevelGeo g = c->geo[k - 1];
-  // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update
-  TRY(launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream));
+  // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update (with Chebyshev
+  // smoothing the cycle's first step is fused into the residual and its last into the update)
+  const bool fuse = fuse_first_step<float>(c, k);
+  TRY(launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream,
+                             fuse ? c->d32[k - 1] : nullptr, fuse ? cheb_e0(c, k) : 0.0));
   if (c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS) return vcycle32_fused(c, k, u);
+  if (k > coarse_cycle_top<float>(c)) return vcycle32(c, k, true, fuse, u);
   TRY(vcycle32(c, k, true));
   TRY(launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream));
   return cudaSuccess;

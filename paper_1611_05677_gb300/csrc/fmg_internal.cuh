@@ -109,14 +109,16 @@ __device__ __forceinline__ T f_only(int kind, T a, T u) {
 template <typename T>
 cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaStream_t s);
 
-// b_c = P^T (b_f - A_f u_f), u_c = 0 (coarse arrays of geometry gc, fine gf)
+// b_c = P^T (b_f - A_f u_f), u_c = 0 (coarse arrays of geometry gc, fine gf).  With d_c the
+// coarse level's first Chebyshev step from zero is fused in: u_c = d_c = e0 b_c.
 template <typename TF, typename TC>
 cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const TF* b_f, LevelGeo gc,
-                                     TC* b_c, TC* u_c, cudaStream_t s);
+                                     TC* b_c, TC* u_c, cudaStream_t s, TC* d_c = nullptr, double e0 = 0.0);
 
-// mixed path: b32 = (float)(b - A u) in FP64, u32 = 0 (same level)
+// mixed path: b32 = (float)(b - A u) in FP64, u32 = 0 (same level); with d32 the first
+// Chebyshev step from zero is fused in: u32 = d32 = e0 b32
 cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const double* b, float* r32,
-                                   float* e32, cudaStream_t s);
+                                   float* e32, cudaStream_t s, float* d32 = nullptr, double e0 = 0.0);
 
 // r = b - A u (FP64, same level)
 cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* b, double* r, cudaStream_t s);
@@ -174,6 +176,9 @@ void set_cheb_shape(int dim, int n, int elem_bytes, ChebShape sh);
 template <typename T>
 cudaError_t launch_cheb_shaped(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr,
                                bool first, ChebShape sh, cudaStream_t s);
+// Last Chebyshev step of the mixed path's top-level FP32 cycle fused with u64 += correction.
+cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* d, const float* b, double* u64,
+                              double cd, double cr, bool first, cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s);
 

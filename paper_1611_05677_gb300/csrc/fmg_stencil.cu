@@ -93,6 +93,35 @@ __global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restric
   }
 }
 
+// The last Chebyshev step of the mixed path's top-level FP32 cycle fused with its FP64
+// update: u64 += u + d_new (the new correction is neither stored nor read back).
+template <int D>
+__global__ void k_cheb_add64(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ b,
+                             double* __restrict__ u64, int n, float bscale, float cd, float cr, int first, int strip) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int j = D == 3 ? blockIdx.y + 1 : 0;
+  const int z0 = (D == 2 ? blockIdx.y : blockIdx.z) * strip + 1;
+  if (i > n - 1) return;
+  const long long np = n + 1;
+  const long long so = D == 2 ? np : np * np;
+  long long c = (D == 2 ? (long long)z0 * np : ((long long)z0 * np + j) * np) + i;
+  float um = u[c - so], uc = u[c];
+  const float inv2d = 1.0f / (2 * D);
+#pragma unroll
+  for (int r = 0; r < kChebStrip; ++r) {
+    if (r >= strip || z0 + r > n - 1) break;
+    const float up = u[c + so];
+    float s = (u[c - 1] + u[c + 1]) + (um + up);
+    if (D == 3) s += u[c - np] + u[c + np];
+    const float zr = (b[c] * bscale + s) * inv2d - uc;
+    const float dn = first ? cr * zr : cd * d[c] + cr * zr;
+    u64[c] += (double)(uc + dn);
+    um = uc;
+    uc = up;
+    c += so;
+  }
+}
+
 template <typename T>
 __global__ void k_copy_t(const T* __restrict__ s, T* __restrict__ d, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -111,9 +140,11 @@ __device__ __forceinline__ T res3(const T* __restrict__ u, const T* __restrict__
   return b[c] - sigma * (T(6) * u[c] - (((u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np])) + (u[c - pl] + u[c + pl])));
 }
 
+// With dc != NULL the coarse level's first Chebyshev step from its zero start is taken here
+// too: u_c = d_c = e0 b_c (e0 = cr_0 / diag of the coarse level).
 template <typename TF, typename TC>
 __global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
-                               TC* __restrict__ uc, int ncells) {
+                               TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int J = blockIdx.y + 1;
   if (I > ncells - 1) return;
@@ -123,13 +154,16 @@ __global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ 
   TF e = (res2(u, b, F + 1, np) + res2(u, b, F - 1, np)) + (res2(u, b, F + np, np) + res2(u, b, F - np, np)) +
          (res2(u, b, F + np + 1, np) + res2(u, b, F - np - 1, np));
   const long long cc = (long long)J * (ncells + 1) + I;
-  bc[cc] = (TC)(r + TF(0.5) * e);
-  uc[cc] = TC(0);
+  const TC bv = (TC)(r + TF(0.5) * e);
+  bc[cc] = bv;
+  const TC e1 = dc ? e0 * bv : TC(0);
+  uc[cc] = e1;
+  if (dc) dc[cc] = e1;
 }
 
 template <typename TF, typename TC>
 __global__ void k_resrestrict3(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TF sigma,
-                               TC* __restrict__ bc, TC* __restrict__ uc, int ncells) {
+                               TC* __restrict__ bc, TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int J = blockIdx.y + 1;
   const int L = blockIdx.z + 1;
@@ -144,13 +178,19 @@ __global__ void k_resrestrict3(const TF* __restrict__ u, const TF* __restrict__ 
   for (int q = 0; q < 7; ++q) e += res3(u, b, F + o[q], np, pl, sigma) + res3(u, b, F - o[q], np, pl, sigma);
   const long long ncp = ncells + 1;
   const long long cc = ((long long)L * ncp + J) * ncp + I;
-  bc[cc] = (TC)(r + TF(0.5) * e);
-  uc[cc] = TC(0);
+  const TC bv = (TC)(r + TF(0.5) * e);
+  bc[cc] = bv;
+  const TC e1 = dc ? e0 * bv : TC(0);
+  uc[cc] = e1;
+  if (dc) dc[cc] = e1;
 }
 
 // ------------------------------------------------------------------ residual on one level
+// With d32 != NULL the first Chebyshev step of the FP32 cycle, which starts from a zero
+// correction, is taken here too: e = d = e0 r (e0 = cr_0 / diag).
 __global__ void k_residual2(const double* __restrict__ u, const double* __restrict__ b, int n,
-                            double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32) {
+                            double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32,
+                            float* __restrict__ d32, float e0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i > n) return;
@@ -160,13 +200,17 @@ __global__ void k_residual2(const double* __restrict__ u, const double* __restri
   if (i > 0 && i < n && j > 0 && j < n) v = res2(u, b, c, np);
   if (r) r[c] = v;
   if (r32) {
-    r32[c] = (float)v;
-    e32[c] = 0.0f;
+    const float vf = (float)v;
+    r32[c] = vf;
+    const float e = d32 ? e0 * vf : 0.0f;
+    e32[c] = e;
+    if (d32) d32[c] = e;
   }
 }
 
 __global__ void k_residual3(const double* __restrict__ u, const double* __restrict__ b, int n, double sigma,
-                            double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32) {
+                            double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32,
+                            float* __restrict__ d32, float e0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   const int l = blockIdx.z;
@@ -178,8 +222,11 @@ __global__ void k_residual3(const double* __restrict__ u, const double* __restri
   if (i > 0 && i < n && j > 0 && j < n && l > 0 && l < n) v = res3(u, b, c, np, pl, sigma);
   if (r) r[c] = v;
   if (r32) {
-    r32[c] = (float)v;
-    e32[c] = 0.0f;
+    const float vf = (float)v;
+    r32[c] = vf;
+    const float e = d32 ? e0 * vf : 0.0f;
+    e32[c] = e;
+    if (d32) d32[c] = e;
   }
 }
 
@@ -528,26 +575,26 @@ cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaS
 
 template <typename TF, typename TC>
 cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const TF* b_f, LevelGeo gc, TC* b_c,
-                                     TC* u_c, cudaStream_t s) {
+                                     TC* u_c, cudaStream_t s, TC* d_c, double e0) {
   const int nc = gc.n;
   const unsigned gx = cdiv(nc - 1, kBlock);
   if (dim == 2) {
-    k_resrestrict2<TF, TC><<<dim3(gx, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc);
+    k_resrestrict2<TF, TC><<<dim3(gx, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
   } else {
     k_resrestrict3<TF, TC><<<dim3(gx, nc - 1, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, TF(1.0) / TF(gf.n), b_c,
-                                                                        u_c, nc);
+                                                                        u_c, nc, d_c, TC(e0));
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const double* b, float* r32, float* e32,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, float* d32, double e0) {
   const int n = g.n;
   const unsigned gx = cdiv(n + 1, kBlock);
   if (dim == 2)
-    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, nullptr, r32, e32);
+    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, nullptr, r32, e32, d32, (float)e0);
   else
-    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, nullptr, r32, e32);
+    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, nullptr, r32, e32, d32, (float)e0);
   return cudaGetLastError();
 }
 
@@ -555,9 +602,9 @@ cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* 
   const int n = g.n;
   const unsigned gx = cdiv(n + 1, kBlock);
   if (dim == 2)
-    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, r, nullptr, nullptr);
+    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, r, nullptr, nullptr, nullptr, 0.0f);
   else
-    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, r, nullptr, nullptr);
+    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, r, nullptr, nullptr, nullptr, 0.0f);
   return cudaGetLastError();
 }
 
@@ -725,6 +772,21 @@ cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b
   return launch_cheb_shaped<T>(dim, g, u, uo, d, b, cd, cr, first, cheb_shape(dim, g.n, (int)sizeof(T)), s);
 }
 
+cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* d, const float* b, double* u64,
+                              double cd, double cr, bool first, cudaStream_t s) {
+  const int n = g.n;
+  const ChebShape sh = cheb_shape(dim, n, 4);
+  const unsigned gx = cdiv(n - 1, sh.block);
+  const unsigned gs = cdiv(n - 1, sh.strip);
+  if (dim == 2)
+    k_cheb_add64<2><<<dim3(gx, gs), sh.block, 0, s>>>(u, d, b, u64, n, 1.0f, (float)cd, (float)cr, first ? 1 : 0,
+                                                      sh.strip);
+  else
+    k_cheb_add64<3><<<dim3(gx, n - 1, gs), sh.block, 0, s>>>(u, d, b, u64, n, (float)n, (float)cd, (float)cr,
+                                                             first ? 1 : 0, sh.strip);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s) {
   k_copy_t<T><<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
@@ -750,9 +812,9 @@ template cudaError_t launch_copy_t<float>(const float*, float*, long long, cudaS
 template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t);
 template cudaError_t launch_rbgs<float>(int, LevelGeo, float*, const float*, int, cudaStream_t);
 template cudaError_t launch_residual_restrict<double, double>(int, LevelGeo, const double*, const double*, LevelGeo,
-                                                              double*, double*, cudaStream_t);
+                                                              double*, double*, cudaStream_t, double*, double);
 template cudaError_t launch_residual_restrict<float, float>(int, LevelGeo, const float*, const float*, LevelGeo,
-                                                            float*, float*, cudaStream_t);
+                                                            float*, float*, cudaStream_t, float*, double);
 template cudaError_t launch_prolong<double, double>(int, LevelGeo, const double*, LevelGeo, double*, int,
                                                     cudaStream_t);
 template cudaError_t launch_prolong<float, float>(int, LevelGeo, const float*, LevelGeo, float*, int, cudaStream_t);
