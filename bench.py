@@ -8,8 +8,10 @@ refinements (2049 x 2049 nodes, 4,190,209 fine DOFs), u* = 8 seeded sin modes
 One step = one fmg_solve of that problem (level-1 Newton, every level's prolongation,
 linearized right-hand side, V-cycles, augmented-space Newton and update) with the inputs
 resident in HBM.  `value` is fine DOFs/s of the mixed-precision path (FP32 cycles inside
-FP64 defect correction); the FP64 path is timed beside it ("fp64").  L2 is flushed
-between steps (a 512 MB write outside the timed events).
+FP64 defect correction); the FP64 path is timed beside it ("fp64").  By default each path
+uses its faster smoother at equal accuracy (mixed: Chebyshev-Jacobi with autotuned launch
+shapes; FP64: red-black Gauss-Seidel).  L2 is flushed between steps (a 512 MB write outside
+the timed events).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 Under torchrun each rank solves its own instance (independent problems, weak scaling);
@@ -58,10 +60,11 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--max-inflight", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--autotune", action="store_true",
-                    help="tune the launch shapes of the Chebyshev step kernel before timing")
-    ap.add_argument("--smoother", default="rbgs", choices=["rbgs", "chebyshev"],
-                    help="smoother of the multigrid cycles (large2d / 3d workloads)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip tuning the launch shapes of the Chebyshev step kernel before timing")
+    ap.add_argument("--smoother", default="auto", choices=["auto", "rbgs", "chebyshev"],
+                    help="smoother of the multigrid cycles (large2d / 3d); auto: each arm's faster one at "
+                         "equal accuracy (2D: Chebyshev for the mixed path, red-black for FP64; 3D: red-black)")
     return ap.parse_args()
 
 
@@ -284,7 +287,11 @@ def run_ours(args):
     # 3D V-cycles with Chebyshev smoothing contract by about 0.33 (red-black Gauss-Seidel 0.26):
     # three cycles per correction step keep the algebraic error below a tenth of the
     # discretization error there
-    m_cycles = 3 if (dim == 3 and args.smoother == "chebyshev") else 2
+    if args.smoother == "auto":
+        smoother = {"mixed": "chebyshev" if dim == 2 else "rbgs", "fp64": "rbgs"}
+    else:
+        smoother = {"mixed": args.smoother, "fp64": args.smoother}
+    m_cycles = {p: 3 if (dim == 3 and smoother[p] == "chebyshev") else 2 for p in smoother}
     g = prob.g_nodal()
     dofs = prob.fine_dofs
     n = prob.n_fine
@@ -295,8 +302,8 @@ def run_ours(args):
     solvers = {}
     log("creating solvers")
     for prec in ("mixed", "fp64"):
-        s = fmg.Solver(fmg.make_params(prob, precision=prec, smoother=args.smoother, m_vcycles=m_cycles), g)
-        if args.autotune:
+        s = fmg.Solver(fmg.make_params(prob, precision=prec, smoother=smoother[prec], m_vcycles=m_cycles[prec]), g)
+        if not args.no_autotune:
             fmg.fmg_autotune(s.ctx)
         st = fmg.fmg_stats()
         s.solve(stats=st)
@@ -348,7 +355,7 @@ def run_ours(args):
                       "traffic": TRAFFIC.get(("augmented", dim)), "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
                       "avg_launch_ms": aug_ms, "launches": aug_n, "algorithmic_flops_per_launch": aug_flops},
     }
-    if dim == 2 and args.smoother == "rbgs":
+    if dim == 2 and smoother["mixed"] == "rbgs":
         pre_ms, pre_n = kt[fmg.KT_PRE_TOP]
         post_ms, post_n = kt[fmg.KT_POST_TOP]
         # fused pre-smoothing on the top level: reads b (4 B/node), writes the correction
@@ -370,7 +377,7 @@ def run_ours(args):
                             "avg_launch_ms": post_ms, "launches": post_n, "algorithmic_bytes_per_launch": post_bytes}
     else:
         sm_ms, sm_n = kt[fmg.KT_SMOOTH_TOP]
-        if args.smoother == "chebyshev":
+        if smoother["mixed"] == "chebyshev":
             # one Chebyshev step in FP32: read u, b (and d after the first step), write the
             # new iterate and d = 16 / 20 B/node, 18 B/node on average over nu = 2 steps
             sm_bytes = 18.0 * nodes
@@ -428,13 +435,13 @@ def run_ours(args):
             "dtype": "f32 cycles + f64 residual/Newton",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if dim == 2 else WORKLOAD_3D, "precision": "mixed",
-                       "smoother": args.smoother, "instances": world,
-                       "autotuned": bool(args.autotune),
+                       "smoother": smoother["mixed"], "fp64_smoother": smoother["fp64"], "instances": world,
+                       "autotuned": not args.no_autotune,
                        "top_level_cheb_shape": (fmg.fmg_tuned_shape(solvers["mixed"].ctx, top)
-                                                if args.smoother == "chebyshev" else None),
+                                                if smoother["mixed"] == "chebyshev" else None),
                        "global_batch": world, "seq_len": None, "parallelism": f"independent instances x{world}",
                        "l2": "flushed between steps (512 MB write outside the timed events)",
-                       "m": m_cycles, "nu": [2, 2], "p": 1},
+                       "m": m_cycles["mixed"], "fp64_m": m_cycles["fp64"], "nu": [2, 2], "p": 1},
             "fp64": {"value": world * dofs / (f64 * 1e-3), "unit": "DOF/s", "ms_per_step": f64,
                      "speedup_mixed_over_fp64": f64 / mix},
             "accuracy": {"l2_err_vs_exact_mixed": acc["mixed"], "l2_err_vs_exact_fp64": acc["fp64"],
@@ -696,11 +703,12 @@ def single_solve(args):
     from paper_1611_05677_gb300 import fmg, workloads as W
 
     prob = W.config_large_2d(refinements=args.refinements)
-    s = fmg.Solver(fmg.make_params(prob, precision=args.precision, smoother=args.smoother), prob.g_nodal())
+    sm = "rbgs" if args.smoother == "auto" else args.smoother
+    s = fmg.Solver(fmg.make_params(prob, precision=args.precision, smoother=sm), prob.g_nodal())
     st = fmg.fmg_stats()
     s.solve(stats=st)
     torch.cuda.synchronize()
-    print(json.dumps({"single_solve": prob.name, "precision": args.precision, "smoother": args.smoother,
+    print(json.dumps({"single_solve": prob.name, "precision": args.precision, "smoother": sm,
                       "newton_iters": list(st.newton_iters[:prob.levels]), "flags": int(st.flags)}))
     s.close()
 
