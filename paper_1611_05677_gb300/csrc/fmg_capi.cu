@@ -233,15 +233,12 @@ const ChebCoef* cheb_coef(const fmg_ctx* c) {
   return c->p.smoother == FMG_SMOOTHER_CHEBYSHEV ? &c->cheb : nullptr;
 }
 
-// Chebyshev-Jacobi steps first..steps-1 on A u = b at level j (one stencil pass each, the
-// iterate alternating between u and alt, d the step direction); the result ends in u.  A
-// caller that already took step 0 (from a zero start, fused into the kernel that produced b)
-// passes first = 1.
+// Chebyshev-Jacobi steps first..steps-1 on A u = b at level j (one stencil pass each, d the
+// step direction), the iterate starting in `cur` and alternating with `oth`; *end receives
+// the buffer that holds the result.
 template <typename T>
-cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int steps, bool top, int first = 0) {
+cudaError_t cheb_run(fmg_ctx* c, int j, T* cur, T* oth, T* d, const T* b, int first, int steps, bool top, T** end) {
   const LevelGeo g = c->geo[j - 1];
-  T* cur = u;
-  T* oth = alt;
   for (int k = first; k < steps; ++k) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
@@ -251,7 +248,27 @@ cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int st
     cur = oth;
     oth = t;
   }
-  if (cur != u) TRY(launch_copy_t<T>(cur, u, g.nodes, c->stream));
+  *end = cur;
+  return cudaSuccess;
+}
+
+// The buffer that a Chebyshev step 0 taken from a zero start (fused into the kernel that
+// produces b) writes, so that the remaining steps first..steps-1 end in u: u when their
+// number is even, alt when it is odd.
+template <typename T>
+T* cheb_start(T* u, T* alt, int steps) {
+  return ((steps - 1) & 1) ? alt : u;
+}
+
+// Chebyshev-Jacobi steps first..steps-1 on A u = b at level j; the iterate starts in
+// cheb_start(u, alt, steps) when first = 1 (step 0 fused upstream), in u otherwise, and the
+// result ends in u (a copy only when first = 0 and the step count is odd).
+template <typename T>
+cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int steps, bool top, int first = 0) {
+  T* start = first ? cheb_start(u, alt, steps) : u;
+  T* end = nullptr;
+  TRY(cheb_run<T>(c, j, start, start == u ? alt : u, d, b, first, steps, top, &end));
+  if (end != u) TRY(launch_copy_t<T>(end, u, c->geo[j - 1].nodes, c->stream));
   return cudaSuccess;
 }
 
@@ -303,7 +320,8 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
     TRY(tend(c, slot));
   }
   const bool fuse = fuse_first_step<double>(c, j - 1);
-  TRY(launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], c->u[j - 2], s,
+  double* uc0 = fuse ? cheb_start(c->u[j - 2], c->ua[j - 2], c->p.nu_pre) : c->u[j - 2];
+  TRY(launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], uc0, s,
                                                fuse ? c->dd[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0));
   TRY(vcycle(c, j - 1, c->u[j - 2], c->b[j - 2], false, fuse));
   TRY(launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s));
@@ -376,14 +394,19 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
     TRY(tend(c, slot));
   }
   const bool fuse = fuse_first_step<float>(c, j - 1);
-  TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], c->u32[j - 2], s,
+  float* uc0 = fuse ? cheb_start(c->u32[j - 2], c->u32b[j - 2], c->p.nu_pre) : c->u32[j - 2];
+  TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], uc0, s,
                                              fuse ? c->d32[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0));
   TRY(vcycle32(c, j - 1, false, fuse));
   TRY(launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s));
   if (cheb && u64_top && c->p.nu_post >= 1) {
+    // steps 0..last-1, then the last one fused with the FP64 update, reading whichever
+    // buffer holds the iterate
     const int last = c->p.nu_post - 1;
-    TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, last, top));
-    TRY(launch_cheb_add64(dim, gf, u, c->d32[j - 1], b, u64_top, c->cheb.cd[last], c->cheb.cr[last], last == 0, s));
+    float* end = nullptr;
+    TRY(cheb_run<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, 0, last, top, &end));
+    TRY(launch_cheb_add64(dim, gf, end, c->d32[j - 1], b, u64_top, c->cheb.cd[last], c->cheb.cr[last], last == 0,
+                          s));
     return cudaSuccess;
   }
   if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_post, top));
@@ -405,7 +428,8 @@ cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
   // defect correction: FP64 residual -> FP32 cycle from e = 0 -> FP64 update (with Chebyshev
   // smoothing the cycle's first step is fused into the residual and its last into the update)
   const bool fuse = fuse_first_step<float>(c, k);
-  TRY(launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], c->u32[k - 1], c->stream,
+  float* e0buf = fuse ? cheb_start(c->u32[k - 1], c->u32b[k - 1], c->p.nu_pre) : c->u32[k - 1];
+  TRY(launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], e0buf, c->stream,
                              fuse ? c->d32[k - 1] : nullptr, fuse ? cheb_e0(c, k) : 0.0));
   if (c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS) return vcycle32_fused(c, k, u);
   if (k > coarse_cycle_top<float>(c)) return vcycle32(c, k, true, fuse, u);

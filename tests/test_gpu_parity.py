@@ -373,3 +373,30 @@ def test_fmg_fixed_point_mixed_below_discretization_error(fmg, dim, H, r, kind):
     assert st.flags == 0
     assert O.discrete_l2(lev, u - res.u[-1]) <= 0.1 * e_disc
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_paper_examples_2_and_3_on_the_cube(fmg, precision):
+    """Sec. 4's second and third examples on the unit cube: f = -exp(-u) with g = 1 (no
+    manufactured solution), and the odd extension of u^{3/2} with u* = prod sin(2 pi x_i)."""
+    ex2 = W.Problem(dim=3, coarse_cells=4, refinements=2, f="neg_exp_neg", a=1.0, g_const=1.0)
+    ex3 = W.Problem(dim=3, coarse_cells=4, refinements=2, f="signed_pow32", a=1.0, modes=[((2, 2, 2), 1.0)])
+    for prob in (ex2, ex3):
+        hier = O.build_hierarchy(3, 4, 2)
+        g = prob.g_nodal()
+        res = O.fmg(hier, g, prob.f, prob.a)
+        lev = hier.level(3)
+        s = make_solver(fmg, prob, precision=precision)
+        st = fmg.fmg_stats()
+        u = s.solve(stats=st).cpu().numpy()
+        assert st.flags == 0
+        if precision == "fp64":
+            assert rel(u, O.to_nodal(lev, res.u[-1])) <= FP64_TOL
+        else:
+            # against the exact discrete solution: the mixed result's algebraic error is the
+            # FP64 method's up to FP32-level rounding
+            ub, _ = O.newton_full(lev, O.load_vector(lev, g), prob.f, prob.a, U0=res.u[-1])
+            e_alg64 = O.discrete_l2(lev, res.u[-1] - ub)
+            e_mixed = O.discrete_l2(lev, O.from_nodal(lev, u) - ub)
+            assert e_mixed <= e_alg64 + 1e-6 * O.discrete_l2(lev, ub)
+        s.close()
