@@ -34,6 +34,7 @@ struct fmg_ctx {
   double* dd[kMaxLevels] = {};
   ChebCoef cheb = {};
   double* Ainv = nullptr;
+  float* Ainv32 = nullptr;   // FP32 copy of A_1^{-1} for the FP32 one-CTA cycles
   DevState* st = nullptr;
   AugBuffers ab = {};
   void* arena = nullptr;
@@ -166,21 +167,19 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
   const int m = p->coarse_cells - 1;
   const long long N1 = ipow(m, p->dim);
   double* Ainv = (double*)take(N1 * N1 * 8);
+  float* Ainv32 = (float*)take(N1 * N1 * 4);
   DevState* st = (DevState*)take(sizeof(DevState));
   AugBuffers cfg = {};
   aug_configure(p->dim, p->coarse_cells, &cfg);
   const size_t items = cfg.partial_items;
-  double* partials = (double*)take(items * aug_nvals(p->dim) * 8);
-  double* cc = (double*)take(ipow(p->coarse_cells + 1, p->dim) * 8);
-  double* sys = (double*)take((2 * N1 + 8 + ipow(p->coarse_cells, p->dim) * ((1 << p->dim) + 1)) * 8);
+  double* partials = (double*)take(2 * items * aug_nvals(p->dim) * 8);
   if (c && base) {
     c->Ainv = Ainv;
+    c->Ainv32 = Ainv32;
     c->st = st;
     c->ab = cfg;
     c->ab.partials = partials;
     c->ab.Ainv = Ainv;
-    c->ab.c = cc;
-    c->ab.sys = sys;
   }
   return off;
 }
@@ -305,8 +304,9 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
     return cudaSuccess;
   }
   if (j <= coarse_cycle_top<double>(c)) {
-    TRY(launch_coarse_cycle<double>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv,
-                                    cheb_coef(c), s));
+    // below the top level the restriction has zeroed u
+    TRY(launch_coarse_cycle<double>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, nullptr,
+                                    cheb_coef(c), !top, s));
     return cudaSuccess;
   }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
@@ -348,8 +348,9 @@ cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
     return cudaSuccess;
   }
   if (j <= coarse_cycle_top<float>(c)) {
+    // the FP32 cycles solve for a correction from zero on every level
     TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, c->u32[j - 1], c->b32[j - 1], c->p.nu_pre,
-                                   c->p.nu_post, c->Ainv, cheb_coef(c), s));
+                                   c->p.nu_post, c->Ainv, c->Ainv32, cheb_coef(c), true, s));
     if (u64_top) TRY(launch_add_f32(c->geo[j - 1], dim, u64_top, c->u32[j - 1], s));
     return cudaSuccess;
   }
@@ -379,8 +380,8 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
     return cudaSuccess;
   }
   if (j <= coarse_cycle_top<float>(c)) {
-    TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv,
-                                   cheb_coef(c), s));
+    TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, u, b, c->p.nu_pre, c->p.nu_post, c->Ainv, c->Ainv32,
+                                   cheb_coef(c), true, s));
     return cudaSuccess;
   }
   const LevelGeo gf = c->geo[j - 1], gc = c->geo[j - 2];
@@ -646,6 +647,8 @@ fmg_status fmg_create(const fmg_params* p, const double* g_fine, int g_on_device
   if (s == FMG_OK) s = load_rhs(c, g_fine, g_on_device);
   if (s == FMG_OK) {
     e = launch_coarse_inverse(p->dim, c->geo[0], c->Ainv, c->st, c->stream);
+    const long long n1 = ipow(p->coarse_cells - 1, p->dim);
+    if (e == cudaSuccess) e = launch_to_f32(c->Ainv, c->Ainv32, n1 * n1, c->stream);
     if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("coarse inverse: ") + cudaGetErrorString(e));
   }
   if (s == FMG_OK) s = read_state(c, nullptr, false);

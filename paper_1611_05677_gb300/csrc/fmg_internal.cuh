@@ -188,9 +188,14 @@ cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s);
 // of them), which need two more arrays per level.
 template <typename T>
 size_t coarse_cycle_smem(int dim, int n0, int jtop, bool cheb);
+// The V(nu_pre, nu_post) cycle on levels jtop..1 in one CTA.  Ainv32: FP32 copy of A_1^{-1}
+// (required for T = float).  zero_start: u is zero on entry (not read).
 template <typename T>
 cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int nu_pre, int nu_post,
-                                const double* Ainv, const ChebCoef* cheb, cudaStream_t s);
+                                const double* Ainv, const float* Ainv32, const ChebCoef* cheb, bool zero_start,
+                                cudaStream_t s);
+// dst = (float) src, n values
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 
 // level-1 setup: Ainv = A_1^{-1} (dense, N_1 x N_1) by Cholesky; flags on failure
 cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s);
@@ -202,9 +207,7 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
 // Augmented problem on V_H + span{u~} (Algorithm 3.1 step 2, eq. 3.6): one cooperative
 // persistent kernel: precompute, Newton iterations, final update u = alpha u~ + P_{H->k} c.
 struct AugBuffers {
-  double* partials;   // [items][nvals]
-  double* c;          // coarse nodal iterate (level-1 layout), length (nH+1)^d
-  double* sys;        // scratch: t, s and the mixed path's first-pass residual sums
+  double* partials;   // two buffers of [items][nvals] (the Newton iterations alternate)
   const double* Ainv; // A_H^{-1} (level-1 inverse; kept with the buffers of the system)
   size_t partial_items;
   int bpc;            // blocks per coarse cell of the cooperative launch (all co-resident)

@@ -56,95 +56,201 @@ __device__ __forceinline__ double recip_pivot(double d) {
   return y * (2.0 - d * y);
 }
 
-// LDL^T factorization (no pivoting) of the n x n SPD matrix A (n <= 64; row-major, leading
-// dimension ld, shared memory, precision T; only the lower triangle is read), in place: below
-// the diagonal A[i][k] keeps the k-th column of the reduced matrix (= L_ik d_k), and
-// rd[k] = 1/d_k.  Step k subtracts A_ik A_jk / d_k from every trailing entry (k < j <= i).
-// The entries of the trailing triangle are dealt to the NT threads through a table of
-// (row, column) offsets listed row by row, so that the triangle of any size m is the table's
-// first m(m+1)/2 entries and a thread touches only live entries.  The thread that updates
-// the next pivot also forms its reciprocal, so a step's critical path is one barrier, one
-// load of 1/d_k and one update.  If drop_last and the last pivot (the Schur complement of the
-// last unknown) falls below drop_tol times the original last diagonal entry, rd[n-1] = 0:
-// that unknown is frozen (*dropped = 1).  Returns false if a pivot is not positive.  Every
-// thread of the block (blockDim.x == NT) calls it.
-template <typename T, int NT>
-__device__ bool ldlt_factor(T* A, int n, int ld, T* rd, bool drop_last, double drop_tol, int* dropped) {
-  __shared__ unsigned short tri[63 * 64 / 2];
-  __shared__ int bad_sh, drop_sh;
-  const int tid = threadIdx.x;
-  for (int di = tid >> 5; di < 63; di += NT / 32)
-    for (int dj = tid & 31; dj <= di; dj += 32) tri[di * (di + 1) / 2 + dj] = (unsigned short)(di | (dj << 8));
+// LDL^T factorization (no pivoting), on ONE warp, of the n x n SPD matrix A whose leading
+// nb = n - border unknowns are banded (A_ij = 0 for i, j < nb and |i - j| > band) and whose
+// last row and column (border = 1) or none (border = 0) are dense: the coarse Jacobians of
+// the Newton steps in lexicographic order (band m or m^2 for the level-1 stencil; m + 1 or
+// m^2 + m + 1 for the coarse-simplex couplings of the augmented system, whose alpha unknown
+// is the border).  Row-major, leading dimension ld, shared memory, precision T; only the
+// lower triangle is read, and its entries outside the pattern must be zero.  Eliminating
+// unknown k touches only the rows R_k = {k+1 .. min(k+band, nb-1)} and the border row, so
+// the pattern is closed under the elimination and step k updates the lower triangle of
+// R_k x R_k -- at most q(q+1)/2 entries, q = band + border -- instead of the whole trailing
+// triangle.  Each entry gets the same operations in the same order as in a dense
+// elimination (the skipped updates subtract exact zeros), so the factor is the dense one.
+// In place: below the diagonal A[i][k] keeps the k-th column of the reduced matrix
+// (= L_ik d_k), and rd[k] = 1/d_k.
+//
+// The positions (a, c), c <= a < q, of R_k x R_k are dealt to the lanes once (NS slots per
+// lane).  A position moves along the diagonal with k (band rows: stride ld + 1) or along the
+// border row (stride 1), so each lane keeps, per slot, the offsets of its entry and of the two
+// column-k entries it needs plus their strides; a slot whose entry has left the matrix keeps
+// the offsets of its last update and stops storing.  At most four slots per lane:
+// (band + border)(band + border + 1) / 2 <= 128.  The step is branch-free (predicated
+// stores; every lane forms a reciprocal and the one that updated the next pivot keeps it),
+// so it costs a few loads, one update and a store per slot, the pivot's reciprocal and one
+// __syncwarp.  If
+// drop_last and the last pivot (the Schur complement of the last unknown) falls below drop_tol
+// times the original last diagonal entry, rd[n-1] = 0: that unknown is frozen (*dropped = 1).
+// Returns false if a pivot is not positive.
+template <typename T, int NS>
+__device__ bool ldlt_band_warp_ns(T* A, int n, int ld, T* rd, int band, int border, bool drop_last, double drop_tol,
+                                  int* dropped) {
+  const int lane = threadIdx.x & 31;
+  const int nb = n - border;
+  const int q = band + border;
+  const int P = q * (q + 1) / 2;
+  int oij[NS], oik[NS], ojk[NS];   // offsets at step k
+  int sij[NS], sik[NS], sjk[NS];   // their strides per step
+  int kend[NS];                    // the entry is updated for k < kend
+  int piv[NS];                     // 1: band pivot, 2: border pivot
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int t = lane + 32 * s;
+    int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= t) ++a;
+    while (a * (a + 1) / 2 > t) --a;
+    const int c = t - a * (a + 1) / 2;
+    kend[s] = 0;
+    piv[s] = 0;
+    oij[s] = oik[s] = ojk[s] = 0;
+    sij[s] = sik[s] = sjk[s] = 0;
+    if (t >= P) continue;
+    if (a < band) {   // band rows k+1+a, k+1+c
+      kend[s] = nb - 1 - a;
+      oij[s] = (1 + a) * ld + 1 + c;
+      oik[s] = (1 + a) * ld;
+      ojk[s] = (1 + c) * ld;
+      sij[s] = sik[s] = sjk[s] = ld + 1;
+      piv[s] = (a == 0) ? 1 : 0;
+    } else if (c < band) {   // border row nb, band column k+1+c
+      kend[s] = nb - 1 - c;
+      oij[s] = nb * ld + 1 + c;
+      oik[s] = nb * ld;
+      ojk[s] = (1 + c) * ld;
+      sij[s] = 1;
+      sik[s] = 1;
+      sjk[s] = ld + 1;
+    } else {   // the border pivot (nb, nb)
+      kend[s] = nb;
+      oij[s] = nb * ld + nb;
+      oik[s] = ojk[s] = nb * ld;
+      sik[s] = sjk[s] = 1;
+      piv[s] = 2;
+    }
+    if (kend[s] <= 0) {   // never updated (the band is wider than the matrix): a safe address
+      oij[s] = oik[s] = ojk[s] = 0;
+      sij[s] = sik[s] = sjk[s] = 0;
+    }
+  }
   const T last0 = drop_last ? A[(n - 1) * ld + (n - 1)] : T(0);
-  // pivot k's reciprocal, or 0 with the flags set (called by one thread per pivot)
-  auto pivot = [&](int k, T d) {
-    T r;
-    if (drop_last && k == n - 1 && !(d > T(drop_tol) * last0)) {
-      drop_sh = 1;
-      r = T(0);
-    } else if (!(d > T(0))) {
-      bad_sh = 1;
-      r = T(0);
-    } else {
-      r = recip_pivot(d);
-    }
-    rd[k] = r;
+  const T drop_at = T(drop_tol) * last0;
+  bool bad = false, drop = false;
+  // reciprocal of pivot k (0 with the flag when it is dropped or not positive)
+  auto pivot_recip = [&](int k, T d, bool& isdrop, bool& isbad) -> T {
+    isdrop = drop_last && k == n - 1 && !(d > drop_at);
+    isbad = !isdrop && !(d > T(0));
+    return (isdrop || isbad) ? T(0) : recip_pivot(d);
   };
-  if (tid == 0) {
-    bad_sh = 0;
-    drop_sh = 0;
-    pivot(0, A[0]);
-  }
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const T r = rd[k];
-    const int m = n - k - 1, cnt = m * (m + 1) / 2;
-    T* trail = A + (size_t)(k + 1) * ld + (k + 1);   // trail[di * ld + dj] = A[k+1+di][k+1+dj]
-    const T* colk = A + (size_t)(k + 1) * ld + k;    // colk[di * ld] = A[k+1+di][k]
-    for (int t = tid; t < cnt; t += NT) {
-      const unsigned e = tri[t];
-      const int di = (int)(e & 255u), dj = (int)(e >> 8);
-      const T v = trail[di * ld + dj] - colk[di * ld] * r * colk[dj * ld];
-      trail[di * ld + dj] = v;
-      if (t == 0) pivot(k + 1, v);   // entry (0, 0) is the next pivot
+  {
+    bool dd, bb;
+    const T r0 = pivot_recip(0, A[0], dd, bb);
+    if (lane == 0) {
+      rd[0] = r0;
+      drop = dd;
+      bad = bb;
     }
-    __syncthreads();
   }
-  if (dropped) *dropped = drop_sh;
-  return bad_sh == 0;
+  __syncwarp();
+  for (int k = 0; k + 1 < n; ++k) {
+    const T r = rd[k];
+    T pv = T(1);
+    bool own = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const bool act = k < kend[s];
+      const T v = A[oij[s]] - A[oik[s]] * r * A[ojk[s]];
+      if (act) A[oij[s]] = v;
+      const bool isp = act && (piv[s] == 1 || (piv[s] == 2 && k == nb - 1));
+      pv = isp ? v : pv;
+      own = own || isp;
+      // advance only while the next step still updates the entry, so that the offsets never
+      // leave the matrix (the loads above run for finished slots too)
+      const bool nxt = k + 1 < kend[s];
+      oij[s] += nxt ? sij[s] : 0;
+      oik[s] += nxt ? sik[s] : 0;
+      ojk[s] += nxt ? sjk[s] : 0;
+    }
+    bool dd, bb;
+    const T rn = pivot_recip(k + 1, pv, dd, bb);
+    if (own) {
+      rd[k + 1] = rn;
+      drop = drop || dd;
+      bad = bad || bb;
+    }
+    __syncwarp();
+  }
+  if (dropped) *dropped = __any_sync(0xffffffffu, drop) ? 1 : 0;
+  return !__any_sync(0xffffffffu, bad);
 }
 
-// Solves L D L^T x = b with the factor of ldlt_factor, on one warp (lane l holds entries l
-// and l + 32; n <= 64): forward substitution column by column, then the backward one row by
-// row, each step one shuffle and no barrier.  b (FP64, shared) is overwritten by x.  Only
-// the calling warp takes part; the caller synchronizes before others read b.
+// Dispatch on the slots per lane the pattern needs; false if it needs more than four.
 template <typename T>
-__device__ void ldlt_solve_warp(const T* A, int n, int ld, const T* rd, double* b) {
+__device__ bool ldlt_band_warp(T* A, int n, int ld, T* rd, int band, int border, bool drop_last, double drop_tol,
+                               int* dropped) {
+  if (border < 0 || border > 1) return false;
+  const int q = band + border;
+  const int ns = (q * (q + 1) / 2 + 31) >> 5;
+  switch (ns) {
+    case 0:
+    case 1: return ldlt_band_warp_ns<T, 1>(A, n, ld, rd, band, border, drop_last, drop_tol, dropped);
+    case 2: return ldlt_band_warp_ns<T, 2>(A, n, ld, rd, band, border, drop_last, drop_tol, dropped);
+    case 3: return ldlt_band_warp_ns<T, 3>(A, n, ld, rd, band, border, drop_last, drop_tol, dropped);
+    case 4: return ldlt_band_warp_ns<T, 4>(A, n, ld, rd, band, border, drop_last, drop_tol, dropped);
+    default: return false;
+  }
+}
+
+// Solves L D L^T x = b with the factor of ldlt_band_warp (same n, band, border), on one warp
+// (lane l holds entries l and l + 32; n <= 64).  Forward substitution column by column over
+// the band rows (one shuffle per step; the rows of the half that the band does not reach are
+// skipped by warp-uniform tests), the border row's part as one dot product after it; then the
+// backward substitution row by row, the border unknown first and its contribution to every
+// other row in one parallel step.  b (FP64, shared) is overwritten by x.  Only the calling
+// warp takes part; the caller synchronizes before others read b.
+template <typename T>
+__device__ void ldlt_solve_band_warp(const T* A, int n, int ld, const T* rd, int band, int border, double* b) {
   const int lane = threadIdx.x & 31;
+  const int nb = n - border;
   const int i0 = lane, i1 = lane + 32;
   T z0 = i0 < n ? (T)b[i0] : T(0), z1 = i1 < n ? (T)b[i1] : T(0);
-  // forward: w_k = z_k / d_k, then z_i -= A_ik w_k for i > k
-#pragma unroll 4
-  for (int k = 0; k < n; ++k) {
+  // forward: w_k = z_k / d_k, then z_i -= A_ik w_k for band rows k < i <= min(k + band, nb - 1)
+  for (int k = 0; k < nb; ++k) {
     const T zk = __shfl_sync(0xffffffffu, k < 32 ? z0 : z1, k & 31);
     const T wk = zk * rd[k];
-    if (i0 > k && i0 < n) z0 -= A[i0 * ld + k] * wk;
-    if (i1 > k && i1 < n) z1 -= A[i1 * ld + k] * wk;
+    const int hi = min(k + band, nb - 1);
+    if (k + 1 < 32 && i0 > k && i0 <= hi) z0 -= A[i0 * ld + k] * wk;
+    if (hi >= 32 && i1 > k && i1 <= hi) z1 -= A[i1 * ld + k] * wk;
     if (i0 == k) z0 = wk;
     if (i1 == k) z1 = wk;
   }
-  // backward: x_k = w_k - (1/d_k) sum_{i>k} A_ik x_i, accumulated row by row
+  // the border row: z_nb -= sum_k A_{nb,k} w_k, then w_nb = z_nb / d_nb
+  if (border) {
+    T part = T(0);
+    if (i0 < nb) part += A[nb * ld + i0] * z0;
+    if (i1 < nb) part += A[nb * ld + i1] * z1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (i0 == nb) z0 = (z0 - part) * rd[nb];
+    if (i1 == nb) z1 = (z1 - part) * rd[nb];
+  }
+  // backward: x_k = w_k - (1/d_k) sum_{i>k} A_ik x_i; s holds the running sums
   T s0 = T(0), s1 = T(0);
-#pragma unroll 4
-  for (int k = n - 1; k >= 0; --k) {
+  if (border) {
+    const T xb = __shfl_sync(0xffffffffu, nb < 32 ? z0 : z1, nb & 31);
+    if (i0 < nb) s0 = A[nb * ld + i0] * xb;
+    if (i1 < nb) s1 = A[nb * ld + i1] * xb;
+  }
+  for (int k = nb - 1; k >= 0; --k) {
     T xk = T(0);
     if (i0 == k) xk = z0 - rd[k] * s0;
     if (i1 == k) xk = z1 - rd[k] * s1;
     xk = __shfl_sync(0xffffffffu, xk, k & 31);
     if (i0 == k) z0 = xk;
     if (i1 == k) z1 = xk;
-    if (i0 < k) s0 += A[k * ld + i0] * xk;
-    if (i1 < k) s1 += A[k * ld + i1] * xk;
+    const int lo = k - band;
+    if (lo < 32 && i0 < k && i0 >= lo) s0 += A[k * ld + i0] * xk;
+    if (k > 32 && i1 < k && i1 >= lo) s1 += A[k * ld + i1] * xk;
   }
   if (i0 < n) b[i0] = (double)z0;
   if (i1 < n) b[i1] = (double)z1;
@@ -193,8 +299,11 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
   const double sigma = dim == 2 ? 1.0 : 1.0 / n1;
   fill_stiffness(M, N, ld, m, dim, sigma);
   __syncthreads();
-  const bool ok = ldlt_factor<double, 64>(M, N, ld, rd, false, 0.0, nullptr);
-  if (!ok && threadIdx.x == 0) atomicOr(&st->flags, kFlagNotSPD);
+  if (threadIdx.x < 32) {
+    const bool ok = ldlt_band_warp<double>(M, N, ld, rd, dim == 2 ? m : m * m, 0, false, 0.0, nullptr);
+    if (!ok && threadIdx.x == 0) atomicOr(&st->flags, kFlagNotSPD);
+  }
+  __syncthreads();
   // column `col` of the inverse: L D L^T x = e_col (A^{-1} is symmetric: column = row), with
   // L_kj = M[k][j] / d_j below the diagonal
   for (int col = threadIdx.x; col < N; col += blockDim.x) {
@@ -230,11 +339,14 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
   T* L = reinterpret_cast<T*>(Fp + N);
   T* work = L + (size_t)N * ld;
   T* invd = work + N;
-  __shared__ int done;
+  __shared__ int done, ok_sh;
   const double h = 1.0 / n1;
   const double sigma = dim == 2 ? 1.0 : h;
   const double w = dim == 2 ? h * h : h * h * h;
+  const int band = dim == 2 ? m : m * m;   // lexicographic half-bandwidth of the 2d+1-point stencil
   for (int i = threadIdx.x; i < N; i += blockDim.x) U[i] = 0.0;
+  // entries outside the band are zero and the factorization never writes them
+  for (int i = threadIdx.x; i < N * ld; i += blockDim.x) L[i] = T(0);
   if (threadIdx.x == 0) done = 0;
   __syncthreads();
   int it = 0;
@@ -257,8 +369,11 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
       Fp[p] = w * D;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int p = idx / N, q = idx % N;
+    // the lower band of the Jacobian A_1 + diag(w f'(U)) (the factor of the previous
+    // iteration overwrote it)
+    for (int idx = threadIdx.x; idx < N * (band + 1); idx += blockDim.x) {
+      const int p = idx / (band + 1), q = p - idx % (band + 1);
+      if (q < 0) continue;
       double v = 0.0;
       if (p == q) {
         v = sigma * 2 * dim + Fp[p];
@@ -274,9 +389,13 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
       L[p * ld + q] = (T)v;
     }
     __syncthreads();
-    const bool ok = ldlt_factor<T, 256>(L, N, ld, invd, false, 0.0, nullptr);
-    if (threadIdx.x < 32) ldlt_solve_warp<T>(L, N, ld, invd, rhs);
+    if (threadIdx.x < 32) {
+      const bool okw = ldlt_band_warp<T>(L, N, ld, invd, band, 0, false, 0.0, nullptr);
+      ldlt_solve_band_warp<T>(L, N, ld, invd, band, 0, rhs);
+      if (threadIdx.x == 0) ok_sh = okw ? 1 : 0;
+    }
     __syncthreads();
+    const bool ok = ok_sh != 0;
     if (threadIdx.x < 32) {
       double dmax = 0.0, umax = 0.0;
       bool finite = true;
@@ -372,9 +491,8 @@ struct AugArgs {
   double a, w, sigma_k, sigma_H, tol;
   double* u;            // u~ on entry, u^{(l+1)} on exit (level-k nodal)
   const double* g;      // level-k nodal g
-  double* partials;     // [cells * bpc][NVAL]
-  double* c;            // coarse nodal iterate ((nc+1)^d, boundary 0)
-  double* sys;          // t[NH], s, (pad), mixed path: first-pass residual sums [ncell (NV+1)]
+  double* partials;     // two buffers of [cells * bpc][NVAL] block partial rows
+  long long pstride;    // doubles per buffer
   const double* Ainv;   // A_H^{-1} (= A_1^{-1}, h_1 = H), dense NH x NH, preconditioner
   DevState* st;
 };
@@ -817,18 +935,94 @@ __device__ double pair_channel(const double* cellsum, int nc, const int* zp, con
   return x;
 }
 
+// Lexicographic half-bandwidth of J_HH: it couples coarse nodes that share a coarse simplex,
+// offsets up to 1 + m (2D) or 1 + m + m^2 (3D), m = nc - 1; alpha is the border unknown.
 template <int D>
-__device__ void newton_update(const AugArgs& A, const double* R, int NH, double alpha, int dropped, bool ok);
+__device__ __forceinline__ int aug_band(int nc) {
+  const int m = nc - 1;
+  return D == 2 ? m + 1 : m * m + m + 1;
+}
 
-// Block 0, after a pass: cell sums, the dense system, the Newton step, convergence.  In the
-// mixed path (JF32) the first iteration factors its Jacobian into L (LDL^T, FP32, with the
-// reciprocal pivots after it) and the later iterations are chord steps with that factor.
+// Block-local state of the Newton iteration, in shared memory past the channel rows, kept
+// from pass to pass.  Every block of the grid (every CTA of a cluster) takes the same Newton
+// step from the same partial sums in the same order, so all hold the same iterate and reach
+// the same decisions: no second barrier and no global copy of the iterate are needed.
+struct StepState {
+  double* c;       // coarse nodal iterate ((nc+1)^d values, boundary 0)
+  double* t;       // t = P^T A_k u~  [N_H]
+  double* sa;      // [0] s = u~.A_k u~, [1] alpha
+  double* basev;   // mixed path: the first pass's FP64 residual sums [ncell (NV+1)]
+  int* flags;      // [0] converged, [1] stop (a pivot was not positive or a value not finite)
+};
+
+// Shared memory of the Newton kernels: the channel rows (reused after each pass for cellsum
+// [ncell NVAL], M [NA (NA+1)] and R [NA+1]), then the StepState arrays, then the factor L
+// [NA (NA+1)] and its reciprocal pivots [NA] in the factor's precision.
+template <int D, bool JF32>
+struct AugSmem {
+  using G = Aug<D, JF32>;
+  using FT = typename std::conditional<JF32, float, double>::type;
+  __host__ __device__ static int ncell(int nc) { return (int)ipow(nc, D); }
+  __host__ __device__ static int NA(int nc) { return (int)ipow(nc - 1, D) + 1; }
+  __host__ __device__ static size_t region(int nc) {
+    const size_t na = (size_t)NA(nc);
+    const size_t scratch = sizeof(double) * ((size_t)ncell(nc) * G::NVAL + na * (na + 1) + na + 1);
+    const size_t r = Rows<D, JF32>::bytes > scratch ? Rows<D, JF32>::bytes : scratch;
+    return (r + 15) & ~size_t(15);
+  }
+  __host__ __device__ static size_t state_doubles(int nc) {
+    return (size_t)ipow(nc + 1, D) + (size_t)(NA(nc) - 1) + 2 + (size_t)ncell(nc) * (G::NV + 1);
+  }
+  __host__ __device__ static size_t bytes(int nc) {
+    const size_t na = (size_t)NA(nc);
+    return region(nc) + sizeof(double) * state_doubles(nc) + sizeof(FT) * (na * (na + 1) + na);
+  }
+  __device__ static void carve(double* sm, int nc, StepState& S, FT*& L) {
+    char* base = reinterpret_cast<char*>(sm) + region(nc);
+    S.c = reinterpret_cast<double*>(base);
+    S.t = S.c + ipow(nc + 1, D);
+    S.sa = S.t + (NA(nc) - 1);
+    S.basev = S.sa + 2;
+    L = reinterpret_cast<FT*>(S.basev + (size_t)ncell(nc) * (G::NV + 1));
+  }
+};
+
+// Sum over the bpc blocks of a cell of one channel of their partial rows, in block order, with
+// the loads of four blocks issued together.
+template <int NVAL>
+__device__ __forceinline__ double sum_blocks(const double* __restrict__ p, int bpc) {
+  double x = 0.0;
+  int b = 0;
+  for (; b + 4 <= bpc; b += 4) {
+    const double v0 = __ldcg(p + (size_t)(b + 0) * NVAL), v1 = __ldcg(p + (size_t)(b + 1) * NVAL);
+    const double v2 = __ldcg(p + (size_t)(b + 2) * NVAL), v3 = __ldcg(p + (size_t)(b + 3) * NVAL);
+    x += v0;
+    x += v1;
+    x += v2;
+    x += v3;
+  }
+  for (; b < bpc; ++b) x += __ldcg(p + (size_t)b * NVAL);
+  return x;
+}
+
+template <int D>
+__device__ void newton_update(const AugArgs& A, const double* R, int NH, const StepState& S, int dropped, bool ok,
+                              bool writer);
+
+// After a pass, in every block: cell sums, the dense system, the Newton step, convergence.
+// In the mixed path (JF32) the first iteration factors its Jacobian into L (LDL^T, FP32, with
+// the reciprocal pivots after it) and the later iterations are chord steps with that factor.
 // The fixed-point iteration (A.fixed_point) factors the Galerkin stiffness [[A_H, t], [t^T, s]]
 // once, in the path's precision, and every iteration solves with it against the residual
-// (y_{k+1} = y_k - K^{-1} R(y_k), i.e. K y_{k+1} = G - B^T W f(B y_k)).
+// (y_{k+1} = y_k - K^{-1} R(y_k), i.e. K y_{k+1} = G - B^T W f(B y_k)).  `partials` is this
+// iteration's buffer of block partial rows; only the writer block reports to DevState.
+// Not inlined: the dense step runs once per pass, and its own register allocation keeps it
+// from raising the pressure in the fine pass.
 template <int D, bool JF32>
-__device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double* R,
-                            typename std::conditional<JF32, float, double>::type* L, double alpha, bool first) {
+__device__ __noinline__ void newton_step(const AugArgs& A, const double* __restrict__ partials, double* cellsum,
+                                         double* M,
+                            double* R, typename std::conditional<JF32, float, double>::type* L, const StepState& S,
+                            bool first, bool writer) {
   using FT = typename std::conditional<JF32, float, double>::type;
   using G = Aug<D, JF32>;
   const int tid = threadIdx.x;
@@ -837,19 +1031,17 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
   const int NA = NH + 1;
   const int ld = NA + 1;
   constexpr int N3 = D == 2 ? 9 : 27;
-  double* t_vec = A.sys;
-  double* s_val = A.sys + NH;        // s; the mixed path's first-pass residual sums follow
-  double* basev = A.sys + NH + 2;
+  const double alpha = S.sa[1];
+  const double* t_vec = S.t;
   if ((JF32 || A.fixed_point) && !first) {
     // chord / fixed-point step: the residual at the new iterate (mixed path: first-pass FP64
     // sums plus this pass's increments; FP64 path: this pass's sums), solved with the factor
     // of the first iteration
     for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
       const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
-      const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
-      double x = 0.0;
-      for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + ch % G::NVAL]);
-      cellsum[ch] = JF32 ? x + basev[idx] : x;
+      const int chn = v < G::NV ? G::RA + v : G::SA;
+      const double x = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + chn, A.bpc);
+      cellsum[(size_t)cell * G::NVAL + chn] = JF32 ? x + S.basev[idx] : x;
     }
     __syncthreads();
     const double sig = A.sigma_H;
@@ -860,10 +1052,10 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       double nb = 0.0;
       long long mul = 1;
       for (int q = 0; q < D; ++q) {
-        nb += __ldcg(&A.c[off - mul]) + __ldcg(&A.c[off + mul]);
+        nb += S.c[off - mul] + S.c[off + mul];
         mul *= (A.nc + 1);
       }
-      const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
+      const double ahc = sig * (2.0 * D * S.c[off] - nb);
       R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA));
     }
     if (tid < 32) {
@@ -872,19 +1064,19 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       for (int p = tid; p < NH; p += 32) {
         int z[3];
         unknown_coords<D>(p, A.nc, z);
-        tc += t_vec[p] * __ldcg(&A.c[coarse_offset<D>(z, A.nc)]);
+        tc += t_vec[p] * S.c[coarse_offset<D>(z, A.nc)];
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         tc += __shfl_xor_sync(0xffffffffu, tc, o);
       }
-      if (tid == 0) R[NH] = -(tc + alpha * s_val[0] + s2);
+      if (tid == 0) R[NH] = -(tc + alpha * S.sa[0] + s2);
     }
     __syncthreads();
-    if (tid < 32) ldlt_solve_warp<FT>(L, NA, ld, L + (size_t)NA * ld, R);
+    if (tid < 32) ldlt_solve_band_warp<FT>(L, NA, ld, L + (size_t)NA * ld, aug_band<D>(A.nc), 1, R);
     __syncthreads();
-    newton_update<D>(A, R, NH, alpha, 0, true);
+    newton_update<D>(A, R, NH, S, 0, true, writer);
     return;
   }
   // cell sums over the blocks of each cell (fixed order)
@@ -892,22 +1084,20 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     const int cell = idx / G::NVAL, v = idx % G::NVAL;
     if (!first && v >= G::TT && v < G::JB) continue;
     if (A.fixed_point && v >= G::JB) continue;
-    double x = 0.0;
-    for (int b = 0; b < A.bpc; ++b) x += __ldcg(&A.partials[((long long)cell * A.bpc + b) * G::NVAL + v]);
-    cellsum[idx] = x;
+    cellsum[idx] = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + v, A.bpc);
   }
   for (int idx = tid; idx < NA * ld; idx += blockDim.x) M[idx] = 0.0;
   __syncthreads();
   if (JF32) {
     // mixed path: after the first pass the residual channels hold increments; the first
-    // pass's FP64 sums are kept in sys and added back (fixed order, same thread each time)
+    // pass's FP64 sums are kept in basev and added back (fixed order, same thread each time)
     for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
       const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
       const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
       if (first)
-        basev[idx] = cellsum[ch];
+        S.basev[idx] = cellsum[ch];
       else
-        cellsum[ch] += basev[idx];
+        cellsum[ch] += S.basev[idx];
     }
     __syncthreads();
   }
@@ -915,14 +1105,14 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     for (int p = tid; p < NH; p += blockDim.x) {
       int z[3];
       unknown_coords<D>(p, A.nc, z);
-      t_vec[p] = node_channel<D, JF32>(cellsum, A.nc, z, G::TT);
+      S.t[p] = node_channel<D, JF32>(cellsum, A.nc, z, G::TT);
     }
     if (tid < 32) {
       double s0 = 0.0;
       for (int c = tid; c < ncell; c += 32) s0 += cellsum[(long long)c * G::NVAL + G::SS];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      if (tid == 0) s_val[0] = s0;
+      if (tid == 0) S.sa[0] = s0;
     }
     __syncthreads();
   }
@@ -958,10 +1148,10 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     double nb = 0.0;
     long long mul = 1;
     for (int q = 0; q < D; ++q) {
-      nb += __ldcg(&A.c[off - mul]) + __ldcg(&A.c[off + mul]);
+      nb += S.c[off - mul] + S.c[off + mul];
       mul *= (A.nc + 1);
     }
-    const double ahc = sig * (2.0 * D * __ldcg(&A.c[off]) - nb);
+    const double ahc = sig * (2.0 * D * S.c[off] - nb);
     R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA));
     const double jb = t_vec[p] + (A.fixed_point ? 0.0 : node_channel<D, JF32>(cellsum, A.nc, z, G::JB));
     M[p * ld + NH] = jb;
@@ -976,7 +1166,7 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
     for (int p = tid; p < NH; p += 32) {
       int z[3];
       unknown_coords<D>(p, A.nc, z);
-      tc += t_vec[p] * __ldcg(&A.c[coarse_offset<D>(z, A.nc)]);
+      tc += t_vec[p] * S.c[coarse_offset<D>(z, A.nc)];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -985,35 +1175,32 @@ __device__ void newton_step(const AugArgs& A, double* cellsum, double* M, double
       tc += __shfl_xor_sync(0xffffffffu, tc, o);
     }
     if (tid == 0) {
-      R[NH] = -(tc + alpha * s_val[0] + s2);
-      M[NH * ld + NH] = s_val[0] + s3;
+      R[NH] = -(tc + alpha * S.sa[0] + s2);
+      M[NH * ld + NH] = S.sa[0] + s3;
     }
   }
   __syncthreads();
-  // Newton step.  FP64 path: LDL^T in FP64.  Mixed path: LDL^T in FP32, kept in L for the
-  // chord steps of the later iterations.
+  // Newton step on warp 0.  FP64 path: LDL^T in FP64.  Mixed path: LDL^T in FP32, kept in L
+  // for the chord steps of the later iterations.
   int dropped = 0;
   bool ok = true;
   for (int idx = tid; idx < NA * ld; idx += blockDim.x) L[idx] = (FT)M[idx];
   __syncthreads();
-  if (JF32) {
-    float* Lf = reinterpret_cast<float*>(L);
-    float* rd = Lf + (size_t)NA * ld;
-    ok = ldlt_factor<float, G::NT>(Lf, NA, ld, rd, true, 1e-6, &dropped);
-    if (tid < 32) ldlt_solve_warp<float>(Lf, NA, ld, rd, R);
-    __syncthreads();
-  } else {
-    FT* rd = L + (size_t)NA * ld;
-    ok = ldlt_factor<FT, G::NT>(L, NA, ld, rd, true, 1e-14, &dropped);
-    if (tid < 32) ldlt_solve_warp<FT>(L, NA, ld, rd, R);
-    __syncthreads();
+  const int band = aug_band<D>(A.nc);
+  FT* rd = L + (size_t)NA * ld;
+  if (tid < 32) {
+    ok = ldlt_band_warp<FT>(L, NA, ld, rd, band, 1, true, JF32 ? 1e-6 : 1e-14, &dropped);
+    ldlt_solve_band_warp<FT>(L, NA, ld, rd, band, 1, R);
   }
-  newton_update<D>(A, R, NH, alpha, dropped, ok);
+  __syncthreads();
+  newton_update<D>(A, R, NH, S, dropped, ok, writer);
 }
 
-// (c, alpha) += the step in R, convergence test and status flags (warp 0 of the solving block).
+// (c, alpha) += the step in R, convergence test and stop flags (warp 0 of every block; the
+// writer block also reports to DevState).
 template <int D>
-__device__ void newton_update(const AugArgs& A, const double* R, int NH, double alpha, int dropped, bool ok) {
+__device__ void newton_update(const AugArgs& A, const double* R, int NH, const StepState& S, int dropped, bool ok,
+                              bool writer) {
   const int tid = threadIdx.x;
   if (tid < 32) {
     double dmax = 0.0, ymax = 0.0;
@@ -1022,13 +1209,13 @@ __device__ void newton_update(const AugArgs& A, const double* R, int NH, double 
       int z[3];
       unknown_coords<D>(p, A.nc, z);
       const long long off = coarse_offset<D>(z, A.nc);
-      const double nv = __ldcg(&A.c[off]) + R[p];
+      const double nv = S.c[off] + R[p];
       if (!isfinite(nv)) finite = false;
-      A.c[off] = nv;
+      S.c[off] = nv;
       dmax = fmax(dmax, fabs(R[p]));
       ymax = fmax(ymax, fabs(nv));
     }
-    const double na = alpha + R[NH];
+    const double na = S.sa[1] + R[NH];
     if (tid == 0) {
       if (!isfinite(na)) finite = false;
       dmax = fmax(dmax, fabs(R[NH]));
@@ -1041,45 +1228,55 @@ __device__ void newton_update(const AugArgs& A, const double* R, int NH, double 
     }
     finite = __all_sync(0xffffffffu, finite);
     if (tid == 0) {
-      A.st->alpha_cur = na;
-      if (dropped) atomicOr(&A.st->flags, kFlagDropped);
-      if (!ok) atomicOr(&A.st->flags, kFlagNotSPD);
-      if (!finite) atomicOr(&A.st->flags, kFlagNonfinite);
-      if (!ok || !finite) A.st->abort = 1;
-      if (dmax <= A.tol * fmax(1.0, ymax)) A.st->converged = 1;
-      __threadfence();
+      S.sa[1] = na;
+      S.flags[1] = (!ok || !finite) ? 1 : 0;
+      S.flags[0] = (dmax <= A.tol * fmax(1.0, ymax)) ? 1 : 0;
+      if (writer) {
+        if (dropped) atomicOr(&A.st->flags, kFlagDropped);
+        if (!ok) atomicOr(&A.st->flags, kFlagNotSPD);
+        if (!finite) atomicOr(&A.st->flags, kFlagNonfinite);
+      }
     }
   }
 }
 
-// Where the solving block keeps the Newton factor.  FP64 Newton: after R (a scratch that the
-// next pass may overwrite).  Mixed path and fixed-point iteration: past the channel rows, so
-// that the first iteration's factor survives the later passes.
-template <int D, bool JF32, typename FT>
-__device__ __forceinline__ FT* aug_factor(double* sm, double* R, int NA, bool fixed_point) {
-  if (JF32 || fixed_point) {
-    char* rows_end = reinterpret_cast<char*>(sm) + Rows<D, JF32>::bytes;
-    char* scratch_end = reinterpret_cast<char*>(R + NA + 1);
-    return reinterpret_cast<FT*>(rows_end > scratch_end ? rows_end : scratch_end);
+// Before the first pass, in every block: c = 0, alpha = 1, flags clear.
+template <int D>
+__device__ void step_state_init(const AugArgs& A, const StepState& S) {
+  const long long cn = ipow(A.nc + 1, D);
+  for (long long i = threadIdx.x; i < cn; i += blockDim.x) S.c[i] = 0.0;
+  if (threadIdx.x == 0) {
+    S.sa[1] = 1.0;
+    S.flags[0] = 0;
+    S.flags[1] = 0;
   }
-  return reinterpret_cast<FT*>(R + NA + 1);
+  __syncthreads();
+}
+
+// After the iteration, the writer block: iteration count, alpha and the Newton-cap flag.
+__device__ void step_report(const AugArgs& A, const StepState& S, int it, bool writer) {
+  if (writer && threadIdx.x == 0) {
+    if (!(S.flags[0] && !S.flags[1])) atomicOr(&A.st->flags, kFlagNewtonCap);
+    A.st->newton_iters[A.level_index] += it > A.maxit ? A.maxit : it;
+    A.st->alpha[A.level_index] = S.sa[1];
+  }
 }
 
 template <int D, bool JF32>
 __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
   using G = Aug<D, JF32>;
+  using FT = typename std::conditional<JF32, float, double>::type;
   extern __shared__ double sm[];
-  double* acc = sm;                                 // NVAL * NT
+  double* acc = sm;                                 // channel rows [NVAL][NT]
   __shared__ double cv[G::NV];
-  __shared__ double alpha_sh;
+  __shared__ int flags_sh[2];
   __shared__ int stop;
   const int tid = threadIdx.x;
   const unsigned nblocks = gridDim.x;
   const int cell = blockIdx.x / A.bpc;
   const int bic = blockIdx.x % A.bpc;
   const int ncell = (int)ipow(A.nc, D);
-  const int NH = (int)ipow(A.nc - 1, D);
-  const int NA = NH + 1;
+  const int NA = (int)ipow(A.nc - 1, D) + 1;
   int cellc[3] = {0, 0, 0};
   {
     int t = cell;
@@ -1096,55 +1293,40 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
       mul *= (A.nc + 1);
     }
   }
-  // block-0 scratch, reusing the channel rows once they are reduced: cellsum [ncell * NVAL],
-  // M [NA * (NA+1)], R [NA], then the factor L [NA * (NA+1)] and work/invd [2 NA] in the
-  // factor's precision
-  using FT = typename std::conditional<JF32, float, double>::type;
   double* cellsum = acc;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  FT* L = aug_factor<D, JF32, FT>(sm, R, NA, A.fixed_point != 0);
-
-  if (blockIdx.x == 0) {
-    const long long cn = ipow(A.nc + 1, D);
-    for (long long i = tid; i < cn; i += blockDim.x) A.c[i] = 0.0;
-    if (tid == 0) {
-      A.st->alpha_cur = 1.0;
-      A.st->converged = 0;
-    }
-  }
+  StepState S;
+  FT* L;
+  AugSmem<D, JF32>::carve(sm, A.nc, S, L);
+  S.flags = flags_sh;
+  step_state_init<D>(A, S);
+  const bool writer = blockIdx.x == 0;
   int it = 0;
   for (it = 1; it <= A.maxit; ++it) {
     const bool first = it == 1;
-    if (tid < G::NV) cv[tid] = first ? 0.0 : __ldcg(&A.c[vert_off]);
-    if (tid == 0) {
-      alpha_sh = first ? 1.0 : ((volatile double*)&A.st->alpha_cur)[0];
-      stop = ((volatile int*)&A.st->abort)[0];
-    }
+    // partial rows alternate between two buffers: a block that starts the next pass cannot
+    // overwrite sums that another block is still reading
+    double* pbuf = A.partials + (size_t)(it & 1) * A.pstride;
+    if (tid < G::NV) cv[tid] = S.c[vert_off];
+    if (tid == 0) stop = ((volatile int*)&A.st->abort)[0];
     // chord steps of the mixed path fill the residual channels RA, SA only
     Rows<D, JF32>::zero(acc, first, A.fixed_point != 0, tid);
     __syncthreads();
     if (stop) break;
-    fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, bic);
-    block_reduce_rows<D, JF32>(acc, A.partials + (long long)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
+    fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, bic);
+    block_reduce_rows<D, JF32>(acc, pbuf + (size_t)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
     grid_barrier(A.st, nblocks);
-    if (blockIdx.x == 0) newton_step<D, JF32>(A, cellsum, M, R, L, alpha_sh, first);
-    grid_barrier(A.st, nblocks);
-    if (tid == 0) stop = ((volatile int*)&A.st->converged)[0] | ((volatile int*)&A.st->abort)[0];
+    newton_step<D, JF32>(A, pbuf, cellsum, M, R, L, S, first, writer);
     __syncthreads();
-    if (stop) break;
+    if (flags_sh[0] || flags_sh[1]) break;
   }
-  if (blockIdx.x == 0 && tid == 0) {
-    const int conv = ((volatile int*)&A.st->converged)[0];
-    if (!conv) atomicOr(&A.st->flags, kFlagNewtonCap);
-    A.st->newton_iters[A.level_index] += it > A.maxit ? A.maxit : it;
-    A.st->alpha[A.level_index] = ((volatile double*)&A.st->alpha_cur)[0];
-  }
+  step_report(A, S, it, writer);
+  if (flags_sh[1] && writer && tid == 0) A.st->abort = 1;
   // final update u = alpha u~ + P_{H->k} c
-  if (tid < G::NV) cv[tid] = __ldcg(&A.c[vert_off]);
-  if (tid == 0) alpha_sh = ((volatile double*)&A.st->alpha_cur)[0];
+  if (tid < G::NV) cv[tid] = S.c[vert_off];
   __syncthreads();
-  fine_pass<D, JF32>(A, kUpdate, acc, cv, alpha_sh, cell, bic);
+  fine_pass<D, JF32>(A, kUpdate, acc, cv, S.sa[1], cell, bic);
 }
 
 // The same Newton iteration for one instance on a thread-block cluster instead of a
@@ -1155,6 +1337,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
 template <int D, bool JF32>
 __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs A) {
   using G = Aug<D, JF32>;
+  using FT = typename std::conditional<JF32, float, double>::type;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -1162,17 +1345,18 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs 
   extern __shared__ double sm[];
   double* acc = sm;
   __shared__ double cv[G::NV];
-  __shared__ double alpha_sh;
+  __shared__ int flags_sh[2];
   __shared__ int stop;
   const int tid = threadIdx.x;
   const int ncell = (int)ipow(A.nc, D);
-  const int NH = (int)ipow(A.nc - 1, D);
-  const int NA = NH + 1;
-  using FT = typename std::conditional<JF32, float, double>::type;
+  const int NA = (int)ipow(A.nc - 1, D) + 1;
   double* cellsum = acc;
   double* M = cellsum + (size_t)ncell * G::NVAL;
   double* R = M + (size_t)NA * (NA + 1);
-  FT* L = aug_factor<D, JF32, FT>(sm, R, NA, A.fixed_point != 0);
+  StepState S;
+  FT* L;
+  AugSmem<D, JF32>::carve(sm, A.nc, S, L);
+  S.flags = flags_sh;
   auto vertex_offset = [&](int cell, int v) {
     long long off = 0, mul = 1;
     int t = cell;
@@ -1183,69 +1367,40 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs 
     }
     return off;
   };
-  if (rank == 0) {
-    const long long cn = ipow(A.nc + 1, D);
-    for (long long i = tid; i < cn; i += blockDim.x) A.c[i] = 0.0;
-    if (tid == 0) {
-      A.st->alpha_cur = 1.0;
-      A.st->converged = 0;
-    }
-  }
+  step_state_init<D>(A, S);
+  const bool writer = rank == 0;
   int it = 0;
   for (it = 1; it <= A.maxit; ++it) {
     const bool first = it == 1;
-    if (tid == 0) {
-      alpha_sh = first ? 1.0 : ((volatile double*)&A.st->alpha_cur)[0];
-      stop = ((volatile int*)&A.st->abort)[0];
-    }
+    double* pbuf = A.partials + (size_t)(it & 1) * A.pstride;
+    if (tid == 0) stop = ((volatile int*)&A.st->abort)[0];
     __syncthreads();
     if (stop) break;
     for (int cell = rank; cell < ncell; cell += CS) {
-      if (tid < G::NV) cv[tid] = first ? 0.0 : __ldcg(&A.c[vertex_offset(cell, tid)]);
+      if (tid < G::NV) cv[tid] = S.c[vertex_offset(cell, tid)];
       Rows<D, JF32>::zero(acc, first, A.fixed_point != 0, tid);
       __syncthreads();
-      fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, alpha_sh, cell, 0);
-      block_reduce_rows<D, JF32>(acc, A.partials + (long long)cell * G::NVAL, first, A.fixed_point != 0);
+      fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, 0);
+      block_reduce_rows<D, JF32>(acc, pbuf + (size_t)cell * G::NVAL, first, A.fixed_point != 0);
     }
     cluster.sync();
-    if (rank == 0) newton_step<D, JF32>(A, cellsum, M, R, L, alpha_sh, first);
-    cluster.sync();
-    if (tid == 0) stop = ((volatile int*)&A.st->converged)[0] | ((volatile int*)&A.st->abort)[0];
+    newton_step<D, JF32>(A, pbuf, cellsum, M, R, L, S, first, writer);
     __syncthreads();
-    if (stop) break;
+    if (flags_sh[0] || flags_sh[1]) break;
   }
-  if (rank == 0 && tid == 0) {
-    const int conv = ((volatile int*)&A.st->converged)[0];
-    if (!conv) atomicOr(&A.st->flags, kFlagNewtonCap);
-    A.st->newton_iters[A.level_index] += it > A.maxit ? A.maxit : it;
-    A.st->alpha[A.level_index] = ((volatile double*)&A.st->alpha_cur)[0];
-  }
-  if (tid == 0) alpha_sh = ((volatile double*)&A.st->alpha_cur)[0];
+  step_report(A, S, it, writer);
+  if (flags_sh[1] && writer && tid == 0) A.st->abort = 1;
   for (int cell = rank; cell < ncell; cell += CS) {
-    if (tid < G::NV) cv[tid] = __ldcg(&A.c[vertex_offset(cell, tid)]);
+    if (tid < G::NV) cv[tid] = S.c[vertex_offset(cell, tid)];
     __syncthreads();
-    fine_pass<D, JF32>(A, kUpdate, acc, cv, alpha_sh, cell, 0);
+    fine_pass<D, JF32>(A, kUpdate, acc, cv, S.sa[1], cell, 0);
     __syncthreads();
   }
 }
 
 template <int D, bool JF32>
 size_t aug_smem(int nc) {
-  using G = Aug<D, JF32>;
-  const int ncell = (int)ipow(nc, D);
-  const int NA = (int)ipow(nc - 1, D) + 1;
-  const size_t rows = (size_t)G::NVAL * G::NT;
-  if (JF32) {
-    // channel rows (reused for cellsum, M, R), then the FP32 factor and its pivots; the factor
-    // sits past the rows, so the rows are padded to the scratch when that is larger
-    const size_t rbytes = Rows<D, JF32>::bytes;
-    const size_t scratch = sizeof(double) * ((size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 1);
-    return (rbytes > scratch ? rbytes : scratch) + sizeof(float) * ((size_t)NA * (NA + 1) + NA);
-  }
-  // cellsum, M, R in the rows (or past them), then the FP64 factor and its pivots (past the
-  // rows, where the fixed-point iteration keeps it from pass to pass)
-  const size_t scratch = (size_t)ncell * G::NVAL + (size_t)NA * (NA + 1) + NA + 1;
-  return sizeof(double) * ((rows > scratch ? rows : scratch) + (size_t)NA * (NA + 1) + NA);
+  return AugSmem<D, JF32>::bytes(nc);
 }
 
 // Blocks per SM of the cooperative kernel when launched with `smem` dynamic bytes (the
@@ -1391,8 +1546,7 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.u = u;
   A.g = gn;
   A.partials = ab.partials;
-  A.c = ab.c;
-  A.sys = ab.sys;
+  A.pstride = (long long)ab.partial_items * (dim == 2 ? Aug<2, false>::NVAL : Aug<3, false>::NVAL);
   A.Ainv = ab.Ainv;
   A.st = st;
   // barrier words and abort/converged flags start cleared

@@ -77,7 +77,8 @@ cudaError_t vcycle(const Ctx& c, int j, int level, double* u, const double* b) {
   cudaError_t e;
   if (j == 1) return launch_coarse_solve_f64(c.dim, c.geo(1), c.ainv, b, u, c.s);
   if (j <= coarse_top(c, level))
-    return launch_coarse_cycle<double>(c.dim, c.nc, j, u, b, c.nu_pre, c.nu_post, c.ainv, nullptr, c.s);
+    return launch_coarse_cycle<double>(c.dim, c.nc, j, u, b, c.nu_pre, c.nu_post, c.ainv, nullptr, nullptr, false,
+                                       c.s);
   const LevelGeo gf = c.geo(j), gc = c.geo(j - 1);
   for (int it = 0; it < c.nu_pre; ++it) {
     if ((e = launch_rbgs<double>(c.dim, gf, u, b, 0, c.s)) != cudaSuccess) return e;

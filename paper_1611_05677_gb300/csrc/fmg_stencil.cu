@@ -128,6 +128,11 @@ __global__ void k_copy_t(const T* __restrict__ s, T* __restrict__ d, long long n
   if (i < n) d[i] = s[i];
 }
 
+__global__ void k_to_f32(const double* __restrict__ s, float* __restrict__ d, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (float)s[i];
+}
+
 // ------------------------------------------------------------------ residual + restriction
 template <typename T>
 __device__ __forceinline__ T res2(const T* __restrict__ u, const T* __restrict__ b, long long c, long long np) {
@@ -277,12 +282,18 @@ __device__ __forceinline__ bool interior_of(long long idx, int n, int dim) {
   return true;
 }
 
+// b = w (g - f(u)) on the interior nodes, 0 on the boundary; one thread per node of row
+// (j[, l]) = (blockIdx.y[, blockIdx.z]), so no index division.
 __global__ void k_nonlinear_rhs(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
-                                long long nodes, int n, int dim, int kind, double a, double w) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nodes) return;
+                                int n, int dim, int kind, double a, double w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, l = blockIdx.z;
+  if (i > n) return;
+  const long long np = n + 1;
+  const long long idx = ((long long)l * np + j) * np + i;
+  const bool inner = i > 0 && i < n && j > 0 && j < n && (dim == 2 || (l > 0 && l < n));
   double v = 0.0;
-  if (interior_of(idx, n, dim)) v = w * (g[idx] - f_only<double>(kind, a, u[idx]));
+  if (inner) v = w * (g[idx] - f_only<double>(kind, a, u[idx]));
   b[idx] = v;
 }
 
@@ -377,15 +388,23 @@ __device__ __forceinline__ void cta_rbgs(const CoarseLevel<T, D>& L, int colour,
   }
 }
 
-// `steps` Chebyshev-Jacobi steps on level L (colour-free: every interior node per step, the
-// iterate alternating between u and ua); the result ends in L.u.
+// The buffer in which a Chebyshev step 0 taken from a zero start (by the code that writes
+// the level's b) leaves the iterate, so that steps 1..steps-1 end in L.u.
 template <typename T, int D>
-__device__ void cta_cheb(const CoarseLevel<T, D>& L, const ChebCoef& cf, int steps, T bscale, T inv2d) {
+__device__ __forceinline__ T* cta_cheb_start(const CoarseLevel<T, D>& L, int steps) {
+  return ((steps - 1) & 1) ? L.ua : L.u;
+}
+
+// Chebyshev-Jacobi steps k0..steps-1 on level L (colour-free: every interior node per step,
+// the iterate alternating between u and ua); they start in L.u (k0 = 0) or in
+// cta_cheb_start(L, steps) with d set (k0 = 1), and the result ends in L.u.
+template <typename T, int D>
+__device__ void cta_cheb(const CoarseLevel<T, D>& L, const ChebCoef& cf, int steps, T bscale, T inv2d, int k0 = 0) {
   const int n = L.n, np = L.np, lg = L.lg;
   const int total = D == 2 ? (1 << (2 * lg)) : (1 << (3 * lg));
-  T* u = L.u;
-  T* ua = L.ua;
-  for (int k = 0; k < steps; ++k) {
+  T* u = k0 ? cta_cheb_start(L, steps) : L.u;
+  T* ua = u == L.u ? L.ua : L.u;
+  for (int k = k0; k < steps; ++k) {
     const T cd = (T)cf.cd[k], cr = (T)cf.cr[k];
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int i = t & (n - 1), j = (t >> lg) & (n - 1), l = D == 3 ? (t >> (2 * lg)) : 0;
@@ -418,12 +437,20 @@ __device__ __forceinline__ T cta_res(const CoarseLevel<T, D>& L, int c, T sigma)
   return L.b[c] - sigma * (T(2 * D) * L.u[c] - s);
 }
 
+// zero_start: the top level's u is zero on entry (a correction from zero): it is not read,
+// and with Chebyshev smoothing the top level's step 0 (pointwise from zero) is taken while b
+// is loaded.  Below the top level the restriction takes the coarse level's step 0 the same
+// way.  The FP32 cycle's level-1 solve uses an FP32 copy of A_1^{-1} (Ainv32), staged in
+// shared memory while the top level loads; the FP64 cycle reads the FP64 A_1^{-1}.
 template <typename T, int D>
 __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, const T* __restrict__ bg, int n0, int jtop, int nu_pre,
-                                int nu_post, const double* __restrict__ Ainv, int cheb, ChebCoef cf) {
+                                int nu_post, const double* __restrict__ Ainv, const float* __restrict__ Ainv32,
+                                int cheb, ChebCoef cf, int zero_start) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   CoarseLevel<T, D> L[8];
+  constexpr bool kStageInv = sizeof(T) == sizeof(float);
+  float* ai = nullptr;   // staged FP32 A_1^{-1} (FP32 cycle)
   {
     int off = 0;
     for (int j = 1; j <= jtop; ++j) {
@@ -439,25 +466,68 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       L[j - 1].d = cheb ? sm + off + 3 * nodes : nullptr;
       off += (cheb ? 4 : 2) * nodes;
     }
+    if (kStageInv) ai = reinterpret_cast<float*>(sm + off);
   }
+  const T inv2d = T(1) / T(2 * D);
+  const int m1 = n0 - 1;
+  const int N1 = D == 2 ? m1 * m1 : m1 * m1 * m1;
   {
     const CoarseLevel<T, D>& top = L[jtop - 1];
-    const int nodes = D == 2 ? top.np * top.np : top.np * top.np * top.np;
-    for (int i = threadIdx.x; i < nodes; i += blockDim.x) {
-      top.u[i] = ug[i];
-      top.b[i] = bg[i];
+    const int np = top.np;
+    const int nodes = D == 2 ? np * np : np * np * np;
+    // top level: b, and u (or, from a zero start, u = 0 or the first Chebyshev step); the
+    // FP32 cycle also stages A_1^{-1}.  Every global load of a thread is issued before the
+    // first store, so the phase costs about one memory latency.
+    const bool first_top = cheb && zero_start && nu_pre >= 1 && jtop >= 2;
+    const T e0 = T(cf.cr[0]) * (D == 2 ? T(1) : T(top.n)) * inv2d;   // step 0 from zero: cr_0 D^{-1} b
+    T* ustart = first_top ? cta_cheb_start(top, nu_pre) : top.u;
+    const int nai = kStageInv ? N1 * N1 : 0;
+    for (int i0 = threadIdx.x; i0 < nodes || i0 < nai; i0 += 4 * blockDim.x) {
+      T bv[4], uv[4];
+      float av[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = i0 + r * blockDim.x;
+        bv[r] = i < nodes ? bg[i] : T(0);
+        uv[r] = (i < nodes && !zero_start) ? ug[i] : T(0);
+        av[r] = i < nai ? __ldg(&Ainv32[i]) : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = i0 + r * blockDim.x;
+        if (i < nai) ai[i] = av[r];
+        if (i >= nodes) continue;
+        top.b[i] = bv[r];
+        top.u[i] = uv[r];
+        if (first_top) {
+          const int x = i % np, y = (i / np) % np, z = D == 3 ? i / (np * np) : 1;
+          const bool inner = x > 0 && x < np - 1 && y > 0 && y < np - 1 && (D == 2 || (z > 0 && z < np - 1));
+          const T e = inner ? e0 * bv[r] : T(0);
+          ustart[i] = e;
+          top.d[i] = e;
+        }
+      }
     }
-    // lower levels: zero (boundary rings stay zero); the Chebyshev buffers of every level too
+    // lower levels: zero (boundary rings stay zero); the other Chebyshev buffers too
     for (int j = 1; j <= jtop; ++j) {
-      const int nn = D == 2 ? L[j - 1].np * L[j - 1].np : L[j - 1].np * L[j - 1].np * L[j - 1].np;
+      const CoarseLevel<T, D>& Lj = L[j - 1];
+      const int nn = D == 2 ? Lj.np * Lj.np : Lj.np * Lj.np * Lj.np;
       if (j < jtop)
-        for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) L[j - 1].u[i] = T(0);
-      if (cheb)
-        for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) L[j - 1].ua[i] = T(0);
+        for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) Lj.u[i] = T(0);
+      if (cheb) {
+        if (j < jtop) {
+          for (int i = threadIdx.x; i < 2 * nn; i += blockDim.x) Lj.ua[i] = T(0);
+        } else {
+          T* other = ustart == top.u ? top.ua : top.u;   // the top level's u, d and start are set above
+          for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+            if (other == top.ua) top.ua[i] = T(0);
+            if (!first_top) top.d[i] = T(0);
+          }
+        }
+      }
     }
   }
   __syncthreads();
-  const T inv2d = T(1) / T(2 * D);
   // descend
   for (int j = jtop; j >= 2; --j) {
     const CoarseLevel<T, D>& F = L[j - 1];
@@ -465,7 +535,9 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
     const T bscale = D == 2 ? T(1) : T(F.n);
     const T sigma = D == 2 ? T(1) : T(1) / T(F.n);
     if (cheb) {
-      cta_cheb<T, D>(F, cf, nu_pre, bscale, inv2d);
+      // step 0 was taken by the load (top level from zero) or by the restriction (below)
+      const bool started = nu_pre >= 1 && (j < jtop || zero_start);
+      cta_cheb<T, D>(F, cf, nu_pre, bscale, inv2d, started ? 1 : 0);
     } else {
       for (int it = 0; it < nu_pre; ++it) {
         cta_rbgs<T, D>(F, 0, bscale, inv2d);
@@ -474,9 +546,14 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
         __syncthreads();
       }
     }
-    // b_c = P^T (b - A u), u_c = 0: items (I, J[, K]) over [0, n_c)^d, boundary skipped
+    // b_c = P^T (b - A u), u_c = 0 -- or, when the coarse level is smoothed by Chebyshev
+    // steps, its step 0 from zero: u_c = d_c = cr_0 D^{-1} b_c in the start buffer.  Items
+    // (I, J[, K]) over [0, n_c)^d, boundary skipped.
     const int lgc = C.lg;
     const int total = D == 2 ? (1 << (2 * lgc)) : (1 << (3 * lgc));
+    const bool first_c = cheb && nu_pre >= 1 && j - 1 >= 2;
+    const T e0c = T(cf.cr[0]) * (D == 2 ? T(1) : T(C.n)) * inv2d;
+    T* ucs = first_c ? cta_cheb_start(C, nu_pre) : C.u;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int I = t & (C.n - 1), J = (t >> lgc) & (C.n - 1), K = D == 3 ? (t >> (2 * lgc)) : 0;
       if (I == 0 || J == 0 || (D == 3 && K == 0)) continue;
@@ -493,8 +570,14 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
         for (int q = 0; q < 4; ++q) e += cta_res<T, D>(F, Fc + o[q], sigma) + cta_res<T, D>(F, Fc - o[q], sigma);
       }
       const int cc = (K * C.np + J) * C.np + I;
-      C.b[cc] = r + T(0.5) * e;
-      C.u[cc] = T(0);
+      const T bv = r + T(0.5) * e;
+      C.b[cc] = bv;
+      if (first_c) {
+        ucs[cc] = e0c * bv;
+        C.d[cc] = e0c * bv;
+      } else {
+        C.u[cc] = T(0);
+      }
     }
     __syncthreads();
   }
@@ -516,11 +599,19 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
     // contiguously), then a shuffle sum (fixed order)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = warp; r < N; r += nw) {
-      double acc = 0.0;
-      for (int c = lane; c < N; c += 32) acc = fma(__ldg(&Ainv[(long long)r * N + c]), b1[c], acc);
+      if (kStageInv) {
+        float acc = 0.f;
+        for (int c = lane; c < N; c += 32) acc = fmaf(ai[r * N + c], (float)b1[c], acc);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) C.u[off1[r]] = (T)acc;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) C.u[off1[r]] = (T)acc;
+      } else {
+        double acc = 0.0;
+        for (int c = lane; c < N; c += 32) acc = fma(__ldg(&Ainv[(long long)r * N + c]), b1[c], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) C.u[off1[r]] = (T)acc;
+      }
     }
     __syncthreads();
   }
@@ -629,7 +720,8 @@ cudaError_t launch_nonlinear_rhs(int dim, LevelGeo g, const double* u, const dou
                                  double a, cudaStream_t s) {
   const double h = 1.0 / g.n;
   const double w = dim == 2 ? h * h : h * h * h;
-  k_nonlinear_rhs<<<cdiv(g.nodes, 256), 256, 0, s>>>(u, gn, b, g.nodes, g.n, dim, kind, a, w);
+  const unsigned gx = cdiv(g.n + 1, kBlock);
+  k_nonlinear_rhs<<<dim3(gx, g.n + 1, dim == 3 ? g.n + 1 : 1), kBlock, 0, s>>>(u, gn, b, g.n, dim, kind, a, w);
   return cudaGetLastError();
 }
 
@@ -671,22 +763,28 @@ size_t coarse_cycle_smem(int dim, int n0, int jtop, bool cheb) {
     const long long np = (long long)(n0 << (j - 1)) + 1;
     tot += (cheb ? 4 : 2) * (size_t)ipow(np, dim);
   }
-  return tot * sizeof(T);
+  // the FP32 cycle stages its FP32 A_1^{-1}
+  const size_t n1 = (size_t)ipow(n0 - 1, dim);
+  return tot * sizeof(T) + (sizeof(T) == sizeof(float) ? n1 * n1 * sizeof(float) : 0);
 }
 
 template <typename T>
 cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int nu_pre, int nu_post,
-                                const double* Ainv, const ChebCoef* cheb, cudaStream_t s) {
+                                const double* Ainv, const float* Ainv32, const ChebCoef* cheb, bool zero_start,
+                                cudaStream_t s) {
+  if (sizeof(T) == sizeof(float) && !Ainv32) return cudaErrorInvalidValue;
   if (cheb && (nu_pre > kMaxCheb || nu_post > kMaxCheb)) return cudaErrorInvalidValue;
   const size_t smem = coarse_cycle_smem<T>(dim, n0, jtop, cheb != nullptr);
   const ChebCoef cf = cheb ? *cheb : ChebCoef{};
   cudaError_t e;
   if (dim == 2) {
     if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 2>, smem)) != cudaSuccess) return e;
-    k_vcycle_coarse<T, 2><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, cheb ? 1 : 0, cf);
+    k_vcycle_coarse<T, 2><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb ? 1 : 0, cf,
+                                                 zero_start ? 1 : 0);
   } else {
     if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 3>, smem)) != cudaSuccess) return e;
-    k_vcycle_coarse<T, 3><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, cheb ? 1 : 0, cf);
+    k_vcycle_coarse<T, 3><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb ? 1 : 0, cf,
+                                                 zero_start ? 1 : 0);
   }
   return cudaGetLastError();
 }
@@ -787,6 +885,12 @@ cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* 
   return cudaGetLastError();
 }
 
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_to_f32<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s) {
   k_copy_t<T><<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
@@ -796,9 +900,9 @@ cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s) {
 template size_t coarse_cycle_smem<double>(int, int, int, bool);
 template size_t coarse_cycle_smem<float>(int, int, int, bool);
 template cudaError_t launch_coarse_cycle<double>(int, int, int, double*, const double*, int, int, const double*,
-                                                 const ChebCoef*, cudaStream_t);
+                                                 const float*, const ChebCoef*, bool, cudaStream_t);
 template cudaError_t launch_coarse_cycle<float>(int, int, int, float*, const float*, int, int, const double*,
-                                                const ChebCoef*, cudaStream_t);
+                                                const float*, const ChebCoef*, bool, cudaStream_t);
 template cudaError_t launch_cheb<double>(int, LevelGeo, const double*, double*, double*, const double*, double, double,
                                          bool, cudaStream_t);
 template cudaError_t launch_cheb<float>(int, LevelGeo, const float*, float*, float*, const float*, double, double, bool,
