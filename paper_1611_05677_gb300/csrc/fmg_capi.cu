@@ -25,6 +25,7 @@ struct fmg_ctx {
   double* u[kMaxLevels] = {};
   double* b[kMaxLevels] = {};
   double* g[kMaxLevels] = {};
+  double* gf[kMaxLevels] = {};    // mixed path: g as float-float (the solve reads this copy)
   float* u32[kMaxLevels] = {};
   float* b32[kMaxLevels] = {};
   float* u32b[kMaxLevels] = {};   // second FP32 buffer: output of the fused pre-smoothing kernel,
@@ -141,8 +142,10 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
     float* d32 = nullptr;
     double* ua = nullptr;
     double* dd = nullptr;
+    double* gf = nullptr;
     const bool cheb = p->smoother == FMG_SMOOTHER_CHEBYSHEV;
     if (p->precision == FMG_PREC_MIXED) {
+      gf = (double*)take(nodes * 8);
       u32 = (float*)take(nodes * 4);
       b32 = (float*)take(nodes * 4);
       if (cheb || fused_cycle_supported(p->dim, p->nu_pre, p->nu_post)) u32b = (float*)take(nodes * 4);
@@ -156,6 +159,7 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
       c->u[k] = u;
       c->b[k] = b;
       c->g[k] = g;
+      c->gf[k] = gf;
       c->u32[k] = u32;
       c->b32[k] = b32;
       c->u32b[k] = u32b;
@@ -340,7 +344,7 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
 // level (the parent's restriction zeroes it; the top level's defect equation starts at zero),
 // pre-smoothing writes the level's second buffer, post-smoothing reads it back into the first
 // one -- or, on the top level, adds the result to the FP64 iterate u64.
-cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
+cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top, bool top_ff = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
   if (j == 1) {
@@ -351,7 +355,8 @@ cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
     // the FP32 cycles solve for a correction from zero on every level
     TRY(launch_coarse_cycle<float>(dim, c->p.coarse_cells, j, c->u32[j - 1], c->b32[j - 1], c->p.nu_pre,
                                    c->p.nu_post, c->Ainv, c->Ainv32, cheb_coef(c), true, s));
-    if (u64_top) TRY(launch_add_f32(c->geo[j - 1], dim, u64_top, c->u32[j - 1], s));
+    if (u64_top && top_ff) TRY(launch_add_f32_ff(c->geo[j - 1], u64_top, c->u32[j - 1], s));
+    if (u64_top && !top_ff) TRY(launch_add_f32(c->geo[j - 1], dim, u64_top, c->u32[j - 1], s));
     return cudaSuccess;
   }
   const LevelGeo gf = c->geo[j - 1];
@@ -363,14 +368,15 @@ cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top) {
   slot = -1;
   if (u64_top) TRY(tbegin(c, FMG_KT_POST_TOP, j, &slot));
   TRY(launch_post_fused(dim, gf, c->p.nu_post, c->u32b[j - 1], c->u32[j - 2], c->b32[j - 1], c->u32[j - 1], u64_top,
-                        s));
+                        s, top_ff));
   return tend(c, slot);
 }
 
 // FP32 cycle on level j (unfused kernels).  started: Chebyshev step 0 was already taken by the
 // kernel that produced b; u64_top (top level of the mixed path): the last post-smoothing step
 // is fused with the FP64 update u64 += correction.
-cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, double* u64_top = nullptr) {
+cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, double* u64_top = nullptr,
+                     bool top_ff = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
   float* u = c->u32[j - 1];
@@ -407,7 +413,7 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
     float* end = nullptr;
     TRY(cheb_run<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, 0, last, top, &end));
     TRY(launch_cheb_add64(dim, gf, end, c->d32[j - 1], b, u64_top, c->cheb.cd[last], c->cheb.cr[last], last == 0,
-                          s));
+                          s, top_ff));
     return cudaSuccess;
   }
   if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_post, top));
@@ -418,7 +424,8 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
     TRY(launch_rbgs<float>(dim, gf, u, b, 0, s));
     TRY(tend(c, slot));
   }
-  if (u64_top) TRY(launch_add_f32(gf, dim, u64_top, u, s));
+  if (u64_top && top_ff) TRY(launch_add_f32_ff(gf, u64_top, u, s));
+  if (u64_top && !top_ff) TRY(launch_add_f32(gf, dim, u64_top, u, s));
   return cudaSuccess;
 }
 
@@ -439,8 +446,25 @@ cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
   return cudaSuccess;
 }
 
-// Algorithm 3.1 at level k >= 2 on the level-k array u.
+// The same cycle on the mixed solve's float-float level data: float-float residual -> FP32
+// cycle from e = 0 -> float-float update (the residual and the update in FP32 error-free
+// transformations instead of FP64 arithmetic).
+cudaError_t top_cycle_ff(fmg_ctx* c, int k, double* u, const double* b) {
+  const LevelGeo g = c->geo[k - 1];
+  const bool fuse = fuse_first_step<float>(c, k);
+  float* e0buf = fuse ? cheb_start(c->u32[k - 1], c->u32b[k - 1], c->p.nu_pre) : c->u32[k - 1];
+  TRY(launch_residual_ff(c->p.dim, g, u, b, c->b32[k - 1], e0buf, c->stream, fuse ? c->d32[k - 1] : nullptr,
+                         fuse ? cheb_e0(c, k) : 0.0));
+  if (c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS) return vcycle32_fused(c, k, u, true);
+  if (k > coarse_cycle_top<float>(c)) return vcycle32(c, k, true, fuse, u, true);
+  TRY(vcycle32(c, k, true));
+  TRY(launch_add_f32_ff(g, u, c->u32[k - 1], c->stream));
+  return cudaSuccess;
+}
+
+// Algorithm 3.1 at level k >= 2 on the level-k array u (FP64 contexts).
 cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
+  if (c->p.precision == FMG_PREC_MIXED) return cudaErrorInvalidValue;
   const LevelGeo g = c->geo[k - 1];
   int slot_step = -1, slot_aug = -1;
   TRY(tbegin(c, FMG_KT_CORRECTION, k, &slot_step));
@@ -456,18 +480,46 @@ cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
   return tend(c, slot_step);
 }
 
+// Algorithm 3.1 at level k >= 2 on the mixed solve's float-float level data (u = u[k-1],
+// b = b[k-1], g = gf[k-1]); out_f64: the result is left as FP64 (the solve's last step).
+cudaError_t correction_step_ff(fmg_ctx* c, int k, bool out_f64) {
+  const LevelGeo g = c->geo[k - 1];
+  double* u = c->u[k - 1];
+  int slot_step = -1, slot_aug = -1;
+  TRY(tbegin(c, FMG_KT_CORRECTION, k, &slot_step));
+  // step 1: b = (g, v) - (f(x, u^{(l)}), v)   (eq. 3.4)
+  TRY(launch_nonlinear_rhs_ff(c->p.dim, g, u, c->gf[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream));
+  for (int i = 0; i < c->p.m_vcycles; ++i) TRY(top_cycle_ff(c, k, u, c->b[k - 1]));
+  // step 2: semilinear problem on V_H + span{u~}  (eq. 3.6)
+  TRY(tbegin(c, FMG_KT_AUGMENTED, k, &slot_aug));
+  TRY(launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->gf[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
+                       c->p.newton_maxit, true, c->ab, c->st, k - 1, c->stream, c->cluster_aug,
+                       c->p.nonlinear == FMG_NONLINEAR_FIXED_POINT ? 1 : 0, out_f64 ? 1 : 0));
+  TRY(tend(c, slot_aug));
+  return tend(c, slot_step);
+}
+
 cudaError_t run_fmg(fmg_ctx* c) {
   c->timed_next = 0;
   // per-solve statistics start at zero (flags, iteration counts, alphas)
   TRY(cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  // the mixed path keeps its level data as float-float; its last step leaves the FP64 result
+  const bool mixed = c->p.precision == FMG_PREC_MIXED;
   TRY(launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
-                           c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream));
+                           c->p.level1_maxit, mixed, c->st, c->stream, mixed && c->nlev > 1));
   for (int k = 2; k <= c->nlev; ++k) {
     // u^{(0)}_{h_k} = u_{h_{k-1}}: the natural inclusion
-    TRY(launch_prolong<double, double>(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], 0,
-                                       c->stream));
-    for (int l = 0; l < c->p.p_corrections; ++l)
-      TRY(correction_step(c, k, c->u[k - 1]));
+    if (mixed)
+      TRY(launch_prolong_ff(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], c->stream));
+    else
+      TRY(launch_prolong<double, double>(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], 0,
+                                         c->stream));
+    for (int l = 0; l < c->p.p_corrections; ++l) {
+      if (mixed)
+        TRY(correction_step_ff(c, k, k == c->nlev && l == c->p.p_corrections - 1));
+      else
+        TRY(correction_step(c, k, c->u[k - 1]));
+    }
   }
   return cudaSuccess;
 }
@@ -509,6 +561,8 @@ fmg_status load_rhs(fmg_ctx* c, const double* g_fine, int on_device) {
   CK(c, launch_zero_boundary(c->p.dim, c->geo[top], c->g[top], c->stream));
   for (int k = top - 1; k >= 0; --k)
     CK(c, launch_decimate(c->p.dim, c->geo[top], c->g[top], c->geo[k], c->g[k], c->stream));
+  if (c->p.precision == FMG_PREC_MIXED)
+    for (int k = 0; k <= top; ++k) CK(c, launch_ff_from_f64(c->g[k], c->gf[k], c->geo[k].nodes, c->stream));
   return FMG_OK;
 }
 
@@ -1016,7 +1070,15 @@ fmg_status fmg_op_correction_step(fmg_ctx* c, int level, double* u, fmg_stats* s
   if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
   CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
   c->timed_next = 0;
-  CK(c, correction_step(c, level, u));
+  if (c->p.precision == FMG_PREC_MIXED) {
+    // the mixed path works on float-float level data: u in, the step, u out
+    const long long nodes = c->geo[level - 1].nodes;
+    CK(c, launch_ff_from_f64(u, c->u[level - 1], nodes, c->stream));
+    CK(c, correction_step_ff(c, level, false));
+    CK(c, launch_ff_to_f64(c->u[level - 1], u, nodes, c->stream));
+  } else {
+    CK(c, correction_step(c, level, u));
+  }
   return read_state(c, st, false);
 }
 

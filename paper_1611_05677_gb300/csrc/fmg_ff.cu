@@ -1,0 +1,145 @@
+// Mixed-precision path with float-float level data (Algorithm 3.1 step 1 and the FMG
+// interpolation of Algorithm 3.2): the level iterate u, the linear right-hand side b of eq.
+// (3.4) and g are stored as float-float pairs in the 8-byte slots of the FP64 arrays, and
+// the kernels that would otherwise do FP64 arithmetic per node (residual, update, right-hand
+// side, interpolation) do it in FP32 error-free transformations instead, so they run at the
+// HBM rate.  The FP32 multigrid cycle between residual and update is unchanged.
+#include "fmg_ff.cuh"
+#include "fmg_internal.cuh"
+
+namespace fmg {
+
+namespace {
+
+constexpr int kB = 128;
+
+unsigned cdiv_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// r = b - sigma (2d u - sum of axis neighbours) = b + sigma * neighbour_sum on the interior,
+// 0 on the boundary; r32 = fl32(r), and with d32 the first Chebyshev step from zero,
+// e = d = e0 r32.
+template <int D>
+__global__ void k_residual_ff(const double* __restrict__ u, const double* __restrict__ b, int n, ff sigma,
+                              float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, l = D == 3 ? blockIdx.z : 0;
+  if (i > n) return;
+  const long long np = n + 1, pl = np * np;
+  const long long c = ((long long)l * np + j) * np + i;
+  float v = 0.f;
+  if (i > 0 && i < n && j > 0 && j < n && (D == 2 || (l > 0 && l < n))) {
+    ff S = neighbour_sum_ff<D>(u, c, np, pl);
+    if (D == 3) S = ff_mul(S, sigma);
+    const ff r = ff_add(ff_load(b + c), S);
+    v = r.hi + r.lo;
+  }
+  r32[c] = v;
+  const float e = d32 ? e0 * v : 0.f;
+  e32[c] = e;
+  if (d32) d32[c] = e;
+}
+
+// b = w (g - a f(u)) on the interior nodes, 0 on the boundary (eq. 3.4 with the vertex rule).
+__global__ void k_nonlinear_rhs_ff(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
+                                   int n, int dim, int kind, ff a, double a64, ff w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, l = blockIdx.z;
+  if (i > n) return;
+  const long long np = n + 1;
+  const long long idx = ((long long)l * np + j) * np + i;
+  ff v{0.f, 0.f};
+  if (i > 0 && i < n && j > 0 && j < n && (dim == 2 || (l > 0 && l < n)))
+    v = ff_mul(ff_sub(ff_load(g + idx), f_ff(kind, a, a64, ff_load(u + idx))), w);
+  ff_store(b + idx, v);
+}
+
+// FMG interpolation u_f = P u_c (the natural inclusion, eq. 3.3) on the interior fine nodes.
+template <int D>
+__global__ void k_prolong_ff(const double* __restrict__ uc, int nc, double* __restrict__ uf, int nf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int j = blockIdx.y + 1;
+  const int l = D == 3 ? blockIdx.z + 1 : 0;
+  if (i > nf - 1) return;
+  const long long cp = nc + 1;
+  long long a, z, f;
+  if (D == 2) {
+    a = (long long)(j >> 1) * cp + (i >> 1);
+    z = (long long)((j + 1) >> 1) * cp + ((i + 1) >> 1);
+    f = (long long)j * (nf + 1) + i;
+  } else {
+    a = ((long long)(l >> 1) * cp + (j >> 1)) * cp + (i >> 1);
+    z = ((long long)((l + 1) >> 1) * cp + ((j + 1) >> 1)) * cp + ((i + 1) >> 1);
+    const long long fp = nf + 1;
+    f = ((long long)l * fp + j) * fp + i;
+  }
+  const ff s = ff_add(ff_load(uc + a), ff_load(uc + z));
+  ff_store(uf + f, ff{0.5f * s.hi, 0.5f * s.lo});
+}
+
+__global__ void k_add_f32_ff(double* __restrict__ uff, const float* __restrict__ e, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ff_store(uff + i, ff_add_f(ff_load(uff + i), e[i]));
+}
+
+__global__ void k_ff_from_f64(const double* __restrict__ s, double* __restrict__ d, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ff_store(d + i, ff_from_double(s[i]));
+}
+
+__global__ void k_ff_to_f64(const double* __restrict__ s, double* __restrict__ d, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = ff_to_double(ff_load(s + i));
+}
+
+}  // namespace
+
+// ============================================================================ launchers
+
+cudaError_t launch_residual_ff(int dim, LevelGeo g, const double* u_ff, const double* b_ff, float* r32, float* e32,
+                               cudaStream_t s, float* d32, double e0) {
+  const int n = g.n;
+  const dim3 grid(cdiv_u(n + 1, kB), n + 1, dim == 3 ? n + 1 : 1);
+  if (dim == 2)
+    k_residual_ff<2><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff{1.f, 0.f}, r32, e32, d32, (float)e0);
+  else
+    k_residual_ff<3><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff_from_double(1.0 / n), r32, e32, d32, (float)e0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonlinear_rhs_ff(int dim, LevelGeo g, const double* u_ff, const double* g_ff, double* b_ff,
+                                    int kind, double a, cudaStream_t s) {
+  const double h = 1.0 / g.n;
+  const double w = dim == 2 ? h * h : h * h * h;
+  const dim3 grid(cdiv_u(g.n + 1, kB), g.n + 1, dim == 3 ? g.n + 1 : 1);
+  k_nonlinear_rhs_ff<<<grid, kB, 0, s>>>(u_ff, g_ff, b_ff, g.n, dim, kind, ff_from_double(a), a, ff_from_double(w));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo gf, double* uf_ff, cudaStream_t s) {
+  const int nf = gf.n;
+  const dim3 grid(cdiv_u(nf - 1, kB), nf - 1, dim == 3 ? nf - 1 : 1);
+  if (dim == 2)
+    k_prolong_ff<2><<<grid, kB, 0, s>>>(uc_ff, gc.n, uf_ff, nf);
+  else
+    k_prolong_ff<3><<<grid, kB, 0, s>>>(uc_ff, gc.n, uf_ff, nf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_f32_ff(LevelGeo g, double* u_ff, const float* e32, cudaStream_t s) {
+  k_add_f32_ff<<<cdiv_u(g.nodes, 256), 256, 0, s>>>(u_ff, e32, g.nodes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ff_from_f64(const double* src, double* dst_ff, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_ff_from_f64<<<cdiv_u(n, 256), 256, 0, s>>>(src, dst_ff, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ff_to_f64(const double* src_ff, double* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_ff_to_f64<<<cdiv_u(n, 256), 256, 0, s>>>(src_ff, dst, n);
+  return cudaGetLastError();
+}
+
+}  // namespace fmg

@@ -1,0 +1,157 @@
+// Float-float ("double-single") arithmetic for the mixed-precision path.
+//
+// A value is an unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2, about 48
+// significant bits.  The operations are built from the error-free transformations of
+// Dekker (1971) and Knuth (TAOCP vol. 2, 4.2.2): TwoSum gives s + e = a + b exactly with
+// s = fl(a + b); with a fused multiply-add, TwoProduct gives p + e = a * b exactly with
+// p = fl(a * b).  On this GPU an FP32 operation issues 64 times as fast as an FP64 one, so a
+// dozen FP32 operations per float-float step still cost a fraction of one FP64 operation.
+// The path's FP64 quantities that feed sums over many nodes (residuals, moment sums) keep
+// ~1e-14 relative accuracy this way, far below the discretization error that bounds the
+// mixed path.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fmg_internal.cuh"
+
+namespace fmg {
+
+struct ff {
+  float hi, lo;
+};
+
+// s + e = a + b exactly (s = fl(a + b)).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// s + e = a + b exactly when |a| >= |b| or a = 0.
+__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+// p + e = a * b exactly (p = fl(a * b)), with one fused multiply-add.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ ff ff_make(float hi, float lo) {
+  ff r;
+  quick_two_sum(hi, lo, r.hi, r.lo);
+  return r;
+}
+
+// x + y, accurate also under cancellation (both parts through TwoSum).
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+  float s, e, t, f;
+  two_sum(x.hi, y.hi, s, e);
+  two_sum(x.lo, y.lo, t, f);
+  e += t;
+  quick_two_sum(s, e, s, e);
+  e += f;
+  ff r;
+  quick_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// x + y for accumulating sums: the lo parts are added without their own TwoSum, so the error
+// is bounded relative to |x| + |y| (as for an FP64 add) rather than to |x + y|.
+__device__ __forceinline__ ff ff_add_fast(ff x, ff y) {
+  float s, e;
+  two_sum(x.hi, y.hi, s, e);
+  e += x.lo + y.lo;
+  ff r;
+  quick_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+
+// x + b for an FP32 b.
+__device__ __forceinline__ ff ff_add_f(ff x, float b) {
+  float s, e;
+  two_sum(x.hi, b, s, e);
+  e += x.lo;
+  ff r;
+  quick_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// x * y (the lo * lo term, below the format's precision, is dropped).
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  float p, e;
+  two_prod(x.hi, y.hi, p, e);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  ff r;
+  quick_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+// x * b for an FP32 b.
+__device__ __forceinline__ ff ff_mul_f(ff x, float b) {
+  float p, e;
+  two_prod(x.hi, b, p, e);
+  e = fmaf(x.lo, b, e);
+  ff r;
+  quick_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+// Conversions.  From FP64: hi = fl32(x), lo = fl32(x - hi) (x - hi is exact in FP64).
+__host__ __device__ __forceinline__ ff ff_from_double(double x) {
+  ff r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__host__ __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
+
+// A float-float value stored in an 8-byte slot (the layout of the double arrays it replaces).
+__device__ __forceinline__ ff ff_load(const double* p) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  return ff{v.x, v.y};
+}
+__device__ __forceinline__ void ff_store(double* p, ff x) { *reinterpret_cast<float2*>(p) = make_float2(x.hi, x.lo); }
+
+// sum_k (u_k - u_c) over the 2d axis neighbours of node c: the hi differences and their sum
+// through TwoSum (exact), the lo parts and the rounding terms added after.
+template <int D>
+__device__ __forceinline__ ff neighbour_sum_ff(const double* __restrict__ u, long long c, long long np, long long pl) {
+  const ff uc = ff_load(u + c);
+  const long long o[3] = {1, np, pl};
+  float s = 0.f, lo = 0.f;
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    const ff um = ff_load(u + c - o[ax]), up = ff_load(u + c + o[ax]);
+    float dm, em, dp, ep, t, et;
+    two_sum(um.hi, -uc.hi, dm, em);
+    two_sum(up.hi, -uc.hi, dp, ep);
+    two_sum(dm, dp, t, et);
+    float s2, e2;
+    two_sum(s, t, s2, e2);
+    s = s2;
+    lo += ((em + ep) + (et + e2)) + ((um.lo - uc.lo) + (up.lo - uc.lo));
+  }
+  ff r;
+  two_sum(s, lo, r.hi, r.lo);
+  return r;
+}
+
+// a f(u) in float-float for the polynomial nonlinearities (Sec. 4 examples); the exponential
+// and |u|^{3/2} ones are evaluated in FP64 from the float-float value.
+__device__ __forceinline__ ff f_ff(int kind, ff a, double a64, ff u) {
+  switch (kind) {
+    case FMG_F_CUBIC: return ff_mul(ff_mul(ff_mul(u, u), u), a);
+    case FMG_F_LINEAR: return ff_mul(u, a);
+    default: return ff_from_double(f_only<double>(kind, a64, ff_to_double(u)));
+  }
+}
+
+}  // namespace fmg

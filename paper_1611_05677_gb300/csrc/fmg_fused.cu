@@ -15,6 +15,7 @@
 // the same order, as in the per-step kernels, so both give identical results.
 #include <cuda_runtime.h>
 
+#include "fmg_ff.cuh"
 #include "fmg_internal.cuh"
 
 namespace fmg {
@@ -134,7 +135,9 @@ __global__ void __launch_bounds__(kFB) k_pre2_fused(const float* __restrict__ b,
   }
 }
 
-template <int NU, bool TOP>
+// MODE 0: the smoothed correction goes to u_out; 1: it is added to the FP64 iterate u64 (the
+// ops' arrays); 2: it is added to the float-float iterate u64 (the solve's level data).
+template <int NU, int MODE>
 __global__ void __launch_bounds__(kFB) k_post2_fused(const float* __restrict__ u_in, const float* __restrict__ ec,
                                                       const float* __restrict__ b, float* __restrict__ u_out,
                                                       double* __restrict__ u64, int n) {
@@ -197,7 +200,9 @@ __global__ void __launch_bounds__(kFB) k_post2_fused(const float* __restrict__ u
       if (gx > 0 && gx < n && gy > 0 && gy < n) {
         const long long g = (long long)gy * np + gx;
         const float v = su[(ty2 + H) * W + (tx2 + H)];
-        if (TOP)
+        if (MODE == 2)
+          ff_store(u64 + g, ff_add_f(ff_load(u64 + g), v));
+        else if (MODE == 1)
           u64[g] += (double)v;
         else
           u_out[g] = v;
@@ -238,7 +243,8 @@ cudaError_t launch_pre_fused(int dim, LevelGeo g, int nu, const float* b, float*
 }
 
 cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, const float* ec, const float* b,
-                              float* u_out, double* u64_top, cudaStream_t s) {
+                              float* u_out, double* u64_top, cudaStream_t s, bool u_ff) {
+  const int mode = u64_top ? (u_ff ? 2 : 1) : 0;
   if (dim != 2) return cudaErrorInvalidValue;
   const unsigned t = (unsigned)((g.n + 1 + kFT - 1) / kFT);
   const dim3 grid(t, t);
@@ -246,22 +252,28 @@ cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, co
   if (nu == 1) {
     constexpr int W = kFT + 2 * 2;
     const size_t smem = sizeof(float) * (2 * W * W + (W / 2 + 2) * (W / 2 + 2));
-    if (u64_top) {
-      if ((e = set_smem(k_post2_fused<1, true>, smem)) != cudaSuccess) return e;
-      k_post2_fused<1, true><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+    if (mode == 2) {
+      if ((e = set_smem(k_post2_fused<1, 2>, smem)) != cudaSuccess) return e;
+      k_post2_fused<1, 2><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+    } else if (mode == 1) {
+      if ((e = set_smem(k_post2_fused<1, 1>, smem)) != cudaSuccess) return e;
+      k_post2_fused<1, 1><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
     } else {
-      if ((e = set_smem(k_post2_fused<1, false>, smem)) != cudaSuccess) return e;
-      k_post2_fused<1, false><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      if ((e = set_smem(k_post2_fused<1, 0>, smem)) != cudaSuccess) return e;
+      k_post2_fused<1, 0><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
     }
   } else {
     constexpr int W = kFT + 2 * 4;
     const size_t smem = sizeof(float) * (2 * W * W + (W / 2 + 2) * (W / 2 + 2));
-    if (u64_top) {
-      if ((e = set_smem(k_post2_fused<2, true>, smem)) != cudaSuccess) return e;
-      k_post2_fused<2, true><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+    if (mode == 2) {
+      if ((e = set_smem(k_post2_fused<2, 2>, smem)) != cudaSuccess) return e;
+      k_post2_fused<2, 2><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+    } else if (mode == 1) {
+      if ((e = set_smem(k_post2_fused<2, 1>, smem)) != cudaSuccess) return e;
+      k_post2_fused<2, 1><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
     } else {
-      if ((e = set_smem(k_post2_fused<2, false>, smem)) != cudaSuccess) return e;
-      k_post2_fused<2, false><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      if ((e = set_smem(k_post2_fused<2, 0>, smem)) != cudaSuccess) return e;
+      k_post2_fused<2, 0><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
     }
   }
   return cudaGetLastError();

@@ -178,7 +178,7 @@ cudaError_t launch_cheb_shaped(int dim, LevelGeo g, const T* u, T* uo, T* d, con
                                bool first, ChebShape sh, cudaStream_t s);
 // Last Chebyshev step of the mixed path's top-level FP32 cycle fused with u64 += correction.
 cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* d, const float* b, double* u64,
-                              double cd, double cr, bool first, cudaStream_t s);
+                              double cd, double cr, bool first, cudaStream_t s, bool u_ff = false);
 template <typename T>
 cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s);
 
@@ -201,8 +201,10 @@ cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream
 cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s);
 
 // level-1 exact semilinear solve (Algorithm 3.2 step 1): Newton, dense, one CTA
+// out_ff: u is written as float-float (the mixed solve's level data)
 cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double* u, int kind, double a,
-                                 double tol, int maxit, bool f32_factor, DevState* st, cudaStream_t s);
+                                 double tol, int maxit, bool f32_factor, DevState* st, cudaStream_t s,
+                                 bool out_ff = false);
 
 // Augmented problem on V_H + span{u~} (Algorithm 3.1 step 2, eq. 3.6): one cooperative
 // persistent kernel: precompute, Newton iterations, final update u = alpha u~ + P_{H->k} c.
@@ -222,11 +224,30 @@ int aug_nvals(int dim);
 // fixed_point: the fixed-point iteration on the Galerkin stiffness instead of Newton.
 // cluster_size > 0: the thread-block-cluster variant (no cooperative launch; used when many
 // instances run concurrently), with that many CTAs; 0: the cooperative grid variant.
+// jac_f32 (mixed path): u and gn hold float-float values; out_f64: the result u is written as
+// FP64 (the last correction step of a solve).
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
-                             DevState* st, int level_index, cudaStream_t s, int cluster_size = 0, int fixed_point = 0);
+                             DevState* st, int level_index, cudaStream_t s, int cluster_size = 0, int fixed_point = 0,
+                             int out_f64 = 0);
 // Largest usable cluster size (<= 16, <= number of coarse cells) for the cluster variant, 0 if none.
 int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem);
+
+// Float-float level data of the mixed solve (fmg_ff.cu): the level iterate u, the linear
+// right-hand side b and g stored as float-float pairs in the 8-byte slots of the FP64 arrays.
+// Residual r = b - A_k u into FP32 (with d32: the first Chebyshev step from zero, e = d = e0 r).
+cudaError_t launch_residual_ff(int dim, LevelGeo g, const double* u_ff, const double* b_ff, float* r32, float* e32,
+                               cudaStream_t s, float* d32 = nullptr, double e0 = 0.0);
+// b = w (g - a f(u)) (eq. 3.4, vertex rule)
+cudaError_t launch_nonlinear_rhs_ff(int dim, LevelGeo g, const double* u_ff, const double* g_ff, double* b_ff,
+                                    int kind, double a, cudaStream_t s);
+// FMG interpolation u_f = P u_c on the interior fine nodes
+cudaError_t launch_prolong_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo gf, double* uf_ff, cudaStream_t s);
+// u += e (FP32 correction)
+cudaError_t launch_add_f32_ff(LevelGeo g, double* u_ff, const float* e32, cudaStream_t s);
+// conversions (in place allowed)
+cudaError_t launch_ff_from_f64(const double* src, double* dst_ff, long long n, cudaStream_t s);
+cudaError_t launch_ff_to_f64(const double* src_ff, double* dst, long long n, cudaStream_t s);
 
 // Fused FP32 cycle kernels of the mixed path (fmg_fused.cu): 2D, nu in {1, 2}.
 bool fused_cycle_supported(int dim, int nu_pre, int nu_post);
@@ -235,7 +256,7 @@ cudaError_t launch_pre_fused(int dim, LevelGeo g, int nu, const float* b, float*
                              cudaStream_t s);
 // u = u_in + P e_c, nu black-red sweeps; stored in u_out, or added to u64_top when non-NULL
 cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, const float* ec, const float* b,
-                              float* u_out, double* u64_top, cudaStream_t s);
+                              float* u_out, double* u64_top, cudaStream_t s, bool u_ff = false);
 
 // Sets the calling thread's error message (what fmg_last_error(NULL) returns).
 // Context services for the request server (fmg_capi.cu).

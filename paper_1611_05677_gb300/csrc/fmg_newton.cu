@@ -36,6 +36,7 @@
 
 #include <type_traits>
 
+#include "fmg_ff.cuh"
 #include "fmg_internal.cuh"
 
 namespace fmg {
@@ -328,7 +329,7 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
 // FP64 residual corrects, so the iteration converges to the same FP64 solution).
 template <typename T>
 __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
-                                double a, double tol, int maxit, DevState* st) {
+                                double a, double tol, int maxit, DevState* st, int out_ff) {
   extern __shared__ double sm[];
   const int m = n1 - 1;
   const int N = dim == 2 ? m * m : m * m * m;
@@ -426,7 +427,12 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
     if (done != 1) atomicOr(&st->flags, kFlagNewtonCap);
     st->level1_iters = it > maxit ? maxit : it;
   }
-  for (int p = threadIdx.x; p < N; p += blockDim.x) u[node_of(p, m, dim)] = U[p];
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    if (out_ff)
+      ff_store(u + node_of(p, m, dim), ff_from_double(U[p]));
+    else
+      u[node_of(p, m, dim)] = U[p];
+  }
 }
 
 // ------------------------------------------------------------------ augmented problem
@@ -488,9 +494,11 @@ __device__ __forceinline__ int pair_index(int NV, int v, int u) {
 struct AugArgs {
   int dim, nc, s, n, kind, maxit, level_index, bpc, chunk;
   int fixed_point;      // 1: fixed-point iteration (Galerkin stiffness only, no Jacobian)
+  int out_f64;          // mixed path: the update writes u as FP64 (the solve's result) instead of float-float
   double a, w, sigma_k, sigma_H, tol;
-  double* u;            // u~ on entry, u^{(l+1)} on exit (level-k nodal)
-  const double* g;      // level-k nodal g
+  ff a_ff, sigma_ff;    // mixed path: a and sigma_k as float-float
+  double* u;            // u~ on entry, u^{(l+1)} on exit (level-k nodal; float-float in the mixed path)
+  const double* g;      // level-k nodal g (float-float in the mixed path)
   double* partials;     // two buffers of [cells * bpc][NVAL] block partial rows
   long long pstride;    // doubles per buffer
   const double* Ainv;   // A_H^{-1} (= A_1^{-1}, h_1 = H), dense NH x NH, preconditioner
@@ -583,7 +591,7 @@ enum { kFirst = 0, kNewton = 1, kUpdate = 2 };
 // (alpha - 1) u~ + P c).  The residual sums of the first pass (FP64, at U = u~) plus these
 // increments give the residual at U to FP64-level accuracy.  signed |u|^{3/2} has no such
 // form and is evaluated in FP64.
-__device__ __forceinline__ void delta_f(int kind, double a, double ut, float utf, float d, float af, float& dF,
+__device__ __forceinline__ void delta_f(int kind, double a, ff ut, float utf, float d, float af, float& dF,
                                         float& Fp) {
   switch (kind) {
     case FMG_F_CUBIC: {
@@ -610,8 +618,9 @@ __device__ __forceinline__ void delta_f(int kind, double a, double ut, float utf
     }
     default: {  // FMG_F_SIGNED_POW32
       double F1, F0, Fp1, Fp0;
-      f_eval<double>(kind, a, ut + (double)d, F1, Fp1);
-      f_eval<double>(kind, a, ut, F0, Fp0);
+      const double u0 = ff_to_double(ut);
+      f_eval<double>(kind, a, u0 + (double)d, F1, Fp1);
+      f_eval<double>(kind, a, u0, F0, Fp0);
       dF = (float)(F1 - F0);
       Fp = (float)Fp1;
       break;
@@ -691,11 +700,15 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         // mixed path: FP32 increments on top of the first pass's FP64 residual sums
         const float pc0f = (float)pc0, pc1f = (float)pc1, am1f = (float)(alpha - 1.0), af = (float)A.a;
         float q0 = 0.f, q1 = 0.f, sa = 0.f;
-        auto node = [&](double ut, float zf, long long o) {
-          const float utf = (float)ut;
+        auto node = [&](ff ut, float zf, long long o) {
+          const float utf = ut.hi;
           const float dl = fmaf(am1f, utf, fmaf(pc1f, zf, pc0f));
           if (phase == kUpdate) {
-            A.u[o] = ut + (double)dl;
+            const ff un = ff_add_f(ut, dl);
+            if (A.out_f64)
+              A.u[o] = ff_to_double(un);
+            else
+              ff_store(A.u + o, un);
             return;
           }
           // chord step: the Jacobian of the first pass is reused, so only the residual
@@ -709,16 +722,62 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         int z = z0;
         // eight independent loads in flight before the arithmetic
         for (; z + 7 <= z1; z += 8, off += 8 * zstride) {
-          double v[8];
+          ff v[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = A.u[off + q * zstride];
+          for (int q = 0; q < 8; ++q) v[q] = ff_load(A.u + off + q * zstride);
 #pragma unroll
           for (int q = 0; q < 8; ++q) node(v[q], (float)(z + q), off + q * zstride);
         }
-        for (; z <= z1; ++z, off += zstride) node(A.u[off], (float)z, off);
+        for (; z <= z1; ++z, off += zstride) node(ff_load(A.u + off), (float)z, off);
         Q0 = q0;
         Q1 = q1;
         SAv = sa;
+      } else if (JF32) {
+        // mixed path, first pass: u~ and g are float-float, and f(u~) - g, A_k u~ and the
+        // residual and t/s moments are formed in float-float (FP32 error-free transformations,
+        // no FP64 arithmetic per node); the Jacobian moments in FP32 from the leading parts
+        const float a32 = (float)A.a;
+        const long long pl = np * np;
+        ff q0{0.f, 0.f}, q1{0.f, 0.f}, sa{0.f, 0.f}, t0{0.f, 0.f}, t1{0.f, 0.f}, ss{0.f, 0.f};
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f, e0 = 0.f, e1 = 0.f, js = 0.f;
+        for (int z = z0; z <= z1; ++z, off += zstride) {
+          const ff U = ff_load(A.u + off);
+          const ff Fm = ff_sub(f_ff(A.kind, A.a_ff, A.a, U), ff_load(A.g + off));
+          const float zf = (float)z;
+          q0 = ff_add_fast(q0, Fm);
+          q1 = ff_add_fast(q1, ff_mul_f(Fm, zf));
+          sa = ff_add_fast(sa, ff_mul(Fm, U));
+          if (!A.fixed_point) {
+            float Ff, Fpf;
+            f_eval<float>(A.kind, a32, U.hi, Ff, Fpf);
+            const float dz = Fpf * zf, du = Fpf * U.hi;
+            d0 += Fpf;
+            d1 += dz;
+            d2 = fmaf(dz, zf, d2);
+            e0 += du;
+            e1 = fmaf(du, zf, e1);
+            js = fmaf(du, U.hi, js);
+          }
+          // A_k u~ = sigma (2d u - sum of axis neighbours) = -sigma * neighbour sum
+          ff nsum = neighbour_sum_ff<D>(A.u, off, np, pl);
+          if (D == 3) nsum = ff_mul(nsum, A.sigma_ff);
+          const ff au = ff_neg(nsum);
+          t0 = ff_add_fast(t0, au);
+          t1 = ff_add_fast(t1, ff_mul_f(au, zf));
+          ss = ff_add_fast(ss, ff_mul(au, U));
+        }
+        Q0 = ff_to_double(q0);
+        Q1 = ff_to_double(q1);
+        SAv = ff_to_double(sa);
+        T0 = ff_to_double(t0);
+        T1 = ff_to_double(t1);
+        SSv = ff_to_double(ss);
+        D0 = d0;
+        D1 = d1;
+        D2 = d2;
+        E0 = e0;
+        E1 = e1;
+        JSv = js;
       } else
       for (int z = z0; z <= z1; ++z, off += zstride, zd += 1.0) {
         if (((z - z0) & 7) == 0) {
@@ -737,22 +796,10 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
           A.u[off] = U;
           continue;
         }
+        // FP64 path (the mixed path's passes are the branches above)
         double F, Fp = 0.0;
-        JT dj, zj;
-        const JT uj = (JT)ut;
-        if (JF32) {
-          // mixed path: f in FP64 for the residual; f' (the Jacobian's factor) in FP32 from
-          // the FP32 value, so no FP64 work or conversion goes into the Jacobian moments
-          F = f_only<double>(A.kind, A.a, U);
-          float Ff, Fpf;
-          f_eval<float>(A.kind, (float)A.a, (float)uj, Ff, Fpf);
-          dj = (JT)Fpf;
-          zj = (JT)z;
-        } else {
-          f_eval<double>(A.kind, A.a, U, F, Fp);
-          dj = (JT)Fp;
-          zj = (JT)zd;
-        }
+        f_eval<double>(A.kind, A.a, U, F, Fp);
+        const JT dj = (JT)Fp, zj = (JT)zd, uj = (JT)ut;
         const double Fm = F - A.g[off];
         Q0 += Fm;
         Q1 = fma(Fm, zd, Q1);
@@ -1428,18 +1475,18 @@ cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* 
 }
 
 cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double* u, int kind, double a, double tol,
-                                 int maxit, bool f32_factor, DevState* st, cudaStream_t s) {
+                                 int maxit, bool f32_factor, DevState* st, cudaStream_t s, bool out_ff) {
   const int m = g1.n - 1;
   const size_t N = (size_t)ipow(m, dim);
   cudaError_t e;
   if (f32_factor) {
     const size_t smem = sizeof(double) * (3 * N + 2) + sizeof(float) * (N * (N + 1) + 2 * N + 4);
     if ((e = raise_dyn_smem((const void*)k_level1_newton<float>, smem)) != cudaSuccess) return e;
-    k_level1_newton<float><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
+    k_level1_newton<float><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0);
   } else {
     const size_t smem = sizeof(double) * (3 * N + 2 + N * (N + 1) + 2 * N + 4);
     if ((e = raise_dyn_smem((const void*)k_level1_newton<double>, smem)) != cudaSuccess) return e;
-    k_level1_newton<double><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st);
+    k_level1_newton<double><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0);
   }
   return cudaGetLastError();
 }
@@ -1507,7 +1554,8 @@ int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem) {
 
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
-                             DevState* st, int level_index, cudaStream_t s, int cluster_size, int fixed_point) {
+                             DevState* st, int level_index, cudaStream_t s, int cluster_size, int fixed_point,
+                             int out_f64) {
   const size_t smem = ab.smem;
   const int nt = ab.nt;
   if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
@@ -1535,6 +1583,7 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.maxit = maxit;
   A.level_index = level_index;
   A.fixed_point = fixed_point;
+  A.out_f64 = out_f64;
   A.bpc = bpc;
   A.chunk = chunk;
   A.a = a;
@@ -1543,6 +1592,8 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.sigma_k = dim == 2 ? 1.0 : h;
   A.sigma_H = dim == 2 ? 1.0 : 1.0 / coarse_cells;
   A.tol = tol;
+  A.a_ff = ff_from_double(a);
+  A.sigma_ff = ff_from_double(A.sigma_k);
   A.u = u;
   A.g = gn;
   A.partials = ab.partials;

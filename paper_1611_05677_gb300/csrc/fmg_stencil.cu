@@ -17,6 +17,7 @@
 #include <tuple>
 #include <utility>
 
+#include "fmg_ff.cuh"
 #include "fmg_internal.cuh"
 
 namespace fmg {
@@ -93,9 +94,10 @@ __global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restric
   }
 }
 
-// The last Chebyshev step of the mixed path's top-level FP32 cycle fused with its FP64
-// update: u64 += u + d_new (the new correction is neither stored nor read back).
-template <int D>
+// The last Chebyshev step of the mixed path's top-level FP32 cycle fused with its update
+// u64 += u + d_new (the new correction is neither stored nor read back); FF: u64 holds
+// float-float values (the solve's level data) instead of FP64 ones (the ops' arrays).
+template <int D, bool FF>
 __global__ void k_cheb_add64(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ b,
                              double* __restrict__ u64, int n, float bscale, float cd, float cr, int first, int strip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
@@ -115,7 +117,10 @@ __global__ void k_cheb_add64(const float* __restrict__ u, const float* __restric
     if (D == 3) s += u[c - np] + u[c + np];
     const float zr = (b[c] * bscale + s) * inv2d - uc;
     const float dn = first ? cr * zr : cd * d[c] + cr * zr;
-    u64[c] += (double)(uc + dn);
+    if (FF)
+      ff_store(u64 + c, ff_add_f(ff_load(u64 + c), uc + dn));
+    else
+      u64[c] += (double)(uc + dn);
     um = uc;
     uc = up;
     c += so;
@@ -871,17 +876,22 @@ cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b
 }
 
 cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* d, const float* b, double* u64,
-                              double cd, double cr, bool first, cudaStream_t s) {
+                              double cd, double cr, bool first, cudaStream_t s, bool u_ff) {
   const int n = g.n;
   const ChebShape sh = cheb_shape(dim, n, 4);
   const unsigned gx = cdiv(n - 1, sh.block);
   const unsigned gs = cdiv(n - 1, sh.strip);
-  if (dim == 2)
-    k_cheb_add64<2><<<dim3(gx, gs), sh.block, 0, s>>>(u, d, b, u64, n, 1.0f, (float)cd, (float)cr, first ? 1 : 0,
-                                                      sh.strip);
+  const dim3 grid = dim == 2 ? dim3(gx, gs) : dim3(gx, n - 1, gs);
+  const float bs = dim == 2 ? 1.0f : (float)n;
+  const int f = first ? 1 : 0;
+  if (dim == 2 && u_ff)
+    k_cheb_add64<2, true><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
+  else if (dim == 2)
+    k_cheb_add64<2, false><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
+  else if (u_ff)
+    k_cheb_add64<3, true><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
   else
-    k_cheb_add64<3><<<dim3(gx, n - 1, gs), sh.block, 0, s>>>(u, d, b, u64, n, (float)n, (float)cd, (float)cr,
-                                                             first ? 1 : 0, sh.strip);
+    k_cheb_add64<3, false><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
   return cudaGetLastError();
 }
 
