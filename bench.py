@@ -32,11 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FMG fine DOFs/s to discretization error, mixed vs FP64; HBM GB/s; p50/p99"
-FP64_FLOPS_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9  # SMs x DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, keyed by
 # (kind, dim); a kernel changed since its capture has no entry (traffic null)
 TRAFFIC = {("pre_top", 2): 16_792_064 + 6_912,
-           ("augmented", 2): 68_216_064 + 1_809_920}
+           ("augmented", 2): 68_217_856 + 2_853_376,
+           ("smooth_top", 2): 50_357_248 + 261_376}
 WORKLOAD = "2D unit square P1, H=1/8, 8 refinements (2049x2049 nodes, 4,190,209 fine DOFs), u^3, 8 sin modes"
 WORKLOAD_3D = ("3D unit cube P1 on Kuhn tetrahedra, H=1/4, 6 refinements (257^3 nodes, 16,581,375 fine DOFs), "
                "exp(u)-1, 8 sin modes with U[0,1] amplitudes")
@@ -343,18 +343,20 @@ def run_ours(args):
     kt = kernel_times(torch, fmg, solvers["mixed"], flush, max(3, args.steps // 2), top)
     aug_ms, aug_n = kt[fmg.KT_AUGMENTED]
     nodes = (n + 1) ** dim
-    # augmented Newton on the top level: the FP64 work is the first pass, about 24 (2D) / 28 (3D)
-    # FP64 flops per fine node (f and f', the residual moments, the stencil A u~ and the t, G_H,
-    # s, gamma moments); the later passes are FP32 increments
-    aug_flops = (24.0 if dim == 2 else 28.0) * dofs
-    aug_tflops = aug_flops / (aug_ms * 1e-3) / 1e12 if aug_ms > 0 else None
+    # augmented Newton on the top level (mixed path, float-float level data): the first pass
+    # reads u~ and g (16 B/node), each chord pass reads u~ (8 B/node), the update reads u~ and
+    # writes u (16 B/node); the stencil neighbours of the first pass are cache hits
+    newton_top = int(results["mixed"]["stats"].newton_iters[top - 1]) or 1
+    aug_bytes = (32.0 + 8.0 * (newton_top - 1)) * nodes
+    aug_gbs = aug_bytes / (aug_ms * 1e-3) / 1e9 if aug_ms > 0 else None
     shares = {"augmented": aug_ms * aug_n}
     roof = {
-        "augmented": {"kernel": "k_augmented (mixed) on the finest level", "bound": "alu",
-                      "achieved": aug_tflops, "peak": FP64_FLOPS_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
-                      "frac": (aug_tflops * 1e12 / FP64_FLOPS_PEAK_DERIVED) if aug_tflops else None,
-                      "traffic": TRAFFIC.get(("augmented", dim)), "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                      "avg_launch_ms": aug_ms, "launches": aug_n, "algorithmic_flops_per_launch": aug_flops},
+        "augmented": {"kernel": "k_augmented (mixed) on the finest level", "bound": "hbm",
+                      "achieved": aug_gbs, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": (aug_gbs / hbm_peak) if aug_gbs else None,
+                      "traffic": TRAFFIC.get(("augmented", dim)), "peak_source": peak_kind,
+                      "avg_launch_ms": aug_ms, "launches": aug_n, "algorithmic_bytes_per_launch": aug_bytes,
+                      "newton_iterations": newton_top},
     }
     if dim == 2 and smoother["mixed"] == "rbgs":
         pre_ms, pre_n = kt[fmg.KT_PRE_TOP]
