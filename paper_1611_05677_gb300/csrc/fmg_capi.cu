@@ -174,7 +174,7 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
   float* Ainv32 = (float*)take(N1 * N1 * 4);
   DevState* st = (DevState*)take(sizeof(DevState));
   AugBuffers cfg = {};
-  aug_configure(p->dim, p->coarse_cells, &cfg);
+  aug_configure(p->dim, p->coarse_cells, p->precision == FMG_PREC_MIXED, &cfg);
   const size_t items = cfg.partial_items;
   double* partials = (double*)take(2 * items * aug_nvals(p->dim) * 8);
   if (c && base) {

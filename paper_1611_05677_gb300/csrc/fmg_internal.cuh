@@ -218,7 +218,7 @@ struct AugBuffers {
   int sms;            // multiprocessors of the device
 };
 // Fills bpc/nt/smem/partial_items for this device (occupancy-based), outside any capture.
-void aug_configure(int dim, int coarse_cells, AugBuffers* ab);
+void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab);
 int aug_nvals(int dim);
 // jac_f32: Jacobian moments in FP32 (residual stays FP64) -- the mixed-precision path.
 // fixed_point: the fixed-point iteration on the Galerkin stiffness instead of Newton.

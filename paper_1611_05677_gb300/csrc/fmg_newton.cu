@@ -741,6 +741,16 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         ff q0{0.f, 0.f}, q1{0.f, 0.f}, sa{0.f, 0.f}, t0{0.f, 0.f}, t1{0.f, 0.f}, ss{0.f, 0.f};
         float d0 = 0.f, d1 = 0.f, d2 = 0.f, e0 = 0.f, e1 = 0.f, js = 0.f;
         for (int z = z0; z <= z1; ++z, off += zstride) {
+          if (((z - z0) & 7) == 0) {
+            // touch the next eight column entries of u~ (their cache lines hold the x
+            // neighbours too) and of g, so that their loads are in flight together
+#pragma unroll
+            for (int q = 1; q <= 8; ++q)
+              if (z + q <= z1 + 1) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.u + off + q * zstride));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.g + off + q * zstride));
+              }
+          }
           const ff U = ff_load(A.u + off);
           const ff Fm = ff_sub(f_ff(A.kind, A.a_ff, A.a, U), ff_load(A.g + off));
           const float zf = (float)z;
@@ -1084,11 +1094,28 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
     // chord / fixed-point step: the residual at the new iterate (mixed path: first-pass FP64
     // sums plus this pass's increments; FP64 path: this pass's sums), solved with the factor
     // of the first iteration
-    for (int idx = tid; idx < ncell * (G::NV + 1); idx += blockDim.x) {
-      const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
-      const int chn = v < G::NV ? G::RA + v : G::SA;
-      const double x = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + chn, A.bpc);
-      cellsum[(size_t)cell * G::NVAL + chn] = JF32 ? x + S.basev[idx] : x;
+    const int total = ncell * (G::NV + 1);
+    for (int base = tid; base < total; base += 4 * blockDim.x) {
+      double x[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int idx = base + r * blockDim.x;
+        x[r] = 0.0;
+        if (idx < total) {
+          const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
+          const int chn = v < G::NV ? G::RA + v : G::SA;
+          x[r] = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + chn, A.bpc);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int idx = base + r * blockDim.x;
+        if (idx < total) {
+          const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
+          const int chn = v < G::NV ? G::RA + v : G::SA;
+          cellsum[(size_t)cell * G::NVAL + chn] = JF32 ? x[r] + S.basev[idx] : x[r];
+        }
+      }
     }
     __syncthreads();
     const double sig = A.sigma_H;
@@ -1126,12 +1153,30 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
     newton_update<D>(A, R, NH, S, 0, true, writer);
     return;
   }
-  // cell sums over the blocks of each cell (fixed order)
-  for (int idx = tid; idx < ncell * G::NVAL; idx += blockDim.x) {
-    const int cell = idx / G::NVAL, v = idx % G::NVAL;
-    if (!first && v >= G::TT && v < G::JB) continue;
-    if (A.fixed_point && v >= G::JB) continue;
-    cellsum[idx] = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + v, A.bpc);
+  // cell sums over the blocks of each cell (fixed order); with one block per cell (small
+  // levels) the partial rows are the cell sums, and eight of them are loaded together
+  auto needed = [&](int v) { return !((!first && v >= G::TT && v < G::JB) || (A.fixed_point && v >= G::JB)); };
+  if (A.bpc == 1) {
+    const int total = ncell * G::NVAL;
+    for (int base = tid; base < total; base += 8 * blockDim.x) {
+      double x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = base + r * blockDim.x;
+        x[r] = (idx < total && needed(idx % G::NVAL)) ? __ldcg(partials + idx) : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = base + r * blockDim.x;
+        if (idx < total && needed(idx % G::NVAL)) cellsum[idx] = x[r];
+      }
+    }
+  } else {
+    for (int idx = tid; idx < ncell * G::NVAL; idx += blockDim.x) {
+      const int cell = idx / G::NVAL, v = idx % G::NVAL;
+      if (!needed(v)) continue;
+      cellsum[idx] = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + v, A.bpc);
+    }
   }
   for (int idx = tid; idx < NA * ld; idx += blockDim.x) M[idx] = 0.0;
   __syncthreads();
@@ -1450,8 +1495,8 @@ size_t aug_smem(int nc) {
   return AugSmem<D, JF32>::bytes(nc);
 }
 
-// Blocks per SM of the cooperative kernel when launched with `smem` dynamic bytes (the
-// launch uses the larger of the two precisions' needs, so both kernels are sized with it).
+// Blocks per SM of the cooperative kernel of one precision when launched with `smem` dynamic
+// bytes.
 template <int D, bool JF32>
 int aug_occupancy(size_t smem) {
   int occ = 0;
@@ -1493,26 +1538,22 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
 
 int aug_nvals(int dim) { return dim == 2 ? Aug<2, false>::NVAL : Aug<3, false>::NVAL; }
 
-void aug_configure(int dim, int coarse_cells, AugBuffers* ab) {
+void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                  cudaSuccess)
     sms = 0;
   const int ncell = (int)ipow(coarse_cells, dim);
-  const size_t s0 = dim == 2 ? aug_smem<2, false>(coarse_cells) : aug_smem<3, false>(coarse_cells);
-  const size_t s1 = dim == 2 ? aug_smem<2, true>(coarse_cells) : aug_smem<3, true>(coarse_cells);
-  const size_t smem = s0 > s1 ? s0 : s1;
-  int occ[2] = {0, 0};
+  // the context's precision picks the kernel: its shared memory and residency set the grid
+  const size_t smem = mixed ? (dim == 2 ? aug_smem<2, true>(coarse_cells) : aug_smem<3, true>(coarse_cells))
+                            : (dim == 2 ? aug_smem<2, false>(coarse_cells) : aug_smem<3, false>(coarse_cells));
+  int occ_min = 0;
   if (sms > 0) {
-    if (dim == 2) {
-      occ[0] = aug_occupancy<2, false>(smem);
-      occ[1] = aug_occupancy<2, true>(smem);
-    } else {
-      occ[0] = aug_occupancy<3, false>(smem);
-      occ[1] = aug_occupancy<3, true>(smem);
-    }
+    if (dim == 2)
+      occ_min = mixed ? aug_occupancy<2, true>(smem) : aug_occupancy<2, false>(smem);
+    else
+      occ_min = mixed ? aug_occupancy<3, true>(smem) : aug_occupancy<3, false>(smem);
   }
-  const int occ_min = occ[0] < occ[1] ? occ[0] : occ[1];
   int bpc = sms > 0 ? (occ_min * sms) / ncell : 1;
   if (bpc < 0) bpc = 0;
   ab->bpc = bpc;
@@ -1561,18 +1602,27 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
   const int ncell = (int)ipow(coarse_cells, dim);
   const int sfine = 1 << (level - 1);
-  // column chunks of up to 32 nodes; on smaller levels shorter ones, until every
-  // co-resident thread has an item (each chunk costs one moment-to-channel conversion, so
-  // they are no shorter than that needs, and at least 2 nodes long)
+  // column chunks of up to 32 nodes; on smaller levels shorter ones, until every thread has
+  // an item (each chunk costs one moment-to-channel conversion, so they are no shorter than
+  // that needs, and at least 2 nodes long).  FP64 path: every co-resident thread of the
+  // grid, since its per-node work is FP64 and one SM sub-partition issues one FP64 warp
+  // instruction per ~64 clocks.  Mixed path (FP32 float-float work per node): the threads of
+  // one block per cell, and only as many blocks as the chunks fill -- on small levels one
+  // per cell, which keeps the partial rows every block gathers and the arrivals at each grid
+  // barrier few.
   const long long ncol = ipow(sfine, dim - 1);
-  const long long target = (long long)ab.bpc * nt * ncell;
+  const long long target = (long long)(jac_f32 ? 1 : ab.bpc) * nt * ncell;
   int chunk = sfine < 32 ? sfine : 32;
   while (chunk > 2 && ncol * (sfine / chunk) * ncell < target) chunk >>= 1;
   const long long items = ncol * (sfine / chunk);
-  // blocks per cell: about one chunk per thread; when that leaves blocks unfilled, the
-  // chunks are spread over all co-resident blocks of the cell instead
+  // blocks per cell: about one chunk per thread; on the FP64 path, when that leaves blocks
+  // unfilled, the chunks are spread over all co-resident blocks of the cell instead
   int bpc = (int)((items + nt - 1) / nt);
-  if (bpc > ab.bpc || items < (long long)ab.bpc * nt) bpc = (int)(items < ab.bpc ? items : ab.bpc);
+  if (jac_f32) {
+    if (bpc > ab.bpc) bpc = ab.bpc;
+  } else if (bpc > ab.bpc || items < (long long)ab.bpc * nt) {
+    bpc = (int)(items < ab.bpc ? items : ab.bpc);
+  }
   if (bpc < 1) bpc = 1;
   AugArgs A;
   A.dim = dim;

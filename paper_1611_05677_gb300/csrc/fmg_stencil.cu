@@ -453,10 +453,12 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
                                 int cheb, ChebCoef cf, int zero_start) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  CoarseLevel<T, D> L[8];
+  // level descriptors, the same for every thread: in shared memory (a per-thread copy would
+  // be local memory, 1024 copies of it)
+  __shared__ CoarseLevel<T, D> L[8];
+  __shared__ int ai_off;
   constexpr bool kStageInv = sizeof(T) == sizeof(float);
-  float* ai = nullptr;   // staged FP32 A_1^{-1} (FP32 cycle)
-  {
+  if (threadIdx.x == 0) {
     int off = 0;
     for (int j = 1; j <= jtop; ++j) {
       const int n = n0 << (j - 1);
@@ -471,8 +473,10 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
       L[j - 1].d = cheb ? sm + off + 3 * nodes : nullptr;
       off += (cheb ? 4 : 2) * nodes;
     }
-    if (kStageInv) ai = reinterpret_cast<float*>(sm + off);
+    ai_off = off;
   }
+  __syncthreads();
+  float* ai = kStageInv ? reinterpret_cast<float*>(sm + ai_off) : nullptr;   // staged FP32 A_1^{-1}
   const T inv2d = T(1) / T(2 * D);
   const int m1 = n0 - 1;
   const int N1 = D == 2 ? m1 * m1 : m1 * m1 * m1;
