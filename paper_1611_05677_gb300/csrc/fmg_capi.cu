@@ -238,14 +238,17 @@ const ChebCoef* cheb_coef(const fmg_ctx* c) {
 
 // Chebyshev-Jacobi steps first..steps-1 on A u = b at level j (one stencil pass each, d the
 // step direction), the iterate starting in `cur` and alternating with `oth`; *end receives
-// the buffer that holds the result.
+// the buffer that holds the result.  ec: the coarse correction, prolongated into the first
+// step's iterate (the cycle's prolongation fused into its first post-smoothing step).
 template <typename T>
-cudaError_t cheb_run(fmg_ctx* c, int j, T* cur, T* oth, T* d, const T* b, int first, int steps, bool top, T** end) {
+cudaError_t cheb_run(fmg_ctx* c, int j, T* cur, T* oth, T* d, const T* b, int first, int steps, bool top, T** end,
+                     const T* ec = nullptr) {
   const LevelGeo g = c->geo[j - 1];
   for (int k = first; k < steps; ++k) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    TRY(launch_cheb<T>(c->p.dim, g, cur, oth, d, b, c->cheb.cd[k], c->cheb.cr[k], k == 0, c->stream));
+    TRY(launch_cheb<T>(c->p.dim, g, cur, oth, d, b, c->cheb.cd[k], c->cheb.cr[k], k == 0, c->stream,
+                       k == first ? ec : nullptr));
     TRY(tend(c, slot));
     T* t = cur;
     cur = oth;
@@ -267,10 +270,11 @@ T* cheb_start(T* u, T* alt, int steps) {
 // cheb_start(u, alt, steps) when first = 1 (step 0 fused upstream), in u otherwise, and the
 // result ends in u (a copy only when first = 0 and the step count is odd).
 template <typename T>
-cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int steps, bool top, int first = 0) {
+cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int steps, bool top, int first = 0,
+                       const T* ec = nullptr) {
   T* start = first ? cheb_start(u, alt, steps) : u;
   T* end = nullptr;
-  TRY(cheb_run<T>(c, j, start, start == u ? alt : u, d, b, first, steps, top, &end));
+  TRY(cheb_run<T>(c, j, start, start == u ? alt : u, d, b, first, steps, top, &end, ec));
   if (end != u) TRY(launch_copy_t<T>(end, u, c->geo[j - 1].nodes, c->stream));
   return cudaSuccess;
 }
@@ -405,18 +409,22 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
   TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], uc0, s,
                                              fuse ? c->d32[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0));
   TRY(vcycle32(c, j - 1, false, fuse));
-  TRY(launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s));
+  // the prolongation u += P e_c, fused into the first post-smoothing Chebyshev step when that
+  // is a plain step (not the top level's single step fused with the update)
+  const bool prol_fused = cheb && c->p.nu_post >= 1 && (!u64_top || c->p.nu_post >= 2);
+  const float* ec = prol_fused ? c->u32[j - 2] : nullptr;
+  if (!prol_fused) TRY(launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s));
   if (cheb && u64_top && c->p.nu_post >= 1) {
     // steps 0..last-1, then the last one fused with the FP64 update, reading whichever
     // buffer holds the iterate
     const int last = c->p.nu_post - 1;
     float* end = nullptr;
-    TRY(cheb_run<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, 0, last, top, &end));
+    TRY(cheb_run<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, 0, last, top, &end, ec));
     TRY(launch_cheb_add64(dim, gf, end, c->d32[j - 1], b, u64_top, c->cheb.cd[last], c->cheb.cr[last], last == 0,
                           s, top_ff));
     return cudaSuccess;
   }
-  if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_post, top));
+  if (cheb) TRY(cheb_steps<float>(c, j, u, c->u32b[j - 1], c->d32[j - 1], b, c->p.nu_post, top, 0, ec));
   for (int it = 0; !cheb && it < c->p.nu_post; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));

@@ -160,9 +160,11 @@ struct ChebCoef {
 // Coefficients of steps 0..kMaxCheb-1 (host).
 ChebCoef cheb_coefficients();
 // One Chebyshev step on level geometry g: reads u (stencil), b and d (k > 0), writes uo and d.
+// With ec (the next coarser level's correction) the step's iterate is u + P ec (the cycle's
+// prolongation, fused into its first post-smoothing step).
 template <typename T>
 cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr, bool first,
-                        cudaStream_t s);
+                        cudaStream_t s, const T* ec = nullptr);
 // Launch shape of the Chebyshev step kernel: threads per block along x and nodes per thread
 // along the outer axis.  cheb_shape: the autotuned shape of this device and size if there
 // is one, else the default rule; set_cheb_shape records a tuned one (process-wide).
@@ -175,7 +177,7 @@ bool cheb_shape_tuned(int dim, int n, int elem_bytes, ChebShape* out);
 void set_cheb_shape(int dim, int n, int elem_bytes, ChebShape sh);
 template <typename T>
 cudaError_t launch_cheb_shaped(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr,
-                               bool first, ChebShape sh, cudaStream_t s);
+                               bool first, ChebShape sh, cudaStream_t s, const T* ec = nullptr);
 // Last Chebyshev step of the mixed path's top-level FP32 cycle fused with u64 += correction.
 cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* d, const float* b, double* u64,
                               double cd, double cr, bool first, cudaStream_t s, bool u_ff = false);

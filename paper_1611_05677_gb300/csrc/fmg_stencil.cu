@@ -66,24 +66,49 @@ __global__ void k_rbgs3(T* __restrict__ u, const T* __restrict__ b, int n, int c
 // once per node from memory along the strip plus the in-plane neighbours from cache.
 constexpr int kChebStrip = 8;
 
+// With ec (the first post-smoothing step of a cycle) the iterate is u + P e_c: the coarse
+// correction prolongated on the fly (two coarse values per fine node, P of eq. 3.3) for the
+// node and its stencil neighbours, in place of a separate prolongation pass.
 template <typename T, int D>
+__device__ __forceinline__ T prolong_at(const T* __restrict__ ec, long long cp, int i, int j, int l) {
+  if (D == 2)
+    return T(0.5) * (ec[(long long)(j >> 1) * cp + (i >> 1)] + ec[(long long)((j + 1) >> 1) * cp + ((i + 1) >> 1)]);
+  return T(0.5) * (ec[((long long)(l >> 1) * cp + (j >> 1)) * cp + (i >> 1)] +
+                   ec[((long long)((l + 1) >> 1) * cp + ((j + 1) >> 1)) * cp + ((i + 1) >> 1)]);
+}
+
+template <typename T, int D, bool PROL>
 __global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restrict__ d, const T* __restrict__ b, int n,
-                       T bscale, T cd, T cr, int first, int strip) {
+                       T bscale, T cd, T cr, int first, int strip, const T* __restrict__ ec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = D == 3 ? blockIdx.y + 1 : 0;                 // in-plane row (3D only)
   const int z0 = (D == 2 ? blockIdx.y : blockIdx.z) * strip + 1;   // strip start (outer axis)
   if (i > n - 1) return;
   const long long np = n + 1;
   const long long so = D == 2 ? np : np * np;                // stride of the outer axis
+  const long long cp = (n >> 1) + 1;                         // coarse row length (PROL)
+  // iterate at fine node (x, y[, w]) with the outer axis last: u (+ P e_c)
+  auto iter = [&](long long cc, int x, int y, int w) -> T {
+    T v = u[cc];
+    if (PROL) v += D == 2 ? prolong_at<T, 2>(ec, cp, x, y, 0) : prolong_at<T, 3>(ec, cp, x, y, w);
+    return v;
+  };
   long long c = (D == 2 ? (long long)z0 * np : ((long long)z0 * np + j) * np) + i;
-  T um = u[c - so], uc = u[c];
+  T um = D == 2 ? iter(c - so, i, z0 - 1, 0) : iter(c - so, i, j, z0 - 1);
+  T uc = D == 2 ? iter(c, i, z0, 0) : iter(c, i, j, z0);
   const T inv2d = T(1) / T(2 * D);
 #pragma unroll
   for (int r = 0; r < kChebStrip; ++r) {
     if (r >= strip || z0 + r > n - 1) break;
-    const T up = u[c + so];
-    T s = (u[c - 1] + u[c + 1]) + (um + up);
-    if (D == 3) s += u[c - np] + u[c + np];
+    const int z = z0 + r;
+    const T up = D == 2 ? iter(c + so, i, z + 1, 0) : iter(c + so, i, j, z + 1);
+    T s;
+    if (D == 2) {
+      s = (iter(c - 1, i - 1, z, 0) + iter(c + 1, i + 1, z, 0)) + (um + up);
+    } else {
+      s = (iter(c - 1, i - 1, j, z) + iter(c + 1, i + 1, j, z)) + (um + up);
+      s += iter(c - np, i, j - 1, z) + iter(c + np, i, j + 1, z);
+    }
     const T zr = (b[c] * bscale + s) * inv2d - uc;
     const T dn = first ? cr * zr : cd * d[c] + cr * zr;
     d[c] = dn;
@@ -859,24 +884,30 @@ void set_cheb_shape(int dim, int n, int elem_bytes, ChebShape sh) {
 
 template <typename T>
 cudaError_t launch_cheb_shaped(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr,
-                               bool first, ChebShape sh, cudaStream_t s) {
+                               bool first, ChebShape sh, cudaStream_t s, const T* ec) {
   const int n = g.n;
   if (sh.block < 32 || sh.block > 1024 || (sh.block & 31) || sh.strip < 1 || sh.strip > kChebStrip)
     return cudaErrorInvalidValue;
   const unsigned gx = cdiv(n - 1, sh.block);
   const unsigned gs = cdiv(n - 1, sh.strip);
-  if (dim == 2)
-    k_cheb<T, 2><<<dim3(gx, gs), sh.block, 0, s>>>(u, uo, d, b, n, T(1), T(cd), T(cr), first ? 1 : 0, sh.strip);
+  const dim3 grid = dim == 2 ? dim3(gx, gs) : dim3(gx, n - 1, gs);
+  const T bs = dim == 2 ? T(1) : T(n);
+  const int f = first ? 1 : 0;
+  if (dim == 2 && ec)
+    k_cheb<T, 2, true><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
+  else if (dim == 2)
+    k_cheb<T, 2, false><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
+  else if (ec)
+    k_cheb<T, 3, true><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
   else
-    k_cheb<T, 3><<<dim3(gx, n - 1, gs), sh.block, 0, s>>>(u, uo, d, b, n, T(n), T(cd), T(cr), first ? 1 : 0,
-                                                          sh.strip);
+    k_cheb<T, 3, false><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cheb(int dim, LevelGeo g, const T* u, T* uo, T* d, const T* b, double cd, double cr, bool first,
-                        cudaStream_t s) {
-  return launch_cheb_shaped<T>(dim, g, u, uo, d, b, cd, cr, first, cheb_shape(dim, g.n, (int)sizeof(T)), s);
+                        cudaStream_t s, const T* ec) {
+  return launch_cheb_shaped<T>(dim, g, u, uo, d, b, cd, cr, first, cheb_shape(dim, g.n, (int)sizeof(T)), s, ec);
 }
 
 cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* d, const float* b, double* u64,
@@ -918,13 +949,13 @@ template cudaError_t launch_coarse_cycle<double>(int, int, int, double*, const d
 template cudaError_t launch_coarse_cycle<float>(int, int, int, float*, const float*, int, int, const double*,
                                                 const float*, const ChebCoef*, bool, cudaStream_t);
 template cudaError_t launch_cheb<double>(int, LevelGeo, const double*, double*, double*, const double*, double, double,
-                                         bool, cudaStream_t);
+                                         bool, cudaStream_t, const double*);
 template cudaError_t launch_cheb<float>(int, LevelGeo, const float*, float*, float*, const float*, double, double, bool,
-                                        cudaStream_t);
+                                        cudaStream_t, const float*);
 template cudaError_t launch_cheb_shaped<double>(int, LevelGeo, const double*, double*, double*, const double*, double,
-                                                double, bool, ChebShape, cudaStream_t);
+                                                double, bool, ChebShape, cudaStream_t, const double*);
 template cudaError_t launch_cheb_shaped<float>(int, LevelGeo, const float*, float*, float*, const float*, double,
-                                               double, bool, ChebShape, cudaStream_t);
+                                               double, bool, ChebShape, cudaStream_t, const float*);
 template cudaError_t launch_copy_t<double>(const double*, double*, long long, cudaStream_t);
 template cudaError_t launch_copy_t<float>(const float*, float*, long long, cudaStream_t);
 template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t);
