@@ -457,12 +457,15 @@ cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
 // The same cycle on the mixed solve's float-float level data: float-float residual -> FP32
 // cycle from e = 0 -> float-float update (the residual and the update in FP32 error-free
 // transformations instead of FP64 arithmetic).
-cudaError_t top_cycle_ff(fmg_ctx* c, int k, double* u, const double* b) {
+// residual_ready: the residual (and the first step from zero) is already in b32 / u32 (the
+// level start computed it).
+cudaError_t top_cycle_ff(fmg_ctx* c, int k, double* u, const double* b, bool residual_ready = false) {
   const LevelGeo g = c->geo[k - 1];
   const bool fuse = fuse_first_step<float>(c, k);
   float* e0buf = fuse ? cheb_start(c->u32[k - 1], c->u32b[k - 1], c->p.nu_pre) : c->u32[k - 1];
-  TRY(launch_residual_ff(c->p.dim, g, u, b, c->b32[k - 1], e0buf, c->stream, fuse ? c->d32[k - 1] : nullptr,
-                         fuse ? cheb_e0(c, k) : 0.0));
+  if (!residual_ready)
+    TRY(launch_residual_ff(c->p.dim, g, u, b, c->b32[k - 1], e0buf, c->stream, fuse ? c->d32[k - 1] : nullptr,
+                           fuse ? cheb_e0(c, k) : 0.0));
   if (c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS) return vcycle32_fused(c, k, u, true);
   if (k > coarse_cycle_top<float>(c)) return vcycle32(c, k, true, fuse, u, true);
   TRY(vcycle32(c, k, true));
@@ -489,15 +492,25 @@ cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
 }
 
 // Algorithm 3.1 at level k >= 2 on the mixed solve's float-float level data (u = u[k-1],
-// b = b[k-1], g = gf[k-1]); out_f64: the result is left as FP64 (the solve's last step).
-cudaError_t correction_step_ff(fmg_ctx* c, int k, bool out_f64) {
+// b = b[k-1], g = gf[k-1]); out_f64: the result is left as FP64 (the solve's last step);
+// from_coarse: u starts as the FMG interpolation of level k-1 (the first step of the level),
+// formed here together with b and the first residual in one pass.
+cudaError_t correction_step_ff(fmg_ctx* c, int k, bool out_f64, bool from_coarse = false) {
   const LevelGeo g = c->geo[k - 1];
   double* u = c->u[k - 1];
   int slot_step = -1, slot_aug = -1;
   TRY(tbegin(c, FMG_KT_CORRECTION, k, &slot_step));
   // step 1: b = (g, v) - (f(x, u^{(l)}), v)   (eq. 3.4)
-  TRY(launch_nonlinear_rhs_ff(c->p.dim, g, u, c->gf[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream));
-  for (int i = 0; i < c->p.m_vcycles; ++i) TRY(top_cycle_ff(c, k, u, c->b[k - 1]));
+  if (from_coarse) {
+    const bool fuse = fuse_first_step<float>(c, k);
+    float* e0buf = fuse ? cheb_start(c->u32[k - 1], c->u32b[k - 1], c->p.nu_pre) : c->u32[k - 1];
+    TRY(launch_level_start_ff(c->p.dim, c->geo[k - 2], c->u[k - 2], g, u, c->gf[k - 1], c->b[k - 1], c->p.f,
+                              c->p.f_scale, c->b32[k - 1], e0buf, fuse ? c->d32[k - 1] : nullptr,
+                              fuse ? cheb_e0(c, k) : 0.0, c->stream));
+  } else {
+    TRY(launch_nonlinear_rhs_ff(c->p.dim, g, u, c->gf[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream));
+  }
+  for (int i = 0; i < c->p.m_vcycles; ++i) TRY(top_cycle_ff(c, k, u, c->b[k - 1], from_coarse && i == 0));
   // step 2: semilinear problem on V_H + span{u~}  (eq. 3.6)
   TRY(tbegin(c, FMG_KT_AUGMENTED, k, &slot_aug));
   TRY(launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->gf[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
@@ -516,15 +529,14 @@ cudaError_t run_fmg(fmg_ctx* c) {
   TRY(launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
                            c->p.level1_maxit, mixed, c->st, c->stream, mixed && c->nlev > 1));
   for (int k = 2; k <= c->nlev; ++k) {
-    // u^{(0)}_{h_k} = u_{h_{k-1}}: the natural inclusion
-    if (mixed)
-      TRY(launch_prolong_ff(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], c->stream));
-    else
+    // u^{(0)}_{h_k} = u_{h_{k-1}}: the natural inclusion (the mixed path forms it in the pass
+    // that starts its first correction step)
+    if (!mixed)
       TRY(launch_prolong<double, double>(c->p.dim, c->geo[k - 2], c->u[k - 2], c->geo[k - 1], c->u[k - 1], 0,
                                          c->stream));
     for (int l = 0; l < c->p.p_corrections; ++l) {
       if (mixed)
-        TRY(correction_step_ff(c, k, k == c->nlev && l == c->p.p_corrections - 1));
+        TRY(correction_step_ff(c, k, k == c->nlev && l == c->p.p_corrections - 1, l == 0));
       else
         TRY(correction_step(c, k, c->u[k - 1]));
     }

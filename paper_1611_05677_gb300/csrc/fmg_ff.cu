@@ -76,6 +76,75 @@ __global__ void k_prolong_ff(const double* __restrict__ uc, int nc, double* __re
   ff_store(uf + f, ff{0.5f * s.hi, 0.5f * s.lo});
 }
 
+// The start of a level of Algorithm 3.2 in one pass: the FMG interpolation u = P u_c, the
+// right-hand side b = w (g - a f(u)) of eq. (3.4) and the first residual r = b - A_k u of the
+// defect correction (with d32: the first Chebyshev step from zero, e = d = e0 r).  The
+// interpolated values at the stencil neighbours are formed on the fly from u_c, with the
+// same operations as the stored ones, so the result is that of the three separate passes.
+template <int D>
+__device__ __forceinline__ ff interp_ff(const double* __restrict__ uc, long long cp, int i, int j, int l) {
+  long long a, z;
+  if (D == 2) {
+    a = (long long)(j >> 1) * cp + (i >> 1);
+    z = (long long)((j + 1) >> 1) * cp + ((i + 1) >> 1);
+  } else {
+    a = ((long long)(l >> 1) * cp + (j >> 1)) * cp + (i >> 1);
+    z = ((long long)((l + 1) >> 1) * cp + ((j + 1) >> 1)) * cp + ((i + 1) >> 1);
+  }
+  const ff s = ff_add(ff_load(uc + a), ff_load(uc + z));
+  return ff{0.5f * s.hi, 0.5f * s.lo};
+}
+
+template <int D>
+__global__ void k_level_start_ff(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
+                                 double* __restrict__ b, int n, int kind, ff a, double a64, ff w, ff sigma,
+                                 float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32,
+                                 float e0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, l = D == 3 ? blockIdx.z : 0;
+  if (i > n) return;
+  const long long np = n + 1;
+  const long long cp = (n >> 1) + 1;
+  const long long c = ((long long)l * np + j) * np + i;
+  auto inner = [&](int x, int y, int z) {
+    return x > 0 && x < n && y > 0 && y < n && (D == 2 || (z > 0 && z < n));
+  };
+  float v = 0.f;
+  ff bv{0.f, 0.f};
+  if (inner(i, j, l)) {
+    const ff U = interp_ff<D>(uc, cp, i, j, l);
+    ff_store(u + c, U);
+    bv = ff_mul(ff_sub(ff_load(g + c), f_ff(kind, a, a64, U)), w);
+    // sum_k (u_k - u_c) as in neighbour_sum_ff, from the interpolated neighbours (zero on the
+    // boundary)
+    float s = 0.f, lo = 0.f;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      const int dx = ax == 0, dy = ax == 1, dz = ax == 2;
+      const ff um = inner(i - dx, j - dy, l - dz) ? interp_ff<D>(uc, cp, i - dx, j - dy, l - dz) : ff{0.f, 0.f};
+      const ff up = inner(i + dx, j + dy, l + dz) ? interp_ff<D>(uc, cp, i + dx, j + dy, l + dz) : ff{0.f, 0.f};
+      float dm, em, dp, ep, t, et;
+      two_sum(um.hi, -U.hi, dm, em);
+      two_sum(up.hi, -U.hi, dp, ep);
+      two_sum(dm, dp, t, et);
+      float s2, e2;
+      two_sum(s, t, s2, e2);
+      s = s2;
+      lo += ((em + ep) + (et + e2)) + ((um.lo - U.lo) + (up.lo - U.lo));
+    }
+    ff S;
+    two_sum(s, lo, S.hi, S.lo);
+    if (D == 3) S = ff_mul(S, sigma);
+    const ff r = ff_add(bv, S);
+    v = r.hi + r.lo;
+  }
+  ff_store(b + c, bv);
+  r32[c] = v;
+  const float e = d32 ? e0 * v : 0.f;
+  e32[c] = e;
+  if (d32) d32[c] = e;
+}
+
 __global__ void k_add_f32_ff(double* __restrict__ uff, const float* __restrict__ e, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) ff_store(uff + i, ff_add_f(ff_load(uff + i), e[i]));
@@ -122,6 +191,23 @@ cudaError_t launch_prolong_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGe
     k_prolong_ff<2><<<grid, kB, 0, s>>>(uc_ff, gc.n, uf_ff, nf);
   else
     k_prolong_ff<3><<<grid, kB, 0, s>>>(uc_ff, gc.n, uf_ff, nf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo g, double* u_ff,
+                                  const double* g_ff, double* b_ff, int kind, double a, float* r32, float* e32,
+                                  float* d32, double e0, cudaStream_t s) {
+  const int n = g.n;
+  if (gc.n * 2 != n) return cudaErrorInvalidValue;
+  const double h = 1.0 / n;
+  const double w = dim == 2 ? h * h : h * h * h;
+  const dim3 grid(cdiv_u(n + 1, kB), n + 1, dim == 3 ? n + 1 : 1);
+  if (dim == 2)
+    k_level_start_ff<2><<<grid, kB, 0, s>>>(uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w),
+                                            ff{1.f, 0.f}, r32, e32, d32, (float)e0);
+  else
+    k_level_start_ff<3><<<grid, kB, 0, s>>>(uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w),
+                                            ff_from_double(h), r32, e32, d32, (float)e0);
   return cudaGetLastError();
 }
 

@@ -247,6 +247,11 @@ cudaError_t launch_nonlinear_rhs_ff(int dim, LevelGeo g, const double* u_ff, con
 cudaError_t launch_prolong_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo gf, double* uf_ff, cudaStream_t s);
 // u += e (FP32 correction)
 cudaError_t launch_add_f32_ff(LevelGeo g, double* u_ff, const float* e32, cudaStream_t s);
+// The start of level g in one pass: u = P u_c (FMG interpolation), b = w (g - a f(u)), and the
+// first residual r32 = b - A u with e32 (and d32 with e0) as launch_residual_ff writes them.
+cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo g, double* u_ff,
+                                  const double* g_ff, double* b_ff, int kind, double a, float* r32, float* e32,
+                                  float* d32, double e0, cudaStream_t s);
 // conversions (in place allowed)
 cudaError_t launch_ff_from_f64(const double* src, double* dst_ff, long long n, cudaStream_t s);
 cudaError_t launch_ff_to_f64(const double* src_ff, double* dst, long long n, cudaStream_t s);
