@@ -35,7 +35,7 @@ METRIC = "FMG fine DOFs/s to discretization error, mixed vs FP64; HBM GB/s; p50/
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, keyed by
 # (kind, dim); a kernel changed since its capture has no entry (traffic null)
 TRAFFIC = {("pre_top", 2): 16_792_064 + 6_912,
-           ("augmented", 2): 68_217_856 + 2_853_376,
+           ("augmented", 2): 67_914_496 + 2_956_288,
            ("smooth_top", 2): 50_357_248 + 261_376}
 WORKLOAD = "2D unit square P1, H=1/8, 8 refinements (2049x2049 nodes, 4,190,209 fine DOFs), u^3, 8 sin modes"
 WORKLOAD_3D = ("3D unit cube P1 on Kuhn tetrahedra, H=1/4, 6 refinements (257^3 nodes, 16,581,375 fine DOFs), "
@@ -435,7 +435,7 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32 cycles + f64 residual/Newton",
+            "dtype": "f32 cycles + float-float (f32 pair) level data + f64 Newton",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if dim == 2 else WORKLOAD_3D, "precision": "mixed",
                        "smoother": smoother["mixed"], "fp64_smoother": smoother["fp64"], "instances": world,
@@ -554,7 +554,7 @@ def run_batch(args):
         line = {
             "metric": METRIC, "value": world * dofs / (mix * 1e-3), "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mix, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 residual/Newton",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + float-float (f32 pair) level data + f64 Newton",
             "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "instances": len(probs) * world, "fine_dofs_per_step": dofs,
                        "precision": "mixed", "l2": "flushed between steps (512 MB write outside the timed events)",
@@ -678,7 +678,7 @@ def run_serve(args):
         line = {
             "metric": METRIC, "value": world * dofs / span, "unit": "DOF/s", "n_gpus": world,
             "steps": len(measured), "warmup": args.serve_warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + f64 residual/Newton", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + float-float (f32 pair) level data + f64 Newton", "data": "synthetic",
             "config": {"workload": SERVE_WORKLOAD, "requests": len(reqs), "measured": len(measured),
                        "rate_per_s": args.serve_rate, "max_inflight": args.max_inflight,
                        "g": "pool of 2 seeded random-mode fields per (dim, refinements)"},

@@ -752,7 +752,9 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
               }
           }
           const ff U = ff_load(A.u + off);
-          const ff Fm = ff_sub(f_ff(A.kind, A.a_ff, A.a, U), ff_load(A.g + off));
+          // f(u~) - g enters the sums only: an add whose error is bounded relative to |f| + |g|
+          // (as for an FP64 subtraction) suffices
+          const ff Fm = ff_add_fast(f_ff(A.kind, A.a_ff, A.a, U), ff_neg(ff_load(A.g + off)));
           const float zf = (float)z;
           q0 = ff_add_fast(q0, Fm);
           q1 = ff_add_fast(q1, ff_mul_f(Fm, zf));
@@ -1554,6 +1556,10 @@ void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab) {
     else
       occ_min = mixed ? aug_occupancy<3, true>(smem) : aug_occupancy<3, false>(smem);
   }
+  // at most two blocks per SM: every block takes the dense Newton step, so a third one per SM
+  // adds a contending copy of it and more partial rows to gather, while the passes do not
+  // speed up (FP64 path: bound by the SM's FP64 pipe); measured 20 % slower at three
+  if (occ_min > 2) occ_min = 2;
   int bpc = sms > 0 ? (occ_min * sms) / ncell : 1;
   if (bpc < 0) bpc = 0;
   ab->bpc = bpc;
