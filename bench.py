@@ -35,7 +35,7 @@ METRIC = "FMG fine DOFs/s to discretization error, mixed vs FP64; HBM GB/s; p50/
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, keyed by
 # (kind, dim); a kernel changed since its capture has no entry (traffic null)
 TRAFFIC = {("pre_top", 2): 16_792_064 + 6_912,
-           ("augmented", 2): 67_914_496 + 2_956_288,
+           ("augmented", 2): 68_189_696 + 2_465_792,
            ("smooth_top", 2): 50_357_248 + 261_376}
 WORKLOAD = "2D unit square P1, H=1/8, 8 refinements (2049x2049 nodes, 4,190,209 fine DOFs), u^3, 8 sin modes"
 WORKLOAD_3D = ("3D unit cube P1 on Kuhn tetrahedra, H=1/4, 6 refinements (257^3 nodes, 16,581,375 fine DOFs), "

@@ -13,6 +13,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "fmg_internal.cuh"
 
 namespace fmg {
@@ -113,6 +115,84 @@ __host__ __device__ __forceinline__ ff ff_from_double(double x) {
 }
 __host__ __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
 
+__host__ __device__ __forceinline__ unsigned ff_bits(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, sizeof u);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double ff_double_from_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
+
+// hi + lo rounded to the nearest double (ties to even), the value ff_to_double gives, formed
+// with integer operations only: this GPU issues FP64 instructions (conversions included) at
+// 1/64 of the FP32 rate, and a pass that writes an FP64 result per node is otherwise bound by
+// them.  From the IEEE-754 binary32/binary64 formats: for a pair with hi normal, lo normal or
+// zero and |lo| <= ulp(hi)/2, the significands are aligned on a 64-bit integer (hi's leading
+// bit at bit 62), added or subtracted with a sticky bit for the bits of lo shifted out,
+// normalized by at most one place and rounded at bit 10.  Zero, subnormal, infinite and NaN
+// parts take the FP64 add.
+__host__ __device__ __forceinline__ double ff_to_double_rn(ff x) {
+  const unsigned bh = ff_bits(x.hi), bl = ff_bits(x.lo);
+  const int eh = (int)((bh >> 23) & 0xffu), el = (int)((bl >> 23) & 0xffu);
+  const unsigned long long sign = (unsigned long long)(bh >> 31) << 63;
+  const int d = eh - el;
+  const bool lo_zero = (bl & 0x7fffffffu) == 0u;
+  if (eh == 0 || eh == 255 || (!lo_zero && (el == 0 || d < 24))) return ff_to_double(x);
+  const unsigned long long H = (unsigned long long)((bh & 0x7fffffu) | 0x800000u);
+  if (lo_zero) return ff_double_from_bits(sign | ((unsigned long long)(eh + 896) << 52) | ((H & 0x7fffffull) << 29));
+  const unsigned long long Lm = (unsigned long long)((bl & 0x7fffffu) | 0x800000u);
+  // lo on hi's grid: hi = H 2^(eh-150) = (H << 39) 2^(eh-189); lo = Lm 2^(el-150) = (Lm << (39-d)) 2^(eh-189)
+  unsigned long long L;
+  bool sticky = false;
+  if (d <= 39) {
+    L = Lm << (39 - d);
+  } else if (d < 64) {
+    L = Lm >> (d - 39);
+    sticky = (Lm & ((1ull << (d - 39)) - 1ull)) != 0ull;
+  } else {
+    L = 0ull;
+    sticky = true;
+  }
+  unsigned long long R = H << 39;
+  int e = eh + 896;                                 // double exponent field of 2^(eh-127)
+  if (((bh ^ bl) >> 31) == 0u) {
+    R += L;                                         // true value: R + (a fraction if sticky)
+  } else {
+    R -= L;
+    if (sticky) R -= 1ull;                          // true value: R + a fraction in (0, 1)
+  }
+  if (R >> 63) {                                    // carried past bit 62
+    sticky = sticky || (R & 1ull);
+    R >>= 1;
+    ++e;
+  } else if (!(R >> 62)) {                          // borrowed below bit 62 (at most one place)
+    R <<= 1;
+    --e;
+  }
+  unsigned long long m = R >> 10;                   // 53 significant bits
+  const bool round = (R >> 9) & 1ull;
+  sticky = sticky || (R & 0x1ffull) != 0ull;
+  if (round && (sticky || (m & 1ull))) {
+    ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++e;
+    }
+  }
+  return ff_double_from_bits(sign | ((unsigned long long)e << 52) | (m & 0xfffffffffffffull));
+}
+
 // A float-float value stored in an 8-byte slot (the layout of the double arrays it replaces).
 __device__ __forceinline__ ff ff_load(const double* p) {
   const float2 v = *reinterpret_cast<const float2*>(p);
@@ -120,28 +200,39 @@ __device__ __forceinline__ ff ff_load(const double* p) {
 }
 __device__ __forceinline__ void ff_store(double* p, ff x) { *reinterpret_cast<float2*>(p) = make_float2(x.hi, x.lo); }
 
-// sum_k (u_k - u_c) over the 2d axis neighbours of node c: the hi differences and their sum
+// sum_k (u_k - u_c) over the 2d axis neighbours of a node with value uc, from the neighbour
+// values um[ax] (at -1 along axis ax) and up[ax] (at +1): the hi differences and their sum
 // through TwoSum (exact), the lo parts and the rounding terms added after.
 template <int D>
-__device__ __forceinline__ ff neighbour_sum_ff(const double* __restrict__ u, long long c, long long np, long long pl) {
-  const ff uc = ff_load(u + c);
-  const long long o[3] = {1, np, pl};
+__device__ __forceinline__ ff neighbour_sum_ff_v(ff uc, const ff* um, const ff* up) {
   float s = 0.f, lo = 0.f;
 #pragma unroll
   for (int ax = 0; ax < D; ++ax) {
-    const ff um = ff_load(u + c - o[ax]), up = ff_load(u + c + o[ax]);
     float dm, em, dp, ep, t, et;
-    two_sum(um.hi, -uc.hi, dm, em);
-    two_sum(up.hi, -uc.hi, dp, ep);
+    two_sum(um[ax].hi, -uc.hi, dm, em);
+    two_sum(up[ax].hi, -uc.hi, dp, ep);
     two_sum(dm, dp, t, et);
     float s2, e2;
     two_sum(s, t, s2, e2);
     s = s2;
-    lo += ((em + ep) + (et + e2)) + ((um.lo - uc.lo) + (up.lo - uc.lo));
+    lo += ((em + ep) + (et + e2)) + ((um[ax].lo - uc.lo) + (up[ax].lo - uc.lo));
   }
   ff r;
   two_sum(s, lo, r.hi, r.lo);
   return r;
+}
+
+// The same at node c of a nodal array (axis strides 1, np, pl).
+template <int D>
+__device__ __forceinline__ ff neighbour_sum_ff(const double* __restrict__ u, long long c, long long np, long long pl) {
+  const long long o[3] = {1, np, pl};
+  ff um[D], up[D];
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    um[ax] = ff_load(u + c - o[ax]);
+    up[ax] = ff_load(u + c + o[ax]);
+  }
+  return neighbour_sum_ff_v<D>(ff_load(u + c), um, up);
 }
 
 // a f(u) in float-float for the polynomial nonlinearities (Sec. 4 examples); the exponential

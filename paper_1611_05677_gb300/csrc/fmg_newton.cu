@@ -628,6 +628,104 @@ __device__ __forceinline__ void delta_f(int kind, double a, ff ut, float utf, fl
   }
 }
 
+// Moments of the mixed first pass over a run of column nodes: the residual and t/s moments in
+// float-float, the Jacobian moments in FP32.
+struct FirstMoments {
+  ff q0, q1, sa, t0, t1, ss;
+  float d0, d1, d2, e0, e1, js;
+};
+
+// One node of the mixed first pass: u~ = U and g = G at the node, its axis neighbours um[ax]
+// and up[ax], fine z coordinate z.  CUBIC selects a f(u) = a u^3 at compile time (no branch in
+// the node's arithmetic); otherwise the nonlinearity is chosen by A.kind.  The Jacobian
+// moments are formed also in the fixed-point iteration, which does not read them.
+template <int D, bool CUBIC>
+__device__ __forceinline__ void first_node(const AugArgs& A, FirstMoments& m, ff U, ff G, const ff* um, const ff* up,
+                                           int z) {
+  ff F;
+  float Fpf;
+  if (CUBIC) {
+    F = ff_mul(ff_mul(ff_mul(U, U), U), A.a_ff);
+    Fpf = 3.0f * (A.a_ff.hi * (U.hi * U.hi));   // the FP32 derivative of the cubic, as f_eval forms it
+  } else {
+    F = f_ff(A.kind, A.a_ff, A.a, U);
+    float Ff;
+    f_eval<float>(A.kind, A.a_ff.hi, U.hi, Ff, Fpf);
+  }
+  // f(u~) - g enters the sums only: an add whose error is bounded relative to |f| + |g| (as
+  // for an FP64 subtraction) suffices
+  const ff Fm = ff_add_fast(F, ff_neg(G));
+  const float zf = (float)z;
+  m.q0 = ff_add_fast(m.q0, Fm);
+  m.q1 = ff_add_fast(m.q1, ff_mul_f(Fm, zf));
+  m.sa = ff_add_fast(m.sa, ff_mul(Fm, U));
+  const float dz = Fpf * zf, du = Fpf * U.hi;
+  m.d0 += Fpf;
+  m.d1 += dz;
+  m.d2 = fmaf(dz, zf, m.d2);
+  m.e0 += du;
+  m.e1 = fmaf(du, zf, m.e1);
+  m.js = fmaf(du, U.hi, m.js);
+  // A_k u~ = sigma (2d u - sum of axis neighbours) = -sigma * neighbour sum
+  ff nsum = neighbour_sum_ff_v<D>(U, um, up);
+  if (D == 3) nsum = ff_mul(nsum, A.sigma_ff);
+  const ff au = ff_neg(nsum);
+  m.t0 = ff_add_fast(m.t0, au);
+  m.t1 = ff_add_fast(m.t1, ff_mul_f(au, zf));
+  m.ss = ff_add_fast(m.ss, ff_mul(au, U));
+}
+
+// A batch of up to B consecutive column nodes z .. z+cnt-1 (offset `off` at z) of the mixed
+// first pass.  Every value the batch needs -- u~ at z-1 .. z+B, g and the in-plane axis
+// neighbours at the B nodes -- is loaded into registers before the arithmetic, so the batch
+// costs one memory latency; loads past the run (cnt < B) repeat its last valid node and their
+// nodes are not summed.
+template <int D, bool CUBIC, int B>
+__device__ __forceinline__ void first_batch(const AugArgs& A, FirstMoments& m, long long off, int z, int cnt,
+                                            long long zstride, long long np) {
+  constexpr int NI = D - 1;                  // in-plane axes: x (and y in 3D); the column is the last
+  const long long io[2] = {1, np};
+  ff uz[B + 2], gv[B], um[NI > 0 ? NI : 1][B], up[NI > 0 ? NI : 1][B];
+#pragma unroll
+  for (int q = 0; q < B + 2; ++q) uz[q] = ff_load(A.u + off + (long long)(min(q, cnt + 1) - 1) * zstride);
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    const long long c = off + (long long)min(q, cnt - 1) * zstride;
+    gv[q] = ff_load(A.g + c);
+#pragma unroll
+    for (int ax = 0; ax < NI; ++ax) {
+      um[ax][q] = ff_load(A.u + c - io[ax]);
+      up[ax][q] = ff_load(A.u + c + io[ax]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    if (q >= cnt) break;
+    ff nm[D], nq[D];
+#pragma unroll
+    for (int ax = 0; ax < NI; ++ax) {
+      nm[ax] = um[ax][q];
+      nq[ax] = up[ax][q];
+    }
+    nm[D - 1] = uz[q];
+    nq[D - 1] = uz[q + 2];
+    first_node<D, CUBIC>(A, m, uz[q + 1], gv[q], nm, nq, z + q);
+  }
+}
+
+// The mixed first pass over the column nodes z0..z1 (offset `off` at z0), in register batches
+// of B nodes (B smaller in 3D, whose nodes have two more in-plane neighbours to hold).
+template <int D, bool CUBIC>
+__device__ __forceinline__ void first_pass_segment(const AugArgs& A, long long off, int z0, int z1,
+                                                   long long zstride, FirstMoments& m) {
+  constexpr int B = D == 2 ? 8 : 4;
+  const long long np = A.n + 1;
+  m.q0 = m.q1 = m.sa = m.t0 = m.t1 = m.ss = ff{0.f, 0.f};
+  m.d0 = m.d1 = m.d2 = m.e0 = m.e1 = m.js = 0.f;
+  for (int z = z0; z <= z1; z += B, off += B * zstride)
+    first_batch<D, CUBIC, B>(A, m, off, z, min(B, z1 - z + 1), zstride, np);
+}
+
 // The fine pass of one block: columns of its cell, chunk by chunk.  `acc` holds the
 // per-thread channel rows ([NVAL][NT] doubles), zero on entry.
 template <int D, bool JF32>
@@ -706,7 +804,7 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
           if (phase == kUpdate) {
             const ff un = ff_add_f(ut, dl);
             if (A.out_f64)
-              A.u[o] = ff_to_double(un);
+              A.u[o] = ff_to_double_rn(un);
             else
               ff_store(A.u + o, un);
             return;
@@ -719,16 +817,20 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
           q1 = fmaf(dF, zf, q1);
           sa = fmaf(dF, utf, sa);
         };
-        int z = z0;
-        // eight independent loads in flight before the arithmetic
-        for (; z + 7 <= z1; z += 8, off += 8 * zstride) {
-          ff v[8];
+        // sixteen independent loads in flight before the arithmetic, one memory latency per
+        // batch; loads past the run repeat its last node and are not processed
+        constexpr int BU = 16;
+        for (int z = z0; z <= z1; z += BU, off += BU * zstride) {
+          const int cnt = min(BU, z1 - z + 1);
+          ff v[BU];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = ff_load(A.u + off + q * zstride);
+          for (int q = 0; q < BU; ++q) v[q] = ff_load(A.u + off + (long long)min(q, cnt - 1) * zstride);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) node(v[q], (float)(z + q), off + q * zstride);
+          for (int q = 0; q < BU; ++q) {
+            if (q >= cnt) break;
+            node(v[q], (float)(z + q), off + q * zstride);
+          }
         }
-        for (; z <= z1; ++z, off += zstride) node(ff_load(A.u + off), (float)z, off);
         Q0 = q0;
         Q1 = q1;
         SAv = sa;
@@ -736,60 +838,23 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         // mixed path, first pass: u~ and g are float-float, and f(u~) - g, A_k u~ and the
         // residual and t/s moments are formed in float-float (FP32 error-free transformations,
         // no FP64 arithmetic per node); the Jacobian moments in FP32 from the leading parts
-        const float a32 = (float)A.a;
-        const long long pl = np * np;
-        ff q0{0.f, 0.f}, q1{0.f, 0.f}, sa{0.f, 0.f}, t0{0.f, 0.f}, t1{0.f, 0.f}, ss{0.f, 0.f};
-        float d0 = 0.f, d1 = 0.f, d2 = 0.f, e0 = 0.f, e1 = 0.f, js = 0.f;
-        for (int z = z0; z <= z1; ++z, off += zstride) {
-          if (((z - z0) & 7) == 0) {
-            // touch the next eight column entries of u~ (their cache lines hold the x
-            // neighbours too) and of g, so that their loads are in flight together
-#pragma unroll
-            for (int q = 1; q <= 8; ++q)
-              if (z + q <= z1 + 1) {
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.u + off + q * zstride));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(A.g + off + q * zstride));
-              }
-          }
-          const ff U = ff_load(A.u + off);
-          // f(u~) - g enters the sums only: an add whose error is bounded relative to |f| + |g|
-          // (as for an FP64 subtraction) suffices
-          const ff Fm = ff_add_fast(f_ff(A.kind, A.a_ff, A.a, U), ff_neg(ff_load(A.g + off)));
-          const float zf = (float)z;
-          q0 = ff_add_fast(q0, Fm);
-          q1 = ff_add_fast(q1, ff_mul_f(Fm, zf));
-          sa = ff_add_fast(sa, ff_mul(Fm, U));
-          if (!A.fixed_point) {
-            float Ff, Fpf;
-            f_eval<float>(A.kind, a32, U.hi, Ff, Fpf);
-            const float dz = Fpf * zf, du = Fpf * U.hi;
-            d0 += Fpf;
-            d1 += dz;
-            d2 = fmaf(dz, zf, d2);
-            e0 += du;
-            e1 = fmaf(du, zf, e1);
-            js = fmaf(du, U.hi, js);
-          }
-          // A_k u~ = sigma (2d u - sum of axis neighbours) = -sigma * neighbour sum
-          ff nsum = neighbour_sum_ff<D>(A.u, off, np, pl);
-          if (D == 3) nsum = ff_mul(nsum, A.sigma_ff);
-          const ff au = ff_neg(nsum);
-          t0 = ff_add_fast(t0, au);
-          t1 = ff_add_fast(t1, ff_mul_f(au, zf));
-          ss = ff_add_fast(ss, ff_mul(au, U));
-        }
-        Q0 = ff_to_double(q0);
-        Q1 = ff_to_double(q1);
-        SAv = ff_to_double(sa);
-        T0 = ff_to_double(t0);
-        T1 = ff_to_double(t1);
-        SSv = ff_to_double(ss);
-        D0 = d0;
-        D1 = d1;
-        D2 = d2;
-        E0 = e0;
-        E1 = e1;
-        JSv = js;
+        FirstMoments m;
+        if (A.kind == FMG_F_CUBIC)
+          first_pass_segment<D, true>(A, off, z0, z1, zstride, m);
+        else
+          first_pass_segment<D, false>(A, off, z0, z1, zstride, m);
+        Q0 = ff_to_double_rn(m.q0);
+        Q1 = ff_to_double_rn(m.q1);
+        SAv = ff_to_double_rn(m.sa);
+        T0 = ff_to_double_rn(m.t0);
+        T1 = ff_to_double_rn(m.t1);
+        SSv = ff_to_double_rn(m.ss);
+        D0 = m.d0;
+        D1 = m.d1;
+        D2 = m.d2;
+        E0 = m.e0;
+        E1 = m.e1;
+        JSv = m.js;
       } else
       for (int z = z0; z <= z1; ++z, off += zstride, zd += 1.0) {
         if (((z - z0) & 7) == 0) {
@@ -1357,7 +1422,7 @@ __device__ void step_report(const AugArgs& A, const StepState& S, int it, bool w
 }
 
 template <int D, bool JF32>
-__global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
+__global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented(AugArgs A) {
   using G = Aug<D, JF32>;
   using FT = typename std::conditional<JF32, float, double>::type;
   extern __shared__ double sm[];
@@ -1429,7 +1494,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented(AugArgs A) {
 // many instances can run this kernel concurrently (batched solves) without the risk of two
 // partially resident cooperative grids waiting on each other.
 template <int D, bool JF32>
-__global__ void __launch_bounds__(Aug<D, JF32>::NT) k_augmented_cluster(AugArgs A) {
+__global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented_cluster(AugArgs A) {
   using G = Aug<D, JF32>;
   using FT = typename std::conditional<JF32, float, double>::type;
   namespace cg = cooperative_groups;
@@ -1556,10 +1621,12 @@ void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab) {
     else
       occ_min = mixed ? aug_occupancy<3, true>(smem) : aug_occupancy<3, false>(smem);
   }
-  // at most two blocks per SM: every block takes the dense Newton step, so a third one per SM
-  // adds a contending copy of it and more partial rows to gather, while the passes do not
-  // speed up (FP64 path: bound by the SM's FP64 pipe); measured 20 % slower at three
-  if (occ_min > 2) occ_min = 2;
+  // at most 16 warps per SM (two 2D blocks, four 3D ones): every block takes the dense Newton
+  // step, so more blocks per SM add contending copies of it and more partial rows to gather,
+  // while the passes do not speed up (FP64 path: bound by the SM's FP64 pipe); the 2D FP64
+  // solve measured 20 % slower at three blocks (24 warps) than at two
+  const int nt = dim == 2 ? Aug<2, false>::NT : Aug<3, false>::NT;
+  if (occ_min > 512 / nt) occ_min = 512 / nt;
   int bpc = sms > 0 ? (occ_min * sms) / ncell : 1;
   if (bpc < 0) bpc = 0;
   ab->bpc = bpc;
