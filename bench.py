@@ -7,8 +7,8 @@ refinements (2049 x 2049 nodes, 4,190,209 fine DOFs), u* = 8 seeded sin modes
 
 One step = one fmg_solve of that problem (level-1 Newton, every level's prolongation,
 linearized right-hand side, V-cycles, augmented-space Newton and update) with the inputs
-resident in HBM.  `value` is fine DOFs/s of the mixed-precision path (FP32 cycles inside
-FP64 defect correction); the FP64 path is timed beside it ("fp64").  By default each path
+resident in HBM.  `value` is fine DOFs/s of the mixed-precision path (FP32 cycles inside a
+float-float defect correction); the FP64 path is timed beside it ("fp64").  By default each path
 uses its faster smoother at equal accuracy (mixed: Chebyshev-Jacobi with autotuned launch
 shapes; FP64: red-black Gauss-Seidel).  L2 is flushed between steps (a 512 MB write outside
 the timed events).
@@ -40,6 +40,30 @@ TRAFFIC = {("pre_top", 2): 16_792_064 + 6_912,
 WORKLOAD = "2D unit square P1, H=1/8, 8 refinements (2049x2049 nodes, 4,190,209 fine DOFs), u^3, 8 sin modes"
 WORKLOAD_3D = ("3D unit cube P1 on Kuhn tetrahedra, H=1/4, 6 refinements (257^3 nodes, 16,581,375 fine DOFs), "
                "exp(u)-1, 8 sin modes with U[0,1] amplitudes")
+
+
+def solve_bytes_per_dof(dim: int, mixed: bool, m: int, smoother: str, nu=(2, 2), newton_passes: int = 3) -> float:
+    """Compulsory HBM bytes per fine DOF of one FMG solve (Algorithm 3.2, p = 1), every pass
+    streaming its arrays once.  A correction step on a level costs, per node: the right-hand
+    side w (g - f(u)) of eq. (3.4) (24 B), m V-cycles, the augmented precompute (16 B),
+    `newton_passes` Newton passes (8 B each) and the update (16 B).  A V-cycle costs, per node of
+    its top level, its smoothing steps (red-black sweep 24 B in FP64 / 12 B in FP32; Chebyshev
+    step 40 / 20 B), a residual + restriction and a prolongation + correction (16 + 8/2^d B each
+    in FP64, half that in FP32), times the level sum 2^d / (2^d - 1); the mixed path adds its
+    defect correction around each cycle (residual 20 B, update 20 B).  The FMG schedule
+    multiplies a step by the same level sum."""
+    ratio = 2 ** dim / (2 ** dim - 1)
+    if mixed:
+        sweep = 20.0 if smoother == "chebyshev" else 12.0
+        transfer = 8 + 4 / 2 ** dim
+        outer = 40.0
+    else:
+        sweep = 40.0 if smoother == "chebyshev" else 24.0
+        transfer = 16 + 8 / 2 ** dim
+        outer = 0.0
+    cycle = outer + ((nu[0] + nu[1]) * sweep + 2 * transfer) * ratio
+    step = 24 + m * cycle + 16 + newton_passes * 8 + 16
+    return step * ratio
 
 
 def parse():
@@ -424,6 +448,17 @@ def run_ours(args):
     if rank == 0:
         mix = results["mixed"]["mean_ms"]
         f64 = results["fp64"]["mean_ms"]
+        # the whole solve against the HBM roofline: compulsory bytes of the method as run (its
+        # smoother, m, nu = 2/2, three Newton passes per step) over the measured solve time
+        solve_hbm = {"unit": "GB/s", "peak": hbm_peak, "peak_source": peak_kind,
+                     "model": "compulsory bytes per fine DOF: per correction step 24 (rhs) + m V-cycles + 16 "
+                              "(precompute) + 3 x 8 (Newton passes) + 16 (update), cycles and steps summed "
+                              "over levels (x 2^d/(2^d-1)); each pass streams its arrays once"}
+        for prec, ms in (("mixed", mix), ("fp64", f64)):
+            bpd = solve_bytes_per_dof(dim, prec == "mixed", m_cycles[prec], smoother[prec])
+            achieved = bpd * dofs / (ms * 1e-3) / 1e9
+            solve_hbm[prec] = {"bytes_per_dof": bpd, "achieved": achieved, "frac": achieved / hbm_peak,
+                               "ceiling_dofs_per_s": hbm_peak * 1e9 / bpd}
         line = {
             "metric": METRIC,
             "value": world * dofs / (mix * 1e-3),
@@ -453,6 +488,7 @@ def run_ours(args):
                          "flags": int(results["mixed"]["stats"].flags)},
             "roofline": roofline,
             "roofline_other": other,
+            "solve_hbm": solve_hbm,
             "cpu_baseline": cpu,
             "e2e": {"value": world * dofs / (e2e_mean * 1e-3), "unit": "DOF/s", "ms_per_step": e2e_mean,
                     "h2d_bytes_per_step": int(g.nbytes), "d2h_bytes_per_step": int(g.nbytes),
