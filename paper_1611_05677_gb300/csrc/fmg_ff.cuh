@@ -24,32 +24,32 @@ struct ff {
 };
 
 // s + e = a + b exactly (s = fl(a + b)).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
 
 // s + e = a + b exactly when |a| >= |b| or a = 0.
-__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
+__host__ __device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   e = b - (s - a);
 }
 
 // p + e = a * b exactly (p = fl(a * b)), with one fused multiply-add.
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+__host__ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
   p = a * b;
   e = fmaf(a, b, -p);
 }
 
-__device__ __forceinline__ ff ff_make(float hi, float lo) {
+__host__ __device__ __forceinline__ ff ff_make(float hi, float lo) {
   ff r;
   quick_two_sum(hi, lo, r.hi, r.lo);
   return r;
 }
 
 // x + y, accurate also under cancellation (both parts through TwoSum).
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
+__host__ __device__ __forceinline__ ff ff_add(ff x, ff y) {
   float s, e, t, f;
   two_sum(x.hi, y.hi, s, e);
   two_sum(x.lo, y.lo, t, f);
@@ -63,7 +63,7 @@ __device__ __forceinline__ ff ff_add(ff x, ff y) {
 
 // x + y for accumulating sums: the lo parts are added without their own TwoSum, so the error
 // is bounded relative to |x| + |y| (as for an FP64 add) rather than to |x + y|.
-__device__ __forceinline__ ff ff_add_fast(ff x, ff y) {
+__host__ __device__ __forceinline__ ff ff_add_fast(ff x, ff y) {
   float s, e;
   two_sum(x.hi, y.hi, s, e);
   e += x.lo + y.lo;
@@ -72,11 +72,11 @@ __device__ __forceinline__ ff ff_add_fast(ff x, ff y) {
   return r;
 }
 
-__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
-__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+__host__ __device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+__host__ __device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
 
 // x + b for an FP32 b.
-__device__ __forceinline__ ff ff_add_f(ff x, float b) {
+__host__ __device__ __forceinline__ ff ff_add_f(ff x, float b) {
   float s, e;
   two_sum(x.hi, b, s, e);
   e += x.lo;
@@ -86,7 +86,7 @@ __device__ __forceinline__ ff ff_add_f(ff x, float b) {
 }
 
 // x * y (the lo * lo term, below the format's precision, is dropped).
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+__host__ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
   float p, e;
   two_prod(x.hi, y.hi, p, e);
   e = fmaf(x.hi, y.lo, e);
@@ -97,7 +97,7 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
 }
 
 // x * b for an FP32 b.
-__device__ __forceinline__ ff ff_mul_f(ff x, float b) {
+__host__ __device__ __forceinline__ ff ff_mul_f(ff x, float b) {
   float p, e;
   two_prod(x.hi, b, p, e);
   e = fmaf(x.lo, b, e);
@@ -204,7 +204,7 @@ __device__ __forceinline__ void ff_store(double* p, ff x) { *reinterpret_cast<fl
 // values um[ax] (at -1 along axis ax) and up[ax] (at +1): the hi differences and their sum
 // through TwoSum (exact), the lo parts and the rounding terms added after.
 template <int D>
-__device__ __forceinline__ ff neighbour_sum_ff_v(ff uc, const ff* um, const ff* up) {
+__host__ __device__ __forceinline__ ff neighbour_sum_ff_v(ff uc, const ff* um, const ff* up) {
   float s = 0.f, lo = 0.f;
 #pragma unroll
   for (int ax = 0; ax < D; ++ax) {

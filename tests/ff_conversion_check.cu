@@ -1,8 +1,14 @@
-// Host-side check of the float-float helpers of the mixed path (compiled as host code):
+// Host-side check of the float-float helpers of the mixed path (compiled as host code).
 // ff_to_double_rn, the integer conversion of a float-float pair to FP64, must give the bits of
-// the FP64 addition hi + lo (round to nearest, ties to even) for every normalized pair, and
-// ff_from_double / ff_add must be error-free where the transformations they use are.
-// Prints the number of pairs checked and of mismatches; exits non-zero on a mismatch.
+// the FP64 addition hi + lo (round to nearest, ties to even) for every normalized pair.  The
+// error-free transformations must be exact: two_sum gives s + e = a + b and two_prod gives
+// p + e = a b, checked in FP64 where these sums are exact.  The float-float operations must stay
+// within their error bounds, checked against quad-precision sums of the float parts (113 bits hold every sum here exactly): ff_add
+// within 2^-44 |x + y| (also under cancellation), ff_add_fast within 2^-44 (|x| + |y|), ff_mul
+// within 2^-44 |x y|, and the stencil neighbour sum within 2^-42 of its largest input.
+// Prints the number of conversion pairs checked and the number of failed checks; exits
+// non-zero on a failure.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -12,6 +18,14 @@
 #include "fmg_ff.cuh"
 
 using fmg::ff;
+// quad precision, the exact reference of the float-float bounds: IEEE binary128 is long double
+// on AArch64 and GCC's __float128 on x86-64
+#if defined(__aarch64__)
+typedef long double Q;
+#else
+typedef __float128 Q;
+#endif
+static Q qabs(Q x) { return x < 0 ? -x : x; }
 
 static ff two_sum_pair(float a, float b) {
   const float s = a + b, bb = s - a;
@@ -52,6 +66,45 @@ int main(int argc, char** argv) {
     check(two_sum_pair(std::ldexp(1.0f, k) * (Bit(rng) ? 1.f : -1.f), std::ldexp(1.0f, k - 24 - Gap(rng) / 8) * (float)U(rng)));
     // hi with an all-ones significand and lo = +-ulp(hi)/2 (the round-half and carry cases)
     check(two_sum_pair(std::nextafter(std::ldexp(1.0f, k + 1), 0.f), std::ldexp(1.0f, k - 24) * (Bit(rng) ? 1.f : -1.f)));
+  }
+  // error-free transformations and float-float error bounds (moderate exponents: no underflow)
+  std::uniform_int_distribution<int> Em(-20, 20), Small(0, 28);
+  auto rf = [&](int e) { return (float)std::ldexp(U(rng), e); };
+  auto rff = [&](int e) { return fmg::ff_from_double(std::ldexp(U(rng), e)); };
+  auto ld = [](ff x) { return (Q)x.hi + (Q)x.lo; };
+  auto fail = [&](const char* what, double err, double bound) {
+    if (bad < 5) printf("%s: error %g above %g\n", what, err, bound);
+    ++bad;
+  };
+  const double u44 = std::ldexp(1.0, -44), u42 = std::ldexp(1.0, -42);
+  for (long long i = 0; i < rounds; ++i) {
+    const int e = Em(rng);
+    const float a = rf(e), b = rf(e - Small(rng));
+    float s, t;
+    fmg::two_sum(a, b, s, t);
+    if (s != a + b || (double)s + (double)t != (double)a + (double)b) fail("two_sum", std::fabs((double)s + t - ((double)a + b)), 0);
+    fmg::two_prod(a, b, s, t);
+    if (s != a * b || (double)s + (double)t != (double)a * (double)b) fail("two_prod", std::fabs((double)s + t - (double)a * b), 0);
+    const ff x = rff(e), y = Bit(rng) ? rff(e - Small(rng)) : ff{-x.hi, -x.lo * (float)U(rng)};   // cancellation too
+    const Q xs = ld(x), ys = ld(y);
+    const Q sum = xs + ys;
+    const double e_add = (double)qabs(ld(fmg::ff_add(x, y)) - sum);
+    if (e_add > u44 * (double)qabs(sum) && e_add > 0) fail("ff_add", e_add, u44 * (double)qabs(sum));
+    const double e_fast = (double)qabs(ld(fmg::ff_add_fast(x, y)) - sum);
+    if (e_fast > u44 * (double)(qabs(xs) + qabs(ys))) fail("ff_add_fast", e_fast, u44 * (double)(qabs(xs) + qabs(ys)));
+    const double e_mul = (double)qabs(ld(fmg::ff_mul(x, y)) - xs * ys);
+    if (e_mul > u44 * (double)qabs(xs * ys)) fail("ff_mul", e_mul, u44 * (double)qabs(xs * ys));
+    // sum over the 2d axis neighbours of (u_k - u_c), values of one magnitude as on a smooth grid
+    ff uc = rff(0), um[3], up[3];
+    Q exact = 0, big = qabs(ld(uc));
+    for (int ax = 0; ax < 3; ++ax) {
+      um[ax] = fmg::ff_from_double((double)ld(uc) + std::ldexp(U(rng), -Small(rng)));
+      up[ax] = fmg::ff_from_double((double)ld(uc) + std::ldexp(U(rng), -Small(rng)));
+      exact += (ld(um[ax]) - ld(uc)) + (ld(up[ax]) - ld(uc));
+      big = std::max(big, std::max(qabs(ld(um[ax])), qabs(ld(up[ax]))));
+    }
+    const double e_nb = (double)qabs(ld(fmg::neighbour_sum_ff_v<3>(uc, um, up)) - exact);
+    if (e_nb > u42 * (double)big) fail("neighbour_sum_ff_v", e_nb, u42 * (double)big);
   }
   const float sp[] = {0.f, -0.f, 1e-40f, -1e-40f, INFINITY, -INFINITY, NAN, 1.f, -1.f, 3.4e38f, 1.2e-38f};
   for (float a : sp)

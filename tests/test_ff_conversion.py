@@ -1,8 +1,12 @@
-"""The mixed path's float-float helpers, checked on the host: the integer conversion of a
-float-float pair to FP64 (which the augmented kernel uses for its FP64 result and moments) must
-give the bits of the FP64 addition hi + lo, round to nearest even, on random pairs over a wide
-range of exponent gaps and on the borrow, carry, tie and special cases.  The helpers are
-host/device inline functions, so the check compiles them as host code."""
+"""The mixed path's float-float arithmetic, checked on the host against exact references.
+- The integer conversion of a float-float pair to FP64, used by the augmented kernel for its
+  FP64 result and moments, must give the bits of the FP64 addition hi + lo (round to nearest
+  even). Checked on random pairs over a wide range of exponent gaps and on the borrow, carry,
+  tie and special cases.
+- TwoSum and TwoProduct must be exact.
+- The float-float add, fast add and multiply, and the stencil neighbour sum must stay within
+  their error bounds, measured against quad-precision sums of the float parts.
+The helpers are host/device inline functions, so the check compiles them as host code."""
 import os
 import shutil
 import subprocess
@@ -18,7 +22,7 @@ def nvcc():
     return path if os.path.exists(path) else None
 
 
-def test_ff_to_double_rn_is_the_fp64_add(tmp_path):
+def test_float_float_helpers(tmp_path):
     cc = nvcc()
     if cc is None:
         pytest.skip("nvcc not available")
