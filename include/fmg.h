@@ -350,7 +350,8 @@ int fmg_server_poll(fmg_server* s, fmg_server_result* out, int max);
  * timeout_s seconds (FMG_ERR_TIMEOUT). */
 fmg_status fmg_server_drain(fmg_server* s, double timeout_s);
 fmg_status fmg_server_get_info(fmg_server* s, fmg_server_info* info);
-/* Message of the calling thread's last server failure. */
+/* Message of the calling thread's last server failure: a failed server call of this thread, or
+ * the latest failed request that fmg_server_poll returned to it. */
 const char* fmg_server_last_error(void);
 /* Finishes the submitted requests, stops the worker and frees every cached hierarchy. */
 fmg_status fmg_server_destroy(fmg_server* s);

@@ -57,6 +57,7 @@ struct Request {
   double* u = nullptr;
   long long t_submit = 0, t_start = 0, t_done = 0;
   fmg_status status = FMG_OK;
+  std::string err;  // what went wrong, for a failed request (handed to the polling thread)
   fmg_stats stats{};
 };
 
@@ -72,16 +73,19 @@ struct Slot {
 struct fmg_server {
   fmg_server_config cfg{};
   int device = 0;
+  // shared between the worker and callers: under mu
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
   std::deque<Request*> finished;
+  unsigned long long next_ticket = 1;
+  size_t submitted = 0, completed = 0;
+  fmg_server_info pub{};  // the worker's counters as last published
+  // the worker's own state: read and written by the worker thread only
   std::vector<Cached*> cache;
   std::vector<Slot> slots;
   size_t bytes_held = 0;
-  unsigned long long next_ticket = 1;
   int in_flight = 0;
-  size_t submitted = 0, completed = 0;
   fmg_server_info info{};
   std::atomic<bool> stop{false};
   std::thread worker;
@@ -97,10 +101,33 @@ fmg_status srv_fail(fmg_status s, const std::string& m) {
   return s;
 }
 
+// Copies the worker's counters where callers read them (fmg_server_get_info).  Worker thread,
+// with mu held.
+void publish_locked(fmg_server* sv) {
+  sv->pub.contexts_created = sv->info.contexts_created;
+  sv->pub.contexts_evicted = sv->info.contexts_evicted;
+  sv->pub.bytes_held = sv->bytes_held;
+  sv->pub.contexts_cached = (int)sv->cache.size();
+  sv->pub.in_flight = sv->in_flight;
+}
+
+void publish(fmg_server* sv) {
+  std::lock_guard<std::mutex> lk(sv->mu);
+  publish_locked(sv);
+}
+
+// Hands a finished request (its slot already released) to the callers.  Worker thread.  The
+// counters are published with it, so a caller that sees the request completed (a drain) also
+// sees the state it left.
 void finish(fmg_server* sv, Request* r) {
   r->t_done = now_ns();
   std::lock_guard<std::mutex> lk(sv->mu);
-  sv->finished.push_back(r);
+  try {
+    sv->finished.push_back(r);
+  } catch (...) {
+    delete r;  // out of host memory: the result is lost, but the request counts as finished
+  }
+  publish_locked(sv);
   ++sv->completed;
   sv->cv_done.notify_all();
 }
@@ -129,10 +156,13 @@ Cached* context_for(fmg_server* sv, Request* r, const double* g) {
   size_t need = 0;
   if (fmg_workspace_bytes(&r->p, &need) != FMG_OK) {
     r->status = FMG_ERR_INVALID;
+    r->err = std::string("invalid parameters: ") + fmg_last_error(nullptr);
     return nullptr;
   }
   if (need > sv->cfg.hbm_budget) {
     r->status = FMG_ERR_OOM;
+    r->err = "the hierarchy needs " + std::to_string(need) + " bytes, more than the server's HBM budget of " +
+             std::to_string(sv->cfg.hbm_budget);
     return nullptr;
   }
   evict_for(sv, need);
@@ -141,16 +171,31 @@ Cached* context_for(fmg_server* sv, Request* r, const double* g) {
   fmg_status s = fmg_create(&r->p, g, 0, nullptr, nullptr, 0, &ctx);
   if (s == FMG_OK) s = ctx_make_concurrent(ctx);
   if (s != FMG_OK) {
+    r->err = ctx ? ctx_error(ctx) : fmg_last_error(nullptr);
     if (ctx) fmg_destroy(ctx);
     r->status = s;
     return nullptr;
   }
-  Cached* c = new Cached();
+  Cached* c = new (std::nothrow) Cached();
+  bool stored = false;
+  if (c) {
+    try {
+      sv->cache.push_back(c);
+      stored = true;
+    } catch (...) {
+    }
+  }
+  if (!stored) {
+    delete c;
+    fmg_destroy(ctx);
+    r->status = FMG_ERR_OOM;
+    r->err = "host allocation failed";
+    return nullptr;
+  }
   c->ctx = ctx;
   c->p = r->p;
   c->bytes = ctx_bytes(ctx);
   sv->bytes_held += c->bytes;
-  sv->cache.push_back(c);
   ++sv->info.contexts_created;
   return c;
 }
@@ -163,9 +208,10 @@ void retire(fmg_server* sv) {
     Request* r = sl.req;
     if (q != cudaSuccess) {
       r->status = FMG_ERR_CUDA;
-      t_srv_err = std::string("request ") + std::to_string(r->ticket) + ": " + cudaGetErrorString(q);
+      r->err = cudaGetErrorString(q);
     } else {
       r->status = ctx_decode(sl.cc->ctx, *sl.state, &r->stats);
+      if (r->status != FMG_OK) r->err = ctx_error(sl.cc->ctx);
     }
     sl.cc->busy = false;
     sl.cc->last_used = now_ns();
@@ -211,6 +257,7 @@ bool admit(fmg_server* sv) {
     if (s == FMG_OK) e = cudaEventRecord(free_slot->done, ctx_stream(cc->ctx));
     if (s != FMG_OK || e != cudaSuccess) {
       r->status = s != FMG_OK ? s : FMG_ERR_CUDA;
+      r->err = s != FMG_OK ? std::string(ctx_error(cc->ctx)) : std::string(cudaGetErrorString(e));
       cc->busy = false;
       finish(sv, r);
       continue;
@@ -226,6 +273,7 @@ void worker_main(fmg_server* sv) {
   for (;;) {
     retire(sv);
     const bool admitted = admit(sv);
+    publish(sv);
     bool idle;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
@@ -313,6 +361,9 @@ int fmg_server_poll(fmg_server* sv, fmg_server_result* out, int max) {
     std::memset(&o, 0, sizeof(o));
     o.ticket = r->ticket;
     o.status = r->status;
+    if (r->status != FMG_OK)
+      t_srv_err = "request " + std::to_string(r->ticket) + ": " +
+                  (r->err.empty() ? "status " + std::to_string((int)r->status) : r->err);
     o.stats = r->stats;
     o.queue_ms = (r->t_start > 0 ? r->t_start - r->t_submit : r->t_done - r->t_submit) * 1e-6;
     o.latency_ms = (r->t_done - r->t_submit) * 1e-6;
@@ -333,11 +384,8 @@ fmg_status fmg_server_drain(fmg_server* sv, double timeout_s) {
 fmg_status fmg_server_get_info(fmg_server* sv, fmg_server_info* info) {
   if (!sv || !info) return srv_fail(FMG_ERR_INVALID, "NULL argument");
   std::lock_guard<std::mutex> lk(sv->mu);
-  *info = sv->info;
-  info->bytes_held = sv->bytes_held;
+  *info = sv->pub;
   info->hbm_budget = sv->cfg.hbm_budget;
-  info->contexts_cached = (int)sv->cache.size();
-  info->in_flight = sv->in_flight;
   info->queued = (int)sv->queue.size();
   info->submitted = sv->submitted;
   info->completed = sv->completed;
