@@ -759,6 +759,8 @@ fmg_status fmg_sync(fmg_ctx* c, fmg_stats* st) {
 
 fmg_status fmg_solve_batch(fmg_ctx** cs, int count, double** u_outs, fmg_stats* sts) {
   if (!cs || count < 1) return fail(nullptr, FMG_ERR_INVALID, "bad batch arguments");
+  for (int i = 0; i < count; ++i)
+    if (!cs[i]) return fail(nullptr, FMG_ERR_INVALID, "NULL context in batch");
   fmg_batch* b = nullptr;
   fmg_status s = fmg_batch_create(cs, count, cs[0]->stream, &b);
   if (s != FMG_OK) return s;

@@ -76,6 +76,17 @@ def test_null_arguments_are_rejected(lib):
     p = fmg.fmg_default_params()
     assert lib.fmg_create(ctypes.byref(p), None, 0, None, None, 0, ctypes.byref(out)) == fmg.FMG_ERR_INVALID
     assert not out.value
+    # batches: a NULL context anywhere in the list is rejected before any context is touched
+    two = (ctypes.c_void_p * 2)(None, None)
+    assert lib.fmg_solve_batch(two, 2, None, None) == fmg.FMG_ERR_INVALID
+    assert lib.fmg_solve_batch(None, 1, None, None) == fmg.FMG_ERR_INVALID
+    batch = ctypes.c_void_p()
+    assert lib.fmg_batch_create(two, 2, None, ctypes.byref(batch)) == fmg.FMG_ERR_INVALID
+    assert lib.fmg_batch_destroy(None) == fmg.FMG_OK
+    # the request server's calls reject NULL servers
+    assert lib.fmg_server_submit(None, None, None, None, None) == fmg.FMG_ERR_INVALID
+    assert lib.fmg_server_poll(None, None, 1) == 0
+    assert lib.fmg_server_destroy(None) == fmg.FMG_OK
 
 
 def test_workspace_grows_with_levels(lib):
