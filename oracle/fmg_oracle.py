@@ -24,7 +24,9 @@ assembled sparse matrices:
 * Algorithm 3.1 step 2, eq. (3.6): the semilinear problem on
   V_{H,h_k} = V_H + span{u~}, solved by Newton's method on the assembled
   (N_H+1)-dimensional Galerkin system (the nonlinear iteration is left open
-  by the paper after Theorem 3.2; Newton is one of the two it names).
+  by the paper after Theorem 3.2; Newton is one of the two it names).  The
+  fixed-point iteration, the other one it names, and the chord (simplified
+  Newton) iteration, the mixed-precision path's reading, are options.
 * Algorithm 3.2: the full multigrid schedule (exact solve on V_{h_1}, then
   p correction steps per level).
 * Brute force: Newton on the full discrete problem (2.7) with sparse direct
@@ -467,6 +469,33 @@ def augmented_newton(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarr
     raise RuntimeError("augmented Newton did not converge")
 
 
+def augmented_chord(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarray, kind: str, a: float,
+                    tol: float = 1e-6, maxit: int = 30):
+    """The chord (simplified Newton) iteration on (3.6): Newton's step with the Jacobian of the
+    first iterate, assembled and factored once.  Its fixed point is Newton's (the residual is
+    the same); only the rate differs, linear instead of quadratic.  Same start (c, alpha) =
+    (0, 1) and stopping rule as augmented_newton.  This is the reading the mixed-precision
+    GPU path takes for the nonlinear solver the paper leaves open."""
+    NH = PHk.shape[1]
+    B = sp.hstack([PHk, sp.csr_matrix(ut[:, None])]).tocsr()
+    Kaug = (B.T @ (lev.A @ B)).toarray()
+    Gaug = B.T @ G
+    y = np.zeros(NH + 1)
+    y[-1] = 1.0
+    fac = None
+    for it in range(1, maxit + 1):
+        U = B @ y
+        R = Kaug @ y + B.T @ (lev.w * f_val(kind, a, U)) - Gaug
+        if fac is None:
+            D = sp.diags(lev.w * f_der(kind, a, U))
+            fac = sla.cho_factor(Kaug + (B.T @ (D @ B)).toarray(), lower=True)
+        delta = -sla.cho_solve(fac, R)
+        y = y + delta
+        if np.max(np.abs(delta)) <= tol * max(1.0, np.max(np.abs(y))):
+            return y, B, it
+    raise RuntimeError("augmented chord iteration did not converge")
+
+
 def augmented_fixed_point(lev: Level, PHk: sp.csr_matrix, ut: np.ndarray, G: np.ndarray, kind: str, a: float,
                           tol: float = 1e-6, maxit: int = 60):
     """The fixed-point iteration on (3.6), the other nonlinear solver the paper names: the
@@ -501,7 +530,7 @@ def correction_step(hier: Hierarchy, k: int, u: np.ndarray, G: np.ndarray, kind:
     for _ in range(m):                     # eq. (3.5): m multigrid steps from u^{(l)}
         ut = vcycle(hier, k, b, ut, nu_pre, nu_post, smoother)
     # step 2 (eq. 3.6): semilinear problem on V_H + span{u~}
-    solve = augmented_fixed_point if nonlinear == "fixed_point" else augmented_newton
+    solve = {"newton": augmented_newton, "chord": augmented_chord, "fixed_point": augmented_fixed_point}[nonlinear]
     y, B, iters = solve(lev, hier.P_H[k - 1], ut, G, kind, a, tol)
     info = StepInfo(newton_iters=iters, alpha=float(y[-1]), c=y[:-1].copy(), u_tilde=ut)
     return B @ y, info

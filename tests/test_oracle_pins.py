@@ -524,3 +524,43 @@ def test_fmg_with_fixed_point_reaches_discretization_accuracy():
     assert O.discrete_l2(lev, res.u[-1] - ub) <= 0.1 * e_disc
     assert O.discrete_l2(lev, res.u[-1] - newton.u[-1]) <= 1e-3 * e_disc
     assert sum(i.newton_iters for _, i in res.steps) > sum(i.newton_iters for _, i in newton.steps)
+
+
+# ---------------------------------------------------------------------------
+# The chord iteration (the mixed path's reading of the nonlinear solver of eq. (3.6), which the
+# paper leaves open after Theorem 3.2): Newton's fixed point, reached at a linear rate
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("make", [lambda: W.config_large_2d(seed=0, refinements=5),
+                                  lambda: W.config_3d(seed=0, refinements=3)])
+def test_chord_fmg_matches_newton_fmg(make):
+    """Algorithm 3.2 with the chord iteration gives Newton's result to rounding, and takes at
+    most one more iteration per correction step."""
+    prob = make()
+    hier = O.build_hierarchy(prob.dim, prob.coarse_cells, prob.refinements)
+    g = prob.g_nodal()
+    rn = O.fmg(hier, g, prob.f, prob.a)
+    rc = O.fmg(hier, g, prob.f, prob.a, nonlinear="chord")
+    rel = np.max(np.abs(rn.u[-1] - rc.u[-1])) / np.max(np.abs(rn.u[-1]))
+    assert rel <= 1e-11
+    for (kn, sn), (kc, sc) in zip(rn.steps, rc.steps):
+        assert kn == kc and sn.newton_iters <= sc.newton_iters <= sn.newton_iters + 1
+
+
+def test_chord_is_slower_than_newton_far_from_the_solution():
+    """From a far start on a strong nonlinearity the chord step (Jacobian of the first iterate)
+    needs more iterations than Newton, and reaches the same (c, alpha)."""
+    prob = W.config_large_2d(seed=0, refinements=3)
+    hier = O.build_hierarchy(2, 8, 3)
+    k = 4
+    lev = hier.level(k)
+    G = O.load_vector(lev, prob.g_nodal())
+    a = 30.0
+    ub, _ = O.newton_full(lev, G, "cubic", a)
+    u0 = ub + 0.3 * np.random.default_rng(0).standard_normal(ub.shape)
+    un, n_info = O.correction_step(hier, k, u0, G, "cubic", a, nonlinear="newton")
+    uc, c_info = O.correction_step(hier, k, u0, G, "cubic", a, nonlinear="chord")
+    assert c_info.newton_iters > n_info.newton_iters
+    assert abs(c_info.alpha - n_info.alpha) <= 1e-7
+    assert np.max(np.abs(uc - un)) <= 1e-7 * np.max(np.abs(un))
