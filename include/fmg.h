@@ -230,8 +230,10 @@ fmg_status fmg_op_residual(fmg_ctx* c, int level, const double* b, const double*
 fmg_status fmg_op_vcycle(fmg_ctx* c, int level, const double* b, double* u, int cycles);
 
 /* One correction step u <- SemilinearMG(V_H, u, V_{h_k}) of Algorithm 3.1 at level k >= 2,
- * with the context's g (restricted to level k), m and precision.  Newton iterations and
- * alpha go to st (index k-1) when st is non-NULL. */
+ * with the context's g (restricted to level k), m and precision.  u is FP64 in and out; an
+ * FMG_PREC_MIXED context converts it to its float-float level data, takes the step as a mixed
+ * solve does (FP32 cycles, float-float residual and update, chord iteration on eq. 3.6) and
+ * converts back.  Newton iterations and alpha go to st (index k-1) when st is non-NULL. */
 fmg_status fmg_op_correction_step(fmg_ctx* c, int level, double* u, fmg_stats* st);
 
 /* Exact semilinear solve on level 1 (Algorithm 3.2 step 1) into u (level-1 layout). */
