@@ -70,11 +70,14 @@ typedef enum {
 
 typedef enum {
   FMG_PREC_FP64 = 0,   /* every step in FP64 */
-  FMG_PREC_MIXED = 1   /* multigrid cycles in FP32 inside an FP64 defect-correction loop:
-                          FP64 residual and update on the cycle's top level, FP64 coarsest
-                          solve, FP64 augmented Newton residual and its quadrature sums; the
-                          Newton Jacobian's per-node products are FP32 (summed in FP64 across
-                          threads), which changes the convergence rate, not the solution */
+  FMG_PREC_MIXED = 1   /* multigrid cycles in FP32 inside a defect correction whose level
+                          iterate, right-hand side, residual and update are float-float (an
+                          unevaluated sum of two FP32 numbers, ~48 significant bits); the
+                          augmented Newton residual and its quadrature sums are float-float per
+                          node and FP64 across nodes; the Newton Jacobians' per-node products
+                          and the small factorizations (level 1 and eq. 3.6) are FP32, with the
+                          chord iteration on eq. 3.6, which changes the convergence rate, not
+                          the solution; the result is written as FP64 */
 } fmg_precision;
 
 typedef enum {
