@@ -254,7 +254,7 @@ typedef enum {
   FMG_KT_SMOOTH_TOP = 1,  /* one red-black sweep (both colours) on the cycle's top level */
   FMG_KT_CORRECTION = 2,  /* a whole correction step (Algorithm 3.1) */
   FMG_KT_PRE_TOP = 3,     /* mixed path, 2D: fused pre-smoothing + residual + restriction, top level */
-  FMG_KT_POST_TOP = 4     /* mixed path, 2D: fused prolongation + post-smoothing + FP64 update, top level */
+  FMG_KT_POST_TOP = 4     /* mixed path, 2D: fused prolongation + post-smoothing + update of the iterate, top level */
 } fmg_kernel_kind;
 
 /* on != 0: the next fmg_solve recaptures its graph with a pair of CUDA events around every
