@@ -251,7 +251,7 @@ fmg_status fmg_op_prolong(fmg_ctx* c, int level, const double* u_coarse, double*
 
 typedef enum {
   FMG_KT_AUGMENTED = 0,   /* the augmented-space Newton kernel of a correction step (eq. 3.6) */
-  FMG_KT_SMOOTH_TOP = 1,  /* one red-black sweep (both colours) on the cycle's top level */
+  FMG_KT_SMOOTH_TOP = 1,  /* one smoothing step on the cycle's top level: a red-black sweep (both colours) or a Chebyshev step */
   FMG_KT_CORRECTION = 2,  /* a whole correction step (Algorithm 3.1) */
   FMG_KT_PRE_TOP = 3,     /* mixed path, 2D: fused pre-smoothing + residual + restriction, top level */
   FMG_KT_POST_TOP = 4     /* mixed path, 2D: fused prolongation + post-smoothing + update of the iterate, top level */
