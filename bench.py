@@ -389,7 +389,7 @@ def run_ours(args):
         # (4 B/node) and the coarse b and u (8 B per coarse node = 2 B/node)
         pre_bytes = 10.0 * nodes
         # fused post-smoothing on the top level: reads the correction and b (8 B/node), the
-        # coarse correction (1 B/node), read-modify-writes the FP64 iterate (16 B/node)
+        # coarse correction (1 B/node), read-modify-writes the iterate (8-byte slots: 16 B/node)
         post_bytes = 25.0 * nodes
         pre_gbs = pre_bytes / (pre_ms * 1e-3) / 1e9 if pre_ms > 0 else None
         post_gbs = post_bytes / (post_ms * 1e-3) / 1e9 if post_ms > 0 else None

@@ -347,7 +347,8 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
 // FP32 cycle below level j with the fused kernels: the correction starts at zero on every
 // level (the parent's restriction zeroes it; the top level's defect equation starts at zero),
 // pre-smoothing writes the level's second buffer, post-smoothing reads it back into the first
-// one -- or, on the top level, adds the result to the FP64 iterate u64.
+// one -- or, on the top level, adds the result to the iterate u64 (FP64 in the ops, float-float
+// in a mixed solve: top_ff).
 cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top, bool top_ff = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
@@ -378,7 +379,7 @@ cudaError_t vcycle32_fused(fmg_ctx* c, int j, double* u64_top, bool top_ff = fal
 
 // FP32 cycle on level j (unfused kernels).  started: Chebyshev step 0 was already taken by the
 // kernel that produced b; u64_top (top level of the mixed path): the last post-smoothing step
-// is fused with the FP64 update u64 += correction.
+// is fused with the update u64 += correction (u64 FP64, or float-float when top_ff).
 cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, double* u64_top = nullptr,
                      bool top_ff = false) {
   const int dim = c->p.dim;
@@ -415,7 +416,7 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
   const float* ec = prol_fused ? c->u32[j - 2] : nullptr;
   if (!prol_fused) TRY(launch_prolong<float, float>(dim, gc, c->u32[j - 2], gf, u, 1, s));
   if (cheb && u64_top && c->p.nu_post >= 1) {
-    // steps 0..last-1, then the last one fused with the FP64 update, reading whichever
+    // steps 0..last-1, then the last one fused with the update of u64, reading whichever
     // buffer holds the iterate
     const int last = c->p.nu_post - 1;
     float* end = nullptr;

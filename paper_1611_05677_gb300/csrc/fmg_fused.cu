@@ -5,7 +5,8 @@
 //         defect-correction loop, or a coarser level of the cycle, always starts at zero),
 //         then b_c = P^T (b - A u) and u_c = 0 on the next coarser level;
 //   post: u += P e_c, then nu black-red sweeps; on the cycle's top level the result is added
-//         to the FP64 iterate (the update of the defect correction) instead of being stored.
+//         to the iterate (the update of the defect correction; FP64 in the ops, float-float in
+//         a mixed solve) instead of being stored.
 // Each block owns a 64 x 64 tile of fine nodes and works in shared memory on the tile plus
 // a halo as wide as the sweeps' reach (2 nu, plus 2 for the residual and restriction), so
 // neighbouring tiles are independent: every sweep is computed redundantly on the part of
