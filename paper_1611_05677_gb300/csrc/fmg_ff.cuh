@@ -206,7 +206,9 @@ __device__ __forceinline__ void ff_store(double* p, ff x) { *reinterpret_cast<fl
 template <int D>
 __host__ __device__ __forceinline__ ff neighbour_sum_ff_v(ff uc, const ff* um, const ff* up) {
   float s = 0.f, lo = 0.f;
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
   for (int ax = 0; ax < D; ++ax) {
     float dm, em, dp, ep, t, et;
     two_sum(um[ax].hi, -uc.hi, dm, em);
