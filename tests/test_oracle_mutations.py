@@ -109,3 +109,45 @@ def test_wrong_chebyshev_coefficient_is_caught(monkeypatch):
     u = e0.copy()
     O.chebyshev_smooth(lev, np.zeros_like(e0), u, 3)
     assert np.max(np.abs(u - p * e0)) > 1e-3 * np.max(np.abs(e0))
+
+
+def _far_start_iterations(a=30.0):
+    prob = W.config_large_2d(seed=0, refinements=3)
+    hier = O.build_hierarchy(2, 8, 3)
+    k = 4
+    lev = hier.level(k)
+    G = O.load_vector(lev, prob.g_nodal())
+    ub, _ = O.newton_full(lev, G, "cubic", a)
+    u0 = ub + 0.3 * np.random.default_rng(0).standard_normal(ub.shape)
+    _, n_info = O.correction_step(hier, k, u0, G, "cubic", a, nonlinear="newton")
+    _, c_info = O.correction_step(hier, k, u0, G, "cubic", a, nonlinear="chord")
+    return n_info.newton_iters, c_info.newton_iters
+
+
+def test_chord_that_refactors_every_step_is_caught(monkeypatch):
+    """A 'chord' step that assembles the Jacobian at every iterate is Newton: the far-start pin
+    (chord strictly slower than Newton) no longer holds."""
+    n, c = _far_start_iterations()
+    assert c > n
+    monkeypatch.setattr(O, "augmented_chord", O.augmented_newton)
+    n, c = _far_start_iterations()
+    assert c == n
+
+
+def test_chord_with_a_dropped_load_term_is_caught(monkeypatch):
+    """A chord step whose residual omits B^T G converges to another fixed point: the FMG result
+    moves far from Newton's."""
+    orig = O.augmented_chord
+
+    def bad(lev, PHk, ut, G, kind, a, tol=1e-6, maxit=30):
+        return orig(lev, PHk, ut, 0.0 * G, kind, a, tol, maxit)
+
+    prob = W.config_large_2d(seed=0, refinements=3)
+    hier = O.build_hierarchy(2, 8, 3)
+    g = prob.g_nodal()
+    good = O.fmg(hier, g, prob.f, prob.a).u[-1]
+    # unmutated: the chord result is Newton's up to the stopping rule's error (~1e-10 at this size)
+    assert np.max(np.abs(O.fmg(hier, g, prob.f, prob.a, nonlinear="chord").u[-1] - good)) <= 1e-8 * np.max(np.abs(good))
+    monkeypatch.setattr(O, "augmented_chord", bad)
+    worse = O.fmg(hier, g, prob.f, prob.a, nonlinear="chord").u[-1]
+    assert np.max(np.abs(worse - good)) > 1e-3 * np.max(np.abs(good))
