@@ -281,8 +281,10 @@ int fmg_graph_kernels(const fmg_ctx* c);
  * a workspace (its own or the caller's); this call needs none.
  *
  * It runs `cycles` FP64 V(nu_pre, nu_post) cycles on A_k u = b at level `level` (1-based; the
- * mesh of level k has coarse_cells * 2^(k-1) cells per side) -- the same cycle as
- * fmg_op_vcycle on an FMG_PREC_FP64 context.  b and u are the caller's DEVICE arrays in the
+ * mesh of level k has coarse_cells * 2^(k-1) cells per side), always with red-black
+ * Gauss-Seidel smoothing (nu_pre / nu_post are numbers of red-black sweeps) -- the same cycle
+ * as fmg_op_vcycle on an FMG_PREC_FP64 context with FMG_SMOOTHER_RBGS (a Chebyshev context's
+ * fmg_op_vcycle smooths differently).  b and u are the caller's DEVICE arrays in the
  * level-k nodal layout ((n+1)^d doubles, boundary entries zero); u holds the initial guess
  * and receives the result.  All coarser levels and the dense level-1 inverse live in one
  * file-scope device array of FMG_VCYCLE_NOALLOC_MAX_BYTES bytes, which every GPU that loads
@@ -292,7 +294,10 @@ int fmg_graph_kernels(const fmg_ctx* c);
  *
  * The first call on a device, with that device current, looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture on the device.  The
- * first call for a (dim, coarse_cells) pair also computes A_1^{-1} into the array.  Every
+ * first call for a (dim, coarse_cells) pair also computes A_1^{-1} into the array.  Both are
+ * kept per device index for the life of the process, so the call supports only the device's
+ * primary context (the one the CUDA runtime and PyTorch use): after cudaDeviceReset, or from a
+ * context created with the driver API, the kept address would not be valid.  Every
  * call shares the array, which keeps the last call's contents; the call clears the parts that
  * must start at zero itself.  Calls that overlap on the GPU (on different streams, or from
  * different threads on one device) race on the array and give wrong results.  The call only

@@ -294,12 +294,39 @@ def fmg_graph_kernels(ctx) -> int:
 
 
 def fmg_vcycle_noalloc(dim, coarse_cells, level, b, u, cycles=1, nu_pre=2, nu_post=2, stream=None):
-    """V-cycles with no device allocation (scratch in a fixed device array of the library);
-    queues work on `stream` (a torch.cuda.Stream, a raw handle, or None for the default
-    stream) and returns without waiting."""
-    _device_sync()
-    sp = getattr(stream, "cuda_stream", stream)
-    _check(load().fmg_vcycle_noalloc(dim, coarse_cells, level, _ptr(b)[0], _ptr(u)[0], cycles, nu_pre, nu_post, sp))
+    """V-cycles with no device allocation (scratch in a fixed device array of the library).
+
+    b and u must be contiguous float64 CUDA tensors of (coarse_cells 2^(level-1) + 1)^dim
+    elements each (the level's nodal layout); anything else is rejected before the C call, so
+    that no kernel ever sees a buffer of the wrong size, type or memory space.  The work is
+    queued on `stream` (a torch.cuda.Stream, a raw cudaStream_t handle, or None for the legacy
+    default stream) after the caller's current torch stream, and the call returns without
+    waiting for the device."""
+    import torch
+
+    if dim not in (2, 3) or coarse_cells < 1 or not 1 <= level <= 23:
+        raise FMGError(FMG_ERR_INVALID, "bad dim, coarse_cells or level")
+    nodes = ((coarse_cells << (level - 1)) + 1) ** dim
+    for name, x in (("b", b), ("u", u)):
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise FMGError(FMG_ERR_INVALID, f"{name} must be a contiguous float64 CUDA tensor")
+        if x.numel() != nodes:
+            raise FMGError(FMG_ERR_INVALID, f"{name} has {x.numel()} elements; level {level} needs {nodes}")
+    if isinstance(stream, torch.cuda.Stream):
+        run_on = stream
+    elif stream is None:
+        run_on = None
+    else:
+        run_on = torch.cuda.ExternalStream(int(stream))
+    # order the caller's queued work (which produced b and u) before the cycles, by stream
+    # order rather than a device-wide synchronization
+    if run_on is not None:
+        run_on.wait_stream(torch.cuda.current_stream())
+    elif torch.cuda.current_stream().cuda_stream != 0:
+        torch.cuda.current_stream().synchronize()
+    sp = None if run_on is None else run_on.cuda_stream
+    _check(load().fmg_vcycle_noalloc(dim, coarse_cells, level, b.data_ptr(), u.data_ptr(), cycles, nu_pre, nu_post,
+                                     sp))
 
 
 def fmg_batch_create(ctxs, stream=None):

@@ -57,9 +57,25 @@ def test_noalloc_vcycle_matches_context_vcycle(fmg, dim, H, level):
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(fmg):
-    # a 2D level with 2048 cells per side needs more than the fixed array holds
-    u = torch.zeros(4, dtype=torch.float64, device="cuda")
+    # a 2D level with 2048 cells per side needs more than the fixed array holds; the buffers
+    # have that level's full size, so even a check that let the call through would launch on
+    # arrays of the right extent
+    b = torch.zeros((2049, 2049), dtype=torch.float64, device="cuda")
+    u = torch.zeros((2049, 2049), dtype=torch.float64, device="cuda")
     with pytest.raises(fmg.FMGError) as ei:
-        fmg.fmg_vcycle_noalloc(2, 4, 10, u, u, cycles=1)
+        fmg.fmg_vcycle_noalloc(2, 4, 10, b, u, cycles=1)
     assert ei.value.status == fmg.FMG_ERR_INVALID
     assert "at most" in fmg.fmg_last_error()
+    assert float(u.abs().max()) == 0.0
+
+
+def test_noalloc_wrapper_rejects_wrong_buffers(fmg):
+    # wrong element count, FP32 and host arrays never reach the C entry point
+    n = 4 << 4
+    good = torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda")
+    for bad in (torch.zeros(16, dtype=torch.float64, device="cuda"),
+                torch.zeros((n + 1, n + 1), dtype=torch.float32, device="cuda"),
+                torch.zeros((n + 1, n + 1), dtype=torch.float64)):
+        with pytest.raises(fmg.FMGError) as ei:
+            fmg.fmg_vcycle_noalloc(2, 4, 5, good, bad, cycles=1)
+        assert ei.value.status == fmg.FMG_ERR_INVALID
