@@ -171,11 +171,18 @@ def config_large_2d(seed: int = 0, refinements: int = 8) -> Problem:
                    name=f"2d_H8_r{refinements}_cubic_8modes_seed{seed}")
 
 
+# Multigrid cycles per correction step on the cube.  With m = 2 the algebraic error of the 3D
+# full multigrid solve grows past a tenth of the discretization error from 3 refinements on
+# (0.10 at 3 refinements and rising per level), with m = 3 it stays near 0.03 (red-black
+# Gauss-Seidel); Theorem 3.2 only bounds it, so m is raised for every 3D workload.
+M_VCYCLES_3D = 3
+
+
 def config_3d(seed: int = 0, refinements: int = 6) -> Problem:
     """3D Kuhn, H=1/4, 6 refinements (257^3 nodes), exp(u)-1, 8 seeded modes, amplitudes U[0,1]."""
     rng = np.random.default_rng(seed)
     return Problem(dim=3, coarse_cells=4, refinements=refinements, f="expm1", a=1.0,
-                   modes=_draw_modes(rng, 3, 4, 8, "uniform"),
+                   modes=_draw_modes(rng, 3, 4, 8, "uniform"), m_vcycles=M_VCYCLES_3D,
                    name=f"3d_H4_r{refinements}_expm1_8modes_seed{seed}")
 
 
@@ -212,5 +219,5 @@ def request_stream(seed: int = 0, count: int = 2200, rate: float = 200.0,
         f = "cubic" if rng.uniform() < 0.5 else "expm1"
         gm = _draw_modes(rng, dim, 6 if is2d else 4, 8, "normal")
         out.append((t, Problem(dim=dim, coarse_cells=4, refinements=r, f=f, a=1.0, g_modes=gm,
-                               name=f"req{i}_{dim}d_r{r}_{f}")))
+                               m_vcycles=2 if is2d else M_VCYCLES_3D, name=f"req{i}_{dim}d_r{r}_{f}")))
     return out

@@ -333,16 +333,28 @@ def test_fmg_optimal_orders_small_2d():
     assert all(abs(r - 1.0) < 0.1 for r in rh1[1:]), rh1
 
 
-@pytest.mark.parametrize("dim,H,r,kind", [(2, 4, 4, "cubic"), (2, 8, 3, "cubic"), (3, 4, 2, "expm1")])
-def test_fmg_reaches_discretization_accuracy(dim, H, r, kind):
+def _two_mode_problem(dim, H, r, kind):
+    return W.Problem(dim=dim, coarse_cells=H, refinements=r, f=kind, a=1.0,
+                     modes=[((1,) * dim, 1.0), ((2, 1, 3)[:dim], 0.5)])
+
+
+@pytest.mark.parametrize("make,m", [
+    (lambda: _two_mode_problem(2, 4, 4, "cubic"), 2),
+    (lambda: _two_mode_problem(2, 8, 3, "cubic"), 2),
+    (lambda: _two_mode_problem(3, 4, 2, "expm1"), 2),
+    (lambda: _two_mode_problem(3, 4, 3, "expm1"), 3),
+    (lambda: W.config_3d(seed=0, refinements=3), 3),
+])
+def test_fmg_reaches_discretization_accuracy(make, m):
     """Theorem 3.2: ||u_bar_h - u_h|| stays a fraction of the discretization
     error; read as algebraic error <= 0.1 x discretization error (discrete L2)
-    at every level."""
-    prob = W.Problem(dim=dim, coarse_cells=H, refinements=r, f=kind, a=1.0,
-                     modes=[((1,) * dim, 1.0), ((2, 1, 3)[:dim], 0.5)])
-    hier = O.build_hierarchy(dim, H, r)
+    at every level.  On the cube the bar needs m = 3 cycles per step from 3
+    refinements on (the 3D workloads' setting)."""
+    prob = make()
+    dim, r = prob.dim, prob.refinements
+    hier = O.build_hierarchy(dim, prob.coarse_cells, r)
     g = prob.g_nodal()
-    res = O.fmg(hier, g, prob.f, prob.a)
+    res = O.fmg(hier, g, prob.f, prob.a, m=m)
     for k in range(2, r + 2):
         lev = hier.level(k)
         G = O.load_vector(lev, O.restrict_nodal(g, dim, prob.n_fine, lev.n))
@@ -350,6 +362,44 @@ def test_fmg_reaches_discretization_accuracy(dim, H, r, kind):
         e_alg = O.discrete_l2(lev, res.u[k - 1] - ub)
         e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star(lev.n)))
         assert e_alg <= 0.1 * e_disc, (k, e_alg, e_disc)
+
+
+def test_3d_with_two_cycles_misses_the_accuracy_bar():
+    """The reason the 3D workloads take m = 3: with the paper's m = 2 the algebraic error on
+    the cube passes a tenth of the discretization error at 3 refinements."""
+    prob = W.config_3d(seed=0, refinements=3)
+    hier = O.build_hierarchy(3, 4, 3)
+    g = prob.g_nodal()
+    res = O.fmg(hier, g, prob.f, prob.a, m=2)
+    lev = hier.level(4)
+    G = O.load_vector(lev, g)
+    ub, _ = O.newton_full(lev, G, prob.f, prob.a, U0=res.u[-1])
+    e_alg = O.discrete_l2(lev, res.u[-1] - ub)
+    e_disc = O.discrete_l2(lev, ub - O.from_nodal(lev, prob.u_star()))
+    assert e_alg > 0.1 * e_disc
+    assert W.M_VCYCLES_3D == 3 and prob.m_vcycles == 3
+
+
+@pytest.mark.parametrize("make,m", [
+    (W.config_small_2d, 2),
+    (lambda: W.config_large_2d(seed=0, refinements=4), 2),
+    (lambda: _two_mode_problem(3, 4, 3, "expm1"), 2),
+    (lambda: W.config_3d(seed=0, refinements=3), 3),
+])
+def test_newton_stopping_rule_gives_the_tight_tolerance_result(make, m):
+    """The reading of the stopping rule the paper leaves open (Newton on eq. 3.6 and on level 1
+    stops after the update whose increment is <= 1e-6 max(1, ||y||)): Newton's quadratic
+    convergence leaves an error of order 1e-12 after that update, so the full multigrid
+    result is the one a 1e-13 tolerance gives, to 1e-11 relative in the max norm."""
+    prob = make()
+    hier = O.build_hierarchy(prob.dim, prob.coarse_cells, prob.refinements)
+    g = prob.g_nodal()
+    loose = O.fmg(hier, g, prob.f, prob.a, m=m)
+    tight = O.fmg(hier, g, prob.f, prob.a, m=m, tol=1e-13, tol_level1=1e-13)
+    a, b = loose.u[-1], tight.u[-1]
+    assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(b))
+    # the tight rule takes at least as many iterations on every level
+    assert all(sb.newton_iters >= sa.newton_iters for (_, sa), (_, sb) in zip(loose.steps, tight.steps))
 
 
 def test_level_one_is_exact():
