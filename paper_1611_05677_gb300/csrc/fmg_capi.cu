@@ -177,6 +177,7 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
   aug_configure(p->dim, p->coarse_cells, p->precision == FMG_PREC_MIXED, &cfg);
   const size_t items = cfg.partial_items;
   double* partials = (double*)take(2 * items * aug_nvals(p->dim) * 8);
+  double* cfin = (double*)take((ipow(p->coarse_cells + 1, p->dim) + 1) * 8);
   if (c && base) {
     c->Ainv = Ainv;
     c->Ainv32 = Ainv32;
@@ -184,6 +185,7 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
     c->ab = cfg;
     c->ab.partials = partials;
     c->ab.Ainv = Ainv;
+    c->ab.cfin = cfin;
   }
   return off;
 }
@@ -524,7 +526,7 @@ cudaError_t correction_step_ff(fmg_ctx* c, int k, bool out_f64, bool from_coarse
 cudaError_t run_fmg(fmg_ctx* c) {
   c->timed_next = 0;
   // per-solve statistics start at zero (flags, iteration counts, alphas)
-  TRY(cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  TRY(cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream));
   // the mixed path keeps its level data as float-float; its last step leaves the FP64 result
   const bool mixed = c->p.precision == FMG_PREC_MIXED;
   TRY(launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
@@ -1091,7 +1093,7 @@ fmg_status fmg_op_vcycle(fmg_ctx* c, int level, const double* b, double* u, int 
 fmg_status fmg_op_correction_step(fmg_ctx* c, int level, double* u, fmg_stats* st) {
   if (fmg_status s = check_level(c, level, 2)) return s;
   if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
-  CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream));
   c->timed_next = 0;
   if (c->p.precision == FMG_PREC_MIXED) {
     // the mixed path works on float-float level data: u in, the step, u out
@@ -1108,7 +1110,7 @@ fmg_status fmg_op_correction_step(fmg_ctx* c, int level, double* u, fmg_stats* s
 fmg_status fmg_op_level1_solve(fmg_ctx* c, double* u, fmg_stats* st) {
   if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
   if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
-  CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, bar_count), c->stream));
+  CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream));
   CK(c, launch_level1_newton(c->p.dim, c->geo[0], c->g[0], u, c->p.f, c->p.f_scale, c->p.level1_tol,
                              c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream));
   return read_state(c, st, false);

@@ -157,7 +157,7 @@ __global__ void k_ff_from_f64(const double* __restrict__ s, double* __restrict__
 
 __global__ void k_ff_to_f64(const double* __restrict__ s, double* __restrict__ d, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) d[i] = ff_to_double_rn(ff_load(s + i));
+  if (i < n) d[i] = ff_to_double_fast(ff_load(s + i));
 }
 
 }  // namespace

@@ -193,6 +193,30 @@ __host__ __device__ __forceinline__ double ff_to_double_rn(ff x) {
   return ff_double_from_bits(sign | ((unsigned long long)e << 52) | (m & 0xfffffffffffffull));
 }
 
+// The exact FP64 value of an FP32 number, built from its bits for normal numbers and zeros
+// (sign; exponent rebiased from 127 to 1023, i.e. + 896; significand moved up by 29 places), so
+// that no FP64 conversion instruction is issued; subnormal, infinite and NaN inputs take the
+// conversion.
+__host__ __device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned b = ff_bits(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if ((b & 0x7fffffffu) == 0u) return ff_double_from_bits((unsigned long long)(b >> 31) << 63);
+  if (e == 0u || e == 255u) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  const unsigned lo = b << 29;
+#ifdef __CUDA_ARCH__
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  return ff_double_from_bits(((unsigned long long)hi << 32) | lo);
+#endif
+}
+
+// hi + lo rounded to the nearest double: the two exact conversions above and one FP64 add, the
+// value ff_to_double gives with one FP64 instruction per pair instead of three.
+__host__ __device__ __forceinline__ double ff_to_double_fast(ff x) {
+  return f32_to_f64_bits(x.hi) + f32_to_f64_bits(x.lo);
+}
+
 // A float-float value stored in an 8-byte slot (the layout of the double arrays it replaces).
 __device__ __forceinline__ ff ff_load(const double* p) {
   const float2 v = *reinterpret_cast<const float2*>(p);

@@ -213,6 +213,8 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
 struct AugBuffers {
   double* partials;   // two buffers of [items][nvals] (the Newton iterations alternate)
   const double* Ainv; // A_H^{-1} (level-1 inverse; kept with the buffers of the system)
+  double* cfin;       // the final coarse iterate c ((1/H + 1)^d nodal values) and alpha, for the
+                      // separate update kernel of the largest levels
   size_t partial_items;
   int bpc;            // blocks per coarse cell of the cooperative launch (all co-resident)
   int nt;             // threads per block

@@ -454,10 +454,12 @@ struct Aug {
   static constexpr int NT = D == 2 ? 256 : 128;
 };
 
-// Channel rows of a block: one row of NT per-thread partial sums per channel.  Residual
-// channels (RA .. SS) are FP64; in the mixed path the Jacobian channels (JB .. JS) are FP32
-// rows after them (FP32 products to begin with), which halves their shared memory and
-// keeps FP64 work out of their accumulation.
+// Channel rows of a block: one row of NT per-thread partial sums per channel.  FP64 path:
+// every channel FP64, already scaled by its quadrature weight.  Mixed path: the residual
+// channels (RA .. SS) are float-float pairs (hi, lo) in their 8-byte slots and carry no weight
+// (RA is scaled by w/s, SA by w, TT by 1/s when the block sum is converted to FP64), so a pass
+// does no FP64 arithmetic; the Jacobian channels (JB .. JS) are FP32 rows after them (FP32
+// products to begin with), which halves their shared memory.
 template <int D, bool JF32>
 struct Rows {
   using G = Aug<D, JF32>;
@@ -495,6 +497,7 @@ struct AugArgs {
   int dim, nc, s, n, kind, maxit, level_index, bpc, chunk;
   int fixed_point;      // 1: fixed-point iteration (Galerkin stiffness only, no Jacobian)
   int out_f64;          // mixed path: the update writes u as FP64 (the solve's result) instead of float-float
+  int split_update;     // 1: the final update is left to k_aug_update (block 0 writes c and alpha to cfin)
   double a, w, sigma_k, sigma_H, tol;
   ff a_ff, sigma_ff;    // mixed path: a and sigma_k as float-float
   double* u;            // u~ on entry, u^{(l+1)} on exit (level-k nodal; float-float in the mixed path)
@@ -503,6 +506,7 @@ struct AugArgs {
   long long pstride;    // doubles per buffer
   const double* Ainv;   // A_H^{-1} (= A_1^{-1}, h_1 = H), dense NH x NH, preconditioner
   DevState* st;
+  double* cfin;         // [(nc+1)^d] c, then alpha (split_update)
 };
 
 // Bounded grid barrier for the cooperative launch (all blocks co-resident).  On timeout the
@@ -750,6 +754,15 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
   const long long items = (long long)ncol * nch;
   const double inv_s = 1.0 / s;
   const double inv_s2 = inv_s * inv_s;
+  // the mixed path's FP32 quantities, formed once per pass: Jacobian weights, alpha - 1, a,
+  // 1/s and the coarse cell's vertex values of c
+  const float jw0 = JF32 ? (float)A.w : 0.f, jw1 = JF32 ? (float)(A.w * inv_s) : 0.f,
+              jw2 = JF32 ? (float)(A.w * inv_s2) : 0.f;
+  const float am1f = JF32 ? (float)(alpha - 1.0) : 0.f, a_f = JF32 ? (float)A.a : 0.f;
+  const float inv_sf = 1.0f / (float)s;
+  float cvf[G::NV];
+#pragma unroll
+  for (int v = 0; v < G::NV; ++v) cvf[v] = (JF32 && phase != kFirst) ? (float)cv[v] : 0.f;
   // Items (column chunks) are dealt to the cell's blocks contiguously when they fill every
   // block; on small levels they are interleaved across the blocks, so that the cell's work
   // spreads over as many SM sub-partitions as there are items (the FP64 rate of one
@@ -778,9 +791,19 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
       const int z0 = max(max(S.z0, zlo_chunk), zmin);
       const int z1 = min(S.z1, zhi_chunk);
       if (z0 > z1) continue;
-      // P c on the segment: pc0 + pc1 z
+      // P c on the segment: pc0 + pc1 z (the mixed path forms it in FP32: it is the small
+      // Newton correction, and the passes after the first work in FP32 increments)
       double pc0 = 0.0, pc1 = 0.0;
-      if (phase != kFirst) {
+      float pc0f = 0.f, pc1f = 0.f;
+      if (JF32 && phase != kFirst) {
+#pragma unroll
+        for (int t = 0; t <= D; ++t) {
+          pc0f = fmaf((float)S.P[t], cvf[S.vid[t]], pc0f);
+          pc1f = fmaf((float)S.R[t], cvf[S.vid[t]], pc1f);
+        }
+        pc0f *= inv_sf;
+        pc1f *= inv_sf;
+      } else if (phase != kFirst) {
 #pragma unroll
         for (int t = 0; t <= D; ++t) {
           pc0 += S.P[t] * cv[S.vid[t]];
@@ -792,11 +815,13 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
       double Q0 = 0.0, Q1 = 0.0, SAv = 0.0;                 // residual moments
       JT D0 = 0, D1 = 0, D2 = 0, E0 = 0, E1 = 0, JSv = 0;   // Jacobian moments
       double T0 = 0.0, T1 = 0.0, SSv = 0.0;                 // first pass
+      FirstMoments fm;                                      // mixed path, first pass
+      float cq0 = 0.f, cq1 = 0.f, csa = 0.f;                // mixed path, chord pass
       double zd = (double)z0;
       long long off = base + (long long)(zc + z0) * zstride;
       if (JF32 && phase != kFirst) {
         // mixed path: FP32 increments on top of the first pass's FP64 residual sums
-        const float pc0f = (float)pc0, pc1f = (float)pc1, am1f = (float)(alpha - 1.0), af = (float)A.a;
+        const float af = a_f;
         float q0 = 0.f, q1 = 0.f, sa = 0.f;
         auto node = [&](ff ut, float zf, long long o) {
           const float utf = ut.hi;
@@ -804,7 +829,7 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
           if (phase == kUpdate) {
             const ff un = ff_add_f(ut, dl);
             if (A.out_f64)
-              A.u[o] = ff_to_double_rn(un);
+              A.u[o] = ff_to_double_fast(un);
             else
               ff_store(A.u + o, un);
             return;
@@ -831,30 +856,23 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
             node(v[q], (float)(z + q), off + q * zstride);
           }
         }
-        Q0 = q0;
-        Q1 = q1;
-        SAv = sa;
+        cq0 = q0;
+        cq1 = q1;
+        csa = sa;
       } else if (JF32) {
         // mixed path, first pass: u~ and g are float-float, and f(u~) - g, A_k u~ and the
         // residual and t/s moments are formed in float-float (FP32 error-free transformations,
         // no FP64 arithmetic per node); the Jacobian moments in FP32 from the leading parts
-        FirstMoments m;
         if (A.kind == FMG_F_CUBIC)
-          first_pass_segment<D, true>(A, off, z0, z1, zstride, m);
+          first_pass_segment<D, true>(A, off, z0, z1, zstride, fm);
         else
-          first_pass_segment<D, false>(A, off, z0, z1, zstride, m);
-        Q0 = ff_to_double_rn(m.q0);
-        Q1 = ff_to_double_rn(m.q1);
-        SAv = ff_to_double_rn(m.sa);
-        T0 = ff_to_double_rn(m.t0);
-        T1 = ff_to_double_rn(m.t1);
-        SSv = ff_to_double_rn(m.ss);
-        D0 = m.d0;
-        D1 = m.d1;
-        D2 = m.d2;
-        E0 = m.e0;
-        E1 = m.e1;
-        JSv = m.js;
+          first_pass_segment<D, false>(A, off, z0, z1, zstride, fm);
+        D0 = fm.d0;
+        D1 = fm.d1;
+        D2 = fm.d2;
+        E0 = fm.e0;
+        E1 = fm.e1;
+        JSv = fm.js;
       } else
       for (int z = z0; z <= z1; ++z, off += zstride, zd += 1.0) {
         if (((z - z0) & 7) == 0) {
@@ -908,30 +926,47 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
       if (phase == kUpdate) continue;
       // moments -> vertex channels of this thread's row
       const double w = A.w;
-      if (JF32 && phase != kFirst) {
-        // mixed path, chord step: residual channels only, converted in FP32 (the moments
-        // are FP32 sums of increments) and added to the FP64 rows
-        const float wf = (float)(w * inv_s), q0f = (float)Q0, q1f = (float)Q1;
+      if (JF32) {
+        // mixed path: the residual (and first-pass t, s) channels are float-float rows without
+        // their weights; the chord pass's moments are FP32 sums of increments
+        float2* fr = reinterpret_cast<float2*>(acc);
+        auto add = [&](int ch, ff x) {
+          const float2 o = fr[ch * G::NT + tid];
+          const ff r = ff_add_fast(ff{o.x, o.y}, x);
+          fr[ch * G::NT + tid] = make_float2(r.hi, r.lo);
+        };
+        if (phase != kFirst) {
 #pragma unroll
-        for (int t = 0; t <= D; ++t)
-          acc[(G::RA + S.vid[t]) * G::NT + tid] += (double)(wf * fmaf((float)S.P[t], q0f, (float)S.R[t] * q1f));
-        acc[G::SA * G::NT + tid] += (double)((float)w * (float)SAv);
-        continue;
-      }
+          for (int t = 0; t <= D; ++t)
+            add(G::RA + S.vid[t], ff{fmaf((float)S.P[t], cq0, (float)S.R[t] * cq1), 0.f});
+          add(G::SA, ff{csa, 0.f});
+          continue;
+        }
 #pragma unroll
-      for (int t = 0; t <= D; ++t) {
-        const double Pt = S.P[t], Rt = S.R[t];
-        const int v = S.vid[t];
-        acc[(G::RA + v) * G::NT + tid] += w * inv_s * (Pt * Q0 + Rt * Q1);
-        if (phase == kFirst) acc[(G::TT + v) * G::NT + tid] += inv_s * (Pt * T0 + Rt * T1);
+        for (int t = 0; t <= D; ++t) {
+          const float Pt = (float)S.P[t], Rt = (float)S.R[t];
+          const int v = S.vid[t];
+          add(G::RA + v, ff_add(ff_mul_f(fm.q0, Pt), ff_mul_f(fm.q1, Rt)));
+          add(G::TT + v, ff_add(ff_mul_f(fm.t0, Pt), ff_mul_f(fm.t1, Rt)));
+        }
+        add(G::SA, fm.sa);
+        add(G::SS, fm.ss);
+      } else {
+#pragma unroll
+        for (int t = 0; t <= D; ++t) {
+          const double Pt = S.P[t], Rt = S.R[t];
+          const int v = S.vid[t];
+          acc[(G::RA + v) * G::NT + tid] += w * inv_s * (Pt * Q0 + Rt * Q1);
+          if (phase == kFirst) acc[(G::TT + v) * G::NT + tid] += inv_s * (Pt * T0 + Rt * T1);
+        }
+        acc[G::SA * G::NT + tid] += w * SAv;
+        if (phase == kFirst) acc[G::SS * G::NT + tid] += SSv;
       }
-      acc[G::SA * G::NT + tid] += w * SAv;
-      if (phase == kFirst) acc[G::SS * G::NT + tid] += SSv;
       if (A.fixed_point) continue;   // the fixed-point iteration needs no Jacobian
       if (JF32) {
         // FP32 Jacobian channels, converted in FP32 into the FP32 rows
         float* fj = Rows<D, JF32>::jac(acc);
-        const float wf = (float)(w * inv_s), wf2 = (float)(w * inv_s2);
+        const float wf = jw1, wf2 = jw2;
         const float d0 = (float)D0, d1 = (float)D1, d2 = (float)D2, e0 = (float)E0, e1 = (float)E1;
 #pragma unroll
         for (int t = 0; t <= D; ++t) {
@@ -945,7 +980,7 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
                 wf2 * fmaf(Pt * Pr, d0, fmaf(fmaf(Pt, Rr, Rt * Pr), d1, Rt * Rr * d2));
           }
         }
-        fj[(G::JS - G::JB) * G::NT + tid] += (float)w * (float)JSv;
+        fj[(G::JS - G::JB) * G::NT + tid] += jw0 * (float)JSv;
       } else {
 #pragma unroll
         for (int t = 0; t <= D; ++t) {
@@ -970,7 +1005,7 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
 // pass); in the mixed path the Jacobian channels, FP32 products to begin with, are summed in
 // FP32 -- FP64 adds issue slowly on this part.
 template <int D, bool JF32>
-__device__ void block_reduce_rows(const double* acc, double* out, bool first, bool fixed_point) {
+__device__ void block_reduce_rows(const AugArgs& A, const double* acc, double* out, bool first, bool fixed_point) {
   using G = Aug<D, JF32>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = G::NT / 32;
   __syncthreads();
@@ -984,7 +1019,26 @@ __device__ void block_reduce_rows(const double* acc, double* out, bool first, bo
       for (int t = lane; t < G::NT; t += 32) x += fj[(v - G::JB) * G::NT + t];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) out[v] = (double)x;
+      // the FP32 sum stays FP32: it is stored in the low word of the channel's 8-byte slot
+      if (lane == 0) reinterpret_cast<float*>(out + v)[0] = x;
+    } else if (JF32) {
+      // float-float rows: summed in float-float (fixed order), then weighted and converted
+      const float2* fr = reinterpret_cast<const float2*>(acc);
+      ff x{0.f, 0.f};
+      for (int t = lane; t < G::NT; t += 32) {
+        const float2 o = fr[v * G::NT + t];
+        x = ff_add_fast(x, ff{o.x, o.y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const ff y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+        x = ff_add_fast(x, y);
+      }
+      if (lane == 0) {
+        const double inv_s = 1.0 / A.s;
+        const double wgt = v < G::SA ? A.w * inv_s : v == G::SA ? A.w : v < G::SS ? inv_s : 1.0;
+        out[v] = wgt * ff_to_double(x);
+      }
     } else {
       double x = 0.0;
       for (int t = lane; t < G::NT; t += 32) x += acc[v * G::NT + t];
@@ -1133,6 +1187,411 @@ template <int D>
 __device__ void newton_update(const AugArgs& A, const double* R, int NH, const StepState& S, int dropped, bool ok,
                               bool writer);
 
+// Sum of the FP32 channel `ch` (stored in the low word of its slot) at vertex p over the cells
+// around coarse node p.
+template <int D>
+__device__ __forceinline__ float node_channel_f(const double* cellsum, int nc, const int* z, int ch) {
+  using G = Aug<D, true>;
+  float x = 0.f;
+#pragma unroll
+  for (int o = 0; o < G::NV; ++o) {
+    bool ok = true;
+    int cell = 0, mul = 1;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const int cc = z[q] - ((o >> q) & 1);
+      if (cc < 0 || cc >= nc) ok = false;
+      cell += cc * mul;
+      mul *= nc;
+    }
+    if (ok) x += reinterpret_cast<const float*>(cellsum + (long long)cell * G::NVAL + ch + o)[0];
+  }
+  return x;
+}
+
+// FP32 Jacobian pair channel of coarse nodes zp, zq summed over the cells that hold both.
+template <int D>
+__device__ __forceinline__ float pair_channel_f(const double* cellsum, int nc, const int* zp, const int* zq) {
+  using G = Aug<D, true>;
+  float x = 0.f;
+#pragma unroll
+  for (int o = 0; o < G::NV; ++o) {
+    bool ok = true;
+    int cell = 0, mul = 1, vq = 0;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const int cc = zp[q] - ((o >> q) & 1);
+      if (cc < 0 || cc >= nc) ok = false;
+      const int dq = zq[q] - cc;
+      if (dq < 0 || dq > 1) ok = false;
+      vq |= dq << q;
+      cell += cc * mul;
+      mul *= nc;
+    }
+    if (ok)
+      x += reinterpret_cast<const float*>(cellsum + (long long)cell * G::NVAL + G::JP + pair_index(G::NV, o, vq))[0];
+  }
+  return x;
+}
+
+// Largest lexicographic half-bandwidth of J_HH (aug_band) of a dimension: 2D 1/H <= 8 gives
+// 8, 3D 1/H <= 4 gives 13.
+template <int D>
+__host__ __device__ constexpr int aug_band_max() {
+  return D == 2 ? 8 : 13;
+}
+
+// Column c of J^{-1} from the band LDL^T factor of ldlt_band_warp (A in place: A[i][k] =
+// L_ik d_k below the diagonal, rd[k] = 1/d_k; band rows 0..nb-1, dense border row nb = n - 1):
+// the forward substitution L w = e_c with y = D^{-1} w kept in X's column, then the backward
+// substitution L^T x = y over the band and the border entry.  The band window of the last KB
+// values is kept in registers; every thread walks the same rows, so the factor's entries are
+// shared-memory broadcasts.
+template <int D>
+__device__ __forceinline__ void band_inverse_column(const float* __restrict__ Af, const float* __restrict__ rd, int n,
+                                                    int ld, int band, int c, float* __restrict__ X) {
+  constexpr int KB = aug_band_max<D>();
+  const int nb = n - 1;
+  // win[t] holds the value of the row t + 1 steps back (forward) or ahead (backward); the
+  // newest one (t = 0) enters each sum last, so the rest of the sum does not wait for it
+  float win[KB];
+#pragma unroll
+  for (int t = 0; t < KB; ++t) win[t] = 0.f;
+  for (int k = 0; k < nb; ++k) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int t = KB - 1; t >= 1; --t) {
+      const int j = k - 1 - t;
+      if (t < band && j >= 0) {
+        if (t & 1)
+          s1 = fmaf(Af[k * ld + j], win[t], s1);
+        else
+          s0 = fmaf(Af[k * ld + j], win[t], s0);
+      }
+    }
+    const float a0 = k >= 1 ? Af[k * ld + k - 1] : 0.f;
+    const float y = ((k == c ? 1.f : 0.f) - fmaf(a0, win[0], s0 + s1)) * rd[k];
+    X[k * ld + c] = y;
+#pragma unroll
+    for (int t = KB - 1; t > 0; --t) win[t] = win[t - 1];
+    win[0] = y;
+  }
+  {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int j = 0;
+    for (; j + 3 < nb; j += 4) {
+      s0 = fmaf(Af[nb * ld + j], X[j * ld + c], s0);
+      s1 = fmaf(Af[nb * ld + j + 1], X[(j + 1) * ld + c], s1);
+      s2 = fmaf(Af[nb * ld + j + 2], X[(j + 2) * ld + c], s2);
+      s3 = fmaf(Af[nb * ld + j + 3], X[(j + 3) * ld + c], s3);
+    }
+    for (; j < nb; ++j) s0 = fmaf(Af[nb * ld + j], X[j * ld + c], s0);
+    X[nb * ld + c] = ((nb == c ? 1.f : 0.f) - ((s0 + s1) + (s2 + s3))) * rd[nb];
+  }
+  const float xb = X[nb * ld + c];
+#pragma unroll
+  for (int t = 0; t < KB; ++t) win[t] = 0.f;
+  for (int k = nb - 1; k >= 0; --k) {
+    float s0 = Af[nb * ld + k] * xb, s1 = 0.f;
+#pragma unroll
+    for (int t = KB - 1; t >= 1; --t) {
+      const int i = k + 1 + t;
+      if (t < band && i < nb) {
+        if (t & 1)
+          s1 = fmaf(Af[i * ld + k], win[t], s1);
+        else
+          s0 = fmaf(Af[i * ld + k], win[t], s0);
+      }
+    }
+    const float a0 = k + 1 < nb ? Af[(k + 1) * ld + k] : 0.f;
+    const float x = X[k * ld + c] - rd[k] * fmaf(a0, win[0], s0 + s1);
+    X[k * ld + c] = x;
+#pragma unroll
+    for (int t = KB - 1; t > 0; --t) win[t] = win[t - 1];
+    win[0] = x;
+  }
+}
+
+// y = X r for the n x n matrix X (leading dimension ld) and r in FP32, by all warps (a row per
+// warp, the columns over its lanes, a shuffle sum in fixed order).
+__device__ __forceinline__ void small_matvec(const float* X, int n, int ld, const float* r, float* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nw) {
+    float y = 0.f;
+    if (lane < n) y = X[i * ld + lane] * r[lane];
+    if (lane + 32 < n) y = fmaf(X[i * ld + lane + 32], r[lane + 32], y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0) out[i] = y;
+  }
+}
+
+// (c, alpha) += y (FP64) and the convergence test ||y||_inf <= tol max(1, ||(c, alpha)||_inf),
+// every thread taking unknowns; the maxima of the nonnegative FP32 magnitudes are formed with
+// integer atomics on their bit patterns (order-independent).  red: three words, zero on entry.
+template <int D>
+__device__ void newton_update_mixed(const AugArgs& A, const float* y, int NH, const StepState& S, int dropped,
+                                    bool ok, bool writer, unsigned* red) {
+  const int tid = threadIdx.x;
+  for (int p = tid; p <= NH; p += blockDim.x) {
+    double nv;
+    if (p < NH) {
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      const long long off = coarse_offset<D>(z, A.nc);
+      nv = S.c[off] + (double)y[p];
+      S.c[off] = nv;
+    } else {
+      nv = S.sa[1] + (double)y[NH];
+      S.sa[1] = nv;
+    }
+    const float dv = fabsf(y[p]), av = fabsf((float)nv);
+    if (!(dv <= 3.0e38f) || !(av <= 3.0e38f)) atomicOr(&red[2], 1u);
+    atomicMax(&red[0], __float_as_uint(dv));
+    atomicMax(&red[1], __float_as_uint(av));
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const bool finite = red[2] == 0u;
+    const float dmax = __uint_as_float(red[0]), ymax = __uint_as_float(red[1]);
+    S.flags[1] = (!ok || !finite) ? 1 : 0;
+    S.flags[0] = (finite && dmax <= (float)A.tol * fmaxf(1.f, ymax)) ? 1 : 0;
+    if (writer) {
+      if (dropped) atomicOr(&A.st->flags, kFlagDropped);
+      if (!ok) atomicOr(&A.st->flags, kFlagNotSPD);
+      if (!finite) atomicOr(&A.st->flags, kFlagNonfinite);
+    }
+  }
+}
+
+// The dense step of the mixed path, after a pass, in every block.  The residual R of the
+// (N_H+1)-dimensional system of eq. 3.6 on V_H + span{u~} is formed in FP64 from the cell
+// sums (the first pass's sums are kept and the later passes' increments added to them).  The
+// first iteration also assembles the Jacobian (fixed point: the Galerkin stiffness) in FP32
+// from the FP32 channels directly into the band-plus-border pattern, factors it by the band
+// LDL^T on one warp and forms its inverse from the factor (a column per thread), which is
+// kept in shared memory: every iteration's step is then y = J^{-1} R, a block-wide
+// matrix-vector product, so the later iterations are chord steps at the cost of one product.
+// If the last pivot (the Schur complement of alpha) falls below 1e-6 of its original
+// diagonal entry, alpha is frozen (its row and column of the inverse are zero).
+template <int D>
+__device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* __restrict__ partials,
+                                               double* cellsum, double* Mreg, double* R, float* L,
+                                               const StepState& S, bool first, bool writer) {
+  using G = Aug<D, true>;
+  constexpr int N3 = D == 2 ? 9 : 27;
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+  const int lane = tid & 31;
+  const int ncell = (int)ipow(A.nc, D);
+  const int NH = (int)ipow(A.nc - 1, D);
+  const int NA = NH + 1;
+  const int ld = NA + 1;
+  const bool fixedp = A.fixed_point != 0;
+  float* X = reinterpret_cast<float*>(Mreg);   // J^{-1} as it is formed [NA][ld]
+  float* rf = X + (size_t)NA * ld;             // R in FP32 [NA]
+  float* dl = rf + NA;                         // the step y = J^{-1} R [NA]
+  __shared__ float s3_sh;
+  __shared__ int fac_sh[2];
+  __shared__ unsigned red_sh[3];
+  if (tid == 0) red_sh[0] = red_sh[1] = red_sh[2] = 0u;
+  // ---- cell sums (fixed order over the cell's blocks): the residual channels in FP64, in the
+  // first iteration also t, s (FP64) and the Jacobian channels (FP32); eight items per thread
+  // are loaded together.  With one block per cell the partial rows are the cell sums and are
+  // copied as they are.
+  const int nneed = first ? G::NVAL : G::NV + 1;
+  const int total = ncell * nneed;
+  for (int base = tid; base < total; base += 8 * nthr) {
+    int dst[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = base + r * nthr;
+      dst[r] = -1;
+      if (idx < total) {
+        const int cell = idx / nneed, q = idx - cell * nneed;
+        const int v = first ? q : (q < G::NV ? G::RA + q : G::SA);
+        if (!(fixedp && v >= G::JB)) dst[r] = cell * G::NVAL + v;
+      }
+    }
+    if (A.bpc == 1) {
+      unsigned long long wv[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        wv[r] = dst[r] >= 0 ? __ldcg(reinterpret_cast<const unsigned long long*>(partials) + dst[r]) : 0ull;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (dst[r] >= 0) reinterpret_cast<unsigned long long*>(cellsum)[dst[r]] = wv[r];
+      continue;
+    }
+    double xd[8];
+    float xf[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      xd[r] = 0.0;
+      xf[r] = 0.f;
+    }
+    for (int b = 0; b < A.bpc; ++b) {
+      double wv[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int cell = dst[r] >= 0 ? dst[r] / G::NVAL : 0;
+        wv[r] = dst[r] >= 0 ? __ldcg(partials + ((size_t)cell * A.bpc + b) * G::NVAL + (dst[r] - cell * G::NVAL))
+                            : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (dst[r] < 0) continue;
+        if (dst[r] % G::NVAL >= G::JB)
+          xf[r] += __int_as_float(__double2loint(wv[r]));
+        else
+          xd[r] += wv[r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if (dst[r] < 0) continue;
+      if (dst[r] % G::NVAL >= G::JB)
+        reinterpret_cast<float*>(cellsum + dst[r])[0] = xf[r];
+      else
+        cellsum[dst[r]] = xd[r];
+    }
+  }
+  __syncthreads();
+  // the first pass's residual sums are kept in basev; the later passes' increments are added
+  // to them (fixed order, same thread each time)
+  for (int idx = tid; idx < ncell * (G::NV + 1); idx += nthr) {
+    const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
+    const long long ch = (long long)cell * G::NVAL + (v < G::NV ? G::RA + v : G::SA);
+    if (first)
+      S.basev[idx] = cellsum[ch];
+    else
+      cellsum[ch] += S.basev[idx];
+  }
+  if (first) {
+    for (int p = tid; p < NH; p += nthr) {
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      S.t[p] = node_channel<D, true>(cellsum, A.nc, z, G::TT);
+    }
+    if (tid >= nthr - 32) {
+      double s0 = 0.0;
+      float s3 = 0.f;
+      for (int c = lane; c < ncell; c += 32) {
+        s0 += cellsum[(long long)c * G::NVAL + G::SS];
+        if (!fixedp) s3 += reinterpret_cast<const float*>(cellsum + (long long)c * G::NVAL + G::JS)[0];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+      }
+      if (lane == 0) {
+        S.sa[0] = s0;
+        s3_sh = s3;
+      }
+    }
+    // the factor's pattern: everything outside it reads as zero
+    for (int i = tid; i < NA * ld; i += nthr) L[i] = 0.f;
+  }
+  __syncthreads();
+  // ---- residual (FP64): R = -(A_H c + alpha t + P^T w (f(U) - g), t.c + alpha s + u~.w (f(U) - g))
+  const double alpha = S.sa[1];
+  const double sig = A.sigma_H;
+  for (int p = tid; p < NH; p += nthr) {
+    int z[3];
+    unknown_coords<D>(p, A.nc, z);
+    const long long off = coarse_offset<D>(z, A.nc);
+    double nb = 0.0;
+    long long mul = 1;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      nb += S.c[off - mul] + S.c[off + mul];
+      mul *= (A.nc + 1);
+    }
+    const double ahc = sig * (2.0 * D * S.c[off] - nb);
+    rf[p] = (float)(-(ahc + alpha * S.t[p] + node_channel<D, true>(cellsum, A.nc, z, G::RA)));
+  }
+  if (tid >= nthr - 32) {
+    double s2 = 0.0, tc = 0.0;
+    for (int c = lane; c < ncell; c += 32) s2 += cellsum[(long long)c * G::NVAL + G::SA];
+    for (int p = lane; p < NH; p += 32) {
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      tc += S.t[p] * S.c[coarse_offset<D>(z, A.nc)];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      tc += __shfl_xor_sync(0xffffffffu, tc, o);
+    }
+    if (lane == 0) {
+      rf[NH] = (float)(-(tc + alpha * S.sa[0] + s2));
+      if (first) L[NH * ld + NH] = (float)S.sa[0] + (fixedp ? 0.f : s3_sh);
+    }
+  }
+  if (first) {
+    // the Jacobian (fixed point: the Galerkin stiffness) in FP32 from the FP32 channels: the
+    // lower band (neighbours q <= p of unknown p in the 3^d box) and the border row, an entry
+    // per thread
+    const float sigf = (float)sig;
+    for (int e = tid; e < NH * (N3 + 1); e += nthr) {
+      const int p = e / (N3 + 1), rr = e - p * (N3 + 1);
+      int z[3];
+      unknown_coords<D>(p, A.nc, z);
+      if (rr == N3) {
+        L[NH * ld + p] = (float)S.t[p] + (fixedp ? 0.f : node_channel_f<D>(cellsum, A.nc, z, G::JB));
+        continue;
+      }
+      int zq[3], q = 0, mulq = 1, dist = 0, r2 = rr;
+      bool okq = true;
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        const int d = r2 % 3 - 1;
+        r2 /= 3;
+        zq[ax] = z[ax] + d;
+        if (zq[ax] < 1 || zq[ax] > A.nc - 1) okq = false;
+        q += (zq[ax] - 1) * mulq;
+        mulq *= (A.nc - 1);
+        dist += abs(d);
+      }
+      if (!okq || q > p) continue;
+      float v = fixedp ? 0.f : pair_channel_f<D>(cellsum, A.nc, z, zq);
+      if (dist == 0) v += sigf * (float)(2 * D);
+      else if (dist == 1) v -= sigf;
+      L[p * ld + q] = v;
+    }
+  }
+  __syncthreads();
+  int dropped = 0;
+  bool ok = true;
+  const float* Xuse = L;   // the kept inverse (chord steps)
+  if (first) {
+    // ---- band LDL^T of J on one warp, then its inverse, a column per thread
+    const int band = aug_band<D>(A.nc);
+    float* rd = L + (size_t)NA * ld;
+    if (tid < 32) {
+      int dr = 0;
+      const bool okw = ldlt_band_warp<float>(L, NA, ld, rd, band, 1, true, 1e-6, &dr);
+      if (tid == 0) {
+        fac_sh[0] = okw ? 1 : 0;
+        fac_sh[1] = dr;
+      }
+    }
+    __syncthreads();
+    ok = fac_sh[0] != 0;
+    dropped = fac_sh[1];
+    if (tid < NA) band_inverse_column<D>(L, rd, NA, ld, band, tid, X);
+    __syncthreads();
+    // keep J^{-1} where the factor was (the factor is no longer needed)
+    for (int i = tid; i < NA * ld; i += nthr) L[i] = X[i];
+    Xuse = X;
+  }
+  // ---- the step y = J^{-1} R, then (c, alpha) += y and the convergence test
+  small_matvec(Xuse, NA, ld, rf, dl);
+  __syncthreads();
+  newton_update_mixed<D>(A, dl, NH, S, dropped, ok, writer, red_sh);
+}
+
 // After a pass, in every block: cell sums, the dense system, the Newton step, convergence.
 // In the mixed path (JF32) the first iteration factors its Jacobian into L (LDL^T, FP32, with
 // the reciprocal pivots after it) and the later iterations are chord steps with that factor.
@@ -1155,6 +1614,10 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
   const int NA = NH + 1;
   const int ld = NA + 1;
   constexpr int N3 = D == 2 ? 9 : 27;
+  if constexpr (JF32) {
+    newton_step_mixed<D>(A, partials, cellsum, M, R, L, S, first, writer);
+    return;
+  }
   const double alpha = S.sa[1];
   const double* t_vec = S.t;
   if ((JF32 || A.fixed_point) && !first) {
@@ -1474,7 +1937,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
     __syncthreads();
     if (stop) break;
     fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, bic);
-    block_reduce_rows<D, JF32>(acc, pbuf + (size_t)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
+    block_reduce_rows<D, JF32>(A, acc, pbuf + (size_t)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
     grid_barrier(A.st, nblocks);
     newton_step<D, JF32>(A, pbuf, cellsum, M, R, L, S, first, writer);
     __syncthreads();
@@ -1482,17 +1945,98 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
   }
   step_report(A, S, it, writer);
   if (flags_sh[1] && writer && tid == 0) A.st->abort = 1;
+  if (A.split_update) {
+    // the update runs as a kernel of its own: block 0 hands over c and alpha - 1 in FP32 (the
+    // update forms the increment (alpha - 1) u~ + P c in FP32)
+    if (blockIdx.x == 0) {
+      float* cf = reinterpret_cast<float*>(A.cfin);
+      const int cn = (int)ipow(A.nc + 1, D);
+      for (int i = tid; i < cn; i += blockDim.x) cf[i] = (float)S.c[i];
+      if (tid == 0) cf[cn] = (float)(S.sa[1] - 1.0);
+    }
+    return;
+  }
   // final update u = alpha u~ + P_{H->k} c
   if (tid < G::NV) cv[tid] = S.c[vert_off];
   __syncthreads();
   fine_pass<D, JF32>(A, kUpdate, acc, cv, S.sa[1], cell, bic);
 }
 
-// The same Newton iteration for one instance on a thread-block cluster instead of a
-// cooperative grid: CTA r of the cluster takes coarse cells r, r + CS, ...; the hardware
-// cluster barrier replaces the grid barrier.  Clusters are co-scheduled by the hardware, so
-// many instances can run this kernel concurrently (batched solves) without the risk of two
-// partially resident cooperative grids waiting on each other.
+// The final update of a correction step's mixed path, u = alpha u~ + P_{H->k} c, as a
+// node-parallel kernel at full occupancy (the largest levels, where the Newton kernel's own pass
+// at its 16 warps per SM is latency-bound).  Node (x, y[, z]) lies in coarse cell x >> ls (s =
+// 2^ls fine cells per coarse cell) at offsets o = x & (s-1); sorting the offsets in decreasing
+// order (ties: x before y before z) gives the Kuhn simplex v_0 = 0, v_{t+1} = v_t + e_{pi_t}
+// with barycentric weights lambda_0 = (s - o_{pi_0})/s, lambda_t = (o_{pi_{t-1}} - o_{pi_t})/s,
+// lambda_d = o_{pi_{d-1}}/s -- the simplices and weights of the column walk.  The increment
+// (alpha - 1) u~ + P c is formed in FP32 from the FP32 coarse values the Newton kernel left in
+// cf (then alpha - 1) and added to the float-float u~; the result is float-float, or FP64 for
+// the solve's last step (out_f64).  Threads run along x; each block walks rows y (and z) with
+// the grid's row stride, so the coarse values are staged once per block.
+template <int D>
+__global__ void __launch_bounds__(256) k_aug_update(double* __restrict__ u, int n, int ls, int nc,
+                                                    const float* __restrict__ cf, int out_f64) {
+  __shared__ float cs[128];
+  __shared__ float am1;
+  const int cn = (int)ipow(nc + 1, D);
+  for (int i = threadIdx.x; i < cn; i += blockDim.x) cs[i] = cf[i];
+  if (threadIdx.x == 0) am1 = cf[cn];
+  __syncthreads();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < 1 || x >= n) return;
+  const long long np = n + 1;
+  const int s = 1 << ls;
+  const float inv_s = 1.0f / (float)s;
+  const int cp = nc + 1;
+  const int ox = x & (s - 1), cx = x >> ls;
+  const long long rows = D == 2 ? (long long)(n - 1) : (long long)(n - 1) * (n - 1);
+  for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int y = (int)(D == 2 ? r : r % (n - 1)) + 1;
+    const int z = D == 3 ? (int)(r / (n - 1)) + 1 : 0;
+    const long long idx = (D == 2 ? (long long)y : (long long)z * np + y) * np + x;
+    const int o[3] = {ox, y & (s - 1), D == 3 ? (z & (s - 1)) : 0};
+    const int cc[3] = {cx, y >> ls, D == 3 ? (z >> ls) : 0};
+    // axes in decreasing offset order, ties to the lower axis
+    int pi[3] = {0, 1, 2};
+    if (D == 2) {
+      if (o[1] > o[0]) {
+        pi[0] = 1;
+        pi[1] = 0;
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2 - a; ++b)
+          if (o[pi[b + 1]] > o[pi[b]]) {
+            const int t = pi[b];
+            pi[b] = pi[b + 1];
+            pi[b + 1] = t;
+          }
+    }
+    int vo[3] = {0, 0, 0};   // the current simplex vertex, coarse offsets
+    auto cval = [&]() {
+      const int base = D == 2 ? (cc[1] + vo[1]) * cp + cc[0] + vo[0]
+                              : ((cc[2] + vo[2]) * cp + cc[1] + vo[1]) * cp + cc[0] + vo[0];
+      return cs[base];
+    };
+    float pc = (float)(s - o[pi[0]]) * cval();
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      vo[pi[t]] = 1;
+      const int w = t + 1 < D ? o[pi[t]] - o[pi[t + 1]] : o[pi[t]];
+      pc = fmaf((float)w, cval(), pc);
+    }
+    pc *= inv_s;
+    const ff ut = ff_load(u + idx);
+    const ff un = ff_add_f(ut, fmaf(am1, ut.hi, pc));
+    if (out_f64)
+      u[idx] = (y & 1) ? ff_to_double_rn(un) : ff_to_double_fast(un);
+    else
+      ff_store(u + idx, un);
+  }
+}
+
 template <int D, bool JF32>
 __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented_cluster(AugArgs A) {
   using G = Aug<D, JF32>;
@@ -1540,7 +2084,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
       Rows<D, JF32>::zero(acc, first, A.fixed_point != 0, tid);
       __syncthreads();
       fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, 0);
-      block_reduce_rows<D, JF32>(acc, pbuf + (size_t)cell * G::NVAL, first, A.fixed_point != 0);
+      block_reduce_rows<D, JF32>(A, acc, pbuf + (size_t)cell * G::NVAL, first, A.fixed_point != 0);
     }
     cluster.sync();
     newton_step<D, JF32>(A, pbuf, cellsum, M, R, L, S, first, writer);
@@ -1723,9 +2267,14 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.pstride = (long long)ab.partial_items * (dim == 2 ? Aug<2, false>::NVAL : Aug<3, false>::NVAL);
   A.Ainv = ab.Ainv;
   A.st = st;
-  // barrier words and abort/converged flags start cleared
-  cudaError_t e = cudaMemsetAsync(&st->bar_count, 0, 4 * sizeof(unsigned), s);
-  if (e != cudaSuccess) return e;
+  A.cfin = ab.cfin;
+  // the largest levels of the mixed path update in a kernel of their own (cooperative launch)
+  A.split_update = (dim == 2 && jac_f32 && cluster_size == 0 && ab.cfin && gk.nodes >= (1ll << 21) &&
+                    (int)ipow(coarse_cells + 1, dim) < 128) ? 1 : 0;
+  // the barrier words and the abort flag are cleared once per solve (or component call) with
+  // the statistics; a completed barrier leaves its count at zero and generations only grow, so
+  // the launches of one solve need no reset between them
+  cudaError_t e = cudaSuccess;
   if (cluster_size > 0) {
     A.bpc = 1;
     cudaLaunchConfig_t cc = {};
@@ -1758,11 +2307,25 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (dim == 2) {
-    if (jac_f32) return cudaLaunchKernelEx(&cfg, k_augmented<2, true>, A);
-    return cudaLaunchKernelEx(&cfg, k_augmented<2, false>, A);
+    e = jac_f32 ? cudaLaunchKernelEx(&cfg, k_augmented<2, true>, A) : cudaLaunchKernelEx(&cfg, k_augmented<2, false>, A);
+  } else {
+    e = jac_f32 ? cudaLaunchKernelEx(&cfg, k_augmented<3, true>, A) : cudaLaunchKernelEx(&cfg, k_augmented<3, false>, A);
   }
-  if (jac_f32) return cudaLaunchKernelEx(&cfg, k_augmented<3, true>, A);
-  return cudaLaunchKernelEx(&cfg, k_augmented<3, false>, A);
+  if (e != cudaSuccess || !A.split_update) return e;
+  int ls = 0;
+  while ((1 << ls) < sfine) ++ls;
+  // about eight blocks of rows per SM, every block staging the coarse values once
+  const unsigned gx = (unsigned)((gk.n + 1 + 255) / 256);
+  const long long rows = dim == 2 ? (long long)(gk.n - 1) : (long long)(gk.n - 1) * (gk.n - 1);
+  long long gy = (8ll * (ab.sms > 0 ? ab.sms : 152) + gx - 1) / gx;
+  if (gy > rows) gy = rows;
+  if (gy > 65535) gy = 65535;
+  const float* cf = reinterpret_cast<const float*>(ab.cfin);
+  if (dim == 2)
+    k_aug_update<2><<<dim3(gx, (unsigned)gy), 256, 0, s>>>(u, gk.n, ls, coarse_cells, cf, out_f64);
+  else
+    k_aug_update<3><<<dim3(gx, (unsigned)gy), 256, 0, s>>>(u, gk.n, ls, coarse_cells, cf, out_f64);
+  return cudaGetLastError();
 }
 
 }  // namespace fmg

@@ -1,6 +1,7 @@
 // Host-side check of the float-float helpers of the mixed path (compiled as host code).
-// ff_to_double_rn, the integer conversion of a float-float pair to FP64, must give the bits of
-// the FP64 addition hi + lo (round to nearest, ties to even) for every normalized pair.  The
+// ff_to_double_rn, the integer conversion of a float-float pair to FP64, and ff_to_double_fast,
+// the conversion through FP64 values built from the FP32 bits, must give the bits of the FP64
+// addition hi + lo (round to nearest, ties to even) for every normalized pair.  The
 // error-free transformations must be exact: two_sum gives s + e = a + b and two_prod gives
 // p + e = a b, checked in FP64 where these sums are exact.  The float-float operations must stay
 // within their error bounds, checked against quad-precision sums of the float parts (113 bits hold every sum here exactly): ff_add
@@ -40,12 +41,18 @@ int main(int argc, char** argv) {
   long long n = 0, bad = 0;
   auto check = [&](ff x) {
     const double want = (double)x.hi + (double)x.lo, got = fmg::ff_to_double_rn(x);
-    uint64_t a, b;
+    const double got2 = fmg::ff_to_double_fast(x);
+    uint64_t a, b, c;
     memcpy(&a, &want, 8);
     memcpy(&b, &got, 8);
+    memcpy(&c, &got2, 8);
     ++n;
     if (a != b && !(std::isnan(want) && std::isnan(got))) {
       if (bad < 5) printf("mismatch: hi=%a lo=%a add=%a int=%a\n", x.hi, x.lo, want, got);
+      ++bad;
+    }
+    if (a != c && !(std::isnan(want) && std::isnan(got2))) {
+      if (bad < 5) printf("mismatch: hi=%a lo=%a add=%a bits+add=%a\n", x.hi, x.lo, want, got2);
       ++bad;
     }
   };
