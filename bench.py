@@ -35,7 +35,6 @@ METRIC = "FMG fine DOFs/s to discretization error, mixed vs FP64; HBM GB/s; p50/
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, keyed by
 # (kind, dim); a kernel changed since its capture has no entry (traffic null)
 TRAFFIC = {("pre_top", 2): 16_792_064 + 6_912,
-           ("augmented", 2): 68_189_696 + 2_465_792,
            ("smooth_top", 2): 50_357_248 + 261_376}
 WORKLOAD = "2D unit square P1, H=1/8, 8 refinements (2049x2049 nodes, 4,190,209 fine DOFs), u^3, 8 sin modes"
 WORKLOAD_3D = ("3D unit cube P1 on Kuhn tetrahedra, H=1/4, 6 refinements (257^3 nodes, 16,581,375 fine DOFs), "
@@ -64,6 +63,19 @@ def solve_bytes_per_dof(dim: int, mixed: bool, m: int, smoother: str, nu=(2, 2),
     cycle = outer + ((nu[0] + nu[1]) * sweep + 2 * transfer) * ratio
     step = 24 + m * cycle + 16 + newton_passes * 8 + 16
     return step * ratio
+
+
+# FP64 operations (an FMA counts as two) per fine node of the FP64 path's augmented-space kernel
+# for a u^3 (cubic) nonlinearity, counted from its per-node code: the first pass (f and f' at
+# u~: 4; f - g: 1; the residual moments: 5; the Jacobian moments: 11; A u~ and the t, s moments:
+# 11; the z counter: 1), each later Newton pass (U = alpha u~ + P c: 4; then 4 + 1 + 5 + 11 + 1)
+# and the update (U: 4, z: 1).
+AUG64_FLOPS_FIRST = 33
+AUG64_FLOPS_NEWTON = 26
+AUG64_FLOPS_UPDATE = 5
+# FP64 operations per node of one red-black sweep (both colours): 2D (4 neighbours summed: 3,
+# + b: 1, * 1/4: 1), 3D (6 neighbours: 5, b * h + s: 2, * 1/6: 1)
+RBGS64_FLOPS = {2: 5, 3: 8}
 
 
 def parse():
@@ -443,6 +455,36 @@ def run_ours(args):
     roofline = roof[dominant]
     other = {k: v for k, v in roof.items() if k != dominant}
 
+    # ---- FP64 arm: its ALU-bound kernels against the measured FP64 FMA rate
+    log("fp64 roofline")
+    fp64_peak = fmg.fmg_fp64_fma_rate(10) / 1e12
+    kt64 = kernel_times(torch, fmg, solvers["fp64"], flush, max(3, args.steps // 2), top)
+    fp64_roof = {}
+    interior = (n - 1) ** dim
+    sw_ms, sw_n = kt64[fmg.KT_SMOOTH_TOP]
+    if sw_ms > 0:
+        tf = RBGS64_FLOPS[dim] * interior / (sw_ms * 1e-3) / 1e12
+        fp64_roof["rbgs_sweep"] = {"kernel": f"k_rbgs{dim}<double> sweep (both colours) on the finest level",
+                                   "bound": "fp64_alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                                   "frac": tf / fp64_peak, "flops_per_node": RBGS64_FLOPS[dim],
+                                   "avg_launch_ms": sw_ms, "launches": sw_n}
+    a64_ms, a64_n = kt64[fmg.KT_AUGMENTED]
+    its64 = int(results["fp64"]["stats"].newton_iters[top - 1]) or 1
+    if a64_ms > 0 and prob.f == "cubic":
+        fpn = AUG64_FLOPS_FIRST + AUG64_FLOPS_NEWTON * (its64 - 1) + AUG64_FLOPS_UPDATE
+        tf = fpn * interior / (a64_ms * 1e-3) / 1e12
+        fp64_roof["augmented"] = {"kernel": f"k_augmented<{dim}, 0> (FP64 path) on the finest level",
+                                  "bound": "fp64_alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                                  "frac": tf / fp64_peak, "flops_per_node": fpn, "newton_iterations": its64,
+                                  "avg_launch_ms": a64_ms, "launches": a64_n}
+    fp64_dom = max(fp64_roof, key=lambda k: fp64_roof[k]["avg_launch_ms"] * fp64_roof[k]["launches"]) \
+        if fp64_roof else None
+    fp64_roofline = dict(fp64_roof[fp64_dom]) if fp64_dom else None
+    if fp64_roofline is not None:
+        fp64_roofline["peak_source"] = ("measured: fmg_fp64_fma_rate, independent FP64 FMA chains on every SM "
+                                        "(an FMA counts as two)")
+        fp64_roofline["other"] = {k: v for k, v in fp64_roof.items() if k != fp64_dom}
+
     # ---- end to end through the public API with host buffers (pinned)
     log("e2e")
     g_host = torch.from_numpy(np.ascontiguousarray(g)).pin_memory()
@@ -500,7 +542,7 @@ def run_ours(args):
                        "l2": "flushed between steps (512 MB write outside the timed events)",
                        "m": m_cycles["mixed"], "fp64_m": m_cycles["fp64"], "nu": [2, 2], "p": 1},
             "fp64": {"value": world * dofs / (f64 * 1e-3), "unit": "DOF/s", "ms_per_step": f64,
-                     "speedup_mixed_over_fp64": f64 / mix},
+                     "speedup_mixed_over_fp64": f64 / mix, "roofline": fp64_roofline},
             "accuracy": {"l2_err_vs_exact_mixed": acc["mixed"], "l2_err_vs_exact_fp64": acc["fp64"],
                          "l2_diff_mixed_fp64": diff, "discretization": alg,
                          "newton_iters": list(results["mixed"]["stats"].newton_iters[:top]),

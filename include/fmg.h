@@ -270,6 +270,24 @@ fmg_status fmg_kernel_time(fmg_ctx* c, int kind, int level, double* total_ms, in
 /* Kernel nodes in the captured solve graph (0 before the first solve, -1 for NULL). */
 int fmg_graph_kernels(const fmg_ctx* c);
 
+/* Failure-detection test hook (the paper has no counterpart: it exercises this library's
+ * bounded device waits).  The augmented-space Newton kernel of a solve is one cooperative
+ * launch whose blocks meet at a grid barrier after every pass; a waiting block polls at most
+ * `spins` times (0 restores the default, 2^25) and then sets the timeout flag (fmg_stats.flags
+ * bit 4) and an abort word that makes every block leave, so the solve returns FMG_ERR_TIMEOUT
+ * instead of waiting without bound.  skip_block >= 0 makes that block skip its arrival at the
+ * first barrier of every such launch, so the others run out of polls; -1 turns it off.  Nothing
+ * faults or hangs: every wait is bounded.  The next solve recaptures its graph; a later solve
+ * with the hook off starts from cleared barrier words and flags. */
+fmg_status fmg_debug_barrier_fault(fmg_ctx* c, long long spins, int skip_block);
+
+/* The current device's FP64 fused multiply-add rate, the roofline of the FP64 path's ALU-bound
+ * kernels (the paper has no counterpart: it is a measurement service of this library).  Runs
+ * `reps` (1..1000) timed launches of independent FMA chains, eight 256-thread blocks per SM,
+ * and writes the rate in FP64 FLOP/s (an FMA counts as two) to *flops.  It allocates a few
+ * bytes of device memory and a stream of its own, and waits for them. */
+fmg_status fmg_fp64_fma_rate(int reps, double* flops);
+
 /* ---------------------------------------------------------------------------------------
  * V-cycles that allocate no device memory.
  *

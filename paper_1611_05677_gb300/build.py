@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libfmg_gb300.so")
 SOURCES = ["fmg_stencil.cu", "fmg_newton.cu", "fmg_fused.cu", "fmg_ff.cu", "fmg_capi.cu", "fmg_noalloc.cu",
-           "fmg_server.cu"]
+           "fmg_server.cu", "fmg_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -186,6 +186,8 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
     c->ab.partials = partials;
     c->ab.Ainv = Ainv;
     c->ab.cfin = cfin;
+    c->ab.bar_spins = 0;
+    c->ab.bar_skip = -1;
   }
   return off;
 }
@@ -921,6 +923,19 @@ fmg_status fmg_set_kernel_timing(fmg_ctx* c, int on) {
     c->graph = nullptr;
     c->timing = on != 0;
   }
+  return FMG_OK;
+}
+
+fmg_status fmg_debug_barrier_fault(fmg_ctx* c, long long spins, int skip_block) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if (spins < 0 || skip_block < -1) return fail(c, FMG_ERR_INVALID, "bad arguments");
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  c->ab.bar_spins = spins;
+  c->ab.bar_skip = skip_block;
   return FMG_OK;
 }
 

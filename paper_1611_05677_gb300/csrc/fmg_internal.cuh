@@ -220,6 +220,8 @@ struct AugBuffers {
   int nt;             // threads per block
   size_t smem;        // dynamic shared memory per block
   int sms;            // multiprocessors of the device
+  long long bar_spins; // grid-barrier polls before a timeout (0: the default, 2^25)
+  int bar_skip;        // failure-detection test hook: block that skips its first arrival (-1: none)
 };
 // Fills bpc/nt/smem/partial_items for this device (occupancy-based), outside any capture.
 void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab);

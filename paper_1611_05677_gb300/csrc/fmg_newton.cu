@@ -507,18 +507,22 @@ struct AugArgs {
   const double* Ainv;   // A_H^{-1} (= A_1^{-1}, h_1 = H), dense NH x NH, preconditioner
   DevState* st;
   double* cfin;         // [(nc+1)^d] c, then alpha (split_update)
+  long long bar_spins;  // polls of the grid barrier before it times out
+  int bar_skip;         // test hook: this block skips its first barrier arrival (-1: none)
 };
 
-// Bounded grid barrier for the cooperative launch (all blocks co-resident).  On timeout the
-// abort word is set and every block leaves at its next check.
-__device__ void grid_barrier(DevState* st, unsigned nblocks) {
+// Bounded grid barrier for the cooperative launch (all blocks co-resident).  A waiting block
+// gives up after `spins` polls: the timeout flag and the abort word are set and every block
+// leaves at its next check.  skip (the failure-detection test hook): this block does not
+// arrive, so the others run out of polls; no block waits without bound.
+__device__ void grid_barrier(DevState* st, unsigned nblocks, long long spins_max, bool skip) {
   __syncthreads();
   if (nblocks > 1 && threadIdx.x == 0) {
     volatile unsigned* genp = &st->bar_gen;
     const unsigned gen = *genp;
     __threadfence();
-    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-    if (arrived == nblocks - 1) {
+    const unsigned arrived = skip ? 0u : atomicAdd(&st->bar_count, 1u);
+    if (!skip && arrived == nblocks - 1) {
       atomicExch(&st->bar_count, 0u);
       __threadfence();
       atomicAdd(&st->bar_gen, 1u);
@@ -526,7 +530,7 @@ __device__ void grid_barrier(DevState* st, unsigned nblocks) {
       long long spins = 0;
       while (*genp == gen) {
         __nanosleep(32);
-        if (++spins > (1ll << 25)) {
+        if (++spins > spins_max) {
           atomicOr(&st->flags, kFlagTimeout);
           atomicExch(&st->abort, 1);
           break;
@@ -1938,7 +1942,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
     if (stop) break;
     fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, bic);
     block_reduce_rows<D, JF32>(A, acc, pbuf + (size_t)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
-    grid_barrier(A.st, nblocks);
+    grid_barrier(A.st, nblocks, A.bar_spins, first && (int)blockIdx.x == A.bar_skip);
     newton_step<D, JF32>(A, pbuf, cellsum, M, R, L, S, first, writer);
     __syncthreads();
     if (flags_sh[0] || flags_sh[1]) break;
@@ -2268,6 +2272,8 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.Ainv = ab.Ainv;
   A.st = st;
   A.cfin = ab.cfin;
+  A.bar_spins = ab.bar_spins > 0 ? ab.bar_spins : (1ll << 25);
+  A.bar_skip = ab.bar_skip;
   // the largest levels of the mixed path update in a kernel of their own (cooperative launch)
   A.split_update = (dim == 2 && jac_f32 && cluster_size == 0 && ab.cfin && gk.nodes >= (1ll << 21) &&
                     (int)ipow(coarse_cells + 1, dim) < 128) ? 1 : 0;

@@ -71,8 +71,9 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
            "fmg_solve_batch", "fmg_destroy", "fmg_last_error", "fmg_solution", "fmg_levels", "fmg_level_cells",
            "fmg_op_smooth", "fmg_op_smooth_f32", "fmg_op_residual", "fmg_op_vcycle", "fmg_op_correction_step",
            "fmg_op_level1_solve", "fmg_op_prolong", "fmg_set_kernel_timing", "fmg_kernel_time",
-           "fmg_graph_kernels", "fmg_vcycle_noalloc", "fmg_batch_create", "fmg_batch_solve", "fmg_batch_sync",
-           "fmg_batch_destroy", "fmg_server_create", "fmg_server_submit", "fmg_server_poll", "fmg_server_drain",
+           "fmg_graph_kernels", "fmg_vcycle_noalloc", "fmg_debug_barrier_fault", "fmg_fp64_fma_rate",
+           "fmg_batch_create",
+           "fmg_batch_solve", "fmg_batch_sync", "fmg_batch_destroy", "fmg_server_create", "fmg_server_submit", "fmg_server_poll", "fmg_server_drain",
            "fmg_server_get_info", "fmg_server_last_error", "fmg_server_destroy", "fmg_autotune", "fmg_tuned_shape")
 KT_AUGMENTED = 0
 KT_SMOOTH_TOP = 1
@@ -120,6 +121,8 @@ def load():
         "fmg_kernel_time": (c_int, [c_void_p, c_int, c_int, POINTER(c_double), POINTER(c_int)]),
         "fmg_graph_kernels": (c_int, [c_void_p]),
         "fmg_vcycle_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+        "fmg_debug_barrier_fault": (c_int, [c_void_p, ctypes.c_longlong, c_int]),
+        "fmg_fp64_fma_rate": (c_int, [c_int, POINTER(c_double)]),
         "fmg_batch_create": (c_int, [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]),
         "fmg_batch_solve": (c_int, [c_void_p, S]),
         "fmg_batch_sync": (c_int, [c_void_p]),
@@ -291,6 +294,18 @@ def fmg_kernel_time(ctx, kind: int, level: int = 0):
 
 def fmg_graph_kernels(ctx) -> int:
     return load().fmg_graph_kernels(ctx)
+
+
+def fmg_debug_barrier_fault(ctx, spins: int = 0, skip_block: int = -1):
+    """Failure-detection test hook: grid-barrier poll limit and a block that skips its first arrival."""
+    _check(load().fmg_debug_barrier_fault(ctx, spins, skip_block), ctx)
+
+
+def fmg_fp64_fma_rate(reps: int = 20) -> float:
+    """The device's FP64 FMA rate in FLOP/s (an FMA counts as two), measured by the library."""
+    r = c_double(0.0)
+    _check(load().fmg_fp64_fma_rate(reps, byref(r)))
+    return r.value
 
 
 def fmg_vcycle_noalloc(dim, coarse_cells, level, b, u, cycles=1, nu_pre=2, nu_post=2, stream=None):
