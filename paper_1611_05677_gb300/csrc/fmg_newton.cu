@@ -84,9 +84,14 @@ __device__ __forceinline__ double recip_pivot(double d) {
 // drop_last and the last pivot (the Schur complement of the last unknown) falls below drop_tol
 // times the original last diagonal entry, rd[n-1] = 0: that unknown is frozen (*dropped = 1).
 // Returns false if a pivot is not positive.
-template <typename T, int NS>
-__device__ bool ldlt_band_warp_ns(T* A, int n, int ld, T* rd, int band, int border, bool drop_last, double drop_tol,
-                                  int* dropped) {
+template <typename T, int NS, int FN = 0, int FBAND = 0>
+__device__ bool ldlt_band_warp_ns(T* A, int n_arg, int ld_arg, T* rd, int band_arg, int border, bool drop_last,
+                                  double drop_tol, int* dropped) {
+  // FN, FBAND > 0: the size and band fixed at compile time (ld = FN + 1), which folds the
+  // offsets and strides into constants
+  const int n = FN > 0 ? FN : n_arg;
+  const int ld = FN > 0 ? FN + 1 : ld_arg;
+  const int band = FBAND > 0 ? FBAND : band_arg;
   const int lane = threadIdx.x & 31;
   const int nb = n - border;
   const int q = band + border;
@@ -153,6 +158,7 @@ __device__ bool ldlt_band_warp_ns(T* A, int n, int ld, T* rd, int band, int bord
     }
   }
   __syncwarp();
+#pragma unroll 2
   for (int k = 0; k + 1 < n; ++k) {
     const T r = rd[k];
     T pv = T(1);
@@ -1316,6 +1322,95 @@ __device__ __forceinline__ void band_inverse_column(const float* __restrict__ Af
   }
 }
 
+// The same column for a size and band fixed at compile time (the dense systems of the
+// benchmark shapes).  The band window lives in W = BAND + 1 registers addressed modulo W, and
+// the substitutions are unrolled W steps at a time, so every window slot and every offset into
+// the factor is a compile-time constant: the loads of a step are issued ahead and only the FMA
+// chain through the newest value stays on the critical path.
+template <int NA, int BAND>
+__device__ __forceinline__ void band_inverse_column_fixed(const float* __restrict__ Af, const float* __restrict__ rd,
+                                                          int c, float* __restrict__ X) {
+  constexpr int ld = NA + 1, nb = NA - 1, W = BAND + 1;
+  float win[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) win[m] = 0.f;
+  // one forward step: y_k = ([k == c] - sum_{t=1..BAND} A[k][k-t] y_{k-t}) / d_k; the older
+  // terms go into two partial sums, the newest (t = 1) is added last; `guard`: rows near the top,
+  // where k - t < 0 (decided at compile time in the peeled first block)
+  auto fwd = [&](int k, int kk, bool guard) {
+    float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+    for (int t = BAND; t >= 2; --t) {
+      if (guard && k - t < 0) continue;
+      if (t & 1)
+        p1 = fmaf(Af[k * ld + k - t], win[(kk - t + W) % W], p1);
+      else
+        p0 = fmaf(Af[k * ld + k - t], win[(kk - t + W) % W], p0);
+    }
+    float sum = p0 + p1;
+    if (!guard || k >= 1) sum = fmaf(Af[k * ld + k - 1], win[(kk - 1 + W) % W], sum);
+    const float y = ((k == c ? 1.f : 0.f) - sum) * rd[k];
+    win[kk] = y;
+    X[k * ld + c] = y;
+  };
+#pragma unroll
+  for (int kk = 0; kk < W; ++kk)
+    if (kk < nb) fwd(kk, kk, true);
+  for (int k0 = W; k0 < nb; k0 += W) {
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk)
+      if (k0 + kk < nb) fwd(k0 + kk, kk, false);
+  }
+  {
+    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = 0; j < nb; ++j) s4[j & 3] = fmaf(Af[nb * ld + j], X[j * ld + c], s4[j & 3]);
+    X[nb * ld + c] = ((nb == c ? 1.f : 0.f) - ((s4[0] + s4[1]) + (s4[2] + s4[3]))) * rd[nb];
+  }
+  const float xb = X[nb * ld + c];
+  // one backward step: x_k = y_k - (sum_{t=1..BAND} A[k+t][k] x_{k+t} + A[nb][k] x_nb) / d_k,
+  // from the top (guard: rows where k + t >= nb)
+#pragma unroll
+  for (int m = 0; m < W; ++m) win[m] = 0.f;
+  auto bwd = [&](int k, int kk, bool guard) {
+    float p0 = Af[nb * ld + k] * xb, p1 = 0.f;
+#pragma unroll
+    for (int t = BAND; t >= 2; --t) {
+      if (guard && k + t >= nb) continue;
+      if (t & 1)
+        p1 = fmaf(Af[(k + t) * ld + k], win[(kk - t + W) % W], p1);
+      else
+        p0 = fmaf(Af[(k + t) * ld + k], win[(kk - t + W) % W], p0);
+    }
+    float sum = p0 + p1;
+    if (!guard || k + 1 < nb) sum = fmaf(Af[(k + 1) * ld + k], win[(kk - 1 + W) % W], sum);
+    const float x = X[k * ld + c] - rd[k] * sum;
+    win[kk] = x;
+    X[k * ld + c] = x;
+  };
+#pragma unroll
+  for (int kk = 0; kk < W; ++kk)
+    if (nb - 1 - kk >= 0) bwd(nb - 1 - kk, kk, true);
+  for (int k0 = nb - 1 - W; k0 >= 0; k0 -= W) {
+#pragma unroll
+    for (int kk = 0; kk < W; ++kk)
+      if (k0 - kk >= 0) bwd(k0 - kk, kk, false);
+  }
+}
+
+// Column c of J^{-1}: the unrolled form for the sizes it is instantiated for, else the loop.
+template <int D>
+__device__ __forceinline__ void band_inverse_dispatch(const float* Af, const float* rd, int n, int ld, int band, int c,
+                                                      float* X) {
+  if constexpr (D == 2) {
+    if (n == 50 && band == 8) return band_inverse_column_fixed<50, 8>(Af, rd, c, X);
+    if (n == 10 && band == 4) return band_inverse_column_fixed<10, 4>(Af, rd, c, X);
+  } else {
+    if (n == 28 && band == 13) return band_inverse_column_fixed<28, 13>(Af, rd, c, X);
+  }
+  band_inverse_column<D>(Af, rd, n, ld, band, c, X);
+}
+
 // y = X r for the n x n matrix X (leading dimension ld) and r in FP32, by all warps (a row per
 // warp, the columns over its lanes, a shuffle sum in fixed order).
 __device__ __forceinline__ void small_matvec(const float* X, int n, int ld, const float* r, float* out) {
@@ -1575,7 +1670,16 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
     float* rd = L + (size_t)NA * ld;
     if (tid < 32) {
       int dr = 0;
-      const bool okw = ldlt_band_warp<float>(L, NA, ld, rd, band, 1, true, 1e-6, &dr);
+      bool okw;
+      // the benchmark shapes with their size and band fixed at compile time
+      if (D == 2 && NA == 50 && band == 8)
+        okw = ldlt_band_warp_ns<float, 2, 50, 8>(L, NA, ld, rd, band, 1, true, 1e-6, &dr);
+      else if (D == 2 && NA == 10 && band == 4)
+        okw = ldlt_band_warp_ns<float, 1, 10, 4>(L, NA, ld, rd, band, 1, true, 1e-6, &dr);
+      else if (D == 3 && NA == 28 && band == 13)
+        okw = ldlt_band_warp_ns<float, 4, 28, 13>(L, NA, ld, rd, band, 1, true, 1e-6, &dr);
+      else
+        okw = ldlt_band_warp<float>(L, NA, ld, rd, band, 1, true, 1e-6, &dr);
       if (tid == 0) {
         fac_sh[0] = okw ? 1 : 0;
         fac_sh[1] = dr;
@@ -1584,7 +1688,7 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
     __syncthreads();
     ok = fac_sh[0] != 0;
     dropped = fac_sh[1];
-    if (tid < NA) band_inverse_column<D>(L, rd, NA, ld, band, tid, X);
+    if (tid < NA) band_inverse_dispatch<D>(L, rd, NA, ld, band, tid, X);
     __syncthreads();
     // keep J^{-1} where the factor was (the factor is no longer needed)
     for (int i = tid; i < NA * ld; i += nthr) L[i] = X[i];
