@@ -397,7 +397,12 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-      const bool okw = ldlt_band_warp<T>(L, N, ld, invd, band, 0, false, 0.0, nullptr);
+      // the benchmark shapes (2D 1/H = 8, 3D 1/H = 4) with their size and band fixed at compile time
+      const bool okw = (dim == 2 && N == 49 && band == 7)
+                           ? ldlt_band_warp_ns<T, 1, 49, 7>(L, N, ld, invd, band, 0, false, 0.0, nullptr)
+                       : (dim == 3 && N == 27 && band == 9)
+                           ? ldlt_band_warp_ns<T, 2, 27, 9>(L, N, ld, invd, band, 0, false, 0.0, nullptr)
+                           : ldlt_band_warp<T>(L, N, ld, invd, band, 0, false, 0.0, nullptr);
       ldlt_solve_band_warp<T>(L, N, ld, invd, band, 0, rhs);
       if (threadIdx.x == 0) ok_sh = okw ? 1 : 0;
     }
@@ -1593,45 +1598,51 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
     for (int i = tid; i < NA * ld; i += nthr) L[i] = 0.f;
   }
   __syncthreads();
-  // ---- residual (FP64): R = -(A_H c + alpha t + P^T w (f(U) - g), t.c + alpha s + u~.w (f(U) - g))
+  // ---- residual (FP64): R = -(A_H c + alpha t + P^T w (f(U) - g), t.c + alpha s + u~.w (f(U) - g)),
+  // by the threads t0, t0 + stride, ...; the last warp also forms the alpha row
   const double alpha = S.sa[1];
   const double sig = A.sigma_H;
-  for (int p = tid; p < NH; p += nthr) {
-    int z[3];
-    unknown_coords<D>(p, A.nc, z);
-    const long long off = coarse_offset<D>(z, A.nc);
-    double nb = 0.0;
-    long long mul = 1;
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      nb += S.c[off - mul] + S.c[off + mul];
-      mul *= (A.nc + 1);
-    }
-    const double ahc = sig * (2.0 * D * S.c[off] - nb);
-    rf[p] = (float)(-(ahc + alpha * S.t[p] + node_channel<D, true>(cellsum, A.nc, z, G::RA)));
-  }
-  if (tid >= nthr - 32) {
-    double s2 = 0.0, tc = 0.0;
-    for (int c = lane; c < ncell; c += 32) s2 += cellsum[(long long)c * G::NVAL + G::SA];
-    for (int p = lane; p < NH; p += 32) {
+  auto form_residual = [&](int t0, int stride) {
+    for (int p = t0; p < NH; p += stride) {
       int z[3];
       unknown_coords<D>(p, A.nc, z);
-      tc += S.t[p] * S.c[coarse_offset<D>(z, A.nc)];
-    }
+      const long long off = coarse_offset<D>(z, A.nc);
+      double nb = 0.0;
+      long long mul = 1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-      tc += __shfl_xor_sync(0xffffffffu, tc, o);
+      for (int q = 0; q < D; ++q) {
+        nb += S.c[off - mul] + S.c[off + mul];
+        mul *= (A.nc + 1);
+      }
+      const double ahc = sig * (2.0 * D * S.c[off] - nb);
+      rf[p] = (float)(-(ahc + alpha * S.t[p] + node_channel<D, true>(cellsum, A.nc, z, G::RA)));
     }
-    if (lane == 0) {
-      rf[NH] = (float)(-(tc + alpha * S.sa[0] + s2));
-      if (first) L[NH * ld + NH] = (float)S.sa[0] + (fixedp ? 0.f : s3_sh);
+    if (tid >= nthr - 32) {
+      double s2 = 0.0, tc = 0.0;
+      for (int c = lane; c < ncell; c += 32) s2 += cellsum[(long long)c * G::NVAL + G::SA];
+      for (int p = lane; p < NH; p += 32) {
+        int z[3];
+        unknown_coords<D>(p, A.nc, z);
+        tc += S.t[p] * S.c[coarse_offset<D>(z, A.nc)];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        tc += __shfl_xor_sync(0xffffffffu, tc, o);
+      }
+      if (lane == 0) rf[NH] = (float)(-(tc + alpha * S.sa[0] + s2));
     }
-  }
-  if (first) {
+  };
+  int dropped = 0;
+  bool ok = true;
+  const float* Xuse = L;   // the kept inverse (chord steps)
+  if (!first) {
+    form_residual(tid, nthr);
+    __syncthreads();
+  } else {
     // the Jacobian (fixed point: the Galerkin stiffness) in FP32 from the FP32 channels: the
-    // lower band (neighbours q <= p of unknown p in the 3^d box) and the border row, an entry
-    // per thread
+    // lower band (neighbours q <= p of unknown p in the 3^d box), the border row and the corner,
+    // an entry per thread
     const float sigf = (float)sig;
     for (int e = tid; e < NH * (N3 + 1); e += nthr) {
       const int p = e / (N3 + 1), rr = e - p * (N3 + 1);
@@ -1659,13 +1670,10 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
       else if (dist == 1) v -= sigf;
       L[p * ld + q] = v;
     }
-  }
-  __syncthreads();
-  int dropped = 0;
-  bool ok = true;
-  const float* Xuse = L;   // the kept inverse (chord steps)
-  if (first) {
-    // ---- band LDL^T of J on one warp, then its inverse, a column per thread
+    if (tid == 0) L[NH * ld + NH] = (float)S.sa[0] + (fixedp ? 0.f : s3_sh);
+    __syncthreads();
+    // ---- band LDL^T of J on warp 0 while the other warps form the residual, then the inverse,
+    // a column per thread
     const int band = aug_band<D>(A.nc);
     float* rd = L + (size_t)NA * ld;
     if (tid < 32) {
@@ -1684,6 +1692,8 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
         fac_sh[0] = okw ? 1 : 0;
         fac_sh[1] = dr;
       }
+    } else {
+      form_residual(tid - 32, nthr - 32);
     }
     __syncthreads();
     ok = fac_sh[0] != 0;
