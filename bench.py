@@ -204,8 +204,10 @@ def max_over_ranks(dist, torch, x: float) -> float:
 
 # ------------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(refinements: int, repeats: int, seed: int = 0, dim: int = 2):
-    """FP64 oracle FMG on a bounded sample of the workload: same H, fewer refinements."""
+def oracle_sample(refinements: int, repeats: int, seed: int = 0, dim: int = 2, threads: int | None = 1,
+                  prob=None):
+    """FP64 oracle FMG on a bounded sample of the workload: same H, fewer refinements (or the
+    given problem), BLAS limited to `threads` (None: every core)."""
     try:
         from threadpoolctl import threadpool_limits
     except ImportError:  # pragma: no cover
@@ -213,18 +215,19 @@ def oracle_sample(refinements: int, repeats: int, seed: int = 0, dim: int = 2):
     from oracle import fmg_oracle as O
     from paper_1611_05677_gb300 import workloads as W
 
-    prob = (W.config_large_2d(seed=seed, refinements=refinements) if dim == 2
-            else W.config_3d(seed=seed, refinements=refinements))
+    if prob is None:
+        prob = (W.config_large_2d(seed=seed, refinements=refinements) if dim == 2
+                else W.config_3d(seed=seed, refinements=refinements))
     g = prob.g_nodal()
-    hier = O.build_hierarchy(dim, prob.coarse_cells, refinements)
-    ctx = threadpool_limits(1) if threadpool_limits else None
+    hier = O.build_hierarchy(prob.dim, prob.coarse_cells, prob.refinements)
+    ctx = threadpool_limits(threads) if threadpool_limits else None
     times = []
     try:
         if ctx is not None:
             ctx.__enter__()
         for _ in range(repeats):
             t0 = time.perf_counter()
-            O.fmg(hier, g, prob.f, prob.a, keep_levels=False)
+            O.fmg(hier, g, prob.f, prob.a, m=prob.m_vcycles, keep_levels=False)
             times.append(time.perf_counter() - t0)
     finally:
         if ctx is not None:
@@ -232,13 +235,53 @@ def oracle_sample(refinements: int, repeats: int, seed: int = 0, dim: int = 2):
     return prob.fine_dofs, times
 
 
+def host_cpu():
+    """The host's core count and CPU model (from /proc/cpuinfo where it exists)."""
+    import platform
+
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model in ("", platform.machine()):
+        try:   # Arm hosts: /proc/cpuinfo has no model name; lscpu decodes the part number
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name:"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
 def cpu_baseline(refinements: int = 7, repeats: int = 5, dim: int = 2):
+    """The FP64 oracle on the host: one thread (the reported value), all cores (the oracle is
+    sparse and mostly single-threaded, so this is close), and the small configuration."""
+    from paper_1611_05677_gb300 import workloads as W
+
     dofs, times = oracle_sample(refinements, repeats, dim=dim)
     t = statistics.median(times)
+    dofs_all, times_all = oracle_sample(refinements, repeats, dim=dim, threads=None)
+    small = W.config_small_2d() if dim == 2 else W.config_3d(seed=0, refinements=2)
+    dofs_s, times_s = oracle_sample(0, 20, prob=small)
+    host = host_cpu()
     return {"value": dofs / t, "unit": "DOF/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 numpy/scipy oracle FMG of the same problem family at {refinements} refinements "
                       f"({dofs} fine DOFs), median of {repeats} solves, hierarchy assembly excluded, BLAS "
-                      f"limited to 1 thread"}
+                      f"limited to 1 thread",
+            "host": host,
+            "all_cores": {"value": dofs_all / statistics.median(times_all), "unit": "DOF/s",
+                          "threads": host["nproc"],
+                          "note": "same solves with BLAS on every core; the sparse steps stay single-threaded"},
+            "small_config": {"value": dofs_s / statistics.median(times_s), "unit": "DOF/s", "cores": 1,
+                             "workload": small.name, "fine_dofs": dofs_s, "median_of": 20}}
 
 
 def run_reference(args):
@@ -250,12 +293,14 @@ def run_reference(args):
     dofs, times = oracle_sample(7, args.warmup + args.steps)
     t = statistics.mean(times[args.warmup:]) if args.steps > 0 else statistics.mean(times)
     v = dofs / t
+    host = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": "7 refinements (1,046,529 fine DOFs) per step"},
             "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                             "sample": "FP64 oracle FMG at 7 refinements of the workload's problem family"},
+                             "sample": "FP64 oracle FMG at 7 refinements of the workload's problem family",
+                             "host": host},
             "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
