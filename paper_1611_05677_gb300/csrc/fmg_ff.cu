@@ -145,6 +145,73 @@ __global__ void k_level_start_ff(const double* __restrict__ uc, double* __restri
   if (d32) d32[c] = e;
 }
 
+// The same level start in 2D with each thread walking a strip of rows of one column (lanes
+// along x): the interpolated iterate is formed once per node, the rows above and below are
+// carried along the strip and the x-neighbours come from the adjacent lanes (every lane forms
+// one more value, the one beyond the warp's edge on its side, which lanes 0 and 31 use).  The operations on each node are those of k_level_start_ff, in
+// the same order.  Lanes past the last column store nothing.
+__global__ void k_level_start_ff2(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
+                                  double* __restrict__ b, int n, int kind, ff a, double a64, ff w,
+                                  float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
+                                  int strip) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = i <= n;
+  const int ic = act ? i : n;
+  const int j0 = blockIdx.y * strip;
+  const long long np = n + 1;
+  const long long cp = (n >> 1) + 1;
+  auto inner = [&](int x, int y) { return x > 0 && x < n && y > 0 && y < n; };
+  auto U = [&](int x, int y) { return inner(x, y) ? interp_ff<2>(uc, cp, x, y, 0) : ff{0.f, 0.f}; };
+  ff um = U(ic, j0 - 1), ucur = U(ic, j0);
+  for (int r = 0; r < strip; ++r) {
+    const int j = j0 + r;
+    if (j > n) break;
+    const ff up = U(ic, j + 1);
+    // the edge value without a branch: lane 0 needs x - 1, lane 31 x + 1
+    const ff ve = U(lane == 0 ? ic - 1 : (act ? ic + 1 : n), j);
+    const ff sl{__shfl_up_sync(0xffffffffu, ucur.hi, 1), __shfl_up_sync(0xffffffffu, ucur.lo, 1)};
+    const ff sr{__shfl_down_sync(0xffffffffu, ucur.hi, 1), __shfl_down_sync(0xffffffffu, ucur.lo, 1)};
+    const ff left = lane == 0 ? ve : sl;
+    const ff right = lane == 31 ? ve : sr;
+    const long long c = (long long)j * np + ic;
+    float v = 0.f;
+    ff bv{0.f, 0.f};
+    if (act && inner(ic, j)) {
+      const ff Uc = ucur;
+      ff_store(u + c, Uc);
+      bv = ff_mul(ff_sub(ff_load(g + c), f_ff(kind, a, a64, Uc)), w);
+      float s = 0.f, lo = 0.f;
+#pragma unroll
+      for (int ax = 0; ax < 2; ++ax) {
+        const ff nm = ax == 0 ? left : um;
+        const ff nq = ax == 0 ? right : up;
+        float dm, em, dp, ep, t, et;
+        two_sum(nm.hi, -Uc.hi, dm, em);
+        two_sum(nq.hi, -Uc.hi, dp, ep);
+        two_sum(dm, dp, t, et);
+        float s2, e2;
+        two_sum(s, t, s2, e2);
+        s = s2;
+        lo += ((em + ep) + (et + e2)) + ((nm.lo - Uc.lo) + (nq.lo - Uc.lo));
+      }
+      ff S;
+      two_sum(s, lo, S.hi, S.lo);
+      const ff rr = ff_add(bv, S);
+      v = rr.hi + rr.lo;
+    }
+    if (act) {
+      ff_store(b + c, bv);
+      r32[c] = v;
+      const float e = d32 ? e0 * v : 0.f;
+      e32[c] = e;
+      if (d32) d32[c] = e;
+    }
+    um = ucur;
+    ucur = up;
+  }
+}
+
 __global__ void k_add_f32_ff(double* __restrict__ uff, const float* __restrict__ e, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) ff_store(uff + i, ff_add_f(ff_load(uff + i), e[i]));
@@ -202,10 +269,13 @@ cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, Lev
   const double h = 1.0 / n;
   const double w = dim == 2 ? h * h : h * h * h;
   const dim3 grid(cdiv_u(n + 1, kB), n + 1, dim == 3 ? n + 1 : 1);
-  if (dim == 2)
-    k_level_start_ff<2><<<grid, kB, 0, s>>>(uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w),
-                                            ff{1.f, 0.f}, r32, e32, d32, (float)e0);
-  else
+  if (dim == 2) {
+    // strips of up to 8 rows, shorter on small levels so that the grid keeps ~1000 blocks
+    int strip = 8;
+    while (strip > 1 && (long long)cdiv_u(n + 1, kB) * cdiv_u(n + 1, strip) < 1024) strip >>= 1;
+    k_level_start_ff2<<<dim3(cdiv_u(n + 1, kB), cdiv_u(n + 1, strip)), kB, 0, s>>>(
+        uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w), r32, e32, d32, (float)e0, strip);
+  } else
     k_level_start_ff<3><<<grid, kB, 0, s>>>(uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w),
                                             ff_from_double(h), r32, e32, d32, (float)e0);
   return cudaGetLastError();
