@@ -261,13 +261,83 @@ __device__ __forceinline__ ff neighbour_sum_ff(const double* __restrict__ u, lon
   return neighbour_sum_ff_v<D>(ff_load(u + c), um, up);
 }
 
-// a f(u) in float-float for the polynomial nonlinearities (Sec. 4 examples); the exponential
-// and |u|^{3/2} ones are evaluated in FP64 from the float-float value.
+// 2^k x for an integer k with |k| <= 126 (exact unless the parts underflow).
+__host__ __device__ __forceinline__ ff ff_ldexp(ff x, int k) {
+  const float sc = ldexpf(1.0f, k);
+  return ff{x.hi * sc, x.lo * sc};
+}
+
+// exp(x) - 1 in float-float, from the exponential's own properties: x = k ln2 + r with k the
+// nearest integer to x / ln2 (|r| <= ln2 / 2, r formed in float-float with ln2 split into two
+// FP32 parts), then r = 2^5 s with |s| <= 0.011, expm1(s) by its Taylor series through s^6 (the
+// next term is below 4e-18), five squarings in the form q <- q (2 + q) (that is (1+q)^2 - 1,
+// which keeps the relative accuracy of a small q), and expm1(x) = 2^k q + (2^k - 1).  Relative
+// error about 1e-13 over the range the nonlinearities meet; |x| beyond 80 returns the FP32
+// limit (exp overflows there in FP32 anyway).
+__host__ __device__ __forceinline__ ff ff_expm1(ff x) {
+  // the float-float split hi = fl32(c), lo = fl32(c - hi) of the constants, as exact hex literals
+  const float kLn2Hi = 0x1.62e430p-1f, kLn2Lo = -0x1.05c610p-29f;   // ln 2
+  const float kInvLn2 = 0x1.715476p+0f;                                // fl32(1 / ln 2)
+  if (!(x.hi > -80.f && x.hi < 80.f)) {
+    const float e = expm1f(x.hi);
+    return ff{e, 0.f};
+  }
+  const float kf = rintf(x.hi * kInvLn2);
+  const int k = (int)kf;
+  // r = x - k ln2: both products exact (TwoProduct), then float-float sums
+  float p1, e1, p2, e2;
+  two_prod(kf, kLn2Hi, p1, e1);
+  two_prod(kf, kLn2Lo, p2, e2);
+  ff r = ff_add(x, ff{-p1, -e1});
+  r = ff_add(r, ff{-p2, -e2});
+  const ff sx = ff_ldexp(r, -5);
+  // Taylor series of expm1 at s: s (1 + s (1/2 + s (1/6 + s (1/24 + s (1/120 + s / 720)))))
+  const ff c720 = ff{0x1.6c16c2p-10f, -0x1.27d27ep-35f};   // 1/720
+  const ff c120 = ff{0x1.111112p-7f, -0x1.dddddep-32f};   // 1/120
+  const ff c24 = ff{0x1.555556p-5f, -0x1.555556p-30f};     // 1/24
+  const ff c6 = ff{0x1.555556p-3f, -0x1.555556p-28f};      // 1/6
+  ff q = ff_add(ff_mul(c720, sx), c120);
+  q = ff_add(ff_mul(q, sx), c24);
+  q = ff_add(ff_mul(q, sx), c6);
+  q = ff_add(ff_mul(q, sx), ff{0.5f, 0.f});
+  q = ff_add(ff_mul(q, sx), ff{1.f, 0.f});
+  q = ff_mul(q, sx);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) q = ff_mul(q, ff_add_f(q, 2.0f));
+  if (k == 0) return q;
+  // 2^k (1 + q) - 1 = 2^k q + (2^k - 1); 2^k - 1 is exact in FP32 for |k| <= 24
+  const float pk = ldexpf(1.0f, k) - 1.0f;
+  if (k >= -24 && k <= 24) return ff_add(ff_ldexp(q, k), ff{pk, 0.f});
+  return ff_add_f(ff_ldexp(q, k), pk);
+}
+
+// sqrt(x) for x >= 0 in float-float: the FP32 root s, then one Newton step
+// s + (x - s^2) / (2 s) with the residual x - s^2 formed exactly (TwoProduct).
+__host__ __device__ __forceinline__ ff ff_sqrt(ff x) {
+  if (!(x.hi > 0.f)) return ff{0.f, 0.f};
+  const float s = sqrtf(x.hi);
+  float p, e;
+  two_prod(s, s, p, e);
+  const ff res = ff_add(x, ff{-p, -e});
+  const float corr = (res.hi + res.lo) / (2.0f * s);
+  ff r;
+  quick_two_sum(s, corr, r.hi, r.lo);
+  return r;
+}
+
+__host__ __device__ __forceinline__ ff ff_abs(ff x) { return x.hi < 0.f ? ff_neg(x) : x; }
+
+// a f(u) in float-float for the nonlinearities of Sec. 4 (the mixed path's per-node f, which
+// enters the residual sums): polynomial ones directly, the exponential ones through ff_expm1,
+// sign(u)|u|^{3/2} through ff_sqrt.
 __device__ __forceinline__ ff f_ff(int kind, ff a, double a64, ff u) {
+  (void)a64;
   switch (kind) {
     case FMG_F_CUBIC: return ff_mul(ff_mul(ff_mul(u, u), u), a);
     case FMG_F_LINEAR: return ff_mul(u, a);
-    default: return ff_from_double(f_only<double>(kind, a64, ff_to_double(u)));
+    case FMG_F_EXPM1: return ff_mul(ff_expm1(u), a);
+    case FMG_F_NEG_EXP_NEG: return ff_neg(ff_mul(ff_add_f(ff_expm1(ff_neg(u)), 1.0f), a));   // -a (expm1(-u) + 1)
+    default: return ff_mul(ff_mul(u, ff_sqrt(ff_abs(u))), a);                                   // a u |u|^{1/2}
   }
 }
 

@@ -6,7 +6,8 @@
 // p + e = a b, checked in FP64 where these sums are exact.  The float-float operations must stay
 // within their error bounds, checked against quad-precision sums of the float parts (113 bits hold every sum here exactly): ff_add
 // within 2^-44 |x + y| (also under cancellation), ff_add_fast within 2^-44 (|x| + |y|), ff_mul
-// within 2^-44 |x y|, and the stencil neighbour sum within 2^-42 of its largest input.
+// within 2^-44 |x y|, and the stencil neighbour sum within 2^-42 of its largest input.  The
+// float-float expm1 and sqrt of the nonlinearities are checked against the host's FP64 functions.
 // Prints the number of conversion pairs checked and the number of failed checks; exits
 // non-zero on a failure.
 #include <algorithm>
@@ -113,6 +114,28 @@ int main(int argc, char** argv) {
     const double e_nb = (double)qabs(ld(fmg::neighbour_sum_ff_v<3>(uc, um, up)) - exact);
     if (e_nb > u42 * (double)big) fail("neighbour_sum_ff_v", e_nb, u42 * (double)big);
   }
+  // the float-float exponential and root of the mixed path's nonlinearities, against the host's
+  // FP64 expm1 and sqrt (errors near 2^-53, far below the bounds checked): expm1 within 2^-42
+  // relative over [-12, 12] (small arguments included, where expm1 keeps its relative accuracy),
+  // sqrt within 2^-44 relative
+  std::uniform_real_distribution<double> X(-12.0, 12.0);
+  const double u42r = std::ldexp(1.0, -42);
+  for (long long i = 0; i < rounds / 4; ++i) {
+    double x = X(rng);
+    if (i % 3 == 1) x = std::ldexp(U(rng), -Small(rng));            // small arguments
+    const ff fx = fmg::ff_from_double(x);
+    const double xe = (double)fx.hi + (double)fx.lo;                   // the argument as represented
+    const double want = std::expm1(xe);
+    const double got = (double)fmg::ff_expm1(fx).hi + (double)fmg::ff_expm1(fx).lo;
+    if (std::fabs(got - want) > u42r * std::fabs(want)) fail("ff_expm1", std::fabs(got - want), u42r * std::fabs(want));
+    const double ax = std::fabs(xe) * 7.0;
+    const ff fa = fmg::ff_from_double(ax);
+    const double wr = std::sqrt((double)fa.hi + (double)fa.lo);
+    const ff r = fmg::ff_sqrt(fa);
+    const double gr = (double)r.hi + (double)r.lo;
+    if (std::fabs(gr - wr) > u44 * wr) fail("ff_sqrt", std::fabs(gr - wr), u44 * wr);
+  }
+  if (fmg::ff_expm1(ff{0.f, 0.f}).hi != 0.f) fail("ff_expm1(0)", 1.0, 0.0);
   const float sp[] = {0.f, -0.f, 1e-40f, -1e-40f, INFINITY, -INFINITY, NAN, 1.f, -1.f, 3.4e38f, 1.2e-38f};
   for (float a : sp)
     for (float b : sp) {
