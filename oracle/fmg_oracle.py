@@ -180,10 +180,23 @@ class Level:
     extra: dict = field(default_factory=dict)
 
 
-def assemble_level(dim: int, n: int, chunk: int = 1 << 20) -> Level:
+def element_coefficients(coef: np.ndarray, dim: int, nc: int, Xs: np.ndarray) -> np.ndarray:
+    """A on each element: the diagonal of the coarse cell of T_H (1/H = nc cells per side)
+    that holds the element's centroid; coef has one row of d diagonal entries per coarse cell,
+    x fastest."""
+    cen = Xs.mean(axis=1)                                    # (M, d) centroids
+    cell = np.minimum(np.floor(cen * nc).astype(np.int64), nc - 1)
+    cid = cell @ np.array([nc ** a for a in range(dim)])
+    return coef[cid]                                         # (M, d)
+
+
+def assemble_level(dim: int, n: int, chunk: int = 1 << 20, coef: np.ndarray | None = None,
+                   coef_cells: int = 0) -> Level:
     """Element-by-element P1 stiffness and vertex-rule weights (eq. 2.3, 2.6).
 
-    S_ab = sum_K |K| grad(lam_a).grad(lam_b);  w_a = sum_{K ni a} |K|/(d+1).
+    S_ab = sum_K |K| grad(lam_a).A_K grad(lam_b);  w_a = sum_{K ni a} |K|/(d+1).
+    A_K = I, or with `coef` (shape (coef_cells^d, d)) the diagonal SPD coefficient of eq. (2.1)
+    that is constant on each cell of the coarsest mesh T_H (coef_cells = 1/H cells per side).
     Entries that cancel exactly in exact arithmetic (the diagonal couplings
     of these meshes) come out as round-off of size ~1e-17 |S_aa|; they are set
     to zero so that the sparsity is the true one.
@@ -197,7 +210,11 @@ def assemble_level(dim: int, n: int, chunk: int = 1 << 20) -> Level:
     for s0 in range(0, simp.shape[0], chunk):
         sc = simp[s0:s0 + chunk]
         grads, vol = barycentric_gradients(X[sc])
-        Ke = vol[:, None, None] * np.einsum("mad,mbd->mab", grads, grads)
+        if coef is None:
+            Ke = vol[:, None, None] * np.einsum("mad,mbd->mab", grads, grads)
+        else:
+            Ak = element_coefficients(coef, dim, coef_cells, X[sc])
+            Ke = vol[:, None, None] * np.einsum("mad,md,mbd->mab", grads, Ak, grads)
         rows.append(np.repeat(sc, dim + 1, axis=1).ravel())
         cols.append(np.tile(sc, (1, dim + 1)).ravel())
         vals.append(Ke.ravel())
@@ -295,11 +312,13 @@ class Hierarchy:
         return self.levels[k - 1]
 
 
-def build_hierarchy(dim: int, coarse_cells: int, refinements: int) -> Hierarchy:
+def build_hierarchy(dim: int, coarse_cells: int, refinements: int, coef: np.ndarray | None = None) -> Hierarchy:
+    """Levels 1..refinements+1 of T_H (1/H = coarse_cells); coef: the diagonal coefficient per
+    cell of T_H (see assemble_level), the same bilinear form on every level."""
     levs = []
     for k in range(refinements + 1):
         n = coarse_cells << k
-        lev = assemble_level(dim, n)
+        lev = assemble_level(dim, n, coef=coef, coef_cells=coarse_cells)
         if k > 0:
             lev.P = prolongation(dim, n // 2)
         levs.append(lev)

@@ -643,3 +643,70 @@ def test_chord_is_slower_than_newton_far_from_the_solution():
     assert c_info.newton_iters > n_info.newton_iters
     assert abs(c_info.alpha - n_info.alpha) <= 1e-7
     assert np.max(np.abs(uc - un)) <= 1e-7 * np.max(np.abs(un))
+
+
+# ---------------------------------------------------------------------------
+# Variable SPD coefficient A(x) of eq. (2.1): diagonal, constant on each cell of T_H
+# ---------------------------------------------------------------------------
+
+
+def _cell_coefficient(dim, nc, seed=3):
+    return np.random.default_rng(seed).uniform(0.5, 2.0, size=(nc ** dim, dim))
+
+
+@pytest.mark.parametrize("dim,nc,r", [(2, 4, 3), (3, 2, 2)])
+def test_coefficient_keeps_the_galerkin_identity(dim, nc, r):
+    """With A constant on each cell of T_H every level discretizes the same bilinear form on
+    nested P1 spaces, so A_{k-1} = P_k^T A_k P_k holds exactly (as for A = I)."""
+    hier = O.build_hierarchy(dim, nc, r, coef=_cell_coefficient(dim, nc))
+    for k in range(2, r + 2):
+        A, P, Ac = hier.level(k).A, hier.level(k).P, hier.level(k - 1).A
+        assert abs(P.T @ A @ P - Ac).max() <= 1e-13 * abs(Ac).max()
+
+
+@pytest.mark.parametrize("dim,nc,n", [(2, 4, 16), (3, 2, 8)])
+def test_coefficient_energy_of_linear_functions(dim, nc, n):
+    """a(u, u) = sum_K |K| grad(u).A_K grad(u): for u = g.x (boundary nodes included) that is
+    sum over the cells of T_H of |cell| sum_a A_a g_a^2, in closed form."""
+    coef = _cell_coefficient(dim, nc)
+    lev = O.assemble_level(dim, n, coef=coef, coef_cells=nc)
+    g = np.random.default_rng(7).standard_normal(dim)
+    u = (lev.nodes.astype(np.float64) / n) @ g
+    exact = np.sum(coef * g ** 2) / nc ** dim
+    assert abs(u @ (lev.S @ u) - exact) <= 1e-13 * exact
+
+
+@pytest.mark.parametrize("dim,nc,n", [(2, 4, 16), (3, 2, 8)])
+def test_coefficient_stiffness_is_an_axis_stencil(dim, nc, n):
+    """A diagonal A keeps the couplings of the right-triangle and Kuhn meshes on the axis
+    edges: only 2d+1 entries per row, non-positive off the diagonal, zero row sums over all
+    nodes; A = c I scales the textbook stencil by c."""
+    coef = _cell_coefficient(dim, nc)
+    lev = O.assemble_level(dim, n, coef=coef, coef_cells=nc)
+    S = lev.S.tocoo()
+    dist = np.abs(lev.nodes[S.row] - lev.nodes[S.col]).sum(axis=1)
+    assert np.all(dist <= 1)
+    assert np.all(S.data[dist == 1] < 0)
+    assert np.max(np.abs(np.asarray(lev.S.sum(axis=1)))) <= 1e-13 * np.abs(lev.S.diagonal()).max()
+    c = np.full((nc ** dim, dim), 1.7)
+    A1 = O.assemble_level(dim, n).A
+    Ac = O.assemble_level(dim, n, coef=c, coef_cells=nc).A
+    assert abs(Ac - 1.7 * A1).max() <= 1e-13 * abs(Ac).max()
+
+
+@pytest.mark.parametrize("dim,nc,r", [(2, 8, 3), (3, 4, 2)])
+def test_fmg_with_coefficient_reaches_discretization_accuracy(dim, nc, r):
+    """Theorem 3.2 with a variable coefficient: the algebraic error stays below a tenth of the
+    discretization error, estimated by Richardson as ||u_bar_h - P u_bar_2h|| / 3 (random-mode g,
+    no closed-form solution)."""
+    coef = _cell_coefficient(dim, nc)
+    prob = W.Problem(dim=dim, coarse_cells=nc, refinements=r, f="cubic", a=1.0,
+                     g_modes=[((1,) * dim, 3.0), ((2, 1, 3)[:dim], -2.0)])
+    hier = O.build_hierarchy(dim, nc, r, coef=coef)
+    g = prob.g_nodal()
+    res = O.fmg(hier, g, prob.f, prob.a)
+    lev, levc = hier.level(r + 1), hier.level(r)
+    ub, _ = O.newton_full(lev, O.load_vector(lev, g), prob.f, prob.a, U0=res.u[-1])
+    ubc, _ = O.newton_full(levc, O.load_vector(levc, O.restrict_nodal(g, dim, prob.n_fine, levc.n)), prob.f, prob.a)
+    e_disc = O.discrete_l2(lev, ub - lev.P @ ubc) / 3.0
+    assert O.discrete_l2(lev, res.u[-1] - ub) <= 0.1 * e_disc
