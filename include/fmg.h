@@ -112,6 +112,18 @@ typedef struct {
   int level1_maxit;    /* level-1 Newton iteration cap (<= 64) */
   int smoother;        /* fmg_smoother of the multigrid cycles */
   int nonlinear;       /* fmg_nonlinear_solver of the augmented problem (3.6) */
+  const double* coefficient;
+                       /* the diffusion coefficient A(x) of eq. (2.1): NULL for A = I, or a host
+                          array of coarse_cells^dim rows of dim doubles, the diagonal entries
+                          (a_11, .., a_dd) of A on each cell of T_H (cell (cx, cy[, cz]) at row
+                          cx + nc cy [+ nc^2 cz], nc = coarse_cells; entry order x, y[, z]).  A is
+                          diagonal, SPD (every entry finite and > 0, else FMG_ERR_INVALID) and
+                          constant on each coarse cell, so every level's P1 stiffness keeps the
+                          (2d+1)-point pattern with a weight per mesh edge and the Galerkin
+                          identity A_H = P^T A_h P holds level to level.  fmg_create copies the
+                          array (the pointer is not kept).  Taken with the red-black smoother
+                          only (FMG_SMOOTHER_CHEBYSHEV: FMG_ERR_INVALID); batches and the server
+                          take A = I only. */
 } fmg_params;
 
 typedef struct {

@@ -38,6 +38,7 @@ struct fmg_ctx {
   float* Ainv32 = nullptr;   // FP32 copy of A_1^{-1} for the FP32 one-CTA cycles
   DevState* st = nullptr;
   AugBuffers ab = {};
+  VarCoef vc = {};   // the coefficient A(x) on the device (vc.a64 == nullptr: A = I)
   void* arena = nullptr;
   size_t arena_bytes = 0;
   bool own_arena = false;
@@ -111,6 +112,13 @@ const char* validate(const fmg_params* p) {
     return "unknown nonlinear solver";
   if (p->smoother == FMG_SMOOTHER_CHEBYSHEV && (p->nu_pre > kMaxCheb || p->nu_post > kMaxCheb))
     return "Chebyshev smoothing takes at most 16 steps";
+  if (p->coefficient) {
+    if (p->smoother != FMG_SMOOTHER_RBGS) return "a variable coefficient takes the red-black smoother";
+    const long long n = ipow(p->coarse_cells, p->dim) * p->dim;
+    for (long long i = 0; i < n; ++i)
+      if (!(p->coefficient[i] > 0.0) || !std::isfinite(p->coefficient[i]))
+        return "coefficient entries must be finite and > 0";
+  }
   return nullptr;
 }
 
@@ -178,7 +186,16 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
   const size_t items = cfg.partial_items;
   double* partials = (double*)take(2 * items * aug_nvals(p->dim) * 8);
   double* cfin = (double*)take((ipow(p->coarse_cells + 1, p->dim) + 1) * 8);
+  // the coefficient table in FP64, FP32 and float-float (a row of d entries per cell of T_H)
+  const long long ncoef = ipow(p->coarse_cells, p->dim) * p->dim;
+  double* a64 = (double*)take(ncoef * 8);
+  float* a32 = (float*)take(ncoef * 4);
+  double* aff = (double*)take(ncoef * 8);
   if (c && base) {
+    c->vc.a64 = p->coefficient ? a64 : nullptr;
+    c->vc.a32 = p->coefficient ? a32 : nullptr;
+    c->vc.aff = p->coefficient ? aff : nullptr;
+    c->vc.nc = p->coarse_cells;
     c->Ainv = Ainv;
     c->Ainv32 = Ainv32;
     c->st = st;
@@ -283,10 +300,15 @@ cudaError_t cheb_steps(fmg_ctx* c, int j, T* u, T* alt, T* d, const T* b, int st
   return cudaSuccess;
 }
 
+// The coefficient for the launch calls: nullptr when A = I (the constant-coefficient kernels).
+const VarCoef* vcp(const fmg_ctx* c) { return c->vc.a64 ? &c->vc : nullptr; }
+
 // Largest level handled by the one-CTA coarse cycle: its level arrays (u and b of every level
-// up to it) must fit in shared memory; 2D up to 64 cells per side, 3D up to 16.
+// up to it) must fit in shared memory; 2D up to 64 cells per side, 3D up to 16.  With a
+// variable coefficient every level above 1 runs the per-level kernels.
 template <typename T>
 int coarse_cycle_top(const fmg_ctx* c) {
+  if (c->vc.a64) return 1;
   const int nmax = c->p.dim == 2 ? 64 : 16;
   int j = 1;
   while (j < c->nlev && c->geo[j].n <= nmax &&
@@ -308,6 +330,12 @@ bool fuse_first_step(const fmg_ctx* c, int j) {
   return c->p.smoother == FMG_SMOOTHER_CHEBYSHEV && c->p.nu_pre >= 1 && j > coarse_cycle_top<T>(c);
 }
 
+// Whether the mixed cycle on level k runs the fused 2D FP32 kernels (red-black smoothing with
+// the constant-coefficient stencil; their buffers exist).
+bool fused_cycle_used(const fmg_ctx* c, int k) {
+  return c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS && !c->vc.a64;
+}
+
 cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = false, bool started = false) {
   const int dim = c->p.dim;
   cudaStream_t s = c->stream;
@@ -327,22 +355,22 @@ cudaError_t vcycle(fmg_ctx* c, int j, double* u, const double* b, bool top = fal
   for (int it = 0; !cheb && it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    TRY(launch_rbgs<double>(dim, gf, u, b, 0, s));
-    TRY(launch_rbgs<double>(dim, gf, u, b, 1, s));
+    TRY(launch_rbgs<double>(dim, gf, u, b, 0, s, vcp(c)));
+    TRY(launch_rbgs<double>(dim, gf, u, b, 1, s, vcp(c)));
     TRY(tend(c, slot));
   }
   const bool fuse = fuse_first_step<double>(c, j - 1);
   double* uc0 = fuse ? cheb_start(c->u[j - 2], c->ua[j - 2], c->p.nu_pre) : c->u[j - 2];
   TRY(launch_residual_restrict<double, double>(dim, gf, u, b, gc, c->b[j - 2], uc0, s,
-                                               fuse ? c->dd[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0));
+                                               fuse ? c->dd[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0, vcp(c)));
   TRY(vcycle(c, j - 1, c->u[j - 2], c->b[j - 2], false, fuse));
   TRY(launch_prolong<double, double>(dim, gc, c->u[j - 2], gf, u, 1, s));
   if (cheb) TRY(cheb_steps<double>(c, j, u, c->ua[j - 1], c->dd[j - 1], b, c->p.nu_post, top));
   for (int it = 0; !cheb && it < c->p.nu_post; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    TRY(launch_rbgs<double>(dim, gf, u, b, 1, s));
-    TRY(launch_rbgs<double>(dim, gf, u, b, 0, s));
+    TRY(launch_rbgs<double>(dim, gf, u, b, 1, s, vcp(c)));
+    TRY(launch_rbgs<double>(dim, gf, u, b, 0, s, vcp(c)));
     TRY(tend(c, slot));
   }
   return cudaSuccess;
@@ -405,14 +433,14 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
   for (int it = 0; !cheb && it < c->p.nu_pre; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    TRY(launch_rbgs<float>(dim, gf, u, b, 0, s));
-    TRY(launch_rbgs<float>(dim, gf, u, b, 1, s));
+    TRY(launch_rbgs<float>(dim, gf, u, b, 0, s, vcp(c)));
+    TRY(launch_rbgs<float>(dim, gf, u, b, 1, s, vcp(c)));
     TRY(tend(c, slot));
   }
   const bool fuse = fuse_first_step<float>(c, j - 1);
   float* uc0 = fuse ? cheb_start(c->u32[j - 2], c->u32b[j - 2], c->p.nu_pre) : c->u32[j - 2];
   TRY(launch_residual_restrict<float, float>(dim, gf, u, b, gc, c->b32[j - 2], uc0, s,
-                                             fuse ? c->d32[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0));
+                                             fuse ? c->d32[j - 2] : nullptr, fuse ? cheb_e0(c, j - 1) : 0.0, vcp(c)));
   TRY(vcycle32(c, j - 1, false, fuse));
   // the prolongation u += P e_c, fused into the first post-smoothing Chebyshev step when that
   // is a plain step (not the top level's single step fused with the update)
@@ -433,8 +461,8 @@ cudaError_t vcycle32(fmg_ctx* c, int j, bool top = false, bool started = false, 
   for (int it = 0; !cheb && it < c->p.nu_post; ++it) {
     int slot = -1;
     if (top) TRY(tbegin(c, FMG_KT_SMOOTH_TOP, j, &slot));
-    TRY(launch_rbgs<float>(dim, gf, u, b, 1, s));
-    TRY(launch_rbgs<float>(dim, gf, u, b, 0, s));
+    TRY(launch_rbgs<float>(dim, gf, u, b, 1, s, vcp(c)));
+    TRY(launch_rbgs<float>(dim, gf, u, b, 0, s, vcp(c)));
     TRY(tend(c, slot));
   }
   if (u64_top && top_ff) TRY(launch_add_f32_ff(gf, u64_top, u, s));
@@ -451,8 +479,8 @@ cudaError_t top_cycle(fmg_ctx* c, int k, double* u, const double* b) {
   const bool fuse = fuse_first_step<float>(c, k);
   float* e0buf = fuse ? cheb_start(c->u32[k - 1], c->u32b[k - 1], c->p.nu_pre) : c->u32[k - 1];
   TRY(launch_residual_to_f32(c->p.dim, g, u, b, c->b32[k - 1], e0buf, c->stream,
-                             fuse ? c->d32[k - 1] : nullptr, fuse ? cheb_e0(c, k) : 0.0));
-  if (c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS) return vcycle32_fused(c, k, u);
+                             fuse ? c->d32[k - 1] : nullptr, fuse ? cheb_e0(c, k) : 0.0, vcp(c)));
+  if (fused_cycle_used(c, k)) return vcycle32_fused(c, k, u);
   if (k > coarse_cycle_top<float>(c)) return vcycle32(c, k, true, fuse, u);
   TRY(vcycle32(c, k, true));
   TRY(launch_add_f32(g, c->p.dim, u, c->u32[k - 1], c->stream));
@@ -470,8 +498,8 @@ cudaError_t top_cycle_ff(fmg_ctx* c, int k, double* u, const double* b, bool res
   float* e0buf = fuse ? cheb_start(c->u32[k - 1], c->u32b[k - 1], c->p.nu_pre) : c->u32[k - 1];
   if (!residual_ready)
     TRY(launch_residual_ff(c->p.dim, g, u, b, c->b32[k - 1], e0buf, c->stream, fuse ? c->d32[k - 1] : nullptr,
-                           fuse ? cheb_e0(c, k) : 0.0));
-  if (c->u32b[k - 1] && c->p.smoother == FMG_SMOOTHER_RBGS) return vcycle32_fused(c, k, u, true);
+                           fuse ? cheb_e0(c, k) : 0.0, vcp(c)));
+  if (fused_cycle_used(c, k)) return vcycle32_fused(c, k, u, true);
   if (k > coarse_cycle_top<float>(c)) return vcycle32(c, k, true, fuse, u, true);
   TRY(vcycle32(c, k, true));
   TRY(launch_add_f32_ff(g, u, c->u32[k - 1], c->stream));
@@ -491,7 +519,7 @@ cudaError_t correction_step(fmg_ctx* c, int k, double* u) {
   TRY(tbegin(c, FMG_KT_AUGMENTED, k, &slot_aug));
   TRY(launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->g[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
                        c->p.newton_maxit, c->p.precision == FMG_PREC_MIXED, c->ab, c->st, k - 1, c->stream,
-                       c->cluster_aug, c->p.nonlinear == FMG_NONLINEAR_FIXED_POINT ? 1 : 0));
+                       c->cluster_aug, c->p.nonlinear == FMG_NONLINEAR_FIXED_POINT ? 1 : 0, 0, vcp(c)));
   TRY(tend(c, slot_aug));
   return tend(c, slot_step);
 }
@@ -511,7 +539,7 @@ cudaError_t correction_step_ff(fmg_ctx* c, int k, bool out_f64, bool from_coarse
     float* e0buf = fuse ? cheb_start(c->u32[k - 1], c->u32b[k - 1], c->p.nu_pre) : c->u32[k - 1];
     TRY(launch_level_start_ff(c->p.dim, c->geo[k - 2], c->u[k - 2], g, u, c->gf[k - 1], c->b[k - 1], c->p.f,
                               c->p.f_scale, c->b32[k - 1], e0buf, fuse ? c->d32[k - 1] : nullptr,
-                              fuse ? cheb_e0(c, k) : 0.0, c->stream));
+                              fuse ? cheb_e0(c, k) : 0.0, c->stream, vcp(c)));
   } else {
     TRY(launch_nonlinear_rhs_ff(c->p.dim, g, u, c->gf[k - 1], c->b[k - 1], c->p.f, c->p.f_scale, c->stream));
   }
@@ -520,7 +548,7 @@ cudaError_t correction_step_ff(fmg_ctx* c, int k, bool out_f64, bool from_coarse
   TRY(tbegin(c, FMG_KT_AUGMENTED, k, &slot_aug));
   TRY(launch_augmented(c->p.dim, c->p.coarse_cells, k, g, u, c->gf[k - 1], c->p.f, c->p.f_scale, c->p.newton_tol,
                        c->p.newton_maxit, true, c->ab, c->st, k - 1, c->stream, c->cluster_aug,
-                       c->p.nonlinear == FMG_NONLINEAR_FIXED_POINT ? 1 : 0, out_f64 ? 1 : 0));
+                       c->p.nonlinear == FMG_NONLINEAR_FIXED_POINT ? 1 : 0, out_f64 ? 1 : 0, vcp(c)));
   TRY(tend(c, slot_aug));
   return tend(c, slot_step);
 }
@@ -532,7 +560,7 @@ cudaError_t run_fmg(fmg_ctx* c) {
   // the mixed path keeps its level data as float-float; its last step leaves the FP64 result
   const bool mixed = c->p.precision == FMG_PREC_MIXED;
   TRY(launch_level1_newton(c->p.dim, c->geo[0], c->g[0], c->u[0], c->p.f, c->p.f_scale, c->p.level1_tol,
-                           c->p.level1_maxit, mixed, c->st, c->stream, mixed && c->nlev > 1));
+                           c->p.level1_maxit, mixed, c->st, c->stream, mixed && c->nlev > 1, vcp(c)));
   for (int k = 2; k <= c->nlev; ++k) {
     // u^{(0)}_{h_k} = u_{h_{k-1}}: the natural inclusion (the mixed path forms it in the pass
     // that starts its first correction step)
@@ -724,8 +752,29 @@ fmg_status fmg_create(const fmg_params* p, const double* g_fine, int g_on_device
   e = cudaMemsetAsync(c->arena, 0, need, c->stream);
   if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   if (s == FMG_OK) s = load_rhs(c, g_fine, g_on_device);
+  // the coefficient table: FP64 as given, its FP32 rounding and its float-float split
+  std::vector<double> coef64, coefff;
+  std::vector<float> coef32;
+  if (s == FMG_OK && p->coefficient) {
+    const long long n = ipow(p->coarse_cells, p->dim) * p->dim;
+    coef64.assign(p->coefficient, p->coefficient + n);
+    coef32.resize(n);
+    coefff.resize(n);
+    for (long long i = 0; i < n; ++i) {
+      const float hi = (float)coef64[i];
+      const float lo = (float)(coef64[i] - (double)hi);
+      coef32[i] = hi;
+      std::memcpy(reinterpret_cast<char*>(&coefff[i]), &hi, 4);
+      std::memcpy(reinterpret_cast<char*>(&coefff[i]) + 4, &lo, 4);
+    }
+    e = cudaMemcpyAsync((void*)c->vc.a64, coef64.data(), n * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void*)c->vc.a32, coef32.data(), n * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void*)c->vc.aff, coefff.data(), n * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("coefficient upload: ") + cudaGetErrorString(e));
+  }
+  c->p.coefficient = nullptr;   // the caller's array is not kept
   if (s == FMG_OK) {
-    e = launch_coarse_inverse(p->dim, c->geo[0], c->Ainv, c->st, c->stream);
+    e = launch_coarse_inverse(p->dim, c->geo[0], c->Ainv, c->st, c->stream, vcp(c));
     const long long n1 = ipow(p->coarse_cells - 1, p->dim);
     if (e == cudaSuccess) e = launch_to_f32(c->Ainv, c->Ainv32, n1 * n1, c->stream);
     if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("coarse inverse: ") + cudaGetErrorString(e));
@@ -805,6 +854,7 @@ fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** o
     if (!cs[i]) return fail(nullptr, FMG_ERR_INVALID, "NULL context in batch");
     if (dev < 0) dev = cs[i]->device;
     if (cs[i]->device != dev) return fail(nullptr, FMG_ERR_INVALID, "batch contexts on different devices");
+    if (cs[i]->vc.a64) return fail(nullptr, FMG_ERR_INVALID, "batches take A = I only (no coefficient)");
   }
   fmg_batch* b = new (std::nothrow) fmg_batch();
   if (!b) return fail(nullptr, FMG_ERR_OOM, "host allocation failed");
@@ -1067,8 +1117,8 @@ fmg_status fmg_op_smooth(fmg_ctx* c, int level, const double* b, double* u, int 
   }
   const int first = order ? 1 : 0;
   for (int i = 0; i < sweeps; ++i) {
-    CK(c, launch_rbgs<double>(c->p.dim, c->geo[level - 1], u, b, first, c->stream));
-    CK(c, launch_rbgs<double>(c->p.dim, c->geo[level - 1], u, b, 1 - first, c->stream));
+    CK(c, launch_rbgs<double>(c->p.dim, c->geo[level - 1], u, b, first, c->stream, vcp(c)));
+    CK(c, launch_rbgs<double>(c->p.dim, c->geo[level - 1], u, b, 1 - first, c->stream, vcp(c)));
   }
   return read_state(c, nullptr, false);
 }
@@ -1084,8 +1134,8 @@ fmg_status fmg_op_smooth_f32(fmg_ctx* c, int level, const float* b, float* u, in
   }
   const int first = order ? 1 : 0;
   for (int i = 0; i < sweeps; ++i) {
-    CK(c, launch_rbgs<float>(c->p.dim, c->geo[level - 1], u, b, first, c->stream));
-    CK(c, launch_rbgs<float>(c->p.dim, c->geo[level - 1], u, b, 1 - first, c->stream));
+    CK(c, launch_rbgs<float>(c->p.dim, c->geo[level - 1], u, b, first, c->stream, vcp(c)));
+    CK(c, launch_rbgs<float>(c->p.dim, c->geo[level - 1], u, b, 1 - first, c->stream, vcp(c)));
   }
   return read_state(c, nullptr, false);
 }
@@ -1093,7 +1143,7 @@ fmg_status fmg_op_smooth_f32(fmg_ctx* c, int level, const float* b, float* u, in
 fmg_status fmg_op_residual(fmg_ctx* c, int level, const double* b, const double* u, double* r) {
   if (fmg_status s = check_level(c, level, 1)) return s;
   if (!b || !u || !r) return fail(c, FMG_ERR_INVALID, "NULL array");
-  CK(c, launch_residual(c->p.dim, c->geo[level - 1], u, b, r, c->stream));
+  CK(c, launch_residual(c->p.dim, c->geo[level - 1], u, b, r, c->stream, vcp(c)));
   return read_state(c, nullptr, false);
 }
 
@@ -1127,7 +1177,8 @@ fmg_status fmg_op_level1_solve(fmg_ctx* c, double* u, fmg_stats* st) {
   if (!u) return fail(c, FMG_ERR_INVALID, "NULL array");
   CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream));
   CK(c, launch_level1_newton(c->p.dim, c->geo[0], c->g[0], u, c->p.f, c->p.f_scale, c->p.level1_tol,
-                             c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream));
+                             c->p.level1_maxit, c->p.precision == FMG_PREC_MIXED, c->st, c->stream, false,
+                             vcp(c)));
   return read_state(c, st, false);
 }
 

@@ -20,7 +20,8 @@ unsigned cdiv_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); 
 // e = d = e0 r32.
 template <int D>
 __global__ void k_residual_ff(const double* __restrict__ u, const double* __restrict__ b, int n, ff sigma,
-                              float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0) {
+                              float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
+                              VarCoef vc, int ls) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y, l = D == 3 ? blockIdx.z : 0;
   if (i > n) return;
@@ -28,7 +29,19 @@ __global__ void k_residual_ff(const double* __restrict__ u, const double* __rest
   const long long c = ((long long)l * np + j) * np + i;
   float v = 0.f;
   if (i > 0 && i < n && j > 0 && j < n && (D == 2 || (l > 0 && l < n))) {
-    ff S = neighbour_sum_ff<D>(u, c, np, pl);
+    ff S;
+    if (vc.a64) {
+      const long long o[3] = {1, np, pl};
+      ff nb[2 * D];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        nb[2 * ax] = ff_load(u + c - o[ax]);
+        nb[2 * ax + 1] = ff_load(u + c + o[ax]);
+      }
+      S = weighted_neighbour_sum_ff<D>(ff_load(u + c), nb, vc, ls, i, j, l);
+    } else {
+      S = neighbour_sum_ff<D>(u, c, np, pl);
+    }
     if (D == 3) S = ff_mul(S, sigma);
     const ff r = ff_add(ff_load(b + c), S);
     v = r.hi + r.lo;
@@ -99,7 +112,7 @@ template <int D>
 __global__ void k_level_start_ff(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
                                  double* __restrict__ b, int n, int kind, ff a, double a64, ff w, ff sigma,
                                  float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32,
-                                 float e0) {
+                                 float e0, VarCoef vc, int ls) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y, l = D == 3 ? blockIdx.z : 0;
   if (i > n) return;
@@ -117,23 +130,32 @@ __global__ void k_level_start_ff(const double* __restrict__ uc, double* __restri
     bv = ff_mul(ff_sub(ff_load(g + c), f_ff(kind, a, a64, U)), w);
     // sum_k (u_k - u_c) as in neighbour_sum_ff, from the interpolated neighbours (zero on the
     // boundary)
-    float s = 0.f, lo = 0.f;
+    ff nbv[2 * D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
       const int dx = ax == 0, dy = ax == 1, dz = ax == 2;
-      const ff um = inner(i - dx, j - dy, l - dz) ? interp_ff<D>(uc, cp, i - dx, j - dy, l - dz) : ff{0.f, 0.f};
-      const ff up = inner(i + dx, j + dy, l + dz) ? interp_ff<D>(uc, cp, i + dx, j + dy, l + dz) : ff{0.f, 0.f};
-      float dm, em, dp, ep, t, et;
-      two_sum(um.hi, -U.hi, dm, em);
-      two_sum(up.hi, -U.hi, dp, ep);
-      two_sum(dm, dp, t, et);
-      float s2, e2;
-      two_sum(s, t, s2, e2);
-      s = s2;
-      lo += ((em + ep) + (et + e2)) + ((um.lo - U.lo) + (up.lo - U.lo));
+      nbv[2 * ax] = inner(i - dx, j - dy, l - dz) ? interp_ff<D>(uc, cp, i - dx, j - dy, l - dz) : ff{0.f, 0.f};
+      nbv[2 * ax + 1] = inner(i + dx, j + dy, l + dz) ? interp_ff<D>(uc, cp, i + dx, j + dy, l + dz) : ff{0.f, 0.f};
     }
     ff S;
-    two_sum(s, lo, S.hi, S.lo);
+    if (vc.a64) {
+      S = weighted_neighbour_sum_ff<D>(U, nbv, vc, ls, i, j, l);
+    } else {
+      float s = 0.f, lo = 0.f;
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        const ff um = nbv[2 * ax], up = nbv[2 * ax + 1];
+        float dm, em, dp, ep, t, et;
+        two_sum(um.hi, -U.hi, dm, em);
+        two_sum(up.hi, -U.hi, dp, ep);
+        two_sum(dm, dp, t, et);
+        float s2, e2;
+        two_sum(s, t, s2, e2);
+        s = s2;
+        lo += ((em + ep) + (et + e2)) + ((um.lo - U.lo) + (up.lo - U.lo));
+      }
+      two_sum(s, lo, S.hi, S.lo);
+    }
     if (D == 3) S = ff_mul(S, sigma);
     const ff r = ff_add(bv, S);
     v = r.hi + r.lo;
@@ -153,7 +175,7 @@ __global__ void k_level_start_ff(const double* __restrict__ uc, double* __restri
 __global__ void k_level_start_ff2(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
                                   double* __restrict__ b, int n, int kind, ff a, double a64, ff w,
                                   float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
-                                  int strip) {
+                                  int strip, VarCoef vc, int ls) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool act = i <= n;
@@ -181,22 +203,27 @@ __global__ void k_level_start_ff2(const double* __restrict__ uc, double* __restr
       const ff Uc = ucur;
       ff_store(u + c, Uc);
       bv = ff_mul(ff_sub(ff_load(g + c), f_ff(kind, a, a64, Uc)), w);
-      float s = 0.f, lo = 0.f;
-#pragma unroll
-      for (int ax = 0; ax < 2; ++ax) {
-        const ff nm = ax == 0 ? left : um;
-        const ff nq = ax == 0 ? right : up;
-        float dm, em, dp, ep, t, et;
-        two_sum(nm.hi, -Uc.hi, dm, em);
-        two_sum(nq.hi, -Uc.hi, dp, ep);
-        two_sum(dm, dp, t, et);
-        float s2, e2;
-        two_sum(s, t, s2, e2);
-        s = s2;
-        lo += ((em + ep) + (et + e2)) + ((nm.lo - Uc.lo) + (nq.lo - Uc.lo));
-      }
       ff S;
-      two_sum(s, lo, S.hi, S.lo);
+      if (vc.a64) {
+        const ff nb[4] = {left, right, um, up};
+        S = weighted_neighbour_sum_ff<2>(Uc, nb, vc, ls, ic, j, 0);
+      } else {
+        float s = 0.f, lo = 0.f;
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) {
+          const ff nm = ax == 0 ? left : um;
+          const ff nq = ax == 0 ? right : up;
+          float dm, em, dp, ep, t, et;
+          two_sum(nm.hi, -Uc.hi, dm, em);
+          two_sum(nq.hi, -Uc.hi, dp, ep);
+          two_sum(dm, dp, t, et);
+          float s2, e2;
+          two_sum(s, t, s2, e2);
+          s = s2;
+          lo += ((em + ep) + (et + e2)) + ((nm.lo - Uc.lo) + (nq.lo - Uc.lo));
+        }
+        two_sum(s, lo, S.hi, S.lo);
+      }
       const ff rr = ff_add(bv, S);
       v = rr.hi + rr.lo;
     }
@@ -231,14 +258,23 @@ __global__ void k_ff_to_f64(const double* __restrict__ s, double* __restrict__ d
 
 // ============================================================================ launchers
 
+// fine cells per coarse cell of a level with n cells per side, as a power of two (VarCoef)
+int vc_level_shift(const VarCoef* vc, int n) {
+  int ls = 0;
+  while (vc && vc->a64 && (vc->nc << ls) < n) ++ls;
+  return ls;
+}
+
 cudaError_t launch_residual_ff(int dim, LevelGeo g, const double* u_ff, const double* b_ff, float* r32, float* e32,
-                               cudaStream_t s, float* d32, double e0) {
+                               cudaStream_t s, float* d32, double e0, const VarCoef* vc) {
   const int n = g.n;
   const dim3 grid(cdiv_u(n + 1, kB), n + 1, dim == 3 ? n + 1 : 1);
+  const VarCoef v = vc ? *vc : VarCoef{};
+  const int ls = vc_level_shift(vc, n);
   if (dim == 2)
-    k_residual_ff<2><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff{1.f, 0.f}, r32, e32, d32, (float)e0);
+    k_residual_ff<2><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff{1.f, 0.f}, r32, e32, d32, (float)e0, v, ls);
   else
-    k_residual_ff<3><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff_from_double(1.0 / n), r32, e32, d32, (float)e0);
+    k_residual_ff<3><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff_from_double(1.0 / n), r32, e32, d32, (float)e0, v, ls);
   return cudaGetLastError();
 }
 
@@ -263,9 +299,11 @@ cudaError_t launch_prolong_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGe
 
 cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo g, double* u_ff,
                                   const double* g_ff, double* b_ff, int kind, double a, float* r32, float* e32,
-                                  float* d32, double e0, cudaStream_t s) {
+                                  float* d32, double e0, cudaStream_t s, const VarCoef* vc) {
   const int n = g.n;
   if (gc.n * 2 != n) return cudaErrorInvalidValue;
+  const VarCoef v = vc ? *vc : VarCoef{};
+  const int ls = vc_level_shift(vc, n);
   const double h = 1.0 / n;
   const double w = dim == 2 ? h * h : h * h * h;
   const dim3 grid(cdiv_u(n + 1, kB), n + 1, dim == 3 ? n + 1 : 1);
@@ -274,10 +312,11 @@ cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, Lev
     int strip = 8;
     while (strip > 1 && (long long)cdiv_u(n + 1, kB) * cdiv_u(n + 1, strip) < 1024) strip >>= 1;
     k_level_start_ff2<<<dim3(cdiv_u(n + 1, kB), cdiv_u(n + 1, strip)), kB, 0, s>>>(
-        uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w), r32, e32, d32, (float)e0, strip);
+        uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w), r32, e32, d32, (float)e0, strip, v,
+        ls);
   } else
     k_level_start_ff<3><<<grid, kB, 0, s>>>(uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w),
-                                            ff_from_double(h), r32, e32, d32, (float)e0);
+                                            ff_from_double(h), r32, e32, d32, (float)e0, v, ls);
   return cudaGetLastError();
 }
 

@@ -248,6 +248,35 @@ __host__ __device__ __forceinline__ ff neighbour_sum_ff_v(ff uc, const ff* um, c
   return r;
 }
 
+// The variable-coefficient form (VarCoef, A(x) != I): sum_e w_e (u_e - u_c) over the 2d axis
+// edges, nb[] in the order x-, x+, y-, y+ (, z-, z+); the differences are formed exactly (TwoSum
+// on the leading parts), weighted by the float-float edge sums of the coefficient table and
+// summed in float-float, and the total is scaled by the weights' common factor (1/2 in 2D,
+// 1/6 in 3D).
+template <int D>
+__device__ __forceinline__ ff weighted_neighbour_sum_ff(ff uc, const ff* nb, const VarCoef& vc, int ls, int i, int j,
+                                                        int l) {
+  ff W[2 * D];
+  edge_weights<D, ff>(
+      vc.nc, ls, i, j, l,
+      [&](int k) {
+        const float2 v = *reinterpret_cast<const float2*>(vc.aff + k);
+        return ff{v.x, v.y};
+      },
+      [](ff a, ff b) { return ff_add(a, b); }, [](ff x) { return x; }, W);
+  ff S{0.f, 0.f};
+#pragma unroll
+  for (int e = 0; e < 2 * D; ++e) {
+    float dh, de;
+    two_sum(nb[e].hi, -uc.hi, dh, de);
+    ff d;
+    quick_two_sum(dh, de + (nb[e].lo - uc.lo), d.hi, d.lo);
+    S = ff_add(S, ff_mul(d, W[e]));
+  }
+  if (D == 2) return ff{0.5f * S.hi, 0.5f * S.lo};
+  return ff_mul(S, ff{0x1.555556p-3f, -0x1.555556p-28f});   // x 1/6
+}
+
 // The same at node c of a nodal array (axis strides 1, np, pl).
 template <int D>
 __device__ __forceinline__ ff neighbour_sum_ff(const double* __restrict__ u, long long c, long long np, long long pl) {

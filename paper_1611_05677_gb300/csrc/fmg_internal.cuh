@@ -54,6 +54,76 @@ __host__ __device__ inline long long ipow(long long b, int e) {
   return r;
 }
 
+// Variable SPD coefficient A(x) of -div(A grad u) (Sec. 2, eq. 2.1): diagonal and constant on
+// each cell of T_H (nc cells per side), one row of d entries per cell, x fastest; a64 == nullptr
+// means A = I.  On the right-triangle and Kuhn meshes a diagonal A couples a simplex's vertices
+// only along its axis path edges, so the stiffness stays a (2d+1)-point stencil, with a weight
+// per axis edge: in 2D an x edge from (i, j) bounds fine cells (i, j) and (i, j-1), a y edge from
+// (i, j) cells (i, j) and (i-1, j), each through one triangle, so w = (A(c1) + A(c2)) / 2; in 3D
+// an x edge from (i, j, l) is a path edge of 2 Kuhn tetrahedra of fine cubes (i, j, l) and
+// (i, j-1, l-1) and of 1 of cubes (i, j-1, l) and (i, j, l-1) (y and z alike by symmetry), so
+// w = (2 A(c1) + 2 A(c2) + A(c3) + A(c4)) / 6, the stiffness being h times these sums.  A fine
+// cell (p, q[, r]) of a level with 2^ls fine cells per coarse cell lies in coarse cell
+// (p >> ls, q >> ls[, r >> ls]).  With A = I every weight is 1.
+struct VarCoef {
+  const double* a64;   // FP64 entries, nullptr: A = I
+  const float* a32;    // FP32 entries
+  const double* aff;   // float-float entries (hi, lo) in 8-byte slots
+  int nc;              // cells per side of T_H
+};
+
+template <int D>
+__host__ __device__ __forceinline__ int coef_index(int nc, int cx, int cy, int cz, int axis) {
+  return (D == 2 ? cy * nc + cx : (cz * nc + cy) * nc + cx) * D + axis;
+}
+
+// The weights of the 2d axis edges at node (i, j[, l]) of a level with 2^ls fine cells per
+// coarse cell, in the order x-, x+, y-, y+ (, z-, z+), from the entries val(k) (an index into the
+// table as coef_index gives it), combined by add(x, y) and scaled by half(x) (x / 2) or sixth(x)
+// (x / 6): the precision-agnostic form the FP64, FP32 and float-float kernels share.
+template <int D, typename V, typename Val, typename Add, typename Scale>
+__host__ __device__ __forceinline__ void edge_weights(int nc, int ls, int i, int j, int l, Val val, Add add,
+                                                      Scale scale, V* w) {
+  auto C = [&](int p, int q, int r, int axis) { return val(coef_index<D>(nc, p >> ls, q >> ls, r >> ls, axis)); };
+  if constexpr (D == 2) {
+    // x edge from (p, q): cells (p, q), (p, q-1); y edge from (p, q): cells (p, q), (p-1, q)
+    auto wx = [&](int p, int q) { return scale(add(C(p, q, 0, 0), C(p, q - 1, 0, 0))); };
+    auto wy = [&](int p, int q) { return scale(add(C(p, q, 0, 1), C(p - 1, q, 0, 1))); };
+    w[0] = wx(i - 1, j);
+    w[1] = wx(i, j);
+    w[2] = wy(i, j - 1);
+    w[3] = wy(i, j);
+  } else {
+    auto tw = [&](V a, V b, V c, V d) { return scale(add(add(add(a, a), add(b, b)), add(c, d))); };
+    auto wx = [&](int p, int q, int r) {
+      return tw(C(p, q, r, 0), C(p, q - 1, r - 1, 0), C(p, q - 1, r, 0), C(p, q, r - 1, 0));
+    };
+    auto wy = [&](int p, int q, int r) {
+      return tw(C(p, q, r, 1), C(p - 1, q, r - 1, 1), C(p - 1, q, r, 1), C(p, q, r - 1, 1));
+    };
+    auto wz = [&](int p, int q, int r) {
+      return tw(C(p, q, r, 2), C(p - 1, q - 1, r, 2), C(p - 1, q, r, 2), C(p, q - 1, r, 2));
+    };
+    w[0] = wx(i - 1, j, l);
+    w[1] = wx(i, j, l);
+    w[2] = wy(i, j - 1, l);
+    w[3] = wy(i, j, l);
+    w[4] = wz(i, j, l - 1);
+    w[5] = wz(i, j, l);
+  }
+}
+
+// The edge weights in FP64 / FP32 (T = double reads a64, T = float reads a32).
+template <int D, typename T>
+__host__ __device__ __forceinline__ void edge_weights_t(const VarCoef& vc, int ls, int i, int j, int l, T* w) {
+  const T* tab = nullptr;
+  if constexpr (sizeof(T) == 8) tab = reinterpret_cast<const T*>(vc.a64);
+  else tab = reinterpret_cast<const T*>(vc.a32);
+  edge_weights<D, T>(
+      vc.nc, ls, i, j, l, [&](int k) { return tab[k]; }, [](T x, T y) { return x + y; },
+      [](T x) { return D == 2 ? x * T(0.5) : x / T(6); }, w);
+}
+
 // Nonlinearity a*f(u) and its derivative (Sec. 4 examples; monotone for a > 0).
 template <typename T>
 __device__ __forceinline__ void f_eval(int kind, T a, T u, T& F, T& Fp) {
@@ -107,21 +177,25 @@ __device__ __forceinline__ T f_only(int kind, T a, T u) {
 
 // red-black Gauss-Seidel half sweep of colour `colour` (0 red, 1 black) on level geometry g
 template <typename T>
-cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaStream_t s);
+cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaStream_t s,
+                        const VarCoef* vc = nullptr);
 
 // b_c = P^T (b_f - A_f u_f), u_c = 0 (coarse arrays of geometry gc, fine gf).  With d_c the
 // coarse level's first Chebyshev step from zero is fused in: u_c = d_c = e0 b_c.
 template <typename TF, typename TC>
 cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const TF* b_f, LevelGeo gc,
-                                     TC* b_c, TC* u_c, cudaStream_t s, TC* d_c = nullptr, double e0 = 0.0);
+                                     TC* b_c, TC* u_c, cudaStream_t s, TC* d_c = nullptr, double e0 = 0.0,
+                                     const VarCoef* vc = nullptr);
 
 // mixed path: b32 = (float)(b - A u) in FP64, u32 = 0 (same level); with d32 the first
 // Chebyshev step from zero is fused in: u32 = d32 = e0 b32
 cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const double* b, float* r32,
-                                   float* e32, cudaStream_t s, float* d32 = nullptr, double e0 = 0.0);
+                                   float* e32, cudaStream_t s, float* d32 = nullptr, double e0 = 0.0,
+                                   const VarCoef* vc = nullptr);
 
 // r = b - A u (FP64, same level)
-cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* b, double* r, cudaStream_t s);
+cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* b, double* r, cudaStream_t s,
+                            const VarCoef* vc = nullptr);
 
 // u_f += P e_c  (add = 1) or u_f = P e_c (add = 0)
 template <typename TF, typename TC>
@@ -200,13 +274,14 @@ cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 
 // level-1 setup: Ainv = A_1^{-1} (dense, N_1 x N_1) by Cholesky; flags on failure
-cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s);
+cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s,
+                                  const VarCoef* vc = nullptr);
 
 // level-1 exact semilinear solve (Algorithm 3.2 step 1): Newton, dense, one CTA
 // out_ff: u is written as float-float (the mixed solve's level data)
 cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double* u, int kind, double a,
                                  double tol, int maxit, bool f32_factor, DevState* st, cudaStream_t s,
-                                 bool out_ff = false);
+                                 bool out_ff = false, const VarCoef* vc = nullptr);
 
 // Augmented problem on V_H + span{u~} (Algorithm 3.1 step 2, eq. 3.6): one cooperative
 // persistent kernel: precompute, Newton iterations, final update u = alpha u~ + P_{H->k} c.
@@ -235,7 +310,7 @@ int aug_nvals(int dim);
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
                              DevState* st, int level_index, cudaStream_t s, int cluster_size = 0, int fixed_point = 0,
-                             int out_f64 = 0);
+                             int out_f64 = 0, const VarCoef* vc = nullptr);
 // Largest usable cluster size (<= 16, <= number of coarse cells) for the cluster variant, 0 if none.
 int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem);
 
@@ -243,7 +318,7 @@ int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem);
 // right-hand side b and g stored as float-float pairs in the 8-byte slots of the FP64 arrays.
 // Residual r = b - A_k u into FP32 (with d32: the first Chebyshev step from zero, e = d = e0 r).
 cudaError_t launch_residual_ff(int dim, LevelGeo g, const double* u_ff, const double* b_ff, float* r32, float* e32,
-                               cudaStream_t s, float* d32 = nullptr, double e0 = 0.0);
+                               cudaStream_t s, float* d32 = nullptr, double e0 = 0.0, const VarCoef* vc = nullptr);
 // b = w (g - a f(u)) (eq. 3.4, vertex rule)
 cudaError_t launch_nonlinear_rhs_ff(int dim, LevelGeo g, const double* u_ff, const double* g_ff, double* b_ff,
                                     int kind, double a, cudaStream_t s);
@@ -255,7 +330,7 @@ cudaError_t launch_add_f32_ff(LevelGeo g, double* u_ff, const float* e32, cudaSt
 // first residual r32 = b - A u with e32 (and d32 with e0) as launch_residual_ff writes them.
 cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo g, double* u_ff,
                                   const double* g_ff, double* b_ff, int kind, double a, float* r32, float* e32,
-                                  float* d32, double e0, cudaStream_t s);
+                                  float* d32, double e0, cudaStream_t s, const VarCoef* vc = nullptr);
 // conversions (in place allowed)
 cudaError_t launch_ff_from_f64(const double* src, double* dst_ff, long long n, cudaStream_t s);
 cudaError_t launch_ff_to_f64(const double* src_ff, double* dst, long long n, cudaStream_t s);

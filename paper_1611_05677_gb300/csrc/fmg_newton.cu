@@ -273,30 +273,53 @@ __device__ __forceinline__ long long node_of(int r, int m, int dim) {
   return ((long long)l * np + j) * np + i;
 }
 
-// Writes the dense A_1 = sigma (2d on the diagonal, -1 for axis neighbours) into M.
-__device__ void fill_stiffness(double* M, int N, int ld, int m, int dim, double sigma) {
+// The 2d edge weights at level-1 unknown p (interior node of T_H, order as node_of): the
+// coefficient's weights at level shift 0 (every cell of T_H is a coefficient cell).
+__device__ __forceinline__ void level1_weights(const VarCoef& vc, int p, int m, int dim, double* w) {
+  const int i = p % m + 1, j = (p / m) % m + 1, l = dim == 3 ? p / (m * m) + 1 : 0;
+  if (dim == 2)
+    edge_weights_t<2, double>(vc, 0, i, j, l, w);
+  else
+    edge_weights_t<3, double>(vc, 0, i, j, l, w);
+}
+
+// Entry (p, q) of the level-1 stiffness A_1: sigma times the sum of p's edge weights on the
+// diagonal, minus sigma times the weight of their common edge for axis neighbours, zero
+// otherwise (A = I: every weight 1, i.e. 2d sigma and -sigma).
+__device__ double level1_entry(int p, int q, int m, int dim, double sigma, const VarCoef& vc) {
+  int dist = 0, axis = 0, dir = 0;
+  int pp = p, qq = q;
+  for (int a = 0; a < dim; ++a) {
+    const int d = qq % m - pp % m;
+    if (d != 0) {
+      axis = a;
+      dir = d;
+    }
+    dist += abs(d);
+    pp /= m;
+    qq /= m;
+  }
+  if (dist > 1) return 0.0;
+  if (!vc.a64) return dist == 0 ? sigma * 2 * dim : -sigma;
+  double w[6];
+  level1_weights(vc, p, m, dim, w);
+  if (dist == 1) return -sigma * w[2 * axis + (dir > 0 ? 1 : 0)];
+  double sw = 0.0;
+  for (int e = 0; e < 2 * dim; ++e) sw += w[e];
+  return sigma * sw;
+}
+
+// Writes the dense A_1 into M.
+__device__ void fill_stiffness(double* M, int N, int ld, int m, int dim, double sigma, const VarCoef& vc) {
   for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
     const int p = idx / N, q = idx % N;
-    double v = 0.0;
-    if (p == q) {
-      v = sigma * 2 * dim;
-    } else {
-      int dist = 0;
-      int pp = p, qq = q;
-      for (int a = 0; a < dim; ++a) {
-        dist += abs(pp % m - qq % m);
-        pp /= m;
-        qq /= m;
-      }
-      if (dist == 1) v = -sigma;
-    }
-    M[p * ld + q] = v;
+    M[p * ld + q] = level1_entry(p, q, m, dim, sigma, vc);
   }
 }
 
 // Level-1 setup: LDL^T of A_1 once, then A_1^{-1} column by column (one thread per column).
 // Launched with 64 threads.
-__global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, DevState* st) {
+__global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, DevState* st, VarCoef vc) {
   extern __shared__ double sm[];
   const int m = n1 - 1;
   const int N = dim == 2 ? m * m : m * m * m;
@@ -304,7 +327,7 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
   double* M = sm;
   double* rd = M + (size_t)N * ld;
   const double sigma = dim == 2 ? 1.0 : 1.0 / n1;
-  fill_stiffness(M, N, ld, m, dim, sigma);
+  fill_stiffness(M, N, ld, m, dim, sigma, vc);
   __syncthreads();
   if (threadIdx.x < 32) {
     const bool ok = ldlt_band_warp<double>(M, N, ld, rd, dim == 2 ? m : m * m, 0, false, 0.0, nullptr);
@@ -335,7 +358,7 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
 // FP64 residual corrects, so the iteration converges to the same FP64 solution).
 template <typename T>
 __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
-                                double a, double tol, int maxit, DevState* st, int out_ff) {
+                                double a, double tol, int maxit, DevState* st, int out_ff, VarCoef vc) {
   extern __shared__ double sm[];
   const int m = n1 - 1;
   const int N = dim == 2 ? m * m : m * m * m;
@@ -361,17 +384,34 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       double F, D;
       f_eval<double>(kind, a, U[p], F, D);
-      // (A U)_p from the stencil: sigma (2d U_p - sum of interior axis neighbours)
-      double nb = 0.0;
-      int rem = p, mul = 1;
-      for (int ax = 0; ax < dim; ++ax) {
-        const int c = rem % m;
-        rem /= m;
-        if (c > 0) nb += U[p - mul];
-        if (c < m - 1) nb += U[p + mul];
-        mul *= m;
+      // (A U)_p from the stencil: sigma (2d U_p - sum of interior axis neighbours), or with
+      // the coefficient sigma sum_e w_e (U_p - U_e) (boundary neighbours are zero)
+      double au;
+      if (vc.a64) {
+        double wt[6];
+        level1_weights(vc, p, m, dim, wt);
+        double acc = 0.0;
+        int rem = p, mul = 1;
+        for (int ax = 0; ax < dim; ++ax) {
+          const int c = rem % m;
+          rem /= m;
+          acc += wt[2 * ax] * (U[p] - (c > 0 ? U[p - mul] : 0.0));
+          acc += wt[2 * ax + 1] * (U[p] - (c < m - 1 ? U[p + mul] : 0.0));
+          mul *= m;
+        }
+        au = sigma * acc;
+      } else {
+        double nb = 0.0;
+        int rem = p, mul = 1;
+        for (int ax = 0; ax < dim; ++ax) {
+          const int c = rem % m;
+          rem /= m;
+          if (c > 0) nb += U[p - mul];
+          if (c < m - 1) nb += U[p + mul];
+          mul *= m;
+        }
+        au = sigma * (2.0 * dim * U[p] - nb);
       }
-      const double au = sigma * (2.0 * dim * U[p] - nb);
       rhs[p] = -(au + w * F - w * g[node_of(p, m, dim)]);
       Fp[p] = w * D;
     }
@@ -381,18 +421,7 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
     for (int idx = threadIdx.x; idx < N * (band + 1); idx += blockDim.x) {
       const int p = idx / (band + 1), q = p - idx % (band + 1);
       if (q < 0) continue;
-      double v = 0.0;
-      if (p == q) {
-        v = sigma * 2 * dim + Fp[p];
-      } else {
-        int dist = 0, pp = p, qq = q;
-        for (int ax = 0; ax < dim; ++ax) {
-          dist += abs(pp % m - qq % m);
-          pp /= m;
-          qq /= m;
-        }
-        if (dist == 1) v = -sigma;
-      }
+      const double v = level1_entry(p, q, m, dim, sigma, vc) + (p == q ? Fp[p] : 0.0);
       L[p * ld + q] = (T)v;
     }
     __syncthreads();
@@ -505,7 +534,7 @@ __device__ __forceinline__ int pair_index(int NV, int v, int u) {
 }
 
 struct AugArgs {
-  int dim, nc, s, n, kind, maxit, level_index, bpc, chunk;
+  int dim, nc, s, ls, n, kind, maxit, level_index, bpc, chunk;   // s = 2^ls fine cells per coarse cell
   int fixed_point;      // 1: fixed-point iteration (Galerkin stiffness only, no Jacobian)
   int out_f64;          // mixed path: the update writes u as FP64 (the solve's result) instead of float-float
   int split_update;     // 1: the final update is left to k_aug_update (block 0 writes c and alpha to cfin)
@@ -520,6 +549,7 @@ struct AugArgs {
   double* cfin;         // [(nc+1)^d] c, then alpha (split_update)
   long long bar_spins;  // polls of the grid barrier before it times out
   int bar_skip;         // test hook: this block skips its first barrier arrival (-1: none)
+  VarCoef vc;           // the coefficient A(x) (vc.a64 == nullptr: A = I)
 };
 
 // Bounded grid barrier for the cooperative launch (all blocks co-resident).  A waiting block
@@ -605,6 +635,56 @@ __device__ __forceinline__ int column_segments(const int* o, int s, Seg<D>* sg) 
 
 enum { kFirst = 0, kNewton = 1, kUpdate = 2 };
 
+// (A_H c) at the interior coarse node z (offset off in the coarse nodal array c, boundary
+// zero): sigma_H (2d c - sum of axis neighbours), or with the coefficient
+// sigma_H sum_e w_e (c - c_e) (T_H is the coefficient's own mesh: level shift 0).
+template <int D>
+__device__ __forceinline__ double coarse_apply(const AugArgs& A, const double* c, long long off, const int* z) {
+  const double sig = A.sigma_H;
+  long long mul = 1;
+  if (A.vc.a64) {
+    double w[2 * D];
+    edge_weights_t<D, double>(A.vc, 0, z[0], z[1], D == 3 ? z[2] : 0, w);
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      acc += w[2 * q] * (c[off] - c[off - mul]) + w[2 * q + 1] * (c[off] - c[off + mul]);
+      mul *= (A.nc + 1);
+    }
+    return sig * acc;
+  }
+  double nb = 0.0;
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    nb += c[off - mul] + c[off + mul];
+    mul *= (A.nc + 1);
+  }
+  return sig * (2.0 * D * c[off] - nb);
+}
+
+// Entry of A_H between the interior coarse node z and its box neighbour z + dv (|dv|_1 = dist):
+// the diagonal, an axis neighbour's coupling, or zero (dist >= 2: the diagonal couplings of
+// these meshes vanish for a diagonal coefficient).
+template <int D>
+__device__ __forceinline__ double coarse_stiffness(const AugArgs& A, const int* z, const int* dv, int dist) {
+  const double sig = A.sigma_H;
+  if (dist > 1) return 0.0;
+  if (!A.vc.a64) return dist == 0 ? sig * 2.0 * D : -sig;
+  double w[2 * D];
+  edge_weights_t<D, double>(A.vc, 0, z[0], z[1], D == 3 ? z[2] : 0, w);
+  if (dist == 1) {
+    int e = 0;
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+      if (dv[q] != 0) e = 2 * q + (dv[q] > 0 ? 1 : 0);
+    return -sig * w[e];
+  }
+  double sw = 0.0;
+#pragma unroll
+  for (int e = 0; e < 2 * D; ++e) sw += w[e];
+  return sig * sw;
+}
+
 // Mixed path, passes after the first: the increment dF = a (f(u~ + d) - f(u~)) and a f'(u~ + d)
 // in FP32, from closed forms that do not cancel (d is the small Newton correction
 // (alpha - 1) u~ + P c).  The residual sums of the first pass (FP64, at U = u~) plus these
@@ -658,9 +738,9 @@ struct FirstMoments {
 // and up[ax], fine z coordinate z.  CUBIC selects a f(u) = a u^3 at compile time (no branch in
 // the node's arithmetic); otherwise the nonlinearity is chosen by A.kind.  The Jacobian
 // moments are formed also in the fixed-point iteration, which does not read them.
-template <int D, bool CUBIC>
+template <int D, bool CUBIC, bool VC>
 __device__ __forceinline__ void first_node(const AugArgs& A, FirstMoments& m, ff U, ff G, const ff* um, const ff* up,
-                                           int z) {
+                                           int z, int x, int y, int zc) {
   ff F;
   float Fpf;
   if (CUBIC) {
@@ -685,8 +765,21 @@ __device__ __forceinline__ void first_node(const AugArgs& A, FirstMoments& m, ff
   m.e0 += du;
   m.e1 = fmaf(du, zf, m.e1);
   m.js = fmaf(du, U.hi, m.js);
-  // A_k u~ = sigma (2d u - sum of axis neighbours) = -sigma * neighbour sum
-  ff nsum = neighbour_sum_ff_v<D>(U, um, up);
+  // A_k u~ = sigma (2d u - sum of axis neighbours) = -sigma * neighbour sum; with the
+  // coefficient -sigma * sum_e w_e (u_e - u) at fine node (x, z) / (x, y, z) (z = zc + local z)
+  ff nsum;
+  if constexpr (VC) {
+    ff nb[2 * D];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      nb[2 * ax] = um[ax];
+      nb[2 * ax + 1] = up[ax];
+    }
+    const int za = zc + z;
+    nsum = weighted_neighbour_sum_ff<D>(U, nb, A.vc, A.ls, x, D == 2 ? za : y, D == 3 ? za : 0);
+  } else {
+    nsum = neighbour_sum_ff_v<D>(U, um, up);
+  }
   if (D == 3) nsum = ff_mul(nsum, A.sigma_ff);
   const ff au = ff_neg(nsum);
   m.t0 = ff_add_fast(m.t0, au);
@@ -699,9 +792,9 @@ __device__ __forceinline__ void first_node(const AugArgs& A, FirstMoments& m, ff
 // neighbours at the B nodes -- is loaded into registers before the arithmetic, so the batch
 // costs one memory latency; loads past the run (cnt < B) repeat its last valid node and their
 // nodes are not summed.
-template <int D, bool CUBIC, int B>
+template <int D, bool CUBIC, int B, bool VC>
 __device__ __forceinline__ void first_batch(const AugArgs& A, FirstMoments& m, long long off, int z, int cnt,
-                                            long long zstride, long long np) {
+                                            long long zstride, long long np, int x, int y, int zc) {
   constexpr int NI = D - 1;                  // in-plane axes: x (and y in 3D); the column is the last
   const long long io[2] = {1, np};
   ff uz[B + 2], gv[B], um[NI > 0 ? NI : 1][B], up[NI > 0 ? NI : 1][B];
@@ -728,26 +821,28 @@ __device__ __forceinline__ void first_batch(const AugArgs& A, FirstMoments& m, l
     }
     nm[D - 1] = uz[q];
     nq[D - 1] = uz[q + 2];
-    first_node<D, CUBIC>(A, m, uz[q + 1], gv[q], nm, nq, z + q);
+    first_node<D, CUBIC, VC>(A, m, uz[q + 1], gv[q], nm, nq, z + q, x, y, zc);
   }
 }
 
 // The mixed first pass over the column nodes z0..z1 (offset `off` at z0), in register batches
-// of B nodes (B smaller in 3D, whose nodes have two more in-plane neighbours to hold).
-template <int D, bool CUBIC>
+// of B nodes (B smaller in 3D, whose nodes have two more in-plane neighbours to hold).  x, y:
+// the column's fine in-plane coordinates; zc: the fine z of local z = 0 (the coefficient's
+// edge weights need the node's position).
+template <int D, bool CUBIC, bool VC>
 __device__ __forceinline__ void first_pass_segment(const AugArgs& A, long long off, int z0, int z1,
-                                                   long long zstride, FirstMoments& m) {
+                                                   long long zstride, FirstMoments& m, int x, int y, int zc) {
   constexpr int B = D == 2 ? 8 : 4;
   const long long np = A.n + 1;
   m.q0 = m.q1 = m.sa = m.t0 = m.t1 = m.ss = ff{0.f, 0.f};
   m.d0 = m.d1 = m.d2 = m.e0 = m.e1 = m.js = 0.f;
   for (int z = z0; z <= z1; z += B, off += B * zstride)
-    first_batch<D, CUBIC, B>(A, m, off, z, min(B, z1 - z + 1), zstride, np);
+    first_batch<D, CUBIC, B, VC>(A, m, off, z, min(B, z1 - z + 1), zstride, np, x, y, zc);
 }
 
 // The fine pass of one block: columns of its cell, chunk by chunk.  `acc` holds the
 // per-thread channel rows ([NVAL][NT] doubles), zero on entry.
-template <int D, bool JF32>
+template <int D, bool JF32, bool VC = false>
 __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double* cv, double alpha, int cell,
                           int bic) {
   using G = Aug<D, JF32>;
@@ -879,9 +974,9 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
         // residual and t/s moments are formed in float-float (FP32 error-free transformations,
         // no FP64 arithmetic per node); the Jacobian moments in FP32 from the leading parts
         if (A.kind == FMG_F_CUBIC)
-          first_pass_segment<D, true>(A, off, z0, z1, zstride, fm);
+          first_pass_segment<D, true, VC>(A, off, z0, z1, zstride, fm, x, y, zc);
         else
-          first_pass_segment<D, false>(A, off, z0, z1, zstride, fm);
+          first_pass_segment<D, false, VC>(A, off, z0, z1, zstride, fm, x, y, zc);
         D0 = fm.d0;
         D1 = fm.d1;
         D2 = fm.d2;
@@ -925,14 +1020,28 @@ __device__ void fine_pass(const AugArgs& A, int phase, double* acc, const double
           JSv += du * uj;
         }
         if (phase == kFirst) {
-          double nb;
-          if constexpr (D == 2) {
-            nb = (A.u[off - 1] + A.u[off + 1]) + (A.u[off - zstride] + A.u[off + zstride]);
+          double au;
+          if constexpr (VC) {
+            // sigma sum_e w_e (u - u_e) with the coefficient's edge weights at the node
+            double wt[2 * D];
+            const int za = zc + z;
+            edge_weights_t<D, double>(A.vc, A.ls, x, D == 2 ? za : y, D == 3 ? za : 0, wt);
+            const long long o3[3] = {1, np, zstride};
+            double acc2 = 0.0;
+#pragma unroll
+            for (int ax = 0; ax < D; ++ax)
+              acc2 += wt[2 * ax] * (ut - A.u[off - o3[ax]]) + wt[2 * ax + 1] * (ut - A.u[off + o3[ax]]);
+            au = A.sigma_k * acc2;
           } else {
-            nb = ((A.u[off - 1] + A.u[off + 1]) + (A.u[off - np] + A.u[off + np])) +
-                 (A.u[off - zstride] + A.u[off + zstride]);
+            double nb;
+            if constexpr (D == 2) {
+              nb = (A.u[off - 1] + A.u[off + 1]) + (A.u[off - zstride] + A.u[off + zstride]);
+            } else {
+              nb = ((A.u[off - 1] + A.u[off + 1]) + (A.u[off - np] + A.u[off + np])) +
+                   (A.u[off - zstride] + A.u[off + zstride]);
+            }
+            au = A.sigma_k * (2.0 * D * ut - nb);
           }
-          const double au = A.sigma_k * (2.0 * D * ut - nb);
           T0 += au;
           T1 = fma(au, zd, T1);
           SSv = fma(au, ut, SSv);
@@ -1606,15 +1715,7 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
     for (int p = t0; p < NH; p += stride) {
       int z[3];
       unknown_coords<D>(p, A.nc, z);
-      const long long off = coarse_offset<D>(z, A.nc);
-      double nb = 0.0;
-      long long mul = 1;
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        nb += S.c[off - mul] + S.c[off + mul];
-        mul *= (A.nc + 1);
-      }
-      const double ahc = sig * (2.0 * D * S.c[off] - nb);
+      const double ahc = coarse_apply<D>(A, S.c, coarse_offset<D>(z, A.nc), z);
       rf[p] = (float)(-(ahc + alpha * S.t[p] + node_channel<D, true>(cellsum, A.nc, z, G::RA)));
     }
     if (tid >= nthr - 32) {
@@ -1652,12 +1753,13 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
         L[NH * ld + p] = (float)S.t[p] + (fixedp ? 0.f : node_channel_f<D>(cellsum, A.nc, z, G::JB));
         continue;
       }
-      int zq[3], q = 0, mulq = 1, dist = 0, r2 = rr;
+      int zq[3], dv[3], q = 0, mulq = 1, dist = 0, r2 = rr;
       bool okq = true;
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
         const int d = r2 % 3 - 1;
         r2 /= 3;
+        dv[ax] = d;
         zq[ax] = z[ax] + d;
         if (zq[ax] < 1 || zq[ax] > A.nc - 1) okq = false;
         q += (zq[ax] - 1) * mulq;
@@ -1666,8 +1768,12 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
       }
       if (!okq || q > p) continue;
       float v = fixedp ? 0.f : pair_channel_f<D>(cellsum, A.nc, z, zq);
-      if (dist == 0) v += sigf * (float)(2 * D);
-      else if (dist == 1) v -= sigf;
+      if (A.vc.a64) {
+        v += (float)coarse_stiffness<D>(A, z, dv, dist);
+      } else {
+        if (dist == 0) v += sigf * (float)(2 * D);
+        else if (dist == 1) v -= sigf;
+      }
       L[p * ld + q] = v;
     }
     if (tid == 0) L[NH * ld + NH] = (float)S.sa[0] + (fixedp ? 0.f : s3_sh);
@@ -1766,18 +1872,10 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
       }
     }
     __syncthreads();
-    const double sig = A.sigma_H;
     for (int p = tid; p < NH; p += blockDim.x) {
       int z[3];
       unknown_coords<D>(p, A.nc, z);
-      const long long off = coarse_offset<D>(z, A.nc);
-      double nb = 0.0;
-      long long mul = 1;
-      for (int q = 0; q < D; ++q) {
-        nb += S.c[off - mul] + S.c[off + mul];
-        mul *= (A.nc + 1);
-      }
-      const double ahc = sig * (2.0 * D * S.c[off] - nb);
+      const double ahc = coarse_apply<D>(A, S.c, coarse_offset<D>(z, A.nc), z);
       R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA));
     }
     if (tid < 32) {
@@ -1856,18 +1954,18 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
     }
     __syncthreads();
   }
-  const double sig = A.sigma_H;
   // J_HH on the coarse-edge pattern (entries for every neighbour in the 3^d box)
   for (int idx = tid; idx < NH * N3; idx += blockDim.x) {
     const int p = idx / N3;
     int r = idx % N3;
-    int z[3], zq[3];
+    int z[3], zq[3], dv[3];
     unknown_coords<D>(p, A.nc, z);
     bool ok = true;
     int q = 0, mul = 1, dist = 0;
     for (int ax = 0; ax < D; ++ax) {
       const int d = r % 3 - 1;
       r /= 3;
+      dv[ax] = d;
       zq[ax] = z[ax] + d;
       if (zq[ax] < 1 || zq[ax] > A.nc - 1) ok = false;
       q += (zq[ax] - 1) * mul;
@@ -1876,22 +1974,14 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
     }
     if (!ok) continue;
     double v = A.fixed_point ? 0.0 : pair_channel<D, JF32>(cellsum, A.nc, z, zq);
-    if (dist == 0) v += sig * 2.0 * D;
-    else if (dist == 1) v -= sig;
+    v += coarse_stiffness<D>(A, z, dv, dist);
     M[p * ld + q] = v;
   }
   // residual and the alpha border
   for (int p = tid; p < NH; p += blockDim.x) {
     int z[3];
     unknown_coords<D>(p, A.nc, z);
-    const long long off = coarse_offset<D>(z, A.nc);
-    double nb = 0.0;
-    long long mul = 1;
-    for (int q = 0; q < D; ++q) {
-      nb += S.c[off - mul] + S.c[off + mul];
-      mul *= (A.nc + 1);
-    }
-    const double ahc = sig * (2.0 * D * S.c[off] - nb);
+    const double ahc = coarse_apply<D>(A, S.c, coarse_offset<D>(z, A.nc), z);
     R[p] = -(ahc + alpha * t_vec[p] + node_channel<D, JF32>(cellsum, A.nc, z, G::RA));
     const double jb = t_vec[p] + (A.fixed_point ? 0.0 : node_channel<D, JF32>(cellsum, A.nc, z, G::JB));
     M[p * ld + NH] = jb;
@@ -2002,7 +2092,9 @@ __device__ void step_report(const AugArgs& A, const StepState& S, int it, bool w
   }
 }
 
-template <int D, bool JF32>
+// VC: the first pass forms A_k u~ with the coefficient's edge weights (a variant of its own, so
+// that the constant-coefficient kernels keep their register allocation).
+template <int D, bool JF32, bool VC>
 __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented(AugArgs A) {
   using G = Aug<D, JF32>;
   using FT = typename std::conditional<JF32, float, double>::type;
@@ -2054,7 +2146,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
     Rows<D, JF32>::zero(acc, first, A.fixed_point != 0, tid);
     __syncthreads();
     if (stop) break;
-    fine_pass<D, JF32>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, bic);
+    fine_pass<D, JF32, VC>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, bic);
     block_reduce_rows<D, JF32>(A, acc, pbuf + (size_t)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
     grid_barrier(A.st, nblocks, A.bar_spins, first && (int)blockIdx.x == A.bar_skip);
     newton_step<D, JF32>(A, pbuf, cellsum, M, R, L, S, first, writer);
@@ -2077,7 +2169,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
   // final update u = alpha u~ + P_{H->k} c
   if (tid < G::NV) cv[tid] = S.c[vert_off];
   __syncthreads();
-  fine_pass<D, JF32>(A, kUpdate, acc, cv, S.sa[1], cell, bic);
+  fine_pass<D, JF32, VC>(A, kUpdate, acc, cv, S.sa[1], cell, bic);
 }
 
 // The final update of a correction step's mixed path, u = alpha u~ + P_{H->k} c, as a
@@ -2225,42 +2317,47 @@ size_t aug_smem(int nc) {
 }
 
 // Blocks per SM of the cooperative kernel of one precision when launched with `smem` dynamic
-// bytes.
+// bytes (the smaller of its constant- and variable-coefficient variants).
 template <int D, bool JF32>
 int aug_occupancy(size_t smem) {
-  int occ = 0;
-  raise_dyn_smem((const void*)k_augmented<D, JF32>, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_augmented<D, JF32>, Aug<D, JF32>::NT, smem);
-  return occ;
+  int occ = 0, occ_vc = 0;
+  raise_dyn_smem((const void*)k_augmented<D, JF32, false>, smem);
+  raise_dyn_smem((const void*)k_augmented<D, JF32, true>, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_augmented<D, JF32, false>, Aug<D, JF32>::NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_vc, k_augmented<D, JF32, true>, Aug<D, JF32>::NT, smem);
+  return occ < occ_vc ? occ : occ_vc;
 }
 
 }  // namespace
 
 // ============================================================================ launchers
 
-cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s) {
+cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* st, cudaStream_t s,
+                                  const VarCoef* vc) {
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
   const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 3 * N + 4);
   cudaError_t e = raise_dyn_smem((const void*)k_coarse_inverse, smem);
   if (e != cudaSuccess) return e;
-  k_coarse_inverse<<<1, 64, smem, s>>>(dim, g1.n, Ainv, st);
+  k_coarse_inverse<<<1, 64, smem, s>>>(dim, g1.n, Ainv, st, vc ? *vc : VarCoef{});
   return cudaGetLastError();
 }
 
 cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double* u, int kind, double a, double tol,
-                                 int maxit, bool f32_factor, DevState* st, cudaStream_t s, bool out_ff) {
+                                 int maxit, bool f32_factor, DevState* st, cudaStream_t s, bool out_ff,
+                                 const VarCoef* vc) {
+  const VarCoef v = vc ? *vc : VarCoef{};
   const int m = g1.n - 1;
   const size_t N = (size_t)ipow(m, dim);
   cudaError_t e;
   if (f32_factor) {
     const size_t smem = sizeof(double) * (3 * N + 2) + sizeof(float) * (N * (N + 1) + 2 * N + 4);
     if ((e = raise_dyn_smem((const void*)k_level1_newton<float>, smem)) != cudaSuccess) return e;
-    k_level1_newton<float><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0);
+    k_level1_newton<float><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0, v);
   } else {
     const size_t smem = sizeof(double) * (3 * N + 2 + N * (N + 1) + 2 * N + 4);
     if ((e = raise_dyn_smem((const void*)k_level1_newton<double>, smem)) != cudaSuccess) return e;
-    k_level1_newton<double><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0);
+    k_level1_newton<double><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0, v);
   }
   return cudaGetLastError();
 }
@@ -2331,7 +2428,7 @@ int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem) {
 cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
                              int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
                              DevState* st, int level_index, cudaStream_t s, int cluster_size, int fixed_point,
-                             int out_f64) {
+                             int out_f64, const VarCoef* vc) {
   const size_t smem = ab.smem;
   const int nt = ab.nt;
   if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
@@ -2363,6 +2460,7 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.dim = dim;
   A.nc = coarse_cells;
   A.s = sfine;
+  A.ls = level - 1;
   A.n = gk.n;
   A.kind = kind;
   A.maxit = maxit;
@@ -2388,14 +2486,16 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.cfin = ab.cfin;
   A.bar_spins = ab.bar_spins > 0 ? ab.bar_spins : (1ll << 25);
   A.bar_skip = ab.bar_skip;
+  A.vc = vc ? *vc : VarCoef{};
   // the largest levels of the mixed path update in a kernel of their own (cooperative launch)
-  A.split_update = (dim == 2 && jac_f32 && cluster_size == 0 && ab.cfin && gk.nodes >= (1ll << 21) &&
+  A.split_update = (dim == 2 && jac_f32 && cluster_size == 0 && !A.vc.a64 && ab.cfin && gk.nodes >= (1ll << 21) &&
                     (int)ipow(coarse_cells + 1, dim) < 128) ? 1 : 0;
   // the barrier words and the abort flag are cleared once per solve (or component call) with
   // the statistics; a completed barrier leaves its count at zero and generations only grow, so
   // the launches of one solve need no reset between them
   cudaError_t e = cudaSuccess;
   if (cluster_size > 0) {
+    if (A.vc.a64) return cudaErrorInvalidValue;   // batches and the server take A = I only
     A.bpc = 1;
     cudaLaunchConfig_t cc = {};
     cc.gridDim = dim3(cluster_size);
@@ -2426,10 +2526,19 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const bool v = A.vc.a64 != nullptr;
   if (dim == 2) {
-    e = jac_f32 ? cudaLaunchKernelEx(&cfg, k_augmented<2, true>, A) : cudaLaunchKernelEx(&cfg, k_augmented<2, false>, A);
+    if (jac_f32)
+      e = v ? cudaLaunchKernelEx(&cfg, k_augmented<2, true, true>, A) : cudaLaunchKernelEx(&cfg, k_augmented<2, true, false>, A);
+    else
+      e = v ? cudaLaunchKernelEx(&cfg, k_augmented<2, false, true>, A)
+            : cudaLaunchKernelEx(&cfg, k_augmented<2, false, false>, A);
   } else {
-    e = jac_f32 ? cudaLaunchKernelEx(&cfg, k_augmented<3, true>, A) : cudaLaunchKernelEx(&cfg, k_augmented<3, false>, A);
+    if (jac_f32)
+      e = v ? cudaLaunchKernelEx(&cfg, k_augmented<3, true, true>, A) : cudaLaunchKernelEx(&cfg, k_augmented<3, true, false>, A);
+    else
+      e = v ? cudaLaunchKernelEx(&cfg, k_augmented<3, false, true>, A)
+            : cudaLaunchKernelEx(&cfg, k_augmented<3, false, false>, A);
   }
   if (e != cudaSuccess || !A.split_update) return e;
   int ls = 0;

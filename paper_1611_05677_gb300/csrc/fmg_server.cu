@@ -331,6 +331,7 @@ fmg_status fmg_server_create(const fmg_server_config* cfg, fmg_server** out) {
 fmg_status fmg_server_submit(fmg_server* sv, const fmg_params* p, const double* g_host, double* u_host,
                              unsigned long long* ticket) {
   if (!sv || !p || !g_host || !u_host) return srv_fail(FMG_ERR_INVALID, "NULL argument");
+  if (p->coefficient) return srv_fail(FMG_ERR_INVALID, "the server takes A = I only (no coefficient)");
   size_t need = 0;
   if (fmg_status s = fmg_workspace_bytes(p, &need)) return s;
   Request* r = new (std::nothrow) Request();

@@ -265,6 +265,116 @@ __global__ void k_residual3(const double* __restrict__ u, const double* __restri
   }
 }
 
+// ------------------------------------------------------------------ variable coefficient
+// The stencil kernels for A(x) != I (VarCoef): the weights w_e of the 2d axis edges at each node
+// come from the per-cell table (edge_weights_t), A u = s sum_e w_e (u_c - u_e) with s = 1 in 2D
+// and h in 3D.  Red-black Gauss-Seidel: u_c = (b / s + sum_e w_e u_e) / sum_e w_e.
+template <int D>
+__device__ __forceinline__ void vc_offsets(long long np, long long* o) {
+  o[0] = -1;
+  o[1] = 1;
+  o[2] = -np;
+  o[3] = np;
+  if (D == 3) {
+    o[4] = -np * np;
+    o[5] = np * np;
+  }
+}
+
+template <typename T, int D>
+__global__ void k_rbgs_vc(T* __restrict__ u, const T* __restrict__ b, int n, int colour, int ls, VarCoef vc) {
+  const int j = blockIdx.y + 1;
+  const int l = D == 3 ? blockIdx.z + 1 : 0;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int par = (colour + j + l) & 1;
+  const int i = par ? 2 * t + 1 : 2 * t + 2;
+  if (i > n - 1) return;
+  const long long np = n + 1;
+  const long long c = (D == 2 ? (long long)j * np : ((long long)l * np + j) * np) + i;
+  long long o[2 * D];
+  vc_offsets<D>(np, o);
+  T w[2 * D];
+  edge_weights_t<D, T>(vc, ls, i, j, l, w);
+  T sw = T(0), su = T(0);
+#pragma unroll
+  for (int e = 0; e < 2 * D; ++e) {
+    sw += w[e];
+    su += w[e] * u[c + o[e]];
+  }
+  u[c] = (b[c] * (D == 2 ? T(1) : T(n)) + su) / sw;
+}
+
+// r = b - A u at node c (interior), A with the variable coefficient
+template <typename T, int D>
+__device__ __forceinline__ T res_vc(const T* __restrict__ u, const T* __restrict__ b, long long c, int i, int j, int l,
+                                    int n, int ls, const VarCoef& vc) {
+  const long long np = n + 1;
+  long long o[2 * D];
+  vc_offsets<D>(np, o);
+  T w[2 * D];
+  edge_weights_t<D, T>(vc, ls, i, j, l, w);
+  const T uc = u[c];
+  T a = T(0);
+#pragma unroll
+  for (int e = 0; e < 2 * D; ++e) a += w[e] * (uc - u[c + o[e]]);
+  return b[c] - (D == 2 ? T(1) : T(1) / T(n)) * a;
+}
+
+// residual + restriction with the variable coefficient: b_c = P^T (b - A u) (coarse nodes of
+// the interior), u_c = 0 (or the first Chebyshev step, unused with A(x): red-black only)
+template <typename TF, typename TC, int D>
+__global__ void k_resrestrict_vc(const TF* __restrict__ u, const TF* __restrict__ b, int nf, int ls, VarCoef vc,
+                                 TC* __restrict__ bc, TC* __restrict__ uc, int ncells) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int J = blockIdx.y + 1;
+  const int L = D == 3 ? blockIdx.z + 1 : 0;
+  if (I > ncells - 1) return;
+  const long long np = nf + 1;
+  const int fi = 2 * I, fj = 2 * J, fl = 2 * L;
+  const long long F = (D == 2 ? (long long)fj * np : ((long long)fl * np + fj) * np) + fi;
+  TF r = res_vc<TF, D>(u, b, F, fi, fj, fl, nf, ls, vc);
+  TF e = TF(0);
+  // the fine nodes at the mesh-edge neighbours of the coarse node: +-(1,0[,0]), +-(0,1[,0]),
+  // +-(1,1[,0]) and in 3D +-(0,0,1), +-(1,0,1), +-(0,1,1), +-(1,1,1)
+  constexpr int NQ = D == 2 ? 3 : 7;
+  const int dq[7][3] = {{1, 0, 0}, {0, 1, 0}, {1, 1, 0}, {0, 0, 1}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const long long off = dq[q][0] + dq[q][1] * np + (D == 3 ? dq[q][2] * np * np : 0);
+    e += res_vc<TF, D>(u, b, F + off, fi + dq[q][0], fj + dq[q][1], fl + dq[q][2], nf, ls, vc) +
+         res_vc<TF, D>(u, b, F - off, fi - dq[q][0], fj - dq[q][1], fl - dq[q][2], nf, ls, vc);
+  }
+  const long long ncp = ncells + 1;
+  const long long cc = (D == 2 ? (long long)J * ncp : ((long long)L * ncp + J) * ncp) + I;
+  bc[cc] = (TC)(r + TF(0.5) * e);
+  uc[cc] = TC(0);
+}
+
+// FP64 residual on one level with the variable coefficient (with r32: its FP32 copy, e = 0)
+template <int D>
+__global__ void k_residual_vc(const double* __restrict__ u, const double* __restrict__ b, int n, int ls, VarCoef vc,
+                              double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const int l = D == 3 ? blockIdx.z : 0;
+  if (i > n) return;
+  const long long np = n + 1;
+  const long long c = (D == 2 ? (long long)j * np : ((long long)l * np + j) * np) + i;
+  double v = 0.0;
+  if (i > 0 && i < n && j > 0 && j < n && (D == 2 || (l > 0 && l < n))) v = res_vc<double, D>(u, b, c, i, j, l, n, ls, vc);
+  if (r) r[c] = v;
+  if (r32) {
+    r32[c] = (float)v;
+    e32[c] = 0.f;
+  }
+}
+
+int vc_ls(const VarCoef& vc, int n) {
+  int ls = 0;
+  while ((vc.nc << ls) < n) ++ls;
+  return ls;
+}
+
 // ------------------------------------------------------------------ prolongation (+ correction)
 template <typename TF, typename TC>
 __global__ void k_prolong2(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) {
@@ -687,9 +797,17 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
 // ============================================================================ launchers
 
 template <typename T>
-cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaStream_t s) {
+cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaStream_t s, const VarCoef* vc) {
   const int n = g.n;
   const unsigned gx = cdiv(n / 2, kBlock);
+  if (vc && vc->a64) {
+    const int ls = vc_ls(*vc, n);
+    if (dim == 2)
+      k_rbgs_vc<T, 2><<<dim3(gx, n - 1), kBlock, 0, s>>>(u, b, n, colour, ls, *vc);
+    else
+      k_rbgs_vc<T, 3><<<dim3(gx, n - 1, n - 1), kBlock, 0, s>>>(u, b, n, colour, ls, *vc);
+    return cudaGetLastError();
+  }
   if (dim == 2) {
     k_rbgs2<T><<<dim3(gx, n - 1), kBlock, 0, s>>>(u, b, n, colour);
   } else {
@@ -700,9 +818,18 @@ cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaS
 
 template <typename TF, typename TC>
 cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const TF* b_f, LevelGeo gc, TC* b_c,
-                                     TC* u_c, cudaStream_t s, TC* d_c, double e0) {
+                                     TC* u_c, cudaStream_t s, TC* d_c, double e0, const VarCoef* vc) {
   const int nc = gc.n;
   const unsigned gx = cdiv(nc - 1, kBlock);
+  if (vc && vc->a64) {
+    if (d_c) return cudaErrorInvalidValue;   // Chebyshev smoothing does not take A(x)
+    const int ls = vc_ls(*vc, gf.n);
+    if (dim == 2)
+      k_resrestrict_vc<TF, TC, 2><<<dim3(gx, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, ls, *vc, b_c, u_c, nc);
+    else
+      k_resrestrict_vc<TF, TC, 3><<<dim3(gx, nc - 1, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, ls, *vc, b_c, u_c, nc);
+    return cudaGetLastError();
+  }
   if (dim == 2) {
     k_resrestrict2<TF, TC><<<dim3(gx, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
   } else {
@@ -713,9 +840,18 @@ cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const 
 }
 
 cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const double* b, float* r32, float* e32,
-                                   cudaStream_t s, float* d32, double e0) {
+                                   cudaStream_t s, float* d32, double e0, const VarCoef* vc) {
   const int n = g.n;
   const unsigned gx = cdiv(n + 1, kBlock);
+  if (vc && vc->a64) {
+    if (d32) return cudaErrorInvalidValue;
+    const int ls = vc_ls(*vc, n);
+    if (dim == 2)
+      k_residual_vc<2><<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, nullptr, r32, e32);
+    else
+      k_residual_vc<3><<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, nullptr, r32, e32);
+    return cudaGetLastError();
+  }
   if (dim == 2)
     k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, nullptr, r32, e32, d32, (float)e0);
   else
@@ -723,9 +859,18 @@ cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* b, double* r, cudaStream_t s) {
+cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* b, double* r, cudaStream_t s,
+                            const VarCoef* vc) {
   const int n = g.n;
   const unsigned gx = cdiv(n + 1, kBlock);
+  if (vc && vc->a64) {
+    const int ls = vc_ls(*vc, n);
+    if (dim == 2)
+      k_residual_vc<2><<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, r, nullptr, nullptr);
+    else
+      k_residual_vc<3><<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, r, nullptr, nullptr);
+    return cudaGetLastError();
+  }
   if (dim == 2)
     k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, r, nullptr, nullptr, nullptr, 0.0f);
   else
@@ -958,12 +1103,14 @@ template cudaError_t launch_cheb_shaped<float>(int, LevelGeo, const float*, floa
                                                double, bool, ChebShape, cudaStream_t, const float*);
 template cudaError_t launch_copy_t<double>(const double*, double*, long long, cudaStream_t);
 template cudaError_t launch_copy_t<float>(const float*, float*, long long, cudaStream_t);
-template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t);
-template cudaError_t launch_rbgs<float>(int, LevelGeo, float*, const float*, int, cudaStream_t);
+template cudaError_t launch_rbgs<double>(int, LevelGeo, double*, const double*, int, cudaStream_t, const VarCoef*);
+template cudaError_t launch_rbgs<float>(int, LevelGeo, float*, const float*, int, cudaStream_t, const VarCoef*);
 template cudaError_t launch_residual_restrict<double, double>(int, LevelGeo, const double*, const double*, LevelGeo,
-                                                              double*, double*, cudaStream_t, double*, double);
+                                                              double*, double*, cudaStream_t, double*, double,
+                                                              const VarCoef*);
 template cudaError_t launch_residual_restrict<float, float>(int, LevelGeo, const float*, const float*, LevelGeo,
-                                                            float*, float*, cudaStream_t, float*, double);
+                                                            float*, float*, cudaStream_t, float*, double,
+                                                            const VarCoef*);
 template cudaError_t launch_prolong<double, double>(int, LevelGeo, const double*, LevelGeo, double*, int,
                                                     cudaStream_t);
 template cudaError_t launch_prolong<float, float>(int, LevelGeo, const float*, LevelGeo, float*, int, cudaStream_t);

@@ -37,7 +37,7 @@ class fmg_params(ctypes.Structure):
                 ("f_scale", c_double), ("m_vcycles", c_int), ("nu_pre", c_int), ("nu_post", c_int),
                 ("p_corrections", c_int), ("precision", c_int), ("newton_tol", c_double),
                 ("newton_maxit", c_int), ("level1_tol", c_double), ("level1_maxit", c_int), ("smoother", c_int),
-                ("nonlinear", c_int)]
+                ("nonlinear", c_int), ("coefficient", c_void_p)]
 
 
 class fmg_stats(ctypes.Structure):
@@ -443,7 +443,23 @@ def make_params(problem=None, **kw) -> fmg_params:
         p.nu_pre = problem.nu_pre
         p.nu_post = problem.nu_post
         p.p_corrections = problem.p_corrections
-    for k, v in kw.items():
+        if getattr(problem, "coefficient", None) is not None:
+            kw.setdefault("coefficient", problem.coefficient)
+    # the coefficient last: its size check reads dim and coarse_cells
+    for k, v in sorted(kw.items(), key=lambda kv: kv[0] == "coefficient"):
+        if k == "coefficient":
+            # the (coarse_cells^dim, dim) table of A's diagonal per cell of T_H; the array is
+            # kept with the params (fmg_create copies it)
+            if v is None:
+                p.coefficient = None
+                p._coefficient = None
+                continue
+            arr = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+            if arr.size != (p.coarse_cells ** p.dim) * p.dim:
+                raise FMGError(FMG_ERR_INVALID, "coefficient must hold coarse_cells^dim rows of dim entries")
+            p._coefficient = arr
+            p.coefficient = arr.ctypes.data
+            continue
         if k == "f" and isinstance(v, str):
             v = NONLIN[v]
         if k == "precision" and isinstance(v, str):

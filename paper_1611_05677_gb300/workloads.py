@@ -6,8 +6,9 @@ the instance mixes of the batched and served workloads.  It holds none of the
 multigrid or multilevel-correction arithmetic, so both the FP64 oracle and the
 CUDA path can take their inputs from here without sharing any method code.
 
-The problem class is the model problem of Sec. 2 (eq. 2.1) with A = I on
-Omega = (0,1)^d; the nonlinearities are those of the examples of Sec. 4
+The problem class is the model problem of Sec. 2 (eq. 2.1) on Omega = (0,1)^d
+with A = I, or with a diagonal SPD coefficient A(x) that is constant on each cell
+of the coarsest mesh T_H (entries drawn here, see cell_coefficient); the nonlinearities are those of the examples of Sec. 4
 (Example 1: u^3; Example 2: -exp(-u); Example 3: the odd extension of
 u^{3/2}) plus exp(u)-1 and the linear a*u used as a closed-form test case.
 
@@ -52,6 +53,8 @@ class Problem:
                    or None when g is given directly (random-mode g)
     g_modes        list of (wave-vector, amplitude) of a direct g (no u*)
     g_const        constant g (Example 2 uses g = 1)
+    coefficient    None (A = I) or the (coarse_cells^dim, dim) table of A's diagonal
+                   entries per cell of T_H (cell (cx, cy[, cz]) at row cx + nc cy [+ nc^2 cz])
     """
 
     dim: int
@@ -67,6 +70,7 @@ class Problem:
     nu_pre: int = 2
     nu_post: int = 2
     p_corrections: int = 1
+    coefficient: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
 
     @property
@@ -146,6 +150,13 @@ class Problem:
         return np.ascontiguousarray(g)
 
 
+def cell_coefficient(dim: int, coarse_cells: int, seed: int = 3, lo: float = 0.5, hi: float = 2.0) -> np.ndarray:
+    """A diagonal SPD coefficient constant on each cell of T_H: entries U[lo, hi] (contrast
+    hi/lo = 4 between neighbouring cells and between the axes of one cell), shape
+    (coarse_cells^dim, dim), x fastest over the cells."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=(coarse_cells ** dim, dim))
+
+
 def _draw_modes(rng: np.random.Generator, dim: int, kmax: int, count: int, amp: str):
     grid = [tuple(int(v) for v in t) for t in np.ndindex(*([kmax] * dim))]
     pick = rng.choice(len(grid), size=count, replace=False)
@@ -176,6 +187,22 @@ def config_large_2d(seed: int = 0, refinements: int = 8) -> Problem:
 # (0.10 at 3 refinements and rising per level), with m = 3 it stays near 0.03 (red-black
 # Gauss-Seidel); Theorem 3.2 only bounds it, so m is raised for every 3D workload.
 M_VCYCLES_3D = 3
+
+
+def config_coefficient(dim: int = 2, seed: int = 0, refinements: int | None = None) -> Problem:
+    """The 2D (H = 1/8) or 3D (H = 1/4) workload shape with the variable coefficient of
+    cell_coefficient(seed = 3) and a random-mode g (no closed-form solution with a coefficient
+    that jumps across the cells of T_H); 2D cubic, 3D exp(u) - 1."""
+    rng = np.random.default_rng(seed)
+    if dim == 2:
+        r = 8 if refinements is None else refinements
+        return Problem(dim=2, coarse_cells=8, refinements=r, f="cubic", a=1.0,
+                       g_modes=_draw_modes(rng, 2, 6, 8, "normal"), coefficient=cell_coefficient(2, 8),
+                       name=f"2d_H8_r{r}_cubic_coefficient_seed{seed}")
+    r = 6 if refinements is None else refinements
+    return Problem(dim=3, coarse_cells=4, refinements=r, f="expm1", a=1.0,
+                   g_modes=_draw_modes(rng, 3, 4, 8, "uniform"), coefficient=cell_coefficient(3, 4),
+                   m_vcycles=M_VCYCLES_3D, name=f"3d_H4_r{r}_expm1_coefficient_seed{seed}")
 
 
 def config_3d(seed: int = 0, refinements: int = 6) -> Problem:

@@ -65,6 +65,32 @@ def test_default_params_and_validation(lib):
         assert fmg.fmg_last_error()
 
 
+def test_coefficient_validation(lib):
+    """The coefficient table is checked entry by entry (finite, > 0) and only with the
+    red-black smoother; its size follows coarse_cells^dim rows of dim entries."""
+    from paper_1611_05677_gb300 import fmg
+    from paper_1611_05677_gb300 import workloads as W
+
+    for dim, nc in ((2, 4), (3, 2)):
+        coef = W.cell_coefficient(dim, nc)
+        p = fmg.make_params(dim=dim, coarse_cells=nc, refinements=2, coefficient=coef)
+        assert fmg.fmg_workspace_bytes(p) > 0
+        for bad in (0.0, -1.0, float("nan"), float("inf")):
+            c2 = coef.copy()
+            c2[-1, -1] = bad
+            q = fmg.make_params(dim=dim, coarse_cells=nc, refinements=2, coefficient=c2)
+            with pytest.raises(fmg.FMGError) as ei:
+                fmg.fmg_workspace_bytes(q)
+            assert ei.value.status == fmg.FMG_ERR_INVALID
+            assert "coefficient" in fmg.fmg_last_error()
+        q = fmg.make_params(dim=dim, coarse_cells=nc, refinements=2, coefficient=coef, smoother="chebyshev")
+        with pytest.raises(fmg.FMGError) as ei:
+            fmg.fmg_workspace_bytes(q)
+        assert ei.value.status == fmg.FMG_ERR_INVALID
+        with pytest.raises(fmg.FMGError):
+            fmg.make_params(dim=dim, coarse_cells=nc, refinements=2, coefficient=coef[:-1])
+
+
 def test_null_arguments_are_rejected(lib):
     from paper_1611_05677_gb300 import fmg
 

@@ -651,7 +651,7 @@ def test_chord_is_slower_than_newton_far_from_the_solution():
 
 
 def _cell_coefficient(dim, nc, seed=3):
-    return np.random.default_rng(seed).uniform(0.5, 2.0, size=(nc ** dim, dim))
+    return W.cell_coefficient(dim, nc, seed)
 
 
 @pytest.mark.parametrize("dim,nc,r", [(2, 4, 3), (3, 2, 2)])
