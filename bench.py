@@ -847,9 +847,13 @@ def single_solve(args):
     __graft_entry__.build()
     from paper_1611_05677_gb300 import fmg, workloads as W
 
-    prob = W.config_large_2d(refinements=args.refinements)
+    if args.workload == "3d":
+        prob = W.config_3d(refinements=6 if args.refinements == 8 else args.refinements)
+    else:
+        prob = W.config_large_2d(refinements=args.refinements)
     sm = "rbgs" if args.smoother == "auto" else args.smoother
-    s = fmg.Solver(fmg.make_params(prob, precision=args.precision, smoother=sm), prob.g_nodal())
+    s = fmg.Solver(fmg.make_params(prob, precision=args.precision, smoother=sm, m_vcycles=prob.m_vcycles),
+                   prob.g_nodal())
     st = fmg.fmg_stats()
     s.solve(stats=st)
     torch.cuda.synchronize()

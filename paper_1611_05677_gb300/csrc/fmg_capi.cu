@@ -184,8 +184,9 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
   AugBuffers cfg = {};
   aug_configure(p->dim, p->coarse_cells, p->precision == FMG_PREC_MIXED, &cfg);
   const size_t items = cfg.partial_items;
-  double* partials = (double*)take(2 * items * aug_nvals(p->dim) * 8);
+  double* partials = (double*)take(2 * (items + ipow(p->coarse_cells, p->dim)) * aug_nvals(p->dim) * 8);
   double* cfin = (double*)take((ipow(p->coarse_cells + 1, p->dim) + 1) * 8);
+  int* jtab = (int*)take(aug_jtab_ints(p->dim, p->coarse_cells) * 4);
   // the coefficient table in FP64, FP32 and float-float (a row of d entries per cell of T_H)
   const long long ncoef = ipow(p->coarse_cells, p->dim) * p->dim;
   double* a64 = (double*)take(ncoef * 8);
@@ -203,6 +204,7 @@ size_t layout(fmg_ctx* c, const fmg_params* p, char* base) {
     c->ab.partials = partials;
     c->ab.Ainv = Ainv;
     c->ab.cfin = cfin;
+    c->ab.jtab = jtab;
     c->ab.bar_spins = 0;
     c->ab.bar_skip = -1;
   }
@@ -777,6 +779,7 @@ fmg_status fmg_create(const fmg_params* p, const double* g_fine, int g_on_device
     e = launch_coarse_inverse(p->dim, c->geo[0], c->Ainv, c->st, c->stream, vcp(c));
     const long long n1 = ipow(p->coarse_cells - 1, p->dim);
     if (e == cudaSuccess) e = launch_to_f32(c->Ainv, c->Ainv32, n1 * n1, c->stream);
+    if (e == cudaSuccess) e = launch_aug_jtab(p->dim, p->coarse_cells, (int*)c->ab.jtab, c->stream);
     if (e != cudaSuccess) s = fail(c, FMG_ERR_CUDA, std::string("coarse inverse: ") + cudaGetErrorString(e));
   }
   if (s == FMG_OK) s = read_state(c, nullptr, false);

@@ -37,6 +37,9 @@ struct DevState {
   unsigned int bar_gen;
   int abort;
   int converged;
+  // arrivals of a pass's blocks per coarse cell (the last block of a cell sums its partial
+  // rows; it resets the count to zero)
+  unsigned int cell_count[64];
   // current augmented iterate
   double alpha_cur;
   double pad[3];
@@ -286,7 +289,8 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
 // Augmented problem on V_H + span{u~} (Algorithm 3.1 step 2, eq. 3.6): one cooperative
 // persistent kernel: precompute, Newton iterations, final update u = alpha u~ + P_{H->k} c.
 struct AugBuffers {
-  double* partials;   // two buffers of [items][nvals] (the Newton iterations alternate)
+  double* partials;   // two buffers of [items][nvals] (the Newton iterations alternate), then two
+                      // buffers of [cells][nvals] cell sums
   const double* Ainv; // A_H^{-1} (level-1 inverse; kept with the buffers of the system)
   double* cfin;       // the final coarse iterate c ((1/H + 1)^d nodal values) and alpha, for the
                       // separate update kernel of the largest levels
@@ -295,12 +299,16 @@ struct AugBuffers {
   int nt;             // threads per block
   size_t smem;        // dynamic shared memory per block
   int sms;            // multiprocessors of the device
+  const int* jtab;     // the mixed path's Jacobian gather table (launch_aug_jtab, once per context)
   long long bar_spins; // grid-barrier polls before a timeout (0: the default, 2^25)
   int bar_skip;        // failure-detection test hook: block that skips its first arrival (-1: none)
 };
 // Fills bpc/nt/smem/partial_items for this device (occupancy-based), outside any capture.
 void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab);
 int aug_nvals(int dim);
+// ints of the mixed path's Jacobian gather table, and the kernel that fills it
+size_t aug_jtab_ints(int dim, int coarse_cells);
+cudaError_t launch_aug_jtab(int dim, int coarse_cells, int* tab, cudaStream_t s);
 // jac_f32: Jacobian moments in FP32 (residual stays FP64) -- the mixed-precision path.
 // fixed_point: the fixed-point iteration on the Galerkin stiffness instead of Newton.
 // cluster_size > 0: the thread-block-cluster variant (no cooperative launch; used when many

@@ -550,6 +550,7 @@ struct AugArgs {
   long long bar_spins;  // polls of the grid barrier before it times out
   int bar_skip;         // test hook: this block skips its first barrier arrival (-1: none)
   VarCoef vc;           // the coefficient A(x) (vc.a64 == nullptr: A = I)
+  const int* jtab;      // mixed path: the Jacobian gather table (k_aug_jtab)
 };
 
 // Bounded grid barrier for the cooperative launch (all blocks co-resident).  A waiting block
@@ -1290,72 +1291,143 @@ struct AugSmem {
 };
 
 // Sum over the bpc blocks of a cell of one channel of their partial rows, in block order, with
-// the loads of four blocks issued together.
-template <int NVAL>
+// the loads of four blocks issued together.  FP32: the channel's FP32 value in the low word of
+// each slot.
+template <int NVAL, bool F32>
 __device__ __forceinline__ double sum_blocks(const double* __restrict__ p, int bpc) {
   double x = 0.0;
+  float xf = 0.f;
   int b = 0;
+  auto add = [&](double v) {
+    if (F32)
+      xf += __int_as_float(__double2loint(v));
+    else
+      x += v;
+  };
   for (; b + 4 <= bpc; b += 4) {
     const double v0 = __ldcg(p + (size_t)(b + 0) * NVAL), v1 = __ldcg(p + (size_t)(b + 1) * NVAL);
     const double v2 = __ldcg(p + (size_t)(b + 2) * NVAL), v3 = __ldcg(p + (size_t)(b + 3) * NVAL);
-    x += v0;
-    x += v1;
-    x += v2;
-    x += v3;
+    add(v0);
+    add(v1);
+    add(v2);
+    add(v3);
   }
-  for (; b < bpc; ++b) x += __ldcg(p + (size_t)b * NVAL);
-  return x;
+  for (; b < bpc; ++b) add(__ldcg(p + (size_t)b * NVAL));
+  return F32 ? __hiloint2double(0, __float_as_int(xf)) : x;
+}
+
+// Several blocks per coarse cell: after its block sum, each block arrives at its cell's counter,
+// and the one that arrives last sums the cell's partial rows (block order, the channels this
+// pass filled) into the cell's row of cbuf and resets the counter, all before the grid barrier.
+// After the barrier every block reads one row per cell instead of the rows of every block.
+template <int D, bool JF32>
+__device__ void cell_reduce(const AugArgs& A, const double* __restrict__ pbuf, double* __restrict__ cbuf, int cell,
+                            bool first, int* last_sh) {
+  using G = Aug<D, JF32>;
+  __threadfence();   // this block's partial row before its arrival
+  __syncthreads();
+  if (threadIdx.x == 0) *last_sh = atomicAdd(&A.st->cell_count[cell], 1u) == (unsigned)(A.bpc - 1) ? 1 : 0;
+  __syncthreads();
+  if (!*last_sh) return;
+  __threadfence();   // the other blocks' rows, after their arrivals
+  const bool fixed_point = A.fixed_point != 0;
+  const double* rows = pbuf + (size_t)cell * A.bpc * G::NVAL;
+  for (int v = threadIdx.x; v < G::NVAL; v += blockDim.x) {
+    if (v >= G::TT && v < G::JB && !first) continue;                   // t, s: first pass only
+    if (v >= G::JB && (fixed_point || (JF32 && !first))) continue;      // no Jacobian channels
+    cbuf[(size_t)cell * G::NVAL + v] = (JF32 && v >= G::JB) ? sum_blocks<G::NVAL, true>(rows + v, A.bpc)
+                                                            : sum_blocks<G::NVAL, false>(rows + v, A.bpc);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(&A.st->cell_count[cell], 0u);
 }
 
 template <int D>
 __device__ void newton_update(const AugArgs& A, const double* R, int NH, const StepState& S, int dropped, bool ok,
                               bool writer);
 
-// Sum of the FP32 channel `ch` (stored in the low word of its slot) at vertex p over the cells
-// around coarse node p.
+// Gather table of the mixed path's FP32 Jacobian (first iteration of a correction step): one
+// record of kJW<D> ints per entry e of the assembly, e = p (3^d + 1) + r for coarse unknown p and
+// r < 3^d its neighbour z_p + (r digits in base 3) - 1, r = 3^d the border entry of p:
+//   [0] the entry's index into the factor's array (p ld + q, or N_H ld + p), -1: outside the
+//       lower band or the mesh;
+//   [1] |dv|_1 (bits 0-1), border flag (bit 2), p (bits 8-15), r (bits 16-23);
+//   [2 + o] for each of the 2^d cells around the node (o: the vertex bits of p in the cell), the
+//       cell-sum slot of the channel the entry takes from that cell, or -1.
+// The entry is the sum of those FP32 channels in o order (the same order as summing cell by
+// cell), so a table-driven assembly does no index arithmetic on the coarse mesh.
 template <int D>
-__device__ __forceinline__ float node_channel_f(const double* cellsum, int nc, const int* z, int ch) {
-  using G = Aug<D, true>;
-  float x = 0.f;
-#pragma unroll
-  for (int o = 0; o < G::NV; ++o) {
-    bool ok = true;
-    int cell = 0, mul = 1;
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      const int cc = z[q] - ((o >> q) & 1);
-      if (cc < 0 || cc >= nc) ok = false;
-      cell += cc * mul;
-      mul *= nc;
-    }
-    if (ok) x += reinterpret_cast<const float*>(cellsum + (long long)cell * G::NVAL + ch + o)[0];
+constexpr int kJW = D == 2 ? 8 : 12;
+
+template <int D>
+__host__ __device__ constexpr int aug_jtab_entries(int nc) {
+  int nh = 1, n3 = 1;
+  for (int q = 0; q < D; ++q) {
+    nh *= nc - 1;
+    n3 *= 3;
   }
-  return x;
+  return nh * (n3 + 1);
 }
 
-// FP32 Jacobian pair channel of coarse nodes zp, zq summed over the cells that hold both.
 template <int D>
-__device__ __forceinline__ float pair_channel_f(const double* cellsum, int nc, const int* zp, const int* zq) {
+__global__ void k_aug_jtab(int nc, int* __restrict__ tab) {
   using G = Aug<D, true>;
-  float x = 0.f;
-#pragma unroll
-  for (int o = 0; o < G::NV; ++o) {
-    bool ok = true;
-    int cell = 0, mul = 1, vq = 0;
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      const int cc = zp[q] - ((o >> q) & 1);
-      if (cc < 0 || cc >= nc) ok = false;
-      const int dq = zq[q] - cc;
-      if (dq < 0 || dq > 1) ok = false;
-      vq |= dq << q;
-      cell += cc * mul;
-      mul *= nc;
+  constexpr int N3 = D == 2 ? 9 : 27;
+  const int NH = (int)ipow(nc - 1, D);
+  const int ld = NH + 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NH * (N3 + 1); e += gridDim.x * blockDim.x) {
+    int* w = tab + (size_t)e * kJW<D>;
+    for (int i = 0; i < kJW<D>; ++i) w[i] = -1;
+    const int p = e / (N3 + 1), rr = e - p * (N3 + 1);
+    int z[3];
+    unknown_coords<D>(p, nc, z);
+    if (rr == N3) {   // border entry: the channel JB of the vertex z in each cell around it
+      w[0] = NH * ld + p;
+      w[1] = 4 | (p << 8) | (rr << 16);
+      for (int o = 0; o < G::NV; ++o) {
+        bool ok = true;
+        int cell = 0, mul = 1;
+        for (int q = 0; q < D; ++q) {
+          const int cc = z[q] - ((o >> q) & 1);
+          if (cc < 0 || cc >= nc) ok = false;
+          cell += cc * mul;
+          mul *= nc;
+        }
+        if (ok) w[2 + o] = cell * G::NVAL + G::JB + o;
+      }
+      continue;
     }
-    if (ok)
-      x += reinterpret_cast<const float*>(cellsum + (long long)cell * G::NVAL + G::JP + pair_index(G::NV, o, vq))[0];
+    int zq[3], q = 0, mulq = 1, dist = 0, r2 = rr;
+    bool okq = true;
+    for (int ax = 0; ax < D; ++ax) {
+      const int d = r2 % 3 - 1;
+      r2 /= 3;
+      zq[ax] = z[ax] + d;
+      if (zq[ax] < 1 || zq[ax] > nc - 1) okq = false;
+      q += (zq[ax] - 1) * mulq;
+      mulq *= (nc - 1);
+      dist += d < 0 ? -d : d;
+    }
+    if (!okq || q > p) continue;
+    w[0] = p * ld + q;
+    w[1] = (dist > 2 ? 2 : dist) | (p << 8) | (rr << 16);
+    // the pair channel of (z, zq) in each cell that holds both
+    for (int o = 0; o < G::NV; ++o) {
+      bool ok = true;
+      int cell = 0, mul = 1, vq = 0;
+      for (int qq = 0; qq < D; ++qq) {
+        const int cc = z[qq] - ((o >> qq) & 1);
+        if (cc < 0 || cc >= nc) ok = false;
+        const int dq = zq[qq] - cc;
+        if (dq < 0 || dq > 1) ok = false;
+        vq |= dq << qq;
+        cell += cc * mul;
+        mul *= nc;
+      }
+      if (ok) w[2 + o] = cell * G::NVAL + G::JP + pair_index(G::NV, o, vq);
+    }
   }
-  return x;
 }
 
 // Largest lexicographic half-bandwidth of J_HH (aug_band) of a dimension: 2D 1/H <= 8 gives
@@ -1608,10 +1680,9 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
   __shared__ int fac_sh[2];
   __shared__ unsigned red_sh[3];
   if (tid == 0) red_sh[0] = red_sh[1] = red_sh[2] = 0u;
-  // ---- cell sums (fixed order over the cell's blocks): the residual channels in FP64, in the
-  // first iteration also t, s (FP64) and the Jacobian channels (FP32); eight items per thread
-  // are loaded together.  With one block per cell the partial rows are the cell sums and are
-  // copied as they are.
+  // ---- cell sums (one row per coarse cell): the residual channels in FP64, in the first
+  // iteration also t, s (FP64) and the Jacobian channels (FP32, low word of the slot); eight
+  // items per thread are loaded together and copied as they are.
   const int nneed = first ? G::NVAL : G::NV + 1;
   const int total = ncell * nneed;
   for (int base = tid; base < total; base += 8 * nthr) {
@@ -1626,48 +1697,13 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
         if (!(fixedp && v >= G::JB)) dst[r] = cell * G::NVAL + v;
       }
     }
-    if (A.bpc == 1) {
-      unsigned long long wv[8];
+    unsigned long long wv[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        wv[r] = dst[r] >= 0 ? __ldcg(reinterpret_cast<const unsigned long long*>(partials) + dst[r]) : 0ull;
+    for (int r = 0; r < 8; ++r)
+      wv[r] = dst[r] >= 0 ? __ldcg(reinterpret_cast<const unsigned long long*>(partials) + dst[r]) : 0ull;
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        if (dst[r] >= 0) reinterpret_cast<unsigned long long*>(cellsum)[dst[r]] = wv[r];
-      continue;
-    }
-    double xd[8];
-    float xf[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      xd[r] = 0.0;
-      xf[r] = 0.f;
-    }
-    for (int b = 0; b < A.bpc; ++b) {
-      double wv[8];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int cell = dst[r] >= 0 ? dst[r] / G::NVAL : 0;
-        wv[r] = dst[r] >= 0 ? __ldcg(partials + ((size_t)cell * A.bpc + b) * G::NVAL + (dst[r] - cell * G::NVAL))
-                            : 0.0;
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        if (dst[r] < 0) continue;
-        if (dst[r] % G::NVAL >= G::JB)
-          xf[r] += __int_as_float(__double2loint(wv[r]));
-        else
-          xd[r] += wv[r];
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      if (dst[r] < 0) continue;
-      if (dst[r] % G::NVAL >= G::JB)
-        reinterpret_cast<float*>(cellsum + dst[r])[0] = xf[r];
-      else
-        cellsum[dst[r]] = xd[r];
-    }
+    for (int r = 0; r < 8; ++r)
+      if (dst[r] >= 0) reinterpret_cast<unsigned long long*>(cellsum)[dst[r]] = wv[r];
   }
   __syncthreads();
   // the first pass's residual sums are kept in basev; the later passes' increments are added
@@ -1745,36 +1781,44 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
     // lower band (neighbours q <= p of unknown p in the 3^d box), the border row and the corner,
     // an entry per thread
     const float sigf = (float)sig;
+    const int4* jt = reinterpret_cast<const int4*>(A.jtab);
     for (int e = tid; e < NH * (N3 + 1); e += nthr) {
-      const int p = e / (N3 + 1), rr = e - p * (N3 + 1);
-      int z[3];
-      unknown_coords<D>(p, A.nc, z);
-      if (rr == N3) {
-        L[NH * ld + p] = (float)S.t[p] + (fixedp ? 0.f : node_channel_f<D>(cellsum, A.nc, z, G::JB));
+      int w[kJW<D>];
+#pragma unroll
+      for (int i = 0; i < kJW<D> / 4; ++i) {
+        const int4 t4 = __ldg(jt + (size_t)e * (kJW<D> / 4) + i);
+        w[4 * i] = t4.x;
+        w[4 * i + 1] = t4.y;
+        w[4 * i + 2] = t4.z;
+        w[4 * i + 3] = t4.w;
+      }
+      if (w[0] < 0) continue;
+      float x = 0.f;
+      if (!fixedp) {
+#pragma unroll
+        for (int o = 0; o < G::NV; ++o)
+          if (w[2 + o] >= 0) x += reinterpret_cast<const float*>(cellsum + w[2 + o])[0];
+      }
+      const int p = (w[1] >> 8) & 255;
+      if (w[1] & 4) {
+        L[w[0]] = (float)S.t[p] + x;
         continue;
       }
-      int zq[3], dv[3], q = 0, mulq = 1, dist = 0, r2 = rr;
-      bool okq = true;
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        const int d = r2 % 3 - 1;
-        r2 /= 3;
-        dv[ax] = d;
-        zq[ax] = z[ax] + d;
-        if (zq[ax] < 1 || zq[ax] > A.nc - 1) okq = false;
-        q += (zq[ax] - 1) * mulq;
-        mulq *= (A.nc - 1);
-        dist += abs(d);
-      }
-      if (!okq || q > p) continue;
-      float v = fixedp ? 0.f : pair_channel_f<D>(cellsum, A.nc, z, zq);
+      const int dist = w[1] & 3;
       if (A.vc.a64) {
-        v += (float)coarse_stiffness<D>(A, z, dv, dist);
+        int z[3], dv[3], r2 = (w[1] >> 16) & 255;
+        unknown_coords<D>(p, A.nc, z);
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          dv[ax] = r2 % 3 - 1;
+          r2 /= 3;
+        }
+        x += (float)coarse_stiffness<D>(A, z, dv, dist);
       } else {
-        if (dist == 0) v += sigf * (float)(2 * D);
-        else if (dist == 1) v -= sigf;
+        if (dist == 0) x += sigf * (float)(2 * D);
+        else if (dist == 1) x -= sigf;
       }
-      L[p * ld + q] = v;
+      L[w[0]] = x;
     }
     if (tid == 0) L[NH * ld + NH] = (float)S.sa[0] + (fixedp ? 0.f : s3_sh);
     __syncthreads();
@@ -1821,8 +1865,8 @@ __device__ __noinline__ void newton_step_mixed(const AugArgs& A, const double* _
 // the reciprocal pivots after it) and the later iterations are chord steps with that factor.
 // The fixed-point iteration (A.fixed_point) factors the Galerkin stiffness [[A_H, t], [t^T, s]]
 // once, in the path's precision, and every iteration solves with it against the residual
-// (y_{k+1} = y_k - K^{-1} R(y_k), i.e. K y_{k+1} = G - B^T W f(B y_k)).  `partials` is this
-// iteration's buffer of block partial rows; only the writer block reports to DevState.
+// (y_{k+1} = y_k - K^{-1} R(y_k), i.e. K y_{k+1} = G - B^T W f(B y_k)).  `partials` holds this
+// iteration's sums, one row per coarse cell; only the writer block reports to DevState.
 // Not inlined: the dense step runs once per pass, and its own register allocation keeps it
 // from raising the pressure in the fine pass.
 template <int D, bool JF32>
@@ -1858,7 +1902,7 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
         if (idx < total) {
           const int cell = idx / (G::NV + 1), v = idx % (G::NV + 1);
           const int chn = v < G::NV ? G::RA + v : G::SA;
-          x[r] = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + chn, A.bpc);
+          x[r] = __ldcg(partials + (size_t)cell * G::NVAL + chn);
         }
       }
 #pragma unroll
@@ -1899,10 +1943,9 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
     newton_update<D>(A, R, NH, S, 0, true, writer);
     return;
   }
-  // cell sums over the blocks of each cell (fixed order); with one block per cell (small
-  // levels) the partial rows are the cell sums, and eight of them are loaded together
+  // the cell sums (one row per coarse cell), eight loaded together
   auto needed = [&](int v) { return !((!first && v >= G::TT && v < G::JB) || (A.fixed_point && v >= G::JB)); };
-  if (A.bpc == 1) {
+  {
     const int total = ncell * G::NVAL;
     for (int base = tid; base < total; base += 8 * blockDim.x) {
       double x[8];
@@ -1916,12 +1959,6 @@ __device__ __noinline__ void newton_step(const AugArgs& A, const double* __restr
         const int idx = base + r * blockDim.x;
         if (idx < total && needed(idx % G::NVAL)) cellsum[idx] = x[r];
       }
-    }
-  } else {
-    for (int idx = tid; idx < ncell * G::NVAL; idx += blockDim.x) {
-      const int cell = idx / G::NVAL, v = idx % G::NVAL;
-      if (!needed(v)) continue;
-      cellsum[idx] = sum_blocks<G::NVAL>(partials + (size_t)cell * A.bpc * G::NVAL + v, A.bpc);
     }
   }
   for (int idx = tid; idx < NA * ld; idx += blockDim.x) M[idx] = 0.0;
@@ -2103,6 +2140,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
   __shared__ double cv[G::NV];
   __shared__ int flags_sh[2];
   __shared__ int stop;
+  __shared__ int last_sh;
   const int tid = threadIdx.x;
   const unsigned nblocks = gridDim.x;
   const int cell = blockIdx.x / A.bpc;
@@ -2148,8 +2186,16 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
     if (stop) break;
     fine_pass<D, JF32, VC>(A, first ? kFirst : kNewton, acc, cv, S.sa[1], cell, bic);
     block_reduce_rows<D, JF32>(A, acc, pbuf + (size_t)blockIdx.x * G::NVAL, first, A.fixed_point != 0);
+    // one row per cell for the dense step: with one block per cell its partial row, else the
+    // cell sums of this iteration's buffer (formed by the cell's last block)
+    const double* rows = pbuf;
+    if (A.bpc > 1) {
+      double* cbuf = A.partials + 2 * A.pstride + (size_t)(it & 1) * ncell * G::NVAL;
+      cell_reduce<D, JF32>(A, pbuf, cbuf, cell, first, &last_sh);
+      rows = cbuf;
+    }
     grid_barrier(A.st, nblocks, A.bar_spins, first && (int)blockIdx.x == A.bar_skip);
-    newton_step<D, JF32>(A, pbuf, cellsum, M, R, L, S, first, writer);
+    newton_step<D, JF32>(A, rows, cellsum, M, R, L, S, first, writer);
     __syncthreads();
     if (flags_sh[0] || flags_sh[1]) break;
   }
@@ -2364,6 +2410,19 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
 
 int aug_nvals(int dim) { return dim == 2 ? Aug<2, false>::NVAL : Aug<3, false>::NVAL; }
 
+size_t aug_jtab_ints(int dim, int coarse_cells) {
+  return dim == 2 ? (size_t)aug_jtab_entries<2>(coarse_cells) * kJW<2>
+                  : (size_t)aug_jtab_entries<3>(coarse_cells) * kJW<3>;
+}
+
+cudaError_t launch_aug_jtab(int dim, int coarse_cells, int* tab, cudaStream_t s) {
+  if (dim == 2)
+    k_aug_jtab<2><<<4, 256, 0, s>>>(coarse_cells, tab);
+  else
+    k_aug_jtab<3><<<4, 256, 0, s>>>(coarse_cells, tab);
+  return cudaGetLastError();
+}
+
 void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
@@ -2487,6 +2546,7 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   A.bar_spins = ab.bar_spins > 0 ? ab.bar_spins : (1ll << 25);
   A.bar_skip = ab.bar_skip;
   A.vc = vc ? *vc : VarCoef{};
+  A.jtab = ab.jtab;
   // the largest levels of the mixed path update in a kernel of their own (cooperative launch)
   A.split_update = (dim == 2 && jac_f32 && cluster_size == 0 && !A.vc.a64 && ab.cfin && gk.nodes >= (1ll << 21) &&
                     (int)ipow(coarse_cells + 1, dim) < 128) ? 1 : 0;
