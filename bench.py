@@ -20,6 +20,7 @@ the reported time is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -614,6 +615,21 @@ BATCH_WORKLOAD = ("batched: independent 2D P1 instances, H=1/4, refinements U{5.
                   "seeded random-mode g; one CUDA graph, a branch per instance")
 
 
+def prolong_2d(uc):
+    """Nodal P1 interpolation onto the once-refined 2D mesh (right triangles split along the
+    (0,0)-(1,1) diagonal; arrays x fastest): coincident nodes copy, edge midpoints average the
+    edge's two ends."""
+    import numpy as np
+
+    nc = uc.shape[0] - 1
+    uf = np.zeros((2 * nc + 1, 2 * nc + 1))
+    uf[::2, ::2] = uc
+    uf[::2, 1::2] = 0.5 * (uc[:, :-1] + uc[:, 1:])
+    uf[1::2, ::2] = 0.5 * (uc[:-1, :] + uc[1:, :])
+    uf[1::2, 1::2] = 0.5 * (uc[:-1, :-1] + uc[1:, 1:])
+    return uf
+
+
 def run_batch(args):
     """Batched solves: one step = one launch of the batch graph (every instance solved once)."""
     import numpy as np
@@ -630,36 +646,50 @@ def run_batch(args):
     probs = W.config_batch(seed=rank, count=args.batch_count)
     dofs = sum(p.fine_dofs for p in probs)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    # each precision on its faster smoother, as in the single-instance workloads
+    if args.smoother == "auto":
+        smoother = {"mixed": "chebyshev", "fp64": "rbgs"}
+    else:
+        smoother = {"mixed": args.smoother, "fp64": args.smoother}
     res = {}
     for prec in ("mixed", "fp64"):
         log(f"batch {prec}: creating {len(probs)} solvers")
         t0 = time.perf_counter()
-        solvers = [fmg.Solver(fmg.make_params(p, precision=prec), p.g_nodal()) for p in probs]
-        batch = fmg.Batch(solvers)
+        solvers = [fmg.Solver(fmg.make_params(p, precision=prec, smoother=smoother[prec]), p.g_nodal()) for p in probs]
+        if not args.no_autotune and smoother[prec] == "chebyshev":
+            # the launch-shape table is per level size: the deepest instance covers every level
+            fmg.fmg_autotune(max(solvers, key=lambda s: s.params.refinements).ctx)
+        batch = fmg.Batch(solvers, mode="phases")
         stats = batch.solve(wait=True)
         setup_s = time.perf_counter() - t0
-        res[prec] = {"solvers": solvers, "batch": batch, "setup_s": setup_s,
+        branches = fmg.Batch(solvers, mode="branches")
+        branches.solve(wait=True)
+        res[prec] = {"solvers": solvers, "batch": batch, "branches": branches, "setup_s": setup_s,
                      "flags": int(np.bitwise_or.reduce([st.flags for st in stats]))}
+
+    def time_batch(b):
+        for _ in range(args.warmup):
+            b.solve()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(b.stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            fmg.fmg_batch_solve(b.handle, None)
+            e1.record(b.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return max_over_ranks(dist, torch, statistics.mean(ms))
+
     barrier(dist, torch)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for prec in ("mixed", "fp64"):
-            b = res[prec]["batch"]
-            for _ in range(args.warmup):
-                b.solve()
-            torch.cuda.synchronize()
-            ms = []
-            for _ in range(args.steps):
-                with torch.cuda.stream(b.stream):
-                    flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(b.stream)
-                fmg.fmg_batch_solve(b.handle, None)
-                e1.record(b.stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            res[prec]["ms"] = max_over_ranks(dist, torch, statistics.mean(ms))
+            res[prec]["ms"] = time_batch(res[prec]["batch"])
+            res[prec]["branches_ms"] = time_batch(res[prec]["branches"])
     torch.cuda.synchronize()
     barrier(dist, torch)
     # one instance at a time (each instance's own graph), for comparison
@@ -683,6 +713,7 @@ def run_batch(args):
         e1.synchronize()
         seq[prec] = e0.elapsed_time(e1)
     # accuracy: the mixed results against the FP64 results, relative discrete L2 per instance
+    # (the two arms' smoothers may differ, so this includes the algorithms' own difference)
     res["mixed"]["batch"].solve(wait=True)
     res["fp64"]["batch"].solve(wait=True)
     worst = 0.0
@@ -690,7 +721,28 @@ def run_batch(args):
         a = sm.solution().double()
         b = sd.solution().double()
         worst = max(worst, float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)))
-    launches = sum(fmg.fmg_graph_kernels(s.ctx) for s in res["mixed"]["solvers"])
+    # "solved to discretization accuracy" on one instance per level count: e_alg = ||u - u_bar_h||
+    # with u_bar_h the FP64 solve at 8 correction steps per level, against e_disc estimated by
+    # Richardson as ||u_bar_h - P u_bar_2h|| / 3 (random-mode g has no exact solution)
+    log("batch accuracy sample")
+    alg = {}
+    first = {}
+    for i, p in enumerate(probs):
+        first.setdefault(p.refinements, i)
+    for r, i in sorted(first.items()):
+        p = probs[i]
+        ub = {}
+        for rr in (r, r - 1):
+            q = dataclasses.replace(p, refinements=rr)
+            sb = fmg.Solver(fmg.make_params(q, precision="fp64", smoother="rbgs", p_corrections=8), q.g_nodal())
+            ub[rr] = sb.solve().cpu().numpy()
+            sb.close()
+        n = p.n_fine
+        l2 = lambda e: float(math.sqrt(np.sum(e * e) / n ** 2))
+        e_disc = l2(ub[r] - prolong_2d(ub[r - 1])) / 3.0
+        alg[f"r{r}"] = {prec: l2(res[prec]["solvers"][i].solution().cpu().numpy() - ub[r]) / e_disc
+                        for prec in ("mixed", "fp64")}
+    launches = res["mixed"]["batch"].kernel_nodes
     if rank == 0:
         mix, f64 = res["mixed"]["ms"], res["fp64"]["ms"]
         line = {
@@ -705,7 +757,19 @@ def run_batch(args):
                      "speedup_mixed_over_fp64": f64 / mix},
             "one_at_a_time": {"mixed_ms": seq["mixed"], "fp64_ms": seq["fp64"],
                               "batch_speedup_mixed": seq["mixed"] / mix},
+            "layout": {"timed": "phases: one launch per phase over every instance that has the level",
+                       "phase_launches_per_solve": {p: res[p]["batch"].kernel_nodes for p in ("mixed", "fp64")},
+                       "phase_groups": {p: res[p]["batch"].groups for p in ("mixed", "fp64")},
+                       "branches": {p: {"ms_per_step": res[p]["branches_ms"],
+                                        "value": world * dofs / (res[p]["branches_ms"] * 1e-3),
+                                        "launches_per_solve": res[p]["branches"].kernel_nodes}
+                                    for p in ("mixed", "fp64")}},
+            "smoother": smoother,
             "accuracy": {"max_rel_l2_diff_mixed_fp64": worst,
+                         "e_alg_over_e_disc": alg,
+                         "e_alg_over_e_disc_max": max(max(v.values()) for v in alg.values()),
+                         "e_disc": "Richardson: ||u_bar_h - P u_bar_2h|| / 3, u_bar from FP64 solves with 8 "
+                                   "correction steps per level; one instance per level count",
                          "flags": res["mixed"]["flags"] | res["fp64"]["flags"]},
             "setup_s": {p: res[p]["setup_s"] for p in ("mixed", "fp64")},
             "gpu_launches": launches * args.steps, "clocks": clk.summary(),
@@ -713,6 +777,7 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
     for prec in ("mixed", "fp64"):
         res[prec]["batch"].close()
+        res[prec]["branches"].close()
         for s in res[prec]["solvers"]:
             s.close()
     if dist is not None:

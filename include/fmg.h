@@ -183,14 +183,44 @@ fmg_status fmg_sync(fmg_ctx* c, fmg_stats* st);
  * for the work; sts (count entries) receives each instance's statistics when non-NULL. */
 fmg_status fmg_solve_batch(fmg_ctx** cs, int count, double** u_outs, fmg_stats* sts);
 
-/* A reusable batch: one CUDA graph in which every instance's whole Algorithm 3.2 schedule is
- * an independent branch on a stream of its own, so their work overlaps on the device.  The
- * instances' augmented-space Newton kernels run on thread-block clusters (hardware barriers,
- * no cooperative launch), which many instances can run concurrently.  The contexts must stay
- * alive and must not be solved on their own while a batch solve is running; their results
- * are at fmg_solution(ctx).  stream: the launch stream (NULL: one the batch creates). */
+/* A reusable batch: one CUDA graph that solves every instance once (Algorithm 3.2 for each).
+ * The instances' augmented-space Newton kernels run on thread-block clusters (hardware
+ * barriers, no cooperative launch), which many instances can run concurrently.  Two layouts:
+ *
+ *   FMG_BATCH_PHASES: level-synchronous phases.  Instances whose schedules agree launch for
+ *     launch (same dimension, 1/H, precision, smoother, cycle and Newton settings; any number
+ *     of refinements and any g and f_scale) form a group.  Stage k of Algorithm 3.2 (the
+ *     correction step on level k) is the same sequence of kernels with the same grids for
+ *     every member that has a level k, so each kernel of the stage is ONE launch over the
+ *     work list of (instance, tile) items of all members still active at that stage (members
+ *     sorted by their level count, so the active ones are a prefix): the kernel's own tiles in
+ *     x and y, the instance in z, each instance's arguments read from a device table built at
+ *     creation.  A solve is then as many launches as the longest member's schedule, per
+ *     group, instead of the sum over instances.  2D only (the 3D kernels tile z).
+ *   FMG_BATCH_BRANCHES: every instance's whole schedule is an independent branch on a
+ *     stream of its own, so their kernels overlap on the device.
+ *   FMG_BATCH_AUTO: PHASES when every instance's schedule is made of phase-batchable kernels
+ *     (the 2D forms), BRANCHES otherwise.
+ *
+ * Both layouts run the same kernels with the same arguments for each instance, so they give
+ * the same bits.  The contexts must stay alive and must not be solved on their own while a
+ * batch solve is running; their results are at fmg_solution(ctx).  stream: the launch stream
+ * (NULL: one the batch creates).  fmg_batch_create uses FMG_BATCH_AUTO. */
 typedef struct fmg_batch fmg_batch;
+typedef enum { FMG_BATCH_AUTO = 0, FMG_BATCH_PHASES = 1, FMG_BATCH_BRANCHES = 2 } fmg_batch_mode;
 fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** out);
+/* mode: an fmg_batch_mode; FMG_BATCH_PHASES fails with FMG_ERR_INVALID (and a message naming
+ * the first kernel that is not phase-batchable) instead of falling back to branches.
+ * phase_split (phase layout): each set of instances whose schedules agree is dealt round-robin
+ * (after sorting by level count) into that many groups, which run as parallel branches of
+ * phases, so that one group's latency-bound phases (the Newton kernels, the one-CTA coarse
+ * cycles) overlap another's streaming ones; 0: the default; 1..1024. */
+fmg_status fmg_batch_create_mode(fmg_ctx** cs, int count, void* stream, int mode, int phase_split,
+                                 fmg_batch** out);
+/* The layout a batch uses (FMG_BATCH_PHASES or FMG_BATCH_BRANCHES), the kernel nodes of its
+ * graph (launches per batch solve) and its number of phase groups (0 for branches); each
+ * output may be NULL. */
+fmg_status fmg_batch_info(const fmg_batch* b, int* mode, int* kernel_nodes, int* groups);
 /* Launches the batch graph (after work already queued on the contexts' own streams).  With
  * sts == NULL it returns at once; otherwise it waits and fills count fmg_stats. */
 fmg_status fmg_batch_solve(fmg_batch* b, fmg_stats* sts);

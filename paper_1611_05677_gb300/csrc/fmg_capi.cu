@@ -7,11 +7,13 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "fmg_internal.cuh"
+#include "fmg_phase.cuh"
 
 using namespace fmg;
 
@@ -67,6 +69,9 @@ struct fmg_batch {
   std::vector<cudaEvent_t> events;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int mode = FMG_BATCH_BRANCHES;
+  int kernels = 0;             // kernel nodes of the graph
+  int groups = 0;              // phase groups (FMG_BATCH_PHASES)
 };
 
 namespace {
@@ -627,6 +632,21 @@ fmg_status check_level(fmg_ctx* c, int level, int lo) {
   return FMG_OK;
 }
 
+// Kernel nodes of a graph (the launches of one replay).
+int graph_kernel_nodes(cudaGraph_t graph) {
+  size_t nn = 0;
+  int k = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+      }
+  }
+  return k;
+}
+
 // Captures the whole schedule of Algorithm 3.2 into the context's graph (once).
 fmg_status ensure_graph(fmg_ctx* c) {
   if (c->gexec) return FMG_OK;
@@ -641,16 +661,7 @@ fmg_status ensure_graph(fmg_ctx* c) {
       return fail(c, FMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2) +
                                        (t_site ? std::string(" at ") + t_site : std::string()));
     }
-    size_t nn = 0;
-    c->graph_kernels = 0;
-    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
-      std::vector<cudaGraphNode_t> nodes(nn);
-      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
-        for (size_t i = 0; i < nn; ++i) {
-          cudaGraphNodeType t;
-          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c->graph_kernels;
-        }
-    }
+    c->graph_kernels = graph_kernel_nodes(graph);
     e = cudaGraphInstantiate(&c->gexec, graph, 0);
     if (e != cudaSuccess) {
       cudaGraphDestroy(graph);
@@ -660,6 +671,282 @@ fmg_status ensure_graph(fmg_ctx* c) {
     c->graph = graph;
   }
   return FMG_OK;
+}
+
+// ------------------------------------------------------------------ phase-batched graph
+// Phase groups per set of instances whose schedules agree, when the caller leaves it open.
+constexpr int kDefaultPhaseSplit = 8;
+
+// One step of an instance's captured schedule: a kernel launch (its phase-batchable form and
+// its arguments packed as a table entry) or a memset.
+struct PhaseStep {
+  bool memset = false;
+  cudaMemsetParams ms = {};
+  const PhaseKernel* pk = nullptr;
+  dim3 grid, block;
+  unsigned smem = 0;
+  dim3 cluster = dim3(0, 0, 0);   // x == 0: no cluster
+  std::vector<unsigned char> args;
+};
+
+const std::vector<PhaseKernel>& phase_registry() {
+  static const std::vector<PhaseKernel> reg = [] {
+    std::vector<PhaseKernel> r;
+    phase_kernels_stencil(r);
+    phase_kernels_ff(r);
+    phase_kernels_fused(r);
+    phase_kernels_newton(r);
+    return r;
+  }();
+  return reg;
+}
+
+const PhaseKernel* phase_lookup(const void* f) {
+  for (const PhaseKernel& k : phase_registry())
+    if (k.solo == f) return &k;
+  return nullptr;
+}
+
+bool same_step(const PhaseStep& a, const PhaseStep& b) {
+  if (a.memset != b.memset) return false;
+  if (a.memset) return true;
+  return a.pk == b.pk && a.grid.x == b.grid.x && a.grid.y == b.grid.y && a.block.x == b.block.x &&
+         a.block.y == b.block.y && a.block.z == b.block.z && a.smem == b.smem && a.cluster.x == b.cluster.x &&
+         a.cluster.y == b.cluster.y && a.cluster.z == b.cluster.z;
+}
+
+// Captures instance c's whole schedule (the cluster Newton kernel of size csz) on stream cap and
+// reads it back as a chain of steps.  False, with the reason, if a node is neither a memset nor
+// a phase-batchable kernel with a z extent of one.
+bool phase_chain(fmg_ctx* c, int csz, cudaStream_t cap, std::vector<PhaseStep>& chain, std::string& why) {
+  cudaStream_t saved = c->stream;
+  const bool timing = c->timing;
+  const int cluster = c->cluster_aug;
+  c->stream = cap;
+  c->cluster_aug = csz;
+  c->timing = false;
+  t_site = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  cudaError_t ce = e == cudaSuccess ? run_fmg(c) : e;
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) e = cudaStreamEndCapture(cap, &g);
+  c->stream = saved;
+  c->cluster_aug = cluster;
+  c->timing = timing;
+  if (ce != cudaSuccess || e != cudaSuccess) {
+    why = std::string("capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : e);
+    if (g) cudaGraphDestroy(g);
+    return false;
+  }
+  bool ok = true;
+  size_t nr = 0;
+  cudaGraphNode_t node = nullptr;
+  if (cudaGraphGetRootNodes(g, nullptr, &nr) != cudaSuccess || nr != 1 ||
+      cudaGraphGetRootNodes(g, &node, &nr) != cudaSuccess) {
+    why = "the schedule is not a single chain";
+    ok = false;
+  }
+  while (ok && node) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(node, &t) != cudaSuccess) {
+      why = "node type";
+      ok = false;
+      break;
+    }
+    if (t == cudaGraphNodeTypeKernel) {
+      cudaKernelNodeParams kp = {};
+      PhaseStep st;
+      if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess || !(st.pk = phase_lookup(kp.func))) {
+        why = "a kernel of the schedule has no phase-batched form";
+        ok = false;
+        break;
+      }
+      if (kp.gridDim.z != 1) {
+        why = "a kernel of the schedule tiles z";
+        ok = false;
+        break;
+      }
+      st.grid = kp.gridDim;
+      st.block = kp.blockDim;
+      st.smem = kp.sharedMemBytes;
+      cudaLaunchAttributeValue v = {};
+      if (cudaGraphKernelNodeGetAttribute(node, cudaKernelNodeAttributeClusterDimension, &v) == cudaSuccess &&
+          v.clusterDim.x > 0)
+        st.cluster = dim3(v.clusterDim.x, v.clusterDim.y, v.clusterDim.z);
+      cudaGetLastError();
+      st.args.resize(st.pk->arg_bytes);
+      st.pk->pack(kp.kernelParams, st.args.data());
+      chain.push_back(std::move(st));
+    } else if (t == cudaGraphNodeTypeMemset) {
+      PhaseStep st;
+      st.memset = true;
+      if (cudaGraphMemsetNodeGetParams(node, &st.ms) != cudaSuccess) {
+        why = "memset node";
+        ok = false;
+        break;
+      }
+      chain.push_back(std::move(st));
+    } else if (t != cudaGraphNodeTypeEmpty) {
+      why = "a node of the schedule is neither a kernel nor a memset";
+      ok = false;
+      break;
+    }
+    size_t nd = 0;
+    if (cudaGraphNodeGetDependentNodes(node, nullptr, nullptr, &nd) != cudaSuccess || nd > 1) {
+      why = "the schedule is not a single chain";
+      ok = false;
+      break;
+    }
+    cudaGraphNode_t next = nullptr;
+    if (nd == 1 && cudaGraphNodeGetDependentNodes(node, &next, nullptr, &nd) != cudaSuccess) {
+      why = "dependent node";
+      ok = false;
+      break;
+    }
+    node = nd == 1 ? next : nullptr;
+  }
+  cudaGraphDestroy(g);
+  return ok;
+}
+
+// Builds b's graph in the phase layout.  Instances are taken longest schedule first; each joins
+// the first group whose leader's chain agrees with its own step for step (a shorter schedule is
+// a prefix of a longer one), else it leads a new group; each group is then dealt into `split`.  Step p of a group is one launch over
+// its first n_p members (those with more than p steps) -- or their memsets -- after step p - 1;
+// the groups are independent branches between a fork and a join.
+bool build_phase_graph(fmg_batch* b, const std::vector<int>& csz, int split, std::string& why) {
+  const int n = (int)b->cs.size();
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    why = "capture stream";
+    return false;
+  }
+  std::vector<std::vector<PhaseStep>> chains(n);
+  bool ok = true;
+  for (int i = 0; i < n && ok; ++i) ok = phase_chain(b->cs[i], csz[i], cap, chains[i], why);
+  cudaStreamDestroy(cap);
+  if (!ok) return false;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return chains[x].size() > chains[y].size(); });
+  std::vector<std::vector<int>> groups;
+  for (int i : order) {
+    bool placed = false;
+    for (auto& gr : groups) {
+      const auto& lead = chains[gr[0]];
+      bool match = chains[i].size() <= lead.size();
+      for (size_t p = 0; match && p < chains[i].size(); ++p) match = same_step(chains[i][p], lead[p]);
+      if (match) {
+        gr.push_back(i);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back({i});
+  }
+  // each group dealt round-robin into `split` groups of similar level counts, which run as
+  // parallel branches (the latency-bound phases of one overlap the streaming ones of another)
+  if (split > 1) {
+    std::vector<std::vector<int>> dealt;
+    for (const auto& gr : groups) {
+      const int parts = std::min(split, (int)gr.size());
+      std::vector<std::vector<int>> sub(parts);
+      for (size_t k = 0; k < gr.size(); ++k) sub[k % parts].push_back(gr[k]);
+      for (auto& sg : sub) dealt.push_back(std::move(sg));
+    }
+    groups.swap(dealt);
+  }
+  // the active members of a group at step p (those with more than p steps: a prefix)
+  auto active = [&](const std::vector<int>& gr, size_t p) {
+    int k = 0;
+    while (k < (int)gr.size() && chains[gr[k]].size() > p) ++k;
+    return k;
+  };
+  cudaError_t e;
+  cudaGraph_t g = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) {
+    why = std::string("graph: ") + cudaGetErrorString(e);
+    return false;
+  }
+  auto bail = [&](cudaError_t err, const char* what) {
+    why = std::string(what) + ": " + cudaGetErrorString(err);
+    cudaGraphDestroy(g);
+    return false;
+  };
+  cudaGraphNode_t fork = nullptr;
+  if ((e = cudaGraphAddEmptyNode(&fork, g, nullptr, 0)) != cudaSuccess) return bail(e, "fork node");
+  std::vector<cudaGraphNode_t> tails;
+  int kernels = 0;
+  for (size_t q = 0; q < groups.size(); ++q) {
+    const auto& lead = chains[groups[q][0]];
+    cudaGraphNode_t prev = fork;
+    for (size_t p = 0; p < lead.size(); ++p) {
+      const int na = active(groups[q], p);
+      if (lead[p].memset) {
+        std::vector<cudaGraphNode_t> ms(na);
+        for (int k = 0; k < na; ++k)
+          if ((e = cudaGraphAddMemsetNode(&ms[k], g, &prev, 1, &chains[groups[q][k]][p].ms)) != cudaSuccess)
+            return bail(e, "memset node");
+        cudaGraphNode_t join = nullptr;
+        if ((e = cudaGraphAddEmptyNode(&join, g, ms.data(), ms.size())) != cudaSuccess) return bail(e, "join node");
+        prev = join;
+        continue;
+      }
+      const PhaseStep& st = lead[p];
+      if (st.smem > 48 * 1024 &&
+          (e = cudaFuncSetAttribute(st.pk->batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st.smem)) !=
+              cudaSuccess)
+        return bail(e, "phase kernel shared memory");
+      if (st.cluster.x * st.cluster.y * st.cluster.z > 8 &&
+          (e = cudaFuncSetAttribute(st.pk->batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+        return bail(e, "phase kernel cluster size");
+      // one launch per `cap` members: its table (the kernel's parameter) holds their entries
+      std::vector<cudaGraphNode_t> part;
+      std::vector<unsigned char> tab((size_t)st.pk->cap * st.pk->arg_bytes);
+      for (int k0 = 0; k0 < na; k0 += st.pk->cap) {
+        const int nk = std::min(st.pk->cap, na - k0);
+        std::fill(tab.begin(), tab.end(), (unsigned char)0);
+        for (int k = 0; k < nk; ++k)
+          std::memcpy(tab.data() + (size_t)k * st.pk->arg_bytes, chains[groups[q][k0 + k]][p].args.data(),
+                      st.pk->arg_bytes);
+        void* params[1] = {tab.data()};
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void*>(st.pk->batch);
+        kp.gridDim = dim3(st.grid.x, st.grid.y, (unsigned)nk);
+        kp.blockDim = st.block;
+        kp.sharedMemBytes = st.smem;
+        kp.kernelParams = params;
+        cudaGraphNode_t nd = nullptr;
+        if ((e = cudaGraphAddKernelNode(&nd, g, &prev, 1, &kp)) != cudaSuccess) return bail(e, "phase kernel node");
+        if (st.cluster.x > 0) {
+          cudaLaunchAttributeValue v = {};
+          v.clusterDim.x = st.cluster.x;
+          v.clusterDim.y = st.cluster.y;
+          v.clusterDim.z = st.cluster.z;
+          if ((e = cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributeClusterDimension, &v)) != cudaSuccess)
+            return bail(e, "phase kernel cluster");
+        }
+        ++kernels;
+        part.push_back(nd);
+      }
+      cudaGraphNode_t nd = part[0];
+      if (part.size() > 1 && (e = cudaGraphAddEmptyNode(&nd, g, part.data(), part.size())) != cudaSuccess)
+        return bail(e, "join node");
+      prev = nd;
+    }
+    tails.push_back(prev);
+  }
+  cudaGraphNode_t join = nullptr;
+  if ((e = cudaGraphAddEmptyNode(&join, g, tails.data(), tails.size())) != cudaSuccess) return bail(e, "join node");
+  if ((e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) {
+    b->exec = nullptr;
+    return bail(e, "phase graph instantiate");
+  }
+  b->graph = g;
+  b->kernels = kernels;
+  b->groups = (int)groups.size();
+  b->mode = FMG_BATCH_PHASES;
+  return true;
 }
 
 }  // namespace
@@ -850,7 +1137,24 @@ fmg_status fmg_batch_destroy(fmg_batch* b) {
 }
 
 fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** out) {
+  return fmg_batch_create_mode(cs, count, stream, FMG_BATCH_AUTO, 0, out);
+}
+
+fmg_status fmg_batch_info(const fmg_batch* b, int* mode, int* kernel_nodes, int* groups) {
+  if (!b) return fail(nullptr, FMG_ERR_INVALID, "batch is NULL");
+  if (mode) *mode = b->mode;
+  if (kernel_nodes) *kernel_nodes = b->kernels;
+  if (groups) *groups = b->groups;
+  return FMG_OK;
+}
+
+fmg_status fmg_batch_create_mode(fmg_ctx** cs, int count, void* stream, int mode, int phase_split,
+                                 fmg_batch** out) {
   if (!out || !cs || count < 1) return fail(nullptr, FMG_ERR_INVALID, "bad batch arguments");
+  if (mode != FMG_BATCH_AUTO && mode != FMG_BATCH_PHASES && mode != FMG_BATCH_BRANCHES)
+    return fail(nullptr, FMG_ERR_INVALID, "unknown batch mode");
+  if (phase_split < 0 || phase_split > 1024) return fail(nullptr, FMG_ERR_INVALID, "phase_split out of range");
+  if (phase_split == 0) phase_split = kDefaultPhaseSplit;
   *out = nullptr;
   int dev = -1;
   for (int i = 0; i < count; ++i) {
@@ -872,10 +1176,7 @@ fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** o
     if ((e = cudaStreamCreateWithFlags(&b->launch, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
     b->own_launch = true;
   }
-  b->streams.resize(count, nullptr);
   b->events.resize(count + 1, nullptr);
-  for (int i = 0; i < count; ++i)
-    if ((e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
   for (int i = 0; i <= count; ++i)
     if ((e = cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
   // cluster size of each instance's Newton kernel (outside the capture)
@@ -888,6 +1189,23 @@ fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** o
       return fail(nullptr, FMG_ERR_CUDA, "no usable thread-block cluster size for the batched Newton kernel");
     }
   }
+  if (mode != FMG_BATCH_BRANCHES) {
+    std::string why;
+    if (build_phase_graph(b, csz, phase_split, why)) {
+      *out = b;
+      return FMG_OK;
+    }
+    if (mode == FMG_BATCH_PHASES) {
+      fmg_batch_destroy(b);
+      return fail(nullptr, FMG_ERR_INVALID, "no phase layout for this batch: " + why);
+    }
+    // fall back to branches
+    cudaGetLastError();
+  }
+  b->mode = FMG_BATCH_BRANCHES;
+  b->streams.resize(count, nullptr);
+  for (int i = 0; i < count; ++i)
+    if ((e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
   // one graph: fork on the launch stream, every instance's whole schedule on its own stream, join
   if ((e = cudaStreamBeginCapture(b->launch, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return bail(e, "begin capture");
@@ -922,6 +1240,7 @@ fmg_status fmg_batch_create(fmg_ctx** cs, int count, void* stream, fmg_batch** o
   }
   b->graph = g;
   if ((e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) return bail(e, "batch instantiate");
+  b->kernels = graph_kernel_nodes(g);
   *out = b;
   return FMG_OK;
 }

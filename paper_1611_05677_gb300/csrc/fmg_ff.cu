@@ -6,6 +6,7 @@
 // HBM rate.  The FP32 multigrid cycle between residual and update is unchanged.
 #include "fmg_ff.cuh"
 #include "fmg_internal.cuh"
+#include "fmg_phase.cuh"
 
 namespace fmg {
 
@@ -19,7 +20,7 @@ unsigned cdiv_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); 
 // 0 on the boundary; r32 = fl32(r), and with d32 the first Chebyshev step from zero,
 // e = d = e0 r32.
 template <int D>
-__global__ void k_residual_ff(const double* __restrict__ u, const double* __restrict__ b, int n, ff sigma,
+__device__ __forceinline__ void k_residual_ff_body(const double* __restrict__ u, const double* __restrict__ b, int n, ff sigma,
                               float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
                               VarCoef vc, int ls) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,11 +53,16 @@ __global__ void k_residual_ff(const double* __restrict__ u, const double* __rest
   if (d32) d32[c] = e;
 }
 
+template <int D>
+__global__ void k_residual_ff(const double* __restrict__ u, const double* __restrict__ b, int n, ff sigma,
+                              float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
+                              VarCoef vc, int ls) { k_residual_ff_body<D>(u, b, n, sigma, r32, e32, d32, e0, vc, ls); }
+
 // b = w (g - a f(u)) on the interior nodes, 0 on the boundary (eq. 3.4 with the vertex rule).
-__global__ void k_nonlinear_rhs_ff(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
+__device__ __forceinline__ void k_nonlinear_rhs_ff_body(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
                                    int n, int dim, int kind, ff a, double a64, ff w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, l = blockIdx.z;
+  const int j = blockIdx.y, l = dim == 3 ? (int)blockIdx.z : 0;
   if (i > n) return;
   const long long np = n + 1;
   const long long idx = ((long long)l * np + j) * np + i;
@@ -65,6 +71,9 @@ __global__ void k_nonlinear_rhs_ff(const double* __restrict__ u, const double* _
     v = ff_mul(ff_sub(ff_load(g + idx), f_ff(kind, a, a64, ff_load(u + idx))), w);
   ff_store(b + idx, v);
 }
+
+__global__ void k_nonlinear_rhs_ff(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
+                                   int n, int dim, int kind, ff a, double a64, ff w) { k_nonlinear_rhs_ff_body(u, g, b, n, dim, kind, a, a64, w); }
 
 // FMG interpolation u_f = P u_c (the natural inclusion, eq. 3.3) on the interior fine nodes.
 template <int D>
@@ -172,7 +181,7 @@ __global__ void k_level_start_ff(const double* __restrict__ uc, double* __restri
 // carried along the strip and the x-neighbours come from the adjacent lanes (every lane forms
 // one more value, the one beyond the warp's edge on its side, which lanes 0 and 31 use).  The operations on each node are those of k_level_start_ff, in
 // the same order.  Lanes past the last column store nothing.
-__global__ void k_level_start_ff2(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
+__device__ __forceinline__ void k_level_start_ff2_body(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
                                   double* __restrict__ b, int n, int kind, ff a, double a64, ff w,
                                   float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
                                   int strip, VarCoef vc, int ls) {
@@ -239,10 +248,17 @@ __global__ void k_level_start_ff2(const double* __restrict__ uc, double* __restr
   }
 }
 
-__global__ void k_add_f32_ff(double* __restrict__ uff, const float* __restrict__ e, long long n) {
+__global__ void k_level_start_ff2(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
+                                  double* __restrict__ b, int n, int kind, ff a, double a64, ff w,
+                                  float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
+                                  int strip, VarCoef vc, int ls) { k_level_start_ff2_body(uc, u, g, b, n, kind, a, a64, w, r32, e32, d32, e0, strip, vc, ls); }
+
+__device__ __forceinline__ void k_add_f32_ff_body(double* __restrict__ uff, const float* __restrict__ e, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) ff_store(uff + i, ff_add_f(ff_load(uff + i), e[i]));
 }
+
+__global__ void k_add_f32_ff(double* __restrict__ uff, const float* __restrict__ e, long long n) { k_add_f32_ff_body(uff, e, n); }
 
 __global__ void k_ff_from_f64(const double* __restrict__ s, double* __restrict__ d, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -335,6 +351,15 @@ cudaError_t launch_ff_to_f64(const double* src_ff, double* dst, long long n, cud
   if (n <= 0) return cudaSuccess;
   k_ff_to_f64<<<cdiv_u(n, 256), 256, 0, s>>>(src_ff, dst, n);
   return cudaGetLastError();
+}
+
+
+// The 2D float-float kernels of the mixed solve, for phase-batched launches.
+void phase_kernels_ff(std::vector<PhaseKernel>& out) {
+  out.push_back(phase_kernel<&k_residual_ff_body<2>, kB, 16>(&k_residual_ff<2>));
+  out.push_back(phase_kernel<&k_nonlinear_rhs_ff_body, kB, 1>(&k_nonlinear_rhs_ff));
+  out.push_back(phase_kernel<&k_level_start_ff2_body, kB, 9>(&k_level_start_ff2));
+  out.push_back(phase_kernel<&k_add_f32_ff_body, 256, 1>(&k_add_f32_ff));
 }
 
 }  // namespace fmg

@@ -18,6 +18,7 @@
 
 #include "fmg_ff.cuh"
 #include "fmg_internal.cuh"
+#include "fmg_phase.cuh"
 
 namespace fmg {
 
@@ -69,7 +70,7 @@ __device__ __forceinline__ void tile_halfsweep(float* su, const float* sb, int l
 }
 
 template <int NU>
-__global__ void __launch_bounds__(kFB) k_pre2_fused(const float* __restrict__ b, float* __restrict__ u_out,
+__device__ __forceinline__ void k_pre2_fused_body(const float* __restrict__ b, float* __restrict__ u_out,
                                                      float* __restrict__ bc, float* __restrict__ uc, int n) {
   constexpr int H = 2 * NU + 2;
   constexpr int W = kFT + 2 * H;
@@ -136,10 +137,14 @@ __global__ void __launch_bounds__(kFB) k_pre2_fused(const float* __restrict__ b,
   }
 }
 
+template <int NU>
+__global__ void __launch_bounds__(kFB) k_pre2_fused(const float* __restrict__ b, float* __restrict__ u_out,
+                                                     float* __restrict__ bc, float* __restrict__ uc, int n) { k_pre2_fused_body<NU>(b, u_out, bc, uc, n); }
+
 // MODE 0: the smoothed correction goes to u_out; 1: it is added to the FP64 iterate u64 (the
 // ops' arrays); 2: it is added to the float-float iterate u64 (the solve's level data).
 template <int NU, int MODE>
-__global__ void __launch_bounds__(kFB) k_post2_fused(const float* __restrict__ u_in, const float* __restrict__ ec,
+__device__ __forceinline__ void k_post2_fused_body(const float* __restrict__ u_in, const float* __restrict__ ec,
                                                       const float* __restrict__ b, float* __restrict__ u_out,
                                                       double* __restrict__ u64, int n) {
   constexpr int H = 2 * NU;
@@ -212,6 +217,11 @@ __global__ void __launch_bounds__(kFB) k_post2_fused(const float* __restrict__ u
   }
 }
 
+template <int NU, int MODE>
+__global__ void __launch_bounds__(kFB) k_post2_fused(const float* __restrict__ u_in, const float* __restrict__ ec,
+                                                      const float* __restrict__ b, float* __restrict__ u_out,
+                                                      double* __restrict__ u64, int n) { k_post2_fused_body<NU, MODE>(u_in, ec, b, u_out, u64, n); }
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
   return raise_dyn_smem((const void*)kernel, bytes);
@@ -278,6 +288,19 @@ cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, co
     }
   }
   return cudaGetLastError();
+}
+
+
+// The fused 2D FP32 red-black kernels, for phase-batched launches.
+void phase_kernels_fused(std::vector<PhaseKernel>& out) {
+  out.push_back(phase_kernel<&k_pre2_fused_body<1>, kFB, 8>(&k_pre2_fused<1>));
+  out.push_back(phase_kernel<&k_pre2_fused_body<2>, kFB, 8>(&k_pre2_fused<2>));
+  out.push_back(phase_kernel<&k_post2_fused_body<1, 0>, kFB, 8>(&k_post2_fused<1, 0>));
+  out.push_back(phase_kernel<&k_post2_fused_body<1, 1>, kFB, 8>(&k_post2_fused<1, 1>));
+  out.push_back(phase_kernel<&k_post2_fused_body<1, 2>, kFB, 8>(&k_post2_fused<1, 2>));
+  out.push_back(phase_kernel<&k_post2_fused_body<2, 0>, kFB, 8>(&k_post2_fused<2, 0>));
+  out.push_back(phase_kernel<&k_post2_fused_body<2, 1>, kFB, 8>(&k_post2_fused<2, 1>));
+  out.push_back(phase_kernel<&k_post2_fused_body<2, 2>, kFB, 8>(&k_post2_fused<2, 2>));
 }
 
 }  // namespace fmg

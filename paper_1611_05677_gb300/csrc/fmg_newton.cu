@@ -38,6 +38,7 @@
 
 #include "fmg_ff.cuh"
 #include "fmg_internal.cuh"
+#include "fmg_phase.cuh"
 
 namespace fmg {
 
@@ -357,7 +358,7 @@ __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, Dev
 // in precision T (T = float in the mixed path: an inexact Newton step whose error the next
 // FP64 residual corrects, so the iteration converges to the same FP64 solution).
 template <typename T>
-__global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
+__device__ __forceinline__ void k_level1_newton_body(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
                                 double a, double tol, int maxit, DevState* st, int out_ff, VarCoef vc) {
   extern __shared__ double sm[];
   const int m = n1 - 1;
@@ -474,6 +475,10 @@ __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, d
       u[node_of(p, m, dim)] = U[p];
   }
 }
+
+template <typename T>
+__global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
+                                double a, double tol, int maxit, DevState* st, int out_ff, VarCoef vc) { k_level1_newton_body<T>(dim, n1, g, u, kind, a, tol, maxit, st, out_ff, vc); }
 
 // ------------------------------------------------------------------ augmented problem
 template <int D, bool JF32>
@@ -2294,7 +2299,7 @@ __global__ void __launch_bounds__(256) k_aug_update(double* __restrict__ u, int 
 }
 
 template <int D, bool JF32>
-__global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented_cluster(AugArgs A) {
+__device__ __forceinline__ void k_augmented_cluster_body(const AugArgs& A) {
   using G = Aug<D, JF32>;
   using FT = typename std::conditional<JF32, float, double>::type;
   namespace cg = cooperative_groups;
@@ -2355,6 +2360,11 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
     fine_pass<D, JF32>(A, kUpdate, acc, cv, S.sa[1], cell, 0);
     __syncthreads();
   }
+}
+
+template <int D, bool JF32>
+__global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented_cluster(const __grid_constant__ AugArgs A) {
+  k_augmented_cluster_body<D, JF32>(A);
 }
 
 template <int D, bool JF32>
@@ -2615,6 +2625,18 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   else
     k_aug_update<3><<<dim3(gx, (unsigned)gy), 256, 0, s>>>(u, gk.n, ls, coarse_cells, cf, out_f64);
   return cudaGetLastError();
+}
+
+
+// The level-1 Newton kernel and the cluster form of the augmented Newton kernel (2D), for
+// phase-batched launches.
+void phase_kernels_newton(std::vector<PhaseKernel>& out) {
+  out.push_back(phase_kernel<&k_level1_newton_body<float>, 256, 2>(&k_level1_newton<float>));
+  out.push_back(phase_kernel<&k_level1_newton_body<double>, 256, 2>(&k_level1_newton<double>));
+  out.push_back(phase_kernel<&k_augmented_cluster_body<2, true>, Aug<2, true>::NT, 512 / Aug<2, true>::NT>(
+      &k_augmented_cluster<2, true>));
+  out.push_back(phase_kernel<&k_augmented_cluster_body<2, false>, Aug<2, false>::NT, 512 / Aug<2, false>::NT>(
+      &k_augmented_cluster<2, false>));
 }
 
 }  // namespace fmg

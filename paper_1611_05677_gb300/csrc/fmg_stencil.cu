@@ -19,6 +19,7 @@
 
 #include "fmg_ff.cuh"
 #include "fmg_internal.cuh"
+#include "fmg_phase.cuh"
 
 namespace fmg {
 
@@ -31,7 +32,7 @@ inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) /
 
 // ------------------------------------------------------------------ red-black Gauss-Seidel
 template <typename T>
-__global__ void k_rbgs2(T* __restrict__ u, const T* __restrict__ b, int n, int colour) {
+__device__ __forceinline__ void k_rbgs2_body(T* __restrict__ u, const T* __restrict__ b, int n, int colour) {
   const int j = blockIdx.y + 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int par = (colour + j) & 1;
@@ -42,6 +43,9 @@ __global__ void k_rbgs2(T* __restrict__ u, const T* __restrict__ b, int n, int c
   const T s = (u[c - 1] + u[c + 1]) + (u[c - np] + u[c + np]);
   u[c] = (b[c] + s) * T(0.25);
 }
+
+template <typename T>
+__global__ void k_rbgs2(T* __restrict__ u, const T* __restrict__ b, int n, int colour) { k_rbgs2_body<T>(u, b, n, colour); }
 
 template <typename T>
 __global__ void k_rbgs3(T* __restrict__ u, const T* __restrict__ b, int n, int colour, T bscale, T inv6) {
@@ -78,7 +82,7 @@ __device__ __forceinline__ T prolong_at(const T* __restrict__ ec, long long cp, 
 }
 
 template <typename T, int D, bool PROL>
-__global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restrict__ d, const T* __restrict__ b, int n,
+__device__ __forceinline__ void k_cheb_body(const T* __restrict__ u, T* __restrict__ uo, T* __restrict__ d, const T* __restrict__ b, int n,
                        T bscale, T cd, T cr, int first, int strip, const T* __restrict__ ec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = D == 3 ? blockIdx.y + 1 : 0;                 // in-plane row (3D only)
@@ -119,11 +123,15 @@ __global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restric
   }
 }
 
+template <typename T, int D, bool PROL>
+__global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restrict__ d, const T* __restrict__ b, int n,
+                       T bscale, T cd, T cr, int first, int strip, const T* __restrict__ ec) { k_cheb_body<T, D, PROL>(u, uo, d, b, n, bscale, cd, cr, first, strip, ec); }
+
 // The last Chebyshev step of the mixed path's top-level FP32 cycle fused with its update
 // u64 += u + d_new (the new correction is neither stored nor read back); FF: u64 holds
 // float-float values (the solve's level data) instead of FP64 ones (the ops' arrays).
 template <int D, bool FF>
-__global__ void k_cheb_add64(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ b,
+__device__ __forceinline__ void k_cheb_add64_body(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ b,
                              double* __restrict__ u64, int n, float bscale, float cd, float cr, int first, int strip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = D == 3 ? blockIdx.y + 1 : 0;
@@ -152,11 +160,18 @@ __global__ void k_cheb_add64(const float* __restrict__ u, const float* __restric
   }
 }
 
+template <int D, bool FF>
+__global__ void k_cheb_add64(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ b,
+                             double* __restrict__ u64, int n, float bscale, float cd, float cr, int first, int strip) { k_cheb_add64_body<D, FF>(u, d, b, u64, n, bscale, cd, cr, first, strip); }
+
 template <typename T>
-__global__ void k_copy_t(const T* __restrict__ s, T* __restrict__ d, long long n) {
+__device__ __forceinline__ void k_copy_t_body(const T* __restrict__ s, T* __restrict__ d, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = s[i];
 }
+
+template <typename T>
+__global__ void k_copy_t(const T* __restrict__ s, T* __restrict__ d, long long n) { k_copy_t_body<T>(s, d, n); }
 
 __global__ void k_to_f32(const double* __restrict__ s, float* __restrict__ d, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,7 +193,7 @@ __device__ __forceinline__ T res3(const T* __restrict__ u, const T* __restrict__
 // With dc != NULL the coarse level's first Chebyshev step from its zero start is taken here
 // too: u_c = d_c = e0 b_c (e0 = cr_0 / diag of the coarse level).
 template <typename TF, typename TC>
-__global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
+__device__ __forceinline__ void k_resrestrict2_body(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
                                TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int J = blockIdx.y + 1;
@@ -195,6 +210,10 @@ __global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ 
   uc[cc] = e1;
   if (dc) dc[cc] = e1;
 }
+
+template <typename TF, typename TC>
+__global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
+                               TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) { k_resrestrict2_body<TF, TC>(u, b, nf, bc, uc, ncells, dc, e0); }
 
 template <typename TF, typename TC>
 __global__ void k_resrestrict3(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TF sigma,
@@ -377,7 +396,7 @@ int vc_ls(const VarCoef& vc, int n) {
 
 // ------------------------------------------------------------------ prolongation (+ correction)
 template <typename TF, typename TC>
-__global__ void k_prolong2(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) {
+__device__ __forceinline__ void k_prolong2_body(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   if (i > nf - 1) return;
@@ -388,6 +407,9 @@ __global__ void k_prolong2(const TC* __restrict__ e, int nc, TF* __restrict__ u,
   const long long f = (long long)j * (nf + 1) + i;
   u[f] = add ? u[f] + v : v;
 }
+
+template <typename TF, typename TC>
+__global__ void k_prolong2(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) { k_prolong2_body<TF, TC>(e, nc, u, nf, add); }
 
 template <typename TF, typename TC>
 __global__ void k_prolong3(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) {
@@ -424,10 +446,10 @@ __device__ __forceinline__ bool interior_of(long long idx, int n, int dim) {
 
 // b = w (g - f(u)) on the interior nodes, 0 on the boundary; one thread per node of row
 // (j[, l]) = (blockIdx.y[, blockIdx.z]), so no index division.
-__global__ void k_nonlinear_rhs(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
+__device__ __forceinline__ void k_nonlinear_rhs_body(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
                                 int n, int dim, int kind, double a, double w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, l = blockIdx.z;
+  const int j = blockIdx.y, l = dim == 3 ? (int)blockIdx.z : 0;
   if (i > n) return;
   const long long np = n + 1;
   const long long idx = ((long long)l * np + j) * np + i;
@@ -436,6 +458,9 @@ __global__ void k_nonlinear_rhs(const double* __restrict__ u, const double* __re
   if (inner) v = w * (g[idx] - f_only<double>(kind, a, u[idx]));
   b[idx] = v;
 }
+
+__global__ void k_nonlinear_rhs(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
+                                int n, int dim, int kind, double a, double w) { k_nonlinear_rhs_body(u, g, b, n, dim, kind, a, w); }
 
 __global__ void k_decimate(const double* __restrict__ src, int nf, double* __restrict__ dst, int nc, int dim) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -473,7 +498,7 @@ __device__ __forceinline__ long long coarse_node(int r, int m, int dim) {
 // u = A_1^{-1} b on the level-1 unknowns.  b is staged in shared memory; A_1^{-1} is
 // symmetric, so thread r reads column r (coalesced across threads).
 template <typename T>
-__global__ void k_coarse_solve(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ u, int m,
+__device__ __forceinline__ void k_coarse_solve_body(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ u, int m,
                                int N, int dim) {
   extern __shared__ double bs[];
   for (int c = threadIdx.x; c < N; c += blockDim.x) bs[c] = (double)b[coarse_node(c, m, dim)];
@@ -489,6 +514,10 @@ __global__ void k_coarse_solve(const double* __restrict__ Ainv, const T* __restr
     u[coarse_node(r, m, dim)] = (T)(a0 + a1);
   }
 }
+
+template <typename T>
+__global__ void k_coarse_solve(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ u, int m,
+                               int N, int dim) { k_coarse_solve_body<T>(Ainv, b, u, m, N, dim); }
 
 // ------------------------------------------------------------------ coarse V-cycle in one CTA
 // The V(nu_pre, nu_post) cycle on levels jtop..1 with every level's u and b in shared
@@ -583,9 +612,9 @@ __device__ __forceinline__ T cta_res(const CoarseLevel<T, D>& L, int c, T sigma)
 // way.  The FP32 cycle's level-1 solve uses an FP32 copy of A_1^{-1} (Ainv32), staged in
 // shared memory while the top level loads; the FP64 cycle reads the FP64 A_1^{-1}.
 template <typename T, int D>
-__global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, const T* __restrict__ bg, int n0, int jtop, int nu_pre,
+__device__ __forceinline__ void k_vcycle_coarse_body(T* __restrict__ ug, const T* __restrict__ bg, int n0, int jtop, int nu_pre,
                                 int nu_post, const double* __restrict__ Ainv, const float* __restrict__ Ainv32,
-                                int cheb, ChebCoef cf, int zero_start) {
+                                int cheb, const ChebCoef& cf, int zero_start) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   // level descriptors, the same for every thread: in shared memory (a per-thread copy would
@@ -791,6 +820,11 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, cons
     for (int i = threadIdx.x; i < nodes; i += blockDim.x) ug[i] = top.u[i];
   }
 }
+
+template <typename T, int D>
+__global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, const T* __restrict__ bg, int n0, int jtop, int nu_pre,
+                                int nu_post, const double* __restrict__ Ainv, const float* __restrict__ Ainv32,
+                                int cheb, const __grid_constant__ ChebCoef cf, int zero_start) { k_vcycle_coarse_body<T, D>(ug, bg, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb, cf, zero_start); }
 
 }  // namespace
 
@@ -1131,6 +1165,30 @@ cudaError_t raise_dyn_smem(const void* kernel, size_t bytes) {
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) cur = bytes;
   return e;
+}
+
+
+// The 2D kernels of the solve's cycles, for phase-batched launches.
+void phase_kernels_stencil(std::vector<PhaseKernel>& out) {
+  out.push_back(phase_kernel<&k_rbgs2_body<float>, kBlock, 1>(&k_rbgs2<float>));
+  out.push_back(phase_kernel<&k_rbgs2_body<double>, kBlock, 1>(&k_rbgs2<double>));
+  out.push_back(phase_kernel<&k_cheb_body<float, 2, false>, 512, 1>(&k_cheb<float, 2, false>));
+  out.push_back(phase_kernel<&k_cheb_body<float, 2, true>, 512, 3>(&k_cheb<float, 2, true>));
+  out.push_back(phase_kernel<&k_cheb_body<double, 2, false>, 512, 4>(&k_cheb<double, 2, false>));
+  out.push_back(phase_kernel<&k_cheb_body<double, 2, true>, 512, 2>(&k_cheb<double, 2, true>));
+  out.push_back(phase_kernel<&k_cheb_add64_body<2, true>, 512, 1>(&k_cheb_add64<2, true>));
+  out.push_back(phase_kernel<&k_cheb_add64_body<2, false>, 512, 1>(&k_cheb_add64<2, false>));
+  out.push_back(phase_kernel<&k_copy_t_body<float>, 256, 1>(&k_copy_t<float>));
+  out.push_back(phase_kernel<&k_copy_t_body<double>, 256, 1>(&k_copy_t<double>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<float, float>, kBlock, 16>(&k_resrestrict2<float, float>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<double, double>, kBlock, 10>(&k_resrestrict2<double, double>));
+  out.push_back(phase_kernel<&k_prolong2_body<float, float>, kBlock, 1>(&k_prolong2<float, float>));
+  out.push_back(phase_kernel<&k_prolong2_body<double, double>, kBlock, 1>(&k_prolong2<double, double>));
+  out.push_back(phase_kernel<&k_nonlinear_rhs_body, kBlock, 1>(&k_nonlinear_rhs));
+  out.push_back(phase_kernel<&k_coarse_solve_body<float>, 64, 24>(&k_coarse_solve<float>));
+  out.push_back(phase_kernel<&k_coarse_solve_body<double>, 64, 24>(&k_coarse_solve<double>));
+  out.push_back(phase_kernel<&k_vcycle_coarse_body<float, 2>, 1024, 1>(&k_vcycle_coarse<float, 2>));
+  out.push_back(phase_kernel<&k_vcycle_coarse_body<double, 2>, 1024, 1>(&k_vcycle_coarse<double, 2>));
 }
 
 }  // namespace fmg

@@ -72,7 +72,7 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
            "fmg_op_smooth", "fmg_op_smooth_f32", "fmg_op_residual", "fmg_op_vcycle", "fmg_op_correction_step",
            "fmg_op_level1_solve", "fmg_op_prolong", "fmg_set_kernel_timing", "fmg_kernel_time",
            "fmg_graph_kernels", "fmg_vcycle_noalloc", "fmg_debug_barrier_fault", "fmg_fp64_fma_rate",
-           "fmg_batch_create",
+           "fmg_batch_create", "fmg_batch_create_mode", "fmg_batch_info",
            "fmg_batch_solve", "fmg_batch_sync", "fmg_batch_destroy", "fmg_server_create", "fmg_server_submit", "fmg_server_poll", "fmg_server_drain",
            "fmg_server_get_info", "fmg_server_last_error", "fmg_server_destroy", "fmg_autotune", "fmg_tuned_shape")
 KT_AUGMENTED = 0
@@ -124,6 +124,8 @@ def load():
         "fmg_debug_barrier_fault": (c_int, [c_void_p, ctypes.c_longlong, c_int]),
         "fmg_fp64_fma_rate": (c_int, [c_int, POINTER(c_double)]),
         "fmg_batch_create": (c_int, [POINTER(c_void_p), c_int, c_void_p, POINTER(c_void_p)]),
+        "fmg_batch_create_mode": (c_int, [POINTER(c_void_p), c_int, c_void_p, c_int, c_int, POINTER(c_void_p)]),
+        "fmg_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fmg_batch_solve": (c_int, [c_void_p, S]),
         "fmg_batch_sync": (c_int, [c_void_p]),
         "fmg_batch_destroy": (c_int, [c_void_p]),
@@ -344,11 +346,33 @@ def fmg_vcycle_noalloc(dim, coarse_cells, level, b, u, cycles=1, nu_pre=2, nu_po
                                      sp))
 
 
+BATCH_AUTO, BATCH_PHASES, BATCH_BRANCHES = 0, 1, 2
+_BATCH_MODES = {"auto": BATCH_AUTO, "phases": BATCH_PHASES, "branches": BATCH_BRANCHES}
+
+
 def fmg_batch_create(ctxs, stream=None):
     arr = (c_void_p * len(ctxs))(*[c.value for c in ctxs])
     out = c_void_p()
     _check(load().fmg_batch_create(arr, len(ctxs), getattr(stream, "cuda_stream", stream), byref(out)))
     return out
+
+
+def fmg_batch_create_mode(ctxs, stream=None, mode="auto", phase_split=0):
+    """mode: "auto", "phases" or "branches" (or the FMG_BATCH_* value); phase_split: phase groups
+    per set of agreeing schedules (0: the library's default)."""
+    arr = (c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    out = c_void_p()
+    m = _BATCH_MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(load().fmg_batch_create_mode(arr, len(ctxs), getattr(stream, "cuda_stream", stream), m, int(phase_split),
+                                        byref(out)))
+    return out
+
+
+def fmg_batch_info(batch):
+    """(mode, kernel nodes per solve, phase groups) of a batch; mode is "phases" or "branches"."""
+    m, k, g = c_int(), c_int(), c_int()
+    _check(load().fmg_batch_info(batch, byref(m), byref(k), byref(g)))
+    return {BATCH_PHASES: "phases", BATCH_BRANCHES: "branches"}.get(m.value, "?"), k.value, g.value
 
 
 def fmg_batch_solve(batch, stats=None):
@@ -541,18 +565,21 @@ class Solver:
 
 
 class Batch:
-    """Several Solver instances solved together: one CUDA graph with a branch per instance.
+    """Several Solver instances solved together in one CUDA graph.
 
-    solve() launches it after the caller's current stream and orders the caller's
-    stream after it; results are each solver's solution().
+    mode: "phases" (one launch per phase over all instances, 2D), "branches" (a branch per
+    instance) or "auto" (phases where the schedules allow it).  solve() launches it after the
+    caller's current stream and orders the caller's stream after it; results are each
+    solver's solution().
     """
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, mode="auto", phase_split=0):
         import torch
 
         self.solvers = list(solvers)
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        self.handle = fmg_batch_create([s.ctx for s in self.solvers], self.stream.cuda_stream)
+        self.handle = fmg_batch_create_mode([s.ctx for s in self.solvers], self.stream.cuda_stream, mode, phase_split)
+        self.mode, self.kernel_nodes, self.groups = fmg_batch_info(self.handle)
 
     def solve(self, wait: bool = False):
         import torch

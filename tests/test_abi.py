@@ -108,6 +108,10 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fmg_solve_batch(None, 1, None, None) == fmg.FMG_ERR_INVALID
     batch = ctypes.c_void_p()
     assert lib.fmg_batch_create(two, 2, None, ctypes.byref(batch)) == fmg.FMG_ERR_INVALID
+    for mode in (fmg.BATCH_AUTO, fmg.BATCH_PHASES, fmg.BATCH_BRANCHES, 7):
+        assert lib.fmg_batch_create_mode(two, 2, None, mode, 0, ctypes.byref(batch)) == fmg.FMG_ERR_INVALID
+    assert b"unknown batch mode" in lib.fmg_last_error(None)
+    assert lib.fmg_batch_info(None, None, None, None) == fmg.FMG_ERR_INVALID
     assert lib.fmg_batch_destroy(None) == fmg.FMG_OK
     # the request server's calls reject NULL servers
     assert lib.fmg_server_submit(None, None, None, None, None) == fmg.FMG_ERR_INVALID

@@ -30,3 +30,25 @@ def test_cycles_and_smoother_enter_linearly():
     assert three - two == pytest.approx(two - one)
     # a Chebyshev step streams u, b, d and writes u, d: 20 B in FP32 against a sweep's 12
     assert two - bench.solve_bytes_per_dof(2, True, 2, "rbgs") == pytest.approx(2 * 4 * 8 * (4 / 3) ** 2)
+
+
+def test_batch_richardson_prolongation_is_the_p1_interpolation():
+    # the nodal P1 interpolation of the batch bench's Richardson estimate reproduces linear
+    # functions, and at the midpoint of a cell's (0,0)-(1,1) diagonal it averages that
+    # diagonal's ends (not the other two corners)
+    import numpy as np
+
+    import bench
+
+    n = 8
+    x = np.arange(n + 1) / n
+    X, Y = np.meshgrid(x, x)          # rows y, columns x: x fastest
+    lin = 0.3 + 1.7 * X - 2.1 * Y
+    xf = np.arange(2 * n + 1) / (2 * n)
+    Xf, Yf = np.meshgrid(xf, xf)
+    assert np.allclose(bench.prolong_2d(lin), 0.3 + 1.7 * Xf - 2.1 * Yf, atol=1e-14)
+    e = np.zeros((n + 1, n + 1))
+    e[2, 3] = 1.0                      # coarse node x = 3, y = 2
+    f = bench.prolong_2d(e)
+    assert f[5, 7] == 0.5 and f[3, 5] == 0.5   # diagonal midpoints towards (+1, +1) and (-1, -1)
+    assert f[5, 5] == 0.0 and f[3, 7] == 0.0   # the other diagonal is not an edge

@@ -130,3 +130,117 @@ def test_contexts_of_different_sizes_in_any_order(fmg):
         assert st.flags == 0
         sb.close()
         ss.close()
+
+
+def phase_problems(H=4, rs=(1, 4, 2, 5, 3, 4), seed=11):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, r in enumerate(rs):
+        k = 1 + i % 3
+        modes = [((1, 1), 1.0), ((k, 2), float(rng.uniform(-0.5, 0.5)))]
+        out.append(W.Problem(dim=2, coarse_cells=H, refinements=r, f="cubic", a=float(rng.uniform(0.5, 2.0)),
+                             modes=modes))
+    return out
+
+
+@pytest.mark.parametrize("prec,smoother", [("mixed", "chebyshev"), ("mixed", "rbgs"), ("fp64", "rbgs"),
+                                           ("fp64", "chebyshev")])
+def test_phase_batch_gives_the_branch_batch_bits(fmg, prec, smoother):
+    # uneven level counts (1..5 refinements), per-instance a and g: one phase group whose
+    # stages run every instance that still has the level; same kernels, same arguments per
+    # instance as the branch layout, so the same bits and the same Newton counts
+    probs = phase_problems()
+    res = {}
+    for mode in ("branches", "phases"):
+        solvers = [fmg.Solver(fmg.make_params(p, precision=prec, smoother=smoother), p.g_nodal()) for p in probs]
+        b = fmg.Batch(solvers, mode=mode, phase_split=1)
+        assert b.mode == mode
+        stats = b.solve(wait=True)
+        res[mode] = ([s.solution().cpu().numpy() for s in solvers], stats, b.kernel_nodes, b.groups)
+        # a second launch gives the same bits
+        b.solve(wait=True)
+        for s, u in zip(solvers, res[mode][0]):
+            assert np.array_equal(s.solution().cpu().numpy(), u)
+        b.close()
+        for s in solvers:
+            s.close()
+    ub, sb, kb, _ = res["branches"]
+    up, sp, kp, gp = res["phases"]
+    assert gp == 1
+    assert kp < kb   # one launch per phase instead of one per instance
+    for i, p in enumerate(probs):
+        assert sp[i].flags == 0, p.name
+        assert np.array_equal(up[i], ub[i]), p.name
+        assert list(sp[i].newton_iters[:p.levels]) == list(sb[i].newton_iters[:p.levels]), p.name
+
+
+def test_phase_batch_fp64_matches_the_oracle(fmg):
+    probs = phase_problems(rs=(3, 1, 2))
+    solvers = [fmg.Solver(fmg.make_params(p, precision="fp64"), p.g_nodal()) for p in probs]
+    b = fmg.Batch(solvers, mode="phases")
+    stats = b.solve(wait=True)
+    for i, p in enumerate(probs):
+        assert stats[i].flags == 0
+        hier = O.build_hierarchy(p.dim, p.coarse_cells, p.refinements)
+        res = O.fmg(hier, p.g_nodal(), p.f, p.a)
+        ref = O.to_nodal(hier.level(p.refinements + 1), res.u[-1])
+        assert rel(solvers[i].solution().cpu().numpy(), ref) <= FP64_TOL, p.name
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_phase_batch_groups_by_schedule(fmg):
+    # two coarse meshes (1/H = 4 and 8) cannot share launches: two groups, each a branch of
+    # phases, and the results are the branch layout's
+    probs = phase_problems(H=4, rs=(2, 3)) + phase_problems(H=8, rs=(1, 2), seed=3)
+    res = {}
+    for mode in ("branches", "phases"):
+        solvers = [fmg.Solver(fmg.make_params(p, precision="mixed", smoother="chebyshev"), p.g_nodal())
+                   for p in probs]
+        b = fmg.Batch(solvers, mode=mode, phase_split=1)
+        b.solve(wait=True)
+        res[mode] = ([s.solution().cpu().numpy() for s in solvers], b.groups)
+        b.close()
+        for s in solvers:
+            s.close()
+    assert res["phases"][1] == 2
+    for a, c in zip(res["phases"][0], res["branches"][0]):
+        assert np.array_equal(a, c)
+
+
+def test_phase_layout_refuses_3d_and_auto_falls_back(fmg):
+    probs = phase_problems(rs=(2,)) + [W.Problem(dim=3, coarse_cells=4, refinements=1, f="cubic",
+                                                 modes=[((1, 1, 1), 1.0)])]
+    solvers = [fmg.Solver(fmg.make_params(p, precision="fp64"), p.g_nodal()) for p in probs]
+    with pytest.raises(fmg.FMGError) as ei:
+        fmg.Batch(solvers, mode="phases")
+    assert "phase" in str(ei.value)
+    b = fmg.Batch(solvers)   # auto: branches
+    assert b.mode == "branches"
+    stats = b.solve(wait=True)
+    assert all(st.flags == 0 for st in stats)
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_phase_groups_split_into_parallel_branches(fmg):
+    # the default deals one set of agreeing schedules into several groups of similar level
+    # counts; each still gives every instance the same bits
+    probs = phase_problems(rs=(4, 1, 3, 2, 4, 1, 3, 2, 5))
+    solvers = [fmg.Solver(fmg.make_params(p, precision="mixed", smoother="chebyshev"), p.g_nodal()) for p in probs]
+    ref = fmg.Batch(solvers, mode="branches")
+    ref.solve(wait=True)
+    want = [s.solution().cpu().numpy() for s in solvers]
+    ref.close()
+    for split, groups in ((3, 3), (0, 8), (64, 9)):
+        b = fmg.Batch(solvers, mode="phases", phase_split=split)
+        assert b.groups == groups
+        stats = b.solve(wait=True)
+        assert all(st.flags == 0 for st in stats)
+        for s, u in zip(solvers, want):
+            assert np.array_equal(s.solution().cpu().numpy(), u)
+        b.close()
+    for s in solvers:
+        s.close()
