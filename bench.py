@@ -798,11 +798,39 @@ def percentile(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
+def random_mode_g(p, out):
+    """Writes the request's own random-mode g = sum_q c_q prod_ax sin(k_q,ax pi x_ax) on its nodal
+    grid (x fastest) into the host tensor `out`, as one matrix product of the separable factors
+    (the last axis' factors times the in-plane ones): milliseconds on the host cores even for a
+    16.8M-node field."""
+    import torch
+
+    n = p.n_fine
+    x = torch.arange(n + 1, dtype=torch.float64) / n
+    outer, inner = [], []
+    for kv, c in p.g_modes:
+        sx = torch.sin(kv[0] * math.pi * x)
+        if p.dim == 2:
+            inner.append(sx)
+            outer.append(float(c) * torch.sin(kv[1] * math.pi * x))
+        else:
+            inner.append(torch.outer(torch.sin(kv[1] * math.pi * x), sx).reshape(-1))
+            outer.append(float(c) * torch.sin(kv[2] * math.pi * x))
+    torch.mm(torch.stack(outer).T, torch.stack(inner), out=out.view(n + 1, -1))
+
+
+def size_class(p):
+    if p.dim == 2:
+        return "2d_r5-7" if p.refinements <= 7 else "2d_r8-10"
+    return "3d_r3-4" if p.refinements <= 4 else "3d_r5-6"
+
+
 def run_serve(args):
     """Open-loop serving: requests submitted at their Poisson arrival times; then the same
-    requests submitted at once (the server's capacity).  Host buffers are pinned; g fields come
-    from a pool of two seeded random-mode fields per shape (drawing a 16.8M-node field on the
-    host takes longer than the mean gap between requests)."""
+    requests submitted at once (the server's capacity).  Every request carries its own seeded
+    random-mode g, written into a pinned host buffer just before it is submitted (a ring of
+    buffers per shape; a buffer is refilled only after the request that used it last has
+    completed)."""
     import numpy as np
     import torch
 
@@ -814,26 +842,20 @@ def run_serve(args):
     __graft_entry__.build()
     from paper_1611_05677_gb300 import fmg, workloads as W
 
+    torch.set_num_threads(os.cpu_count() or 1)
     reqs = W.request_stream(seed=rank, count=args.serve_count, rate=args.serve_rate)
-    log("drawing g pool")
-    pool = {}
+    ring = args.max_inflight + 4
+    shapes = {}
     for _, p in reqs:
-        key = (p.dim, p.refinements)
-        lst = pool.setdefault(key, [])
-        if len(lst) < 2:
-            lst.append(torch.from_numpy(p.g_nodal()).pin_memory())
-    outs = {k: [torch.empty(v[0].shape, dtype=torch.float64).pin_memory() for _ in range(args.max_inflight + 2)]
-            for k, v in pool.items()}
+        shapes.setdefault((p.dim, p.refinements), (p.n_fine + 1,) * p.dim)
+    log("allocating pinned rings")
+    gbuf = {k: [torch.empty(v, dtype=torch.float64).pin_memory() for _ in range(ring)] for k, v in shapes.items()}
+    ubuf = {k: [torch.empty(v, dtype=torch.float64).pin_memory() for _ in range(ring)] for k, v in shapes.items()}
+    last = {k: [None] * ring for k in shapes}
+    nxt = {k: 0 for k in shapes}
     params = [fmg.make_params(p, precision="mixed") for _, p in reqs]
     server = fmg.Server(max_inflight=args.max_inflight)
-    rr = {k: 0 for k in pool}
-
-    def buffers(i):
-        p = reqs[i][1]
-        key = (p.dim, p.refinements)
-        j = rr[key]
-        rr[key] = (j + 1) % len(outs[key])
-        return pool[key][i % len(pool[key])], outs[key][j]
+    gen_ms = []
 
     def collect(into):
         while True:
@@ -842,6 +864,25 @@ def run_serve(args):
                 return
             for r in rs:
                 into[r.ticket] = r
+
+    def buffers(i, into):
+        p = reqs[i][1]
+        key = (p.dim, p.refinements)
+        j = nxt[key]
+        nxt[key] = (j + 1) % ring
+        while last[key][j] is not None and last[key][j] not in into:
+            collect(into)
+            time.sleep(0.0002)
+        t = time.perf_counter()
+        random_mode_g(p, gbuf[key][j])
+        gen_ms.append((time.perf_counter() - t) * 1e3)
+        return key, j
+
+    def submit(i, into, tickets):
+        key, j = buffers(i, into)
+        tk = server.submit(params[i], gbuf[key][j], ubuf[key][j])
+        last[key][j] = tk
+        tickets.append(tk)
 
     # ---- open loop at the arrival times
     log("open loop")
@@ -856,19 +897,17 @@ def run_serve(args):
                     break
                 collect(done)
                 time.sleep(min(dt, 0.0005))
-            g, u = buffers(i)
-            tickets.append(server.submit(params[i], g, u))
+            submit(i, done, tickets)
         server.drain(600.0)
         t_end = time.perf_counter()
         collect(done)
         # ---- closed loop: everything at once (capacity)
         log("burst")
-        burst = {}
+        burst = dict(done)
         tb0 = time.perf_counter()
         btickets = []
         for i in range(args.serve_warmup, len(reqs)):
-            g, u = buffers(i)
-            btickets.append(server.submit(params[i], g, u))
+            submit(i, burst, btickets)
         server.drain(600.0)
         tb1 = time.perf_counter()
         collect(burst)
@@ -876,6 +915,17 @@ def run_serve(args):
     measured = range(args.serve_warmup, len(reqs))
     lat = [done[tickets[i]].latency_ms for i in measured]
     que = [done[tickets[i]].queue_ms for i in measured]
+    by_class = {}
+    for i in measured:
+        r = done[tickets[i]]
+        c = by_class.setdefault(size_class(reqs[i][1]), {"lat": [], "queue": [], "service": []})
+        c["lat"].append(r.latency_ms)
+        c["queue"].append(r.queue_ms)
+        c["service"].append(r.latency_ms - r.queue_ms)
+    classes = {k: {"count": len(v["lat"]), "latency_p50": percentile(v["lat"], 0.5),
+                   "latency_p99": percentile(v["lat"], 0.99), "queue_p50": percentile(v["queue"], 0.5),
+                   "queue_p99": percentile(v["queue"], 0.99), "service_p50": percentile(v["service"], 0.5),
+                   "service_p99": percentile(v["service"], 0.99)} for k, v in sorted(by_class.items())}
     bad = sum(1 for t in tickets if done[t].status != fmg.FMG_OK) + sum(
         1 for t in btickets if burst[t].status != fmg.FMG_OK)
     dofs = sum(reqs[i][1].fine_dofs for i in measured)
@@ -888,9 +938,11 @@ def run_serve(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 cycles + float-float (f32 pair) level data + f64 Newton", "data": "synthetic",
             "config": {"workload": SERVE_WORKLOAD, "requests": len(reqs), "measured": len(measured),
                        "rate_per_s": args.serve_rate, "max_inflight": args.max_inflight,
-                       "g": "pool of 2 seeded random-mode fields per (dim, refinements)"},
+                       "g": "each request's own seeded random-mode field, written on the host before its submit"},
             "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99), "max": max(lat),
                            "queue_p50": percentile(que, 0.5), "queue_p99": percentile(que, 0.99)},
+            "latency_by_size": classes,
+            "g_generation_ms": {"p50": percentile(gen_ms, 0.5), "p99": percentile(gen_ms, 0.99)},
             "served_dofs_per_s_open_loop": dofs / span,
             "offered_dofs_per_s": dofs / (reqs[-1][0] - reqs[args.serve_warmup][0]),
             "capacity_dofs_per_s_burst": dofs / (tb1 - tb0),

@@ -52,3 +52,23 @@ def test_batch_richardson_prolongation_is_the_p1_interpolation():
     f = bench.prolong_2d(e)
     assert f[5, 7] == 0.5 and f[3, 5] == 0.5   # diagonal midpoints towards (+1, +1) and (-1, -1)
     assert f[5, 5] == 0.0 and f[3, 7] == 0.0   # the other diagonal is not an edge
+
+
+def test_serve_requests_get_their_own_g():
+    # the serving bench writes each request's random-mode g from its separable factors; it is
+    # the workload's own g (closed-form mode sum), 2D and 3D
+    import numpy as np
+    import torch
+
+    import bench
+    from paper_1611_05677_gb300 import workloads as W
+
+    seen = set()
+    for _, p in W.request_stream(seed=2, count=200):
+        if p.n_fine > 128 or p.dim in seen:
+            continue
+        seen.add(p.dim)
+        out = torch.empty((p.n_fine + 1,) * p.dim, dtype=torch.float64)
+        bench.random_mode_g(p, out)
+        assert np.max(np.abs(out.numpy() - p.g_nodal())) <= 1e-12
+    assert seen == {2, 3}
