@@ -296,48 +296,119 @@ __host__ __device__ __forceinline__ ff ff_ldexp(ff x, int k) {
   return ff{x.hi * sc, x.lo * sc};
 }
 
-// exp(x) - 1 in float-float, from the exponential's own properties: x = k ln2 + r with k the
-// nearest integer to x / ln2 (|r| <= ln2 / 2, r formed in float-float with ln2 split into two
-// FP32 parts), then r = 2^5 s with |s| <= 0.011, expm1(s) by its Taylor series through s^6 (the
-// next term is below 4e-18), five squarings in the form q <- q (2 + q) (that is (1+q)^2 - 1,
-// which keeps the relative accuracy of a small q), and expm1(x) = 2^k q + (2^k - 1).  Relative
-// error about 1e-13 over the range the nonlinearities meet; |x| beyond 80 returns the FP32
-// limit (exp overflows there in FP32 anyway).
+// 2^(j/64) for j = -32 .. 31 (row j + 32) and 2^(j/64) - 1, as float-float pairs (hi = fl32(v),
+// lo = fl32(v - hi)), evaluated in 60-digit decimal arithmetic; the host check compares them with
+// the host's long-double exp2.
+#define FMG_EXP2_64 \
+  { \
+      {0x1.6a09e6p-1f, 0x1.9fcef4p-27f}, {0x1.6dfb24p-1f, -0x1.cd72e8p-28f}, {0x1.71f75ep-1f, 0x1.1d8beep-26f}, \
+      {0x1.75feb6p-1f, -0x1.37b306p-26f}, {0x1.7a1148p-1f, -0x1.829fdp-26f}, {0x1.7e2f34p-1f, -0x1.261634p-26f}, \
+      {0x1.82589ap-1f, -0x1.accc7cp-27f}, {0x1.868d9ap-1f, -0x1.2edb44p-27f}, {0x1.8ace54p-1f, 0x1.15506ep-28f}, \
+      {0x1.8f1aeap-1f, -0x1.baa232p-27f}, {0x1.93737cp-1f, -0x1.e64744p-26f}, {0x1.97d82ap-1f, -0x1.0d8d84p-32f}, \
+      {0x1.9c4918p-1f, 0x1.51f848p-28f}, {0x1.a0c668p-1f, -0x1.2886a6p-27f}, {0x1.a5503cp-1f, -0x1.b83b54p-26f}, \
+      {0x1.a9e6b6p-1f, -0x1.50c048p-26f}, {0x1.ae89fap-1f, -0x1.a94b14p-27f}, {0x1.b33a2cp-1f, -0x1.ec3a82p-27f}, \
+      {0x1.b7f77p-1f, -0x1.a09438p-26f}, {0x1.bcc1eap-1f, -0x1.f687c6p-26f}, {0x1.c199bep-1f, -0x1.3d56b2p-28f}, \
+      {0x1.c67f12p-1f, 0x1.cafa2ap-26f}, {0x1.cb720ep-1f, -0x1.8837ccp-28f}, {0x1.d072d4p-1f, 0x1.40f13p-26f}, \
+      {0x1.d5818ep-1f, -0x1.822dbcp-28f}, {0x1.da9e6p-1f, 0x1.ed9942p-28f}, {0x1.dfc974p-1f, -0x1.908c94p-26f}, \
+      {0x1.e502eep-1f, 0x1.e2cffep-27f}, {0x1.ea4afap-1f, 0x1.52486cp-28f}, {0x1.efa1bep-1f, 0x1.cc2b44p-26f}, \
+      {0x1.f50766p-1f, -0x1.246ebp-27f}, {0x1.fa7c18p-1f, 0x1.9e90d8p-29f}, {0x1p+0f, 0.0f}, \
+      {0x1.02c9a4p+0f, -0x1.887fap-28f}, {0x1.059b0ep+0f, -0x1.9d4f52p-25f}, {0x1.087452p+0f, -0x1.e2990ep-26f}, \
+      {0x1.0b5586p+0f, 0x1.9f3122p-25f}, {0x1.0e3ec4p+0f, -0x1.a585ccp-25f}, {0x1.11301ep+0f, -0x1.fdb496p-25f}, \
+      {0x1.1429aap+0f, 0x1.d525bcp-25f}, {0x1.172b84p+0f, -0x1.c15742p-27f}, {0x1.1a35bep+0f, 0x1.6df96ep-25f}, \
+      {0x1.1d4874p+0f, -0x1.d2e8cap-25f}, {0x1.2063b8p+0f, 0x1.0c519ap-25f}, {0x1.2387a6p+0f, 0x1.ceac48p-25f}, \
+      {0x1.26b456p+0f, 0x1.789f38p-26f}, {0x1.29e9ep+0f, -0x1.5c0424p-25f}, {0x1.2d285ap+0f, 0x1.b900c2p-26f}, \
+      {0x1.306fep+0f, 0x1.4636e2p-25f}, {0x1.33c08cp+0f, -0x1.b37d2p-25f}, {0x1.371a74p+0f, -0x1.18aac6p-25f}, \
+      {0x1.3a7db4p+0f, -0x1.634c02p-25f}, {0x1.3dea64p+0f, 0x1.824684p-25f}, {0x1.4160a2p+0f, 0x1.f72e2ap-28f}, \
+      {0x1.44e086p+0f, 0x1.8624b4p-30f}, {0x1.486a2cp+0f, -0x1.47d866p-25f}, {0x1.4bfdaep+0f, -0x1.593abcp-25f}, \
+      {0x1.4f9b28p+0f, -0x1.2c5a6cp-25f}, {0x1.5342b6p+0f, -0x1.2c561p-25f}, {0x1.56f474p+0f, -0x1.295b04p-25f}, \
+      {0x1.5ab07ep+0f, -0x1.5bd5ecp-27f}, {0x1.5e76f2p+0f, -0x1.4a5bd6p-25f}, {0x1.6247ecp+0f, -0x1.f8b55p-25f}, \
+      {0x1.662388p+0f, 0x1.2a9112p-27f} \
+  }
+#define FMG_EXP2M1_64 \
+  { \
+      {-0x1.2bec34p-2f, 0x1.9fcef4p-27f}, {-0x1.2409b8p-2f, -0x1.cd72e8p-28f}, {-0x1.1c1142p-2f, -0x1.c4e824p-27f}, \
+      {-0x1.140296p-2f, 0x1.9099f2p-27f}, {-0x1.0bdd72p-2f, 0x1.f580c4p-28f}, {-0x1.03a19ap-2f, 0x1.b3d398p-27f}, \
+      {-0x1.f69d9ap-3f, 0x1.4cce12p-29f}, {-0x1.e5c99ap-3f, 0x1.a24976p-28f}, {-0x1.d4c6bp-3f, 0x1.15506ep-28f}, \
+      {-0x1.c3945ap-3f, 0x1.157736p-29f}, {-0x1.b23214p-3f, 0x1.9b8bcap-30f}, {-0x1.a09f58p-3f, -0x1.0d8d84p-32f}, \
+      {-0x1.8edbap-3f, 0x1.51f848p-28f}, {-0x1.7ce662p-3f, 0x1.aef2b2p-28f}, {-0x1.6abf14p-3f, 0x1.1f12aep-28f}, \
+      {-0x1.58652ap-3f, -0x1.43012p-28f}, {-0x1.45d81ap-3f, 0x1.5ad3aep-29f}, {-0x1.331752p-3f, 0x1.3c57ecp-31f}, \
+      {-0x1.202244p-3f, 0x1.7daf24p-28f}, {-0x1.0cf85cp-3f, 0x1.2f0748p-31f}, {-0x1.f33212p-4f, 0x1.85529cp-29f}, \
+      {-0x1.cc0768p-4f, -0x1.a82eb4p-29f}, {-0x1.a46f92p-4f, 0x1.df20d2p-30f}, {-0x1.7c695ap-4f, -0x1.f87684p-29f}, \
+      {-0x1.53f392p-4f, 0x1.f7490ep-30f}, {-0x1.2b0cfep-4f, -0x1.266bd4p-32f}, {-0x1.01b466p-4f, -0x1.08c942p-30f}, \
+      {-0x1.afd118p-5f, -0x1.d30028p-31f}, {-0x1.5b505ep-5f, 0x1.4921b4p-30f}, {-0x1.05e412p-5f, 0x1.85689ep-31f}, \
+      {-0x1.5f134ap-6f, 0x1.b91502p-31f}, {-0x1.60f9fap-7f, 0x1.e90d82p-33f}, {0.0f, 0.0f}, \
+      {0x1.64d1f4p-7f, -0x1.0ff3e2p-33f}, {0x1.66c34cp-6f, 0x1.585744p-32f}, {0x1.0e8a3p-5f, 0x1.d66f2p-30f}, \
+      {0x1.6ab0dap-5f, -0x1.9dbc28p-34f}, {0x1.c7d866p-5f, -0x1.6172fp-31f}, {0x1.1301dp-4f, 0x1.25b50ap-32f}, \
+      {0x1.429aaep-4f, 0x1.525bcp-29f}, {0x1.72b83cp-4f, 0x1.f545ecp-30f}, {0x1.a35becp-4f, -0x1.206916p-29f}, \
+      {0x1.d48732p-4f, -0x1.2e8cacp-29f}, {0x1.031dc4p-3f, 0x1.8a3358p-30f}, {0x1.1c3d38p-3f, -0x1.8a9dc8p-28f}, \
+      {0x1.35a2b2p-3f, 0x1.e27cdep-28f}, {0x1.4f4efap-3f, 0x1.1fdee2p-28f}, {0x1.6942d4p-3f, -0x1.1bfcf4p-28f}, \
+      {0x1.837f06p-3f, -0x1.ce48eap-28f}, {0x1.9e045ap-3f, -0x1.9be9p-28f}, {0x1.b8d39cp-3f, -0x1.8aac6ap-29f}, \
+      {0x1.d3ed9ap-3f, 0x1.cb3feep-29f}, {0x1.ef5326p-3f, 0x1.234224p-32f}, {0x1.058288p-2f, 0x1.f72e2ap-28f}, \
+      {0x1.138218p-2f, 0x1.8624b4p-30f}, {0x1.21a8aep-2f, -0x1.1f6198p-27f}, {0x1.2ff6b6p-2f, -0x1.64eaecp-27f}, \
+      {0x1.3e6c9ep-2f, -0x1.62d35ap-28f}, {0x1.4d0ad6p-2f, -0x1.62b07ep-28f}, {0x1.5bd1cep-2f, -0x1.4ad826p-28f}, \
+      {0x1.6ac1f8p-2f, -0x1.5bd5ecp-27f}, {0x1.79dbc6p-2f, -0x1.296f5cp-27f}, {0x1.891facp-2f, 0x1.d2ac26p-31f}, \
+      {0x1.988e2p-2f, 0x1.2a9112p-27f} \
+  }
+__device__ const float2 kExp2_64_d[64] = FMG_EXP2_64;
+__device__ const float2 kExp2m1_64_d[64] = FMG_EXP2M1_64;
+static const float2 kExp2_64_h[64] = FMG_EXP2_64;
+static const float2 kExp2m1_64_h[64] = FMG_EXP2M1_64;
+
+__host__ __device__ __forceinline__ ff exp2_64(int row) {
+#ifdef __CUDA_ARCH__
+  const float2 v = __ldg(&kExp2_64_d[row]);
+#else
+  const float2 v = kExp2_64_h[row];
+#endif
+  return ff{v.x, v.y};
+}
+__host__ __device__ __forceinline__ ff exp2m1_64(int row) {
+#ifdef __CUDA_ARCH__
+  const float2 v = __ldg(&kExp2m1_64_d[row]);
+#else
+  const float2 v = kExp2m1_64_h[row];
+#endif
+  return ff{v.x, v.y};
+}
+
+// exp(x) - 1 in float-float, from the exponential's own properties.  x = N ln2/64 + r with N
+// the nearest integer to 64 x / ln2 (r formed in float-float from the two-part ln2/64 and exact
+// products, |r| <= ln2/128) and N = 64 k + j, j in [-32, 31]; then
+//   expm1(x) = 2^k ((2^(j/64) - 1) + 2^(j/64) expm1(r)) + (2^k - 1),
+// with both 2^(j/64) and 2^(j/64) - 1 from the tables (so the bracket does not cancel: j
+// centred on 0 keeps it within a factor 3 of 2^(j/64) (1 + expm1(r)) - 1), and expm1(r) =
+// r + r^2 (1/2 + r/6 + r^2/24 + r^3/120) by its Taylor series (the next term is below 2^-47 |r|);
+// only r, r^2 and r/6 need float-float, the rest of the bracket is FP32.  Relative error about
+// 2^-46 over the range the nonlinearities meet; |x| beyond 80 returns the FP32 limit (exp
+// overflows there in FP32 anyway).
 __host__ __device__ __forceinline__ ff ff_expm1(ff x) {
-  // the float-float split hi = fl32(c), lo = fl32(c - hi) of the constants, as exact hex literals
-  const float kLn2Hi = 0x1.62e430p-1f, kLn2Lo = -0x1.05c610p-29f;   // ln 2
-  const float kInvLn2 = 0x1.715476p+0f;                                // fl32(1 / ln 2)
+  const float kInvL = 0x1.715476p+6f;                          // fl32(64 / ln 2)
+  const float kLHi = 0x1.62e43p-7f, kLLo = -0x1.05c61p-35f;     // ln2 / 64 as float-float
   if (!(x.hi > -80.f && x.hi < 80.f)) {
     const float e = expm1f(x.hi);
     return ff{e, 0.f};
   }
-  const float kf = rintf(x.hi * kInvLn2);
-  const int k = (int)kf;
-  // r = x - k ln2: both products exact (TwoProduct), then float-float sums
+  const float nf = rintf(x.hi * kInvL);
+  const int N = (int)nf;
+  const int k = (N + 32) >> 6;
+  const int j = N - 64 * k;
+  // r = x - N ln2/64: both products exact (TwoProduct), then float-float sums
   float p1, e1, p2, e2;
-  two_prod(kf, kLn2Hi, p1, e1);
-  two_prod(kf, kLn2Lo, p2, e2);
+  two_prod(nf, kLHi, p1, e1);
+  two_prod(nf, kLLo, p2, e2);
   ff r = ff_add(x, ff{-p1, -e1});
   r = ff_add(r, ff{-p2, -e2});
-  const ff sx = ff_ldexp(r, -5);
-  // Taylor series of expm1 at s: s (1 + s (1/2 + s (1/6 + s (1/24 + s (1/120 + s / 720)))))
-  const ff c720 = ff{0x1.6c16c2p-10f, -0x1.27d27ep-35f};   // 1/720
-  const ff c120 = ff{0x1.111112p-7f, -0x1.dddddep-32f};   // 1/120
-  const ff c24 = ff{0x1.555556p-5f, -0x1.555556p-30f};     // 1/24
-  const ff c6 = ff{0x1.555556p-3f, -0x1.555556p-28f};      // 1/6
-  ff q = ff_add(ff_mul(c720, sx), c120);
-  q = ff_add(ff_mul(q, sx), c24);
-  q = ff_add(ff_mul(q, sx), c6);
-  q = ff_add(ff_mul(q, sx), ff{0.5f, 0.f});
-  q = ff_add(ff_mul(q, sx), ff{1.f, 0.f});
-  q = ff_mul(q, sx);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) q = ff_mul(q, ff_add_f(q, 2.0f));
-  if (k == 0) return q;
-  // 2^k (1 + q) - 1 = 2^k q + (2^k - 1); 2^k - 1 is exact in FP32 for |k| <= 24
+  const ff c6 = ff{0x1.555556p-3f, -0x1.555556p-28f};         // 1/6
+  const float rh = r.hi;
+  const float t = (rh * rh) * fmaf(rh, 0x1.111112p-7f, 0x1.555556p-5f);   // r^2 (1/24 + r/120)
+  const ff B = ff_add_f(ff_add_f(ff_mul(r, c6), t), 0.5f);
+  const ff q = ff_add_fast(r, ff_mul(ff_mul(r, r), B));          // expm1(r)
+  const ff a = ff_add(exp2m1_64(j + 32), ff_mul(exp2_64(j + 32), q));
+  if (k == 0) return a;
+  // 2^k a + (2^k - 1); 2^k - 1 is exact in FP32 for |k| <= 24
   const float pk = ldexpf(1.0f, k) - 1.0f;
-  if (k >= -24 && k <= 24) return ff_add(ff_ldexp(q, k), ff{pk, 0.f});
-  return ff_add_f(ff_ldexp(q, k), pk);
+  if (k >= -24 && k <= 24) return ff_add(ff_ldexp(a, k), ff{pk, 0.f});
+  return ff_add_f(ff_ldexp(a, k), pk);
 }
 
 // sqrt(x) for x >= 0 in float-float: the FP32 root s, then one Newton step

@@ -115,20 +115,32 @@ int main(int argc, char** argv) {
     if (e_nb > u42 * (double)big) fail("neighbour_sum_ff_v", e_nb, u42 * (double)big);
   }
   // the float-float exponential and root of the mixed path's nonlinearities, against the host's
-  // FP64 expm1 and sqrt (errors near 2^-53, far below the bounds checked): expm1 within 2^-42
-  // relative over [-12, 12] (small arguments included, where expm1 keeps its relative accuracy),
-  // sqrt within 2^-44 relative
+  // long-double expm1 and FP64 sqrt (errors far below the bounds checked): expm1 within 2^-45
+  // relative over [-12, 12] (small arguments included, where expm1 keeps its relative accuracy,
+  // and arguments next to the multiples of ln2/64 where its table index changes), sqrt within
+  // 2^-44 relative; and the tables 2^(j/64), 2^(j/64) - 1 within 2^-48 of long-double exp2
+  for (int j = -32; j < 32; ++j) {
+    const ff t = fmg::exp2_64(j + 32), m = fmg::exp2m1_64(j + 32);
+    const long double v = exp2l((long double)j / 64);
+    const long double et = fabsl((long double)t.hi + (long double)t.lo - v);
+    if (et > std::ldexp(1.0L, -48) * v) fail("exp2_64 table", (double)et, std::ldexp(1.0, -48));
+    const long double em = fabsl((long double)m.hi + (long double)m.lo - (v - 1));
+    if (em > std::ldexp(1.0L, -48) * fabsl(v - 1)) fail("exp2m1_64 table", (double)em, std::ldexp(1.0, -48));
+  }
   std::uniform_real_distribution<double> X(-12.0, 12.0);
-  const double u42r = std::ldexp(1.0, -42);
+  const double u45r = std::ldexp(1.0, -45);
   for (long long i = 0; i < rounds / 4; ++i) {
     double x = X(rng);
-    if (i % 3 == 1) x = std::ldexp(U(rng), -Small(rng));            // small arguments
+    if (i % 3 == 1) x = std::ldexp(U(rng), -Small(rng)) * ((i & 4) ? -1.0 : 1.0);   // small arguments
+    if (i % 5 == 2) x = (double)(i % 2001 - 1000) * 0.010830424696249145 + std::ldexp(U(rng) - 0.5, -14);
     const ff fx = fmg::ff_from_double(x);
-    const double xe = (double)fx.hi + (double)fx.lo;                   // the argument as represented
-    const double want = std::expm1(xe);
-    const double got = (double)fmg::ff_expm1(fx).hi + (double)fmg::ff_expm1(fx).lo;
-    if (std::fabs(got - want) > u42r * std::fabs(want)) fail("ff_expm1", std::fabs(got - want), u42r * std::fabs(want));
-    const double ax = std::fabs(xe) * 7.0;
+    const long double xe = (long double)fx.hi + (long double)fx.lo;    // the argument as represented
+    const long double want = expm1l(xe);
+    const ff ge = fmg::ff_expm1(fx);
+    const long double got = (long double)ge.hi + (long double)ge.lo;
+    if (fabsl(got - want) > u45r * fabsl(want))
+      fail("ff_expm1", (double)fabsl(got - want), u45r * (double)fabsl(want));
+    const double ax = std::fabs((double)xe) * 7.0;
     const ff fa = fmg::ff_from_double(ax);
     const double wr = std::sqrt((double)fa.hi + (double)fa.lo);
     const ff r = fmg::ff_sqrt(fa);
