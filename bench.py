@@ -101,8 +101,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip tuning the launch shapes of the Chebyshev step kernel before timing")
     ap.add_argument("--smoother", default="auto", choices=["auto", "rbgs", "chebyshev"],
-                    help="smoother of the multigrid cycles (large2d / 3d); auto: each arm's faster one at "
-                         "equal accuracy (2D: Chebyshev for the mixed path, red-black for FP64; 3D: red-black)")
+                    help="smoother of the multigrid cycles (large2d / 3d / batch); auto: each arm's faster one "
+                         "at equal accuracy (Chebyshev for the mixed path, red-black for FP64)")
     return ap.parse_args()
 
 
@@ -370,7 +370,7 @@ def run_ours(args):
     # cycles per correction step: the workload's m (2 in 2D as in the paper's examples; 3 on the
     # cube, where m = 2 leaves an algebraic error above a tenth of the discretization error)
     if args.smoother == "auto":
-        smoother = {"mixed": "chebyshev" if dim == 2 else "rbgs", "fp64": "rbgs"}
+        smoother = {"mixed": "chebyshev", "fp64": "rbgs"}
     else:
         smoother = {"mixed": args.smoother, "fp64": args.smoother}
     m_cycles = {p: prob.m_vcycles for p in smoother}

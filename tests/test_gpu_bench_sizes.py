@@ -60,7 +60,8 @@ def discrete_solution(hier, k, u0, G, kind, a, m):
 CASES = {
     "2d_H8_r7": (lambda: W.config_large_2d(seed=0, refinements=7), "chebyshev"),
     "2d_H8_r8": (lambda: W.config_large_2d(seed=0, refinements=8), "chebyshev"),
-    "3d_H4_r4": (lambda: W.config_3d(seed=0, refinements=4), "rbgs"),
+    "3d_H4_r4": (lambda: W.config_3d(seed=0, refinements=4), "chebyshev"),
+    "3d_H4_r4_rbgs": (lambda: W.config_3d(seed=0, refinements=4), "rbgs"),
 }
 
 
@@ -99,8 +100,9 @@ def test_fmg_matches_oracle_at_benchmark_paths(fmg, case):
 
 
 def test_full_size_cube_reaches_discretization_accuracy(fmg):
-    """257^3 (the 3D benchmark): mixed and FP64 results within a tenth of the discretization
-    error of u_bar, which many FP64 correction steps per level give (their fixed point)."""
+    """257^3 (the 3D benchmark): mixed (red-black and Chebyshev smoothing, the benchmark's
+    mixed arm) and FP64 results within a tenth of the discretization error of u_bar, which many
+    FP64 correction steps per level give (their fixed point)."""
     prob = W.config_3d(seed=0, refinements=6)
     g = prob.g_nodal()
     n = prob.n_fine
@@ -112,8 +114,12 @@ def test_full_size_cube_reaches_discretization_accuracy(fmg):
     res = {}
     for name, kw in (("ubar", dict(precision="fp64", p_corrections=8)),
                      ("ubar12", dict(precision="fp64", p_corrections=12)),
-                     ("fp64", dict(precision="fp64")), ("mixed", dict(precision="mixed"))):
-        s = fmg.Solver(fmg.make_params(prob, smoother="rbgs", **kw), g)
+                     ("fp64", dict(precision="fp64")), ("mixed", dict(precision="mixed")),
+                     ("mixed_cheb", dict(precision="mixed", smoother="chebyshev"))):
+        kw.setdefault("smoother", "rbgs")
+        s = fmg.Solver(fmg.make_params(prob, **kw), g)
+        if kw["smoother"] == "chebyshev":
+            assert fmg.fmg_autotune(s.ctx) > 0
         st = fmg.fmg_stats()
         res[name] = s.solve(stats=st).cpu().numpy()
         s.close()
@@ -121,5 +127,5 @@ def test_full_size_cube_reaches_discretization_accuracy(fmg):
     e_disc = l2(res["ubar"] - us)
     # u_bar has settled: more correction steps do not move it
     assert l2(res["ubar12"] - res["ubar"]) <= 1e-3 * e_disc
-    for name in ("fp64", "mixed"):
+    for name in ("fp64", "mixed", "mixed_cheb"):
         assert l2(res[name] - res["ubar"]) <= 0.1 * e_disc, name
