@@ -192,28 +192,97 @@ __device__ __forceinline__ T res3(const T* __restrict__ u, const T* __restrict__
 
 // With dc != NULL the coarse level's first Chebyshev step from its zero start is taken here
 // too: u_c = d_c = e0 b_c (e0 = cr_0 / diag of the coarse level).
-template <typename TF, typename TC>
-__device__ __forceinline__ void k_resrestrict2_body(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
-                               TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) {
+// 2D: a thread per coarse column I walks a strip of coarse rows.  Per fine row it loads u at the
+// five fine columns 2I-2 .. 2I+2 (neighbouring threads' loads overlap in L1) and forms the
+// residuals at 2I-1, 2I, 2I+1; the previous fine row's residuals and the rows of u stay in
+// registers.  So a thread reads each fine row of u once and forms three residuals per fine row
+// instead of seven residuals from 35 loads per coarse node.  The residual and the restriction's sum are the
+// per-node kernel's expressions in the same order, so the results are the same.  The strip length S
+// is a compile-time constant and its loop unrolled, so that all of a thread's row loads are issued
+// together (a strip costs one memory latency); larger levels take longer strips.
+
+template <typename TF>
+struct RRow {
+  TF ll, l, c, r, rr;   // u at the fine columns 2I-2 .. 2I+2 of one fine row
+};
+
+template <typename TF, typename TC, int S>
+__device__ __forceinline__ void k_resrestrict2_body(const TF* __restrict__ u, const TF* __restrict__ b, int nf,
+                                                    TC* __restrict__ bc, TC* __restrict__ uc, int ncells,
+                                                    TC* __restrict__ dc, TC e0) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int J = blockIdx.y + 1;
-  if (I > ncells - 1) return;
+  const int J0 = blockIdx.y * S + 1;
+  const int J1 = min(J0 + S, ncells);   // coarse rows J0 .. J1-1
   const long long np = nf + 1;
-  const long long F = (long long)(2 * J) * np + 2 * I;
-  TF r = res2(u, b, F, np);
-  TF e = (res2(u, b, F + 1, np) + res2(u, b, F - 1, np)) + (res2(u, b, F + np, np) + res2(u, b, F - np, np)) +
-         (res2(u, b, F + np + 1, np) + res2(u, b, F - np - 1, np));
-  const long long cc = (long long)J * (ncells + 1) + I;
-  const TC bv = (TC)(r + TF(0.5) * e);
-  bc[cc] = bv;
-  const TC e1 = dc ? e0 * bv : TC(0);
-  uc[cc] = e1;
-  if (dc) dc[cc] = e1;
+  const int x0 = 2 * I;
+  const bool v0 = x0 <= nf, v1 = x0 + 1 <= nf;   // the thread's columns inside the row
+  // u at the five columns 2I-2 .. 2I+2 of fine row y (outside the row: 0; those columns are
+  // only read by threads whose coarse column is outside the level)
+  auto load_row = [&](int y) {
+    const long long o = (long long)y * np;
+    RRow<TF> w;
+    w.ll = x0 - 2 <= nf ? u[o + x0 - 2] : TF(0);
+    w.l = x0 - 1 <= nf ? u[o + x0 - 1] : TF(0);
+    w.c = v0 ? u[o + x0] : TF(0);
+    w.r = v1 ? u[o + x0 + 1] : TF(0);
+    w.rr = x0 + 2 <= nf ? u[o + x0 + 2] : TF(0);
+    return w;
+  };
+  // residuals of fine row y at columns 2I-1, 2I, 2I+1 from the rows y-1, y, y+1
+  auto res_row = [&](int y, const RRow<TF>& m, const RRow<TF>& c, const RRow<TF>& p, TF& rl, TF& rc, TF& rr) {
+    const long long o = (long long)y * np;
+    const TF blv = x0 - 1 <= nf ? b[o + x0 - 1] : TF(0);
+    const TF bcv = v0 ? b[o + x0] : TF(0);
+    const TF brv = v1 ? b[o + x0 + 1] : TF(0);
+    rl = blv - (TF(4) * c.l - ((c.ll + c.c) + (m.l + p.l)));
+    rc = bcv - (TF(4) * c.c - ((c.l + c.r) + (m.c + p.c)));
+    rr = brv - (TF(4) * c.r - ((c.c + c.rr) + (m.r + p.r)));
+  };
+  if (J0 >= J1) return;   // uniform over the block
+  RRow<TF> rm = load_row(2 * J0 - 2), r0 = load_row(2 * J0 - 1), rp = load_row(2 * J0);
+  TF pl, pc, pr;   // residuals of fine row 2J - 1
+  res_row(2 * J0 - 1, rm, r0, rp, pl, pc, pr);
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    const int J = J0 + k;
+    if (J >= J1) break;   // uniform over the block
+    rm = r0;
+    r0 = rp;
+    rp = load_row(2 * J + 1);
+    TF al, ac, ar;   // fine row 2J
+    res_row(2 * J, rm, r0, rp, al, ac, ar);
+    rm = r0;
+    r0 = rp;
+    rp = load_row(2 * J + 2);
+    TF ql, qc, qr;   // fine row 2J + 1
+    res_row(2 * J + 1, rm, r0, rp, ql, qc, qr);
+    if (I <= ncells - 1) {
+      // b_c = r(2I, 2J) + (r(2I+1, 2J) + r(2I-1, 2J) + r(2I, 2J+1) + r(2I, 2J-1)
+      //       + r(2I+1, 2J+1) + r(2I-1, 2J-1)) / 2
+      const TF e = (ar + al) + (qc + pc) + (qr + pl);
+      const long long cc = (long long)J * (ncells + 1) + I;
+      const TC bv = (TC)(ac + TF(0.5) * e);
+      bc[cc] = bv;
+      const TC e1 = dc ? e0 * bv : TC(0);
+      uc[cc] = e1;
+      if (dc) dc[cc] = e1;
+    }
+    pl = ql;
+    pc = qc;
+    pr = qr;
+  }
+  (void)pr;
 }
 
-template <typename TF, typename TC>
+template <typename TF, typename TC, int S>
 __global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
-                               TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) { k_resrestrict2_body<TF, TC>(u, b, nf, bc, uc, ncells, dc, e0); }
+                               TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) {
+  k_resrestrict2_body<TF, TC, S>(u, b, nf, bc, uc, ncells, dc, e0);
+}
+
+// Coarse rows per thread of the 2D residual + restriction: 1 on small levels (parallelism), up
+// to 4 on large ones (fewer loads per node).
+inline int rr_strip(int ncells) { return ncells <= 128 ? 1 : (ncells <= 512 ? 2 : 4); }
 
 template <typename TF, typename TC>
 __global__ void k_resrestrict3(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TF sigma,
@@ -865,7 +934,14 @@ cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const 
     return cudaGetLastError();
   }
   if (dim == 2) {
-    k_resrestrict2<TF, TC><<<dim3(gx, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
+    const int S = rr_strip(nc);
+    const dim3 grid(gx, cdiv(nc - 1, S));
+    if (S == 1)
+      k_resrestrict2<TF, TC, 1><<<grid, kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
+    else if (S == 2)
+      k_resrestrict2<TF, TC, 2><<<grid, kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
+    else
+      k_resrestrict2<TF, TC, 4><<<grid, kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
   } else {
     k_resrestrict3<TF, TC><<<dim3(gx, nc - 1, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, TF(1.0) / TF(gf.n), b_c,
                                                                         u_c, nc, d_c, TC(e0));
@@ -1180,8 +1256,12 @@ void phase_kernels_stencil(std::vector<PhaseKernel>& out) {
   out.push_back(phase_kernel<&k_cheb_add64_body<2, false>, 512, 1>(&k_cheb_add64<2, false>));
   out.push_back(phase_kernel<&k_copy_t_body<float>, 256, 1>(&k_copy_t<float>));
   out.push_back(phase_kernel<&k_copy_t_body<double>, 256, 1>(&k_copy_t<double>));
-  out.push_back(phase_kernel<&k_resrestrict2_body<float, float>, kBlock, 16>(&k_resrestrict2<float, float>));
-  out.push_back(phase_kernel<&k_resrestrict2_body<double, double>, kBlock, 10>(&k_resrestrict2<double, double>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<float, float, 1>, kBlock, 8>(&k_resrestrict2<float, float, 1>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<float, float, 2>, kBlock, 8>(&k_resrestrict2<float, float, 2>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<float, float, 4>, kBlock, 8>(&k_resrestrict2<float, float, 4>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<double, double, 1>, kBlock, 6>(&k_resrestrict2<double, double, 1>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<double, double, 2>, kBlock, 6>(&k_resrestrict2<double, double, 2>));
+  out.push_back(phase_kernel<&k_resrestrict2_body<double, double, 4>, kBlock, 6>(&k_resrestrict2<double, double, 4>));
   out.push_back(phase_kernel<&k_prolong2_body<float, float>, kBlock, 1>(&k_prolong2<float, float>));
   out.push_back(phase_kernel<&k_prolong2_body<double, double>, kBlock, 1>(&k_prolong2<double, double>));
   out.push_back(phase_kernel<&k_nonlinear_rhs_body, kBlock, 1>(&k_nonlinear_rhs));
