@@ -391,6 +391,7 @@ def run_ours(args):
         s = fmg.Solver(fmg.make_params(prob, precision=prec, smoother=smoother[prec], m_vcycles=m_cycles[prec]), g)
         if not args.no_autotune:
             fmg.fmg_autotune(s.ctx)
+            fmg.fmg_autotune_augmented(s.ctx)
         st = fmg.fmg_stats()
         s.solve(stats=st)
         solvers[prec] = s
@@ -586,6 +587,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD if dim == 2 else WORKLOAD_3D, "precision": "mixed",
                        "smoother": smoother["mixed"], "fp64_smoother": smoother["fp64"], "instances": world,
                        "autotuned": not args.no_autotune,
+                       "top_level_augmented_shape": {p: fmg.fmg_aug_shape(solvers[p].ctx, top) for p in solvers},
                        "top_level_cheb_shape": (fmg.fmg_tuned_shape(solvers["mixed"].ctx, top)
                                                 if smoother["mixed"] == "chebyshev" else None),
                        "global_batch": world, "seq_len": None, "parallelism": f"independent instances x{world}",

@@ -238,6 +238,19 @@ fmg_status fmg_batch_destroy(fmg_batch* b);
 fmg_status fmg_autotune(fmg_ctx* c, int* tuned);
 /* Launch shape the context's Chebyshev step kernel uses on `level` (tuned or default). */
 fmg_status fmg_tuned_shape(const fmg_ctx* c, int level, int* block, int* strip);
+/* Autotuner of the augmented-space Newton kernel's launch shape (Algorithm 3.1 step 2, eq. 3.6):
+ * for each level 2..n it solves once for the levels' iterates, then times every pair of column-
+ * chunk length (2..32 fine nodes, a power of two within the column) and blocks per coarse cell
+ * (1 up to the co-resident maximum of the cooperative launch) on a copy of that level's data,
+ * and keeps the fastest per (device, dimension, 1/H, level, precision) for the whole process.
+ * Unlike fmg_autotune this changes the order of the kernel's block sums, so results change in
+ * rounding (a solve stays deterministic for a given shape).  Waits for the context stream, must
+ * not overlap other work of the context, and leaves no solve's result in it.  Contexts on the
+ * cluster variant (request server) keep their fixed shape.  *tuned: levels tuned (optional). */
+fmg_status fmg_autotune_augmented(fmg_ctx* c, int* tuned);
+/* Launch shape of the context's augmented kernel on `level` (2..n): chunk length and blocks
+ * per coarse cell (tuned or the default rule). */
+fmg_status fmg_aug_shape(const fmg_ctx* c, int level, int* chunk, int* blocks_per_cell);
 
 /* Frees the context (and the workspace when the library allocated it).  NULL-safe. */
 fmg_status fmg_destroy(fmg_ctx* c);

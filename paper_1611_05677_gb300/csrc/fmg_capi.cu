@@ -1331,6 +1331,93 @@ fmg_status fmg_kernel_time(fmg_ctx* c, int kind, int level, double* total_ms, in
 
 int fmg_graph_kernels(const fmg_ctx* c) { return c ? c->graph_kernels : -1; }
 
+fmg_status fmg_autotune_augmented(fmg_ctx* c, int* tuned) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if (tuned) *tuned = 0;
+  if (c->cluster_aug > 0) return FMG_OK;   // the cluster variant's shape is fixed
+  const bool mixed = c->p.precision == FMG_PREC_MIXED;
+  // one solve: every level holds the iterate its augmented step meets
+  fmg_status st = ensure_graph(c);
+  if (st != FMG_OK) return st;
+  CK(c, cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream));
+  CK(c, cudaGraphLaunch(c->gexec, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  double* pristine = nullptr;
+  CK(c, cudaMalloc(&pristine, c->geo[c->nlev - 1].nodes * sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  int count = 0;
+  const int last = c->nlev;
+  for (int k = 2; k <= last && ce == cudaSuccess; ++k) {
+    const LevelGeo g = c->geo[k - 1];
+    // the level's iterate as the kernel finds it (mixed: float-float; the finest level's FP64
+    // result is converted back)
+    if (mixed && k == last)
+      ce = launch_ff_from_f64(c->u[k - 1], pristine, g.nodes, c->stream);
+    else
+      ce = cudaMemcpyAsync(pristine, c->u[k - 1], g.nodes * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    const AugShape rule = aug_shape(c->p.dim, c->p.coarse_cells, k, mixed, c->ab, false);
+    AugShape best = rule;
+    float best_ms = 0.f;
+    const int sfine = 1 << (k - 1);
+    for (int chunk = 32; chunk >= 2 && ce == cudaSuccess; chunk >>= 1) {
+      if (chunk > sfine) continue;
+      for (int bpc = 1; bpc <= c->ab.bpc && ce == cudaSuccess; ++bpc) {
+        set_aug_shape(c->p.dim, c->p.coarse_cells, k, mixed, AugShape{chunk, bpc});
+        float ms_min = 0.f;
+        for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
+          ce = cudaMemcpyAsync(c->u[k - 1], pristine, g.nodes * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+          if (ce == cudaSuccess) ce = cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream);
+          if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+          if (ce == cudaSuccess)
+            ce = launch_augmented(c->p.dim, c->p.coarse_cells, k, g, c->u[k - 1], mixed ? c->gf[k - 1] : c->g[k - 1],
+                                  c->p.f, c->p.f_scale, c->p.newton_tol, c->p.newton_maxit, mixed, c->ab, c->st, k - 1,
+                                  c->stream, 0, c->p.nonlinear == FMG_NONLINEAR_FIXED_POINT ? 1 : 0,
+                                  mixed && k == last ? 1 : 0, vcp(c));
+          if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+          if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+          if (ce == cudaSuccess && (rep == 0 || ms < ms_min)) ms_min = ms;
+        }
+        if (ce == cudaSuccess && (best_ms == 0.f || ms_min < best_ms)) {
+          best_ms = ms_min;
+          best = AugShape{chunk, bpc};
+        }
+      }
+    }
+    if (ce == cudaSuccess) {
+      set_aug_shape(c->p.dim, c->p.coarse_cells, k, mixed, best);
+      ++count;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(pristine);
+  // the trials leave the statistics and the level data of no solve: the next solve rebuilds both
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) return fail(c, FMG_ERR_CUDA, std::string("augmented autotune: ") + cudaGetErrorString(ce));
+  // the next solve captures its graph again with the tuned shapes
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  if (tuned) *tuned = count;
+  return FMG_OK;
+}
+
+fmg_status fmg_aug_shape(const fmg_ctx* c, int level, int* chunk, int* blocks_per_cell) {
+  if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
+  if (level < 2 || level > c->nlev) return fail(nullptr, FMG_ERR_INVALID, "level out of range");
+  const AugShape sh = aug_shape(c->p.dim, c->p.coarse_cells, level, c->p.precision == FMG_PREC_MIXED, c->ab,
+                                c->cluster_aug == 0);
+  if (chunk) *chunk = sh.chunk;
+  if (blocks_per_cell) *blocks_per_cell = c->cluster_aug > 0 ? 1 : sh.bpc;
+  return FMG_OK;
+}
+
 fmg_status fmg_autotune(fmg_ctx* c, int* tuned) {
   if (!c) return fail(nullptr, FMG_ERR_INVALID, "context is NULL");
   if (tuned) *tuned = 0;

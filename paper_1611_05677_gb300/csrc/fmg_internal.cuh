@@ -303,6 +303,16 @@ struct AugBuffers {
   long long bar_spins; // grid-barrier polls before a timeout (0: the default, 2^25)
   int bar_skip;        // failure-detection test hook: block that skips its first arrival (-1: none)
 };
+// Launch shape of the cooperative augmented kernel on one level: column-chunk length and
+// blocks per coarse cell.  aug_shape gives the tuned one (set_aug_shape, process-wide; tuned =
+// false: the rule only) within the launch's limits, else the rule of launch_augmented.
+struct AugShape {
+  int chunk;
+  int bpc;
+};
+AugShape aug_shape(int dim, int coarse_cells, int level, bool jac_f32, const AugBuffers& ab, bool tuned = true);
+void set_aug_shape(int dim, int coarse_cells, int level, bool mixed, AugShape sh);
+bool aug_shape_tuned(int dim, int coarse_cells, int level, bool mixed, AugShape* out);
 // Fills bpc/nt/smem/partial_items for this device (occupancy-based), outside any capture.
 void aug_configure(int dim, int coarse_cells, bool mixed, AugBuffers* ab);
 int aug_nvals(int dim);

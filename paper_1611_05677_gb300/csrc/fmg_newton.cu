@@ -34,6 +34,9 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "fmg_ff.cuh"
@@ -2494,15 +2497,36 @@ int aug_cluster_size(int dim, int coarse_cells, bool jac_f32, size_t smem) {
   return jac_f32 ? cluster_size_for<3, true>(ncell, smem) : cluster_size_for<3, false>(ncell, smem);
 }
 
-cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
-                             int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
-                             DevState* st, int level_index, cudaStream_t s, int cluster_size, int fixed_point,
-                             int out_f64, const VarCoef* vc) {
-  const size_t smem = ab.smem;
-  const int nt = ab.nt;
-  if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
+// Launch shapes of the cooperative augmented kernel picked by the autotuner
+// (fmg_autotune_augmented), per device, dimension, 1/H, level and precision; absent entries use
+// the rule of aug_shape.
+namespace {
+std::mutex g_aug_mu;
+std::map<std::tuple<int, int, int, int, int>, AugShape> g_aug_shapes;
+std::tuple<int, int, int, int, int> aug_key(int dim, int nc, int level, bool mixed) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return std::make_tuple(dev, dim, nc, level, mixed ? 1 : 0);
+}
+}  // namespace
+
+void set_aug_shape(int dim, int coarse_cells, int level, bool mixed, AugShape sh) {
+  std::lock_guard<std::mutex> lk(g_aug_mu);
+  g_aug_shapes[aug_key(dim, coarse_cells, level, mixed)] = sh;
+}
+
+bool aug_shape_tuned(int dim, int coarse_cells, int level, bool mixed, AugShape* out) {
+  std::lock_guard<std::mutex> lk(g_aug_mu);
+  auto it = g_aug_shapes.find(aug_key(dim, coarse_cells, level, mixed));
+  if (it == g_aug_shapes.end()) return false;
+  if (out) *out = it->second;
+  return true;
+}
+
+AugShape aug_shape(int dim, int coarse_cells, int level, bool jac_f32, const AugBuffers& ab, bool tuned) {
   const int ncell = (int)ipow(coarse_cells, dim);
   const int sfine = 1 << (level - 1);
+  const int nt = ab.nt;
   // column chunks of up to 32 nodes; on smaller levels shorter ones, until every thread has
   // an item (each chunk costs one moment-to-channel conversion, so they are no shorter than
   // that needs, and at least 2 nodes long).  FP64 path: every co-resident thread of the
@@ -2525,6 +2549,29 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
     bpc = (int)(items < ab.bpc ? items : ab.bpc);
   }
   if (bpc < 1) bpc = 1;
+  AugShape sh{chunk, bpc};
+  AugShape t;
+  if (tuned && aug_shape_tuned(dim, coarse_cells, level, jac_f32, &t)) {
+    // a tuned shape within the launch's limits: a power-of-two chunk that divides the column,
+    // at most the co-resident blocks per cell that the partial rows are sized for
+    if (t.chunk >= 2 && t.chunk <= 32 && t.chunk <= sfine && (t.chunk & (t.chunk - 1)) == 0) sh.chunk = t.chunk;
+    if (t.bpc >= 1 && t.bpc <= ab.bpc) sh.bpc = t.bpc;
+  }
+  return sh;
+}
+
+cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, double* u, const double* gn,
+                             int kind, double a, double tol, int maxit, bool jac_f32, const AugBuffers& ab,
+                             DevState* st, int level_index, cudaStream_t s, int cluster_size, int fixed_point,
+                             int out_f64, const VarCoef* vc) {
+  const size_t smem = ab.smem;
+  const int nt = ab.nt;
+  if (ab.bpc < 1 || nt < 1) return cudaErrorInvalidConfiguration;
+  const int ncell = (int)ipow(coarse_cells, dim);
+  const int sfine = 1 << (level - 1);
+  // the cluster variant (one block per cell in turn) takes the rule's chunks, never a tuned shape
+  const AugShape shape = aug_shape(dim, coarse_cells, level, jac_f32, ab, cluster_size == 0);
+  int chunk = shape.chunk, bpc = shape.bpc;
   AugArgs A;
   A.dim = dim;
   A.nc = coarse_cells;

@@ -74,7 +74,8 @@ EXPORTS = ("fmg_default_params", "fmg_workspace_bytes", "fmg_create", "fmg_set_r
            "fmg_graph_kernels", "fmg_vcycle_noalloc", "fmg_debug_barrier_fault", "fmg_fp64_fma_rate",
            "fmg_batch_create", "fmg_batch_create_mode", "fmg_batch_info",
            "fmg_batch_solve", "fmg_batch_sync", "fmg_batch_destroy", "fmg_server_create", "fmg_server_submit", "fmg_server_poll", "fmg_server_drain",
-           "fmg_server_get_info", "fmg_server_last_error", "fmg_server_destroy", "fmg_autotune", "fmg_tuned_shape")
+           "fmg_server_get_info", "fmg_server_last_error", "fmg_server_destroy", "fmg_autotune", "fmg_tuned_shape",
+           "fmg_autotune_augmented", "fmg_aug_shape")
 KT_AUGMENTED = 0
 KT_SMOOTH_TOP = 1
 KT_CORRECTION = 2
@@ -138,6 +139,8 @@ def load():
         "fmg_server_destroy": (c_int, [c_void_p]),
         "fmg_autotune": (c_int, [c_void_p, POINTER(c_int)]),
         "fmg_tuned_shape": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]),
+        "fmg_autotune_augmented": (c_int, [c_void_p, POINTER(c_int)]),
+        "fmg_aug_shape": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -406,6 +409,21 @@ def fmg_tuned_shape(ctx, level: int):
     block, strip = c_int(0), c_int(0)
     _check(load().fmg_tuned_shape(ctx, level, byref(block), byref(strip)), ctx)
     return block.value, strip.value
+
+
+def fmg_autotune_augmented(ctx) -> int:
+    """Tunes the augmented Newton kernel's launch shape per level (changes rounding, see the
+    header); returns the number of levels tuned."""
+    n = c_int()
+    _check(load().fmg_autotune_augmented(ctx, byref(n)), ctx)
+    return n.value
+
+
+def fmg_aug_shape(ctx, level: int):
+    """(chunk length, blocks per coarse cell) of the augmented kernel on `level`."""
+    a, b = c_int(), c_int()
+    _check(load().fmg_aug_shape(ctx, level, byref(a), byref(b)), ctx)
+    return a.value, b.value
 
 
 def fmg_server_last_error() -> str:
