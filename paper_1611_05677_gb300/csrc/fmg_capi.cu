@@ -791,6 +791,8 @@ bool phase_chain(fmg_ctx* c, int csz, cudaStream_t cap, std::vector<PhaseStep>& 
       ok = false;
       break;
     }
+    // the edges of a captured schedule carry data (programmatic edges between the kernels), so
+    // they are read with it
     size_t nd = 0;
     if (cudaGraphNodeGetDependentNodes(node, nullptr, nullptr, &nd) != cudaSuccess || nd > 1) {
       why = "the schedule is not a single chain";
@@ -798,7 +800,8 @@ bool phase_chain(fmg_ctx* c, int csz, cudaStream_t cap, std::vector<PhaseStep>& 
       break;
     }
     cudaGraphNode_t next = nullptr;
-    if (nd == 1 && cudaGraphNodeGetDependentNodes(node, &next, nullptr, &nd) != cudaSuccess) {
+    cudaGraphEdgeData edge = {};
+    if (nd == 1 && cudaGraphNodeGetDependentNodes(node, &next, &edge, &nd) != cudaSuccess) {
       why = "dependent node";
       ok = false;
       break;

@@ -97,13 +97,14 @@ __device__ __forceinline__ void k_residual_ff3s_body(const double* __restrict__ 
 
 __global__ void k_residual_ff3s(const double* __restrict__ u, const double* __restrict__ b, int n, ff sigma,
                                 float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0) {
+  pdl_start();
   k_residual_ff3s_body(u, b, n, sigma, r32, e32, d32, e0);
 }
 
 template <int D>
 __global__ void k_residual_ff(const double* __restrict__ u, const double* __restrict__ b, int n, ff sigma,
                               float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
-                              VarCoef vc, int ls) { k_residual_ff_body<D>(u, b, n, sigma, r32, e32, d32, e0, vc, ls); }
+                              VarCoef vc, int ls) { pdl_start(); k_residual_ff_body<D>(u, b, n, sigma, r32, e32, d32, e0, vc, ls); }
 
 // b = w (g - a f(u)) on the interior nodes, 0 on the boundary (eq. 3.4 with the vertex rule).
 __device__ __forceinline__ void k_nonlinear_rhs_ff_body(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
@@ -120,11 +121,12 @@ __device__ __forceinline__ void k_nonlinear_rhs_ff_body(const double* __restrict
 }
 
 __global__ void k_nonlinear_rhs_ff(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
-                                   int n, int dim, int kind, ff a, double a64, ff w) { k_nonlinear_rhs_ff_body(u, g, b, n, dim, kind, a, a64, w); }
+                                   int n, int dim, int kind, ff a, double a64, ff w) { pdl_start(); k_nonlinear_rhs_ff_body(u, g, b, n, dim, kind, a, a64, w); }
 
 // FMG interpolation u_f = P u_c (the natural inclusion, eq. 3.3) on the interior fine nodes.
 template <int D>
 __global__ void k_prolong_ff(const double* __restrict__ uc, int nc, double* __restrict__ uf, int nf) {
+  pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   const int l = D == 3 ? blockIdx.z + 1 : 0;
@@ -169,6 +171,7 @@ __global__ void k_level_start_ff(const double* __restrict__ uc, double* __restri
                                  double* __restrict__ b, int n, int kind, ff a, double a64, ff w, ff sigma,
                                  float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32,
                                  float e0, VarCoef vc, int ls) {
+  pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y, l = D == 3 ? blockIdx.z : 0;
   if (i > n) return;
@@ -298,21 +301,23 @@ __device__ __forceinline__ void k_level_start_ff2_body(const double* __restrict_
 __global__ void k_level_start_ff2(const double* __restrict__ uc, double* __restrict__ u, const double* __restrict__ g,
                                   double* __restrict__ b, int n, int kind, ff a, double a64, ff w,
                                   float* __restrict__ r32, float* __restrict__ e32, float* __restrict__ d32, float e0,
-                                  int strip, VarCoef vc, int ls) { k_level_start_ff2_body(uc, u, g, b, n, kind, a, a64, w, r32, e32, d32, e0, strip, vc, ls); }
+                                  int strip, VarCoef vc, int ls) { pdl_start(); k_level_start_ff2_body(uc, u, g, b, n, kind, a, a64, w, r32, e32, d32, e0, strip, vc, ls); }
 
 __device__ __forceinline__ void k_add_f32_ff_body(double* __restrict__ uff, const float* __restrict__ e, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) ff_store(uff + i, ff_add_f(ff_load(uff + i), e[i]));
 }
 
-__global__ void k_add_f32_ff(double* __restrict__ uff, const float* __restrict__ e, long long n) { k_add_f32_ff_body(uff, e, n); }
+__global__ void k_add_f32_ff(double* __restrict__ uff, const float* __restrict__ e, long long n) { pdl_start(); k_add_f32_ff_body(uff, e, n); }
 
 __global__ void k_ff_from_f64(const double* __restrict__ s, double* __restrict__ d, long long n) {
+  pdl_start();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) ff_store(d + i, ff_from_double(s[i]));
 }
 
 __global__ void k_ff_to_f64(const double* __restrict__ s, double* __restrict__ d, long long n) {
+  pdl_start();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = ff_to_double_fast(ff_load(s + i));
 }
@@ -335,11 +340,11 @@ cudaError_t launch_residual_ff(int dim, LevelGeo g, const double* u_ff, const do
   const VarCoef v = vc ? *vc : VarCoef{};
   const int ls = vc_level_shift(vc, n);
   if (dim == 2)
-    k_residual_ff<2><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff{1.f, 0.f}, r32, e32, d32, (float)e0, v, ls);
+    launch_k(k_residual_ff<2>, grid, kB, 0, s, u_ff, b_ff, n, ff{1.f, 0.f}, r32, e32, d32, (float)e0, v, ls);
   else if (v.a64)
-    k_residual_ff<3><<<grid, kB, 0, s>>>(u_ff, b_ff, n, ff_from_double(1.0 / n), r32, e32, d32, (float)e0, v, ls);
+    launch_k(k_residual_ff<3>, grid, kB, 0, s, u_ff, b_ff, n, ff_from_double(1.0 / n), r32, e32, d32, (float)e0, v, ls);
   else
-    k_residual_ff3s<<<dim3(grid.x, n + 1, cdiv_u(n + 1, kResStrip)), kB, 0, s>>>(u_ff, b_ff, n, ff_from_double(1.0 / n),
+    launch_k(k_residual_ff3s, dim3(grid.x, n + 1, cdiv_u(n + 1, kResStrip)), kB, 0, s, u_ff, b_ff, n, ff_from_double(1.0 / n),
                                                                                r32, e32, d32, (float)e0);
   return cudaGetLastError();
 }
@@ -349,7 +354,7 @@ cudaError_t launch_nonlinear_rhs_ff(int dim, LevelGeo g, const double* u_ff, con
   const double h = 1.0 / g.n;
   const double w = dim == 2 ? h * h : h * h * h;
   const dim3 grid(cdiv_u(g.n + 1, kB), g.n + 1, dim == 3 ? g.n + 1 : 1);
-  k_nonlinear_rhs_ff<<<grid, kB, 0, s>>>(u_ff, g_ff, b_ff, g.n, dim, kind, ff_from_double(a), a, ff_from_double(w));
+  launch_k(k_nonlinear_rhs_ff, grid, kB, 0, s, u_ff, g_ff, b_ff, g.n, dim, kind, ff_from_double(a), a, ff_from_double(w));
   return cudaGetLastError();
 }
 
@@ -357,9 +362,9 @@ cudaError_t launch_prolong_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGe
   const int nf = gf.n;
   const dim3 grid(cdiv_u(nf - 1, kB), nf - 1, dim == 3 ? nf - 1 : 1);
   if (dim == 2)
-    k_prolong_ff<2><<<grid, kB, 0, s>>>(uc_ff, gc.n, uf_ff, nf);
+    launch_k(k_prolong_ff<2>, grid, kB, 0, s, uc_ff, gc.n, uf_ff, nf);
   else
-    k_prolong_ff<3><<<grid, kB, 0, s>>>(uc_ff, gc.n, uf_ff, nf);
+    launch_k(k_prolong_ff<3>, grid, kB, 0, s, uc_ff, gc.n, uf_ff, nf);
   return cudaGetLastError();
 }
 
@@ -377,29 +382,29 @@ cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, Lev
     // strips of up to 8 rows, shorter on small levels so that the grid keeps ~1000 blocks
     int strip = 8;
     while (strip > 1 && (long long)cdiv_u(n + 1, kB) * cdiv_u(n + 1, strip) < 1024) strip >>= 1;
-    k_level_start_ff2<<<dim3(cdiv_u(n + 1, kB), cdiv_u(n + 1, strip)), kB, 0, s>>>(
+    launch_k(k_level_start_ff2, dim3(cdiv_u(n + 1, kB), cdiv_u(n + 1, strip)), kB, 0, s, 
         uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w), r32, e32, d32, (float)e0, strip, v,
         ls);
   } else
-    k_level_start_ff<3><<<grid, kB, 0, s>>>(uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w),
+    launch_k(k_level_start_ff<3>, grid, kB, 0, s, uc_ff, u_ff, g_ff, b_ff, n, kind, ff_from_double(a), a, ff_from_double(w),
                                             ff_from_double(h), r32, e32, d32, (float)e0, v, ls);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_f32_ff(LevelGeo g, double* u_ff, const float* e32, cudaStream_t s) {
-  k_add_f32_ff<<<cdiv_u(g.nodes, 256), 256, 0, s>>>(u_ff, e32, g.nodes);
+  launch_k(k_add_f32_ff, cdiv_u(g.nodes, 256), 256, 0, s, u_ff, e32, g.nodes);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ff_from_f64(const double* src, double* dst_ff, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_ff_from_f64<<<cdiv_u(n, 256), 256, 0, s>>>(src, dst_ff, n);
+  launch_k(k_ff_from_f64, cdiv_u(n, 256), 256, 0, s, src, dst_ff, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ff_to_f64(const double* src_ff, double* dst, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_ff_to_f64<<<cdiv_u(n, 256), 256, 0, s>>>(src_ff, dst, n);
+  launch_k(k_ff_to_f64, cdiv_u(n, 256), 256, 0, s, src_ff, dst, n);
   return cudaGetLastError();
 }
 

@@ -139,7 +139,7 @@ __device__ __forceinline__ void k_pre2_fused_body(const float* __restrict__ b, f
 
 template <int NU>
 __global__ void __launch_bounds__(kFB) k_pre2_fused(const float* __restrict__ b, float* __restrict__ u_out,
-                                                     float* __restrict__ bc, float* __restrict__ uc, int n) { k_pre2_fused_body<NU>(b, u_out, bc, uc, n); }
+                                                     float* __restrict__ bc, float* __restrict__ uc, int n) { pdl_start(); k_pre2_fused_body<NU>(b, u_out, bc, uc, n); }
 
 // MODE 0: the smoothed correction goes to u_out; 1: it is added to the FP64 iterate u64 (the
 // ops' arrays); 2: it is added to the float-float iterate u64 (the solve's level data).
@@ -220,7 +220,7 @@ __device__ __forceinline__ void k_post2_fused_body(const float* __restrict__ u_i
 template <int NU, int MODE>
 __global__ void __launch_bounds__(kFB) k_post2_fused(const float* __restrict__ u_in, const float* __restrict__ ec,
                                                       const float* __restrict__ b, float* __restrict__ u_out,
-                                                      double* __restrict__ u64, int n) { k_post2_fused_body<NU, MODE>(u_in, ec, b, u_out, u64, n); }
+                                                      double* __restrict__ u64, int n) { pdl_start(); k_post2_fused_body<NU, MODE>(u_in, ec, b, u_out, u64, n); }
 
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
@@ -243,12 +243,12 @@ cudaError_t launch_pre_fused(int dim, LevelGeo g, int nu, const float* b, float*
     constexpr int W = kFT + 2 * 4;
     const size_t smem = sizeof(float) * (2 * W * W + (kFT + 1) * (kFT + 1));
     if ((e = set_smem(k_pre2_fused<1>, smem)) != cudaSuccess) return e;
-    k_pre2_fused<1><<<grid, kFB, smem, s>>>(b, u_out, bc, uc, g.n);
+    launch_k(k_pre2_fused<1>, grid, kFB, smem, s, b, u_out, bc, uc, g.n);
   } else {
     constexpr int W = kFT + 2 * 6;
     const size_t smem = sizeof(float) * (2 * W * W + (kFT + 1) * (kFT + 1));
     if ((e = set_smem(k_pre2_fused<2>, smem)) != cudaSuccess) return e;
-    k_pre2_fused<2><<<grid, kFB, smem, s>>>(b, u_out, bc, uc, g.n);
+    launch_k(k_pre2_fused<2>, grid, kFB, smem, s, b, u_out, bc, uc, g.n);
   }
   return cudaGetLastError();
 }
@@ -265,26 +265,26 @@ cudaError_t launch_post_fused(int dim, LevelGeo g, int nu, const float* u_in, co
     const size_t smem = sizeof(float) * (2 * W * W + (W / 2 + 2) * (W / 2 + 2));
     if (mode == 2) {
       if ((e = set_smem(k_post2_fused<1, 2>, smem)) != cudaSuccess) return e;
-      k_post2_fused<1, 2><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      launch_k(k_post2_fused<1, 2>, grid, kFB, smem, s, u_in, ec, b, u_out, u64_top, g.n);
     } else if (mode == 1) {
       if ((e = set_smem(k_post2_fused<1, 1>, smem)) != cudaSuccess) return e;
-      k_post2_fused<1, 1><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      launch_k(k_post2_fused<1, 1>, grid, kFB, smem, s, u_in, ec, b, u_out, u64_top, g.n);
     } else {
       if ((e = set_smem(k_post2_fused<1, 0>, smem)) != cudaSuccess) return e;
-      k_post2_fused<1, 0><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      launch_k(k_post2_fused<1, 0>, grid, kFB, smem, s, u_in, ec, b, u_out, u64_top, g.n);
     }
   } else {
     constexpr int W = kFT + 2 * 4;
     const size_t smem = sizeof(float) * (2 * W * W + (W / 2 + 2) * (W / 2 + 2));
     if (mode == 2) {
       if ((e = set_smem(k_post2_fused<2, 2>, smem)) != cudaSuccess) return e;
-      k_post2_fused<2, 2><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      launch_k(k_post2_fused<2, 2>, grid, kFB, smem, s, u_in, ec, b, u_out, u64_top, g.n);
     } else if (mode == 1) {
       if ((e = set_smem(k_post2_fused<2, 1>, smem)) != cudaSuccess) return e;
-      k_post2_fused<2, 1><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      launch_k(k_post2_fused<2, 1>, grid, kFB, smem, s, u_in, ec, b, u_out, u64_top, g.n);
     } else {
       if ((e = set_smem(k_post2_fused<2, 0>, smem)) != cudaSuccess) return e;
-      k_post2_fused<2, 0><<<grid, kFB, smem, s>>>(u_in, ec, b, u_out, u64_top, g.n);
+      launch_k(k_post2_fused<2, 0>, grid, kFB, smem, s, u_in, ec, b, u_out, u64_top, g.n);
     }
   }
   return cudaGetLastError();

@@ -324,6 +324,7 @@ __device__ void fill_stiffness(double* M, int N, int ld, int m, int dim, double 
 // Level-1 setup: LDL^T of A_1 once, then A_1^{-1} column by column (one thread per column).
 // Launched with 64 threads.
 __global__ void k_coarse_inverse(int dim, int n1, double* __restrict__ Ainv, DevState* st, VarCoef vc) {
+  pdl_start();
   extern __shared__ double sm[];
   const int m = n1 - 1;
   const int N = dim == 2 ? m * m : m * m * m;
@@ -481,7 +482,7 @@ __device__ __forceinline__ void k_level1_newton_body(int dim, int n1, const doub
 
 template <typename T>
 __global__ void k_level1_newton(int dim, int n1, const double* __restrict__ g, double* __restrict__ u, int kind,
-                                double a, double tol, int maxit, DevState* st, int out_ff, VarCoef vc) { k_level1_newton_body<T>(dim, n1, g, u, kind, a, tol, maxit, st, out_ff, vc); }
+                                double a, double tol, int maxit, DevState* st, int out_ff, VarCoef vc) { pdl_start(); k_level1_newton_body<T>(dim, n1, g, u, kind, a, tol, maxit, st, out_ff, vc); }
 
 // ------------------------------------------------------------------ augmented problem
 template <int D, bool JF32>
@@ -1380,6 +1381,7 @@ __host__ __device__ constexpr int aug_jtab_entries(int nc) {
 
 template <int D>
 __global__ void k_aug_jtab(int nc, int* __restrict__ tab) {
+  pdl_start();
   using G = Aug<D, true>;
   constexpr int N3 = D == 2 ? 9 : 27;
   const int NH = (int)ipow(nc - 1, D);
@@ -2141,6 +2143,7 @@ __device__ void step_report(const AugArgs& A, const StepState& S, int it, bool w
 // that the constant-coefficient kernels keep their register allocation).
 template <int D, bool JF32, bool VC>
 __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented(AugArgs A) {
+  pdl_start();
   using G = Aug<D, JF32>;
   using FT = typename std::conditional<JF32, float, double>::type;
   extern __shared__ double sm[];
@@ -2240,6 +2243,7 @@ __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_au
 template <int D>
 __global__ void __launch_bounds__(256) k_aug_update(double* __restrict__ u, int n, int ls, int nc,
                                                     const float* __restrict__ cf, int out_f64) {
+  pdl_start();
   __shared__ float cs[128];
   __shared__ float am1;
   const int cn = (int)ipow(nc + 1, D);
@@ -2367,6 +2371,7 @@ __device__ __forceinline__ void k_augmented_cluster_body(const AugArgs& A) {
 
 template <int D, bool JF32>
 __global__ void __launch_bounds__(Aug<D, JF32>::NT, 512 / Aug<D, JF32>::NT) k_augmented_cluster(const __grid_constant__ AugArgs A) {
+  pdl_start();
   k_augmented_cluster_body<D, JF32>(A);
 }
 
@@ -2398,7 +2403,7 @@ cudaError_t launch_coarse_inverse(int dim, LevelGeo g1, double* Ainv, DevState* 
   const size_t smem = sizeof(double) * ((size_t)N * (N + 1) + 3 * N + 4);
   cudaError_t e = raise_dyn_smem((const void*)k_coarse_inverse, smem);
   if (e != cudaSuccess) return e;
-  k_coarse_inverse<<<1, 64, smem, s>>>(dim, g1.n, Ainv, st, vc ? *vc : VarCoef{});
+  launch_k(k_coarse_inverse, 1, 64, smem, s, dim, g1.n, Ainv, st, vc ? *vc : VarCoef{});
   return cudaGetLastError();
 }
 
@@ -2412,11 +2417,11 @@ cudaError_t launch_level1_newton(int dim, LevelGeo g1, const double* gn, double*
   if (f32_factor) {
     const size_t smem = sizeof(double) * (3 * N + 2) + sizeof(float) * (N * (N + 1) + 2 * N + 4);
     if ((e = raise_dyn_smem((const void*)k_level1_newton<float>, smem)) != cudaSuccess) return e;
-    k_level1_newton<float><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0, v);
+    launch_k(k_level1_newton<float>, 1, 256, smem, s, dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0, v);
   } else {
     const size_t smem = sizeof(double) * (3 * N + 2 + N * (N + 1) + 2 * N + 4);
     if ((e = raise_dyn_smem((const void*)k_level1_newton<double>, smem)) != cudaSuccess) return e;
-    k_level1_newton<double><<<1, 256, smem, s>>>(dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0, v);
+    launch_k(k_level1_newton<double>, 1, 256, smem, s, dim, g1.n, gn, u, kind, a, tol, maxit, st, out_ff ? 1 : 0, v);
   }
   return cudaGetLastError();
 }
@@ -2430,9 +2435,9 @@ size_t aug_jtab_ints(int dim, int coarse_cells) {
 
 cudaError_t launch_aug_jtab(int dim, int coarse_cells, int* tab, cudaStream_t s) {
   if (dim == 2)
-    k_aug_jtab<2><<<4, 256, 0, s>>>(coarse_cells, tab);
+    launch_k(k_aug_jtab<2>, 4, 256, 0, s, coarse_cells, tab);
   else
-    k_aug_jtab<3><<<4, 256, 0, s>>>(coarse_cells, tab);
+    launch_k(k_aug_jtab<3>, 4, 256, 0, s, coarse_cells, tab);
   return cudaGetLastError();
 }
 
@@ -2668,9 +2673,9 @@ cudaError_t launch_augmented(int dim, int coarse_cells, int level, LevelGeo gk, 
   if (gy > 65535) gy = 65535;
   const float* cf = reinterpret_cast<const float*>(ab.cfin);
   if (dim == 2)
-    k_aug_update<2><<<dim3(gx, (unsigned)gy), 256, 0, s>>>(u, gk.n, ls, coarse_cells, cf, out_f64);
+    launch_k(k_aug_update<2>, dim3(gx, (unsigned)gy), 256, 0, s, u, gk.n, ls, coarse_cells, cf, out_f64);
   else
-    k_aug_update<3><<<dim3(gx, (unsigned)gy), 256, 0, s>>>(u, gk.n, ls, coarse_cells, cf, out_f64);
+    launch_k(k_aug_update<3>, dim3(gx, (unsigned)gy), 256, 0, s, u, gk.n, ls, coarse_cells, cf, out_f64);
   return cudaGetLastError();
 }
 

@@ -45,10 +45,11 @@ __device__ __forceinline__ void k_rbgs2_body(T* __restrict__ u, const T* __restr
 }
 
 template <typename T>
-__global__ void k_rbgs2(T* __restrict__ u, const T* __restrict__ b, int n, int colour) { k_rbgs2_body<T>(u, b, n, colour); }
+__global__ void k_rbgs2(T* __restrict__ u, const T* __restrict__ b, int n, int colour) { pdl_start(); k_rbgs2_body<T>(u, b, n, colour); }
 
 template <typename T>
 __global__ void k_rbgs3(T* __restrict__ u, const T* __restrict__ b, int n, int colour, T bscale, T inv6) {
+  pdl_start();
   const int j = blockIdx.y + 1;
   const int l = blockIdx.z + 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,7 +126,7 @@ __device__ __forceinline__ void k_cheb_body(const T* __restrict__ u, T* __restri
 
 template <typename T, int D, bool PROL>
 __global__ void k_cheb(const T* __restrict__ u, T* __restrict__ uo, T* __restrict__ d, const T* __restrict__ b, int n,
-                       T bscale, T cd, T cr, int first, int strip, const T* __restrict__ ec) { k_cheb_body<T, D, PROL>(u, uo, d, b, n, bscale, cd, cr, first, strip, ec); }
+                       T bscale, T cd, T cr, int first, int strip, const T* __restrict__ ec) { pdl_start(); k_cheb_body<T, D, PROL>(u, uo, d, b, n, bscale, cd, cr, first, strip, ec); }
 
 // The last Chebyshev step of the mixed path's top-level FP32 cycle fused with its update
 // u64 += u + d_new (the new correction is neither stored nor read back); FF: u64 holds
@@ -162,7 +163,7 @@ __device__ __forceinline__ void k_cheb_add64_body(const float* __restrict__ u, c
 
 template <int D, bool FF>
 __global__ void k_cheb_add64(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ b,
-                             double* __restrict__ u64, int n, float bscale, float cd, float cr, int first, int strip) { k_cheb_add64_body<D, FF>(u, d, b, u64, n, bscale, cd, cr, first, strip); }
+                             double* __restrict__ u64, int n, float bscale, float cd, float cr, int first, int strip) { pdl_start(); k_cheb_add64_body<D, FF>(u, d, b, u64, n, bscale, cd, cr, first, strip); }
 
 template <typename T>
 __device__ __forceinline__ void k_copy_t_body(const T* __restrict__ s, T* __restrict__ d, long long n) {
@@ -171,9 +172,10 @@ __device__ __forceinline__ void k_copy_t_body(const T* __restrict__ s, T* __rest
 }
 
 template <typename T>
-__global__ void k_copy_t(const T* __restrict__ s, T* __restrict__ d, long long n) { k_copy_t_body<T>(s, d, n); }
+__global__ void k_copy_t(const T* __restrict__ s, T* __restrict__ d, long long n) { pdl_start(); k_copy_t_body<T>(s, d, n); }
 
 __global__ void k_to_f32(const double* __restrict__ s, float* __restrict__ d, long long n) {
+  pdl_start();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = (float)s[i];
 }
@@ -277,6 +279,7 @@ __device__ __forceinline__ void k_resrestrict2_body(const TF* __restrict__ u, co
 template <typename TF, typename TC, int S>
 __global__ void k_resrestrict2(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TC* __restrict__ bc,
                                TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) {
+  pdl_start();
   k_resrestrict2_body<TF, TC, S>(u, b, nf, bc, uc, ncells, dc, e0);
 }
 
@@ -287,6 +290,7 @@ inline int rr_strip(int ncells) { return ncells <= 128 ? 1 : (ncells <= 512 ? 2 
 template <typename TF, typename TC>
 __global__ void k_resrestrict3(const TF* __restrict__ u, const TF* __restrict__ b, int nf, TF sigma,
                                TC* __restrict__ bc, TC* __restrict__ uc, int ncells, TC* __restrict__ dc, TC e0) {
+  pdl_start();
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int J = blockIdx.y + 1;
   const int L = blockIdx.z + 1;
@@ -314,6 +318,7 @@ __global__ void k_resrestrict3(const TF* __restrict__ u, const TF* __restrict__ 
 __global__ void k_residual2(const double* __restrict__ u, const double* __restrict__ b, int n,
                             double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32,
                             float* __restrict__ d32, float e0) {
+  pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i > n) return;
@@ -334,6 +339,7 @@ __global__ void k_residual2(const double* __restrict__ u, const double* __restri
 __global__ void k_residual3(const double* __restrict__ u, const double* __restrict__ b, int n, double sigma,
                             double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32,
                             float* __restrict__ d32, float e0) {
+  pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   const int l = blockIdx.z;
@@ -371,6 +377,7 @@ __device__ __forceinline__ void vc_offsets(long long np, long long* o) {
 
 template <typename T, int D>
 __global__ void k_rbgs_vc(T* __restrict__ u, const T* __restrict__ b, int n, int colour, int ls, VarCoef vc) {
+  pdl_start();
   const int j = blockIdx.y + 1;
   const int l = D == 3 ? blockIdx.z + 1 : 0;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,6 +420,7 @@ __device__ __forceinline__ T res_vc(const T* __restrict__ u, const T* __restrict
 template <typename TF, typename TC, int D>
 __global__ void k_resrestrict_vc(const TF* __restrict__ u, const TF* __restrict__ b, int nf, int ls, VarCoef vc,
                                  TC* __restrict__ bc, TC* __restrict__ uc, int ncells) {
+  pdl_start();
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int J = blockIdx.y + 1;
   const int L = D == 3 ? blockIdx.z + 1 : 0;
@@ -442,6 +450,7 @@ __global__ void k_resrestrict_vc(const TF* __restrict__ u, const TF* __restrict_
 template <int D>
 __global__ void k_residual_vc(const double* __restrict__ u, const double* __restrict__ b, int n, int ls, VarCoef vc,
                               double* __restrict__ r, float* __restrict__ r32, float* __restrict__ e32) {
+  pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   const int l = D == 3 ? blockIdx.z : 0;
@@ -478,10 +487,11 @@ __device__ __forceinline__ void k_prolong2_body(const TC* __restrict__ e, int nc
 }
 
 template <typename TF, typename TC>
-__global__ void k_prolong2(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) { k_prolong2_body<TF, TC>(e, nc, u, nf, add); }
+__global__ void k_prolong2(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) { pdl_start(); k_prolong2_body<TF, TC>(e, nc, u, nf, add); }
 
 template <typename TF, typename TC>
 __global__ void k_prolong3(const TC* __restrict__ e, int nc, TF* __restrict__ u, int nf, int add) {
+  pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   const int l = blockIdx.z + 1;
@@ -497,6 +507,7 @@ __global__ void k_prolong3(const TC* __restrict__ e, int nc, TF* __restrict__ u,
 
 // ------------------------------------------------------------------ pointwise kernels
 __global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, long long n) {
+  pdl_start();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) u[i] += (double)e[i];
 }
@@ -529,9 +540,10 @@ __device__ __forceinline__ void k_nonlinear_rhs_body(const double* __restrict__ 
 }
 
 __global__ void k_nonlinear_rhs(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
-                                int n, int dim, int kind, double a, double w) { k_nonlinear_rhs_body(u, g, b, n, dim, kind, a, w); }
+                                int n, int dim, int kind, double a, double w) { pdl_start(); k_nonlinear_rhs_body(u, g, b, n, dim, kind, a, w); }
 
 __global__ void k_decimate(const double* __restrict__ src, int nf, double* __restrict__ dst, int nc, int dim) {
+  pdl_start();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long cp = nc + 1;
   const long long total = dim == 2 ? cp * cp : cp * cp * cp;
@@ -543,12 +555,14 @@ __global__ void k_decimate(const double* __restrict__ src, int nf, double* __res
 }
 
 __global__ void k_zero_boundary(double* __restrict__ a, long long nodes, int n, int dim) {
+  pdl_start();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nodes) return;
   if (!interior_of(idx, n, dim)) a[idx] = 0.0;
 }
 
 __global__ void k_copy(const double* __restrict__ s, double* __restrict__ d, long long n) {
+  pdl_start();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = s[i];
 }
@@ -586,7 +600,7 @@ __device__ __forceinline__ void k_coarse_solve_body(const double* __restrict__ A
 
 template <typename T>
 __global__ void k_coarse_solve(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ u, int m,
-                               int N, int dim) { k_coarse_solve_body<T>(Ainv, b, u, m, N, dim); }
+                               int N, int dim) { pdl_start(); k_coarse_solve_body<T>(Ainv, b, u, m, N, dim); }
 
 // ------------------------------------------------------------------ coarse V-cycle in one CTA
 // The V(nu_pre, nu_post) cycle on levels jtop..1 with every level's u and b in shared
@@ -893,7 +907,7 @@ __device__ __forceinline__ void k_vcycle_coarse_body(T* __restrict__ ug, const T
 template <typename T, int D>
 __global__ void __launch_bounds__(1024) k_vcycle_coarse(T* __restrict__ ug, const T* __restrict__ bg, int n0, int jtop, int nu_pre,
                                 int nu_post, const double* __restrict__ Ainv, const float* __restrict__ Ainv32,
-                                int cheb, const __grid_constant__ ChebCoef cf, int zero_start) { k_vcycle_coarse_body<T, D>(ug, bg, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb, cf, zero_start); }
+                                int cheb, const __grid_constant__ ChebCoef cf, int zero_start) { pdl_start(); k_vcycle_coarse_body<T, D>(ug, bg, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb, cf, zero_start); }
 
 }  // namespace
 
@@ -906,15 +920,15 @@ cudaError_t launch_rbgs(int dim, LevelGeo g, T* u, const T* b, int colour, cudaS
   if (vc && vc->a64) {
     const int ls = vc_ls(*vc, n);
     if (dim == 2)
-      k_rbgs_vc<T, 2><<<dim3(gx, n - 1), kBlock, 0, s>>>(u, b, n, colour, ls, *vc);
+      launch_k(k_rbgs_vc<T, 2>, dim3(gx, n - 1), kBlock, 0, s, u, b, n, colour, ls, *vc);
     else
-      k_rbgs_vc<T, 3><<<dim3(gx, n - 1, n - 1), kBlock, 0, s>>>(u, b, n, colour, ls, *vc);
+      launch_k(k_rbgs_vc<T, 3>, dim3(gx, n - 1, n - 1), kBlock, 0, s, u, b, n, colour, ls, *vc);
     return cudaGetLastError();
   }
   if (dim == 2) {
-    k_rbgs2<T><<<dim3(gx, n - 1), kBlock, 0, s>>>(u, b, n, colour);
+    launch_k(k_rbgs2<T>, dim3(gx, n - 1), kBlock, 0, s, u, b, n, colour);
   } else {
-    k_rbgs3<T><<<dim3(gx, n - 1, n - 1), kBlock, 0, s>>>(u, b, n, colour, T(n), T(1.0 / 6.0));
+    launch_k(k_rbgs3<T>, dim3(gx, n - 1, n - 1), kBlock, 0, s, u, b, n, colour, T(n), T(1.0 / 6.0));
   }
   return cudaGetLastError();
 }
@@ -928,22 +942,22 @@ cudaError_t launch_residual_restrict(int dim, LevelGeo gf, const TF* u_f, const 
     if (d_c) return cudaErrorInvalidValue;   // Chebyshev smoothing does not take A(x)
     const int ls = vc_ls(*vc, gf.n);
     if (dim == 2)
-      k_resrestrict_vc<TF, TC, 2><<<dim3(gx, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, ls, *vc, b_c, u_c, nc);
+      launch_k(k_resrestrict_vc<TF, TC, 2>, dim3(gx, nc - 1), kBlock, 0, s, u_f, b_f, gf.n, ls, *vc, b_c, u_c, nc);
     else
-      k_resrestrict_vc<TF, TC, 3><<<dim3(gx, nc - 1, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, ls, *vc, b_c, u_c, nc);
+      launch_k(k_resrestrict_vc<TF, TC, 3>, dim3(gx, nc - 1, nc - 1), kBlock, 0, s, u_f, b_f, gf.n, ls, *vc, b_c, u_c, nc);
     return cudaGetLastError();
   }
   if (dim == 2) {
     const int S = rr_strip(nc);
     const dim3 grid(gx, cdiv(nc - 1, S));
     if (S == 1)
-      k_resrestrict2<TF, TC, 1><<<grid, kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
+      launch_k(k_resrestrict2<TF, TC, 1>, grid, kBlock, 0, s, u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
     else if (S == 2)
-      k_resrestrict2<TF, TC, 2><<<grid, kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
+      launch_k(k_resrestrict2<TF, TC, 2>, grid, kBlock, 0, s, u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
     else
-      k_resrestrict2<TF, TC, 4><<<grid, kBlock, 0, s>>>(u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
+      launch_k(k_resrestrict2<TF, TC, 4>, grid, kBlock, 0, s, u_f, b_f, gf.n, b_c, u_c, nc, d_c, TC(e0));
   } else {
-    k_resrestrict3<TF, TC><<<dim3(gx, nc - 1, nc - 1), kBlock, 0, s>>>(u_f, b_f, gf.n, TF(1.0) / TF(gf.n), b_c,
+    launch_k(k_resrestrict3<TF, TC>, dim3(gx, nc - 1, nc - 1), kBlock, 0, s, u_f, b_f, gf.n, TF(1.0) / TF(gf.n), b_c,
                                                                         u_c, nc, d_c, TC(e0));
   }
   return cudaGetLastError();
@@ -957,15 +971,15 @@ cudaError_t launch_residual_to_f32(int dim, LevelGeo g, const double* u, const d
     if (d32) return cudaErrorInvalidValue;
     const int ls = vc_ls(*vc, n);
     if (dim == 2)
-      k_residual_vc<2><<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, nullptr, r32, e32);
+      launch_k(k_residual_vc<2>, dim3(gx, n + 1), kBlock, 0, s, u, b, n, ls, *vc, nullptr, r32, e32);
     else
-      k_residual_vc<3><<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, nullptr, r32, e32);
+      launch_k(k_residual_vc<3>, dim3(gx, n + 1, n + 1), kBlock, 0, s, u, b, n, ls, *vc, nullptr, r32, e32);
     return cudaGetLastError();
   }
   if (dim == 2)
-    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, nullptr, r32, e32, d32, (float)e0);
+    launch_k(k_residual2, dim3(gx, n + 1), kBlock, 0, s, u, b, n, nullptr, r32, e32, d32, (float)e0);
   else
-    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, nullptr, r32, e32, d32, (float)e0);
+    launch_k(k_residual3, dim3(gx, n + 1, n + 1), kBlock, 0, s, u, b, n, 1.0 / n, nullptr, r32, e32, d32, (float)e0);
   return cudaGetLastError();
 }
 
@@ -976,15 +990,15 @@ cudaError_t launch_residual(int dim, LevelGeo g, const double* u, const double* 
   if (vc && vc->a64) {
     const int ls = vc_ls(*vc, n);
     if (dim == 2)
-      k_residual_vc<2><<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, r, nullptr, nullptr);
+      launch_k(k_residual_vc<2>, dim3(gx, n + 1), kBlock, 0, s, u, b, n, ls, *vc, r, nullptr, nullptr);
     else
-      k_residual_vc<3><<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, ls, *vc, r, nullptr, nullptr);
+      launch_k(k_residual_vc<3>, dim3(gx, n + 1, n + 1), kBlock, 0, s, u, b, n, ls, *vc, r, nullptr, nullptr);
     return cudaGetLastError();
   }
   if (dim == 2)
-    k_residual2<<<dim3(gx, n + 1), kBlock, 0, s>>>(u, b, n, r, nullptr, nullptr, nullptr, 0.0f);
+    launch_k(k_residual2, dim3(gx, n + 1), kBlock, 0, s, u, b, n, r, nullptr, nullptr, nullptr, 0.0f);
   else
-    k_residual3<<<dim3(gx, n + 1, n + 1), kBlock, 0, s>>>(u, b, n, 1.0 / n, r, nullptr, nullptr, nullptr, 0.0f);
+    launch_k(k_residual3, dim3(gx, n + 1, n + 1), kBlock, 0, s, u, b, n, 1.0 / n, r, nullptr, nullptr, nullptr, 0.0f);
   return cudaGetLastError();
 }
 
@@ -993,15 +1007,15 @@ cudaError_t launch_prolong(int dim, LevelGeo gc, const TC* e_c, LevelGeo gf, TF*
   const int nf = gf.n;
   const unsigned gx = cdiv(nf - 1, kBlock);
   if (dim == 2)
-    k_prolong2<TF, TC><<<dim3(gx, nf - 1), kBlock, 0, s>>>(e_c, gc.n, u_f, nf, add);
+    launch_k(k_prolong2<TF, TC>, dim3(gx, nf - 1), kBlock, 0, s, e_c, gc.n, u_f, nf, add);
   else
-    k_prolong3<TF, TC><<<dim3(gx, nf - 1, nf - 1), kBlock, 0, s>>>(e_c, gc.n, u_f, nf, add);
+    launch_k(k_prolong3<TF, TC>, dim3(gx, nf - 1, nf - 1), kBlock, 0, s, e_c, gc.n, u_f, nf, add);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_f32(LevelGeo g, int dim, double* u, const float* e32, cudaStream_t s) {
   (void)dim;
-  k_add_f32<<<cdiv(g.nodes, 256), 256, 0, s>>>(u, e32, g.nodes);
+  launch_k(k_add_f32, cdiv(g.nodes, 256), 256, 0, s, u, e32, g.nodes);
   return cudaGetLastError();
 }
 
@@ -1010,22 +1024,22 @@ cudaError_t launch_nonlinear_rhs(int dim, LevelGeo g, const double* u, const dou
   const double h = 1.0 / g.n;
   const double w = dim == 2 ? h * h : h * h * h;
   const unsigned gx = cdiv(g.n + 1, kBlock);
-  k_nonlinear_rhs<<<dim3(gx, g.n + 1, dim == 3 ? g.n + 1 : 1), kBlock, 0, s>>>(u, gn, b, g.n, dim, kind, a, w);
+  launch_k(k_nonlinear_rhs, dim3(gx, g.n + 1, dim == 3 ? g.n + 1 : 1), kBlock, 0, s, u, gn, b, g.n, dim, kind, a, w);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decimate(int dim, LevelGeo gf, const double* gsrc, LevelGeo gc, double* gdst, cudaStream_t s) {
-  k_decimate<<<cdiv(gc.nodes, 256), 256, 0, s>>>(gsrc, gf.n, gdst, gc.n, dim);
+  launch_k(k_decimate, cdiv(gc.nodes, 256), 256, 0, s, gsrc, gf.n, gdst, gc.n, dim);
   return cudaGetLastError();
 }
 
 cudaError_t launch_zero_boundary(int dim, LevelGeo g, double* a, cudaStream_t s) {
-  k_zero_boundary<<<cdiv(g.nodes, 256), 256, 0, s>>>(a, g.nodes, g.n, dim);
+  launch_k(k_zero_boundary, cdiv(g.nodes, 256), 256, 0, s, a, g.nodes, g.n, dim);
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const double* src, double* dst, long long n, cudaStream_t s) {
-  k_copy<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+  launch_k(k_copy, cdiv(n, 256), 256, 0, s, src, dst, n);
   return cudaGetLastError();
 }
 
@@ -1033,7 +1047,7 @@ cudaError_t launch_coarse_solve_f64(int dim, LevelGeo g1, const double* Ainv, co
                                     cudaStream_t s) {
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
-  k_coarse_solve<double><<<1, 64, N * sizeof(double), s>>>(Ainv, b, u, m, N, dim);
+  launch_k(k_coarse_solve<double>, 1, 64, N * sizeof(double), s, Ainv, b, u, m, N, dim);
   return cudaGetLastError();
 }
 
@@ -1041,7 +1055,7 @@ cudaError_t launch_coarse_solve_f32(int dim, LevelGeo g1, const double* Ainv, co
                                     cudaStream_t s) {
   const int m = g1.n - 1;
   const int N = (int)ipow(m, dim);
-  k_coarse_solve<float><<<1, 64, N * sizeof(double), s>>>(Ainv, b, u, m, N, dim);
+  launch_k(k_coarse_solve<float>, 1, 64, N * sizeof(double), s, Ainv, b, u, m, N, dim);
   return cudaGetLastError();
 }
 
@@ -1068,11 +1082,11 @@ cudaError_t launch_coarse_cycle(int dim, int n0, int jtop, T* u, const T* b, int
   cudaError_t e;
   if (dim == 2) {
     if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 2>, smem)) != cudaSuccess) return e;
-    k_vcycle_coarse<T, 2><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb ? 1 : 0, cf,
+    launch_k(k_vcycle_coarse<T, 2>, 1, 1024, smem, s, u, b, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb ? 1 : 0, cf,
                                                  zero_start ? 1 : 0);
   } else {
     if ((e = raise_dyn_smem((const void*)k_vcycle_coarse<T, 3>, smem)) != cudaSuccess) return e;
-    k_vcycle_coarse<T, 3><<<1, 1024, smem, s>>>(u, b, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb ? 1 : 0, cf,
+    launch_k(k_vcycle_coarse<T, 3>, 1, 1024, smem, s, u, b, n0, jtop, nu_pre, nu_post, Ainv, Ainv32, cheb ? 1 : 0, cf,
                                                  zero_start ? 1 : 0);
   }
   return cudaGetLastError();
@@ -1149,13 +1163,13 @@ cudaError_t launch_cheb_shaped(int dim, LevelGeo g, const T* u, T* uo, T* d, con
   const T bs = dim == 2 ? T(1) : T(n);
   const int f = first ? 1 : 0;
   if (dim == 2 && ec)
-    k_cheb<T, 2, true><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
+    launch_k(k_cheb<T, 2, true>, grid, sh.block, 0, s, u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
   else if (dim == 2)
-    k_cheb<T, 2, false><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
+    launch_k(k_cheb<T, 2, false>, grid, sh.block, 0, s, u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
   else if (ec)
-    k_cheb<T, 3, true><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
+    launch_k(k_cheb<T, 3, true>, grid, sh.block, 0, s, u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
   else
-    k_cheb<T, 3, false><<<grid, sh.block, 0, s>>>(u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
+    launch_k(k_cheb<T, 3, false>, grid, sh.block, 0, s, u, uo, d, b, n, bs, T(cd), T(cr), f, sh.strip, ec);
   return cudaGetLastError();
 }
 
@@ -1175,25 +1189,25 @@ cudaError_t launch_cheb_add64(int dim, LevelGeo g, const float* u, const float* 
   const float bs = dim == 2 ? 1.0f : (float)n;
   const int f = first ? 1 : 0;
   if (dim == 2 && u_ff)
-    k_cheb_add64<2, true><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
+    launch_k(k_cheb_add64<2, true>, grid, sh.block, 0, s, u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
   else if (dim == 2)
-    k_cheb_add64<2, false><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
+    launch_k(k_cheb_add64<2, false>, grid, sh.block, 0, s, u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
   else if (u_ff)
-    k_cheb_add64<3, true><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
+    launch_k(k_cheb_add64<3, true>, grid, sh.block, 0, s, u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
   else
-    k_cheb_add64<3, false><<<grid, sh.block, 0, s>>>(u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
+    launch_k(k_cheb_add64<3, false>, grid, sh.block, 0, s, u, d, b, u64, n, bs, (float)cd, (float)cr, f, sh.strip);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_to_f32<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+  launch_k(k_to_f32, cdiv(n, 256), 256, 0, s, src, dst, n);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_copy_t(const T* src, T* dst, long long n, cudaStream_t s) {
-  k_copy_t<T><<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+  launch_k(k_copy_t<T>, cdiv(n, 256), 256, 0, s, src, dst, n);
   return cudaGetLastError();
 }
 
