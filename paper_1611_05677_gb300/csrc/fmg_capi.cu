@@ -561,6 +561,8 @@ cudaError_t correction_step_ff(fmg_ctx* c, int k, bool out_f64, bool from_coarse
 }
 
 cudaError_t run_fmg(fmg_ctx* c) {
+  // programmatic serialization only for a context that runs alone (no cluster Newton kernel)
+  PdlScope pdl(c->cluster_aug == 0);
   c->timed_next = 0;
   // per-solve statistics start at zero (flags, iteration counts, alphas)
   TRY(cudaMemsetAsync(c->st, 0, offsetof(DevState, alpha_cur), c->stream));

@@ -28,7 +28,6 @@ constexpr unsigned kFlagDropped = 4u;
 constexpr unsigned kFlagNotSPD = 8u;
 constexpr unsigned kFlagTimeout = 16u;
 
-// Small per-context device state (one allocation, part of the workspace).
 // Programmatic dependent launch.  Every kernel of the solve starts with pdl_start(): it lets the
 // next kernel on the stream be scheduled (launch_dependents) and then waits until the previous
 // kernel has completed and its memory is visible (wait), before touching memory.  launch_k
@@ -48,6 +47,19 @@ __device__ __forceinline__ void pdl_start() {
 // (3D solve 4.17 ms with every grid, 4.00 with this limit, 4.03 with none; 2D 1.37, 1.37, 1.45).
 constexpr long long kPdlMaxBlocks = 65536;
 
+// Launches of this thread ask for programmatic serialization only while t_pdl is set.  A context
+// that has the device to itself captures with it set; contexts that run side by side (batch
+// branches, the request server) capture with it clear, since a grid that launches early holds
+// the SM slots its waiting blocks sit in, which the other streams' kernels would use (served
+// requests measured 20-30 % slower with it).
+inline thread_local bool t_pdl = true;
+
+struct PdlScope {
+  bool saved;
+  explicit PdlScope(bool on) : saved(t_pdl) { t_pdl = on; }
+  ~PdlScope() { t_pdl = saved; }
+};
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                             Args&&... args) {
@@ -60,10 +72,11 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = attr;
-  cfg.numAttrs = (long long)grid.x * grid.y * grid.z <= kPdlMaxBlocks ? 1 : 0;
+  cfg.numAttrs = t_pdl && (long long)grid.x * grid.y * grid.z <= kPdlMaxBlocks ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Small per-context device state (one allocation, part of the workspace).
 struct DevState {
   unsigned int flags;
   int level1_iters;
