@@ -35,12 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "FMG fine DOFs/s to discretization error, mixed vs FP64; HBM GB/s; p50/p99"
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, keyed by
 # (kind, dim); a kernel changed since its capture has no entry (traffic null)
-TRAFFIC = {("pre_top", 2): 16_792_064 + 6_912,
-           ("smooth_top", 2): 50_357_248 + 261_376,
+TRAFFIC = {("smooth_top", 2): 50_357_504 + 8_448,
            # the finest level's augmented Newton launch with its update kernel (2D), the Newton
            # launch alone (3D): dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture each
-           ("augmented", 2): 68_462_848 + 2_825_984 + 33_570_000,
-           ("augmented", 3): 582_397_440 + 129_488_640}
+           ("augmented", 2): 68_331_008 + 1_463_040 + 33_567_488,
+           ("augmented", 3): 579_506_944 + 128_349_184}
 WORKLOAD = "2D unit square P1, H=1/8, 8 refinements (2049x2049 nodes, 4,190,209 fine DOFs), u^3, 8 sin modes"
 WORKLOAD_3D = ("3D unit cube P1 on Kuhn tetrahedra, H=1/4, 6 refinements (257^3 nodes, 16,581,375 fine DOFs), "
                "exp(u)-1, 8 sin modes with U[0,1] amplitudes")
