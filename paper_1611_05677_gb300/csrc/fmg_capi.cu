@@ -620,11 +620,8 @@ fmg_status load_rhs(fmg_ctx* c, const double* g_fine, int on_device) {
   const int top = c->nlev - 1;
   CK(c, cudaMemcpyAsync(c->g[top], g_fine, c->geo[top].nodes * sizeof(double),
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-  CK(c, launch_zero_boundary(c->p.dim, c->geo[top], c->g[top], c->stream));
-  for (int k = top - 1; k >= 0; --k)
-    CK(c, launch_decimate(c->p.dim, c->geo[top], c->g[top], c->geo[k], c->g[k], c->stream));
-  if (c->p.precision == FMG_PREC_MIXED)
-    for (int k = 0; k <= top; ++k) CK(c, launch_ff_from_f64(c->g[k], c->gf[k], c->geo[k].nodes, c->stream));
+  // the boundary ring, every coarser level by injection and the float-float copies: one launch
+  CK(c, launch_rhs_levels(c->p.dim, c->nlev, c->geo, c->g, c->gf, c->p.precision == FMG_PREC_MIXED, c->stream));
   return FMG_OK;
 }
 

@@ -396,6 +396,71 @@ cudaError_t launch_add_f32_ff(LevelGeo g, double* u_ff, const float* e32, cudaSt
   return cudaGetLastError();
 }
 
+namespace {
+
+// The right-hand side of every level from the fine g just copied in, in one launch: the fine
+// g's boundary ring set to zero in place; each coarser level's g the fine values at its nodes (the
+// nodal injection of the nested hierarchy: node (i, j[, l]) of level k is fine node
+// (i, j[, l]) n_L / n_k), zero on its boundary; and with ff the float-float copy of every level.
+// Blocks boff[k] .. boff[k+1]-1 take level k.  The fine level's blocks write only its boundary
+// ring and the coarser levels' blocks read only fine interior nodes, so they do not race.
+struct RhsLevels {
+  double* g[kMaxLevels];
+  double* gf[kMaxLevels];
+  int n[kMaxLevels];
+  long long nodes[kMaxLevels];
+  long long boff[kMaxLevels + 1];
+  int nlev, dim, ff;
+};
+
+__global__ void k_rhs_levels(const __grid_constant__ RhsLevels R) {
+  pdl_start();
+  const long long bid = blockIdx.x;
+  int k = 0;
+  while (k + 1 < R.nlev && bid >= R.boff[k + 1]) ++k;
+  const long long idx = (bid - R.boff[k]) * blockDim.x + threadIdx.x;
+  if (idx >= R.nodes[k]) return;
+  const int top = R.nlev - 1;
+  const int n = R.n[k];
+  const long long cp = n + 1;
+  const int i = (int)(idx % cp), j = (int)((idx / cp) % cp), l = R.dim == 3 ? (int)(idx / (cp * cp)) : 0;
+  const bool bnd = i == 0 || i == n || j == 0 || j == n || (R.dim == 3 && (l == 0 || l == n));
+  double v;
+  if (k == top) {
+    v = bnd ? 0.0 : R.g[top][idx];
+    if (bnd) R.g[top][idx] = 0.0;
+  } else {
+    const long long st = R.n[top] / n, fp = R.n[top] + 1;
+    v = bnd ? 0.0 : R.g[top][((l * st) * fp + j * st) * fp + i * st];
+    R.g[k][idx] = v;
+  }
+  if (R.ff) ff_store(R.gf[k] + idx, ff_from_double(v));
+}
+
+}  // namespace
+
+cudaError_t launch_rhs_levels(int dim, int nlev, const LevelGeo* geo, double* const* g, double* const* gf, bool ff,
+                              cudaStream_t s) {
+  if (nlev < 1 || nlev > kMaxLevels) return cudaErrorInvalidValue;
+  RhsLevels R = {};
+  long long off = 0;
+  for (int k = 0; k < nlev; ++k) {
+    R.g[k] = g[k];
+    R.gf[k] = ff ? gf[k] : nullptr;
+    R.n[k] = geo[k].n;
+    R.nodes[k] = geo[k].nodes;
+    R.boff[k] = off;
+    off += (geo[k].nodes + 255) / 256;
+  }
+  R.boff[nlev] = off;
+  R.nlev = nlev;
+  R.dim = dim;
+  R.ff = ff ? 1 : 0;
+  if (off < 1 || off > 0x7fffffffll) return cudaErrorInvalidValue;
+  launch_k(k_rhs_levels, dim3((unsigned)off), 256, 0, s, R);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ff_from_f64(const double* src, double* dst_ff, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   launch_k(k_ff_from_f64, cdiv_u(n, 256), 256, 0, s, src, dst_ff, n);

@@ -399,6 +399,9 @@ cudaError_t launch_add_f32_ff(LevelGeo g, double* u_ff, const float* e32, cudaSt
 cudaError_t launch_level_start_ff(int dim, LevelGeo gc, const double* uc_ff, LevelGeo g, double* u_ff,
                                   const double* g_ff, double* b_ff, int kind, double a, float* r32, float* e32,
                                   float* d32, double e0, cudaStream_t s, const VarCoef* vc = nullptr);
+// every level's g (and its float-float copy gf, with ff) from the fine g, its boundary zeroed
+cudaError_t launch_rhs_levels(int dim, int nlev, const LevelGeo* geo, double* const* g, double* const* gf, bool ff,
+                              cudaStream_t s);
 // conversions (in place allowed)
 cudaError_t launch_ff_from_f64(const double* src, double* dst_ff, long long n, cudaStream_t s);
 cudaError_t launch_ff_to_f64(const double* src_ff, double* dst, long long n, cudaStream_t s);
