@@ -261,12 +261,6 @@ cudaError_t launch_add_f32(LevelGeo g, int dim, double* u, const float* e32, cud
 cudaError_t launch_nonlinear_rhs(int dim, LevelGeo g, const double* u, const double* gn, double* b, int kind,
                                  double a, cudaStream_t s);
 
-// coarse nodal g: gc(x) = gf(stride * x)
-cudaError_t launch_decimate(int dim, LevelGeo gf, const double* gsrc, LevelGeo gc, double* gdst, cudaStream_t s);
-
-// zero the boundary ring of a nodal array
-cudaError_t launch_zero_boundary(int dim, LevelGeo g, double* a, cudaStream_t s);
-
 // copy nodal array (same level)
 cudaError_t launch_copy(const double* src, double* dst, long long n, cudaStream_t s);
 

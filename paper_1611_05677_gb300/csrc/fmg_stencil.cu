@@ -512,18 +512,6 @@ __global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, l
   if (i < n) u[i] += (double)e[i];
 }
 
-__device__ __forceinline__ bool interior_of(long long idx, int n, int dim) {
-  const long long np = n + 1;
-  const int i = (int)(idx % np);
-  const int j = (int)((idx / np) % np);
-  if (i == 0 || i == n || j == 0 || j == n) return false;
-  if (dim == 3) {
-    const int l = (int)(idx / (np * np));
-    if (l == 0 || l == n) return false;
-  }
-  return true;
-}
-
 // b = w (g - f(u)) on the interior nodes, 0 on the boundary; one thread per node of row
 // (j[, l]) = (blockIdx.y[, blockIdx.z]), so no index division.
 __device__ __forceinline__ void k_nonlinear_rhs_body(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
@@ -541,25 +529,6 @@ __device__ __forceinline__ void k_nonlinear_rhs_body(const double* __restrict__ 
 
 __global__ void k_nonlinear_rhs(const double* __restrict__ u, const double* __restrict__ g, double* __restrict__ b,
                                 int n, int dim, int kind, double a, double w) { pdl_start(); k_nonlinear_rhs_body(u, g, b, n, dim, kind, a, w); }
-
-__global__ void k_decimate(const double* __restrict__ src, int nf, double* __restrict__ dst, int nc, int dim) {
-  pdl_start();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long cp = nc + 1;
-  const long long total = dim == 2 ? cp * cp : cp * cp * cp;
-  if (idx >= total) return;
-  const int st = nf / nc;
-  const long long fp = nf + 1;
-  const long long i = idx % cp, j = (idx / cp) % cp, l = idx / (cp * cp);
-  dst[idx] = src[((l * st) * fp + j * st) * fp + i * st];
-}
-
-__global__ void k_zero_boundary(double* __restrict__ a, long long nodes, int n, int dim) {
-  pdl_start();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nodes) return;
-  if (!interior_of(idx, n, dim)) a[idx] = 0.0;
-}
 
 __global__ void k_copy(const double* __restrict__ s, double* __restrict__ d, long long n) {
   pdl_start();
@@ -1025,16 +994,6 @@ cudaError_t launch_nonlinear_rhs(int dim, LevelGeo g, const double* u, const dou
   const double w = dim == 2 ? h * h : h * h * h;
   const unsigned gx = cdiv(g.n + 1, kBlock);
   launch_k(k_nonlinear_rhs, dim3(gx, g.n + 1, dim == 3 ? g.n + 1 : 1), kBlock, 0, s, u, gn, b, g.n, dim, kind, a, w);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_decimate(int dim, LevelGeo gf, const double* gsrc, LevelGeo gc, double* gdst, cudaStream_t s) {
-  launch_k(k_decimate, cdiv(gc.nodes, 256), 256, 0, s, gsrc, gf.n, gdst, gc.n, dim);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_zero_boundary(int dim, LevelGeo g, double* a, cudaStream_t s) {
-  launch_k(k_zero_boundary, cdiv(g.nodes, 256), 256, 0, s, a, g.nodes, g.n, dim);
   return cudaGetLastError();
 }
 
